@@ -1,0 +1,417 @@
+"""Benchmark of the Seele hot path on GB300: 1080p frames/s at 3M Gaussians.
+
+A step is one frame of the whole path -- preprocessing, compaction, depth
+sort, instance emission, tile sort, ranges and rasterization -- for one
+1920x1080 camera of the 3M-Gaussian unbounded-style synthetic scene (2.4M
+Gaussians in 64 dense clusters plus 0.6M on a radius 30-50 shell, SH degree 3,
+16x16 tiles).  Steps cycle over 8 orbit cameras.  The headline path is the
+contribution-aware rasterizer (Alg. 1, 2x2 groups) with the opacity-aware
+online filter (Eqn. 5); the plain path (Sec. 3.1) is timed beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With N > 1 (launched by torchrun) each rank renders its own cameras (views
+are independent: no collective on the data path); value = frames of all
+ranks / max-over-ranks time.  ``--impl reference`` times the FP64 CPU oracle
+as it stands on this host's cores, on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "1080p frames/s at 3M Gaussians vs plain path; fwd+bwd ms; % of roofline"
+UNIT = "frames/s"
+WORKLOAD = ("unbounded_3m: 3M Gaussians (2.4M in 64 clusters sigma 0.15 in [-3,3]^3 + 0.6M on a r 30-50 shell), "
+            "SH degree 3, 1920x1080, 16x16 tiles, 8 orbit cameras at r 5, seed 0")
+FP32_LANES_PER_SM = 128
+N_SM = 152
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            for r in csv.reader(io.StringIO(open(self.path).read())):
+                if len(r) >= 9:
+                    rows.append([x.strip() for x in r])
+            os.unlink(self.path)
+        except Exception:
+            return None
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 0, 1, None
+    import torch.distributed as dist
+    rank, local = int(os.environ["RANK"]), int(os.environ.get("LOCAL_RANK", "0"))
+    import torch
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return rank, local, ws, dist
+
+
+def _barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def _max_over_ranks(dist, v: float) -> float:
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _sum_over_ranks(dist, v: float) -> float:
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------- oracle --
+
+def _oracle_band(s64, cam, opts, y0, h, nthreads):
+    """Oracle frame restricted to rows [y0, y0 + h): the same camera with the
+    principal point shifted, so it renders exactly those rows of the frame."""
+    import oracle
+    band = dict(cam)
+    band["cy"] = float(cam["cy"]) - y0
+    band["height"] = h
+    t = time.perf_counter()
+    oracle.render(s64, band, opts, nthreads)
+    return time.perf_counter() - t
+
+
+def cpu_baseline(scene, cams, bands=4, nthreads=None):
+    """The FP64 oracle, as it stands, on all host cores: one full frame of
+    camera 0 rendered as ``bands`` horizontal bands (same arithmetic as one
+    frame; each band re-runs preprocessing, so this slightly favours the GPU)."""
+    import oracle
+    nthreads = nthreads or os.cpu_count()
+    s64 = oracle.Scene64.from_scene(scene)
+    opts = oracle.Options(cr=True, opacity_filter=True)
+    H = int(cams[0]["height"])
+    hb = H // bands
+    total = 0.0
+    for b in range(bands):
+        y0 = b * hb
+        total += _oracle_band(s64, cams[0], opts, y0, H - y0 if b == bands - 1 else hb, nthreads)
+    return {"value": 1.0 / total, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+            "sample": f"one full 1920x1080 frame (camera 0, contribution-aware + opacity filter) rendered as "
+                      f"{bands} horizontal bands by the FP64 C oracle with OpenMP; {total:.1f} s"}
+
+
+def run_reference(args):
+    rank, _, ws, dist = _dist()
+    if rank != 0:
+        return
+    import scenegen
+    import oracle
+    scene, cams = scenegen.unbounded_3m()
+    s64 = oracle.Scene64.from_scene(scene)
+    opts = oracle.Options(cr=True, opacity_filter=True)
+    nthreads = os.cpu_count()
+    bands = 4
+    H = int(cams[0]["height"])
+    hb = H // bands
+
+    def step(i):
+        cam = cams[(i // bands) % len(cams)]
+        b = i % bands
+        return _oracle_band(s64, cam, opts, b * hb, hb, nthreads)
+
+    for i in range(args.warmup):
+        step(i)
+    total = sum(step(args.warmup + i) for i in range(args.steps))
+    frames = args.steps / bands
+    value = frames / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "path": "CR 2x2 + opacity-aware filter",
+                                            "step": "one horizontal quarter band of a frame"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+                             "sample": f"each step renders one 1920x270 band of a frame; {args.steps} bands"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------------- GPU --
+
+def _timed_frames(r, cams, opts, steps, stream, cam_offset):
+    import torch
+    out = torch.empty(3 * cams[0]["width"] * cams[0]["height"], device=r.device)
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for i in range(steps):
+        r.set_cameras([cams[(cam_offset + i) % len(cams)]])
+        r.render(out=out, options=opts)
+    end.record(stream)
+    return start, end
+
+
+def _source_hash(*names):
+    h = hashlib.sha256()
+    for n in names:
+        h.update(open(os.path.join(ROOT, "paper_2503_05168_gb300", "csrc", n), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel: str, src_hash: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current source of that kernel."""
+    try:
+        t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        e = t.get(kernel)
+        if e and e.get("source_hash") == src_hash:
+            return e["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+def run_gpu(args):
+    import torch
+
+    import __graft_entry__
+    import scenegen
+    from paper_2503_05168_gb300 import Renderer
+
+    rank, local, ws, dist = _dist()
+    if rank == 0:
+        __graft_entry__.build()
+    _barrier(dist)
+    torch.cuda.set_device(local)
+    scene, cams = scenegen.unbounded_3m(n=args.n_gauss)
+    r = Renderer(local)
+    r.load_scene(scene)
+    stream = torch.cuda.current_stream()
+    cr_opts = r.make_options(mode="cr", opacity_filter=True, sync=False)
+    plain_opts = r.make_options(mode="plain", sync=False)
+
+    # warm-up: synchronous renders grow the instance capacity, then async ones
+    for opts in (cr_opts, plain_opts):
+        for i in range(max(args.warmup, 3)):
+            r.set_cameras([cams[(rank + i * ws) % len(cams)]])
+            r.render(mode="cr" if opts.mode else "plain", opacity_filter=bool(opts.opacity_filter))
+            r.render(options=opts)
+        r.synchronize()
+
+    def timed(opts):
+        _barrier(dist)
+        torch.cuda.synchronize()
+        s, e = _timed_frames(r, cams, opts, args.steps, stream, rank)
+        torch.cuda.synchronize()
+        r.synchronize()
+        _barrier(dist)
+        return s.elapsed_time(e) / 1000.0
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_cr = timed(cr_opts)
+    clock_info = clocks.stop()
+    t_plain = timed(plain_opts)
+    t_cr_max = _max_over_ranks(dist, t_cr)
+    t_plain_max = _max_over_ranks(dist, t_plain)
+    frames = args.steps * ws
+    fps = frames / t_cr_max
+    fps_plain = frames / t_plain_max
+
+    # per-stage device times (CUDA events inside the library, same stream)
+    stage = {}
+    n_prof = max(3, min(args.steps, 10))
+    for i in range(n_prof):
+        r.set_cameras([cams[(rank + i) % len(cams)]])
+        r.render(mode="cr", opacity_filter=True, profile=True)
+        for k, v in r.last_stats["stage_ms"].items():
+            stage[k] = stage.get(k, 0.0) + v / n_prof
+    kernels_per_frame = r.last_stats["n_kernels"]
+    n_vis, K = r.last_stats["n_visible"], r.last_stats["n_instances"]
+    stage_plain = {}
+    for i in range(n_prof):
+        r.set_cameras([cams[(rank + i) % len(cams)]])
+        r.render(mode="plain", profile=True)
+        for k, v in r.last_stats["stage_ms"].items():
+            stage_plain[k] = stage_plain.get(k, 0.0) + v / n_prof
+    # algorithmic work of the rasterizer (counting variant, untimed)
+    r.set_cameras([cams[rank % len(cams)]])
+    r.render(mode="cr", opacity_filter=True, count=True)
+    work = {k: r.last_stats[k] for k in ("leader_tests", "pairs_evaluated", "pairs_blended")}
+    work_K = r.last_stats["n_instances"]
+    work_vis = r.last_stats["n_visible"]
+
+    # quality: CR vs plain on the same frame
+    img_cr = r.render(mode="cr", opacity_filter=True).cpu().numpy().astype(np.float64)
+    img_pl = r.render(mode="plain").cpu().numpy().astype(np.float64)
+    mse = float(np.mean((img_cr - img_pl) ** 2))
+    psnr = 10 * math.log10(1.0 / mse) if mse > 0 else float("inf")
+
+    # roofline of the dominant stage
+    peaks = _peaks()
+    dom = max(stage, key=stage.get)
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    n_gauss = int(scene["means"].shape[0])
+    tile_passes = 2
+    stage_bytes = {
+        "preprocess": 16 * n_gauss + 4 * n_gauss + (32 + 192 + 60) * work_vis,
+        "compact": 4 * n_gauss + 8 * work_vis,
+        "depth_sort": (4 * 16 + 4) * work_vis,
+        "tile_scan": 12 * work_vis,
+        "emit": 16 * work_vis + 8 * work_K,
+        "tile_sort": (tile_passes * 16 + 4) * work_K,
+        "ranges": 4 * work_K,
+    }
+    if dom == "raster":
+        ops = 8 * (work["pairs_evaluated"] + work["leader_tests"]) + 7 * work["pairs_blended"]
+        achieved = ops / (stage[dom] / 1000.0) / 1e12
+        peak = N_SM * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": _traffic("raster_fwd", _source_hash("raster.cu")),
+                "kernel": "raster_fwd_kernel (CR 2x2)",
+                "note": f"FP32-pipe ops = 8 per exponent evaluation (leader tests and pixel pairs) + 7 per blended "
+                        f"pair; peak = {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz"}
+    else:
+        b = stage_bytes.get(dom, 0)
+        achieved = b / (stage[dom] / 1000.0) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "kernel": dom, "note": f"peak of {peak_src} (MEASURED_PEAKS hbm_gbs)"}
+
+    # end to end through the public API with host buffers: scene upload from
+    # pinned host memory, render, image read back into pinned host memory
+    pinned = {k: (torch.from_numpy(np.ascontiguousarray(v)).pin_memory() if isinstance(v, np.ndarray) else v)
+              for k, v in scene.items()}
+    host_img = torch.empty(3 * 1920 * 1080, dtype=torch.float32).pin_memory()
+    h2d = sum(v.numel() * v.element_size() for v in pinned.values() if isinstance(v, torch.Tensor))
+    d2h = host_img.numel() * 4
+    e2e_steps = max(2, min(args.steps, 5))
+    for i in range(1):
+        r.load_scene({k: (v.numpy() if isinstance(v, torch.Tensor) else v) for k, v in pinned.items()})
+        r.set_cameras([cams[rank % len(cams)]])
+        r.render(out=host_img.numpy(), mode="cr", opacity_filter=True)
+    _barrier(dist)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        r.load_scene({k: (v.numpy() if isinstance(v, torch.Tensor) else v) for k, v in pinned.items()})
+        r.set_cameras([cams[(rank + i) % len(cams)]])
+        r.render(out=host_img.numpy(), mode="cr", opacity_filter=True)
+    torch.cuda.synchronize()
+    t_e2e = _max_over_ranks(dist, time.perf_counter() - t0)
+    e2e = {"value": e2e_steps * ws / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(d2h), "steps": e2e_steps,
+           "what": "seele_load_scene(COPY from pinned host) + seele_render(out = pinned host image) per frame"}
+
+    line = {
+        "metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * t_cr_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "path": "contribution-aware (Alg. 1, 2x2 groups) + opacity-aware filter",
+                   "l2": "inputs larger than L2 (720 MB of Gaussian attributes per frame)",
+                   "parallelism": f"replicas x{ws} (cameras sharded, no collective)"},
+        "plain_fps": fps_plain, "speedup_vs_plain": fps / fps_plain, "psnr_cr_vs_plain_db": psnr,
+        "stage_ms": {k: round(v, 4) for k, v in stage.items()},
+        "stage_ms_plain": {k: round(v, 4) for k, v in stage_plain.items()},
+        "n_visible": n_vis, "n_instances": K, "raster_work": work,
+        "roofline": roof, "e2e": e2e,
+        "gpu_launches": int(kernels_per_frame * args.steps),
+        "clocks": clock_info,
+    }
+    # the CPU oracle as it stands, rank 0 at N = 1 only
+    if args.n_gauss != 3_000_000:
+        line["config"]["workload"] = line["config"]["workload"].replace("3M Gaussians", f"{args.n_gauss} Gaussians")
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(scene, cams)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    r.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="seele", choices=["seele", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-gauss", type=int, default=3_000_000,
+                    help="scene size (3M is the benchmark; smaller sizes are for profiling captures)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

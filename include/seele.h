@@ -1,0 +1,233 @@
+/*
+ * seele.h -- C ABI of the GB300 (sm_103a) implementation of the Seele
+ * rendering hot path (arxiv 2503.05168, "Seele: A Unified Acceleration
+ * Framework for Real-Time Gaussian Splatting on Mobile Devices").
+ *
+ * The library renders a set of 3D Gaussians (Sec. 3.1: centroid, covariance
+ * from scale and rotation, opacity, spherical-harmonic colour) tile by tile
+ * in three steps -- preprocessing, sorting, rasterization (Sec. 3.1) -- with
+ * the paper's two techniques as options: hybrid preprocessing (Sec. 3.3:
+ * view-cluster filter plus the opacity-aware online filter of Eqns. 3-5) and
+ * contribution-aware rasterization (Sec. 3.4, Algorithm 1).  It also
+ * differentiates the render for the fine-tuning of Sec. 3.5.
+ *
+ * Conventions shared by every call:
+ *   - No C++ exception crosses this boundary; every call returns a status.
+ *     On failure seele_last_error() describes the cause.
+ *   - All GPU work is enqueued on the context's stream (borrowed, never
+ *     destroyed by the library).  Pointers documented as "device" must be
+ *     device (or managed) memory of the context's device; "host or device"
+ *     pointers are classified with cudaPointerGetAttributes.
+ *   - Float tensors are float32, row-major, tightly packed.
+ *   - A context is not thread-safe: one host thread at a time.
+ *
+ * Scene layout (per Gaussian g, n Gaussians):
+ *   means[g*3 + i]            world position, i = x, y, z
+ *   log_scales[g*3 + i]       log of the per-axis standard deviation
+ *   quats[g*4 + i]            rotation quaternion (w, x, y, z), any norm > 0
+ *   opacity_logits[g]         opacity o = sigmoid(logit)
+ *   sh[(g*nc + k)*3 + c]      SH coefficient k = l*l + l + m (real basis,
+ *                             Condon-Shortley phase) of channel c,
+ *                             nc = (sh_degree + 1)^2
+ *   cluster_mask[g]           bit c set: g belongs to view cluster c; shared
+ *                             Gaussians carry every bit (Sec. 3.3)
+ *
+ * Camera model: x right, y down, z forward; X_cam = R x + t with
+ * world_to_cam = [R | t] row-major; u = fx X/Z + cx, v = fy Y/Z + cy in
+ * continuous pixel units; pixel (px, py) is sampled at (px + .5, py + .5).
+ * Output images are planar: for camera j, rgb[off_j*3 + c*H*W + y*W + x] and
+ * T[off_j + y*W + x] with off_j = sum_{i<j} W_i*H_i.
+ */
+#ifndef SEELE_H
+#define SEELE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct seele_ctx seele_ctx;
+
+typedef enum {
+    SEELE_OK = 0,
+    SEELE_ERR_ARG = 1,       /* invalid argument (null pointer, size, option) */
+    SEELE_ERR_STATE = 2,     /* call out of order (no scene, no cameras, no render) */
+    SEELE_ERR_CUDA = 3,      /* a CUDA runtime call failed */
+    SEELE_ERR_CAPACITY = 4,  /* tile-instance capacity exceeded (async mode only) */
+    SEELE_ERR_TIMEOUT = 5,   /* a bounded device spin-wait gave up */
+    SEELE_ERR_OOM = 6        /* device allocation failed */
+} seele_status;
+
+enum { SEELE_SCENE_COPY = 0, SEELE_SCENE_BORROW = 1 };
+
+/* Scene description.  COPY: the library copies the attributes (host or device
+ * pointers) into its own layout and owns that copy.  BORROW: the pointers are
+ * device memory owned by the caller, must stay valid and unchanged in size
+ * until the next seele_load_scene or seele_destroy, and are re-read by every
+ * render (their contents may change between renders, as in training). */
+typedef struct {
+    int64_t n;                    /* number of Gaussians, 1 <= n, n * cameras < 2^31 */
+    int32_t sh_degree;            /* 0..3 */
+    int32_t flags;                /* SEELE_SCENE_COPY or SEELE_SCENE_BORROW */
+    const float* means;           /* [n][3] */
+    const float* log_scales;      /* [n][3] */
+    const float* quats;           /* [n][4] */
+    const float* opacity_logits;  /* [n] */
+    const float* sh;              /* [n][(sh_degree+1)^2][3] */
+    const uint32_t* cluster_mask; /* [n] or NULL (no view clusters) */
+    int32_t n_clusters;           /* 0..32; centroids required if > 0 */
+    float pos_scale;              /* position normalisation s of the cluster features */
+    const float* centroids;       /* host, [n_clusters][6] = (x / s, view dir) */
+} seele_scene_desc;
+
+/* One camera (Sec. 3.1 "Given a camera pose and a view direction"). */
+typedef struct {
+    float world_to_cam[12];       /* [R | t], row-major 3x4 */
+    float fx, fy, cx, cy;         /* pinhole intrinsics, pixels */
+    int32_t width, height;        /* 1..16384 */
+    float near_z;                 /* Gaussians with Z <= near_z are culled (0.2) */
+} seele_camera;
+
+enum { SEELE_MODE_PLAIN = 0, SEELE_MODE_CR = 1 };
+
+/* Render flags */
+enum {
+    SEELE_RENDER_ASYNC = 1,       /* do not synchronise; see seele_render */
+    SEELE_RENDER_PROFILE = 2,     /* time each stage with CUDA events into seele_stats.stage_ms
+                                     (synchronous renders only) */
+    SEELE_RENDER_COUNT = 4        /* count the rasterizer's work into seele_stats (slower
+                                     variant; synchronous renders only) */
+};
+
+/* Stages timed by SEELE_RENDER_PROFILE, in launch order. */
+enum {
+    SEELE_STAGE_PREPROCESS = 0,   /* scene repack (BORROW) + per-(camera, Gaussian) preprocessing */
+    SEELE_STAGE_COMPACT = 1,      /* visible-record compaction */
+    SEELE_STAGE_DEPTH_SORT = 2,   /* histogram + 4 radix passes on fp32 depth */
+    SEELE_STAGE_TILE_SCAN = 3,    /* instance offsets in depth order */
+    SEELE_STAGE_EMIT = 4,         /* tile instances */
+    SEELE_STAGE_TILE_SORT = 5,    /* histogram + radix passes on the tile id */
+    SEELE_STAGE_RANGES = 6,       /* per-tile list ranges */
+    SEELE_STAGE_RASTER = 7,       /* blending (Eqns. 1-2 / Alg. 1) */
+    SEELE_NUM_STAGES = 8
+};
+
+/* Render options.  seele_default_options fills the paper's constants. */
+typedef struct {
+    int32_t mode;                 /* PLAIN (Sec. 3.1) or CR (Alg. 1) */
+    int32_t group_w, group_h;     /* CR pixel group: 2x2 (default), 1x1, 2x4 */
+    int32_t tile_w, tile_h;       /* 16x16 (default) */
+    int32_t opacity_filter;       /* 1: support min(2 ln(o/alpha_theta), 9) (Eqn. 5) */
+    int32_t cluster_filter;       /* 1: render only the selected view clusters (Sec. 3.3) */
+    int32_t n_neighbors;          /* M of Sec. 3.3 (3) */
+    float alpha_min;              /* alpha_theta, 1/255 */
+    float alpha_max;              /* alpha clamp, 0.99 */
+    float t_stop;                 /* Gamma_theta, 1e-4 */
+    int32_t flags;                /* SEELE_RENDER_* */
+} seele_options;
+
+/* Per-render statistics (all cameras of the call). */
+typedef struct {
+    int64_t n_visible;            /* (camera, Gaussian) pairs that reach binning */
+    int64_t n_instances;          /* tile instances K */
+    int64_t capacity;             /* instance capacity after the call */
+    int32_t retries;              /* renders repeated after a capacity growth */
+    int32_t n_kernels;            /* kernel launches of the last attempt */
+    float stage_ms[8];            /* SEELE_RENDER_PROFILE: device time per stage, else 0 */
+    int64_t leader_tests;         /* SEELE_RENDER_COUNT: Alg. 1 leader tests (CR only) */
+    int64_t pairs_evaluated;      /* SEELE_RENDER_COUNT: (pixel, Gaussian) alphas evaluated */
+    int64_t pairs_blended;        /* SEELE_RENDER_COUNT: pairs accumulated into the pixel */
+} seele_stats;
+
+/* Gradients, caller-owned device buffers in the scene layout; overwritten. */
+typedef struct {
+    float* means;                 /* [n][3] */
+    float* log_scales;            /* [n][3] */
+    float* quats;                 /* [n][4] */
+    float* opacity_logits;        /* [n] */
+    float* sh;                    /* [n][nc][3] */
+} seele_grads;
+
+/* Fills *opt with: PLAIN, 2x2 group, 16x16 tiles, filters off, M = 3,
+ * alpha_theta = 1/255 (Sec. 3.1), clamp 0.99, Gamma_theta = 1e-4, flags 0. */
+void seele_default_options(seele_options* opt);
+
+/* Creates a context on CUDA device `device` that enqueues on `cuda_stream`
+ * (a cudaStream_t; NULL = legacy default stream).  *out receives the context,
+ * owned by the caller and released with seele_destroy. */
+seele_status seele_create(seele_ctx** out, int device, void* cuda_stream);
+
+/* Releases every device buffer of the context.  NULL is ignored. */
+void seele_destroy(seele_ctx* ctx);
+
+/* Replaces the stream used by subsequent calls (borrowed). */
+seele_status seele_set_stream(seele_ctx* ctx, void* cuda_stream);
+
+/* Loads (COPY) or references (BORROW) a scene; see seele_scene_desc.
+ * Invalidates any previous render state. */
+seele_status seele_load_scene(seele_ctx* ctx, const seele_scene_desc* scene);
+
+/* Sets n >= 1 cameras (host array, copied).  With view clusters loaded, also
+ * runs the runtime cluster selection of Sec. 3.3 on the host: the nearest
+ * centroid to the camera feature (position / s, view direction) and the
+ * opt-independent M = n_neighbors(3) centroids nearest to it. */
+seele_status seele_set_cameras(seele_ctx* ctx, const seele_camera* cams, int32_t n);
+
+/* Renders every camera set by seele_set_cameras.
+ *   out_rgb  host or device, [sum_j 3 W_j H_j] planar per camera (see top)
+ *   out_T    host, device or NULL, [sum_j W_j H_j] final transmittance
+ *   stats    host or NULL
+ * Without SEELE_RENDER_ASYNC the call synchronises the stream, grows the
+ * instance capacity and re-renders when it was exceeded, and returns the
+ * device status.  With SEELE_RENDER_ASYNC it returns after enqueueing (device
+ * output pointers only); a capacity overflow then leaves the outputs
+ * undefined and is reported by seele_synchronize, after which the next render
+ * uses the grown capacity. */
+seele_status seele_render(seele_ctx* ctx, const seele_options* opt, float* out_rgb, float* out_T,
+                          seele_stats* stats);
+
+/* Waits for the stream and returns the device status of the work enqueued
+ * since the previous check (CAPACITY, TIMEOUT or OK). */
+seele_status seele_synchronize(seele_ctx* ctx);
+
+/* Gradient of sum(dL_drgb * rgb) for the last seele_render (same scene,
+ * cameras and options; else SEELE_ERR_STATE).  dL_drgb is device memory in
+ * the out_rgb layout.  Skip and stop decisions of the forward pass are held
+ * fixed (Sec. 3.5: HP and CR "do not participate in gradient descent");
+ * per-pixel transmittance is recomputed back to front, not stored. */
+seele_status seele_render_backward(seele_ctx* ctx, const float* dL_drgb, const seele_grads* grads);
+
+/* Read-only views of the last render's intermediates (device pointers owned
+ * by the context, valid until the next load/render).  For tests and tools. */
+typedef struct {
+    int64_t n_records;            /* cameras * n */
+    int64_t n_visible;
+    int64_t n_instances;
+    int64_t n_tiles;              /* tiles over all cameras */
+    const uint32_t* inst_tile;    /* [n_instances] global tile id, sorted */
+    const uint32_t* inst_record;  /* [n_instances] record id = camera * n + g */
+    const uint32_t* tile_ranges;  /* [n_tiles][2] = [start, end) into the lists */
+    const uint32_t* tiles_touched;/* [n_records] 0 = culled */
+    const uint32_t* rect;         /* [n_records][2] tile box, packed x | y << 16 */
+    const float* records;         /* [n_records][12] raster record: u, v,
+                                     -A/2*log2e, -B*log2e, -C/2*log2e (conic
+                                     [[A,B],[B,C]] = Sigma'^-1), log2 o, e_thr,
+                                     0, r, g, b, 0; a pixel at offset (dx, dy)
+                                     takes the Gaussian iff
+                                     e = cA dx^2 + cB dx dy + cC dy^2 + log2 o
+                                     >= e_thr, with alpha = min(clamp, 2^e) */
+    const float* depth;           /* [n_records] camera-space Z */
+    const uint32_t* n_contrib;    /* [sum W*H] 1 + last blended list position */
+} seele_debug_view;
+
+seele_status seele_get_debug_view(const seele_ctx* ctx, seele_debug_view* out);
+
+/* Message of the last failed call on this context (library-owned). */
+const char* seele_last_error(const seele_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SEELE_H */

@@ -1,0 +1,236 @@
+"""GB300 (sm_103a) implementation of the Seele rendering hot path (arxiv 2503.05168).
+
+Thin Python binding over the C ABI in ``include/seele.h``: every step of the
+path runs in the CUDA kernels of ``libseele.so``; this module only marshals
+arguments.  PyTorch supplies device memory and the stream.
+
+    from paper_2503_05168_gb300 import Renderer
+    r = Renderer()
+    r.load_scene(scene)            # dict of arrays (numpy: host, torch: device)
+    r.set_cameras(cameras)         # list of dicts (world_to_cam, fx, fy, cx, cy, width, height)
+    img = r.render(mode="cr")      # flat planar float32 CUDA tensor, all cameras
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _abi
+from ._abi import SeeleError, lib
+
+__all__ = ["Renderer", "SeeleError", "lib", "default_options", "build"]
+
+
+def build(force: bool = False) -> str:
+    from .builder import build as _b
+    return _b(force=force)
+
+
+def default_options() -> _abi.Options:
+    o = _abi.Options()
+    lib().seele_default_options(ctypes.byref(o))
+    return o
+
+
+_CUDART = None
+
+
+def _cudart():
+    """The CUDA runtime already loaded by torch (used for debug copies only)."""
+    global _CUDART
+    if _CUDART is None:
+        for name in ("libcudart.so.13", "libcudart.so", "/usr/local/cuda/lib64/libcudart.so"):
+            try:
+                _CUDART = ctypes.CDLL(name)
+                break
+            except OSError:
+                continue
+        if _CUDART is None:
+            raise RuntimeError("CUDA runtime library not found")
+        _CUDART.cudaMemcpy.restype = ctypes.c_int
+        _CUDART.cudaMemcpy.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]
+    return _CUDART
+
+
+def _ptr(x):
+    """Data pointer of a numpy array or torch tensor (None passes through)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+class Renderer:
+    """One library context on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        import torch
+        self._torch = torch
+        self.device = torch.device("cuda", device)
+        torch.cuda.init()
+        h = ctypes.c_void_p()
+        st = lib().seele_create(ctypes.byref(h), device, ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream))
+        if st != 0:
+            raise SeeleError(st, "seele_create failed")
+        self._h = h
+        self._keep = []
+        self.cameras = []
+        self.n = 0
+        self.sh_degree = 0
+        self.last_stats = None
+
+    # -- plumbing -----------------------------------------------------------
+    def _check(self, st):
+        if st != 0:
+            raise SeeleError(st, lib().seele_last_error(self._h).decode(errors="replace"))
+
+    def _sync_stream(self):
+        s = self._torch.cuda.current_stream(self.device).cuda_stream
+        self._check(lib().seele_set_stream(self._h, ctypes.c_void_p(s)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().seele_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- scene and cameras ----------------------------------------------------
+    def load_scene(self, scene: dict, borrow: bool = False):
+        """``scene``: means [n,3], log_scales [n,3], quats [n,4], opacity_logits [n],
+        sh [n,nc,3] (float32), sh_degree, optional cluster_mask [n] uint32,
+        centroids [C,6], pos_scale.  numpy arrays are host memory, torch CUDA
+        tensors device memory.  ``borrow`` keeps references instead of copying
+        (device tensors only)."""
+        torch = self._torch
+
+        def prep(a, dtype):
+            if a is None:
+                return None
+            if isinstance(a, torch.Tensor):
+                return a.contiguous() if a.dtype == dtype else a.to(dtype).contiguous()
+            return np.ascontiguousarray(a, dtype=np.float32 if dtype == torch.float32 else np.uint32)
+
+        arrs = {k: prep(scene.get(k), torch.float32) for k in ("means", "log_scales", "quats", "opacity_logits", "sh")}
+        mask = None
+        m = scene.get("cluster_mask")
+        if m is not None:
+            mask = m.contiguous() if isinstance(m, torch.Tensor) else np.ascontiguousarray(m, dtype=np.uint32)
+        cen = scene.get("centroids")
+        cen = None if cen is None else np.ascontiguousarray(cen, dtype=np.float32)
+        n = int(arrs["means"].shape[0])
+        d = _abi.SceneDesc()
+        d.n = n
+        d.sh_degree = int(scene["sh_degree"])
+        d.flags = _abi.SCENE_BORROW if borrow else _abi.SCENE_COPY
+        d.means, d.log_scales, d.quats = _ptr(arrs["means"]), _ptr(arrs["log_scales"]), _ptr(arrs["quats"])
+        d.opacity_logits, d.sh = _ptr(arrs["opacity_logits"]), _ptr(arrs["sh"])
+        d.cluster_mask = _ptr(mask)
+        d.n_clusters = 0 if cen is None else int(cen.shape[0])
+        d.pos_scale = float(scene.get("pos_scale", 1.0))
+        d.centroids = _ptr(cen)
+        self._sync_stream()
+        self._check(lib().seele_load_scene(self._h, ctypes.byref(d)))
+        self._keep = [arrs, mask, cen] if borrow else []
+        self.n = n
+        self.sh_degree = d.sh_degree
+
+    def set_cameras(self, cams):
+        arr = (_abi.Camera * len(cams))()
+        for i, c in enumerate(cams):
+            w2c = np.asarray(c["world_to_cam"], dtype=np.float64).reshape(3, 4)
+            arr[i].world_to_cam[:] = [float(v) for v in w2c.reshape(-1)]
+            arr[i].fx, arr[i].fy = float(c["fx"]), float(c["fy"])
+            arr[i].cx, arr[i].cy = float(c["cx"]), float(c["cy"])
+            arr[i].width, arr[i].height = int(c["width"]), int(c["height"])
+            arr[i].near_z = float(c.get("near", 0.2))
+        self._check(lib().seele_set_cameras(self._h, arr, len(cams)))
+        self.cameras = [dict(width=int(c["width"]), height=int(c["height"])) for c in cams]
+
+    @property
+    def n_pixels(self):
+        return sum(c["width"] * c["height"] for c in self.cameras)
+
+    # -- rendering -----------------------------------------------------------
+    @staticmethod
+    def make_options(mode="plain", group=(2, 2), tile=(16, 16), opacity_filter=False, cluster_filter=False,
+                     n_neighbors=3, sync=True, profile=False, count=False, **kw) -> _abi.Options:
+        o = default_options()
+        o.mode = _abi.MODE_CR if mode == "cr" else _abi.MODE_PLAIN
+        o.group_w, o.group_h = group
+        o.tile_w, o.tile_h = tile
+        o.opacity_filter = int(bool(opacity_filter))
+        o.cluster_filter = int(bool(cluster_filter))
+        o.n_neighbors = int(n_neighbors)
+        for k in ("alpha_min", "alpha_max", "t_stop"):
+            if k in kw:
+                setattr(o, k, float(kw[k]))
+        o.flags = ((0 if sync else _abi.RENDER_ASYNC) | (_abi.RENDER_PROFILE if profile else 0) |
+                   (_abi.RENDER_COUNT if count else 0))
+        return o
+
+    def render(self, out=None, out_T=None, options: _abi.Options | None = None, **kw):
+        """Renders every camera; returns the flat planar RGB buffer (``out`` if given).
+
+        ``out``/``out_T`` may be CUDA tensors or host (numpy / CPU torch) buffers."""
+        torch = self._torch
+        o = options if options is not None else self.make_options(**kw)
+        if out is None:
+            out = torch.empty(3 * self.n_pixels, dtype=torch.float32, device=self.device)
+        st = _abi.Stats()
+        self._sync_stream()
+        self._check(lib().seele_render(self._h, ctypes.byref(o), ctypes.c_void_p(_ptr(out)),
+                                       ctypes.c_void_p(_ptr(out_T)) if out_T is not None else None,
+                                       ctypes.byref(st)))
+        self.last_stats = dict(n_visible=st.n_visible, n_instances=st.n_instances, capacity=st.capacity,
+                               retries=st.retries, n_kernels=st.n_kernels,
+                               stage_ms=dict(zip(_abi.STAGES, list(st.stage_ms))),
+                               leader_tests=st.leader_tests, pairs_evaluated=st.pairs_evaluated,
+                               pairs_blended=st.pairs_blended)
+        return out
+
+    def synchronize(self):
+        self._check(lib().seele_synchronize(self._h))
+
+    def images(self, flat):
+        """Splits a flat planar buffer into per-camera [3, H, W] views."""
+        res, off = [], 0
+        for c in self.cameras:
+            k = 3 * c["width"] * c["height"]
+            res.append(flat[off:off + k].reshape(3, c["height"], c["width"]))
+            off += k
+        return res
+
+    def debug_view(self) -> dict:
+        """Copies of the last render's intermediates (CUDA tensors)."""
+        torch = self._torch
+        v = _abi.DebugView()
+        self._check(lib().seele_get_debug_view(self._h, ctypes.byref(v)))
+
+        def dev(ptr, count, dtype):
+            if count == 0:
+                return torch.empty(0, dtype=dtype, device=self.device)
+            out = torch.empty(count, dtype=dtype, device=self.device)
+            torch.cuda.current_stream(self.device).synchronize()
+            res = _cudart().cudaMemcpy(ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(ptr),
+                                       ctypes.c_size_t(count * out.element_size()), 3)  # device to device
+            if int(res) != 0:
+                raise RuntimeError(f"cudaMemcpy failed: {res}")
+            return out
+
+        R, K, T = v.n_records, v.n_instances, v.n_tiles
+        i32 = torch.int32
+        return dict(
+            n_records=R, n_visible=v.n_visible, n_instances=K, n_tiles=T,
+            inst_tile=dev(v.inst_tile, K, i32), inst_record=dev(v.inst_record, K, i32),
+            tile_ranges=dev(v.tile_ranges, 2 * T, i32).reshape(T, 2),
+            tiles_touched=dev(v.tiles_touched, R, i32), rect=dev(v.rect, 2 * R, i32).reshape(R, 2),
+            records=dev(v.records, 12 * R, torch.float32).reshape(R, 12), depth=dev(v.depth, R, torch.float32),
+            n_contrib=dev(v.n_contrib, self.n_pixels, i32),
+        )

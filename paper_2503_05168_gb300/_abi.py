@@ -1,0 +1,101 @@
+"""ctypes mirror of include/seele.h (structs, enums, prototypes).
+
+Loading fails loudly when libseele.so is missing: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libseele.so")
+
+SEELE_OK = 0
+STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_STATE", 3: "ERR_CUDA", 4: "ERR_CAPACITY", 5: "ERR_TIMEOUT",
+                6: "ERR_OOM"}
+SCENE_COPY, SCENE_BORROW = 0, 1
+MODE_PLAIN, MODE_CR = 0, 1
+RENDER_ASYNC = 1
+RENDER_PROFILE = 2
+RENDER_COUNT = 4
+STAGES = ("preprocess", "compact", "depth_sort", "tile_scan", "emit", "tile_sort", "ranges", "raster")
+
+P = ctypes.c_void_p
+
+
+class SceneDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("sh_degree", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("means", P), ("log_scales", P), ("quats", P), ("opacity_logits", P), ("sh", P),
+                ("cluster_mask", P), ("n_clusters", ctypes.c_int32), ("pos_scale", ctypes.c_float),
+                ("centroids", P)]
+
+
+class Camera(ctypes.Structure):
+    _fields_ = [("world_to_cam", ctypes.c_float * 12), ("fx", ctypes.c_float), ("fy", ctypes.c_float),
+                ("cx", ctypes.c_float), ("cy", ctypes.c_float), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32), ("near_z", ctypes.c_float)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("group_w", ctypes.c_int32), ("group_h", ctypes.c_int32),
+                ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("opacity_filter", ctypes.c_int32),
+                ("cluster_filter", ctypes.c_int32), ("n_neighbors", ctypes.c_int32),
+                ("alpha_min", ctypes.c_float), ("alpha_max", ctypes.c_float), ("t_stop", ctypes.c_float),
+                ("flags", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_visible", ctypes.c_int64), ("n_instances", ctypes.c_int64), ("capacity", ctypes.c_int64),
+                ("retries", ctypes.c_int32), ("n_kernels", ctypes.c_int32), ("stage_ms", ctypes.c_float * 8),
+                ("leader_tests", ctypes.c_int64), ("pairs_evaluated", ctypes.c_int64),
+                ("pairs_blended", ctypes.c_int64)]
+
+
+class Grads(ctypes.Structure):
+    _fields_ = [("means", P), ("log_scales", P), ("quats", P), ("opacity_logits", P), ("sh", P)]
+
+
+class DebugView(ctypes.Structure):
+    _fields_ = [("n_records", ctypes.c_int64), ("n_visible", ctypes.c_int64), ("n_instances", ctypes.c_int64),
+                ("n_tiles", ctypes.c_int64), ("inst_tile", P), ("inst_record", P), ("tile_ranges", P),
+                ("tiles_touched", P), ("rect", P), ("records", P), ("depth", P), ("n_contrib", P)]
+
+
+# name -> (restype, argtypes); the ABI test checks this table against the header
+PROTOTYPES = {
+    "seele_default_options": (None, [ctypes.POINTER(Options)]),
+    "seele_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, P]),
+    "seele_destroy": (None, [P]),
+    "seele_set_stream": (ctypes.c_int, [P, P]),
+    "seele_load_scene": (ctypes.c_int, [P, ctypes.POINTER(SceneDesc)]),
+    "seele_set_cameras": (ctypes.c_int, [P, ctypes.POINTER(Camera), ctypes.c_int32]),
+    "seele_render": (ctypes.c_int, [P, ctypes.POINTER(Options), P, P, ctypes.POINTER(Stats)]),
+    "seele_synchronize": (ctypes.c_int, [P]),
+    "seele_render_backward": (ctypes.c_int, [P, P, ctypes.POINTER(Grads)]),
+    "seele_get_debug_view": (ctypes.c_int, [P, ctypes.POINTER(DebugView)]),
+    "seele_last_error": (ctypes.c_char_p, [P]),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_2503_05168_gb300.build() "
+                               "(there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in PROTOTYPES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class SeeleError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status

@@ -1,0 +1,649 @@
+// api.cu -- the C ABI of include/seele.h: context, scene and camera state,
+// workspace management and the per-frame kernel sequence.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "seele.h"
+#include "kernels.h"
+
+using namespace seele;
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+constexpr int kMaxCams = 4096;
+constexpr int kHistPasses = 4;
+
+}  // namespace
+
+struct seele_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+
+    // scene
+    bool has_scene = false;
+    int64_t n = 0;
+    int sh_degree = 0;
+    int scene_flags = 0;
+    seele_scene_desc borrowed{};
+    DevBuf pos_logit, quat, log_scale, sh, mask, staging;
+    bool has_mask = false;
+    int n_clusters = 0;
+    std::vector<double> centroids;
+    double pos_scale = 1.0;
+
+    // cameras
+    std::vector<seele_camera> cams;
+    std::vector<CamDev> camdev;
+    DevBuf cams_dev;
+
+    // frame workspace
+    DevBuf rec, rect, tiles, depth, visk[2], visv[2], offs, instk[2], instv[2], ranges, status, hist, lookback, T,
+        nc, rgb_tmp;
+    size_t lookback_entries = 0;
+    DeviceStatus* h_status = nullptr;  // pinned mirror of the device status
+    cudaEvent_t ev[SEELE_NUM_STAGES + 1] = {};
+    uint64_t capacity = 0;
+    uint32_t epoch = 1;
+    bool status_pending = false;
+
+    // last render
+    bool rendered = false;
+    seele_options last_opt{};
+    int inst_final = 0;
+    uint32_t n_tiles_total = 0;
+    uint64_t n_pix_total = 0;
+    FrameParams last_fp{};
+};
+
+namespace {
+
+seele_status fail(seele_ctx* c, seele_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return s;
+}
+
+#define SEELE_CUDA(ctx, call)                                                                              \
+    do {                                                                                                   \
+        cudaError_t e_ = (call);                                                                           \
+        if (e_ != cudaSuccess) {                                                                           \
+            (void)cudaGetLastError();                                                                      \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? SEELE_ERR_OOM : SEELE_ERR_CUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                                \
+        }                                                                                                  \
+    } while (0)
+
+#define SEELE_LAUNCHED(ctx) SEELE_CUDA(ctx, cudaGetLastError())
+
+cudaError_t ensure(DevBuf& b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return cudaSuccess;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e == cudaSuccess) b.bytes = bytes;
+    return e;
+}
+
+void release(DevBuf& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+T* ptr(DevBuf& b) {
+    return static_cast<T*>(b.p);
+}
+
+// Runtime cluster selection (Sec. 3.3 "Algorithm"): nearest centroid to the
+// camera feature (position / s, unit viewing direction), then the M centroids
+// nearest to that centroid; ties go to the lower index.
+uint32_t select_clusters(const seele_ctx* c, const seele_camera& cam, int M) {
+    if (c->n_clusters <= 0) return 0xffffffffu;
+    const float* w = cam.world_to_cam;
+    double R[9] = {w[0], w[1], w[2], w[4], w[5], w[6], w[8], w[9], w[10]};
+    double t[3] = {w[3], w[7], w[11]};
+    double pos[3];
+    for (int i = 0; i < 3; ++i) pos[i] = -(R[i] * t[0] + R[3 + i] * t[1] + R[6 + i] * t[2]);
+    double f[6] = {pos[0] / c->pos_scale, pos[1] / c->pos_scale, pos[2] / c->pos_scale, R[6], R[7], R[8]};
+    const int C = c->n_clusters;
+    auto dist2 = [&](const double* a, const double* b) {
+        double s = 0;
+        for (int i = 0; i < 6; ++i) s += (a[i] - b[i]) * (a[i] - b[i]);
+        return s;
+    };
+    int best = 0;
+    double bd = INFINITY;
+    for (int k = 0; k < C; ++k) {
+        double d = dist2(f, &c->centroids[6 * k]);
+        if (d < bd) {
+            bd = d;
+            best = k;
+        }
+    }
+    uint32_t bits = 1u << best;
+    for (int pick = 0; pick < M && pick < C - 1; ++pick) {
+        int arg = -1;
+        double ad = INFINITY;
+        for (int k = 0; k < C; ++k) {
+            if (bits >> k & 1u) continue;
+            double d = dist2(&c->centroids[6 * best], &c->centroids[6 * k]);
+            if (d < ad) {
+                ad = d;
+                arg = k;
+            }
+        }
+        bits |= 1u << arg;
+    }
+    return bits;
+}
+
+bool group_supported(int gw, int gh) {
+    return (gw == 2 && gh == 2) || (gw == 1 && gh == 1) || (gw == 2 && gh == 4);
+}
+
+int bits_for(uint64_t v) {
+    int b = 0;
+    while (v) {
+        ++b;
+        v >>= 1;
+    }
+    return b;
+}
+
+}  // namespace
+
+extern "C" {
+
+void seele_default_options(seele_options* o) {
+    if (!o) return;
+    o->mode = SEELE_MODE_PLAIN;
+    o->group_w = 2;
+    o->group_h = 2;
+    o->tile_w = 16;
+    o->tile_h = 16;
+    o->opacity_filter = 0;
+    o->cluster_filter = 0;
+    o->n_neighbors = 3;
+    o->alpha_min = 1.0f / 255.0f;
+    o->alpha_max = 0.99f;
+    o->t_stop = 1e-4f;
+    o->flags = 0;
+}
+
+seele_status seele_create(seele_ctx** out, int device, void* cuda_stream) {
+    if (!out) return SEELE_ERR_ARG;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+        (void)cudaGetLastError();
+        return SEELE_ERR_ARG;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return SEELE_ERR_CUDA;
+    seele_ctx* c = new (std::nothrow) seele_ctx();
+    if (!c) return SEELE_ERR_OOM;
+    c->device = device;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (cudaMallocHost(&c->h_status, sizeof(DeviceStatus)) != cudaSuccess) {
+        delete c;
+        return SEELE_ERR_OOM;
+    }
+    std::memset(c->h_status, 0, sizeof(DeviceStatus));
+    *out = c;
+    return SEELE_OK;
+}
+
+void seele_destroy(seele_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    DevBuf* all[] = {&c->pos_logit, &c->quat, &c->log_scale, &c->sh, &c->mask, &c->staging, &c->cams_dev,
+                     &c->rec, &c->rect, &c->tiles, &c->depth, &c->visk[0], &c->visk[1], &c->visv[0],
+                     &c->visv[1], &c->offs, &c->instk[0], &c->instk[1], &c->instv[0], &c->instv[1],
+                     &c->ranges, &c->status, &c->hist, &c->lookback, &c->T, &c->nc, &c->rgb_tmp};
+    for (DevBuf* b : all) release(*b);
+    if (c->h_status) cudaFreeHost(c->h_status);
+    for (cudaEvent_t e : c->ev)
+        if (e) cudaEventDestroy(e);
+    delete c;
+}
+
+seele_status seele_set_stream(seele_ctx* c, void* cuda_stream) {
+    if (!c) return SEELE_ERR_ARG;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    return SEELE_OK;
+}
+
+const char* seele_last_error(const seele_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+seele_status seele_load_scene(seele_ctx* c, const seele_scene_desc* d) {
+    if (!c) return SEELE_ERR_ARG;
+    if (!d) return fail(c, SEELE_ERR_ARG, "scene descriptor is NULL");
+    if (d->n < 1 || d->n >= (int64_t)1 << 31) return fail(c, SEELE_ERR_ARG, "n = %lld out of range", (long long)d->n);
+    if (d->sh_degree < 0 || d->sh_degree > 3) return fail(c, SEELE_ERR_ARG, "sh_degree must be 0..3");
+    if (!d->means || !d->log_scales || !d->quats || !d->opacity_logits || !d->sh)
+        return fail(c, SEELE_ERR_ARG, "scene attribute pointer is NULL");
+    if (d->flags != SEELE_SCENE_COPY && d->flags != SEELE_SCENE_BORROW)
+        return fail(c, SEELE_ERR_ARG, "flags must be COPY or BORROW");
+    if (d->n_clusters < 0 || d->n_clusters > 32) return fail(c, SEELE_ERR_ARG, "n_clusters must be 0..32");
+    if (d->n_clusters > 0 && (!d->centroids || !(d->pos_scale > 0)))
+        return fail(c, SEELE_ERR_ARG, "centroids and a positive pos_scale are required with clusters");
+    SEELE_CUDA(c, cudaSetDevice(c->device));
+    c->has_scene = false;
+    c->rendered = false;
+    const int64_t n = d->n;
+    const int nc = (d->sh_degree + 1) * (d->sh_degree + 1);
+    const int planes = (3 * nc + 3) / 4;
+    SEELE_CUDA(c, ensure(c->pos_logit, 16 * n));
+    SEELE_CUDA(c, ensure(c->quat, 16 * n));
+    SEELE_CUDA(c, ensure(c->log_scale, 16 * n));
+    SEELE_CUDA(c, ensure(c->sh, 16 * n * planes));
+    c->has_mask = d->cluster_mask != nullptr;
+    if (d->flags == SEELE_SCENE_BORROW) {
+        const void* ps[] = {d->means, d->log_scales, d->quats, d->opacity_logits, d->sh};
+        for (const void* p : ps)
+            if (!is_device_ptr(p)) return fail(c, SEELE_ERR_ARG, "BORROW needs device pointers");
+        if (d->cluster_mask && !is_device_ptr(d->cluster_mask))
+            return fail(c, SEELE_ERR_ARG, "BORROW needs a device cluster_mask");
+        c->borrowed = *d;
+    } else {
+        // attributes that live on the host go through one device staging area
+        const float* src[5] = {d->means, d->log_scales, d->quats, d->opacity_logits, d->sh};
+        const size_t cnt[5] = {(size_t)n * 3, (size_t)n * 3, (size_t)n * 4, (size_t)n, (size_t)n * nc * 3};
+        size_t stage_floats = 0;
+        bool dev[5];
+        for (int i = 0; i < 5; ++i) {
+            dev[i] = is_device_ptr(src[i]);
+            if (!dev[i]) stage_floats += cnt[i];
+        }
+        SEELE_CUDA(c, ensure(c->staging, stage_floats * 4));
+        const float* use[5];
+        size_t off = 0;
+        for (int i = 0; i < 5; ++i) {
+            if (dev[i]) {
+                use[i] = src[i];
+            } else {
+                float* dst = ptr<float>(c->staging) + off;
+                SEELE_CUDA(c, cudaMemcpyAsync(dst, src[i], cnt[i] * 4, cudaMemcpyHostToDevice, c->stream));
+                use[i] = dst;
+                off += cnt[i];
+            }
+        }
+        launch_repack((int)n, nc, use[0], use[1], use[2], use[3], use[4], ptr<float4>(c->pos_logit),
+                      ptr<float4>(c->quat), ptr<float4>(c->log_scale), ptr<float4>(c->sh), c->stream);
+        SEELE_LAUNCHED(c);
+        if (c->has_mask) {
+            SEELE_CUDA(c, ensure(c->mask, 4 * n));
+            SEELE_CUDA(c, cudaMemcpyAsync(c->mask.p, d->cluster_mask, 4 * n, cudaMemcpyDefault, c->stream));
+        }
+        SEELE_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    c->n = n;
+    c->sh_degree = d->sh_degree;
+    c->scene_flags = d->flags;
+    c->n_clusters = d->n_clusters;
+    c->pos_scale = d->pos_scale;
+    c->centroids.assign(d->centroids ? d->centroids : nullptr, d->centroids ? d->centroids + 6 * d->n_clusters : nullptr);
+    c->has_scene = true;
+    return SEELE_OK;
+}
+
+seele_status seele_set_cameras(seele_ctx* c, const seele_camera* cams, int32_t n) {
+    if (!c) return SEELE_ERR_ARG;
+    if (!cams || n < 1 || n > kMaxCams) return fail(c, SEELE_ERR_ARG, "need 1..%d cameras", kMaxCams);
+    for (int i = 0; i < n; ++i) {
+        const seele_camera& k = cams[i];
+        if (k.width < 1 || k.height < 1 || k.width > 16384 || k.height > 16384)
+            return fail(c, SEELE_ERR_ARG, "camera %d: size %dx%d out of range", i, k.width, k.height);
+        if (!(k.fx > 0) || !(k.fy > 0) || !(k.near_z > 0))
+            return fail(c, SEELE_ERR_ARG, "camera %d: fx, fy and near_z must be positive", i);
+    }
+    c->cams.assign(cams, cams + n);
+    c->rendered = false;
+    return SEELE_OK;
+}
+
+seele_status seele_synchronize(seele_ctx* c) {
+    if (!c) return SEELE_ERR_ARG;
+    SEELE_CUDA(c, cudaSetDevice(c->device));
+    SEELE_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (!c->status_pending) return SEELE_OK;
+    c->status_pending = false;
+    const DeviceStatus& h = *c->h_status;
+    if (h.error == kErrCapacity) {
+        c->capacity = std::max<uint64_t>(c->capacity, (uint64_t)h.n_instances + h.n_instances / 4 + 1024);
+        c->rendered = false;
+        return fail(c, SEELE_ERR_CAPACITY, "tile instances %u exceed capacity %u", h.n_instances, h.capacity);
+    }
+    if (h.error == kErrTimeout) {
+        c->rendered = false;
+        return fail(c, SEELE_ERR_TIMEOUT, "device wait gave up at site %u", h.timeout_site);
+    }
+    return SEELE_OK;
+}
+
+seele_status seele_render(seele_ctx* c, const seele_options* opt, float* out_rgb, float* out_T, seele_stats* stats) {
+    if (!c) return SEELE_ERR_ARG;
+    if (!c->has_scene) return fail(c, SEELE_ERR_STATE, "no scene loaded");
+    if (c->cams.empty()) return fail(c, SEELE_ERR_STATE, "no cameras set");
+    if (!opt || !out_rgb) return fail(c, SEELE_ERR_ARG, "options and out_rgb are required");
+    if (opt->mode != SEELE_MODE_PLAIN && opt->mode != SEELE_MODE_CR) return fail(c, SEELE_ERR_ARG, "bad mode");
+    if (opt->tile_w != 16 || opt->tile_h != 16) return fail(c, SEELE_ERR_ARG, "tile size must be 16x16");
+    if (opt->mode == SEELE_MODE_CR && !group_supported(opt->group_w, opt->group_h))
+        return fail(c, SEELE_ERR_ARG, "pixel group %dx%d not supported (1x1, 2x2, 2x4)", opt->group_w, opt->group_h);
+    if (!(opt->alpha_min > 0 && opt->alpha_min < opt->alpha_max && opt->alpha_max <= 1.0f))
+        return fail(c, SEELE_ERR_ARG, "need 0 < alpha_min < alpha_max <= 1");
+    if (!(opt->t_stop > 0 && opt->t_stop < 1)) return fail(c, SEELE_ERR_ARG, "need 0 < t_stop < 1");
+    if (opt->cluster_filter && (c->n_clusters <= 0 || !c->has_mask))
+        return fail(c, SEELE_ERR_STATE, "cluster_filter needs a scene with view clusters");
+    if (opt->n_neighbors < 0) return fail(c, SEELE_ERR_ARG, "n_neighbors must be >= 0");
+    const bool async = (opt->flags & SEELE_RENDER_ASYNC) != 0;
+    const bool profile = (opt->flags & SEELE_RENDER_PROFILE) != 0;
+    const bool count = (opt->flags & SEELE_RENDER_COUNT) != 0;
+    if (async && (profile || count)) return fail(c, SEELE_ERR_ARG, "PROFILE and COUNT need a synchronous render");
+    SEELE_CUDA(c, cudaSetDevice(c->device));
+    const bool rgb_dev = is_device_ptr(out_rgb);
+    const bool T_dev = out_T ? is_device_ptr(out_T) : true;
+    if (async && (!rgb_dev || !T_dev)) return fail(c, SEELE_ERR_ARG, "ASYNC renders need device outputs");
+
+    const int ncam = (int)c->cams.size();
+    const uint64_t R = (uint64_t)c->n * ncam;
+    if (R >= (1ull << 31)) return fail(c, SEELE_ERR_ARG, "cameras x Gaussians must be < 2^31");
+
+    // camera constants
+    c->camdev.resize(ncam);
+    uint64_t tiles_total = 0, pix_total = 0;
+    for (int i = 0; i < ncam; ++i) {
+        const seele_camera& k = c->cams[i];
+        CamDev& d = c->camdev[i];
+        std::memset(&d, 0, sizeof d);
+        const float* w = k.world_to_cam;
+        const float Rm[9] = {w[0], w[1], w[2], w[4], w[5], w[6], w[8], w[9], w[10]};
+        const float t[3] = {w[3], w[7], w[11]};
+        std::memcpy(d.R, Rm, sizeof Rm);
+        std::memcpy(d.t, t, sizeof t);
+        d.fx = k.fx;
+        d.fy = k.fy;
+        d.cx = k.cx;
+        d.cy = k.cy;
+        for (int j = 0; j < 3; ++j)
+            d.campos[j] = (float)(-((double)Rm[j] * t[0] + (double)Rm[3 + j] * t[1] + (double)Rm[6 + j] * t[2]));
+        d.lim_x = (float)(1.3 * k.width / (2.0 * k.fx));
+        d.lim_y = (float)(1.3 * k.height / (2.0 * k.fy));
+        d.near_z = k.near_z;
+        d.W = k.width;
+        d.H = k.height;
+        d.tiles_x = (k.width + opt->tile_w - 1) / opt->tile_w;
+        d.tiles_y = (k.height + opt->tile_h - 1) / opt->tile_h;
+        d.tile_offset = (uint32_t)tiles_total;
+        d.pix_offset = (uint32_t)pix_total;
+        d.sel_bits = opt->cluster_filter ? select_clusters(c, k, opt->n_neighbors) : 0xffffffffu;
+        tiles_total += (uint64_t)d.tiles_x * d.tiles_y;
+        pix_total += (uint64_t)k.width * k.height;
+    }
+    if (tiles_total >= (1ull << 31) || pix_total >= (1ull << 31))
+        return fail(c, SEELE_ERR_ARG, "too many tiles or pixels in one render");
+
+    // workspace
+    if (c->capacity == 0) c->capacity = std::max<uint64_t>(1u << 20, 4 * R);
+    const uint32_t sort_tile = sort_tile_items();
+    SEELE_CUDA(c, ensure(c->cams_dev, sizeof(CamDev) * ncam));
+    SEELE_CUDA(c, ensure(c->rec, 48 * R));
+    SEELE_CUDA(c, ensure(c->rect, 8 * R));
+    SEELE_CUDA(c, ensure(c->tiles, 4 * R));
+    SEELE_CUDA(c, ensure(c->depth, 4 * R));
+    for (int i = 0; i < 2; ++i) {
+        SEELE_CUDA(c, ensure(c->visk[i], 4 * R));
+        SEELE_CUDA(c, ensure(c->visv[i], 4 * R));
+    }
+    SEELE_CUDA(c, ensure(c->offs, 4 * R));
+    SEELE_CUDA(c, ensure(c->ranges, 8 * tiles_total));
+    SEELE_CUDA(c, ensure(c->status, sizeof(DeviceStatus)));
+    SEELE_CUDA(c, ensure(c->hist, 2 * kHistPasses * 256 * 4));
+    SEELE_CUDA(c, ensure(c->T, 4 * pix_total));
+    SEELE_CUDA(c, ensure(c->nc, 4 * pix_total));
+    if (!rgb_dev) SEELE_CUDA(c, ensure(c->rgb_tmp, 12 * pix_total));
+
+    const int deg = c->sh_degree;
+    const int ncoef = (deg + 1) * (deg + 1);
+    FrameParams fp{};
+    fp.n = (int32_t)c->n;
+    fp.n_cams = ncam;
+    fp.sh_degree = deg;
+    fp.tile_w = opt->tile_w;
+    fp.tile_h = opt->tile_h;
+    fp.opacity_filter = opt->opacity_filter ? 1 : 0;
+    fp.use_mask = opt->cluster_filter ? 1 : 0;
+    fp.alpha_min = opt->alpha_min;
+    fp.alpha_max = opt->alpha_max;
+    fp.t_stop = opt->t_stop;
+    fp.dilation = 0.3f;
+    fp.frustum_slack = 1.3f;
+    fp.n_tiles_total = (uint32_t)tiles_total;
+    const int tile_passes = std::max(1, (bits_for(tiles_total > 0 ? tiles_total - 1 : 0) + 7) / 8);
+
+    SEELE_CUDA(c, cudaMemcpyAsync(c->cams_dev.p, c->camdev.data(), sizeof(CamDev) * ncam, cudaMemcpyHostToDevice,
+                                  c->stream));
+    if (profile && !c->ev[0])
+        for (cudaEvent_t& e : c->ev) SEELE_CUDA(c, cudaEventCreate(&e));
+#define SEELE_MARK(k) \
+    if (profile) SEELE_CUDA(c, cudaEventRecord(c->ev[k], c->stream))
+
+    int retries = 0, launches = 0;
+    for (int attempt = 0;; ++attempt) {
+        const uint64_t cap = c->capacity;
+        for (int i = 0; i < 2; ++i) {
+            SEELE_CUDA(c, ensure(c->instk[i], 4 * cap));
+            SEELE_CUDA(c, ensure(c->instv[i], 4 * cap));
+        }
+        const size_t lb_entries = ((std::max<uint64_t>(R, cap) + sort_tile - 1) / sort_tile) * 256;
+        if (c->lookback_entries < lb_entries) {
+            SEELE_CUDA(c, ensure(c->lookback, 8 * lb_entries));
+            SEELE_CUDA(c, cudaMemsetAsync(c->lookback.p, 0, 8 * lb_entries, c->stream));
+            c->lookback_entries = lb_entries;
+        }
+        cudaStream_t s = c->stream;
+        DeviceStatus* st = ptr<DeviceStatus>(c->status);
+        uint64_t* lb = ptr<uint64_t>(c->lookback);
+        uint32_t* hist = ptr<uint32_t>(c->hist);
+        launches = 0;
+
+        SEELE_CUDA(c, cudaMemsetAsync(st, 0, sizeof(DeviceStatus), s));
+        SEELE_CUDA(c, cudaMemsetAsync(hist, 0, 2 * kHistPasses * 256 * 4, s));
+        SEELE_CUDA(c, cudaMemsetAsync(c->ranges.p, 0, 8 * tiles_total, s));
+        SEELE_MARK(SEELE_STAGE_PREPROCESS);
+        if (c->scene_flags == SEELE_SCENE_BORROW) {
+            const seele_scene_desc& b = c->borrowed;
+            launch_repack((int)c->n, ncoef, b.means, b.log_scales, b.quats, b.opacity_logits, b.sh,
+                          ptr<float4>(c->pos_logit), ptr<float4>(c->quat), ptr<float4>(c->log_scale),
+                          ptr<float4>(c->sh), s);
+            SEELE_LAUNCHED(c);
+            ++launches;
+        }
+
+        SceneDev sc;
+        sc.pos_logit = ptr<float4>(c->pos_logit);
+        sc.quat = ptr<float4>(c->quat);
+        sc.log_scale = ptr<float4>(c->log_scale);
+        sc.sh = ptr<float4>(c->sh);
+        sc.mask = c->has_mask ? (c->scene_flags == SEELE_SCENE_BORROW ? c->borrowed.cluster_mask
+                                                                      : ptr<const uint32_t>(c->mask))
+                              : nullptr;
+        ProjOut po{ptr<float4>(c->rec), ptr<uint2>(c->rect), ptr<uint32_t>(c->tiles), ptr<float>(c->depth)};
+        const CamDev* cams = ptr<const CamDev>(c->cams_dev);
+        launch_preprocess(sc, cams, fp, po, s);
+        SEELE_LAUNCHED(c);
+        ++launches;
+
+        // visible records -> (depth bits, id), then stable depth sort (4 passes)
+        SEELE_MARK(SEELE_STAGE_COMPACT);
+        launch_compact_visible(po.tiles, po.depth, (uint32_t)R, ptr<uint32_t>(c->visk[0]), ptr<uint32_t>(c->visv[0]),
+                               lb, c->epoch++, st, 0, s);
+        SEELE_LAUNCHED(c);
+        const uint32_t* n_vis = &st->n_visible;
+        SEELE_MARK(SEELE_STAGE_DEPTH_SORT);
+        launch_radix_histogram(ptr<uint32_t>(c->visk[0]), n_vis, 4, hist, 2 * 152, s);
+        SEELE_LAUNCHED(c);
+        launches += 2;
+        for (int p = 0; p < 4; ++p) {
+            const int a = p & 1, b = a ^ 1;
+            launch_onesweep(ptr<uint32_t>(c->visk[a]), ptr<uint32_t>(c->visv[a]), ptr<uint32_t>(c->visk[b]),
+                            ptr<uint32_t>(c->visv[b]), n_vis, (uint32_t)R, 8 * p, hist + 256 * p, lb, c->epoch++,
+                            st, 2 + p, s);
+            SEELE_LAUNCHED(c);
+            ++launches;
+        }
+        // sorted ids are back in buffer 0 after an even number of passes
+        const uint32_t* order = ptr<uint32_t>(c->visv[0]);
+        SEELE_MARK(SEELE_STAGE_TILE_SCAN);
+        launch_scan_tiles(po.tiles, order, (uint32_t)R, ptr<uint32_t>(c->offs), lb, c->epoch++, st, 1,
+                          (uint32_t)std::min<uint64_t>(cap, 0xffffffffu), s);
+        SEELE_LAUNCHED(c);
+        const int emit_blocks = (int)std::min<uint64_t>((R + 255) / 256, 8192);
+        SEELE_MARK(SEELE_STAGE_EMIT);
+        launch_emit(order, ptr<uint32_t>(c->offs), po.rect, cams, (int)c->n, st, ptr<uint32_t>(c->instk[0]),
+                    ptr<uint32_t>(c->instv[0]), std::max(emit_blocks, 1), s);
+        SEELE_LAUNCHED(c);
+        launches += 2;
+
+        // stable sort of the depth-ordered instances by global tile id
+        const uint32_t* n_inst = &st->n_inst_valid;
+        uint32_t* thist = hist + kHistPasses * 256;
+        SEELE_MARK(SEELE_STAGE_TILE_SORT);
+        launch_radix_histogram(ptr<uint32_t>(c->instk[0]), n_inst, tile_passes, thist, 4 * 152, s);
+        SEELE_LAUNCHED(c);
+        ++launches;
+        for (int p = 0; p < tile_passes; ++p) {
+            const int a = p & 1, b = a ^ 1;
+            launch_onesweep(ptr<uint32_t>(c->instk[a]), ptr<uint32_t>(c->instv[a]), ptr<uint32_t>(c->instk[b]),
+                            ptr<uint32_t>(c->instv[b]), n_inst, (uint32_t)cap, 8 * p, thist + 256 * p, lb,
+                            c->epoch++, st, 6 + p, s);
+            SEELE_LAUNCHED(c);
+            ++launches;
+        }
+        const int fin = tile_passes & 1;
+        SEELE_MARK(SEELE_STAGE_RANGES);
+        launch_ranges(ptr<uint32_t>(c->instk[fin]), st, ptr<uint2>(c->ranges), 8 * 152, s);
+        SEELE_LAUNCHED(c);
+        ++launches;
+
+        RasterArgs ra;
+        ra.ranges = ptr<uint2>(c->ranges);
+        ra.inst_rec = ptr<uint32_t>(c->instv[fin]);
+        ra.rec = ptr<float4>(c->rec);
+        ra.cams = cams;
+        ra.n_cams = ncam;
+        ra.n_tiles = (uint32_t)tiles_total;
+        ra.fp = fp;
+        ra.cr = opt->mode == SEELE_MODE_CR;
+        ra.group_w = opt->group_w;
+        ra.group_h = opt->group_h;
+        ra.out_rgb = rgb_dev ? out_rgb : ptr<float>(c->rgb_tmp);
+        ra.out_T = ptr<float>(c->T);
+        ra.out_nc = ptr<uint32_t>(c->nc);
+        ra.count_into = count ? st : nullptr;
+        SEELE_MARK(SEELE_STAGE_RASTER);
+        if (!launch_raster_fwd(ra, s)) return fail(c, SEELE_ERR_ARG, "no rasterizer for these options");
+        SEELE_LAUNCHED(c);
+        ++launches;
+        SEELE_MARK(SEELE_NUM_STAGES);
+
+        SEELE_CUDA(c, cudaMemcpyAsync(c->h_status, st, sizeof(DeviceStatus), cudaMemcpyDeviceToHost, s));
+        c->inst_final = fin;
+        c->n_tiles_total = (uint32_t)tiles_total;
+        c->n_pix_total = pix_total;
+        c->last_opt = *opt;
+        c->last_fp = fp;
+        if (async) {
+            c->status_pending = true;
+            c->rendered = true;
+            break;
+        }
+        SEELE_CUDA(c, cudaStreamSynchronize(s));
+        const DeviceStatus& h = *c->h_status;
+        if (h.error == kErrCapacity && attempt == 0) {
+            c->capacity = (uint64_t)h.n_instances + h.n_instances / 4 + 1024;
+            ++retries;
+            continue;
+        }
+        if (h.error == kErrCapacity) return fail(c, SEELE_ERR_CAPACITY, "capacity still exceeded after growth");
+        if (h.error == kErrTimeout) return fail(c, SEELE_ERR_TIMEOUT, "device wait gave up at site %u", h.timeout_site);
+        c->rendered = true;
+        break;
+    }
+
+    if (!rgb_dev) SEELE_CUDA(c, cudaMemcpyAsync(out_rgb, c->rgb_tmp.p, 12 * pix_total, cudaMemcpyDeviceToHost, c->stream));
+    if (out_T) SEELE_CUDA(c, cudaMemcpyAsync(out_T, c->T.p, 4 * pix_total, cudaMemcpyDefault, c->stream));
+    if (!rgb_dev || (out_T && !T_dev)) SEELE_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (stats) {
+        std::memset(stats->stage_ms, 0, sizeof stats->stage_ms);
+        if (profile)
+            for (int k = 0; k < SEELE_NUM_STAGES; ++k)
+                SEELE_CUDA(c, cudaEventElapsedTime(&stats->stage_ms[k], c->ev[k], c->ev[k + 1]));
+        stats->leader_tests = count ? (int64_t)c->h_status->work[0] : 0;
+        stats->pairs_evaluated = count ? (int64_t)c->h_status->work[1] : 0;
+        stats->pairs_blended = count ? (int64_t)c->h_status->work[2] : 0;
+        stats->n_visible = async ? -1 : (int64_t)c->h_status->n_visible;
+        stats->n_instances = async ? -1 : (int64_t)c->h_status->n_instances;
+        stats->capacity = (int64_t)c->capacity;
+        stats->retries = retries;
+        stats->n_kernels = launches;
+    }
+    return SEELE_OK;
+}
+
+seele_status seele_render_backward(seele_ctx* c, const float* dL_drgb, const seele_grads* g) {
+    if (!c) return SEELE_ERR_ARG;
+    if (!dL_drgb || !g) return fail(c, SEELE_ERR_ARG, "gradient buffers are required");
+    if (!c->rendered) return fail(c, SEELE_ERR_STATE, "no render to differentiate");
+    return fail(c, SEELE_ERR_STATE, "backward pass not available in this build");
+}
+
+seele_status seele_get_debug_view(const seele_ctx* c, seele_debug_view* out) {
+    if (!c || !out) return SEELE_ERR_ARG;
+    if (!c->rendered) return SEELE_ERR_STATE;
+    seele_ctx* m = const_cast<seele_ctx*>(c);
+    std::memset(out, 0, sizeof *out);
+    out->n_records = (int64_t)c->n * (int64_t)c->cams.size();
+    out->n_visible = c->h_status->n_visible;
+    out->n_instances = c->h_status->n_inst_valid;
+    out->n_tiles = c->n_tiles_total;
+    out->inst_tile = ptr<const uint32_t>(m->instk[c->inst_final]);
+    out->inst_record = ptr<const uint32_t>(m->instv[c->inst_final]);
+    out->tile_ranges = ptr<const uint32_t>(m->ranges);
+    out->tiles_touched = ptr<const uint32_t>(m->tiles);
+    out->rect = ptr<const uint32_t>(m->rect);
+    out->records = ptr<const float>(m->rec);
+    out->depth = ptr<const float>(m->depth);
+    out->n_contrib = ptr<const uint32_t>(m->nc);
+    return SEELE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,114 @@
+// common.cuh -- device-side types shared by the Seele kernels (sm_103a).
+//
+// One frame of the hot path, for all cameras at once (record id
+// r = camera * n + g indexes every per-(camera, Gaussian) array):
+//   preprocess    -> records, rect, tiles_touched, depth        (Sec. 3.1, 3.3)
+//   compact       -> visible record ids in id order, depth keys
+//   depth sort    -> visible ids in (fp32 depth, id) order       (Sec. 3.1 "Sorting")
+//   tile scan     -> instance offsets in depth order, K
+//   emit          -> (global tile, record id) pairs, depth-ordered
+//   tile sort     -> stable by tile: (tile, depth, id) order
+//   ranges        -> [start, end) per global tile
+//   raster        -> image, final T, n_contrib                   (Eqns. 1-2, Alg. 1)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace seele {
+
+constexpr float kLog2e = 1.4426950408889634f;
+
+// Device status word: the first error a kernel meets is kept.
+enum : int32_t { kOk = 0, kErrCapacity = 4, kErrTimeout = 5 };
+
+struct DeviceStatus {
+    int32_t error;
+    uint32_t n_visible;      // visible records
+    uint32_t n_instances;    // K
+    uint32_t capacity;       // instance capacity the scan compared K against
+    uint32_t n_inst_valid;   // K if it fits the capacity, else 0 (what the tile sort reads)
+    uint32_t timeout_site;   // which wait gave up (diagnostics)
+    uint32_t pad[2];
+    uint32_t ticket[16];     // dynamic block tickets of the look-back kernels
+    unsigned long long work[4];  // rasterizer work counters (counting variant only)
+};
+
+// Per-camera constants, built on the host.
+struct CamDev {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    float campos[3];
+    float lim_x, lim_y;      // 1.3 * W / (2 fx), 1.3 * H / (2 fy)
+    float near_z;
+    int32_t W, H;
+    int32_t tiles_x, tiles_y;
+    uint32_t tile_offset;    // first global tile id of this camera
+    uint32_t pix_offset;     // sum of W*H of the previous cameras
+    uint32_t sel_bits;       // selected view clusters
+    uint32_t pad;
+};
+
+struct FrameParams {
+    int32_t n;               // Gaussians
+    int32_t n_cams;
+    int32_t sh_degree;
+    int32_t tile_w, tile_h;
+    int32_t opacity_filter;
+    int32_t use_mask;
+    float alpha_min, alpha_max, t_stop;
+    float dilation;
+    float frustum_slack;
+    uint32_t n_tiles_total;
+};
+
+// Scene in the library's layout (structure of arrays, 16-byte aligned).
+struct SceneDev {
+    const float4* pos_logit;   // (x, y, z, opacity logit)
+    const float4* quat;        // (w, x, y, z)
+    const float4* log_scale;   // (lx, ly, lz, 0)
+    const float4* sh;          // plane-major: sh[j * n + g], j < ceil(3 nc / 4)
+    const uint32_t* mask;      // [n] or nullptr
+};
+
+// Per-record outputs of preprocessing.
+struct ProjOut {
+    float4* rec;               // [3 * R]: (u, v, cA, cB), (cC, log2 o, e_thr, 0), (r, g, b, 0)
+    uint2* rect;               // [R] tile box x0 | y0 << 16, x1 | y1 << 16
+    uint32_t* tiles;           // [R] tiles touched (0 = culled)
+    float* depth;              // [R] camera-space Z
+};
+
+// Bounded spin for the decoupled look-back: about a second at most, then the
+// waiting block records a timeout and gives up instead of hanging the GPU.
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+__device__ __forceinline__ void record_error(DeviceStatus* st, int32_t code, uint32_t site) {
+    if (atomicCAS(&st->error, kOk, code) == kOk) st->timeout_site = site;
+}
+
+__device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u64(uint64_t* p, uint64_t v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Look-back status word: [epoch:30][flag:2][value:32].  Entries of another
+// epoch read as "not yet published", so the status arrays need no clearing
+// between scans.
+constexpr uint32_t kFlagAggregate = 1u, kFlagInclusive = 2u;
+
+__device__ __forceinline__ uint64_t pack_status(uint32_t epoch, uint32_t flag, uint32_t value) {
+    return ((uint64_t)(epoch & 0x3fffffffu) << 34) | ((uint64_t)flag << 32) | value;
+}
+
+__device__ __forceinline__ uint32_t status_flag(uint64_t s, uint32_t epoch) {
+    return ((uint32_t)(s >> 34) == (epoch & 0x3fffffffu)) ? (uint32_t)(s >> 32) & 3u : 0u;
+}
+
+}  // namespace seele
