@@ -385,7 +385,8 @@ def run_gpu(args):
     }
     # the CPU oracle as it stands, rank 0 at N = 1 only
     if args.n_gauss != 3_000_000:
-        line["config"]["workload"] = line["config"]["workload"].replace("3M Gaussians", f"{args.n_gauss} Gaussians")
+        line["config"]["workload"] = (f"unbounded, {args.n_gauss} Gaussians (80% in 64 clusters, 20% on a r 30-50 "
+                                      f"shell), SH degree 3, 1920x1080, 16x16 tiles, 8 orbit cameras at r 5, seed 0")
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(scene, cams)
     if rank == 0:

@@ -206,9 +206,12 @@ typedef struct {
     int64_t n_visible;
     int64_t n_instances;
     int64_t n_tiles;              /* tiles over all cameras */
-    const uint32_t* inst_tile;    /* [n_instances] global tile id, sorted */
-    const uint32_t* inst_record;  /* [n_instances] record id = camera * n + g */
-    const uint32_t* tile_ranges;  /* [n_tiles][2] = [start, end) into the lists */
+    const uint32_t* inst_record;  /* [n_instances] record id = camera * n + g, grouped by
+                                     global tile, front to back within a tile */
+    const uint32_t* tile_start;   /* [n_tiles]: tile t's list is inst_record[tile_start[t] ..
+                                     tile_end[t]); a tile without instances has
+                                     tile_start >= tile_end */
+    const uint32_t* tile_end;     /* [n_tiles] */
     const uint32_t* tiles_touched;/* [n_records] 0 = culled */
     const uint32_t* rect;         /* [n_records][2] tile box, packed x | y << 16 */
     const float* records;         /* [n_records][12] raster record: u, v,

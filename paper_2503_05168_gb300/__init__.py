@@ -226,10 +226,16 @@ class Renderer:
 
         R, K, T = v.n_records, v.n_instances, v.n_tiles
         i32 = torch.int32
+        start = dev(v.tile_start, T, i32).to(torch.int64) & 0xFFFFFFFF   # stored as uint32
+        end = dev(v.tile_end, T, i32).to(torch.int64)
+        empty = start >= end
+        ranges = torch.stack([torch.where(empty, 0, start), torch.where(empty, 0, end)], 1).to(i32)
+        counts = (ranges[:, 1] - ranges[:, 0]).to(torch.int64)
+        inst_tile = torch.repeat_interleave(torch.arange(T, device=self.device, dtype=i32), counts)
         return dict(
             n_records=R, n_visible=v.n_visible, n_instances=K, n_tiles=T,
-            inst_tile=dev(v.inst_tile, K, i32), inst_record=dev(v.inst_record, K, i32),
-            tile_ranges=dev(v.tile_ranges, 2 * T, i32).reshape(T, 2),
+            inst_tile=inst_tile, inst_record=dev(v.inst_record, K, i32),
+            tile_ranges=ranges,
             tiles_touched=dev(v.tiles_touched, R, i32), rect=dev(v.rect, 2 * R, i32).reshape(R, 2),
             records=dev(v.records, 12 * R, torch.float32).reshape(R, 12), depth=dev(v.depth, R, torch.float32),
             n_contrib=dev(v.n_contrib, self.n_pixels, i32),

@@ -21,7 +21,7 @@ struct DevBuf {
 };
 
 constexpr int kMaxCams = 4096;
-constexpr int kHistPasses = 4;
+constexpr uint64_t kShortKeyMaxTiles = 65536;   // 16-bit tile keys
 
 }  // namespace
 
@@ -49,10 +49,11 @@ struct seele_ctx {
 
     // frame workspace
     DevBuf rec, rect, tiles, depth, visk[2], visv[2], offs, instk[2], instv[2], ranges, status, hist, lookback, T,
-        nc, rgb_tmp;
+        nc, rgb_tmp, sortcnt;
     size_t lookback_entries = 0;
     DeviceStatus* h_status = nullptr;  // pinned mirror of the device status
     cudaEvent_t ev[SEELE_NUM_STAGES + 1] = {};
+    bool profiling = false;
     uint64_t capacity = 0;
     uint32_t epoch = 1;
     bool status_pending = false;
@@ -121,6 +122,9 @@ T* ptr(DevBuf& b) {
     return static_cast<T*>(b.p);
 }
 
+#define SEELE_MARK_EXT(ctx, k) \
+    if ((ctx)->profiling) cudaEventRecord((ctx)->ev[k], (ctx)->stream)
+
 // Runtime cluster selection (Sec. 3.3 "Algorithm"): nearest centroid to the
 // camera feature (position / s, unit viewing direction), then the M centroids
 // nearest to that centroid; ties go to the lower index.
@@ -177,6 +181,26 @@ int bits_for(uint64_t v) {
     return b;
 }
 
+// Emission, stable radix sort by tile id and tile ranges.  Returns the
+// ping-pong buffer holding the sorted record ids, or -1 on a launch error.
+template <typename KeyT>
+int enqueue_tile_sort(seele_ctx* c, const uint32_t* order, const uint2* rect, const CamDev* cams, DeviceStatus* st,
+                      const uint32_t* n_inst, uint32_t n_tiles, int key_bits, uint64_t cap, int emit_blocks,
+                      uint64_t* lb, uint32_t* scnt, uint32_t* soff, int& launches, cudaStream_t s) {
+    KeyT* keys[2] = {ptr<KeyT>(c->instk[0]), ptr<KeyT>(c->instk[1])};
+    uint32_t* vals[2] = {ptr<uint32_t>(c->instv[0]), ptr<uint32_t>(c->instv[1])};
+    launch_emit<KeyT>(order, ptr<uint32_t>(c->offs), rect, cams, (int)c->n, st, keys[0], vals[0], emit_blocks, s);
+    if (cudaPeekAtLastError() != cudaSuccess) return -1;
+    ++launches;
+    SEELE_MARK_EXT(c, SEELE_STAGE_TILE_SORT);
+    uint32_t* starts = ptr<uint32_t>(c->ranges);
+    const int fin = radix_sort_pairs<KeyT>(keys, vals, n_inst, (uint32_t)cap, key_bits, false, scnt, soff, lb,
+                                           c->epoch, st, 6, launches, s, starts, starts + n_tiles);
+    if (fin < 0) return -1;
+    SEELE_MARK_EXT(c, SEELE_STAGE_RANGES);
+    return fin;
+}
+
 }  // namespace
 
 extern "C" {
@@ -227,7 +251,7 @@ void seele_destroy(seele_ctx* c) {
     DevBuf* all[] = {&c->pos_logit, &c->quat, &c->log_scale, &c->sh, &c->mask, &c->staging, &c->cams_dev,
                      &c->rec, &c->rect, &c->tiles, &c->depth, &c->visk[0], &c->visk[1], &c->visv[0],
                      &c->visv[1], &c->offs, &c->instk[0], &c->instk[1], &c->instv[0], &c->instv[1],
-                     &c->ranges, &c->status, &c->hist, &c->lookback, &c->T, &c->nc, &c->rgb_tmp};
+                     &c->ranges, &c->status, &c->hist, &c->lookback, &c->T, &c->nc, &c->rgb_tmp, &c->sortcnt};
     for (DevBuf* b : all) release(*b);
     if (c->h_status) cudaFreeHost(c->h_status);
     for (cudaEvent_t e : c->ev)
@@ -424,9 +448,10 @@ seele_status seele_render(seele_ctx* c, const seele_options* opt, float* out_rgb
         SEELE_CUDA(c, ensure(c->visv[i], 4 * R));
     }
     SEELE_CUDA(c, ensure(c->offs, 4 * R));
-    SEELE_CUDA(c, ensure(c->ranges, 8 * tiles_total));
+    SEELE_CUDA(c, ensure(c->ranges, 8 * tiles_total));   // starts[n_tiles], then ends[n_tiles]
     SEELE_CUDA(c, ensure(c->status, sizeof(DeviceStatus)));
-    SEELE_CUDA(c, ensure(c->hist, 2 * kHistPasses * 256 * 4));
+    const bool short_keys = tiles_total <= kShortKeyMaxTiles;
+
     SEELE_CUDA(c, ensure(c->T, 4 * pix_total));
     SEELE_CUDA(c, ensure(c->nc, 4 * pix_total));
     if (!rgb_dev) SEELE_CUDA(c, ensure(c->rgb_tmp, 12 * pix_total));
@@ -447,12 +472,13 @@ seele_status seele_render(seele_ctx* c, const seele_options* opt, float* out_rgb
     fp.dilation = 0.3f;
     fp.frustum_slack = 1.3f;
     fp.n_tiles_total = (uint32_t)tiles_total;
-    const int tile_passes = std::max(1, (bits_for(tiles_total > 0 ? tiles_total - 1 : 0) + 7) / 8);
+    const int tile_bits = std::max(1, bits_for(tiles_total > 0 ? tiles_total - 1 : 0));
 
     SEELE_CUDA(c, cudaMemcpyAsync(c->cams_dev.p, c->camdev.data(), sizeof(CamDev) * ncam, cudaMemcpyHostToDevice,
                                   c->stream));
     if (profile && !c->ev[0])
         for (cudaEvent_t& e : c->ev) SEELE_CUDA(c, cudaEventCreate(&e));
+    c->profiling = profile;
 #define SEELE_MARK(k) \
     if (profile) SEELE_CUDA(c, cudaEventRecord(c->ev[k], c->stream))
 
@@ -463,6 +489,8 @@ seele_status seele_render(seele_ctx* c, const seele_options* opt, float* out_rgb
             SEELE_CUDA(c, ensure(c->instk[i], 4 * cap));
             SEELE_CUDA(c, ensure(c->instv[i], 4 * cap));
         }
+        const uint32_t cnt_words = radix_count_words((uint32_t)std::max<uint64_t>(R, cap));
+        SEELE_CUDA(c, ensure(c->sortcnt, 8ull * cnt_words));
         const size_t lb_entries = ((std::max<uint64_t>(R, cap) + sort_tile - 1) / sort_tile) * 256;
         if (c->lookback_entries < lb_entries) {
             SEELE_CUDA(c, ensure(c->lookback, 8 * lb_entries));
@@ -472,12 +500,11 @@ seele_status seele_render(seele_ctx* c, const seele_options* opt, float* out_rgb
         cudaStream_t s = c->stream;
         DeviceStatus* st = ptr<DeviceStatus>(c->status);
         uint64_t* lb = ptr<uint64_t>(c->lookback);
-        uint32_t* hist = ptr<uint32_t>(c->hist);
         launches = 0;
 
         SEELE_CUDA(c, cudaMemsetAsync(st, 0, sizeof(DeviceStatus), s));
-        SEELE_CUDA(c, cudaMemsetAsync(hist, 0, 2 * kHistPasses * 256 * 4, s));
-        SEELE_CUDA(c, cudaMemsetAsync(c->ranges.p, 0, 8 * tiles_total, s));
+        SEELE_CUDA(c, cudaMemsetAsync(c->ranges.p, 0xff, 4 * tiles_total, s));
+        SEELE_CUDA(c, cudaMemsetAsync(ptr<uint32_t>(c->ranges) + tiles_total, 0, 4 * tiles_total, s));
         SEELE_MARK(SEELE_STAGE_PREPROCESS);
         if (c->scene_flags == SEELE_SCENE_BORROW) {
             const seele_scene_desc& b = c->borrowed;
@@ -509,53 +536,39 @@ seele_status seele_render(seele_ctx* c, const seele_options* opt, float* out_rgb
         SEELE_LAUNCHED(c);
         const uint32_t* n_vis = &st->n_visible;
         SEELE_MARK(SEELE_STAGE_DEPTH_SORT);
-        launch_radix_histogram(ptr<uint32_t>(c->visk[0]), n_vis, 4, hist, 2 * 152, s);
-        SEELE_LAUNCHED(c);
-        launches += 2;
-        for (int p = 0; p < 4; ++p) {
-            const int a = p & 1, b = a ^ 1;
-            launch_onesweep(ptr<uint32_t>(c->visk[a]), ptr<uint32_t>(c->visv[a]), ptr<uint32_t>(c->visk[b]),
-                            ptr<uint32_t>(c->visv[b]), n_vis, (uint32_t)R, 8 * p, hist + 256 * p, lb, c->epoch++,
-                            st, 2 + p, s);
-            SEELE_LAUNCHED(c);
-            ++launches;
+        uint32_t* scnt = ptr<uint32_t>(c->sortcnt);
+        uint32_t* soff = scnt + cnt_words;
+        {
+            uint32_t* vk[2] = {ptr<uint32_t>(c->visk[0]), ptr<uint32_t>(c->visk[1])};
+            uint32_t* vv[2] = {ptr<uint32_t>(c->visv[0]), ptr<uint32_t>(c->visv[1])};
+            // positive fp32 depths order like their bit patterns, sign bit clear: 31 bits
+            if (radix_sort_pairs<uint32_t>(vk, vv, n_vis, (uint32_t)R, 31, false, scnt, soff, lb, c->epoch, st, 2,
+                                           launches, s) != 0)
+                return fail(c, SEELE_ERR_CUDA, "depth sort launch failed: %s", cudaGetErrorString(cudaGetLastError()));
         }
+        ++launches;
         // sorted ids are back in buffer 0 after an even number of passes
         const uint32_t* order = ptr<uint32_t>(c->visv[0]);
         SEELE_MARK(SEELE_STAGE_TILE_SCAN);
         launch_scan_tiles(po.tiles, order, (uint32_t)R, ptr<uint32_t>(c->offs), lb, c->epoch++, st, 1,
                           (uint32_t)std::min<uint64_t>(cap, 0xffffffffu), s);
         SEELE_LAUNCHED(c);
-        const int emit_blocks = (int)std::min<uint64_t>((R + 255) / 256, 8192);
+        ++launches;
+        const int emit_blocks = (int)std::max<uint64_t>(std::min<uint64_t>((R + 255) / 256, 8 * 152), 1);
         SEELE_MARK(SEELE_STAGE_EMIT);
-        launch_emit(order, ptr<uint32_t>(c->offs), po.rect, cams, (int)c->n, st, ptr<uint32_t>(c->instk[0]),
-                    ptr<uint32_t>(c->instv[0]), std::max(emit_blocks, 1), s);
-        SEELE_LAUNCHED(c);
-        launches += 2;
-
-        // stable sort of the depth-ordered instances by global tile id
         const uint32_t* n_inst = &st->n_inst_valid;
-        uint32_t* thist = hist + kHistPasses * 256;
-        SEELE_MARK(SEELE_STAGE_TILE_SORT);
-        launch_radix_histogram(ptr<uint32_t>(c->instk[0]), n_inst, tile_passes, thist, 4 * 152, s);
-        SEELE_LAUNCHED(c);
-        ++launches;
-        for (int p = 0; p < tile_passes; ++p) {
-            const int a = p & 1, b = a ^ 1;
-            launch_onesweep(ptr<uint32_t>(c->instk[a]), ptr<uint32_t>(c->instv[a]), ptr<uint32_t>(c->instk[b]),
-                            ptr<uint32_t>(c->instv[b]), n_inst, (uint32_t)cap, 8 * p, thist + 256 * p, lb,
-                            c->epoch++, st, 6 + p, s);
-            SEELE_LAUNCHED(c);
-            ++launches;
-        }
-        const int fin = tile_passes & 1;
-        SEELE_MARK(SEELE_STAGE_RANGES);
-        launch_ranges(ptr<uint32_t>(c->instk[fin]), st, ptr<uint2>(c->ranges), 8 * 152, s);
-        SEELE_LAUNCHED(c);
-        ++launches;
+        int fin;
+        if (short_keys)
+            fin = enqueue_tile_sort<uint16_t>(c, order, po.rect, cams, st, n_inst, (uint32_t)tiles_total, tile_bits,
+                                              cap, emit_blocks, lb, scnt, soff, launches, s);
+        else
+            fin = enqueue_tile_sort<uint32_t>(c, order, po.rect, cams, st, n_inst, (uint32_t)tiles_total, tile_bits,
+                                              cap, emit_blocks, lb, scnt, soff, launches, s);
+        if (fin < 0) return fail(c, SEELE_ERR_CUDA, "tile sort launch failed: %s", cudaGetErrorString(cudaGetLastError()));
 
         RasterArgs ra;
-        ra.ranges = ptr<uint2>(c->ranges);
+        ra.starts = ptr<uint32_t>(c->ranges);
+        ra.ends = ptr<uint32_t>(c->ranges) + tiles_total;
         ra.inst_rec = ptr<uint32_t>(c->instv[fin]);
         ra.rec = ptr<float4>(c->rec);
         ra.cams = cams;
@@ -577,6 +590,7 @@ seele_status seele_render(seele_ctx* c, const seele_options* opt, float* out_rgb
 
         SEELE_CUDA(c, cudaMemcpyAsync(c->h_status, st, sizeof(DeviceStatus), cudaMemcpyDeviceToHost, s));
         c->inst_final = fin;
+
         c->n_tiles_total = (uint32_t)tiles_total;
         c->n_pix_total = pix_total;
         c->last_opt = *opt;
@@ -635,9 +649,9 @@ seele_status seele_get_debug_view(const seele_ctx* c, seele_debug_view* out) {
     out->n_visible = c->h_status->n_visible;
     out->n_instances = c->h_status->n_inst_valid;
     out->n_tiles = c->n_tiles_total;
-    out->inst_tile = ptr<const uint32_t>(m->instk[c->inst_final]);
     out->inst_record = ptr<const uint32_t>(m->instv[c->inst_final]);
-    out->tile_ranges = ptr<const uint32_t>(m->ranges);
+    out->tile_start = ptr<const uint32_t>(m->ranges);
+    out->tile_end = ptr<const uint32_t>(m->ranges) + c->n_tiles_total;
     out->tiles_touched = ptr<const uint32_t>(m->tiles);
     out->rect = ptr<const uint32_t>(m->rect);
     out->records = ptr<const float>(m->rec);

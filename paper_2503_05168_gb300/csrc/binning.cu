@@ -6,55 +6,82 @@
 
 namespace seele {
 
-// One thread per visible record in depth order: writes (global tile, record)
-// for every tile of its rect, row-major.  Emission in depth order means the
-// later stable sort by tile leaves each tile's list front to back.
+// A warp takes 32 consecutive visible records in depth order and writes all
+// their (global tile, record) instances as one contiguous, coalesced run:
+// lane l writes outputs l, l + 32, ... of the run and finds the record it
+// belongs to by a binary search over the warp's exclusive counts.  Emission in
+// depth order means the later stable sort by tile leaves each tile's list
+// front to back; within one record the tiles of its rect go row-major.
+template <typename KeyT>
 __global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ order,
                                                    const uint32_t* __restrict__ offsets,
                                                    const uint2* __restrict__ rect, const CamDev* __restrict__ cams,
                                                    int n_gauss, const DeviceStatus* __restrict__ st,
-                                                   uint32_t* __restrict__ inst_tile, uint32_t* __restrict__ inst_rec) {
-    const uint32_t n = st->n_visible;
+                                                   KeyT* __restrict__ inst_tile, uint32_t* __restrict__ inst_rec) {
     if (st->error != kOk) return;  // capacity overflow: nothing fits, outputs undefined
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        const uint32_t r = __ldg(order + j);
-        uint32_t o = __ldg(offsets + j);
-        const uint2 bx = __ldg(rect + r);
-        const CamDev& C = cams[r / (uint32_t)n_gauss];
-        const uint32_t x0 = bx.x & 0xffffu, y0 = bx.x >> 16, x1 = bx.y & 0xffffu, y1 = bx.y >> 16;
-        for (uint32_t ty = y0; ty <= y1; ++ty) {
-            const uint32_t row = C.tile_offset + ty * (uint32_t)C.tiles_x;
-            for (uint32_t tx = x0; tx <= x1; ++tx) {
-                inst_tile[o] = row + tx;
-                inst_rec[o] = r;
-                ++o;
+    const uint32_t n = st->n_visible;
+    const int lane = threadIdx.x & 31;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t wb = warp * 32; wb < n; wb += nwarps * 32) {
+        const uint32_t j = wb + lane;
+        uint32_t r = 0, x0 = 0, y0 = 0, w = 1, cnt = 0, row0 = 0, tx_n = 0;
+        if (j < n) {
+            r = __ldg(order + j);
+            const uint2 b = __ldg(rect + r);
+            x0 = b.x & 0xffffu;
+            y0 = b.x >> 16;
+            w = (b.y & 0xffffu) - x0 + 1;
+            cnt = w * ((b.y >> 16) - y0 + 1);
+            const CamDev& C = cams[r / (uint32_t)n_gauss];
+            tx_n = (uint32_t)C.tiles_x;
+            row0 = C.tile_offset;
+        }
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t excl = incl - cnt;
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        const uint32_t base = __shfl_sync(0xffffffffu, j < n ? __ldg(offsets + j) : 0u, 0);
+        // warp-uniform trip count: every shuffle below has all 32 lanes present
+        for (uint32_t o0 = 0; o0 < total; o0 += 32) {
+            const uint32_t o = o0 + lane;
+            // largest lane s with excl_s <= o (lanes past the run search harmlessly)
+            int s = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const uint32_t e = __shfl_sync(0xffffffffu, excl, s + step);
+                if (e <= o) s += step;
+            }
+            const uint32_t es = __shfl_sync(0xffffffffu, excl, s);
+            const uint32_t ws = __shfl_sync(0xffffffffu, w, s);
+            const uint32_t rs = __shfl_sync(0xffffffffu, row0, s);
+            const uint32_t ys = __shfl_sync(0xffffffffu, y0, s);
+            const uint32_t ns = __shfl_sync(0xffffffffu, tx_n, s);
+            const uint32_t xs = __shfl_sync(0xffffffffu, x0, s);
+            const uint32_t rr = __shfl_sync(0xffffffffu, r, s);
+            if (o < total) {
+                const uint32_t lt = o - es;
+                const uint32_t ty = lt / ws, tx = lt - ty * ws;
+                inst_tile[base + o] = (KeyT)(rs + (ys + ty) * ns + xs + tx);
+                inst_rec[base + o] = rr;
             }
         }
     }
 }
 
-// ranges[t] = [first, last + 1) of tile t in the sorted list; tiles without
-// instances keep the [0, 0) the caller cleared them to.
-__global__ void __launch_bounds__(256) ranges_kernel(const uint32_t* __restrict__ inst_tile,
-                                                     const DeviceStatus* __restrict__ st, uint2* __restrict__ ranges) {
-    if (st->error != kOk) return;
-    const uint32_t K = st->n_inst_valid;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < K; i += gridDim.x * blockDim.x) {
-        const uint32_t t = __ldg(inst_tile + i);
-        const uint32_t prev = i > 0 ? __ldg(inst_tile + i - 1) : 0xffffffffu;
-        const uint32_t next = i + 1 < K ? __ldg(inst_tile + i + 1) : 0xffffffffu;
-        if (t != prev) ranges[t].x = i;
-        if (t != next) ranges[t].y = i + 1;
-    }
-}
-
+template <typename KeyT>
 void launch_emit(const uint32_t* order, const uint32_t* offsets, const uint2* rect, const CamDev* cams, int n_gauss,
-                 const DeviceStatus* st, uint32_t* inst_tile, uint32_t* inst_rec, int blocks, cudaStream_t s) {
-    emit_kernel<<<blocks, 256, 0, s>>>(order, offsets, rect, cams, n_gauss, st, inst_tile, inst_rec);
+                 const DeviceStatus* st, KeyT* inst_tile, uint32_t* inst_rec, int blocks, cudaStream_t s) {
+    emit_kernel<KeyT><<<blocks, 256, 0, s>>>(order, offsets, rect, cams, n_gauss, st, inst_tile, inst_rec);
 }
 
-void launch_ranges(const uint32_t* inst_tile, const DeviceStatus* st, uint2* ranges, int blocks, cudaStream_t s) {
-    ranges_kernel<<<blocks, 256, 0, s>>>(inst_tile, st, ranges);
-}
+template void launch_emit<uint16_t>(const uint32_t*, const uint32_t*, const uint2*, const CamDev*, int,
+                                    const DeviceStatus*, uint16_t*, uint32_t*, int, cudaStream_t);
+template void launch_emit<uint32_t>(const uint32_t*, const uint32_t*, const uint2*, const CamDev*, int,
+                                    const DeviceStatus*, uint32_t*, uint32_t*, int, cudaStream_t);
 
 }  // namespace seele

@@ -22,19 +22,29 @@ void launch_scan_tiles(const uint32_t* tiles, const uint32_t* order, uint32_t ma
                        uint64_t* status, uint32_t epoch, DeviceStatus* st, int ticket, uint32_t capacity,
                        cudaStream_t s);
 
-uint32_t sort_tile_items();
-void launch_radix_histogram(const uint32_t* keys, const uint32_t* count_ptr, int passes, uint32_t* hist,
-                            int blocks, cudaStream_t s);
-void launch_onesweep(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out,
-                     const uint32_t* count_ptr, uint32_t max_n, int shift, const uint32_t* hist, uint64_t* status,
-                     uint32_t epoch, DeviceStatus* st, int ticket, cudaStream_t s);
+void launch_exclusive_scan(const uint32_t* in, uint32_t n, uint32_t* out, uint64_t* status, uint32_t epoch,
+                           DeviceStatus* st, int ticket, cudaStream_t s);
 
+uint32_t sort_tile_items();
+uint32_t radix_count_words(uint32_t max_n);
+// Stable LSD sort of (keys[0], vals[0]) by their low `key_bits` bits in 8-bit
+// digits; returns the index of the buffer pair holding the result, or -1 on a
+// launch error.  With run_start / run_end (cleared to all-ones / zero, one
+// word per key value) the last pass also records [first, last + 1) of every
+// key value present -- the per-tile ranges.
+template <typename KeyT>
+int radix_sort_pairs(KeyT* keys[2], uint32_t* vals[2], const uint32_t* count_ptr, uint32_t max_n, int key_bits,
+                     bool keys_after_last, uint32_t* counts, uint32_t* offsets, uint64_t* lookback,
+                     uint32_t& epoch, DeviceStatus* st, int ticket, int& launches, cudaStream_t s,
+                     uint32_t* run_start = nullptr, uint32_t* run_end = nullptr);
+
+template <typename KeyT>
 void launch_emit(const uint32_t* order, const uint32_t* offsets, const uint2* rect, const CamDev* cams, int n_gauss,
-                 const DeviceStatus* st, uint32_t* inst_tile, uint32_t* inst_rec, int blocks, cudaStream_t s);
-void launch_ranges(const uint32_t* inst_tile, const DeviceStatus* st, uint2* ranges, int blocks, cudaStream_t s);
+                 const DeviceStatus* st, KeyT* inst_tile, uint32_t* inst_rec, int blocks, cudaStream_t s);
 
 struct RasterArgs {
-    const uint2* ranges;
+    const uint32_t* starts;     // [n_tiles]: tile t's list is [starts[t], ends[t]) (empty if start >= end)
+    const uint32_t* ends;
     const uint32_t* inst_rec;
     const float4* rec;
     const CamDev* cams;

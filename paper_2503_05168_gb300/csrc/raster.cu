@@ -25,7 +25,8 @@ __device__ __forceinline__ float ex2_approx(float x) {
 
 template <int TW, int TH, int PW, int PH, int GW, int GH, bool CR, bool COUNT>
 __global__ void __launch_bounds__((TW / PW) * (TH / PH))
-    raster_fwd_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ inst_rec,
+    raster_fwd_kernel(const uint32_t* __restrict__ starts, const uint32_t* __restrict__ ends,
+                      const uint32_t* __restrict__ inst_rec,
                       const float4* __restrict__ rec, const CamDev* __restrict__ cams, int n_cams, FrameParams fp,
                       float* __restrict__ out_rgb, float* __restrict__ out_T, uint32_t* __restrict__ out_nc,
                       DeviceStatus* __restrict__ counters) {
@@ -57,7 +58,8 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
         nc[p] = 0;
         if (bx + p % PW < C.W && by + p / PW < C.H) live |= 1u << p;
     }
-    const uint2 rg = __ldg(ranges + gtile);
+    uint2 rg = make_uint2(__ldg(starts + gtile), __ldg(ends + gtile));
+    if (rg.x >= rg.y) rg = make_uint2(0u, 0u);  // tile without instances
     const float fx0 = (float)bx + 0.5f, fy0 = (float)by + 0.5f;
     const float amax = fp.alpha_max, tstop = fp.t_stop;
     uint32_t n_lead = 0, n_eval = 0, n_blend = 0;  // counting variant only
@@ -73,6 +75,61 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
         }
         __syncthreads();
         const int cnt = min((uint32_t)NT, rg.y - base);
+        if (CR && GW == PW && GH == PH) {
+            // Alg. 1 with one group per thread.  Phase 1: the leader (pixel 0)
+            // tests every staged Gaussian -- independent of the blending state,
+            // so the tests run back to back.  Phase 2: only the Gaussians the
+            // leader kept are blended, in list order, by the group's pixels.
+            static_assert(NT <= 64, "pass mask holds 64 entries");
+            if (live == 0u) continue;
+            uint64_t pass = 0;
+#pragma unroll 8
+            for (int k = 0; k < cnt; ++k) {
+                const float4 A = s0[k];
+                const float4 B = s1[k];
+                const float dx = fx0 - A.x, dy = fy0 - A.y;
+                const float e0 = fmaf(fmaf(A.z, dx, A.w * dy), dx, fmaf(B.x * dy, dy, B.y));
+                if (COUNT) ++n_lead;
+                pass |= (uint64_t)(e0 >= B.z) << k;
+            }
+            while (pass != 0ull && live != 0u) {
+                const int k = __ffsll((long long)pass) - 1;
+                pass &= pass - 1ull;
+                const float4 A = s0[k];
+                const float4 B = s1[k];
+                const float4 Cc = s2[k];
+                const float dx = fx0 - A.x, dy = fy0 - A.y;
+                const uint32_t pos1 = base + (uint32_t)k - rg.x + 1u;
+#pragma unroll
+                for (int jj = 0; jj < PH; ++jj) {
+                    const float ddy = dy + (float)jj;
+                    const float rb = A.w * ddy, rc = fmaf(B.x * ddy, ddy, B.y);
+#pragma unroll
+                    for (int i = 0; i < PW; ++i) {
+                        const int p = jj * PW + i;
+                        if (!(live >> p & 1u)) continue;
+                        if (COUNT) ++n_eval;
+                        const float ddx = dx + (float)i;
+                        const float e = fmaf(fmaf(A.z, ddx, rb), ddx, rc);
+                        if (e < B.z) continue;  // per-pixel alpha_theta / support rule
+                        const float al = fminf(amax, ex2_approx(e));
+                        const float Tn = T[p] * (1.f - al);
+                        if (Tn < tstop) {
+                            live &= ~(1u << p);
+                            continue;
+                        }
+                        const float wgt = al * T[p];
+                        cr[p] = fmaf(wgt, Cc.x, cr[p]);
+                        cg[p] = fmaf(wgt, Cc.y, cg[p]);
+                        cb[p] = fmaf(wgt, Cc.z, cb[p]);
+                        T[p] = Tn;
+                        nc[p] = pos1;
+                        if (COUNT) ++n_blend;
+                    }
+                }
+            }
+            continue;
+        }
         for (int k = 0; k < cnt; ++k) {
             if (live == 0u) break;
             const float4 A = s0[k];
@@ -102,7 +159,9 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
                 nc[p] = pos1;
                 if (COUNT) ++n_blend;
             };
-            if (CR) {
+            if (CR && GW == PW && GH == PH) {
+                // handled by the two-phase path below
+            } else if (CR) {
 #pragma unroll
                 for (int gy = 0; gy < PH / GH; ++gy)
 #pragma unroll
@@ -159,10 +218,10 @@ static void launch_one(const RasterArgs& a, cudaStream_t s) {
     constexpr int NT = (TW / PW) * (TH / PH);
     if (a.count_into)
         raster_fwd_kernel<TW, TH, PW, PH, GW, GH, CR, true><<<a.n_tiles, NT, 0, s>>>(
-            a.ranges, a.inst_rec, a.rec, a.cams, a.n_cams, a.fp, a.out_rgb, a.out_T, a.out_nc, a.count_into);
+            a.starts, a.ends, a.inst_rec, a.rec, a.cams, a.n_cams, a.fp, a.out_rgb, a.out_T, a.out_nc, a.count_into);
     else
         raster_fwd_kernel<TW, TH, PW, PH, GW, GH, CR, false><<<a.n_tiles, NT, 0, s>>>(
-            a.ranges, a.inst_rec, a.rec, a.cams, a.n_cams, a.fp, a.out_rgb, a.out_T, a.out_nc, nullptr);
+            a.starts, a.ends, a.inst_rec, a.rec, a.cams, a.n_cams, a.fp, a.out_rgb, a.out_T, a.out_nc, nullptr);
 }
 
 bool launch_raster_fwd(const RasterArgs& a, cudaStream_t s) {

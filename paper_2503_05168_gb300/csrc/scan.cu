@@ -167,6 +167,49 @@ __global__ void __launch_bounds__(kScanThreads) scan_tiles_kernel(const uint32_t
     }
 }
 
+// Exclusive scan of n uint32 values (n known on the host).
+__global__ void __launch_bounds__(kScanThreads) exclusive_scan_kernel(const uint32_t* __restrict__ in, uint32_t n,
+                                                                      uint32_t* __restrict__ out, uint64_t* status,
+                                                                      uint32_t epoch, DeviceStatus* st, int ticket) {
+    const uint32_t tile = take_ticket(&st->ticket[ticket]);
+    const uint32_t ntiles = (n + kScanTile - 1) / kScanTile;
+    if (tile >= ntiles) return;
+    const uint32_t base = tile * kScanTile + threadIdx.x * kScanItems;
+    uint32_t c[kScanItems];
+    uint32_t sum = 0;
+    if (base + kScanItems <= n) {
+        const uint4* p4 = reinterpret_cast<const uint4*>(in + base);
+#pragma unroll
+        for (int q = 0; q < kScanItems / 4; ++q) {
+            const uint4 v = __ldg(p4 + q);
+            c[4 * q] = v.x;
+            c[4 * q + 1] = v.y;
+            c[4 * q + 2] = v.z;
+            c[4 * q + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) c[k] = base + k < n ? __ldg(in + base + k) : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) sum += c[k];
+    uint32_t total;
+    const uint32_t excl = block_exclusive_scan(sum, &total);
+    const uint32_t prefix = lookback_prefix(status, tile, total, epoch, st, 4);
+    uint32_t pos = prefix + excl;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n) out[base + k] = pos;
+        pos += c[k];
+    }
+}
+
+void launch_exclusive_scan(const uint32_t* in, uint32_t n, uint32_t* out, uint64_t* status, uint32_t epoch,
+                           DeviceStatus* st, int ticket, cudaStream_t s) {
+    const uint32_t blocks = (n + kScanTile - 1) / kScanTile;
+    exclusive_scan_kernel<<<blocks > 0 ? blocks : 1, kScanThreads, 0, s>>>(in, n, out, status, epoch, st, ticket);
+}
+
 uint32_t scan_tiles_per_launch() { return kScanTile; }
 
 void launch_compact_visible(const uint32_t* tiles, const float* depth, uint32_t R, uint32_t* keys, uint32_t* vals,

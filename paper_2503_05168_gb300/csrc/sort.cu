@@ -1,14 +1,24 @@
-// sort.cu -- stable least-significant-digit radix sort of (uint32 key,
-// uint32 value) pairs, one kernel per 8-bit digit ("onesweep": per-tile
-// ranking, per-digit decoupled look-back, shared-memory staged scatter).
+// sort.cu -- stable least-significant-digit radix sort of (key, uint32 value)
+// pairs with 8-bit digits, as reduce-then-scan passes:
+//   upsweep:   each tile of 4096 elements counts its digits into a
+//              digit-major matrix counts[d * stride + tile];
+//   scan:      one device-wide exclusive scan of that matrix gives, for every
+//              (digit, tile), where the tile's run of that digit starts;
+//   downsweep: each tile ranks its elements stably (warp match + per-warp
+//              counters), stages them in shared memory by digit and writes
+//              each digit's run contiguously.
+// No block waits on another inside the sort.  Ranking uses one warp ballot per
+// significant digit bit.  Used twice per frame: on the visible records keyed
+// by fp32 depth bits (31 bits, 4 passes) and on the tile instances keyed by
+// global tile id (16-bit keys when the frame has <= 65536 tiles); the last
+// pass of each writes values only.  Stability is what makes the two sorts
+// compose into the (tile, depth, record id) order of Sec. 3.1 "Sorting".
 //
-// Used twice per frame: on the visible records keyed by fp32 depth bits (31
-// significant bits, 4 passes) and on the tile instances keyed by global tile
-// id (ceil(bits / 8) passes).  Stability is what makes the composition give
-// the (tile, depth, record id) order of Sec. 3.1 "Sorting".
-//
-// The element count lives on the device (it is produced by the previous
-// kernel), so the grid is sized for the capacity and surplus blocks exit.
+// Element counts live on the device (they are produced by the previous
+// kernel), so grids are sized for the capacity and surplus tiles write
+// nothing but zero counts.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -20,47 +30,65 @@ constexpr int kSortTile = kSortThreads * kSortItems;  // 4096
 constexpr int kRadix = 256;
 constexpr int kWarps = kSortThreads / 32;
 
-// Histograms of every pass at once (the digit multiset of a pass does not
-// depend on the order the previous passes leave behind).
-__global__ void __launch_bounds__(kSortThreads) radix_histogram_kernel(const uint32_t* __restrict__ keys,
-                                                                       const uint32_t* __restrict__ count_ptr,
-                                                                       int passes, uint32_t* __restrict__ hist) {
-    __shared__ uint32_t s_hist[4][kRadix];
-    for (int i = threadIdx.x; i < 4 * kRadix; i += kSortThreads) (&s_hist[0][0])[i] = 0;
-    __syncthreads();
+// Per-tile digit counts, digit-major.  Counting ignores order, so each thread
+// reads 16 consecutive keys with vector loads and adds them to its warp's
+// shared counters.
+template <typename KeyT>
+__global__ void __launch_bounds__(kSortThreads) upsweep_kernel(const KeyT* __restrict__ keys,
+                                                               const uint32_t* __restrict__ count_ptr, int shift,
+                                                               uint32_t* __restrict__ counts, uint32_t stride) {
+    static_assert(kSortItems * sizeof(KeyT) % 16 == 0, "vector loads");
+    __shared__ uint32_t s_w[kWarps][kRadix];
+    const uint32_t tile = blockIdx.x;
     const uint32_t n = *count_ptr;
-    for (uint32_t i = blockIdx.x * kSortThreads + threadIdx.x; i < n; i += gridDim.x * kSortThreads) {
-        const uint32_t k = __ldg(keys + i);
-        for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p][(k >> (8 * p)) & 0xffu], 1u);
+    const int w = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < kWarps * kRadix; i += kSortThreads) (&s_w[0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t base = tile * kSortTile + threadIdx.x * kSortItems;
+    if (base + kSortItems <= n) {
+        constexpr int NV = kSortItems * sizeof(KeyT) / 16;
+        const uint4* p = reinterpret_cast<const uint4*>(keys + base);
+        uint4 v[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) v[q] = __ldg(p + q);
+        const KeyT* kk = reinterpret_cast<const KeyT*>(v);
+#pragma unroll
+        for (int k = 0; k < kSortItems; ++k) atomicAdd(&s_w[w][((uint32_t)kk[k] >> shift) & 0xffu], 1u);
+    } else {
+        for (int k = 0; k < kSortItems; ++k)
+            if (base + k < n) atomicAdd(&s_w[w][((uint32_t)__ldg(keys + base + k) >> shift) & 0xffu], 1u);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < passes * kRadix; i += kSortThreads) {
-        const uint32_t v = (&s_hist[0][0])[i];
-        if (v) atomicAdd(hist + i, v);
-    }
+    const uint32_t d = threadIdx.x;
+    uint32_t total = 0;
+#pragma unroll
+    for (int ww = 0; ww < kWarps; ++ww) total += s_w[ww][d];
+    counts[(size_t)d * stride + tile] = total;
 }
 
-__global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint32_t* __restrict__ keys_in,
-                                                                const uint32_t* __restrict__ vals_in,
-                                                                uint32_t* __restrict__ keys_out,
-                                                                uint32_t* __restrict__ vals_out,
-                                                                const uint32_t* __restrict__ count_ptr, int shift,
-                                                                const uint32_t* __restrict__ hist, uint64_t* status,
-                                                                uint32_t epoch, DeviceStatus* st, int ticket) {
-    __shared__ uint32_t s_keys[kSortTile];
+template <typename KeyT, bool WRITE_KEYS>
+__global__ void __launch_bounds__(kSortThreads) downsweep_kernel(const KeyT* __restrict__ keys_in,
+                                                                 const uint32_t* __restrict__ vals_in,
+                                                                 KeyT* __restrict__ keys_out,
+                                                                 uint32_t* __restrict__ vals_out,
+                                                                 const uint32_t* __restrict__ count_ptr, int shift,
+                                                                 int nbits, const uint32_t* __restrict__ offsets,
+                                                                 uint32_t stride, uint32_t* __restrict__ run_start,
+                                                                 uint32_t* __restrict__ run_end) {
+    __shared__ KeyT s_keys[kSortTile];
     __shared__ uint32_t s_vals[kSortTile];
     __shared__ uint32_t s_wcount[kWarps][kRadix + 1];  // per-warp digit counters, then exclusive prefixes
     __shared__ uint32_t s_local_base[kRadix];          // digit start inside this tile
     __shared__ uint32_t s_global_base[kRadix];         // digit start in the output for this tile
-    __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_scan[kWarps];
 
-    if (threadIdx.x == 0) s_tile = atomicAdd(&st->ticket[ticket], 1u);
-    for (int i = threadIdx.x; i < kWarps * (kRadix + 1); i += kSortThreads) (&s_wcount[0][0])[i] = 0;
-    __syncthreads();
-    const uint32_t tile = s_tile;
+    const uint32_t tile = blockIdx.x;
     const uint32_t n = *count_ptr;
-    const uint32_t ntiles = (n + kSortTile - 1) / kSortTile;
-    if (tile >= ntiles) return;
+    if (tile * (uint32_t)kSortTile >= n) return;
+    const uint32_t d = threadIdx.x;  // kSortThreads == kRadix: thread d owns digit d
+    for (int i = threadIdx.x; i < kWarps * (kRadix + 1); i += kSortThreads) (&s_wcount[0][0])[i] = 0;
+    s_global_base[d] = __ldg(offsets + (size_t)d * stride + tile);
+    __syncthreads();
 
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t wbase = tile * kSortTile + w * (32 * kSortItems);
@@ -68,26 +96,36 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint32_t* 
 
     // load warp-striped: item k of lane l is element wbase + 32 k + l, so the
     // order (k, lane) is the input order and ranking in that order is stable
-    uint32_t key[kSortItems], val[kSortItems];
-    uint32_t rank[kSortItems];
+    uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
         const uint32_t i = wbase + 32 * k + lane;
         const bool ok = i < n;
-        key[k] = ok ? __ldg(keys_in + i) : 0u;
+        key[k] = ok ? (uint32_t)__ldg(keys_in + i) : 0xffffffffu;
         val[k] = ok ? __ldg(vals_in + i) : 0u;
-        const uint32_t d = ok ? (key[k] >> shift) & 0xffu : (uint32_t)kRadix;  // sentinel bucket
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t before = s_wcount[w][d];
+    }
+    // lanes holding the same digit: one ballot per significant digit bit plus
+    // one for validity (elements past n form their own group)
+    const uint32_t valid_base = __ballot_sync(0xffffffffu, true);
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+        const bool ok = key[k] != 0xffffffffu;
+        const uint32_t dg = ok ? (key[k] >> shift) & 0xffu : (uint32_t)kRadix;  // sentinel bucket
+        const uint32_t okm = __ballot_sync(0xffffffffu, ok);
+        uint32_t peers = ok ? okm : (valid_base & ~okm);
+        for (int b = 0; b < nbits; ++b) {
+            const uint32_t bm = __ballot_sync(0xffffffffu, (dg >> b) & 1u);
+            peers &= ((dg >> b) & 1u) ? bm : ~bm;
+        }
+        const uint32_t before = s_wcount[w][dg];
         __syncwarp();
-        if ((peers & lt_mask) == 0u) s_wcount[w][d] = before + __popc(peers);
+        if ((peers & lt_mask) == 0u) s_wcount[w][dg] = before + __popc(peers);
         __syncwarp();
         rank[k] = before + __popc(peers & lt_mask);
     }
     __syncthreads();
 
-    // per digit: totals over warps, per-warp exclusive offsets, publish + look back
-    const uint32_t d = threadIdx.x;  // kSortThreads == kRadix
+    // per digit: per-warp exclusive offsets and the tile-local digit start
     uint32_t total = 0;
 #pragma unroll
     for (int ww = 0; ww < kWarps; ++ww) {
@@ -95,80 +133,26 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint32_t* 
         s_wcount[ww][d] = total;
         total += c;
     }
-    uint64_t* my = status + (size_t)tile * kRadix + d;
-    st_release_u64(my, pack_status(epoch, tile == 0 ? kFlagInclusive : kFlagAggregate, total));
-
-    // tile-local digit starts (exclusive scan of totals over digits)
-    {
-        __shared__ uint32_t s_scan[kSortThreads / 32];
-        uint32_t incl = total;
+    uint32_t incl = total;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (lane == 31) s_scan[w] = incl;
-        __syncthreads();
-        uint32_t add = 0;
-        for (int ww = 0; ww < w; ++ww) add += s_scan[ww];
-        s_local_base[d] = add + incl - total;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
     }
-
-    // global digit start: exclusive prefix of the pass histogram
-    uint32_t gstart;
-    {
-        __shared__ uint32_t s_scan2[kSortThreads / 32];
-        const uint32_t h = __ldg(hist + d);
-        uint32_t incl = h;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (lane == 31) s_scan2[w] = incl;
-        __syncthreads();
-        uint32_t add = 0;
-        for (int ww = 0; ww < w; ++ww) add += s_scan2[ww];
-        gstart = add + incl - h;
-    }
-
-    // decoupled look-back over preceding tiles for this digit
-    __shared__ int s_gave_up;
-    if (threadIdx.x == 0) s_gave_up = 0;
+    if (lane == 31) s_scan[w] = incl;
     __syncthreads();
-    uint32_t prefix = 0;
-    if (tile > 0) {
-        int64_t t = (int64_t)tile - 1;
-        while (t >= 0) {
-            uint32_t spins = 0, flag;
-            uint64_t s;
-            do {
-                s = ld_acquire_u64(status + (size_t)t * kRadix + d);
-                flag = status_flag(s, epoch);
-            } while (flag == 0 && ++spins < kSpinLimit);
-            if (flag == 0) {
-                record_error(st, kErrTimeout, 10 + (uint32_t)shift);
-                s_gave_up = 1;
-                break;
-            }
-            prefix += (uint32_t)s;
-            if (flag == kFlagInclusive) break;
-            --t;
-        }
-        st_release_u64(my, pack_status(epoch, kFlagInclusive, prefix + total));
-    }
-    s_global_base[d] = gstart + prefix;
+    uint32_t add = 0;
+    for (int ww = 0; ww < w; ++ww) add += s_scan[ww];
+    s_local_base[d] = add + incl - total;
     __syncthreads();
-    if (s_gave_up) return;  // offsets unknown: write nothing rather than guess
 
     // stage the tile in shared memory sorted by digit, then write out runs
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
-        const uint32_t i = wbase + 32 * k + lane;
-        if (i < n) {
+        if (key[k] != 0xffffffffu) {
             const uint32_t dg = (key[k] >> shift) & 0xffu;
             const uint32_t p = s_local_base[dg] + s_wcount[w][dg] + rank[k];
-            s_keys[p] = key[k];
+            s_keys[p] = (KeyT)key[k];
             s_vals[p] = val[k];
         }
     }
@@ -179,26 +163,56 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint32_t* 
         const uint32_t dg = (k >> shift) & 0xffu;
         const uint32_t o = s_global_base[dg] + (i - s_local_base[dg]);
         if (o < n) {
-            keys_out[o] = k;
+            if (WRITE_KEYS) keys_out[o] = (KeyT)k;
             vals_out[o] = s_vals[i];
+            // last pass: within a digit run the staged keys are in the lower
+            // digits' sorted order, so equal whole keys are adjacent; each
+            // block reports where its runs of a key begin and end
+            if (run_start != nullptr) {
+                if (i == 0 || (uint32_t)s_keys[i - 1] != k) atomicMin(run_start + k, o);
+                if (i + 1 == tile_n || (uint32_t)s_keys[i + 1] != k) atomicMax(run_end + k, o + 1);
+            }
         }
     }
 }
 
 uint32_t sort_tile_items() { return kSortTile; }
 
-void launch_radix_histogram(const uint32_t* keys, const uint32_t* count_ptr, int passes, uint32_t* hist,
-                            int blocks, cudaStream_t s) {
-    radix_histogram_kernel<<<blocks, kSortThreads, 0, s>>>(keys, count_ptr, passes, hist);
+uint32_t radix_count_words(uint32_t max_n) {
+    return kRadix * std::max<uint32_t>((max_n + kSortTile - 1) / kSortTile, 1u);
 }
 
-void launch_onesweep(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out,
-                     const uint32_t* count_ptr, uint32_t max_n, int shift, const uint32_t* hist, uint64_t* status,
-                     uint32_t epoch, DeviceStatus* st, int ticket, cudaStream_t s) {
-    const uint32_t blocks = (max_n + kSortTile - 1) / kSortTile;
-    onesweep_kernel<<<blocks > 0 ? blocks : 1, kSortThreads, 0, s>>>(keys_in, vals_in, keys_out, vals_out,
-                                                                      count_ptr, shift, hist, status, epoch, st,
-                                                                      ticket);
+template <typename KeyT>
+int radix_sort_pairs(KeyT* keys[2], uint32_t* vals[2], const uint32_t* count_ptr, uint32_t max_n, int key_bits,
+                     bool keys_after_last, uint32_t* counts, uint32_t* offsets, uint64_t* lookback,
+                     uint32_t& epoch, DeviceStatus* st, int ticket, int& launches, cudaStream_t s,
+                     uint32_t* run_start, uint32_t* run_end) {
+    const uint32_t stride = std::max<uint32_t>((max_n + kSortTile - 1) / kSortTile, 1u);
+    const int passes = std::max(1, (key_bits + 7) / 8);
+    for (int p = 0; p < passes; ++p) {
+        const int a = p & 1, b = a ^ 1;
+        const int nbits = std::max(1, std::min(8, key_bits - 8 * p));
+        const bool last = p == passes - 1;
+        uint32_t* rs = last ? run_start : nullptr;
+        uint32_t* re = last ? run_end : nullptr;
+        upsweep_kernel<KeyT><<<stride, kSortThreads, 0, s>>>(keys[a], count_ptr, 8 * p, counts, stride);
+        launch_exclusive_scan(counts, kRadix * stride, offsets, lookback, epoch++, st, ticket + p, s);
+        if (!last || keys_after_last)
+            downsweep_kernel<KeyT, true><<<stride, kSortThreads, 0, s>>>(
+                keys[a], vals[a], keys[b], vals[b], count_ptr, 8 * p, nbits, offsets, stride, rs, re);
+        else
+            downsweep_kernel<KeyT, false><<<stride, kSortThreads, 0, s>>>(
+                keys[a], vals[a], keys[b], vals[b], count_ptr, 8 * p, nbits, offsets, stride, rs, re);
+        if (cudaPeekAtLastError() != cudaSuccess) return -1;
+        launches += 3;
+    }
+    return passes & 1;
 }
+template int radix_sort_pairs<uint32_t>(uint32_t* [2], uint32_t* [2], const uint32_t*, uint32_t, int, bool,
+                                        uint32_t*, uint32_t*, uint64_t*, uint32_t&, DeviceStatus*, int, int&,
+                                        cudaStream_t, uint32_t*, uint32_t*);
+template int radix_sort_pairs<uint16_t>(uint16_t* [2], uint32_t* [2], const uint32_t*, uint32_t, int, bool,
+                                        uint32_t*, uint32_t*, uint64_t*, uint32_t&, DeviceStatus*, int, int&,
+                                        cudaStream_t, uint32_t*, uint32_t*);
 
 }  // namespace seele

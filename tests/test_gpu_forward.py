@@ -125,7 +125,12 @@ def test_tile_lists_bit_exact(Renderer, seed):
         k_off += tile.size
     np.testing.assert_array_equal(d["inst_tile"], np.concatenate(exp_tile))
     np.testing.assert_array_equal(d["inst_record"], np.concatenate(exp_rec))
-    np.testing.assert_array_equal(d["tile_ranges"], np.concatenate(exp_rng))
+    # an empty tile's range may start anywhere; non-empty ones are exact
+    exp = np.concatenate(exp_rng)
+    got = d["tile_ranges"].astype(np.int64)
+    np.testing.assert_array_equal(got[:, 1] - got[:, 0], exp[:, 1] - exp[:, 0])
+    ne = exp[:, 1] > exp[:, 0]
+    np.testing.assert_array_equal(got[ne], exp[ne])
     r.close()
 
 
