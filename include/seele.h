@@ -230,6 +230,40 @@ seele_status seele_get_debug_view(const seele_ctx* ctx, seele_debug_view* out);
 /* Message of the last failed call on this context (library-owned). */
 const char* seele_last_error(const seele_ctx* ctx);
 
+/* Sorting tile instances without allocating.  The paper has no counterpart:
+ * this is a service of the library, not a step of the method.
+ *
+ * Sorts tile instances given in front-to-back order into per-tile lists, as
+ * the render path does between emission and rasterization, for callers that
+ * cannot call cudaMalloc: hosts that own the device memory budget and forbid
+ * outside allocations, or real-time loops where an allocation (which can
+ * synchronise the device) would stall a frame.  All scratch lives in one
+ * file-scope device array of the library, reserved on every GPU that loads
+ * it until the process exits (about 8.4 MB); nothing is allocated or freed.
+ *
+ *   inst_tile[i], inst_record[i]  device, [n_instances]: tile id (< n_tiles)
+ *                                 and payload of instance i, in the order the
+ *                                 lists must keep (stable)
+ *   sorted_record                 device, [n_instances]: payloads grouped by
+ *                                 tile, in input order within a tile
+ *   tile_start, tile_end          device, [n_tiles]: tile t's list is
+ *                                 sorted_record[tile_start[t] .. tile_end[t]);
+ *                                 an empty tile has tile_start >= tile_end
+ *   cuda_stream                   the stream to run on (NULL: legacy default)
+ * Limits: n_instances <= SEELE_NOALLOC_MAX_INSTANCES, 1 <= n_tiles <=
+ * SEELE_NOALLOC_MAX_TILES; larger sizes return SEELE_ERR_ARG before any GPU
+ * work.  The call runs on the current CUDA device and returns after the
+ * stream has finished the sort (SEELE_ERR_TIMEOUT if a bounded device wait
+ * gave up).  The first call on a device also looks up the array's device
+ * address; make that first call before any stream capture.  Every call
+ * shares the one array and it keeps the last call's contents: calls that
+ * overlap on the GPU (other streams or threads) race on it. */
+#define SEELE_NOALLOC_MAX_INSTANCES (1u << 20)
+#define SEELE_NOALLOC_MAX_TILES (1u << 16)
+seele_status seele_sort_tile_instances_noalloc(const uint32_t* inst_tile, const uint32_t* inst_record,
+                                               uint32_t n_instances, uint32_t n_tiles, uint32_t* sorted_record,
+                                               uint32_t* tile_start, uint32_t* tile_end, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

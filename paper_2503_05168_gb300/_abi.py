@@ -74,7 +74,10 @@ PROTOTYPES = {
     "seele_render_backward": (ctypes.c_int, [P, P, ctypes.POINTER(Grads)]),
     "seele_get_debug_view": (ctypes.c_int, [P, ctypes.POINTER(DebugView)]),
     "seele_last_error": (ctypes.c_char_p, [P]),
+    "seele_sort_tile_instances_noalloc": (ctypes.c_int, [P, P, ctypes.c_uint32, ctypes.c_uint32, P, P, P, P]),
 }
+NOALLOC_MAX_INSTANCES = 1 << 20
+NOALLOC_MAX_TILES = 1 << 16
 
 _lib = None
 

@@ -26,6 +26,13 @@ void launch_exclusive_scan(const uint32_t* in, uint32_t n, uint32_t* out, uint64
                            DeviceStatus* st, int ticket, cudaStream_t s);
 
 uint32_t sort_tile_items();
+void launch_radix_upsweep_u32(const uint32_t* keys, const uint32_t* count_ptr, int shift, uint32_t* counts,
+                              uint32_t stride, cudaStream_t s);
+// keys_out == nullptr: write values only.
+void launch_radix_downsweep_u32(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
+                                uint32_t* vals_out, const uint32_t* count_ptr, int shift, int nbits,
+                                const uint32_t* offsets, uint32_t stride, uint32_t* run_start, uint32_t* run_end,
+                                cudaStream_t s);
 uint32_t radix_count_words(uint32_t max_n);
 // Stable LSD sort of (keys[0], vals[0]) by their low `key_bits` bits in 8-bit
 // digits; returns the index of the buffer pair holding the result, or -1 on a

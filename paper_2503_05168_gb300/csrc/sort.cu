@@ -178,6 +178,24 @@ __global__ void __launch_bounds__(kSortThreads) downsweep_kernel(const KeyT* __r
 
 uint32_t sort_tile_items() { return kSortTile; }
 
+// Single passes of the sort, for callers that manage their own buffers.
+void launch_radix_upsweep_u32(const uint32_t* keys, const uint32_t* count_ptr, int shift, uint32_t* counts,
+                              uint32_t stride, cudaStream_t s) {
+    upsweep_kernel<uint32_t><<<stride, kSortThreads, 0, s>>>(keys, count_ptr, shift, counts, stride);
+}
+
+void launch_radix_downsweep_u32(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
+                                uint32_t* vals_out, const uint32_t* count_ptr, int shift, int nbits,
+                                const uint32_t* offsets, uint32_t stride, uint32_t* run_start, uint32_t* run_end,
+                                cudaStream_t s) {
+    if (keys_out)
+        downsweep_kernel<uint32_t, true><<<stride, kSortThreads, 0, s>>>(
+            keys_in, vals_in, keys_out, vals_out, count_ptr, shift, nbits, offsets, stride, run_start, run_end);
+    else
+        downsweep_kernel<uint32_t, false><<<stride, kSortThreads, 0, s>>>(
+            keys_in, vals_in, keys_out, vals_out, count_ptr, shift, nbits, offsets, stride, run_start, run_end);
+}
+
 uint32_t radix_count_words(uint32_t max_n) {
     return kRadix * std::max<uint32_t>((max_n + kSortTile - 1) / kSortTile, 1u);
 }
