@@ -235,6 +235,49 @@ def _traffic(kernel: str, src_hash: str):
     return None
 
 
+def _fwd_bwd(args, device):
+    """ms of one forward + backward for an L1 loss, per raster mode."""
+    import torch
+
+    import scenegen
+    from paper_2503_05168_gb300 import Renderer
+
+    scene, cams, target = scenegen.clusters_1m(n=args.fwd_bwd_n)
+    r = Renderer(device)
+    r.load_scene(target)
+    r.set_cameras(cams)
+    tgt = r.render(mode="plain").clone()
+    params = {k: torch.from_numpy(np.ascontiguousarray(scene[k])).cuda(device)
+              for k in ("means", "log_scales", "quats", "opacity_logits", "sh")}
+    out = {}
+    for mode in ("cr", "plain"):
+        opts = r.make_options(mode=mode, opacity_filter=(mode == "cr"))
+
+        def step():
+            r.load_scene(dict(params, sh_degree=3), borrow=True)
+            img = r.render(options=opts)
+            g = torch.sign(img - tgt) / img.numel()      # d(mean |img - target|)
+            return r.render_backward(g)
+
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        k = max(3, min(args.steps, 20))
+        s.record()
+        for _ in range(k):
+            step()
+        e.record()
+        torch.cuda.synchronize()
+        out[f"{mode}_ms"] = s.elapsed_time(e) / k
+    out["workload"] = (f"clusters_1m: {args.fwd_bwd_n} Gaussians in 64 clusters, 1280x720, L1 loss vs a target "
+                       f"rendered from attributes + N(0, 0.01); gradients for all attributes; CR path with the "
+                       f"opacity filter, plain path without")
+    r.close()
+    return out
+
+
 def run_gpu(args):
     import torch
 
@@ -343,6 +386,11 @@ def run_gpu(args):
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": None, "kernel": dom, "note": f"peak of {peak_src} (MEASURED_PEAKS hbm_gbs)"}
 
+    # forward + backward for an L1 loss (the fine-tuning step of Sec. 3.5):
+    # 1M Gaussians shaped as the clustered scene, 1280x720, target rendered
+    # from attributes perturbed by N(0, 0.01)
+    fwd_bwd = _fwd_bwd(args, local)
+
     # end to end through the public API with host buffers: scene upload from
     # pinned host memory, render, image read back into pinned host memory
     pinned = {k: (torch.from_numpy(np.ascontiguousarray(v)).pin_memory() if isinstance(v, np.ndarray) else v)
@@ -379,7 +427,7 @@ def run_gpu(args):
         "stage_ms": {k: round(v, 4) for k, v in stage.items()},
         "stage_ms_plain": {k: round(v, 4) for k, v in stage_plain.items()},
         "n_visible": n_vis, "n_instances": K, "raster_work": work,
-        "roofline": roof, "e2e": e2e,
+        "roofline": roof, "e2e": e2e, "fwd_bwd": fwd_bwd,
         "gpu_launches": int(kernels_per_frame * args.steps),
         "clocks": clock_info,
     }
@@ -403,6 +451,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="seele", choices=["seele", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fwd-bwd-n", type=int, default=1_000_000)
     ap.add_argument("--n-gauss", type=int, default=3_000_000,
                     help="scene size (3M is the benchmark; smaller sizes are for profiling captures)")
     args = ap.parse_args()

@@ -19,7 +19,7 @@ import numpy as np
 from . import _abi
 from ._abi import SeeleError, lib
 
-__all__ = ["Renderer", "SeeleError", "lib", "default_options", "build"]
+__all__ = ["Renderer", "SeeleError", "SeeleRender", "render", "lib", "default_options", "build"]
 
 
 def build(force: bool = False) -> str:
@@ -198,6 +198,22 @@ class Renderer:
     def synchronize(self):
         self._check(lib().seele_synchronize(self._h))
 
+    def render_backward(self, dL_drgb) -> dict:
+        """Gradients of sum(dL_drgb * rgb) for the last render (CUDA tensors in
+        the scene layout): means, log_scales, quats, opacity_logits, sh."""
+        torch = self._torch
+        dL = dL_drgb.contiguous().to(torch.float32)
+        nc = (self.sh_degree + 1) ** 2
+        n = self.n
+        out = dict(means=torch.empty(n, 3, device=self.device), log_scales=torch.empty(n, 3, device=self.device),
+                   quats=torch.empty(n, 4, device=self.device), opacity_logits=torch.empty(n, device=self.device),
+                   sh=torch.empty(n, nc, 3, device=self.device))
+        G = _abi.Grads(out["means"].data_ptr(), out["log_scales"].data_ptr(), out["quats"].data_ptr(),
+                       out["opacity_logits"].data_ptr(), out["sh"].data_ptr())
+        self._sync_stream()
+        self._check(lib().seele_render_backward(self._h, ctypes.c_void_p(dL.data_ptr()), ctypes.byref(G)))
+        return out
+
     def images(self, flat):
         """Splits a flat planar buffer into per-camera [3, H, W] views."""
         res, off = [], 0
@@ -240,3 +256,47 @@ class Renderer:
             records=dev(v.records, 12 * R, torch.float32).reshape(R, 12), depth=dev(v.depth, R, torch.float32),
             n_contrib=dev(v.n_contrib, self.n_pixels, i32),
         )
+
+
+def _autograd_function():
+    import torch
+
+    class SeeleRender(torch.autograd.Function):
+        """Differentiable render: the forward pass borrows the attribute tensors
+        (no copy) and renders every camera of ``renderer``; the backward pass
+        runs the library's backward kernels.  One render per renderer may be
+        awaiting its backward at a time."""
+
+        @staticmethod
+        def forward(ctx, renderer, options, sh_degree, means, log_scales, quats, opacity_logits, sh):
+            renderer.load_scene(dict(means=means, log_scales=log_scales, quats=quats,
+                                     opacity_logits=opacity_logits, sh=sh, sh_degree=sh_degree), borrow=True)
+            img = renderer.render(options=options)
+            ctx.renderer = renderer
+            return img
+
+        @staticmethod
+        def backward(ctx, grad_img):
+            g = ctx.renderer.render_backward(grad_img)
+            return None, None, None, g["means"], g["log_scales"], g["quats"], g["opacity_logits"], g["sh"]
+
+    return SeeleRender
+
+
+class _Lazy:
+    fn = None
+
+
+def __getattr__(name):
+    if name == "SeeleRender":
+        if _Lazy.fn is None:
+            _Lazy.fn = _autograd_function()
+        return _Lazy.fn
+    raise AttributeError(name)
+
+
+def render(renderer: "Renderer", means, log_scales, quats, opacity_logits, sh, sh_degree: int = 3, **options):
+    """Differentiable render of every camera of ``renderer`` (flat planar RGB)."""
+    fn = __getattr__("SeeleRender")
+    o = renderer.make_options(**options)
+    return fn.apply(renderer, o, sh_degree, means, log_scales, quats, opacity_logits, sh)

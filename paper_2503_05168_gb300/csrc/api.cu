@@ -49,7 +49,7 @@ struct seele_ctx {
 
     // frame workspace
     DevBuf rec, rect, tiles, depth, visk[2], visv[2], offs, instk[2], instv[2], ranges, status, hist, lookback, T,
-        nc, rgb_tmp, sortcnt;
+        nc, rgb_tmp, sortcnt, grad_rec;
     size_t lookback_entries = 0;
     DeviceStatus* h_status = nullptr;  // pinned mirror of the device status
     cudaEvent_t ev[SEELE_NUM_STAGES + 1] = {};
@@ -251,7 +251,7 @@ void seele_destroy(seele_ctx* c) {
     DevBuf* all[] = {&c->pos_logit, &c->quat, &c->log_scale, &c->sh, &c->mask, &c->staging, &c->cams_dev,
                      &c->rec, &c->rect, &c->tiles, &c->depth, &c->visk[0], &c->visk[1], &c->visv[0],
                      &c->visv[1], &c->offs, &c->instk[0], &c->instk[1], &c->instv[0], &c->instv[1],
-                     &c->ranges, &c->status, &c->hist, &c->lookback, &c->T, &c->nc, &c->rgb_tmp, &c->sortcnt};
+                     &c->ranges, &c->status, &c->hist, &c->lookback, &c->T, &c->nc, &c->rgb_tmp, &c->sortcnt, &c->grad_rec};
     for (DevBuf* b : all) release(*b);
     if (c->h_status) cudaFreeHost(c->h_status);
     for (cudaEvent_t e : c->ev)
@@ -635,9 +635,46 @@ seele_status seele_render(seele_ctx* c, const seele_options* opt, float* out_rgb
 
 seele_status seele_render_backward(seele_ctx* c, const float* dL_drgb, const seele_grads* g) {
     if (!c) return SEELE_ERR_ARG;
-    if (!dL_drgb || !g) return fail(c, SEELE_ERR_ARG, "gradient buffers are required");
     if (!c->rendered) return fail(c, SEELE_ERR_STATE, "no render to differentiate");
-    return fail(c, SEELE_ERR_STATE, "backward pass not available in this build");
+    if (!dL_drgb || !g || !g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh)
+        return fail(c, SEELE_ERR_ARG, "dL_drgb and every gradient buffer are required");
+    SEELE_CUDA(c, cudaSetDevice(c->device));
+    const void* dev_ptrs[] = {dL_drgb, g->means, g->log_scales, g->quats, g->opacity_logits, g->sh};
+    for (const void* p : dev_ptrs)
+        if (!is_device_ptr(p)) return fail(c, SEELE_ERR_ARG, "backward buffers must be device memory");
+    const int ncam = (int)c->cams.size();
+    const uint64_t R = (uint64_t)c->n * ncam;
+    SEELE_CUDA(c, ensure(c->grad_rec, 48 * R));
+    cudaStream_t s = c->stream;
+    SEELE_CUDA(c, cudaMemsetAsync(c->grad_rec.p, 0, 48 * R, s));
+    RasterBwdArgs a;
+    a.starts = ptr<uint32_t>(c->ranges);
+    a.ends = ptr<uint32_t>(c->ranges) + c->n_tiles_total;
+    a.inst_rec = ptr<uint32_t>(c->instv[c->inst_final]);
+    a.rec = ptr<float4>(c->rec);
+    a.cams = ptr<const CamDev>(c->cams_dev);
+    a.n_cams = ncam;
+    a.n_tiles = c->n_tiles_total;
+    a.fp = c->last_fp;
+    a.cr = c->last_opt.mode == SEELE_MODE_CR;
+    a.group_w = c->last_opt.group_w;
+    a.group_h = c->last_opt.group_h;
+    a.dL_drgb = dL_drgb;
+    a.T_final = ptr<float>(c->T);
+    a.n_contrib = ptr<uint32_t>(c->nc);
+    a.grad_rec = ptr<float>(c->grad_rec);
+    if (!launch_raster_bwd(a, s)) return fail(c, SEELE_ERR_ARG, "no backward rasterizer for these options");
+    SEELE_LAUNCHED(c);
+    SceneDev sc;
+    sc.pos_logit = ptr<float4>(c->pos_logit);
+    sc.quat = ptr<float4>(c->quat);
+    sc.log_scale = ptr<float4>(c->log_scale);
+    sc.sh = ptr<float4>(c->sh);
+    sc.mask = nullptr;
+    launch_preprocess_bwd(sc, a.cams, c->last_fp, ptr<uint32_t>(c->tiles), a.grad_rec, g->means, g->log_scales,
+                          g->quats, g->opacity_logits, g->sh, s);
+    SEELE_LAUNCHED(c);
+    return SEELE_OK;
 }
 
 seele_status seele_get_debug_view(const seele_ctx* c, seele_debug_view* out) {

@@ -1,0 +1,436 @@
+// backward.cu -- gradients of the render for fine-tuning (Sec. 3.5: HP and
+// CR "do not participate in gradient descent": every skip and stop decision
+// of the forward pass is replayed and held fixed).
+//
+// raster_bwd_kernel: one CTA per tile, the same 2x2-pixels-per-thread layout
+//   as the forward pass.  Each pixel walks its list back to front from its
+//   last blended entry; the transmittance before an entry is recomputed from
+//   the stored final T by T_j = T_{j+1} / (1 - alpha_j) (not stored per
+//   entry), and S, the colour accumulated behind entry j, gives
+//     dC/dc_j = T_j alpha_j,   dC/dalpha_j = T_j c_j - S / (1 - alpha_j).
+//   Gradients w.r.t. the record (u, v, cA, cB, cC, log2 o, r, g, b) are
+//   summed over the warp's pixels and added with one atomic per value.
+// preprocess_bwd_kernel: one thread per Gaussian, summing over cameras, runs
+//   the chain rule back through the raster record, the conic, the EWA
+//   projection, the covariance, the quaternion and the SH colour.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace seele {
+
+constexpr float kLn2 = 0.69314718055994531f;
+
+__device__ __forceinline__ float ex2_approx_b(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+template <int TW, int TH, int PW, int PH, int GW, int GH, bool CR>
+__global__ void __launch_bounds__((TW / PW) * (TH / PH))
+    raster_bwd_kernel(const uint32_t* __restrict__ starts, const uint32_t* __restrict__ ends,
+                      const uint32_t* __restrict__ inst_rec, const float4* __restrict__ rec,
+                      const CamDev* __restrict__ cams, int n_cams, FrameParams fp, const float* __restrict__ dL_drgb,
+                      const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
+                      float* __restrict__ grad_rec) {
+    constexpr int NT = (TW / PW) * (TH / PH);
+    constexpr int NP = PW * PH;
+    constexpr int TXN = TW / PW;
+    __shared__ float4 s0[NT], s1[NT], s2[NT];
+    __shared__ uint32_t s_r[NT];
+    __shared__ uint32_t s_max;
+
+    const uint32_t gtile = blockIdx.x;
+    int lo = 0, hi = n_cams - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (cams[mid].tile_offset <= gtile) lo = mid; else hi = mid - 1;
+    }
+    const CamDev& C = cams[lo];
+    const uint32_t lt = gtile - C.tile_offset;
+    const int tx = (int)(lt % (uint32_t)C.tiles_x), ty = (int)(lt / (uint32_t)C.tiles_x);
+    const int t = threadIdx.x, lane = t & 31;
+    const int bx = tx * TW + (t % TXN) * PW, by = ty * TH + (t / TXN) * PH;
+    uint32_t start = __ldg(starts + gtile), end = __ldg(ends + gtile);
+    if (start >= end) start = end = 0;
+
+    const size_t plane = (size_t)C.W * C.H;
+    const float* gimg = dL_drgb + 3 * (size_t)C.pix_offset;
+    float T[NP], g0[NP], g1[NP], g2[NP], S0[NP], S1[NP], S2[NP];
+    uint32_t last[NP];
+    uint32_t my_max = 0;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const int x = bx + p % PW, y = by + p / PW;
+        T[p] = 1.f;
+        g0[p] = g1[p] = g2[p] = 0.f;
+        S0[p] = S1[p] = S2[p] = 0.f;
+        last[p] = 0;
+        if (x < C.W && y < C.H) {
+            const size_t o = (size_t)y * C.W + x;
+            T[p] = __ldg(T_final + C.pix_offset + o);
+            last[p] = __ldg(n_contrib + C.pix_offset + o);
+            g0[p] = __ldg(gimg + o);
+            g1[p] = __ldg(gimg + plane + o);
+            g2[p] = __ldg(gimg + 2 * plane + o);
+            my_max = max(my_max, last[p]);
+        }
+    }
+    if (t == 0) s_max = 0;
+    __syncthreads();
+    atomicMax(&s_max, my_max);
+    __syncthreads();
+    const uint32_t lmax = min(s_max, end - start);
+    const float fx0 = (float)bx + 0.5f, fy0 = (float)by + 0.5f;
+    const float amax = fp.alpha_max;
+
+    for (int b1 = (int)lmax; b1 > 0; b1 -= NT) {
+        const int b0 = max(0, b1 - NT);
+        __syncthreads();
+        if (t < b1 - b0) {
+            const uint32_t r = __ldg(inst_rec + start + b0 + t);
+            s_r[t] = r;
+            s0[t] = __ldg(rec + 3 * (size_t)r);
+            s1[t] = __ldg(rec + 3 * (size_t)r + 1);
+            s2[t] = __ldg(rec + 3 * (size_t)r + 2);
+        }
+        __syncthreads();
+        for (int k = b1 - b0 - 1; k >= 0; --k) {
+            const uint32_t j = (uint32_t)(b0 + k);  // list position
+            const float4 A = s0[k];
+            const float4 B = s1[k];
+            const float4 Cc = s2[k];
+            const float dx = fx0 - A.x, dy = fy0 - A.y;
+            // the forward pass's exponent, bit for bit
+            auto expo = [&](int i, int jj) {
+                const float ddx = dx + (float)i, ddy = dy + (float)jj;
+                return fmaf(fmaf(A.z, ddx, A.w * ddy), ddx, fmaf(B.x * ddy, ddy, B.y));
+            };
+            float du = 0.f, dv = 0.f, dcA = 0.f, dcB = 0.f, dcC = 0.f, dlo = 0.f, dr = 0.f, dg = 0.f, db = 0.f;
+            bool any = false;
+#pragma unroll
+            for (int gy = 0; gy < PH / GH; ++gy)
+#pragma unroll
+                for (int gx = 0; gx < PW / GW; ++gx) {
+                    bool lead = true;
+                    if (CR) {
+                        bool need = false;
+#pragma unroll
+                        for (int jj = 0; jj < GH; ++jj)
+#pragma unroll
+                            for (int i = 0; i < GW; ++i) need |= j < last[(gy * GH + jj) * PW + gx * GW + i];
+                        if (!need) continue;
+                        lead = expo(gx * GW, gy * GH) >= B.z;
+                    }
+                    if (!lead) continue;
+#pragma unroll
+                    for (int jj = 0; jj < GH; ++jj)
+#pragma unroll
+                        for (int i = 0; i < GW; ++i) {
+                            const int pi = gx * GW + i, pj = gy * GH + jj;
+                            const int p = pj * PW + pi;
+                            if (!(j < last[p])) continue;
+                            const float e = expo(pi, pj);
+                            if (e < B.z) continue;  // skipped in the forward pass too
+                            const float al = fminf(amax, ex2_approx_b(e));
+                            const float om = 1.f - al;
+                            const float Tb = T[p] / om;  // transmittance before this entry
+                            const float wgt = Tb * al;
+                            const float dal = g0[p] * (Tb * Cc.x - S0[p] / om) + g1[p] * (Tb * Cc.y - S1[p] / om) +
+                                              g2[p] * (Tb * Cc.z - S2[p] / om);
+                            dr = fmaf(wgt, g0[p], dr);
+                            dg = fmaf(wgt, g1[p], dg);
+                            db = fmaf(wgt, g2[p], db);
+                            S0[p] = fmaf(wgt, Cc.x, S0[p]);
+                            S1[p] = fmaf(wgt, Cc.y, S1[p]);
+                            S2[p] = fmaf(wgt, Cc.z, S2[p]);
+                            T[p] = Tb;
+                            any = true;
+                            if (al < amax) {  // at the clamp alpha is constant
+                                const float de = dal * al * kLn2;
+                                const float ddx = dx + (float)pi, ddy = dy + (float)pj;
+                                du -= de * (2.f * A.z * ddx + A.w * ddy);
+                                dv -= de * (A.w * ddx + 2.f * B.x * ddy);
+                                dcA = fmaf(de, ddx * ddx, dcA);
+                                dcB = fmaf(de, ddx * ddy, dcB);
+                                dcC = fmaf(de, ddy * ddy, dcC);
+                                dlo += de;
+                            }
+                        }
+                }
+            if (__any_sync(0xffffffffu, any)) {
+                float v[9] = {du, dv, dcA, dcB, dcC, dlo, dr, dg, db};
+#pragma unroll
+                for (int q = 0; q < 9; ++q)
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+                if (lane == 0) {
+                    float* G = grad_rec + 12 * (size_t)s_r[k];
+#pragma unroll
+                    for (int q = 0; q < 9; ++q)
+                        if (v[q] != 0.f) atomicAdd(G + q, v[q]);
+                }
+            }
+        }
+    }
+}
+
+// d/d(x, y, z) of the real SH basis of preprocess.cu (same polynomials).
+template <int DEG>
+__device__ __forceinline__ void sh_basis_grad(float x, float y, float z, float* Y, float (*dY)[3]) {
+    constexpr float c0 = 0.28209479177387814f, c1 = 0.48860251190291992f, c2a = 1.0925484305920792f,
+                    c2b = 0.31539156525252005f, c2c = 0.54627421529603959f, c3a = 0.59004358992664352f,
+                    c3b = 2.8906114426405538f, c3c = 0.45704579946446572f, c3d = 0.37317633259011540f,
+                    c3e = 1.4453057213202769f;
+    Y[0] = c0;
+    dY[0][0] = dY[0][1] = dY[0][2] = 0.f;
+    if (DEG > 0) {
+        Y[1] = -c1 * y; dY[1][0] = 0.f; dY[1][1] = -c1; dY[1][2] = 0.f;
+        Y[2] = c1 * z;  dY[2][0] = 0.f; dY[2][1] = 0.f; dY[2][2] = c1;
+        Y[3] = -c1 * x; dY[3][0] = -c1; dY[3][1] = 0.f; dY[3][2] = 0.f;
+    }
+    if (DEG > 1) {
+        const float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = c2a * x * y;  dY[4][0] = c2a * y; dY[4][1] = c2a * x; dY[4][2] = 0.f;
+        Y[5] = -c2a * y * z; dY[5][0] = 0.f; dY[5][1] = -c2a * z; dY[5][2] = -c2a * y;
+        Y[6] = c2b * (2.f * zz - xx - yy);
+        dY[6][0] = -2.f * c2b * x; dY[6][1] = -2.f * c2b * y; dY[6][2] = 4.f * c2b * z;
+        Y[7] = -c2a * x * z; dY[7][0] = -c2a * z; dY[7][1] = 0.f; dY[7][2] = -c2a * x;
+        Y[8] = c2c * (xx - yy); dY[8][0] = 2.f * c2c * x; dY[8][1] = -2.f * c2c * y; dY[8][2] = 0.f;
+        if (DEG > 2) {
+            Y[9] = -c3a * y * (3.f * xx - yy);
+            dY[9][0] = -6.f * c3a * x * y; dY[9][1] = -c3a * (3.f * xx - 3.f * yy); dY[9][2] = 0.f;
+            Y[10] = c3b * x * y * z;
+            dY[10][0] = c3b * y * z; dY[10][1] = c3b * x * z; dY[10][2] = c3b * x * y;
+            Y[11] = -c3c * y * (4.f * zz - xx - yy);
+            dY[11][0] = 2.f * c3c * x * y; dY[11][1] = -c3c * (4.f * zz - xx - 3.f * yy);
+            dY[11][2] = -8.f * c3c * y * z;
+            Y[12] = c3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+            dY[12][0] = -6.f * c3d * x * z; dY[12][1] = -6.f * c3d * y * z;
+            dY[12][2] = c3d * (6.f * zz - 3.f * xx - 3.f * yy);
+            Y[13] = -c3c * x * (4.f * zz - xx - yy);
+            dY[13][0] = -c3c * (4.f * zz - 3.f * xx - yy); dY[13][1] = 2.f * c3c * x * y;
+            dY[13][2] = -8.f * c3c * x * z;
+            Y[14] = c3e * z * (xx - yy);
+            dY[14][0] = 2.f * c3e * x * z; dY[14][1] = -2.f * c3e * y * z; dY[14][2] = c3e * (xx - yy);
+            Y[15] = -c3a * x * (xx - 3.f * yy);
+            dY[15][0] = -c3a * (3.f * xx - 3.f * yy); dY[15][1] = 6.f * c3a * x * y; dY[15][2] = 0.f;
+        }
+    }
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(128) preprocess_bwd_kernel(SceneDev sc, const CamDev* __restrict__ cams,
+                                                             FrameParams fp, const uint32_t* __restrict__ tiles,
+                                                             const float* __restrict__ grad_rec,
+                                                             float* __restrict__ d_means, float* __restrict__ d_ls,
+                                                             float* __restrict__ d_quat, float* __restrict__ d_logit,
+                                                             float* __restrict__ d_sh) {
+    constexpr int NC = (DEG + 1) * (DEG + 1);
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= fp.n) return;
+    float gm[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, glogit = 0.f;
+    float gsh[3 * NC];
+#pragma unroll
+    for (int i = 0; i < 3 * NC; ++i) gsh[i] = 0.f;
+    const float4 pl = __ldg(sc.pos_logit + g);
+    const float4 q4 = __ldg(sc.quat + g);
+    const float4 ls = __ldg(sc.log_scale + g);
+
+    for (int ci = 0; ci < fp.n_cams; ++ci) {
+        const size_t rid = (size_t)ci * fp.n + g;
+        if (__ldg(tiles + rid) == 0u) continue;
+        const float* G = grad_rec + 12 * rid;
+        const float gu = G[0], gv = G[1], gcA = G[2], gcB = G[3], gcC = G[4], glo = G[5];
+        const float grgb[3] = {G[6], G[7], G[8]};
+        const CamDev& C = cams[ci];
+
+        // ---- recompute the forward quantities
+        const float X = fmaf(C.R[0], pl.x, fmaf(C.R[1], pl.y, fmaf(C.R[2], pl.z, C.t[0])));
+        const float Y = fmaf(C.R[3], pl.x, fmaf(C.R[4], pl.y, fmaf(C.R[5], pl.z, C.t[1])));
+        const float Z = fmaf(C.R[6], pl.x, fmaf(C.R[7], pl.y, fmaf(C.R[8], pl.z, C.t[2])));
+        const float xz = X / Z, yz = Y / Z;
+        const float qn2 = q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w;
+        const float qinv = rsqrtf(qn2);
+        const float qw = q4.x * qinv, qx = q4.y * qinv, qy = q4.z * qinv, qz = q4.w * qinv;
+        const float s[3] = {expf(ls.x), expf(ls.y), expf(ls.z)};
+        float R[9];
+        R[0] = 1.f - 2.f * (qy * qy + qz * qz); R[1] = 2.f * (qx * qy - qw * qz); R[2] = 2.f * (qx * qz + qw * qy);
+        R[3] = 2.f * (qx * qy + qw * qz); R[4] = 1.f - 2.f * (qx * qx + qz * qz); R[5] = 2.f * (qy * qz - qw * qx);
+        R[6] = 2.f * (qx * qz - qw * qy); R[7] = 2.f * (qy * qz + qw * qx); R[8] = 1.f - 2.f * (qx * qx + qy * qy);
+        float WM[9];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                WM[3 * i + j] = (C.R[3 * i] * R[j] + C.R[3 * i + 1] * R[3 + j] + C.R[3 * i + 2] * R[6 + j]) * s[j];
+        const float jx = C.fx / Z, jy = C.fy / Z;
+        float N0[3], N1[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            N0[j] = jx * (WM[j] - xz * WM[6 + j]);
+            N1[j] = jy * (WM[3 + j] - yz * WM[6 + j]);
+        }
+        const float a = N0[0] * N0[0] + N0[1] * N0[1] + N0[2] * N0[2] + fp.dilation;
+        const float b = N0[0] * N1[0] + N0[1] * N1[1] + N0[2] * N1[2];
+        const float c = N1[0] * N1[0] + N1[1] * N1[1] + N1[2] * N1[2] + fp.dilation;
+        const float det = a * c - b * b;
+        const float inv = 1.f / det;
+        const float Pa = c * inv, Pb = -b * inv, Pc = a * inv;  // conic [[Pa, Pb], [Pb, Pc]]
+
+        // ---- record -> conic: cA = -L/2 Pa, cB = -L Pb, cC = -L/2 Pc
+        const float gPa = -0.5f * kLog2e * gcA, gPb = -kLog2e * gcB, gPc = -0.5f * kLog2e * gcC;
+        // conic = Sigma'^-1: dL/dSigma' = -P Gs P with Gs the symmetric gradient
+        // [[gPa, gPb/2], [gPb/2, gPc]]
+        const float h = 0.5f * gPb;
+        const float m00 = gPa * Pa + h * Pb, m01 = gPa * Pb + h * Pc;  // (Gs P) row 0
+        const float m10 = h * Pa + gPc * Pb, m11 = h * Pb + gPc * Pc;  // (Gs P) row 1
+        const float S00 = -(Pa * m00 + Pb * m10);
+        const float S01 = -(Pa * m01 + Pb * m11);
+        const float S11 = -(Pb * m01 + Pc * m11);
+        // Sigma' = [N0.N0, N0.N1; N1.N0, N1.N1] + dilation
+        float gN0[3], gN1[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            gN0[j] = 2.f * S00 * N0[j] + 2.f * S01 * N1[j];
+            gN1[j] = 2.f * S11 * N1[j] + 2.f * S01 * N0[j];
+        }
+        // N0 = jx (WM0 - xz WM2), N1 = jy (WM1 - yz WM2)
+        float gWM[9];
+        float gjx = 0.f, gjy = 0.f, gxz = 0.f, gyz = 0.f;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            gjx += gN0[j] * (WM[j] - xz * WM[6 + j]);
+            gjy += gN1[j] * (WM[3 + j] - yz * WM[6 + j]);
+            gxz -= gN0[j] * jx * WM[6 + j];
+            gyz -= gN1[j] * jy * WM[6 + j];
+            gWM[j] = gN0[j] * jx;
+            gWM[3 + j] = gN1[j] * jy;
+            gWM[6 + j] = -gN0[j] * jx * xz - gN1[j] * jy * yz;
+        }
+        // screen position u = fx xz + cx, v = fy yz + cy
+        gxz += gu * C.fx;
+        gyz += gv * C.fy;
+        // xz = X / Z, yz = Y / Z, jx = fx / Z, jy = fy / Z
+        const float iz = 1.f / Z;
+        const float gX = gxz * iz, gY = gyz * iz;
+        const float gZ = -(gxz * xz + gyz * yz) * iz - (gjx * jx + gjy * jy) * iz;
+        // X_cam = W m + t
+#pragma unroll
+        for (int i = 0; i < 3; ++i) gm[i] += C.R[i] * gX + C.R[3 + i] * gY + C.R[6 + i] * gZ;
+        // WM = W R diag(s): gM = W^T gWM, then split into R and s
+        float gRs[9];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) gRs[3 * i + j] = C.R[i] * gWM[j] + C.R[3 + i] * gWM[3 + j] + C.R[6 + i] * gWM[6 + j];
+        float gR[9];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            float acc = 0.f;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                gR[3 * i + j] = gRs[3 * i + j] * s[j];
+                acc += gRs[3 * i + j] * R[3 * i + j];
+            }
+            gls[j] += acc * s[j];  // d/d log s = s d/ds
+        }
+        // rotation of the unit quaternion, then the normalisation
+        const float gqw = 2.f * (-qz * gR[1] + qy * gR[2] + qz * gR[3] - qx * gR[5] - qy * gR[6] + qx * gR[7]);
+        const float gqx = 2.f * (qy * gR[1] + qz * gR[2] + qy * gR[3] - 2.f * qx * gR[4] - qw * gR[5] + qz * gR[6] +
+                                 qw * gR[7] - 2.f * qx * gR[8]);
+        const float gqy = 2.f * (-2.f * qy * gR[0] + qx * gR[1] + qw * gR[2] + qx * gR[3] + qz * gR[5] - qw * gR[6] +
+                                 qz * gR[7] - 2.f * qy * gR[8]);
+        const float gqz = 2.f * (-2.f * qz * gR[0] - qw * gR[1] + qx * gR[2] + qw * gR[3] - 2.f * qz * gR[4] +
+                                 qy * gR[5] + qx * gR[6] + qy * gR[7]);
+        const float dotq = qw * gqw + qx * gqx + qy * gqy + qz * gqz;
+        gq[0] += (gqw - qw * dotq) * qinv;
+        gq[1] += (gqx - qx * dotq) * qinv;
+        gq[2] += (gqy - qy * dotq) * qinv;
+        gq[3] += (gqz - qz * dotq) * qinv;
+        // opacity: log2 o = -log2(1 + e^-l)  ->  d/dl = (1 - o) / ln 2
+        const float o = 1.f / (1.f + expf(-pl.w));
+        glogit += glo * (1.f - o) / kLn2;
+        // colour: rgb = max(0, sum_k sh_k Y_k(d) + 0.5), d = unit(m - campos)
+        float dd[3] = {pl.x - C.campos[0], pl.y - C.campos[1], pl.z - C.campos[2]};
+        const float rn = rsqrtf(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+        dd[0] *= rn;
+        dd[1] *= rn;
+        dd[2] *= rn;
+        float Yb[NC], dY[NC][3];
+        sh_basis_grad<DEG>(dd[0], dd[1], dd[2], Yb, dY);
+        float gdir[3] = {0.f, 0.f, 0.f};
+        constexpr int NPL = (3 * NC + 3) / 4;
+        float shf[4 * NPL];
+#pragma unroll
+        for (int jp = 0; jp < NPL; ++jp) {
+            const float4 vv = __ldg(sc.sh + (size_t)jp * fp.n + g);
+            shf[4 * jp] = vv.x;
+            shf[4 * jp + 1] = vv.y;
+            shf[4 * jp + 2] = vv.z;
+            shf[4 * jp + 3] = vv.w;
+        }
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float raw = 0.5f;
+#pragma unroll
+            for (int k = 0; k < NC; ++k) raw = fmaf(shf[3 * k + ch], Yb[k], raw);
+            const float gc = raw > 0.f ? grgb[ch] : 0.f;
+            if (gc == 0.f) continue;
+#pragma unroll
+            for (int k = 0; k < NC; ++k) {
+                gsh[3 * k + ch] = fmaf(Yb[k], gc, gsh[3 * k + ch]);
+                const float w = shf[3 * k + ch] * gc;
+                gdir[0] = fmaf(w, dY[k][0], gdir[0]);
+                gdir[1] = fmaf(w, dY[k][1], gdir[1]);
+                gdir[2] = fmaf(w, dY[k][2], gdir[2]);
+            }
+        }
+        const float dot = dd[0] * gdir[0] + dd[1] * gdir[1] + dd[2] * gdir[2];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) gm[i] += (gdir[i] - dd[i] * dot) * rn;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        d_means[3 * (size_t)g + i] = gm[i];
+        d_ls[3 * (size_t)g + i] = gls[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) d_quat[4 * (size_t)g + i] = gq[i];
+    d_logit[g] = glogit;
+#pragma unroll
+    for (int i = 0; i < 3 * NC; ++i) d_sh[(size_t)g * 3 * NC + i] = gsh[i];
+}
+
+template <int TW, int TH, int PW, int PH, int GW, int GH, bool CR>
+static void launch_bwd_one(const RasterBwdArgs& a, cudaStream_t s) {
+    constexpr int NT = (TW / PW) * (TH / PH);
+    raster_bwd_kernel<TW, TH, PW, PH, GW, GH, CR><<<a.n_tiles, NT, 0, s>>>(
+        a.starts, a.ends, a.inst_rec, a.rec, a.cams, a.n_cams, a.fp, a.dL_drgb, a.T_final, a.n_contrib,
+        a.grad_rec);
+}
+
+bool launch_raster_bwd(const RasterBwdArgs& a, cudaStream_t s) {
+    if (a.n_tiles == 0) return true;
+    if (a.fp.tile_w != 16 || a.fp.tile_h != 16) return false;
+    if (!a.cr) launch_bwd_one<16, 16, 2, 2, 1, 1, false>(a, s);
+    else if (a.group_w == 2 && a.group_h == 2) launch_bwd_one<16, 16, 2, 2, 2, 2, true>(a, s);
+    else if (a.group_w == 1 && a.group_h == 1) launch_bwd_one<16, 16, 2, 2, 1, 1, true>(a, s);
+    else if (a.group_w == 2 && a.group_h == 4) launch_bwd_one<16, 16, 2, 4, 2, 4, true>(a, s);
+    else return false;
+    return true;
+}
+
+void launch_preprocess_bwd(const SceneDev& sc, const CamDev* cams, const FrameParams& fp, const uint32_t* tiles,
+                           const float* grad_rec, float* d_means, float* d_ls, float* d_quat, float* d_logit,
+                           float* d_sh, cudaStream_t s) {
+    const int blocks = (fp.n + 127) / 128;
+    switch (fp.sh_degree) {
+        case 0: preprocess_bwd_kernel<0><<<blocks, 128, 0, s>>>(sc, cams, fp, tiles, grad_rec, d_means, d_ls, d_quat, d_logit, d_sh); break;
+        case 1: preprocess_bwd_kernel<1><<<blocks, 128, 0, s>>>(sc, cams, fp, tiles, grad_rec, d_means, d_ls, d_quat, d_logit, d_sh); break;
+        case 2: preprocess_bwd_kernel<2><<<blocks, 128, 0, s>>>(sc, cams, fp, tiles, grad_rec, d_means, d_ls, d_quat, d_logit, d_sh); break;
+        default: preprocess_bwd_kernel<3><<<blocks, 128, 0, s>>>(sc, cams, fp, tiles, grad_rec, d_means, d_ls, d_quat, d_logit, d_sh); break;
+    }
+}
+
+}  // namespace seele

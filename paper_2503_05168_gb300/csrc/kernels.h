@@ -67,4 +67,25 @@ struct RasterArgs {
 };
 bool launch_raster_fwd(const RasterArgs& a, cudaStream_t s);
 
+struct RasterBwdArgs {
+    const uint32_t* starts;
+    const uint32_t* ends;
+    const uint32_t* inst_rec;
+    const float4* rec;
+    const CamDev* cams;
+    int n_cams;
+    uint32_t n_tiles;
+    FrameParams fp;
+    bool cr;
+    int group_w, group_h;
+    const float* dL_drgb;       // planar, the forward's output layout
+    const float* T_final;
+    const uint32_t* n_contrib;
+    float* grad_rec;            // [R][12]: d(u, v, cA, cB, cC, log2 o, r, g, b), zeroed by the caller
+};
+bool launch_raster_bwd(const RasterBwdArgs& a, cudaStream_t s);
+void launch_preprocess_bwd(const SceneDev& sc, const CamDev* cams, const FrameParams& fp, const uint32_t* tiles,
+                           const float* grad_rec, float* d_means, float* d_ls, float* d_quat, float* d_logit,
+                           float* d_sh, cudaStream_t s);
+
 }  // namespace seele
