@@ -68,7 +68,7 @@ enum { SEELE_SCENE_COPY = 0, SEELE_SCENE_BORROW = 1 };
  * until the next seele_load_scene or seele_destroy, and are re-read by every
  * render (their contents may change between renders, as in training). */
 typedef struct {
-    int64_t n;                    /* number of Gaussians, 1 <= n, n * cameras < 2^31 */
+    int64_t n;                    /* number of Gaussians, 1 <= n <= 16776960, n * cameras < 2^31 */
     int32_t sh_degree;            /* 0..3 */
     int32_t flags;                /* SEELE_SCENE_COPY or SEELE_SCENE_BORROW */
     const float* means;           /* [n][3] */
@@ -97,8 +97,13 @@ enum {
     SEELE_RENDER_ASYNC = 1,       /* do not synchronise; see seele_render */
     SEELE_RENDER_PROFILE = 2,     /* time each stage with CUDA events into seele_stats.stage_ms
                                      (synchronous renders only) */
-    SEELE_RENDER_COUNT = 4        /* count the rasterizer's work into seele_stats (slower
+    SEELE_RENDER_COUNT = 4,       /* count the rasterizer's work into seele_stats (slower
                                      variant; synchronous renders only) */
+    SEELE_RENDER_GRAPH = 8        /* capture the frame into a CUDA graph on first use and
+                                     replay it while the camera count and resolutions, the
+                                     options, the instance capacity, the scene and the
+                                     output pointers stay the same; camera poses may change
+                                     between replays.  Device outputs only */
 };
 
 /* Stages timed by SEELE_RENDER_PROFILE, in launch order. */
@@ -118,7 +123,7 @@ enum {
 typedef struct {
     int32_t mode;                 /* PLAIN (Sec. 3.1) or CR (Alg. 1) */
     int32_t group_w, group_h;     /* CR pixel group: 2x2 (default), 1x1, 2x4 */
-    int32_t tile_w, tile_h;       /* 16x16 (default) */
+    int32_t tile_w, tile_h;       /* 16x16 (default), 32x8 or 32x16 */
     int32_t opacity_filter;       /* 1: support min(2 ln(o/alpha_theta), 9) (Eqn. 5) */
     int32_t cluster_filter;       /* 1: render only the selected view clusters (Sec. 3.3) */
     int32_t n_neighbors;          /* M of Sec. 3.3 (3) */
@@ -226,6 +231,18 @@ typedef struct {
 } seele_debug_view;
 
 seele_status seele_get_debug_view(const seele_ctx* ctx, seele_debug_view* out);
+
+/* Per-view completion times of the last completed render: out_ms[j] = time
+ * from the start of preprocessing to the moment the last tile of camera j
+ * finished blending (device clock).  n must equal the camera count; waits for
+ * the stream. */
+seele_status seele_get_view_times(const seele_ctx* ctx, float* out_ms, int32_t n);
+
+/* Chooses the tile shape (16x16, 32x8 or 32x16) that renders the current
+ * scene and cameras fastest with *inout's other options, by timing a few
+ * renders of each; writes it into *inout and the time per render into
+ * *best_ms (nullable).  Leaves no render state behind. */
+seele_status seele_autotune(seele_ctx* ctx, seele_options* inout, float* best_ms);
 
 /* Message of the last failed call on this context (library-owned). */
 const char* seele_last_error(const seele_ctx* ctx);

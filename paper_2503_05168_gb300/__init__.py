@@ -160,7 +160,7 @@ class Renderer:
     # -- rendering -----------------------------------------------------------
     @staticmethod
     def make_options(mode="plain", group=(2, 2), tile=(16, 16), opacity_filter=False, cluster_filter=False,
-                     n_neighbors=3, sync=True, profile=False, count=False, **kw) -> _abi.Options:
+                     n_neighbors=3, sync=True, profile=False, count=False, graph=False, **kw) -> _abi.Options:
         o = default_options()
         o.mode = _abi.MODE_CR if mode == "cr" else _abi.MODE_PLAIN
         o.group_w, o.group_h = group
@@ -172,7 +172,7 @@ class Renderer:
             if k in kw:
                 setattr(o, k, float(kw[k]))
         o.flags = ((0 if sync else _abi.RENDER_ASYNC) | (_abi.RENDER_PROFILE if profile else 0) |
-                   (_abi.RENDER_COUNT if count else 0))
+                   (_abi.RENDER_COUNT if count else 0) | (_abi.RENDER_GRAPH if graph else 0))
         return o
 
     def render(self, out=None, out_T=None, options: _abi.Options | None = None, **kw):
@@ -197,6 +197,21 @@ class Renderer:
 
     def synchronize(self):
         self._check(lib().seele_synchronize(self._h))
+
+    def view_times(self):
+        """Per-camera ms from the start of preprocessing to the view's last tile."""
+        n = len(self.cameras)
+        arr = (ctypes.c_float * n)()
+        self._check(lib().seele_get_view_times(self._h, arr, n))
+        return list(arr)
+
+    def autotune(self, options: _abi.Options | None = None, **kw):
+        """Fastest tile shape for the current scene and cameras: (options, ms)."""
+        o = options if options is not None else self.make_options(**kw)
+        ms = ctypes.c_float()
+        self._sync_stream()
+        self._check(lib().seele_autotune(self._h, ctypes.byref(o), ctypes.byref(ms)))
+        return o, ms.value
 
     def render_backward(self, dL_drgb) -> dict:
         """Gradients of sum(dL_drgb * rgb) for the last render (CUDA tensors in

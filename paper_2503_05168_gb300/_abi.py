@@ -18,6 +18,7 @@ MODE_PLAIN, MODE_CR = 0, 1
 RENDER_ASYNC = 1
 RENDER_PROFILE = 2
 RENDER_COUNT = 4
+RENDER_GRAPH = 8
 STAGES = ("preprocess", "compact", "depth_sort", "tile_scan", "emit", "tile_sort", "ranges", "raster")
 
 P = ctypes.c_void_p
@@ -74,6 +75,8 @@ PROTOTYPES = {
     "seele_render_backward": (ctypes.c_int, [P, P, ctypes.POINTER(Grads)]),
     "seele_get_debug_view": (ctypes.c_int, [P, ctypes.POINTER(DebugView)]),
     "seele_last_error": (ctypes.c_char_p, [P]),
+    "seele_get_view_times": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_float), ctypes.c_int32]),
+    "seele_autotune": (ctypes.c_int, [P, ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_float)]),
     "seele_sort_tile_instances_noalloc": (ctypes.c_int, [P, P, ctypes.c_uint32, ctypes.c_uint32, P, P, P, P]),
 }
 NOALLOC_MAX_INSTANCES = 1 << 20

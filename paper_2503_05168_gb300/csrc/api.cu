@@ -54,6 +54,25 @@ struct seele_ctx {
     DeviceStatus* h_status = nullptr;  // pinned mirror of the device status
     cudaEvent_t ev[SEELE_NUM_STAGES + 1] = {};
     bool profiling = false;
+
+    // pinned staging ring for camera constants (no pageable copies in a frame)
+    struct CamSlot {
+        CamDev* host = nullptr;
+        size_t cap = 0;
+        cudaEvent_t done = nullptr;
+        bool used = false;
+    } cam_ring[4];
+    int cam_next = 0;
+
+    // per-view completion times: [frame start][end per camera][done tiles per camera]
+    DevBuf viewt;
+
+    // captured frame (SEELE_RENDER_GRAPH)
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t cap_stream = nullptr;   // capture happens here (the legacy stream cannot capture)
+    std::vector<uint64_t> gkey;
+    int g_launches = 0, g_fin = 0;
+    uint64_t scene_gen = 0;
     uint64_t capacity = 0;
     uint32_t epoch = 1;
     bool status_pending = false;
@@ -201,6 +220,267 @@ int enqueue_tile_sort(seele_ctx* c, const uint32_t* order, const uint2* rect, co
     return fin;
 }
 
+struct FrameInfo {
+    int ncam = 0;
+    uint64_t R = 0, tiles_total = 0, pix_total = 0, cap = 0;
+    bool short_keys = false, rgb_dev = true, T_dev = true;
+    int tile_bits = 1;
+    uint32_t cnt_words = 0;
+    size_t lb_entries = 0;
+    FrameParams fp{};
+};
+
+bool tile_supported(int w, int h) { return (w == 16 && h == 16) || (w == 32 && h == 8) || (w == 32 && h == 16); }
+
+seele_status check_options(seele_ctx* c, const seele_options* opt) {
+    if (opt->mode != SEELE_MODE_PLAIN && opt->mode != SEELE_MODE_CR) return fail(c, SEELE_ERR_ARG, "bad mode");
+    if (!tile_supported(opt->tile_w, opt->tile_h))
+        return fail(c, SEELE_ERR_ARG, "tile size %dx%d not supported (16x16, 32x8, 32x16)", opt->tile_w, opt->tile_h);
+    if (opt->mode == SEELE_MODE_CR && !group_supported(opt->group_w, opt->group_h))
+        return fail(c, SEELE_ERR_ARG, "pixel group %dx%d not supported (1x1, 2x2, 2x4)", opt->group_w, opt->group_h);
+    if (!(opt->alpha_min > 0 && opt->alpha_min < opt->alpha_max && opt->alpha_max <= 1.0f))
+        return fail(c, SEELE_ERR_ARG, "need 0 < alpha_min < alpha_max <= 1");
+    if (!(opt->t_stop > 0 && opt->t_stop < 1)) return fail(c, SEELE_ERR_ARG, "need 0 < t_stop < 1");
+    if (opt->cluster_filter && (c->n_clusters <= 0 || !c->has_mask))
+        return fail(c, SEELE_ERR_STATE, "cluster_filter needs a scene with view clusters");
+    if (opt->n_neighbors < 0) return fail(c, SEELE_ERR_ARG, "n_neighbors must be >= 0");
+    return SEELE_OK;
+}
+
+// Camera constants for the options' tile size (host only).
+void build_cameras(seele_ctx* c, const seele_options* opt, uint64_t& tiles_total, uint64_t& pix_total) {
+    const int ncam = (int)c->cams.size();
+    c->camdev.resize(ncam);
+    tiles_total = 0;
+    pix_total = 0;
+    for (int i = 0; i < ncam; ++i) {
+        const seele_camera& k = c->cams[i];
+        CamDev& d = c->camdev[i];
+        std::memset(&d, 0, sizeof d);
+        const float* w = k.world_to_cam;
+        const float Rm[9] = {w[0], w[1], w[2], w[4], w[5], w[6], w[8], w[9], w[10]};
+        const float t[3] = {w[3], w[7], w[11]};
+        std::memcpy(d.R, Rm, sizeof Rm);
+        std::memcpy(d.t, t, sizeof t);
+        d.fx = k.fx;
+        d.fy = k.fy;
+        d.cx = k.cx;
+        d.cy = k.cy;
+        for (int j = 0; j < 3; ++j)
+            d.campos[j] = (float)(-((double)Rm[j] * t[0] + (double)Rm[3 + j] * t[1] + (double)Rm[6 + j] * t[2]));
+        d.lim_x = (float)(1.3 * k.width / (2.0 * k.fx));
+        d.lim_y = (float)(1.3 * k.height / (2.0 * k.fy));
+        d.near_z = k.near_z;
+        d.W = k.width;
+        d.H = k.height;
+        d.tiles_x = (k.width + opt->tile_w - 1) / opt->tile_w;
+        d.tiles_y = (k.height + opt->tile_h - 1) / opt->tile_h;
+        d.tile_offset = (uint32_t)tiles_total;
+        d.pix_offset = (uint32_t)pix_total;
+        d.sel_bits = opt->cluster_filter ? select_clusters(c, k, opt->n_neighbors) : 0xffffffffu;
+        tiles_total += (uint64_t)d.tiles_x * d.tiles_y;
+        pix_total += (uint64_t)k.width * k.height;
+    }
+}
+
+void fill_params(seele_ctx* c, const seele_options* opt, FrameInfo& f) {
+    FrameParams& fp = f.fp;
+    fp = FrameParams{};
+    fp.n = (int32_t)c->n;
+    fp.n_cams = f.ncam;
+    fp.sh_degree = c->sh_degree;
+    fp.tile_w = opt->tile_w;
+    fp.tile_h = opt->tile_h;
+    fp.opacity_filter = opt->opacity_filter ? 1 : 0;
+    fp.use_mask = opt->cluster_filter ? 1 : 0;
+    fp.alpha_min = opt->alpha_min;
+    fp.alpha_max = opt->alpha_max;
+    fp.t_stop = opt->t_stop;
+    fp.dilation = 0.3f;
+    fp.frustum_slack = 1.3f;
+    fp.n_tiles_total = (uint32_t)f.tiles_total;
+}
+
+// Sizes every buffer of a frame at the current capacity (may allocate).
+seele_status size_frame(seele_ctx* c, FrameInfo& f) {
+    const uint64_t R = f.R, cap = f.cap;
+    SEELE_CUDA(c, ensure(c->cams_dev, sizeof(CamDev) * f.ncam));
+    SEELE_CUDA(c, ensure(c->rec, 48 * R));
+    SEELE_CUDA(c, ensure(c->rect, 8 * R));
+    SEELE_CUDA(c, ensure(c->tiles, 4 * R));
+    SEELE_CUDA(c, ensure(c->depth, 4 * R));
+    for (int i = 0; i < 2; ++i) {
+        SEELE_CUDA(c, ensure(c->visk[i], 4 * R));
+        SEELE_CUDA(c, ensure(c->visv[i], 4 * R));
+        SEELE_CUDA(c, ensure(c->instk[i], 4 * cap));
+        SEELE_CUDA(c, ensure(c->instv[i], 4 * cap));
+    }
+    SEELE_CUDA(c, ensure(c->offs, 4 * R));
+    SEELE_CUDA(c, ensure(c->ranges, 8 * f.tiles_total));  // starts[n_tiles], then ends[n_tiles]
+    SEELE_CUDA(c, ensure(c->status, sizeof(DeviceStatus)));
+    SEELE_CUDA(c, ensure(c->T, 4 * f.pix_total));
+    SEELE_CUDA(c, ensure(c->nc, 4 * f.pix_total));
+    SEELE_CUDA(c, ensure(c->viewt, 12ull * f.ncam + 8));
+    if (!f.rgb_dev) SEELE_CUDA(c, ensure(c->rgb_tmp, 12 * f.pix_total));
+    f.cnt_words = radix_count_words((uint32_t)std::max<uint64_t>(R, cap));
+    SEELE_CUDA(c, ensure(c->sortcnt, 8ull * f.cnt_words));
+    // look-back status words of the scans of one frame (cleared every frame)
+    const uint32_t items = scan_tiles_per_launch();
+    f.lb_entries = (std::max<uint64_t>(R, f.cnt_words) + items - 1) / items + 1;
+    SEELE_CUDA(c, ensure(c->lookback, 8 * f.lb_entries));
+    return SEELE_OK;
+}
+
+// Copies the camera constants through a ring of pinned staging buffers; a
+// slot is refilled only once its previous copy has run.
+seele_status upload_cameras(seele_ctx* c) {
+    auto& slot = c->cam_ring[c->cam_next];
+    c->cam_next = (c->cam_next + 1) % 4;
+    const size_t bytes = sizeof(CamDev) * c->camdev.size();
+    if (!slot.done) SEELE_CUDA(c, cudaEventCreateWithFlags(&slot.done, cudaEventDisableTiming));
+    if (slot.used) SEELE_CUDA(c, cudaEventSynchronize(slot.done));
+    if (slot.cap < bytes) {
+        if (slot.host) cudaFreeHost(slot.host);
+        slot.host = nullptr;
+        slot.cap = 0;
+        SEELE_CUDA(c, cudaMallocHost(&slot.host, bytes));
+        slot.cap = bytes;
+    }
+    std::memcpy(slot.host, c->camdev.data(), bytes);
+    SEELE_CUDA(c, cudaMemcpyAsync(c->cams_dev.p, slot.host, bytes, cudaMemcpyHostToDevice, c->stream));
+    SEELE_CUDA(c, cudaEventRecord(slot.done, c->stream));
+    slot.used = true;
+    return SEELE_OK;
+}
+
+// Everything a captured frame depends on besides the camera poses.
+std::vector<uint64_t> graph_key(const seele_ctx* c, const seele_options* opt, const FrameInfo& f,
+                                const float* rgb_target, const float* T_copy) {
+    std::vector<uint64_t> k;
+    k.push_back(c->scene_gen);
+    k.push_back((uint64_t)f.ncam);
+    for (const auto& cam : c->cams) k.push_back(((uint64_t)cam.width << 32) | (uint32_t)cam.height);
+    seele_options o = *opt;
+    o.flags = 0;
+    uint64_t words[(sizeof o + 7) / 8] = {};
+    std::memcpy(words, &o, sizeof o);
+    for (uint64_t w : words) k.push_back(w);
+    k.push_back(f.cap);
+    k.push_back((uint64_t)(uintptr_t)rgb_target);
+    k.push_back((uint64_t)(uintptr_t)T_copy);
+    k.push_back((uint64_t)(uintptr_t)c->rec.p);
+    k.push_back((uint64_t)(uintptr_t)c->instk[0].p);
+    return k;
+}
+
+// Enqueues one frame on the context's stream: clears, kernels, status
+// read-back.  Allocates nothing and never waits, so it can be captured.
+seele_status enqueue_frame(seele_ctx* c, const seele_options* opt, const FrameInfo& f, float* rgb_target,
+                           float* T_copy, bool count, int& launches, int& fin) {
+    const uint64_t R = f.R, cap = f.cap, tiles_total = f.tiles_total;
+    const int ncam = f.ncam;
+    cudaStream_t s = c->stream;
+    DeviceStatus* st = ptr<DeviceStatus>(c->status);
+    uint64_t* lb = ptr<uint64_t>(c->lookback);
+    launches = 0;
+#define SEELE_MARK(k) \
+    if (c->profiling) SEELE_CUDA(c, cudaEventRecord(c->ev[k], s))
+
+    SEELE_CUDA(c, cudaMemsetAsync(st, 0, sizeof(DeviceStatus), s));
+    SEELE_CUDA(c, cudaMemsetAsync(lb, 0, 8 * f.lb_entries, s));
+    SEELE_CUDA(c, cudaMemsetAsync(c->viewt.p, 0, 12ull * ncam + 8, s));
+    SEELE_CUDA(c, cudaMemsetAsync(c->ranges.p, 0xff, 4 * tiles_total, s));
+    SEELE_CUDA(c, cudaMemsetAsync(ptr<uint32_t>(c->ranges) + tiles_total, 0, 4 * tiles_total, s));
+    SEELE_MARK(SEELE_STAGE_PREPROCESS);
+    if (c->scene_flags == SEELE_SCENE_BORROW) {
+        const seele_scene_desc& b = c->borrowed;
+        const int ncoef = (c->sh_degree + 1) * (c->sh_degree + 1);
+        launch_repack((int)c->n, ncoef, b.means, b.log_scales, b.quats, b.opacity_logits, b.sh,
+                      ptr<float4>(c->pos_logit), ptr<float4>(c->quat), ptr<float4>(c->log_scale), ptr<float4>(c->sh),
+                      s);
+        SEELE_LAUNCHED(c);
+        ++launches;
+    }
+    SceneDev sc;
+    sc.pos_logit = ptr<float4>(c->pos_logit);
+    sc.quat = ptr<float4>(c->quat);
+    sc.log_scale = ptr<float4>(c->log_scale);
+    sc.sh = ptr<float4>(c->sh);
+    sc.mask = c->has_mask ? (c->scene_flags == SEELE_SCENE_BORROW ? c->borrowed.cluster_mask
+                                                                  : ptr<const uint32_t>(c->mask))
+                          : nullptr;
+    unsigned long long* vt = ptr<unsigned long long>(c->viewt);
+    ProjOut po{ptr<float4>(c->rec), ptr<uint2>(c->rect), ptr<uint32_t>(c->tiles), ptr<float>(c->depth), vt};
+    const CamDev* cams = ptr<const CamDev>(c->cams_dev);
+    launch_preprocess(sc, cams, f.fp, po, s);
+    SEELE_LAUNCHED(c);
+    ++launches;
+
+    // visible records -> (depth bits, id), then the stable depth sort
+    SEELE_MARK(SEELE_STAGE_COMPACT);
+    launch_compact_visible(po.tiles, po.depth, (uint32_t)R, ptr<uint32_t>(c->visk[0]), ptr<uint32_t>(c->visv[0]), lb,
+                           c->epoch++, st, 0, s);
+    SEELE_LAUNCHED(c);
+    ++launches;
+    const uint32_t* n_vis = &st->n_visible;
+    SEELE_MARK(SEELE_STAGE_DEPTH_SORT);
+    uint32_t* scnt = ptr<uint32_t>(c->sortcnt);
+    uint32_t* soff = scnt + f.cnt_words;
+    {
+        uint32_t* vk[2] = {ptr<uint32_t>(c->visk[0]), ptr<uint32_t>(c->visk[1])};
+        uint32_t* vv[2] = {ptr<uint32_t>(c->visv[0]), ptr<uint32_t>(c->visv[1])};
+        // positive fp32 depths order like their bit patterns, sign bit clear: 31 bits
+        if (radix_sort_pairs<uint32_t>(vk, vv, n_vis, (uint32_t)R, 31, false, scnt, soff, lb, c->epoch, st, 2,
+                                       launches, s) != 0)
+            return fail(c, SEELE_ERR_CUDA, "depth sort launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    // sorted ids are back in buffer 0 after an even number of passes
+    const uint32_t* order = ptr<uint32_t>(c->visv[0]);
+    SEELE_MARK(SEELE_STAGE_TILE_SCAN);
+    launch_scan_tiles(po.tiles, order, (uint32_t)R, ptr<uint32_t>(c->offs), lb, c->epoch++, st, 1,
+                      (uint32_t)std::min<uint64_t>(cap, 0xffffffffu), s);
+    SEELE_LAUNCHED(c);
+    ++launches;
+    const int emit_blocks = (int)std::max<uint64_t>(std::min<uint64_t>((R + 255) / 256, 8 * 152), 1);
+    SEELE_MARK(SEELE_STAGE_EMIT);
+    const uint32_t* n_inst = &st->n_inst_valid;
+    if (f.short_keys)
+        fin = enqueue_tile_sort<uint16_t>(c, order, po.rect, cams, st, n_inst, (uint32_t)tiles_total, f.tile_bits, cap,
+                                          emit_blocks, lb, scnt, soff, launches, s);
+    else
+        fin = enqueue_tile_sort<uint32_t>(c, order, po.rect, cams, st, n_inst, (uint32_t)tiles_total, f.tile_bits, cap,
+                                          emit_blocks, lb, scnt, soff, launches, s);
+    if (fin < 0) return fail(c, SEELE_ERR_CUDA, "tile sort launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+
+    RasterArgs ra;
+    ra.starts = ptr<uint32_t>(c->ranges);
+    ra.ends = ptr<uint32_t>(c->ranges) + tiles_total;
+    ra.inst_rec = ptr<uint32_t>(c->instv[fin]);
+    ra.rec = ptr<float4>(c->rec);
+    ra.cams = cams;
+    ra.n_cams = ncam;
+    ra.n_tiles = (uint32_t)tiles_total;
+    ra.fp = f.fp;
+    ra.cr = opt->mode == SEELE_MODE_CR;
+    ra.group_w = opt->group_w;
+    ra.group_h = opt->group_h;
+    ra.out_rgb = rgb_target;
+    ra.out_T = ptr<float>(c->T);
+    ra.out_nc = ptr<uint32_t>(c->nc);
+    ra.count_into = count ? st : nullptr;
+    ra.view_end = vt + 1;
+    ra.view_done = reinterpret_cast<uint32_t*>(vt + 1 + ncam);
+    SEELE_MARK(SEELE_STAGE_RASTER);
+    if (!launch_raster_fwd(ra, s)) return fail(c, SEELE_ERR_ARG, "no rasterizer for these options");
+    SEELE_LAUNCHED(c);
+    ++launches;
+    SEELE_MARK(SEELE_NUM_STAGES);
+#undef SEELE_MARK
+    if (T_copy) SEELE_CUDA(c, cudaMemcpyAsync(T_copy, c->T.p, 4 * f.pix_total, cudaMemcpyDeviceToDevice, s));
+    SEELE_CUDA(c, cudaMemcpyAsync(c->h_status, st, sizeof(DeviceStatus), cudaMemcpyDeviceToHost, s));
+    return SEELE_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -253,6 +533,13 @@ void seele_destroy(seele_ctx* c) {
                      &c->visv[1], &c->offs, &c->instk[0], &c->instk[1], &c->instv[0], &c->instv[1],
                      &c->ranges, &c->status, &c->hist, &c->lookback, &c->T, &c->nc, &c->rgb_tmp, &c->sortcnt, &c->grad_rec};
     for (DevBuf* b : all) release(*b);
+    release(c->viewt);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    for (auto& slot : c->cam_ring) {
+        if (slot.host) cudaFreeHost(slot.host);
+        if (slot.done) cudaEventDestroy(slot.done);
+    }
     if (c->h_status) cudaFreeHost(c->h_status);
     for (cudaEvent_t e : c->ev)
         if (e) cudaEventDestroy(e);
@@ -270,7 +557,8 @@ const char* seele_last_error(const seele_ctx* c) { return c ? c->err.c_str() : "
 seele_status seele_load_scene(seele_ctx* c, const seele_scene_desc* d) {
     if (!c) return SEELE_ERR_ARG;
     if (!d) return fail(c, SEELE_ERR_ARG, "scene descriptor is NULL");
-    if (d->n < 1 || d->n >= (int64_t)1 << 31) return fail(c, SEELE_ERR_ARG, "n = %lld out of range", (long long)d->n);
+    if (d->n < 1 || d->n > (int64_t)65535 * 256)
+        return fail(c, SEELE_ERR_ARG, "n = %lld out of range (1 .. 16776960)", (long long)d->n);
     if (d->sh_degree < 0 || d->sh_degree > 3) return fail(c, SEELE_ERR_ARG, "sh_degree must be 0..3");
     if (!d->means || !d->log_scales || !d->quats || !d->opacity_logits || !d->sh)
         return fail(c, SEELE_ERR_ARG, "scene attribute pointer is NULL");
@@ -282,6 +570,7 @@ seele_status seele_load_scene(seele_ctx* c, const seele_scene_desc* d) {
     SEELE_CUDA(c, cudaSetDevice(c->device));
     c->has_scene = false;
     c->rendered = false;
+    ++c->scene_gen;
     const int64_t n = d->n;
     const int nc = (d->sh_degree + 1) * (d->sh_degree + 1);
     const int planes = (3 * nc + 3) / 4;
@@ -378,229 +667,97 @@ seele_status seele_render(seele_ctx* c, const seele_options* opt, float* out_rgb
     if (!c->has_scene) return fail(c, SEELE_ERR_STATE, "no scene loaded");
     if (c->cams.empty()) return fail(c, SEELE_ERR_STATE, "no cameras set");
     if (!opt || !out_rgb) return fail(c, SEELE_ERR_ARG, "options and out_rgb are required");
-    if (opt->mode != SEELE_MODE_PLAIN && opt->mode != SEELE_MODE_CR) return fail(c, SEELE_ERR_ARG, "bad mode");
-    if (opt->tile_w != 16 || opt->tile_h != 16) return fail(c, SEELE_ERR_ARG, "tile size must be 16x16");
-    if (opt->mode == SEELE_MODE_CR && !group_supported(opt->group_w, opt->group_h))
-        return fail(c, SEELE_ERR_ARG, "pixel group %dx%d not supported (1x1, 2x2, 2x4)", opt->group_w, opt->group_h);
-    if (!(opt->alpha_min > 0 && opt->alpha_min < opt->alpha_max && opt->alpha_max <= 1.0f))
-        return fail(c, SEELE_ERR_ARG, "need 0 < alpha_min < alpha_max <= 1");
-    if (!(opt->t_stop > 0 && opt->t_stop < 1)) return fail(c, SEELE_ERR_ARG, "need 0 < t_stop < 1");
-    if (opt->cluster_filter && (c->n_clusters <= 0 || !c->has_mask))
-        return fail(c, SEELE_ERR_STATE, "cluster_filter needs a scene with view clusters");
-    if (opt->n_neighbors < 0) return fail(c, SEELE_ERR_ARG, "n_neighbors must be >= 0");
+    seele_status st0 = check_options(c, opt);
+    if (st0 != SEELE_OK) return st0;
     const bool async = (opt->flags & SEELE_RENDER_ASYNC) != 0;
     const bool profile = (opt->flags & SEELE_RENDER_PROFILE) != 0;
     const bool count = (opt->flags & SEELE_RENDER_COUNT) != 0;
-    if (async && (profile || count)) return fail(c, SEELE_ERR_ARG, "PROFILE and COUNT need a synchronous render");
+    const bool graph = (opt->flags & SEELE_RENDER_GRAPH) != 0;
+    if ((async || graph) && (profile || count))
+        return fail(c, SEELE_ERR_ARG, "PROFILE and COUNT need a synchronous render without GRAPH");
     SEELE_CUDA(c, cudaSetDevice(c->device));
-    const bool rgb_dev = is_device_ptr(out_rgb);
-    const bool T_dev = out_T ? is_device_ptr(out_T) : true;
-    if (async && (!rgb_dev || !T_dev)) return fail(c, SEELE_ERR_ARG, "ASYNC renders need device outputs");
-
-    const int ncam = (int)c->cams.size();
-    const uint64_t R = (uint64_t)c->n * ncam;
-    if (R >= (1ull << 31)) return fail(c, SEELE_ERR_ARG, "cameras x Gaussians must be < 2^31");
-
-    // camera constants
-    c->camdev.resize(ncam);
-    uint64_t tiles_total = 0, pix_total = 0;
-    for (int i = 0; i < ncam; ++i) {
-        const seele_camera& k = c->cams[i];
-        CamDev& d = c->camdev[i];
-        std::memset(&d, 0, sizeof d);
-        const float* w = k.world_to_cam;
-        const float Rm[9] = {w[0], w[1], w[2], w[4], w[5], w[6], w[8], w[9], w[10]};
-        const float t[3] = {w[3], w[7], w[11]};
-        std::memcpy(d.R, Rm, sizeof Rm);
-        std::memcpy(d.t, t, sizeof t);
-        d.fx = k.fx;
-        d.fy = k.fy;
-        d.cx = k.cx;
-        d.cy = k.cy;
-        for (int j = 0; j < 3; ++j)
-            d.campos[j] = (float)(-((double)Rm[j] * t[0] + (double)Rm[3 + j] * t[1] + (double)Rm[6 + j] * t[2]));
-        d.lim_x = (float)(1.3 * k.width / (2.0 * k.fx));
-        d.lim_y = (float)(1.3 * k.height / (2.0 * k.fy));
-        d.near_z = k.near_z;
-        d.W = k.width;
-        d.H = k.height;
-        d.tiles_x = (k.width + opt->tile_w - 1) / opt->tile_w;
-        d.tiles_y = (k.height + opt->tile_h - 1) / opt->tile_h;
-        d.tile_offset = (uint32_t)tiles_total;
-        d.pix_offset = (uint32_t)pix_total;
-        d.sel_bits = opt->cluster_filter ? select_clusters(c, k, opt->n_neighbors) : 0xffffffffu;
-        tiles_total += (uint64_t)d.tiles_x * d.tiles_y;
-        pix_total += (uint64_t)k.width * k.height;
-    }
-    if (tiles_total >= (1ull << 31) || pix_total >= (1ull << 31))
+    FrameInfo f;
+    f.rgb_dev = is_device_ptr(out_rgb);
+    f.T_dev = out_T ? is_device_ptr(out_T) : true;
+    if ((async || graph) && (!f.rgb_dev || !f.T_dev))
+        return fail(c, SEELE_ERR_ARG, "ASYNC and GRAPH renders need device outputs");
+    f.ncam = (int)c->cams.size();
+    f.R = (uint64_t)c->n * f.ncam;
+    if (f.R >= (1ull << 31)) return fail(c, SEELE_ERR_ARG, "cameras x Gaussians must be < 2^31");
+    build_cameras(c, opt, f.tiles_total, f.pix_total);
+    if (f.tiles_total >= (1ull << 31) || f.pix_total >= (1ull << 31))
         return fail(c, SEELE_ERR_ARG, "too many tiles or pixels in one render");
-
-    // workspace
-    if (c->capacity == 0) c->capacity = std::max<uint64_t>(1u << 20, 4 * R);
-    const uint32_t sort_tile = sort_tile_items();
-    SEELE_CUDA(c, ensure(c->cams_dev, sizeof(CamDev) * ncam));
-    SEELE_CUDA(c, ensure(c->rec, 48 * R));
-    SEELE_CUDA(c, ensure(c->rect, 8 * R));
-    SEELE_CUDA(c, ensure(c->tiles, 4 * R));
-    SEELE_CUDA(c, ensure(c->depth, 4 * R));
-    for (int i = 0; i < 2; ++i) {
-        SEELE_CUDA(c, ensure(c->visk[i], 4 * R));
-        SEELE_CUDA(c, ensure(c->visv[i], 4 * R));
-    }
-    SEELE_CUDA(c, ensure(c->offs, 4 * R));
-    SEELE_CUDA(c, ensure(c->ranges, 8 * tiles_total));   // starts[n_tiles], then ends[n_tiles]
-    SEELE_CUDA(c, ensure(c->status, sizeof(DeviceStatus)));
-    const bool short_keys = tiles_total <= kShortKeyMaxTiles;
-
-    SEELE_CUDA(c, ensure(c->T, 4 * pix_total));
-    SEELE_CUDA(c, ensure(c->nc, 4 * pix_total));
-    if (!rgb_dev) SEELE_CUDA(c, ensure(c->rgb_tmp, 12 * pix_total));
-
-    const int deg = c->sh_degree;
-    const int ncoef = (deg + 1) * (deg + 1);
-    FrameParams fp{};
-    fp.n = (int32_t)c->n;
-    fp.n_cams = ncam;
-    fp.sh_degree = deg;
-    fp.tile_w = opt->tile_w;
-    fp.tile_h = opt->tile_h;
-    fp.opacity_filter = opt->opacity_filter ? 1 : 0;
-    fp.use_mask = opt->cluster_filter ? 1 : 0;
-    fp.alpha_min = opt->alpha_min;
-    fp.alpha_max = opt->alpha_max;
-    fp.t_stop = opt->t_stop;
-    fp.dilation = 0.3f;
-    fp.frustum_slack = 1.3f;
-    fp.n_tiles_total = (uint32_t)tiles_total;
-    const int tile_bits = std::max(1, bits_for(tiles_total > 0 ? tiles_total - 1 : 0));
-
-    SEELE_CUDA(c, cudaMemcpyAsync(c->cams_dev.p, c->camdev.data(), sizeof(CamDev) * ncam, cudaMemcpyHostToDevice,
-                                  c->stream));
+    f.short_keys = f.tiles_total <= kShortKeyMaxTiles;
+    f.tile_bits = std::max(1, bits_for(f.tiles_total > 0 ? f.tiles_total - 1 : 0));
+    fill_params(c, opt, f);
     if (profile && !c->ev[0])
         for (cudaEvent_t& e : c->ev) SEELE_CUDA(c, cudaEventCreate(&e));
     c->profiling = profile;
-#define SEELE_MARK(k) \
-    if (profile) SEELE_CUDA(c, cudaEventRecord(c->ev[k], c->stream))
+    if (c->capacity == 0) c->capacity = std::max<uint64_t>(1u << 20, 4 * f.R);
 
-    int retries = 0, launches = 0;
+    int retries = 0, launches = 0, fin = 0;
     for (int attempt = 0;; ++attempt) {
-        const uint64_t cap = c->capacity;
-        for (int i = 0; i < 2; ++i) {
-            SEELE_CUDA(c, ensure(c->instk[i], 4 * cap));
-            SEELE_CUDA(c, ensure(c->instv[i], 4 * cap));
+        f.cap = c->capacity;
+        seele_status s1 = size_frame(c, f);
+        if (s1 != SEELE_OK) return s1;
+        s1 = upload_cameras(c);
+        if (s1 != SEELE_OK) return s1;
+        float* rgb_target = f.rgb_dev ? out_rgb : ptr<float>(c->rgb_tmp);
+        float* T_copy = (out_T && f.T_dev) ? out_T : nullptr;
+        if (graph) {
+            const std::vector<uint64_t> key = graph_key(c, opt, f, rgb_target, T_copy);
+            if (!c->gexec || key != c->gkey) {
+                if (c->gexec) cudaGraphExecDestroy(c->gexec);  // freed once any replay in flight ends
+                c->gexec = nullptr;
+                if (!c->cap_stream) SEELE_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+                cudaStream_t user = c->stream;
+                c->stream = c->cap_stream;
+                if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                    c->stream = user;
+                    (void)cudaGetLastError();
+                    return fail(c, SEELE_ERR_CUDA, "stream capture could not begin");
+                }
+                const seele_status se = enqueue_frame(c, opt, f, rgb_target, T_copy, false, launches, fin);
+                cudaGraph_t g = nullptr;
+                const cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
+                c->stream = user;
+                if (se != SEELE_OK) {
+                    if (g) cudaGraphDestroy(g);
+                    return se;
+                }
+                if (ee != cudaSuccess || !g) {
+                    (void)cudaGetLastError();
+                    return fail(c, SEELE_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ee));
+                }
+                const cudaError_t ei = cudaGraphInstantiate(&c->gexec, g, 0);
+                cudaGraphDestroy(g);
+                if (ei != cudaSuccess) {
+                    (void)cudaGetLastError();
+                    c->gexec = nullptr;
+                    return fail(c, SEELE_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ei));
+                }
+                c->gkey = key;
+                c->g_launches = launches;
+                c->g_fin = fin;
+            }
+            SEELE_CUDA(c, cudaGraphLaunch(c->gexec, c->stream));
+            launches = c->g_launches;
+            fin = c->g_fin;
+        } else {
+            const seele_status se = enqueue_frame(c, opt, f, rgb_target, T_copy, count, launches, fin);
+            if (se != SEELE_OK) return se;
         }
-        const uint32_t cnt_words = radix_count_words((uint32_t)std::max<uint64_t>(R, cap));
-        SEELE_CUDA(c, ensure(c->sortcnt, 8ull * cnt_words));
-        const size_t lb_entries = ((std::max<uint64_t>(R, cap) + sort_tile - 1) / sort_tile) * 256;
-        if (c->lookback_entries < lb_entries) {
-            SEELE_CUDA(c, ensure(c->lookback, 8 * lb_entries));
-            SEELE_CUDA(c, cudaMemsetAsync(c->lookback.p, 0, 8 * lb_entries, c->stream));
-            c->lookback_entries = lb_entries;
-        }
-        cudaStream_t s = c->stream;
-        DeviceStatus* st = ptr<DeviceStatus>(c->status);
-        uint64_t* lb = ptr<uint64_t>(c->lookback);
-        launches = 0;
-
-        SEELE_CUDA(c, cudaMemsetAsync(st, 0, sizeof(DeviceStatus), s));
-        SEELE_CUDA(c, cudaMemsetAsync(c->ranges.p, 0xff, 4 * tiles_total, s));
-        SEELE_CUDA(c, cudaMemsetAsync(ptr<uint32_t>(c->ranges) + tiles_total, 0, 4 * tiles_total, s));
-        SEELE_MARK(SEELE_STAGE_PREPROCESS);
-        if (c->scene_flags == SEELE_SCENE_BORROW) {
-            const seele_scene_desc& b = c->borrowed;
-            launch_repack((int)c->n, ncoef, b.means, b.log_scales, b.quats, b.opacity_logits, b.sh,
-                          ptr<float4>(c->pos_logit), ptr<float4>(c->quat), ptr<float4>(c->log_scale),
-                          ptr<float4>(c->sh), s);
-            SEELE_LAUNCHED(c);
-            ++launches;
-        }
-
-        SceneDev sc;
-        sc.pos_logit = ptr<float4>(c->pos_logit);
-        sc.quat = ptr<float4>(c->quat);
-        sc.log_scale = ptr<float4>(c->log_scale);
-        sc.sh = ptr<float4>(c->sh);
-        sc.mask = c->has_mask ? (c->scene_flags == SEELE_SCENE_BORROW ? c->borrowed.cluster_mask
-                                                                      : ptr<const uint32_t>(c->mask))
-                              : nullptr;
-        ProjOut po{ptr<float4>(c->rec), ptr<uint2>(c->rect), ptr<uint32_t>(c->tiles), ptr<float>(c->depth)};
-        const CamDev* cams = ptr<const CamDev>(c->cams_dev);
-        launch_preprocess(sc, cams, fp, po, s);
-        SEELE_LAUNCHED(c);
-        ++launches;
-
-        // visible records -> (depth bits, id), then stable depth sort (4 passes)
-        SEELE_MARK(SEELE_STAGE_COMPACT);
-        launch_compact_visible(po.tiles, po.depth, (uint32_t)R, ptr<uint32_t>(c->visk[0]), ptr<uint32_t>(c->visv[0]),
-                               lb, c->epoch++, st, 0, s);
-        SEELE_LAUNCHED(c);
-        const uint32_t* n_vis = &st->n_visible;
-        SEELE_MARK(SEELE_STAGE_DEPTH_SORT);
-        uint32_t* scnt = ptr<uint32_t>(c->sortcnt);
-        uint32_t* soff = scnt + cnt_words;
-        {
-            uint32_t* vk[2] = {ptr<uint32_t>(c->visk[0]), ptr<uint32_t>(c->visk[1])};
-            uint32_t* vv[2] = {ptr<uint32_t>(c->visv[0]), ptr<uint32_t>(c->visv[1])};
-            // positive fp32 depths order like their bit patterns, sign bit clear: 31 bits
-            if (radix_sort_pairs<uint32_t>(vk, vv, n_vis, (uint32_t)R, 31, false, scnt, soff, lb, c->epoch, st, 2,
-                                           launches, s) != 0)
-                return fail(c, SEELE_ERR_CUDA, "depth sort launch failed: %s", cudaGetErrorString(cudaGetLastError()));
-        }
-        ++launches;
-        // sorted ids are back in buffer 0 after an even number of passes
-        const uint32_t* order = ptr<uint32_t>(c->visv[0]);
-        SEELE_MARK(SEELE_STAGE_TILE_SCAN);
-        launch_scan_tiles(po.tiles, order, (uint32_t)R, ptr<uint32_t>(c->offs), lb, c->epoch++, st, 1,
-                          (uint32_t)std::min<uint64_t>(cap, 0xffffffffu), s);
-        SEELE_LAUNCHED(c);
-        ++launches;
-        const int emit_blocks = (int)std::max<uint64_t>(std::min<uint64_t>((R + 255) / 256, 8 * 152), 1);
-        SEELE_MARK(SEELE_STAGE_EMIT);
-        const uint32_t* n_inst = &st->n_inst_valid;
-        int fin;
-        if (short_keys)
-            fin = enqueue_tile_sort<uint16_t>(c, order, po.rect, cams, st, n_inst, (uint32_t)tiles_total, tile_bits,
-                                              cap, emit_blocks, lb, scnt, soff, launches, s);
-        else
-            fin = enqueue_tile_sort<uint32_t>(c, order, po.rect, cams, st, n_inst, (uint32_t)tiles_total, tile_bits,
-                                              cap, emit_blocks, lb, scnt, soff, launches, s);
-        if (fin < 0) return fail(c, SEELE_ERR_CUDA, "tile sort launch failed: %s", cudaGetErrorString(cudaGetLastError()));
-
-        RasterArgs ra;
-        ra.starts = ptr<uint32_t>(c->ranges);
-        ra.ends = ptr<uint32_t>(c->ranges) + tiles_total;
-        ra.inst_rec = ptr<uint32_t>(c->instv[fin]);
-        ra.rec = ptr<float4>(c->rec);
-        ra.cams = cams;
-        ra.n_cams = ncam;
-        ra.n_tiles = (uint32_t)tiles_total;
-        ra.fp = fp;
-        ra.cr = opt->mode == SEELE_MODE_CR;
-        ra.group_w = opt->group_w;
-        ra.group_h = opt->group_h;
-        ra.out_rgb = rgb_dev ? out_rgb : ptr<float>(c->rgb_tmp);
-        ra.out_T = ptr<float>(c->T);
-        ra.out_nc = ptr<uint32_t>(c->nc);
-        ra.count_into = count ? st : nullptr;
-        SEELE_MARK(SEELE_STAGE_RASTER);
-        if (!launch_raster_fwd(ra, s)) return fail(c, SEELE_ERR_ARG, "no rasterizer for these options");
-        SEELE_LAUNCHED(c);
-        ++launches;
-        SEELE_MARK(SEELE_NUM_STAGES);
-
-        SEELE_CUDA(c, cudaMemcpyAsync(c->h_status, st, sizeof(DeviceStatus), cudaMemcpyDeviceToHost, s));
         c->inst_final = fin;
-
-        c->n_tiles_total = (uint32_t)tiles_total;
-        c->n_pix_total = pix_total;
+        c->n_tiles_total = (uint32_t)f.tiles_total;
+        c->n_pix_total = f.pix_total;
         c->last_opt = *opt;
-        c->last_fp = fp;
+        c->last_fp = f.fp;
         if (async) {
             c->status_pending = true;
             c->rendered = true;
             break;
         }
-        SEELE_CUDA(c, cudaStreamSynchronize(s));
+        SEELE_CUDA(c, cudaStreamSynchronize(c->stream));
         const DeviceStatus& h = *c->h_status;
         if (h.error == kErrCapacity && attempt == 0) {
             c->capacity = (uint64_t)h.n_instances + h.n_instances / 4 + 1024;
@@ -613,9 +770,11 @@ seele_status seele_render(seele_ctx* c, const seele_options* opt, float* out_rgb
         break;
     }
 
-    if (!rgb_dev) SEELE_CUDA(c, cudaMemcpyAsync(out_rgb, c->rgb_tmp.p, 12 * pix_total, cudaMemcpyDeviceToHost, c->stream));
-    if (out_T) SEELE_CUDA(c, cudaMemcpyAsync(out_T, c->T.p, 4 * pix_total, cudaMemcpyDefault, c->stream));
-    if (!rgb_dev || (out_T && !T_dev)) SEELE_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (!f.rgb_dev)
+        SEELE_CUDA(c, cudaMemcpyAsync(out_rgb, c->rgb_tmp.p, 12 * f.pix_total, cudaMemcpyDeviceToHost, c->stream));
+    if (out_T && !f.T_dev)
+        SEELE_CUDA(c, cudaMemcpyAsync(out_T, c->T.p, 4 * f.pix_total, cudaMemcpyDeviceToHost, c->stream));
+    if (!f.rgb_dev || !f.T_dev) SEELE_CUDA(c, cudaStreamSynchronize(c->stream));
     if (stats) {
         std::memset(stats->stage_ms, 0, sizeof stats->stage_ms);
         if (profile)
@@ -630,6 +789,78 @@ seele_status seele_render(seele_ctx* c, const seele_options* opt, float* out_rgb
         stats->retries = retries;
         stats->n_kernels = launches;
     }
+    return SEELE_OK;
+}
+
+seele_status seele_get_view_times(const seele_ctx* c, float* out_ms, int32_t n) {
+    if (!c || !out_ms) return SEELE_ERR_ARG;
+    seele_ctx* m = const_cast<seele_ctx*>(c);
+    if (!c->rendered) return fail(m, SEELE_ERR_STATE, "no completed render");
+    const int ncam = (int)c->cams.size();
+    if (n != ncam) return fail(m, SEELE_ERR_ARG, "n must equal the number of cameras (%d)", ncam);
+    SEELE_CUDA(m, cudaSetDevice(c->device));
+    SEELE_CUDA(m, cudaStreamSynchronize(c->stream));
+    std::vector<unsigned long long> t(1 + ncam);
+    SEELE_CUDA(m, cudaMemcpy(t.data(), c->viewt.p, 8ull * (1 + ncam), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < ncam; ++i) out_ms[i] = t[1 + i] >= t[0] ? (float)((t[1 + i] - t[0]) * 1e-6) : 0.f;
+    return SEELE_OK;
+}
+
+seele_status seele_autotune(seele_ctx* c, seele_options* inout, float* best_ms) {
+    if (!c || !inout) return SEELE_ERR_ARG;
+    if (!c->has_scene || c->cams.empty()) return fail(c, SEELE_ERR_STATE, "autotune needs a scene and cameras");
+    static const int shapes[][2] = {{16, 16}, {32, 8}, {32, 16}};
+    std::vector<float> out;
+    size_t pix = 0;
+    for (const auto& k : c->cams) pix += (size_t)k.width * k.height;
+    float* dev_out = nullptr;
+    if (cudaMalloc(&dev_out, 12 * pix) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(c, SEELE_ERR_OOM, "autotune output buffer");
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = INFINITY;
+    int bw = inout->tile_w, bh = inout->tile_h;
+    seele_status result = SEELE_OK;
+    for (const auto& sh : shapes) {
+        seele_options o = *inout;
+        o.tile_w = sh[0];
+        o.tile_h = sh[1];
+        o.flags = 0;
+        seele_status st = SEELE_OK;
+        for (int w = 0; w < 2 && st == SEELE_OK; ++w) st = seele_render(c, &o, dev_out, nullptr, nullptr);
+        if (st != SEELE_OK) {
+            result = st;
+            break;
+        }
+        o.flags = SEELE_RENDER_ASYNC;
+        cudaEventRecord(e0, c->stream);
+        for (int r = 0; r < 5 && st == SEELE_OK; ++r) st = seele_render(c, &o, dev_out, nullptr, nullptr);
+        cudaEventRecord(e1, c->stream);
+        if (st == SEELE_OK) st = seele_synchronize(c);
+        if (st != SEELE_OK) {
+            result = st;
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= 5.f;
+        if (ms < best) {
+            best = ms;
+            bw = sh[0];
+            bh = sh[1];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(dev_out);
+    if (result != SEELE_OK) return result;
+    inout->tile_w = bw;
+    inout->tile_h = bh;
+    if (best_ms) *best_ms = best;
+    c->rendered = false;
     return SEELE_OK;
 }
 

@@ -410,15 +410,22 @@ static void launch_bwd_one(const RasterBwdArgs& a, cudaStream_t s) {
         a.grad_rec);
 }
 
-bool launch_raster_bwd(const RasterBwdArgs& a, cudaStream_t s) {
-    if (a.n_tiles == 0) return true;
-    if (a.fp.tile_w != 16 || a.fp.tile_h != 16) return false;
-    if (!a.cr) launch_bwd_one<16, 16, 2, 2, 1, 1, false>(a, s);
-    else if (a.group_w == 2 && a.group_h == 2) launch_bwd_one<16, 16, 2, 2, 2, 2, true>(a, s);
-    else if (a.group_w == 1 && a.group_h == 1) launch_bwd_one<16, 16, 2, 2, 1, 1, true>(a, s);
-    else if (a.group_w == 2 && a.group_h == 4) launch_bwd_one<16, 16, 2, 4, 2, 4, true>(a, s);
+template <int TW, int TH>
+static bool launch_bwd_shape(const RasterBwdArgs& a, cudaStream_t s) {
+    if (!a.cr) launch_bwd_one<TW, TH, 2, 2, 1, 1, false>(a, s);
+    else if (a.group_w == 2 && a.group_h == 2) launch_bwd_one<TW, TH, 2, 2, 2, 2, true>(a, s);
+    else if (a.group_w == 1 && a.group_h == 1) launch_bwd_one<TW, TH, 2, 2, 1, 1, true>(a, s);
+    else if (a.group_w == 2 && a.group_h == 4) launch_bwd_one<TW, TH, 2, 4, 2, 4, true>(a, s);
     else return false;
     return true;
+}
+
+bool launch_raster_bwd(const RasterBwdArgs& a, cudaStream_t s) {
+    if (a.n_tiles == 0) return true;
+    if (a.fp.tile_w == 16 && a.fp.tile_h == 16) return launch_bwd_shape<16, 16>(a, s);
+    if (a.fp.tile_w == 32 && a.fp.tile_h == 8) return launch_bwd_shape<32, 8>(a, s);
+    if (a.fp.tile_w == 32 && a.fp.tile_h == 16) return launch_bwd_shape<32, 16>(a, s);
+    return false;
 }
 
 void launch_preprocess_bwd(const SceneDev& sc, const CamDev* cams, const FrameParams& fp, const uint32_t* tiles,

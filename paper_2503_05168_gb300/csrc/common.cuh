@@ -78,7 +78,14 @@ struct ProjOut {
     uint2* rect;               // [R] tile box x0 | y0 << 16, x1 | y1 << 16
     uint32_t* tiles;           // [R] tiles touched (0 = culled)
     float* depth;              // [R] camera-space Z
+    unsigned long long* t_frame;  // receives the frame's start time (%globaltimer, ns)
 };
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 // Bounded spin for the decoupled look-back: about a second at most, then the
 // waiting block records a timeout and gives up instead of hanging the GPU.

@@ -64,6 +64,8 @@ struct RasterArgs {
     float* out_T;
     uint32_t* out_nc;
     DeviceStatus* count_into;   // non-null: run the counting variant
+    unsigned long long* view_end;  // [n_cams] time the camera's last tile finished (%globaltimer)
+    uint32_t* view_done;        // [n_cams] finished tiles, cleared per frame
 };
 bool launch_raster_fwd(const RasterArgs& a, cudaStream_t s);
 

@@ -87,8 +87,11 @@ __device__ __forceinline__ float det2_sym(float a, float b, float c) {
 template <int DEG>
 __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev sc, const CamDev* __restrict__ cams,
                                                          FrameParams fp, ProjOut out) {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    const int ci = blockIdx.y;
+    // cameras vary fastest over the grid, so the blocks that read one slice
+    // of the scene run together and share it through L2
+    const int g = blockIdx.y * blockDim.x + threadIdx.x;
+    const int ci = blockIdx.x;
+    if (g == 0 && ci == 0 && out.t_frame) *out.t_frame = global_ns();
     if (g >= fp.n) return;
     const size_t rid = (size_t)ci * fp.n + g;
     const CamDev& C = cams[ci];
@@ -221,7 +224,7 @@ __global__ void repack_kernel(int n, int nc, const float* __restrict__ means, co
 
 void launch_preprocess(const SceneDev& sc, const CamDev* cams, const FrameParams& fp, const ProjOut& out,
                        cudaStream_t s) {
-    dim3 grid((fp.n + 255) / 256, fp.n_cams);
+    dim3 grid(fp.n_cams, (fp.n + 255) / 256);
     switch (fp.sh_degree) {
         case 0: preprocess_kernel<0><<<grid, 256, 0, s>>>(sc, cams, fp, out); break;
         case 1: preprocess_kernel<1><<<grid, 256, 0, s>>>(sc, cams, fp, out); break;

@@ -29,7 +29,8 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
                       const uint32_t* __restrict__ inst_rec,
                       const float4* __restrict__ rec, const CamDev* __restrict__ cams, int n_cams, FrameParams fp,
                       float* __restrict__ out_rgb, float* __restrict__ out_T, uint32_t* __restrict__ out_nc,
-                      DeviceStatus* __restrict__ counters) {
+                      DeviceStatus* __restrict__ counters, unsigned long long* __restrict__ view_end,
+                      uint32_t* __restrict__ view_done) {
     constexpr int NT = (TW / PW) * (TH / PH);
     constexpr int NP = PW * PH;
     constexpr int TXN = TW / PW;
@@ -80,20 +81,21 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
             // tests every staged Gaussian -- independent of the blending state,
             // so the tests run back to back.  Phase 2: only the Gaussians the
             // leader kept are blended, in list order, by the group's pixels.
-            static_assert(NT <= 64, "pass mask holds 64 entries");
             if (live == 0u) continue;
+            for (int c0 = 0; c0 < cnt && live != 0u; c0 += 64) {
+            const int c1 = min(cnt, c0 + 64);
             uint64_t pass = 0;
 #pragma unroll 8
-            for (int k = 0; k < cnt; ++k) {
+            for (int k = c0; k < c1; ++k) {
                 const float4 A = s0[k];
                 const float4 B = s1[k];
                 const float dx = fx0 - A.x, dy = fy0 - A.y;
                 const float e0 = fmaf(fmaf(A.z, dx, A.w * dy), dx, fmaf(B.x * dy, dy, B.y));
                 if (COUNT) ++n_lead;
-                pass |= (uint64_t)(e0 >= B.z) << k;
+                pass |= (uint64_t)(e0 >= B.z) << (k - c0);
             }
             while (pass != 0ull && live != 0u) {
-                const int k = __ffsll((long long)pass) - 1;
+                const int k = c0 + __ffsll((long long)pass) - 1;
                 pass &= pass - 1ull;
                 const float4 A = s0[k];
                 const float4 B = s1[k];
@@ -127,6 +129,7 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
                         if (COUNT) ++n_blend;
                     }
                 }
+            }
             }
             continue;
         }
@@ -211,6 +214,12 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
             out_nc[C.pix_offset + o] = nc[p];
         }
     }
+    // the CTA that finishes a camera's last tile stamps the view's end time
+    if (view_done) {
+        __syncthreads();
+        if (t == 0 && atomicAdd(view_done + lo, 1u) + 1u == (uint32_t)(C.tiles_x * C.tiles_y))
+            view_end[lo] = global_ns();
+    }
 }
 
 template <int TW, int TH, int PW, int PH, int GW, int GH, bool CR>
@@ -218,24 +227,30 @@ static void launch_one(const RasterArgs& a, cudaStream_t s) {
     constexpr int NT = (TW / PW) * (TH / PH);
     if (a.count_into)
         raster_fwd_kernel<TW, TH, PW, PH, GW, GH, CR, true><<<a.n_tiles, NT, 0, s>>>(
-            a.starts, a.ends, a.inst_rec, a.rec, a.cams, a.n_cams, a.fp, a.out_rgb, a.out_T, a.out_nc, a.count_into);
+            a.starts, a.ends, a.inst_rec, a.rec, a.cams, a.n_cams, a.fp, a.out_rgb, a.out_T, a.out_nc, a.count_into,
+            a.view_end, a.view_done);
     else
         raster_fwd_kernel<TW, TH, PW, PH, GW, GH, CR, false><<<a.n_tiles, NT, 0, s>>>(
-            a.starts, a.ends, a.inst_rec, a.rec, a.cams, a.n_cams, a.fp, a.out_rgb, a.out_T, a.out_nc, nullptr);
+            a.starts, a.ends, a.inst_rec, a.rec, a.cams, a.n_cams, a.fp, a.out_rgb, a.out_T, a.out_nc, nullptr,
+            a.view_end, a.view_done);
+}
+
+template <int TW, int TH>
+static bool launch_shape(const RasterArgs& a, cudaStream_t s) {
+    if (!a.cr) launch_one<TW, TH, 2, 2, 1, 1, false>(a, s);
+    else if (a.group_w == 2 && a.group_h == 2) launch_one<TW, TH, 2, 2, 2, 2, true>(a, s);
+    else if (a.group_w == 1 && a.group_h == 1) launch_one<TW, TH, 2, 2, 1, 1, true>(a, s);
+    else if (a.group_w == 2 && a.group_h == 4) launch_one<TW, TH, 2, 4, 2, 4, true>(a, s);
+    else return false;
+    return true;
 }
 
 bool launch_raster_fwd(const RasterArgs& a, cudaStream_t s) {
     if (a.n_tiles == 0) return true;
-    if (a.fp.tile_w != 16 || a.fp.tile_h != 16) return false;
-    if (!a.cr) {
-        launch_one<16, 16, 2, 2, 1, 1, false>(a, s);
-        return true;
-    }
-    if (a.group_w == 2 && a.group_h == 2) launch_one<16, 16, 2, 2, 2, 2, true>(a, s);
-    else if (a.group_w == 1 && a.group_h == 1) launch_one<16, 16, 2, 2, 1, 1, true>(a, s);
-    else if (a.group_w == 2 && a.group_h == 4) launch_one<16, 16, 2, 4, 2, 4, true>(a, s);
-    else return false;
-    return true;
+    if (a.fp.tile_w == 16 && a.fp.tile_h == 16) return launch_shape<16, 16>(a, s);
+    if (a.fp.tile_w == 32 && a.fp.tile_h == 8) return launch_shape<32, 8>(a, s);
+    if (a.fp.tile_w == 32 && a.fp.tile_h == 16) return launch_shape<32, 16>(a, s);
+    return false;
 }
 
 }  // namespace seele

@@ -1,0 +1,113 @@
+"""Batched multi-view rendering: CUDA-graph capture and replay, tile shapes,
+the autotuner and per-view completion times (through the C ABI)."""
+import numpy as np
+import pytest
+
+import oracle
+import scenegen
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Renderer():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2503_05168_gb300 import Renderer as R
+    return R
+
+
+def _cams(seed, sizes):
+    rs = np.random.default_rng(seed)
+    out = []
+    for w, h in sizes:
+        az, el, rad = rs.uniform(0, 2 * np.pi), rs.uniform(-0.4, 0.4), rs.uniform(2.8, 3.6)
+        eye = (rad * np.cos(az) * np.cos(el), -rad * np.sin(el), rad * np.sin(az) * np.cos(el))
+        out.append(scenegen.look_at(eye, (0, 0, 0), w, h))
+    return out
+
+
+SIZES = [(64, 48), (100, 70), (96, 96), (33, 17), (160, 90)]
+
+
+def test_graph_replay_equals_plain_launches_and_follows_new_poses(Renderer):
+    import torch
+    sc, _ = scenegen.uniform_10k()
+    r = Renderer()
+    r.load_scene(sc)
+    out = torch.empty(sum(3 * w * h for w, h in SIZES), device="cuda")
+    for seed in (1, 2, 3):
+        cams = _cams(seed, SIZES)  # same resolutions, new poses: the graph is replayed
+        r.set_cameras(cams)
+        ref = r.render(mode="cr", opacity_filter=True).clone()
+        r.render(out=out, mode="cr", opacity_filter=True, graph=True)
+        torch.cuda.synchronize()
+        torch.testing.assert_close(out, ref, rtol=0, atol=0)
+    # a new resolution forces a new capture
+    cams = _cams(4, SIZES[:-1] + [(128, 72)])
+    r.set_cameras(cams)
+    ref = r.render(mode="plain").clone()
+    out2 = torch.empty_like(ref)
+    r.render(out=out2, mode="plain", graph=True)
+    torch.cuda.synchronize()
+    torch.testing.assert_close(out2, ref, rtol=0, atol=0)
+    r.close()
+
+
+def test_graph_replays_asynchronously(Renderer):
+    import torch
+    sc, _ = scenegen.uniform_10k(n=5000)
+    r = Renderer()
+    r.load_scene(sc)
+    frames = [_cams(10 + i, SIZES) for i in range(4)]
+    refs = []
+    for cams in frames:
+        r.set_cameras(cams)
+        refs.append(r.render(mode="cr").clone())
+    outs = [torch.empty_like(refs[0]) for _ in frames]
+    # one output buffer per frame means one capture per buffer; replay twice
+    for _ in range(2):
+        for cams, o in zip(frames, outs):
+            r.set_cameras(cams)
+            r.render(out=o, mode="cr", graph=True, sync=False)
+    r.synchronize()
+    for o, ref in zip(outs, refs):
+        torch.testing.assert_close(o, ref, rtol=0, atol=0)
+    r.close()
+
+
+@pytest.mark.parametrize("tile", [(32, 8), (32, 16)])
+def test_tile_shapes_render_the_same_image(Renderer, tile):
+    sc, cams = scenegen.uniform_10k()
+    cams = cams + _cams(5, [(100, 70)])
+    r = Renderer()
+    r.load_scene(sc)
+    r.set_cameras(cams)
+    for mode in ("plain", "cr"):
+        a, _ = parity.gpu_render(r, mode=mode)
+        b, _ = parity.gpu_render(r, mode=mode, tile=tile)
+        for x, y in zip(a, b):
+            d = np.abs(x - y)
+            assert d.max() <= parity.RGB_MAX_ABS and (d == 0).mean() > 0.999
+    # and against the oracle with that tile shape
+    ref = oracle.render(oracle.Scene64.from_scene(sc), cams[0],
+                        oracle.Options(cr=True, tile_w=tile[0], tile_h=tile[1]), nthreads=8)[0]
+    imgs, _ = parity.gpu_render(r, mode="cr", tile=tile)
+    ok, rep = parity.compare_images(imgs[0], ref.rgb, ref.margin)
+    assert ok, rep
+    r.close()
+
+
+def test_view_times_and_autotune(Renderer):
+    sc, _ = scenegen.uniform_10k()
+    cams = _cams(6, SIZES * 4)
+    r = Renderer()
+    r.load_scene(sc)
+    r.set_cameras(cams)
+    opts, ms = r.autotune(mode="cr", opacity_filter=True)
+    assert (opts.tile_w, opts.tile_h) in {(16, 16), (32, 8), (32, 16)} and ms > 0
+    r.render(options=opts)
+    t = r.view_times()
+    assert len(t) == len(cams) and all(v > 0 for v in t) and max(t) < 1000
+    r.close()
