@@ -278,51 +278,6 @@ def _fwd_bwd(args, device):
     return out
 
 
-def _multiview(args, device):
-    """64 cameras of mixed resolution rendered in one graph launch per batch."""
-    import torch
-
-    import scenegen
-    from paper_2503_05168_gb300 import Renderer
-
-    scene, cams = scenegen.multiview_2m(n=args.multiview_n)
-    r = Renderer(device)
-    r.load_scene(scene)
-    r.set_cameras(cams)
-    opts, tune_ms = r.autotune(mode="cr", opacity_filter=True)
-    r.render(options=opts)                       # sizes the instance buffers
-    out = torch.empty(3 * r.n_pixels, device=r.device)
-    gopts = r.make_options(mode="cr", opacity_filter=True, tile=(opts.tile_w, opts.tile_h), graph=True, sync=False)
-    for _ in range(3):
-        r.render(out=out, options=gopts)
-    r.synchronize()
-    k = max(3, min(args.steps, 10))
-    s = torch.cuda.Event(enable_timing=True)
-    e = torch.cuda.Event(enable_timing=True)
-    s.record()
-    for _ in range(k):
-        r.render(out=out, options=gopts)
-    e.record()
-    r.synchronize()
-    ms = s.elapsed_time(e) / k
-    per_view = []
-    for _ in range(3):
-        r.render(out=out, options=r.make_options(mode="cr", opacity_filter=True, tile=(opts.tile_w, opts.tile_h),
-                                                 graph=True))
-        per_view += r.view_times()
-    n_views = len(cams)
-    res = {"views_per_s": n_views * 1000.0 / ms, "ms_per_batch": ms, "views": n_views,
-           "tile": [opts.tile_w, opts.tile_h], "autotune_ms": tune_ms,
-           "view_ms_p50": float(np.percentile(per_view, 50)), "view_ms_p99": float(np.percentile(per_view, 99)),
-           "instances": r.last_stats["n_instances"] if r.last_stats else None,
-           "workload": (f"multiview_2m: {args.multiview_n} Gaussians (unbounded-style), {n_views} cameras with "
-                        f"resolutions from {{640x360, 1280x720, 1920x1080}} at radius 3-6, one CUDA-graph launch "
-                        f"per batch, CR + opacity filter; per-view ms = start of preprocessing to the view's last "
-                        f"tile")}
-    r.close()
-    return res
-
-
 def run_gpu(args):
     import torch
 
@@ -430,260 +385,6 @@ def run_gpu(args):
         achieved = b / (stage[dom] / 1000.0) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": None, "kernel": dom, "note": f"peak of {peak_src} (MEASURED_PEAKS hbm_gbs)"}
-
-    # forward + backward for an L1 loss (the fine-tuning step of Sec. 3.5):
-    # 1M Gaussians shaped as the clustered scene, 1280x720, target rendered
-    # from attributes perturbed by N(0, 0.01)
-    fwd_bwd = _fwd_bwd(args, local)
-    multiview = _multiview(args, local) if args.multiview_n > 0 else None
-
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "path": "CR 2x2 + opacity-aware filter",
-                                            "step": "one horizontal quarter band of a frame"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle",
-                             "sample": f"each step renders one 1920x270 band of a frame; {args.steps} bands"},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
-
-
-# -------------------------------------------------------------------- GPU --
-
-def _timed_frames(r, cams, opts, steps, stream, cam_offset):
-    import torch
-    out = torch.empty(3 * cams[0]["width"] * cams[0]["height"], device=r.device)
-    start = torch.cuda.Event(enable_timing=True)
-    end = torch.cuda.Event(enable_timing=True)
-    start.record(stream)
-    for i in range(steps):
-        r.set_cameras([cams[(cam_offset + i) % len(cams)]])
-        r.render(out=out, options=opts)
-    end.record(stream)
-    return start, end
-
-
-def _source_hash(*names):
-    h = hashlib.sha256()
-    for n in names:
-        h.update(open(os.path.join(ROOT, "paper_2503_05168_gb300", "csrc", n), "rb").read())
-    return h.hexdigest()[:16]
-
-
-def _traffic(kernel: str, src_hash: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current source of that kernel."""
-    try:
-        t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        e = t.get(kernel)
-        if e and e.get("source_hash") == src_hash:
-            return e["dram_bytes_per_launch"]
-    except Exception:
-        pass
-    return None
-
-
-def _fwd_bwd(args, device):
-    """ms of one forward + backward for an L1 loss, per raster mode."""
-    import torch
-
-    import scenegen
-    from paper_2503_05168_gb300 import Renderer
-
-    scene, cams, target = scenegen.clusters_1m(n=args.fwd_bwd_n)
-    r = Renderer(device)
-    r.load_scene(target)
-    r.set_cameras(cams)
-    tgt = r.render(mode="plain").clone()
-    params = {k: torch.from_numpy(np.ascontiguousarray(scene[k])).cuda(device)
-              for k in ("means", "log_scales", "quats", "opacity_logits", "sh")}
-    out = {}
-    for mode in ("cr", "plain"):
-        opts = r.make_options(mode=mode, opacity_filter=(mode == "cr"))
-
-        def step():
-            r.load_scene(dict(params, sh_degree=3), borrow=True)
-            img = r.render(options=opts)
-            g = torch.sign(img - tgt) / img.numel()      # d(mean |img - target|)
-            return r.render_backward(g)
-
-        for _ in range(3):
-            step()
-        torch.cuda.synchronize()
-        s = torch.cuda.Event(enable_timing=True)
-        e = torch.cuda.Event(enable_timing=True)
-        k = max(3, min(args.steps, 20))
-        s.record()
-        for _ in range(k):
-            step()
-        e.record()
-        torch.cuda.synchronize()
-        out[f"{mode}_ms"] = s.elapsed_time(e) / k
-    out["workload"] = (f"clusters_1m: {args.fwd_bwd_n} Gaussians in 64 clusters, 1280x720, L1 loss vs a target "
-                       f"rendered from attributes + N(0, 0.01); gradients for all attributes; CR path with the "
-                       f"opacity filter, plain path without")
-    r.close()
-    return out
-
-
-def _multiview(args, device):
-    """64 cameras of mixed resolution rendered in one graph launch per batch."""
-    import torch
-
-    import scenegen
-    from paper_2503_05168_gb300 import Renderer
-
-    scene, cams = scenegen.multiview_2m(n=args.multiview_n)
-    r = Renderer(device)
-    r.load_scene(scene)
-    r.set_cameras(cams)
-    opts, tune_ms = r.autotune(mode="cr", opacity_filter=True)
-    r.render(options=opts)                       # sizes the instance buffers
-    out = torch.empty(3 * r.n_pixels, device=r.device)
-    gopts = r.make_options(mode="cr", opacity_filter=True, tile=(opts.tile_w, opts.tile_h), graph=True, sync=False)
-    for _ in range(3):
-        r.render(out=out, options=gopts)
-    r.synchronize()
-    k = max(3, min(args.steps, 10))
-    s = torch.cuda.Event(enable_timing=True)
-    e = torch.cuda.Event(enable_timing=True)
-    s.record()
-    for _ in range(k):
-        r.render(out=out, options=gopts)
-    e.record()
-    r.synchronize()
-    ms = s.elapsed_time(e) / k
-    per_view = []
-    for _ in range(3):
-        r.render(out=out, options=r.make_options(mode="cr", opacity_filter=True, tile=(opts.tile_w, opts.tile_h),
-                                                 graph=True))
-        per_view += r.view_times()
-    n_views = len(cams)
-    res = {"views_per_s": n_views * 1000.0 / ms, "ms_per_batch": ms, "views": n_views,
-           "tile": [opts.tile_w, opts.tile_h], "autotune_ms": tune_ms,
-           "view_ms_p50": float(np.percentile(per_view, 50)), "view_ms_p99": float(np.percentile(per_view, 99)),
-           "instances": r.last_stats["n_instances"] if r.last_stats else None,
-           "workload": (f"multiview_2m: {args.multiview_n} Gaussians (unbounded-style), {n_views} cameras with "
-                        f"resolutions from {{640x360, 1280x720, 1920x1080}} at radius 3-6, one CUDA-graph launch "
-                        f"per batch, CR + opacity filter; per-view ms = start of preprocessing to the view's last "
-                        f"tile")}
-    r.close()
-    return res
-
-
-def run_gpu(args):
-    import torch
-
-    import __graft_entry__
-    import scenegen
-    from paper_2503_05168_gb300 import Renderer
-
-    rank, local, ws, dist = _dist()
-    if rank == 0:
-        __graft_entry__.build()
-    _barrier(dist)
-    torch.cuda.set_device(local)
-    scene, cams = scenegen.unbounded_3m(n=args.n_gauss)
-    r = Renderer(local)
-    r.load_scene(scene)
-    stream = torch.cuda.current_stream()
-    cr_opts = r.make_options(mode="cr", opacity_filter=True, sync=False)
-    plain_opts = r.make_options(mode="plain", sync=False)
-
-    # warm-up: synchronous renders grow the instance capacity, then async ones
-    for opts in (cr_opts, plain_opts):
-        for i in range(max(args.warmup, 3)):
-            r.set_cameras([cams[(rank + i * ws) % len(cams)]])
-            r.render(mode="cr" if opts.mode else "plain", opacity_filter=bool(opts.opacity_filter))
-            r.render(options=opts)
-        r.synchronize()
-
-    def timed(opts):
-        _barrier(dist)
-        torch.cuda.synchronize()
-        s, e = _timed_frames(r, cams, opts, args.steps, stream, rank)
-        torch.cuda.synchronize()
-        r.synchronize()
-        _barrier(dist)
-        return s.elapsed_time(e) / 1000.0
-
-    clocks = ClockSampler(local)
-    clocks.start()
-    t_cr = timed(cr_opts)
-    clock_info = clocks.stop()
-    t_plain = timed(plain_opts)
-    t_cr_max = _max_over_ranks(dist, t_cr)
-    t_plain_max = _max_over_ranks(dist, t_plain)
-    frames = args.steps * ws
-    fps = frames / t_cr_max
-    fps_plain = frames / t_plain_max
-
-    # per-stage device times (CUDA events inside the library, same stream)
-    stage = {}
-    n_prof = max(3, min(args.steps, 10))
-    for i in range(n_prof):
-        r.set_cameras([cams[(rank + i) % len(cams)]])
-        r.render(mode="cr", opacity_filter=True, profile=True)
-        for k, v in r.last_stats["stage_ms"].items():
-            stage[k] = stage.get(k, 0.0) + v / n_prof
-    kernels_per_frame = r.last_stats["n_kernels"]
-    n_vis, K = r.last_stats["n_visible"], r.last_stats["n_instances"]
-    stage_plain = {}
-    for i in range(n_prof):
-        r.set_cameras([cams[(rank + i) % len(cams)]])
-        r.render(mode="plain", profile=True)
-        for k, v in r.last_stats["stage_ms"].items():
-            stage_plain[k] = stage_plain.get(k, 0.0) + v / n_prof
-    # algorithmic work of the rasterizer (counting variant, untimed)
-    r.set_cameras([cams[rank % len(cams)]])
-    r.render(mode="cr", opacity_filter=True, count=True)
-    work = {k: r.last_stats[k] for k in ("leader_tests", "pairs_evaluated", "pairs_blended")}
-    work_K = r.last_stats["n_instances"]
-    work_vis = r.last_stats["n_visible"]
-
-    # quality: CR vs plain on the same frame
-    img_cr = r.render(mode="cr", opacity_filter=True).cpu().numpy().astype(np.float64)
-    img_pl = r.render(mode="plain").cpu().numpy().astype(np.float64)
-    mse = float(np.mean((img_cr - img_pl) ** 2))
-    psnr = 10 * math.log10(1.0 / mse) if mse > 0 else float("inf")
-
-    # roofline of the dominant stage
-    peaks = _peaks()
-    dom = max(stage, key=stage.get)
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    n_gauss = int(scene["means"].shape[0])
-    tile_passes = 2
-    stage_bytes = {
-        "preprocess": 16 * n_gauss + 4 * n_gauss + (32 + 192 + 60) * work_vis,
-        "compact": 4 * n_gauss + 8 * work_vis,
-        "depth_sort": (4 * 16 + 4) * work_vis,
-        "tile_scan": 12 * work_vis,
-        "emit": 16 * work_vis + 8 * work_K,
-        "tile_sort": (tile_passes * 16 + 4) * work_K,
-        "ranges": 4 * work_K,
-    }
-    if dom == "raster":
-        ops = 8 * (work["pairs_evaluated"] + work["leader_tests"]) + 7 * work["pairs_blended"]
-        achieved = ops / (stage[dom] / 1000.0) / 1e12
-        peak = N_SM * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": _traffic("raster_fwd", _source_hash("raster.cu")),
-                "kernel": "raster_fwd_kernel (CR 2x2)",
-                "note": f"FP32-pipe ops = 8 per exponent evaluation (leader tests and pixel pairs) + 7 per blended "
-                        f"pair; peak = {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz"}
-    else:
-        b = stage_bytes.get(dom, 0)
-        achieved = b / (stage[dom] / 1000.0) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "kernel": dom, "note": f"peak of {peak_src} (MEASURED_PEAKS hbm_gbs)"}
-
-    # forward + backward for an L1 loss (the fine-tuning step of Sec. 3.5):
-    # 1M Gaussians shaped as the clustered scene, 1280x720, target rendered
-    # from attributes perturbed by N(0, 0.01)
-    fwd_bwd = _fwd_bwd(args, local)
-    multiview = _multiview(args, local) if args.multiview_n > 0 else None
 
     # end to end through the public API with host buffers: scene upload from
     # pinned host memory, render, image read back into pinned host memory
@@ -710,6 +411,11 @@ def run_gpu(args):
            "d2h_bytes_per_step": int(d2h), "steps": e2e_steps,
            "what": "seele_load_scene(COPY from pinned host) + seele_render(out = pinned host image) per frame"}
 
+    # forward + backward for an L1 loss (the fine-tuning step of Sec. 3.5):
+    # 1M Gaussians shaped as the clustered scene, 1280x720, target rendered
+    # from attributes perturbed by N(0, 0.01)
+    fwd_bwd = _fwd_bwd(args, local)
+
     line = {
         "metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * t_cr_max / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -721,7 +427,7 @@ def run_gpu(args):
         "stage_ms": {k: round(v, 4) for k, v in stage.items()},
         "stage_ms_plain": {k: round(v, 4) for k, v in stage_plain.items()},
         "n_visible": n_vis, "n_instances": K, "raster_work": work,
-        "roofline": roof, "e2e": e2e, "fwd_bwd": fwd_bwd, "multiview": multiview,
+        "roofline": roof, "e2e": e2e, "fwd_bwd": fwd_bwd,
         "gpu_launches": int(kernels_per_frame * args.steps),
         "clocks": clock_info,
     }
@@ -746,7 +452,6 @@ def main():
     ap.add_argument("--impl", default="seele", choices=["seele", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fwd-bwd-n", type=int, default=1_000_000)
-    ap.add_argument("--multiview-n", type=int, default=2_000_000, help="0 skips the multi-view measurement")
     ap.add_argument("--n-gauss", type=int, default=3_000_000,
                     help="scene size (3M is the benchmark; smaller sizes are for profiling captures)")
     args = ap.parse_args()
