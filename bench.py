@@ -278,6 +278,51 @@ def _fwd_bwd(args, device):
     return out
 
 
+def _multiview(args, device):
+    """64 cameras of mixed resolution rendered in one graph launch per batch."""
+    import torch
+
+    import scenegen
+    from paper_2503_05168_gb300 import Renderer
+
+    scene, cams = scenegen.multiview_2m(n=args.multiview_n)
+    r = Renderer(device)
+    r.load_scene(scene)
+    r.set_cameras(cams)
+    opts, tune_ms = r.autotune(mode="cr", opacity_filter=True)
+    r.render(options=opts)                       # sizes the instance buffers
+    out = torch.empty(3 * r.n_pixels, device=r.device)
+    gopts = r.make_options(mode="cr", opacity_filter=True, tile=(opts.tile_w, opts.tile_h), graph=True, sync=False)
+    for _ in range(3):
+        r.render(out=out, options=gopts)
+    r.synchronize()
+    k = max(3, min(args.steps, 10))
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(k):
+        r.render(out=out, options=gopts)
+    e.record()
+    r.synchronize()
+    ms = s.elapsed_time(e) / k
+    per_view = []
+    for _ in range(3):
+        r.render(out=out, options=r.make_options(mode="cr", opacity_filter=True, tile=(opts.tile_w, opts.tile_h),
+                                                 graph=True))
+        per_view += r.view_times()
+    n_views = len(cams)
+    res = {"views_per_s": n_views * 1000.0 / ms, "ms_per_batch": ms, "views": n_views,
+           "tile": [opts.tile_w, opts.tile_h], "autotune_ms": tune_ms,
+           "view_ms_p50": float(np.percentile(per_view, 50)), "view_ms_p99": float(np.percentile(per_view, 99)),
+           "instances": r.last_stats["n_instances"] if r.last_stats else None,
+           "workload": (f"multiview_2m: {args.multiview_n} Gaussians (unbounded-style), {n_views} cameras with "
+                        f"resolutions from {{640x360, 1280x720, 1920x1080}} at radius 3-6, one CUDA-graph launch "
+                        f"per batch, CR + opacity filter; per-view ms = start of preprocessing to the view's last "
+                        f"tile")}
+    r.close()
+    return res
+
+
 def run_gpu(args):
     import torch
 
@@ -415,6 +460,7 @@ def run_gpu(args):
     # 1M Gaussians shaped as the clustered scene, 1280x720, target rendered
     # from attributes perturbed by N(0, 0.01)
     fwd_bwd = _fwd_bwd(args, local)
+    multiview = _multiview(args, local) if args.multiview_n > 0 else None
 
     line = {
         "metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -427,7 +473,7 @@ def run_gpu(args):
         "stage_ms": {k: round(v, 4) for k, v in stage.items()},
         "stage_ms_plain": {k: round(v, 4) for k, v in stage_plain.items()},
         "n_visible": n_vis, "n_instances": K, "raster_work": work,
-        "roofline": roof, "e2e": e2e, "fwd_bwd": fwd_bwd,
+        "roofline": roof, "e2e": e2e, "fwd_bwd": fwd_bwd, "multiview": multiview,
         "gpu_launches": int(kernels_per_frame * args.steps),
         "clocks": clock_info,
     }
@@ -452,6 +498,7 @@ def main():
     ap.add_argument("--impl", default="seele", choices=["seele", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fwd-bwd-n", type=int, default=1_000_000)
+    ap.add_argument("--multiview-n", type=int, default=2_000_000, help="0 skips the multi-view measurement")
     ap.add_argument("--n-gauss", type=int, default=3_000_000,
                     help="scene size (3M is the benchmark; smaller sizes are for profiling captures)")
     args = ap.parse_args()
