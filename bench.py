@@ -114,11 +114,16 @@ def _barrier(dist):
         dist.barrier()
 
 
+def _reduce_device(dist):
+    return "cpu" if dist.get_backend() == "gloo" else "cuda"
+
+
 def _max_over_ranks(dist, v: float) -> float:
+    """The slowest rank's time (whole-job throughput divides by it)."""
     if dist is None:
         return v
     import torch
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device=_reduce_device(dist))
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -127,9 +132,15 @@ def _sum_over_ranks(dist, v: float) -> float:
     if dist is None:
         return v
     import torch
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device=_reduce_device(dist))
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def view_of(step: int, rank: int, world: int, n_views: int) -> int:
+    """Camera rendered by `rank` at `step`: views are dealt round-robin, so the
+    ranks of one step render distinct views and no data crosses ranks."""
+    return (rank + step * world) % n_views
 
 
 # ----------------------------------------------------------------- oracle --
@@ -202,14 +213,14 @@ def run_reference(args):
 
 # -------------------------------------------------------------------- GPU --
 
-def _timed_frames(r, cams, opts, steps, stream, cam_offset):
+def _timed_frames(r, cams, opts, steps, stream, rank, world):
     import torch
     out = torch.empty(3 * cams[0]["width"] * cams[0]["height"], device=r.device)
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
     start.record(stream)
     for i in range(steps):
-        r.set_cameras([cams[(cam_offset + i) % len(cams)]])
+        r.set_cameras([cams[view_of(i, rank, world, len(cams))]])
         r.render(out=out, options=opts)
     end.record(stream)
     return start, end
@@ -345,7 +356,7 @@ def run_gpu(args):
     # warm-up: synchronous renders grow the instance capacity, then async ones
     for opts in (cr_opts, plain_opts):
         for i in range(max(args.warmup, 3)):
-            r.set_cameras([cams[(rank + i * ws) % len(cams)]])
+            r.set_cameras([cams[view_of(i, rank, ws, len(cams))]])
             r.render(mode="cr" if opts.mode else "plain", opacity_filter=bool(opts.opacity_filter))
             r.render(options=opts)
         r.synchronize()
@@ -353,7 +364,7 @@ def run_gpu(args):
     def timed(opts):
         _barrier(dist)
         torch.cuda.synchronize()
-        s, e = _timed_frames(r, cams, opts, args.steps, stream, rank)
+        s, e = _timed_frames(r, cams, opts, args.steps, stream, rank, ws)
         torch.cuda.synchronize()
         r.synchronize()
         _barrier(dist)
@@ -374,7 +385,7 @@ def run_gpu(args):
     stage = {}
     n_prof = max(3, min(args.steps, 10))
     for i in range(n_prof):
-        r.set_cameras([cams[(rank + i) % len(cams)]])
+        r.set_cameras([cams[view_of(i, rank, ws, len(cams))]])
         r.render(mode="cr", opacity_filter=True, profile=True)
         for k, v in r.last_stats["stage_ms"].items():
             stage[k] = stage.get(k, 0.0) + v / n_prof
@@ -382,7 +393,7 @@ def run_gpu(args):
     n_vis, K = r.last_stats["n_visible"], r.last_stats["n_instances"]
     stage_plain = {}
     for i in range(n_prof):
-        r.set_cameras([cams[(rank + i) % len(cams)]])
+        r.set_cameras([cams[view_of(i, rank, ws, len(cams))]])
         r.render(mode="plain", profile=True)
         for k, v in r.last_stats["stage_ms"].items():
             stage_plain[k] = stage_plain.get(k, 0.0) + v / n_prof
@@ -448,7 +459,7 @@ def run_gpu(args):
     t0 = time.perf_counter()
     for i in range(e2e_steps):
         r.load_scene({k: (v.numpy() if isinstance(v, torch.Tensor) else v) for k, v in pinned.items()})
-        r.set_cameras([cams[(rank + i) % len(cams)]])
+        r.set_cameras([cams[view_of(i, rank, ws, len(cams))]])
         r.render(out=host_img.numpy(), mode="cr", opacity_filter=True)
     torch.cuda.synchronize()
     t_e2e = _max_over_ranks(dist, time.perf_counter() - t0)
