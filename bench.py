@@ -289,6 +289,59 @@ def _fwd_bwd(args, device):
     return out
 
 
+def _ablation(args, device):
+    """The paper's ablation (Tbl. 4) and pixel-group sweep (Fig. 7) on the
+    clustered 500k scene with 16 view clusters, 8 orbit cameras at 1280x720:
+    frames/s and PSNR against the plain render of each variant."""
+    import torch
+
+    import scenegen
+    from paper_2503_05168_gb300 import Renderer
+
+    scene, cams = scenegen.clusters_500k(n=args.ablation_n)
+    r = Renderer(device)
+    r.load_scene(scene)
+    variants = {
+        "plain": dict(mode="plain"),
+        "hp_online": dict(mode="plain", opacity_filter=True),
+        "hp_online_cluster": dict(mode="plain", opacity_filter=True, cluster_filter=True),
+        "cr": dict(mode="cr"),
+        "full": dict(mode="cr", opacity_filter=True, cluster_filter=True),
+        "cr_group_1x1": dict(mode="cr", group=(1, 1)),
+        "cr_group_2x4": dict(mode="cr", group=(2, 4)),
+    }
+    refs = []
+    for c in cams:
+        r.set_cameras([c])
+        refs.append(r.render(mode="plain").clone())
+    out = {}
+    for name, kw in variants.items():
+        imgs = []
+        for c in cams:
+            r.set_cameras([c])
+            imgs.append(r.render(**kw).clone())
+        mse = float(np.mean([torch.mean((a - b) ** 2).item() for a, b in zip(imgs, refs)]))
+        opts = r.make_options(sync=False, **kw)
+        k = max(2, min(args.steps, 10))
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record()
+        for i in range(k * len(cams)):
+            r.set_cameras([cams[i % len(cams)]])
+            r.render(options=opts)
+        e.record()
+        r.synchronize()
+        ms = s.elapsed_time(e) / (k * len(cams))
+        out[name] = {"fps": 1000.0 / ms, "psnr_vs_plain_db": (10 * math.log10(1.0 / mse) if mse > 0 else None)}
+    base = out["plain"]["fps"]
+    for v in out.values():
+        v["speedup"] = v["fps"] / base
+    out["workload"] = (f"clusters_500k: {args.ablation_n} Gaussians in 64 clusters, 16 view clusters (nearest + 3 "
+                       f"neighbours), 8 orbit cameras at r 4, 1280x720, mean over the cameras")
+    r.close()
+    return out
+
+
 def _multiview(args, device):
     """64 cameras of mixed resolution rendered in one graph launch per batch."""
     import torch
@@ -375,6 +428,24 @@ def run_gpu(args):
     t_cr = timed(cr_opts)
     clock_info = clocks.stop()
     t_plain = timed(plain_opts)
+    # the same frames replayed as a captured CUDA graph (poses change per step)
+    gr_opts = r.make_options(mode="cr", opacity_filter=True, sync=False, graph=True)
+    gout = torch.empty(3 * 1920 * 1080, device=r.device)
+    for i in range(3):
+        r.set_cameras([cams[view_of(i, rank, ws, len(cams))]])
+        r.render(out=gout, options=gr_opts)
+    r.synchronize()
+    _barrier(dist)
+    torch.cuda.synchronize()
+    gs, ge = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    gs.record(stream)
+    for i in range(args.steps):
+        r.set_cameras([cams[view_of(i, rank, ws, len(cams))]])
+        r.render(out=gout, options=gr_opts)
+    ge.record(stream)
+    torch.cuda.synchronize()
+    r.synchronize()
+    fps_graph = args.steps * ws / _max_over_ranks(dist, gs.elapsed_time(ge) / 1000.0)
     t_cr_max = _max_over_ranks(dist, t_cr)
     t_plain_max = _max_over_ranks(dist, t_plain)
     frames = args.steps * ws
@@ -472,6 +543,7 @@ def run_gpu(args):
     # from attributes perturbed by N(0, 0.01)
     fwd_bwd = _fwd_bwd(args, local)
     multiview = _multiview(args, local) if args.multiview_n > 0 else None
+    ablation = _ablation(args, local) if args.ablation_n > 0 else None
 
     line = {
         "metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -484,7 +556,8 @@ def run_gpu(args):
         "stage_ms": {k: round(v, 4) for k, v in stage.items()},
         "stage_ms_plain": {k: round(v, 4) for k, v in stage_plain.items()},
         "n_visible": n_vis, "n_instances": K, "raster_work": work,
-        "roofline": roof, "e2e": e2e, "fwd_bwd": fwd_bwd, "multiview": multiview,
+        "roofline": roof, "e2e": e2e, "fwd_bwd": fwd_bwd, "multiview": multiview, "ablation": ablation,
+        "graph_fps": fps_graph,
         "gpu_launches": int(kernels_per_frame * args.steps),
         "clocks": clock_info,
     }
@@ -510,6 +583,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fwd-bwd-n", type=int, default=1_000_000)
     ap.add_argument("--multiview-n", type=int, default=2_000_000, help="0 skips the multi-view measurement")
+    ap.add_argument("--ablation-n", type=int, default=500_000, help="0 skips the ablation")
     ap.add_argument("--n-gauss", type=int, default=3_000_000,
                     help="scene size (3M is the benchmark; smaller sizes are for profiling captures)")
     args = ap.parse_args()
