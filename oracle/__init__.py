@@ -46,7 +46,7 @@ CAMERA_DTYPE = np.dtype(
 )
 OPTIONS_DTYPE = np.dtype(
     [("tile_w", "i4"), ("tile_h", "i4"), ("opacity_filter", "i4"), ("cr", "i4"), ("group_w", "i4"),
-     ("group_h", "i4"), ("use_mask", "i4"), ("sel_bits", "u4"), ("pad", "i4"), ("alpha_min", "f8"),
+     ("group_h", "i4"), ("use_mask", "i4"), ("sel_bits", "u4"), ("tile_test", "i4"), ("alpha_min", "f8"),
      ("alpha_max", "f8"), ("t_stop", "f8"), ("dilation", "f8"), ("frustum_slack", "f8")],
     align=True,
 )
@@ -86,7 +86,7 @@ def _L():
         lib.oc_preprocess.restype = None
         lib.oc_count_instances.argtypes = [I64, P]
         lib.oc_count_instances.restype = I64
-        lib.oc_build_instances.argtypes = [I64, P, I32, I32, P, P, P]
+        lib.oc_build_instances.argtypes = [I64, P, P, I32, I32, P, P, P]
         lib.oc_build_instances.restype = None
         lib.oc_render_tiled.argtypes = [P, P, P, I32, I32, P, P, P, P, P, P, I32]
         lib.oc_render_tiled.restype = None
@@ -124,6 +124,7 @@ class Options:
     group_h: int = 2
     use_mask: bool = False
     sel_bits: int = 0xFFFFFFFF
+    tile_test: str = "ellipse"          # or "rect": every tile of the bounding rect
     alpha_min: float = 1.0 / 255.0
     alpha_max: float = 0.99
     t_stop: float = 1e-4
@@ -139,6 +140,9 @@ class Options:
         o["opacity_filter"] = int(self.opacity_filter)
         o["cr"] = int(self.cr)
         o["use_mask"] = int(self.use_mask)
+        if self.tile_test not in ("ellipse", "rect"):
+            raise ValueError("tile_test must be 'ellipse' or 'rect'")
+        o["tile_test"] = int(self.tile_test == "ellipse")
         o["sel_bits"] = self.sel_bits & 0xFFFFFFFF
         for k in ("alpha_min", "alpha_max", "t_stop", "dilation", "frustum_slack"):
             o[k] = getattr(self, k)
@@ -215,7 +219,8 @@ def instances(proj: np.ndarray, cam, opts: Options):
     tile = np.zeros(max(K, 1), np.int32)
     gid = np.zeros(max(K, 1), np.int32)
     ranges = np.zeros((tx * ty, 2), np.int64)
-    lib.oc_build_instances(proj.shape[0], _p(proj), tx, ty, _p(tile), _p(gid), _p(ranges))
+    o = opts.to_struct()
+    lib.oc_build_instances(proj.shape[0], _p(proj), _p(o), tx, ty, _p(tile), _p(gid), _p(ranges))
     return tile[:K], gid[:K], ranges
 
 

@@ -33,6 +33,11 @@
  *   rect      r = ceil(sqrt(t_g * lambda_max(Sigma'))); pixel box
  *             [floor(u - .5 - r), ceil(u - .5 + r)] clipped to the image, mapped
  *             to tiles by integer division (Sec. 3.3 "Online Filtering").
+ *   tiles     with the ellipse tile test, a tile of the rect is kept only if
+ *             the ellipse q <= t_g (1 + 1e-3) meets the rectangle spanned by
+ *             the tile's pixel centres; the 0.1% inflation keeps the test
+ *             conservative under FP32 rounding.  Every pixel with q <= t_g lies
+ *             in a kept tile, so the image does not depend on the test.
  *   blending  front to back in (fp32 depth, index) order (Sec. 3.1 "Sorting");
  *             skip alpha < alpha_theta; T' = T (1 - alpha); if T' < Gamma_theta
  *             the pixel stops without blending; otherwise C += T alpha c,
@@ -70,7 +75,7 @@ typedef struct {
     int32_t group_w, group_h; /* pixel group P of Alg. 1 */
     int32_t use_mask;         /* 1: view-cluster filter of Sec. 3.3 */
     uint32_t sel_bits;        /* clusters selected for this camera */
-    int32_t pad;
+    int32_t tile_test;        /* 0: every tile of the rect; 1: tiles the support ellipse reaches */
     double alpha_min;         /* alpha_theta = 1/255 (Sec. 3.1) */
     double alpha_max;         /* 0.99 clamp */
     double t_stop;            /* Gamma_theta */
@@ -218,6 +223,50 @@ static double sigmoid(double x) { return 1.0 / (1.0 + exp(-x)); }
 
 static double frac_dist(double x) { return fabs(x - nearbyint(x)); }
 
+#define OC_TILE_INFLATE 1e-3
+
+/* Tiles [*lo, *hi] of tile row ty that the tile-test ellipse q <= t reaches,
+ * within the rect.  The ellipse cut by the row's band of pixel-centre y values
+ * is convex, so its x-range is one interval: the largest x over the band is at
+ * the ellipse's rightmost point (dy = -B x_r / C) clamped to the band, the
+ * smallest at the leftmost point (dy = +B x_r / C) clamped, and a tile is kept
+ * when its pixel-centre x-range overlaps that interval.  Returns 0 for an
+ * empty row.  *margin receives the distance (px) of these decisions to a
+ * flip. */
+static int row_span(const oc_proj* P, const oc_options* opt, int ty, int* lo, int* hi, double* margin) {
+    if (!opt->tile_test) {
+        *lo = P->rect[0];
+        *hi = P->rect[2];
+        return 1;
+    }
+    const double A = P->conic[0], B = P->conic[1], C = P->conic[2];
+    const double t = P->tg * (1.0 + OC_TILE_INFLATE);
+    const double det = A * C - B * B;
+    const double xr = sqrt(t * C / det), yr = sqrt(t * A / det);
+    const int TW = opt->tile_w, TH = opt->tile_h;
+    const double ya = ty * TH + 0.5 - P->uv[1], yb = ty * TH + TH - 0.5 - P->uv[1];
+    double m = fabs(ya - yr);
+    if (fabs(yb + yr) < m) m = fabs(yb + yr);
+    if (m < *margin) *margin = m;
+    const double blo = ya > -yr ? ya : -yr, bhi = yb < yr ? yb : yr;
+    if (blo > bhi) return 0;
+    double dr = -B * xr / C, dl = B * xr / C;
+    dr = dr < blo ? blo : (dr > bhi ? bhi : dr);
+    dl = dl < blo ? blo : (dl > bhi ? bhi : dl);
+    double sr = A * t - det * dr * dr, sl = A * t - det * dl * dl;
+    const double xR = P->uv[0] + (-B * dr + sqrt(sr > 0 ? sr : 0)) / A;
+    const double xL = P->uv[0] + (-B * dl - sqrt(sl > 0 ? sl : 0)) / A;
+    const double fr = (xR - 0.5) / TW, fl = (xL - TW + 0.5) / TW;
+    if (frac_dist(fr) * TW < *margin) *margin = frac_dist(fr) * TW;
+    if (frac_dist(fl) * TW < *margin) *margin = frac_dist(fl) * TW;
+    int a = (int)ceil(fl), b = (int)floor(fr);
+    if (a < P->rect[0]) a = P->rect[0];
+    if (b > P->rect[2]) b = P->rect[2];
+    *lo = a;
+    *hi = b;
+    return b >= a;
+}
+
 static void project_one(int64_t g, int sh_degree, const double* means, const double* log_scales,
                         const double* quats, const double* logits, const double* sh,
                         const uint32_t* mask, const oc_camera* cam, const oc_options* opt,
@@ -323,12 +372,21 @@ static void project_one(int64_t g, int sh_degree, const double* means, const dou
     if (py0 < 0) py0 = 0;
     if (px1 > cam->width - 1) px1 = cam->width - 1;
     if (py1 > cam->height - 1) py1 = cam->height - 1;
-    P->margin_px = mpx;
     P->margin_rel = mrel;
-    if (px0 > px1 || py0 > py1) return;
+    P->tg = tg;
+    if (px0 > px1 || py0 > py1) {
+        P->margin_px = mpx;
+        return;
+    }
     P->rect[0] = px0 / opt->tile_w; P->rect[1] = py0 / opt->tile_h;
     P->rect[2] = px1 / opt->tile_w; P->rect[3] = py1 / opt->tile_h;
-    P->ntiles = (P->rect[2] - P->rect[0] + 1) * (P->rect[3] - P->rect[1] + 1);
+    P->ntiles = 0;
+    for (int ty = P->rect[1]; ty <= P->rect[3]; ++ty) {
+        int lo, hi;
+        if (row_span(P, opt, ty, &lo, &hi, &mpx)) P->ntiles += hi - lo + 1;
+    }
+    P->margin_px = mpx;
+    if (P->ntiles == 0) return;
 
     /* colour from SH in the view direction */
     double cc[3];
@@ -346,7 +404,6 @@ static void project_one(int64_t g, int sh_degree, const double* means, const dou
     }
 
     P->opacity = o;
-    P->tg = tg;
     P->depth32 = (float)Z;
     P->visible = 1;
 }
@@ -386,7 +443,7 @@ int64_t oc_count_instances(int64_t n, const oc_proj* proj) {
 
 /* Writes the sorted instance list (tile id, Gaussian id) and the per-tile
    [start, end) ranges; tile id = ty * tiles_x + tx. */
-void oc_build_instances(int64_t n, const oc_proj* proj, int tiles_x, int tiles_y,
+void oc_build_instances(int64_t n, const oc_proj* proj, const oc_options* opt, int tiles_x, int tiles_y,
                         int32_t* out_tile, int32_t* out_gid, int64_t* out_ranges) {
     int64_t K = oc_count_instances(n, proj);
     oc_inst* inst = (oc_inst*)malloc(sizeof(oc_inst) * (K > 0 ? K : 1));
@@ -396,13 +453,17 @@ void oc_build_instances(int64_t n, const oc_proj* proj, int tiles_x, int tiles_y
         if (!P->visible) continue;
         uint32_t bits;
         memcpy(&bits, &P->depth32, 4);
-        for (int ty = P->rect[1]; ty <= P->rect[3]; ++ty)
-            for (int tx = P->rect[0]; tx <= P->rect[2]; ++tx) {
+        for (int ty = P->rect[1]; ty <= P->rect[3]; ++ty) {
+            int lo, hi;
+            double mdummy = INFINITY;
+            if (!row_span(P, opt, ty, &lo, &hi, &mdummy)) continue;
+            for (int tx = lo; tx <= hi; ++tx) {
                 inst[k].tile = ty * tiles_x + tx;
                 inst[k].dbits = bits;
                 inst[k].gid = (int32_t)g;
                 ++k;
             }
+        }
     }
     qsort(inst, (size_t)K, sizeof(oc_inst), inst_cmp);
     int64_t ntiles = (int64_t)tiles_x * tiles_y;

@@ -275,6 +275,81 @@ def test_opacity_aware_filter_keeps_the_image_and_drops_instances():
     np.testing.assert_allclose(p1["tg"][p1["visible"] == 1], np.minimum(2 * np.log(o / AT), 9.0), rtol=1e-15)
 
 
+def test_ellipse_tile_test_keeps_the_image_and_is_a_subset_of_the_rect():
+    """The ellipse tile test (Sec. 3.3's online filtering, tightened from the
+    bounding rect to the support ellipse) drops tile instances but no pixel
+    that the support q <= t_g reaches, so the image is the same."""
+    s, cam = _random_scene(n=3000)
+    for of in (False, True):
+        rr, pr, tr, gr, _ = oracle.render(oracle.Scene64.from_scene(s), cam,
+                                          oracle.Options(opacity_filter=of, tile_test="rect"), 4)
+        re, pe, te, ge, _ = oracle.render(oracle.Scene64.from_scene(s), cam,
+                                          oracle.Options(opacity_filter=of), 4)
+        np.testing.assert_array_equal(rr.rgb, re.rgb)
+        np.testing.assert_array_equal(rr.T, re.T)
+        assert re.counters["alpha_evals"] < rr.counters["alpha_evals"]
+        rect_set = set(zip(tr.tolist(), gr.tolist()))
+        ell_set = set(zip(te.tolist(), ge.tolist()))
+        assert ell_set < rect_set and len(ell_set) < 0.8 * len(rect_set)
+        np.testing.assert_array_equal(pr["rect"], pe["rect"])
+        assert np.all(pe["ntiles"] <= pr["ntiles"])
+
+
+def _min_q_on_box(A, B, C, x0, x1, y0, y1):
+    """Minimum of q = A x^2 + 2 B x y + C y^2 over the box [x0,x1] x [y0,y1]:
+    zero if the box holds the origin, else the smallest of the four edge
+    minima (each a 1-D quadratic minimised in closed form and clamped)."""
+    if x0 <= 0 <= x1 and y0 <= 0 <= y1:
+        return 0.0
+    best = np.inf
+    for y in (y0, y1):  # horizontal edges: q(x) = A x^2 + 2 B y x + C y^2
+        x = min(max(-B * y / A, x0), x1)
+        best = min(best, A * x * x + 2 * B * x * y + C * y * y)
+    for x in (x0, x1):
+        y = min(max(-B * x / C, y0), y1)
+        best = min(best, A * x * x + 2 * B * x * y + C * y * y)
+    return best
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (32, 8)])
+def test_ellipse_tile_test_brute_force(tile):
+    """A tile of the rect is kept exactly when the inflated support ellipse
+    q <= t_g (1 + 1e-3) meets the rectangle of its pixel centres (minimum of q
+    over that box by edge minimisation, an independent construction), and so
+    every tile holding a pixel centre with q <= t_g is kept (checked on the
+    pixel grid)."""
+    s, cam = _random_scene(n=600)
+    opts = oracle.Options(tile_w=tile[0], tile_h=tile[1], opacity_filter=True)
+    proj = oracle.preprocess(oracle.Scene64.from_scene(s), cam, opts)
+    tiles, gid, _ = oracle.instances(proj, cam, opts)
+    tx_n, _ = oracle.tile_grid(cam, opts)
+    kept = set(zip(gid.tolist(), tiles.tolist()))
+    TW, TH = tile
+    n_checked = n_dropped = 0
+    for g in np.flatnonzero(proj["visible"] == 1):
+        P = proj[g]
+        A, B, C = P["conic"]
+        t = P["tg"] * (1 + 1e-3)
+        u, v = P["uv"]
+        x0r, y0r, x1r, y1r = P["rect"]
+        for ty in range(y0r, y1r + 1):
+            for tx in range(x0r, x1r + 1):
+                qmin = _min_q_on_box(A, B, C, tx * TW + 0.5 - u, tx * TW + TW - 0.5 - u,
+                                     ty * TH + 0.5 - v, ty * TH + TH - 0.5 - v)
+                if abs(qmin - t) < 1e-9 * t:
+                    continue
+                want = qmin <= t
+                assert ((g, ty * tx_n + tx) in kept) == want, (g, tx, ty, qmin, t)
+                xs = tx * TW + 0.5 + np.arange(TW) - u
+                ys = ty * TH + 0.5 + np.arange(TH) - v
+                X, Y = np.meshgrid(xs, ys)
+                if np.min(A * X * X + 2 * B * X * Y + C * Y * Y) <= P["tg"]:
+                    assert want
+                n_checked += 1
+                n_dropped += not want
+    assert n_checked > 1000 and n_dropped > 0.2 * n_checked
+
+
 # ------------------------------------------------------------------- CR --
 
 def test_cr_with_one_pixel_groups_is_plain():
