@@ -57,7 +57,8 @@ typedef enum {
     SEELE_ERR_CUDA = 3,      /* a CUDA runtime call failed */
     SEELE_ERR_CAPACITY = 4,  /* tile-instance capacity exceeded (async mode only) */
     SEELE_ERR_TIMEOUT = 5,   /* a bounded device spin-wait gave up */
-    SEELE_ERR_OOM = 6        /* device allocation failed */
+    SEELE_ERR_OOM = 6,       /* device allocation failed */
+    SEELE_ERR_INTERNAL = 7   /* a device consistency check failed (outputs undefined) */
 } seele_status;
 
 enum { SEELE_SCENE_COPY = 0, SEELE_SCENE_BORROW = 1 };
@@ -91,6 +92,14 @@ typedef struct {
 } seele_camera;
 
 enum { SEELE_MODE_PLAIN = 0, SEELE_MODE_CR = 1 };
+
+/* Tile test: which tiles of a Gaussian's bounding rect get an instance.
+ * RECT keeps every tile of the rect of Sec. 3.3's support radius; ELLIPSE
+ * keeps only the tiles whose pixel centres the support ellipse q <= t_g
+ * reaches (inflated by 0.1% and widened by 1/256 px, so that no blended pixel
+ * is lost to FP32 rounding).  Both give the same image; ELLIPSE has fewer
+ * instances to sort and to rasterize. */
+enum { SEELE_TILES_RECT = 0, SEELE_TILES_ELLIPSE = 1 };
 
 /* Render flags */
 enum {
@@ -131,6 +140,7 @@ typedef struct {
     float alpha_max;              /* alpha clamp, 0.99 */
     float t_stop;                 /* Gamma_theta, 1e-4 */
     int32_t flags;                /* SEELE_RENDER_* */
+    int32_t tile_test;            /* SEELE_TILES_ELLIPSE (default) or SEELE_TILES_RECT */
 } seele_options;
 
 /* Per-render statistics (all cameras of the call). */
@@ -156,7 +166,8 @@ typedef struct {
 } seele_grads;
 
 /* Fills *opt with: PLAIN, 2x2 group, 16x16 tiles, filters off, M = 3,
- * alpha_theta = 1/255 (Sec. 3.1), clamp 0.99, Gamma_theta = 1e-4, flags 0. */
+ * alpha_theta = 1/255 (Sec. 3.1), clamp 0.99, Gamma_theta = 1e-4, flags 0,
+ * ellipse tile test. */
 void seele_default_options(seele_options* opt);
 
 /* Creates a context on CUDA device `device` that enqueues on `cuda_stream`

@@ -35,9 +35,10 @@
  *             to tiles by integer division (Sec. 3.3 "Online Filtering").
  *   tiles     with the ellipse tile test, a tile of the rect is kept only if
  *             the ellipse q <= t_g (1 + 1e-3) meets the rectangle spanned by
- *             the tile's pixel centres; the 0.1% inflation keeps the test
- *             conservative under FP32 rounding.  Every pixel with q <= t_g lies
- *             in a kept tile, so the image does not depend on the test.
+ *             the tile's pixel centres widened by 1/256 px on every side; the
+ *             relative and absolute slack keep the test conservative under
+ *             FP32 rounding.  Every pixel with q <= t_g lies in a kept tile, so
+ *             the image does not depend on the test.
  *   blending  front to back in (fp32 depth, index) order (Sec. 3.1 "Sorting");
  *             skip alpha < alpha_theta; T' = T (1 - alpha); if T' < Gamma_theta
  *             the pixel stops without blending; otherwise C += T alpha c,
@@ -224,6 +225,7 @@ static double sigmoid(double x) { return 1.0 / (1.0 + exp(-x)); }
 static double frac_dist(double x) { return fabs(x - nearbyint(x)); }
 
 #define OC_TILE_INFLATE 1e-3
+#define OC_TILE_SLACK (1.0 / 256.0)
 
 /* Tiles [*lo, *hi] of tile row ty that the tile-test ellipse q <= t reaches,
  * within the rect.  The ellipse cut by the row's band of pixel-centre y values
@@ -244,7 +246,8 @@ static int row_span(const oc_proj* P, const oc_options* opt, int ty, int* lo, in
     const double det = A * C - B * B;
     const double xr = sqrt(t * C / det), yr = sqrt(t * A / det);
     const int TW = opt->tile_w, TH = opt->tile_h;
-    const double ya = ty * TH + 0.5 - P->uv[1], yb = ty * TH + TH - 0.5 - P->uv[1];
+    const double sl_px = OC_TILE_SLACK;
+    const double ya = ty * TH + 0.5 - sl_px - P->uv[1], yb = ty * TH + TH - 0.5 + sl_px - P->uv[1];
     double m = fabs(ya - yr);
     if (fabs(yb + yr) < m) m = fabs(yb + yr);
     if (m < *margin) *margin = m;
@@ -256,7 +259,7 @@ static int row_span(const oc_proj* P, const oc_options* opt, int ty, int* lo, in
     double sr = A * t - det * dr * dr, sl = A * t - det * dl * dl;
     const double xR = P->uv[0] + (-B * dr + sqrt(sr > 0 ? sr : 0)) / A;
     const double xL = P->uv[0] + (-B * dl - sqrt(sl > 0 ? sl : 0)) / A;
-    const double fr = (xR - 0.5) / TW, fl = (xL - TW + 0.5) / TW;
+    const double fr = (xR + sl_px - 0.5) / TW, fl = (xL - sl_px - TW + 0.5) / TW;
     if (frac_dist(fr) * TW < *margin) *margin = frac_dist(fr) * TW;
     if (frac_dist(fl) * TW < *margin) *margin = frac_dist(fl) * TW;
     int a = (int)ceil(fl), b = (int)floor(fr);

@@ -160,8 +160,12 @@ class Renderer:
     # -- rendering -----------------------------------------------------------
     @staticmethod
     def make_options(mode="plain", group=(2, 2), tile=(16, 16), opacity_filter=False, cluster_filter=False,
-                     n_neighbors=3, sync=True, profile=False, count=False, graph=False, **kw) -> _abi.Options:
+                     n_neighbors=3, sync=True, profile=False, count=False, graph=False, tile_test="ellipse",
+                     **kw) -> _abi.Options:
         o = default_options()
+        if tile_test not in ("ellipse", "rect"):
+            raise ValueError("tile_test must be 'ellipse' or 'rect'")
+        o.tile_test = _abi.TILES_ELLIPSE if tile_test == "ellipse" else _abi.TILES_RECT
         o.mode = _abi.MODE_CR if mode == "cr" else _abi.MODE_PLAIN
         o.group_w, o.group_h = group
         o.tile_w, o.tile_h = tile

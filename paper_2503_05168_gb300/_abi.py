@@ -12,9 +12,10 @@ LIB_PATH = os.path.join(HERE, "libseele.so")
 
 SEELE_OK = 0
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_STATE", 3: "ERR_CUDA", 4: "ERR_CAPACITY", 5: "ERR_TIMEOUT",
-                6: "ERR_OOM"}
+                6: "ERR_OOM", 7: "ERR_INTERNAL"}
 SCENE_COPY, SCENE_BORROW = 0, 1
 MODE_PLAIN, MODE_CR = 0, 1
+TILES_RECT, TILES_ELLIPSE = 0, 1
 RENDER_ASYNC = 1
 RENDER_PROFILE = 2
 RENDER_COUNT = 4
@@ -42,7 +43,7 @@ class Options(ctypes.Structure):
                 ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("opacity_filter", ctypes.c_int32),
                 ("cluster_filter", ctypes.c_int32), ("n_neighbors", ctypes.c_int32),
                 ("alpha_min", ctypes.c_float), ("alpha_max", ctypes.c_float), ("t_stop", ctypes.c_float),
-                ("flags", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("tile_test", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):

@@ -203,12 +203,14 @@ int bits_for(uint64_t v) {
 // Emission, stable radix sort by tile id and tile ranges.  Returns the
 // ping-pong buffer holding the sorted record ids, or -1 on a launch error.
 template <typename KeyT>
-int enqueue_tile_sort(seele_ctx* c, const uint32_t* order, const uint2* rect, const CamDev* cams, DeviceStatus* st,
-                      const uint32_t* n_inst, uint32_t n_tiles, int key_bits, uint64_t cap, int emit_blocks,
-                      uint64_t* lb, uint32_t* scnt, uint32_t* soff, int& launches, cudaStream_t s) {
+int enqueue_tile_sort(seele_ctx* c, const uint32_t* order, const uint2* rect, const float4* rec, const CamDev* cams,
+                      const FrameParams& fp, DeviceStatus* st, const uint32_t* n_inst, uint32_t n_tiles, int key_bits,
+                      uint64_t cap, int emit_blocks, uint64_t* lb, uint32_t* scnt, uint32_t* soff, int& launches,
+                      cudaStream_t s) {
     KeyT* keys[2] = {ptr<KeyT>(c->instk[0]), ptr<KeyT>(c->instk[1])};
     uint32_t* vals[2] = {ptr<uint32_t>(c->instv[0]), ptr<uint32_t>(c->instv[1])};
-    launch_emit<KeyT>(order, ptr<uint32_t>(c->offs), rect, cams, (int)c->n, st, keys[0], vals[0], emit_blocks, s);
+    launch_emit<KeyT>(order, ptr<uint32_t>(c->offs), rect, rec, cams, (int)c->n, fp.tile_w, fp.tile_h, fp.tile_test, st,
+                      keys[0], vals[0], emit_blocks, s);
     if (cudaPeekAtLastError() != cudaSuccess) return -1;
     ++launches;
     SEELE_MARK_EXT(c, SEELE_STAGE_TILE_SORT);
@@ -244,6 +246,8 @@ seele_status check_options(seele_ctx* c, const seele_options* opt) {
     if (opt->cluster_filter && (c->n_clusters <= 0 || !c->has_mask))
         return fail(c, SEELE_ERR_STATE, "cluster_filter needs a scene with view clusters");
     if (opt->n_neighbors < 0) return fail(c, SEELE_ERR_ARG, "n_neighbors must be >= 0");
+    if (opt->tile_test != SEELE_TILES_RECT && opt->tile_test != SEELE_TILES_ELLIPSE)
+        return fail(c, SEELE_ERR_ARG, "bad tile_test");
     return SEELE_OK;
 }
 
@@ -292,6 +296,7 @@ void fill_params(seele_ctx* c, const seele_options* opt, FrameInfo& f) {
     fp.tile_w = opt->tile_w;
     fp.tile_h = opt->tile_h;
     fp.opacity_filter = opt->opacity_filter ? 1 : 0;
+    fp.tile_test = opt->tile_test == SEELE_TILES_ELLIPSE ? 1 : 0;
     fp.use_mask = opt->cluster_filter ? 1 : 0;
     fp.alpha_min = opt->alpha_min;
     fp.alpha_max = opt->alpha_max;
@@ -445,10 +450,10 @@ seele_status enqueue_frame(seele_ctx* c, const seele_options* opt, const FrameIn
     SEELE_MARK(SEELE_STAGE_EMIT);
     const uint32_t* n_inst = &st->n_inst_valid;
     if (f.short_keys)
-        fin = enqueue_tile_sort<uint16_t>(c, order, po.rect, cams, st, n_inst, (uint32_t)tiles_total, f.tile_bits, cap,
+        fin = enqueue_tile_sort<uint16_t>(c, order, po.rect, po.rec, cams, f.fp, st, n_inst, (uint32_t)tiles_total, f.tile_bits, cap,
                                           emit_blocks, lb, scnt, soff, launches, s);
     else
-        fin = enqueue_tile_sort<uint32_t>(c, order, po.rect, cams, st, n_inst, (uint32_t)tiles_total, f.tile_bits, cap,
+        fin = enqueue_tile_sort<uint32_t>(c, order, po.rect, po.rec, cams, f.fp, st, n_inst, (uint32_t)tiles_total, f.tile_bits, cap,
                                           emit_blocks, lb, scnt, soff, launches, s);
     if (fin < 0) return fail(c, SEELE_ERR_CUDA, "tile sort launch failed: %s", cudaGetErrorString(cudaGetLastError()));
 
@@ -499,6 +504,7 @@ void seele_default_options(seele_options* o) {
     o->alpha_max = 0.99f;
     o->t_stop = 1e-4f;
     o->flags = 0;
+    o->tile_test = SEELE_TILES_ELLIPSE;
 }
 
 seele_status seele_create(seele_ctx** out, int device, void* cuda_stream) {
@@ -659,6 +665,10 @@ seele_status seele_synchronize(seele_ctx* c) {
         c->rendered = false;
         return fail(c, SEELE_ERR_TIMEOUT, "device wait gave up at site %u", h.timeout_site);
     }
+    if (h.error == kErrInternal) {
+        c->rendered = false;
+        return fail(c, SEELE_ERR_INTERNAL, "device consistency check failed at site %u", h.timeout_site);
+    }
     return SEELE_OK;
 }
 
@@ -766,6 +776,8 @@ seele_status seele_render(seele_ctx* c, const seele_options* opt, float* out_rgb
         }
         if (h.error == kErrCapacity) return fail(c, SEELE_ERR_CAPACITY, "capacity still exceeded after growth");
         if (h.error == kErrTimeout) return fail(c, SEELE_ERR_TIMEOUT, "device wait gave up at site %u", h.timeout_site);
+        if (h.error == kErrInternal)
+            return fail(c, SEELE_ERR_INTERNAL, "device consistency check failed at site %u", h.timeout_site);
         c->rendered = true;
         break;
     }

@@ -3,85 +3,155 @@
 // per-tile ranges into the sorted instance list.
 #include "common.cuh"
 #include "kernels.h"
+#include "tiletest.cuh"
 
 namespace seele {
 
 // A warp takes 32 consecutive visible records in depth order and writes all
-// their (global tile, record) instances as one contiguous, coalesced run:
-// lane l writes outputs l, l + 32, ... of the run and finds the record it
-// belongs to by a binary search over the warp's exclusive counts.  Emission in
-// depth order means the later stable sort by tile leaves each tile's list
-// front to back; within one record the tiles of its rect go row-major.
+// their (global tile, record) instances as one contiguous, coalesced run.
+// The records' tile rows are expanded 32 at a time (lane -> (record, row) by a
+// binary search over the exclusive row counts); each row lane finds its span
+// of tiles with the ellipse test of tiletest.cuh (or takes the whole rect row),
+// and the warp then writes the rows' tiles cooperatively: lane l writes
+// outputs l, l + 32, ... and finds its row by a second binary search.
+// Emission in depth order means the later stable sort by tile leaves each
+// tile's list front to back; within one record tiles go row-major.  Every
+// write stays inside the warp's run [offsets[wb], offsets[wb + 32]); a span
+// sum that disagrees with the preprocessing count is reported as kErrInternal.
+__device__ __forceinline__ int warp_search(uint32_t excl, uint32_t o) {
+    // largest lane s with excl_s <= o (excl non-decreasing over the lanes)
+    int s = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const uint32_t e = __shfl_sync(0xffffffffu, excl, s + step);
+        if (e <= o) s += step;
+    }
+    return s;
+}
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
 template <typename KeyT>
 __global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ order,
                                                    const uint32_t* __restrict__ offsets,
-                                                   const uint2* __restrict__ rect, const CamDev* __restrict__ cams,
-                                                   int n_gauss, const DeviceStatus* __restrict__ st,
+                                                   const uint2* __restrict__ rect, const float4* __restrict__ rec,
+                                                   const CamDev* __restrict__ cams, int n_gauss, int tile_w,
+                                                   int tile_h, int ellipse, DeviceStatus* st,
                                                    KeyT* __restrict__ inst_tile, uint32_t* __restrict__ inst_rec) {
     if (st->error != kOk) return;  // capacity overflow: nothing fits, outputs undefined
     const uint32_t n = st->n_visible;
+    const uint32_t n_inst = st->n_instances;
     const int lane = threadIdx.x & 31;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t wb = warp * 32; wb < n; wb += nwarps * 32) {
         const uint32_t j = wb + lane;
-        uint32_t r = 0, x0 = 0, y0 = 0, w = 1, cnt = 0, row0 = 0, tx_n = 0;
+        uint32_t r = 0, x0 = 0, x1 = 0, y0 = 0, rows = 0, row0 = 0, tx_n = 0;
+        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
         if (j < n) {
             r = __ldg(order + j);
             const uint2 b = __ldg(rect + r);
             x0 = b.x & 0xffffu;
             y0 = b.x >> 16;
-            w = (b.y & 0xffffu) - x0 + 1;
-            cnt = w * ((b.y >> 16) - y0 + 1);
+            x1 = b.y & 0xffffu;
+            rows = (b.y >> 16) - y0 + 1;
             const CamDev& C = cams[r / (uint32_t)n_gauss];
             tx_n = (uint32_t)C.tiles_x;
             row0 = C.tile_offset;
-        }
-        uint32_t incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        const uint32_t excl = incl - cnt;
-        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-        const uint32_t base = __shfl_sync(0xffffffffu, j < n ? __ldg(offsets + j) : 0u, 0);
-        // warp-uniform trip count: every shuffle below has all 32 lanes present
-        for (uint32_t o0 = 0; o0 < total; o0 += 32) {
-            const uint32_t o = o0 + lane;
-            // largest lane s with excl_s <= o (lanes past the run search harmlessly)
-            int s = 0;
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                const uint32_t e = __shfl_sync(0xffffffffu, excl, s + step);
-                if (e <= o) s += step;
+            if (ellipse) {
+                r0 = __ldg(rec + 3 * (size_t)r);
+                r1 = __ldg(rec + 3 * (size_t)r + 1);
             }
-            const uint32_t es = __shfl_sync(0xffffffffu, excl, s);
-            const uint32_t ws = __shfl_sync(0xffffffffu, w, s);
-            const uint32_t rs = __shfl_sync(0xffffffffu, row0, s);
-            const uint32_t ys = __shfl_sync(0xffffffffu, y0, s);
+        }
+        const uint32_t rincl = warp_incl_scan(rows, lane);
+        const uint32_t rexcl = rincl - rows;
+        const uint32_t rtotal = __shfl_sync(0xffffffffu, rincl, 31);
+        const uint32_t base = __shfl_sync(0xffffffffu, j < n ? __ldg(offsets + j) : 0u, 0);
+        const uint32_t end = wb + 32 < n ? __ldg(offsets + wb + 32) : n_inst;
+        uint32_t pos = base;
+        // warp-uniform trip counts: every shuffle below has all 32 lanes present
+        for (uint32_t c0 = 0; c0 < rtotal; c0 += 32) {
+            const uint32_t ro = c0 + lane;
+            const int s = warp_search(rexcl, ro);
+            const uint32_t rs = __shfl_sync(0xffffffffu, r, s);
+            const uint32_t es = __shfl_sync(0xffffffffu, rexcl, s);
+            const int xs0 = (int)__shfl_sync(0xffffffffu, x0, s);
+            const int xs1 = (int)__shfl_sync(0xffffffffu, x1, s);
+            const uint32_t ys0 = __shfl_sync(0xffffffffu, y0, s);
             const uint32_t ns = __shfl_sync(0xffffffffu, tx_n, s);
-            const uint32_t xs = __shfl_sync(0xffffffffu, x0, s);
-            const uint32_t rr = __shfl_sync(0xffffffffu, r, s);
-            if (o < total) {
-                const uint32_t lt = o - es;
-                const uint32_t ty = lt / ws, tx = lt - ty * ws;
-                inst_tile[base + o] = (KeyT)(rs + (ys + ty) * ns + xs + tx);
-                inst_rec[base + o] = rr;
+            const uint32_t os = __shfl_sync(0xffffffffu, row0, s);
+            float4 q0, q1;
+            q0.x = __shfl_sync(0xffffffffu, r0.x, s);
+            q0.y = __shfl_sync(0xffffffffu, r0.y, s);
+            q0.z = __shfl_sync(0xffffffffu, r0.z, s);
+            q0.w = __shfl_sync(0xffffffffu, r0.w, s);
+            q1.x = __shfl_sync(0xffffffffu, r1.x, s);
+            q1.w = __shfl_sync(0xffffffffu, r1.w, s);
+            q1.y = q1.z = 0.f;
+            int lo = 0, hi = -1;
+            uint32_t ty = 0;
+            if (ro < rtotal) {
+                ty = ys0 + (ro - es);
+                if (ellipse) {
+                    const Ellipse E = make_ellipse(q0, q1);
+                    row_span(E, (int)ty, tile_w, tile_h, xs0, xs1, &lo, &hi);
+                } else {
+                    lo = xs0;
+                    hi = xs1;
+                }
+            }
+            const uint32_t cnt = hi >= lo ? (uint32_t)(hi - lo + 1) : 0u;
+            const uint32_t cincl = warp_incl_scan(cnt, lane);
+            const uint32_t cexcl = cincl - cnt;
+            const uint32_t ctotal = __shfl_sync(0xffffffffu, cincl, 31);
+            const uint32_t first = os + ty * ns + (uint32_t)lo;  // global id of the row's first kept tile
+            for (uint32_t o0 = 0; o0 < ctotal; o0 += 32) {
+                const uint32_t o = o0 + lane;
+                const int t = warp_search(cexcl, o);
+                const uint32_t et = __shfl_sync(0xffffffffu, cexcl, t);
+                const uint32_t ft = __shfl_sync(0xffffffffu, first, t);
+                const uint32_t rt = __shfl_sync(0xffffffffu, rs, t);
+                const uint32_t p = pos + o;
+                if (o < ctotal && p < end) {
+                    inst_tile[p] = (KeyT)(ft + (o - et));
+                    inst_rec[p] = rt;
+                }
+            }
+            pos += ctotal;
+        }
+        if (pos != end) {
+            // never expected: both counts come from the same row_span on the
+            // same stored floats.  Report it and keep every slot a valid
+            // (tile, record) pair so that the sort and the rasterizer stay in
+            // bounds.
+            if (lane == 0) record_error(st, kErrInternal, 7);
+            const uint32_t t0 = __shfl_sync(0xffffffffu, row0, 0), rr0 = __shfl_sync(0xffffffffu, r, 0);
+            for (uint32_t p = pos + lane; p < end; p += 32) {
+                inst_tile[p] = (KeyT)t0;
+                inst_rec[p] = rr0;
             }
         }
     }
 }
 
 template <typename KeyT>
-void launch_emit(const uint32_t* order, const uint32_t* offsets, const uint2* rect, const CamDev* cams, int n_gauss,
-                 const DeviceStatus* st, KeyT* inst_tile, uint32_t* inst_rec, int blocks, cudaStream_t s) {
-    emit_kernel<KeyT><<<blocks, 256, 0, s>>>(order, offsets, rect, cams, n_gauss, st, inst_tile, inst_rec);
+void launch_emit(const uint32_t* order, const uint32_t* offsets, const uint2* rect, const float4* rec,
+                 const CamDev* cams, int n_gauss, int tile_w, int tile_h, int ellipse, DeviceStatus* st,
+                 KeyT* inst_tile, uint32_t* inst_rec, int blocks, cudaStream_t s) {
+    emit_kernel<KeyT><<<blocks, 256, 0, s>>>(order, offsets, rect, rec, cams, n_gauss, tile_w, tile_h, ellipse, st,
+                                             inst_tile, inst_rec);
 }
 
-template void launch_emit<uint16_t>(const uint32_t*, const uint32_t*, const uint2*, const CamDev*, int,
-                                    const DeviceStatus*, uint16_t*, uint32_t*, int, cudaStream_t);
-template void launch_emit<uint32_t>(const uint32_t*, const uint32_t*, const uint2*, const CamDev*, int,
-                                    const DeviceStatus*, uint32_t*, uint32_t*, int, cudaStream_t);
+template void launch_emit<uint16_t>(const uint32_t*, const uint32_t*, const uint2*, const float4*, const CamDev*,
+                                    int, int, int, int, DeviceStatus*, uint16_t*, uint32_t*, int, cudaStream_t);
+template void launch_emit<uint32_t>(const uint32_t*, const uint32_t*, const uint2*, const float4*, const CamDev*,
+                                    int, int, int, int, DeviceStatus*, uint32_t*, uint32_t*, int, cudaStream_t);
 
 }  // namespace seele

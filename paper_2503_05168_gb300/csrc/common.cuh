@@ -20,7 +20,7 @@ namespace seele {
 constexpr float kLog2e = 1.4426950408889634f;
 
 // Device status word: the first error a kernel meets is kept.
-enum : int32_t { kOk = 0, kErrCapacity = 4, kErrTimeout = 5 };
+enum : int32_t { kOk = 0, kErrCapacity = 4, kErrTimeout = 5, kErrInternal = 7 };
 
 struct DeviceStatus {
     int32_t error;
@@ -56,6 +56,7 @@ struct FrameParams {
     int32_t sh_degree;
     int32_t tile_w, tile_h;
     int32_t opacity_filter;
+    int32_t tile_test;       // 1: ellipse tile test, 0: every tile of the rect
     int32_t use_mask;
     float alpha_min, alpha_max, t_stop;
     float dilation;
@@ -74,7 +75,7 @@ struct SceneDev {
 
 // Per-record outputs of preprocessing.
 struct ProjOut {
-    float4* rec;               // [3 * R]: (u, v, cA, cB), (cC, log2 o, e_thr, 0), (r, g, b, 0)
+    float4* rec;               // [3 * R]: (u, v, cA, cB), (cC, log2 o, e_thr, T_tile), (r, g, b, 0)
     uint2* rect;               // [R] tile box x0 | y0 << 16, x1 | y1 << 16
     uint32_t* tiles;           // [R] tiles touched (0 = culled)
     float* depth;              // [R] camera-space Z

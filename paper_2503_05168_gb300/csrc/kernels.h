@@ -46,8 +46,9 @@ int radix_sort_pairs(KeyT* keys[2], uint32_t* vals[2], const uint32_t* count_ptr
                      uint32_t* run_start = nullptr, uint32_t* run_end = nullptr);
 
 template <typename KeyT>
-void launch_emit(const uint32_t* order, const uint32_t* offsets, const uint2* rect, const CamDev* cams, int n_gauss,
-                 const DeviceStatus* st, KeyT* inst_tile, uint32_t* inst_rec, int blocks, cudaStream_t s);
+void launch_emit(const uint32_t* order, const uint32_t* offsets, const uint2* rect, const float4* rec,
+                 const CamDev* cams, int n_gauss, int tile_w, int tile_h, int ellipse, DeviceStatus* st,
+                 KeyT* inst_tile, uint32_t* inst_rec, int blocks, cudaStream_t s);
 
 struct RasterArgs {
     const uint32_t* starts;     // [n_tiles]: tile t's list is [starts[t], ends[t]) (empty if start >= end)

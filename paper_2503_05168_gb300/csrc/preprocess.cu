@@ -7,6 +7,7 @@
 // plane.  The kernel is HBM-bound: 64 B of geometry + 16..192 B of SH per
 // selected Gaussian in, 64 B of record/rect/count/depth out.
 #include "common.cuh"
+#include "tiletest.cuh"
 #include "kernels.h"
 
 namespace seele {
@@ -167,7 +168,25 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev sc, const CamD
         if (fx0 > fx1 || fy0 > fy1) break;
         const int tx0 = (int)fx0 / fp.tile_w, tx1 = (int)fx1 / fp.tile_w;
         const int ty0 = (int)fy0 / fp.tile_h, ty1 = (int)fy1 / fp.tile_h;
-        ntiles = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+
+        // raster record: exponent e = log2(o) - q log2(e) / 2 and one threshold
+        // for "inside the support and alpha >= alpha_theta" (both are e >= bound);
+        // the last slot holds the tile test's bound on -(cA dx^2 + cB dx dy + cC dy^2)
+        const float lo = log2f(o);
+        const float thr = fmaxf(fmaf(-0.5f * kLog2e, tg, lo), log2f(fp.alpha_min));
+        const float4 rec0 = make_float4(u, v, -0.5f * kLog2e * c * inv, kLog2e * b * inv);
+        const float4 rec1 = make_float4(-0.5f * kLog2e * a * inv, lo, thr,
+                                        __fmul_rn(tg, 0.5f * kLog2e * (1.f + kTileInflate)));
+        if (fp.tile_test) {
+            const Ellipse E = make_ellipse(rec0, rec1);
+            for (int ty = ty0; ty <= ty1; ++ty) {
+                int l, h;
+                if (row_span(E, ty, fp.tile_w, fp.tile_h, tx0, tx1, &l, &h)) ntiles += (uint32_t)(h - l + 1);
+            }
+            if (ntiles == 0) break;
+        } else {
+            ntiles = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+        }
 
         // colour: SH in the direction from the camera centre to the mean
         float dxw = pl.x - C.campos[0], dyw = pl.y - C.campos[1], dzw = pl.z - C.campos[2];
@@ -189,12 +208,8 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev sc, const CamD
             rgb[ch] = fmaxf(s, 0.f);
         }
 
-        // raster record: exponent e = log2(o) - q log2(e) / 2 and one threshold
-        // for "inside the support and alpha >= alpha_theta" (both are e >= bound)
-        const float lo = log2f(o);
-        const float thr = fmaxf(fmaf(-0.5f * kLog2e, tg, lo), log2f(fp.alpha_min));
-        out.rec[3 * rid + 0] = make_float4(u, v, -0.5f * kLog2e * c * inv, kLog2e * b * inv);
-        out.rec[3 * rid + 1] = make_float4(-0.5f * kLog2e * a * inv, lo, thr, 0.f);
+        out.rec[3 * rid + 0] = rec0;
+        out.rec[3 * rid + 1] = rec1;
         out.rec[3 * rid + 2] = make_float4(rgb[0], rgb[1], rgb[2], 0.f);
         out.rect[rid] = make_uint2((uint32_t)tx0 | ((uint32_t)ty0 << 16), (uint32_t)tx1 | ((uint32_t)ty1 << 16));
         out.depth[rid] = Z;

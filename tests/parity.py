@@ -66,23 +66,27 @@ def records_to_proj(rec):
     return u, v, np.stack([A, B, C], 1), o, rec[:, 8:11]
 
 
-def oracle_lists_for_tiles(proj, cam, opts: oracle.Options, tiles):
-    """Oracle tile lists restricted to ``tiles``, in the (fp32 depth, index)
-    order of Sec. 3.1, built from the oracle's own per-Gaussian rects."""
-    tx_n, ty_n = oracle.tile_grid(cam, opts)
-    vis = np.nonzero(proj["visible"])[0]
-    rect = proj["rect"][vis]
-    dbits = proj["depth32"][vis].view(np.uint32)
-    gids, ranges = [], np.zeros((tx_n * ty_n, 2), np.int64)
-    pos = 0
-    for t in sorted(int(x) for x in tiles):
+def oracle_render_tiles(proj, cam, opts: oracle.Options, tiles, nthreads: int = 8):
+    """The oracle's render of the given tiles only, for workloads too large to
+    bin whole on the CPU: the Gaussians whose rect covers a sampled tile go
+    through the oracle's own instance builder (tile test, (depth, index) sort),
+    every other tile's list is emptied, and the oracle rasterizes the rest.
+    Returns (Render, global Gaussian ids of each sampled tile's list)."""
+    tx_n, _ = oracle.tile_grid(cam, opts)
+    tiles = np.unique(np.asarray(tiles, np.int64))
+    rect = proj["rect"]
+    vis = proj["visible"] == 1
+    sel = np.zeros(proj.shape[0], bool)
+    for t in tiles:
         tx, ty = t % tx_n, t // tx_n
-        sel = (rect[:, 0] <= tx) & (tx <= rect[:, 2]) & (rect[:, 1] <= ty) & (ty <= rect[:, 3])
-        g = vis[sel]
-        order = np.lexsort((g, dbits[sel]))
-        g = g[order]
-        ranges[t] = (pos, pos + g.size)
-        gids.append(g)
-        pos += g.size
-    gid = np.concatenate(gids).astype(np.int32) if gids else np.zeros(0, np.int32)
-    return gid, ranges
+        sel |= vis & (rect[:, 0] <= tx) & (tx <= rect[:, 2]) & (rect[:, 1] <= ty) & (ty <= rect[:, 3])
+    idx = np.nonzero(sel)[0]
+    sub = np.ascontiguousarray(proj[idx])
+    _, gid, ranges = oracle.instances(sub, cam, opts)
+    keep = np.zeros(ranges.shape[0], bool)
+    keep[tiles] = True
+    ranges = ranges.copy()
+    ranges[~keep] = 0
+    ref = oracle.render_tiled(sub, gid, ranges, cam, opts, nthreads)
+    lists = {int(t): idx[gid[ranges[t, 0]:ranges[t, 1]]] for t in tiles}
+    return ref, lists

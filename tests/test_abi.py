@@ -40,6 +40,7 @@ def test_default_options_are_the_papers_constants(lib):
     lib.seele_default_options(ctypes.byref(o))
     assert abs(o.alpha_min - 1 / 255) < 1e-9 and (o.group_w, o.group_h) == (2, 2)
     assert o.mode == _abi.MODE_PLAIN and abs(o.alpha_max - 0.99) < 1e-7 and abs(o.t_stop - 1e-4) < 1e-10
+    assert o.tile_test == _abi.TILES_ELLIPSE
     assert o.n_neighbors == 3
 
 

@@ -101,20 +101,22 @@ def _clear_tiny_scene(seed, n=48, W=64, H=48):
     raise RuntimeError("no clear scene found")
 
 
+@pytest.mark.parametrize("tile_test", ["ellipse", "rect"])
 @pytest.mark.parametrize("seed", [0, 1, 2, 3])
-def test_tile_lists_bit_exact(Renderer, seed):
+def test_tile_lists_bit_exact(Renderer, seed, tile_test):
     s, cams = _clear_tiny_scene(seed)
     r = Renderer()
     r.load_scene(s)
     r.set_cameras(cams)
-    parity.gpu_render(r)
+    parity.gpu_render(r, tile_test=tile_test)
     d = parity.debug_numpy(r)
     n = s["means"].shape[0]
     exp_tile, exp_rec, exp_rng = [], [], []
     tile_off, k_off = 0, 0
+    oo = oracle.Options(tile_test=tile_test)
     for ci, c in enumerate(cams):
-        proj = oracle.preprocess(oracle.Scene64.from_scene(s), c, oracle.Options())
-        tile, gid, ranges = oracle.instances(proj, c, oracle.Options())
+        proj = oracle.preprocess(oracle.Scene64.from_scene(s), c, oo)
+        tile, gid, ranges = oracle.instances(proj, c, oo)
         exp_tile.append(tile + tile_off)
         exp_rec.append(gid + ci * n)
         rr = ranges.copy()
@@ -223,6 +225,26 @@ def test_opacity_filter_keeps_image_and_cuts_instances(Renderer):
     assert k1 < k0
     diff = np.abs(a[0] - b[0])
     assert diff.max() <= parity.RGB_MAX_ABS and (diff == 0).mean() > 0.999
+    r.close()
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (32, 8)])
+def test_ellipse_tile_test_keeps_image_and_cuts_instances(Renderer, tile):
+    """Dropping the tiles the support ellipse does not reach removes only
+    entries the rasterizer would skip, so the images are bit-identical."""
+    sc, cams = scenegen.uniform_10k()
+    cams = cams + [scenegen.look_at((0.9, -0.4, -2.5), (0, 0, 0), 200, 120)]
+    r = Renderer()
+    r.load_scene(sc)
+    r.set_cameras(cams)
+    for kw in (dict(mode="plain"), dict(mode="cr", opacity_filter=True)):
+        a, ta = parity.gpu_render(r, tile=tile, tile_test="rect", **kw)
+        k_rect = r.last_stats["n_instances"]
+        b, tb = parity.gpu_render(r, tile=tile, tile_test="ellipse", **kw)
+        k_ell = r.last_stats["n_instances"]
+        assert k_ell < 0.85 * k_rect, (k_ell, k_rect)
+        for x, y in zip(a + ta, b + tb):
+            np.testing.assert_array_equal(x, y)
     r.close()
 
 

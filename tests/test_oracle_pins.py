@@ -314,10 +314,10 @@ def _min_q_on_box(A, B, C, x0, x1, y0, y1):
 @pytest.mark.parametrize("tile", [(16, 16), (32, 8)])
 def test_ellipse_tile_test_brute_force(tile):
     """A tile of the rect is kept exactly when the inflated support ellipse
-    q <= t_g (1 + 1e-3) meets the rectangle of its pixel centres (minimum of q
-    over that box by edge minimisation, an independent construction), and so
-    every tile holding a pixel centre with q <= t_g is kept (checked on the
-    pixel grid)."""
+    q <= t_g (1 + 1e-3) meets the rectangle of its pixel centres widened by
+    1/256 px (minimum of q over that box by edge minimisation, an independent
+    construction), and so every tile holding a pixel centre with q <= t_g is
+    kept (checked on the pixel grid)."""
     s, cam = _random_scene(n=600)
     opts = oracle.Options(tile_w=tile[0], tile_h=tile[1], opacity_filter=True)
     proj = oracle.preprocess(oracle.Scene64.from_scene(s), cam, opts)
@@ -334,8 +334,9 @@ def test_ellipse_tile_test_brute_force(tile):
         x0r, y0r, x1r, y1r = P["rect"]
         for ty in range(y0r, y1r + 1):
             for tx in range(x0r, x1r + 1):
-                qmin = _min_q_on_box(A, B, C, tx * TW + 0.5 - u, tx * TW + TW - 0.5 - u,
-                                     ty * TH + 0.5 - v, ty * TH + TH - 0.5 - v)
+                e = 1.0 / 256
+                qmin = _min_q_on_box(A, B, C, tx * TW + 0.5 - e - u, tx * TW + TW - 0.5 + e - u,
+                                     ty * TH + 0.5 - e - v, ty * TH + TH - 0.5 + e - v)
                 if abs(qmin - t) < 1e-9 * t:
                     continue
                 want = qmin <= t

@@ -33,19 +33,13 @@ def Renderer():
 
 def _front_to_back_instances(d, tiles_x):
     """Instances in the order the render path emits them: visible records by
-    (fp32 depth, record id), each record's tiles row-major over its rect."""
-    vis = np.nonzero(d["tiles_touched"] > 0)[0]
-    dbits = d["depth"].view(np.uint32)[vis]
-    vis = vis[np.lexsort((vis, dbits))]
-    rect = d["rect"].view(np.uint32)[vis]
-    tiles, recs = [], []
-    for r, (lo, hi) in zip(vis, rect):
-        x0, y0, x1, y1 = lo & 0xFFFF, lo >> 16, hi & 0xFFFF, hi >> 16
-        ty, tx = np.mgrid[y0:y1 + 1, x0:x1 + 1]
-        t = (ty * tiles_x + tx).reshape(-1)
-        tiles.append(t)
-        recs.append(np.full(t.size, r))
-    return np.concatenate(tiles).astype(np.uint32), np.concatenate(recs).astype(np.uint32)
+    (fp32 depth, record id), each record's tiles in row-major order.  The
+    (tile, record) pairs are the render's own sorted lists, reordered."""
+    rec = d["inst_record"].astype(np.int64)
+    tile = d["inst_tile"].astype(np.int64)
+    dbits = d["depth"].view(np.uint32).astype(np.int64)
+    order = np.lexsort((tile, rec, dbits[rec]))
+    return tile[order].astype(np.uint32), rec[order].astype(np.uint32)
 
 
 def _call(lib, stream, tiles, recs, n_tiles):
