@@ -262,7 +262,8 @@ def _fwd_bwd(args, device):
               for k in ("means", "log_scales", "quats", "opacity_logits", "sh")}
     out = {}
     for mode in ("cr", "plain"):
-        opts = r.make_options(mode=mode, opacity_filter=(mode == "cr"))
+        # training bins by tiles: the backward walks per-tile lists
+        opts = r.make_options(mode=mode, opacity_filter=(mode == "cr"), binning="tiles")
 
         def step():
             r.load_scene(dict(params, sh_degree=3), borrow=True)
@@ -284,7 +285,7 @@ def _fwd_bwd(args, device):
         out[f"{mode}_ms"] = s.elapsed_time(e) / k
     out["workload"] = (f"clusters_1m: {args.fwd_bwd_n} Gaussians in 64 clusters, 1280x720, L1 loss vs a target "
                        f"rendered from attributes + N(0, 0.01); gradients for all attributes; CR path with the "
-                       f"opacity filter, plain path without")
+                       f"opacity filter, plain path without; tile binning")
     r.close()
     return out
 
@@ -474,6 +475,9 @@ def run_gpu(args):
     work = {k: r.last_stats[k] for k in ("leader_tests", "pairs_evaluated", "pairs_blended")}
     work_K = r.last_stats["n_instances"]
     work_vis = r.last_stats["n_visible"]
+    # (tile, Gaussian) instances of the same frame binned by tiles (untimed)
+    r.render(mode="cr", opacity_filter=True, binning="tiles")
+    K_tiles = r.last_stats["n_instances"]
 
     # quality: CR vs plain on the same frame
     img_cr = r.render(mode="cr", opacity_filter=True).cpu().numpy().astype(np.float64)
@@ -488,16 +492,24 @@ def run_gpu(args):
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     n_gauss = int(scene["means"].shape[0])
-    tile_passes = 2
+    # algorithmic bytes per stage (block binning, one 1920x1080 camera:
+    # 15 x 17 = 255 tile blocks, so the block sort is one 8-bit pass)
+    n_blocks = 15 * 17
+    block_passes = max(1, math.ceil(max(1, (n_blocks - 1).bit_length()) / 8))
     stage_bytes = {
-        "preprocess": 16 * n_gauss + 4 * n_gauss + (32 + 192 + 60) * work_vis,
-        "compact": 4 * n_gauss + 8 * work_vis,
-        "depth_sort": (4 * 16 + 4) * work_vis,
+        # position/logit of every Gaussian, count out; quat, scale, 48 SH floats in and
+        # 48 B record + 8 B rect + 4 B depth + 4 B block count out per visible one
+        "preprocess": 16 * n_gauss + 4 * n_gauss + (32 + 192 + 64) * work_vis,
+        "compact": 4 * n_gauss + 12 * work_vis,
+        "depth_sort": 4 * 20 * work_vis,
         "tile_scan": 12 * work_vis,
-        "emit": 16 * work_vis + 8 * work_K,
-        "tile_sort": (tile_passes * 16 + 4) * work_K,
+        "emit": 48 * work_vis + 10 * work_K,
+        "tile_sort": block_passes * 22 * work_K,
         "ranges": 4 * work_K,
     }
+    stage_roof = {k: {"GB_s": round(v / (stage[k] / 1000.0) / 1e9, 1),
+                      "frac": round(v / (stage[k] / 1000.0) / 1e9 / hbm, 3)}
+                  for k, v in stage_bytes.items() if stage.get(k, 0) > 0}
     if dom == "raster":
         ops = 8 * (work["pairs_evaluated"] + work["leader_tests"]) + 7 * work["pairs_blended"]
         achieved = ops / (stage[dom] / 1000.0) / 1e12
@@ -549,14 +561,16 @@ def run_gpu(args):
         "metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * t_cr_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "path": "contribution-aware (Alg. 1, 2x2 groups) + opacity-aware filter",
+        "config": {"workload": WORKLOAD, "path": "contribution-aware (Alg. 1, 2x2 groups) + opacity-aware filter; "
+                                                 "ellipse tile test; block binning (8x4-tile blocks with tile masks)",
                    "l2": "inputs larger than L2 (720 MB of Gaussian attributes per frame)",
                    "parallelism": f"replicas x{ws} (cameras sharded, no collective)"},
         "plain_fps": fps_plain, "speedup_vs_plain": fps / fps_plain, "psnr_cr_vs_plain_db": psnr,
         "stage_ms": {k: round(v, 4) for k, v in stage.items()},
         "stage_ms_plain": {k: round(v, 4) for k, v in stage_plain.items()},
-        "n_visible": n_vis, "n_instances": K, "raster_work": work,
-        "roofline": roof, "e2e": e2e, "fwd_bwd": fwd_bwd, "multiview": multiview, "ablation": ablation,
+        "n_visible": n_vis, "n_block_instances": K, "n_tile_instances": K_tiles, "raster_work": work,
+        "roofline": roof, "stage_roofline_hbm": stage_roof,
+        "e2e": e2e, "fwd_bwd": fwd_bwd, "multiview": multiview, "ablation": ablation,
         "graph_fps": fps_graph,
         "gpu_launches": int(kernels_per_frame * args.steps),
         "clocks": clock_info,

@@ -101,6 +101,17 @@ enum { SEELE_MODE_PLAIN = 0, SEELE_MODE_CR = 1 };
  * instances to sort and to rasterize. */
 enum { SEELE_TILES_RECT = 0, SEELE_TILES_ELLIPSE = 1 };
 
+/* Binning: the unit the sorted instance lists are kept per.
+ * TILES: one (tile, Gaussian) instance per tile, sorted by tile after the
+ * depth sort (Sec. 3.1).  BLOCKS: one instance per 8x4-tile block, carrying
+ * a 32-bit mask of the block's tiles that the Gaussian reaches (same tile
+ * test), sorted by block; each tile's rasterizer walks its block's list and
+ * keeps the entries with its bit -- its tile list, in the same order.  Both
+ * give the same image and per-pixel list positions; BLOCKS sorts several
+ * times fewer instances and reads only the part of each list it rasterizes.
+ * A backward pass after a BLOCKS render first re-bins the frame by tiles. */
+enum { SEELE_BIN_TILES = 0, SEELE_BIN_BLOCKS = 1 };
+
 /* Render flags */
 enum {
     SEELE_RENDER_ASYNC = 1,       /* do not synchronise; see seele_render */
@@ -141,12 +152,14 @@ typedef struct {
     float t_stop;                 /* Gamma_theta, 1e-4 */
     int32_t flags;                /* SEELE_RENDER_* */
     int32_t tile_test;            /* SEELE_TILES_ELLIPSE (default) or SEELE_TILES_RECT */
+    int32_t binning;              /* SEELE_BIN_BLOCKS (default) or SEELE_BIN_TILES */
 } seele_options;
 
 /* Per-render statistics (all cameras of the call). */
 typedef struct {
     int64_t n_visible;            /* (camera, Gaussian) pairs that reach binning */
-    int64_t n_instances;          /* tile instances K */
+    int64_t n_instances;          /* sorted instances: (tile, Gaussian) pairs K, or
+                                     (tile block, Gaussian) pairs with SEELE_BIN_BLOCKS */
     int64_t capacity;             /* instance capacity after the call */
     int32_t retries;              /* renders repeated after a capacity growth */
     int32_t n_kernels;            /* kernel launches of the last attempt */
@@ -167,7 +180,7 @@ typedef struct {
 
 /* Fills *opt with: PLAIN, 2x2 group, 16x16 tiles, filters off, M = 3,
  * alpha_theta = 1/255 (Sec. 3.1), clamp 0.99, Gamma_theta = 1e-4, flags 0,
- * ellipse tile test. */
+ * ellipse tile test, block binning. */
 void seele_default_options(seele_options* opt);
 
 /* Creates a context on CUDA device `device` that enqueues on `cuda_stream`
@@ -221,11 +234,12 @@ typedef struct {
     int64_t n_records;            /* cameras * n */
     int64_t n_visible;
     int64_t n_instances;
-    int64_t n_tiles;              /* tiles over all cameras */
+    int64_t n_tiles;              /* list units over all cameras: tiles, or tile blocks
+                                     with SEELE_BIN_BLOCKS */
     const uint32_t* inst_record;  /* [n_instances] record id = camera * n + g, grouped by
-                                     global tile, front to back within a tile */
-    const uint32_t* tile_start;   /* [n_tiles]: tile t's list is inst_record[tile_start[t] ..
-                                     tile_end[t]); a tile without instances has
+                                     global unit, front to back within a unit */
+    const uint32_t* tile_start;   /* [n_tiles]: unit t's list is inst_record[tile_start[t] ..
+                                     tile_end[t]); a unit without instances has
                                      tile_start >= tile_end */
     const uint32_t* tile_end;     /* [n_tiles] */
     const uint32_t* tiles_touched;/* [n_records] 0 = culled */
@@ -238,7 +252,10 @@ typedef struct {
                                      e = cA dx^2 + cB dx dy + cC dy^2 + log2 o
                                      >= e_thr, with alpha = min(clamp, 2^e) */
     const float* depth;           /* [n_records] camera-space Z */
-    const uint32_t* n_contrib;    /* [sum W*H] 1 + last blended list position */
+    const uint32_t* n_contrib;    /* [sum W*H] 1 + last blended position in the
+                                     pixel's tile list */
+    const uint32_t* inst_mask;    /* SEELE_BIN_BLOCKS: [n_instances] tiles of the block the
+                                     entry reaches, bit j*8 + i for tile (i, j); else NULL */
 } seele_debug_view;
 
 seele_status seele_get_debug_view(const seele_ctx* ctx, seele_debug_view* out);

@@ -161,11 +161,14 @@ class Renderer:
     @staticmethod
     def make_options(mode="plain", group=(2, 2), tile=(16, 16), opacity_filter=False, cluster_filter=False,
                      n_neighbors=3, sync=True, profile=False, count=False, graph=False, tile_test="ellipse",
-                     **kw) -> _abi.Options:
+                     binning="blocks", **kw) -> _abi.Options:
         o = default_options()
         if tile_test not in ("ellipse", "rect"):
             raise ValueError("tile_test must be 'ellipse' or 'rect'")
+        if binning not in ("blocks", "tiles"):
+            raise ValueError("binning must be 'blocks' or 'tiles'")
         o.tile_test = _abi.TILES_ELLIPSE if tile_test == "ellipse" else _abi.TILES_RECT
+        o.binning = _abi.BIN_BLOCKS if binning == "blocks" else _abi.BIN_TILES
         o.mode = _abi.MODE_CR if mode == "cr" else _abi.MODE_PLAIN
         o.group_w, o.group_h = group
         o.tile_w, o.tile_h = tile
@@ -274,6 +277,7 @@ class Renderer:
             tiles_touched=dev(v.tiles_touched, R, i32), rect=dev(v.rect, 2 * R, i32).reshape(R, 2),
             records=dev(v.records, 12 * R, torch.float32).reshape(R, 12), depth=dev(v.depth, R, torch.float32),
             n_contrib=dev(v.n_contrib, self.n_pixels, i32),
+            inst_mask=dev(v.inst_mask, K, i32) if v.inst_mask else None,
         )
 
 
@@ -315,7 +319,9 @@ def __getattr__(name):
 
 
 def render(renderer: "Renderer", means, log_scales, quats, opacity_logits, sh, sh_degree: int = 3, **options):
-    """Differentiable render of every camera of ``renderer`` (flat planar RGB)."""
+    """Differentiable render of every camera of ``renderer`` (flat planar RGB).
+    Bins by tiles unless told otherwise: the backward pass walks tile lists."""
     fn = __getattr__("SeeleRender")
+    options.setdefault("binning", "tiles")
     o = renderer.make_options(**options)
     return fn.apply(renderer, o, sh_degree, means, log_scales, quats, opacity_logits, sh)

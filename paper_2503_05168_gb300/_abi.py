@@ -16,6 +16,7 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_STATE", 3: "ERR_CUDA", 4: "ERR_CA
 SCENE_COPY, SCENE_BORROW = 0, 1
 MODE_PLAIN, MODE_CR = 0, 1
 TILES_RECT, TILES_ELLIPSE = 0, 1
+BIN_TILES, BIN_BLOCKS = 0, 1
 RENDER_ASYNC = 1
 RENDER_PROFILE = 2
 RENDER_COUNT = 4
@@ -43,7 +44,7 @@ class Options(ctypes.Structure):
                 ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("opacity_filter", ctypes.c_int32),
                 ("cluster_filter", ctypes.c_int32), ("n_neighbors", ctypes.c_int32),
                 ("alpha_min", ctypes.c_float), ("alpha_max", ctypes.c_float), ("t_stop", ctypes.c_float),
-                ("flags", ctypes.c_int32), ("tile_test", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("tile_test", ctypes.c_int32), ("binning", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -60,7 +61,8 @@ class Grads(ctypes.Structure):
 class DebugView(ctypes.Structure):
     _fields_ = [("n_records", ctypes.c_int64), ("n_visible", ctypes.c_int64), ("n_instances", ctypes.c_int64),
                 ("n_tiles", ctypes.c_int64), ("inst_record", P), ("tile_start", P), ("tile_end", P),
-                ("tiles_touched", P), ("rect", P), ("records", P), ("depth", P), ("n_contrib", P)]
+                ("tiles_touched", P), ("rect", P), ("records", P), ("depth", P), ("n_contrib", P),
+                ("inst_mask", P)]
 
 
 # name -> (restype, argtypes); the ABI test checks this table against the header

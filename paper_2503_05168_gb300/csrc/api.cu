@@ -48,8 +48,8 @@ struct seele_ctx {
     DevBuf cams_dev;
 
     // frame workspace
-    DevBuf rec, rect, tiles, depth, visk[2], visv[2], offs, instk[2], instv[2], ranges, status, hist, lookback, T,
-        nc, rgb_tmp, sortcnt, grad_rec;
+    DevBuf rec, rect, tiles, blocks, depth, visk[2], visv[2], offs, instk[2], instv[2], instm[2], ranges, msum,
+        border, status, hist, lookback, T, nc, rgb_tmp, sortcnt, grad_rec;
     size_t lookback_entries = 0;
     DeviceStatus* h_status = nullptr;  // pinned mirror of the device status
     cudaEvent_t ev[SEELE_NUM_STAGES + 1] = {};
@@ -82,6 +82,7 @@ struct seele_ctx {
     seele_options last_opt{};
     int inst_final = 0;
     uint32_t n_tiles_total = 0;
+    uint32_t n_units_total = 0;   // list units: tiles, or tile blocks with block binning
     uint64_t n_pix_total = 0;
     FrameParams last_fp{};
 };
@@ -200,37 +201,54 @@ int bits_for(uint64_t v) {
     return b;
 }
 
-// Emission, stable radix sort by tile id and tile ranges.  Returns the
-// ping-pong buffer holding the sorted record ids, or -1 on a launch error.
-template <typename KeyT>
-int enqueue_tile_sort(seele_ctx* c, const uint32_t* order, const uint2* rect, const float4* rec, const CamDev* cams,
-                      const FrameParams& fp, DeviceStatus* st, const uint32_t* n_inst, uint32_t n_tiles, int key_bits,
-                      uint64_t cap, int emit_blocks, uint64_t* lb, uint32_t* scnt, uint32_t* soff, int& launches,
-                      cudaStream_t s) {
-    KeyT* keys[2] = {ptr<KeyT>(c->instk[0]), ptr<KeyT>(c->instk[1])};
-    uint32_t* vals[2] = {ptr<uint32_t>(c->instv[0]), ptr<uint32_t>(c->instv[1])};
-    launch_emit<KeyT>(order, ptr<uint32_t>(c->offs), rect, rec, cams, (int)c->n, fp.tile_w, fp.tile_h, fp.tile_test, st,
-                      keys[0], vals[0], emit_blocks, s);
-    if (cudaPeekAtLastError() != cudaSuccess) return -1;
-    ++launches;
-    SEELE_MARK_EXT(c, SEELE_STAGE_TILE_SORT);
-    uint32_t* starts = ptr<uint32_t>(c->ranges);
-    const int fin = radix_sort_pairs<KeyT>(keys, vals, n_inst, (uint32_t)cap, key_bits, false, scnt, soff, lb,
-                                           c->epoch, st, 6, launches, s, starts, starts + n_tiles);
-    if (fin < 0) return -1;
-    SEELE_MARK_EXT(c, SEELE_STAGE_RANGES);
-    return fin;
-}
-
 struct FrameInfo {
     int ncam = 0;
-    uint64_t R = 0, tiles_total = 0, pix_total = 0, cap = 0;
-    bool short_keys = false, rgb_dev = true, T_dev = true;
-    int tile_bits = 1;
+    uint64_t R = 0, tiles_total = 0, blocks_total = 0, pix_total = 0, cap = 0;
+    uint64_t units_total = 0;  // list units: tiles, or tile blocks with block binning
+    bool blocks = false, short_keys = false, rgb_dev = true, T_dev = true;
+    int tile_bits = 1;         // key bits of a list unit id
     uint32_t cnt_words = 0;
     size_t lb_entries = 0;
     FrameParams fp{};
 };
+
+// Emission, stable radix sort by list unit and the unit ranges (from the last
+// pass).  Tile binning: (tile, record) instances sorted by tile.  Block
+// binning: (block, record, tile mask) instances sorted by block, then the
+// mask summaries and the order in which the rasterizer visits the blocks.
+// Returns the ping-pong buffer holding the sorted lists, or -1 on a launch
+// error.
+template <typename KeyT>
+int enqueue_tile_sort(seele_ctx* c, const FrameInfo& f, const uint32_t* order, const uint2* rect, const float4* rec,
+                      const CamDev* cams, DeviceStatus* st, const uint32_t* n_inst, uint64_t cap, int emit_blocks,
+                      uint64_t* lb, uint32_t* scnt, uint32_t* soff, int& launches, cudaStream_t s) {
+    const FrameParams& fp = f.fp;
+    KeyT* keys[2] = {ptr<KeyT>(c->instk[0]), ptr<KeyT>(c->instk[1])};
+    uint32_t* vals[2] = {ptr<uint32_t>(c->instv[0]), ptr<uint32_t>(c->instv[1])};
+    uint32_t* masks[2] = {ptr<uint32_t>(c->instm[0]), ptr<uint32_t>(c->instm[1])};
+    if (f.blocks)
+        launch_emit_blocks<KeyT>(order, ptr<uint32_t>(c->offs), rect, rec, cams, (int)c->n, fp.tile_w, fp.tile_h,
+                                 fp.tile_test, st, keys[0], vals[0], masks[0], emit_blocks, s);
+    else
+        launch_emit<KeyT>(order, ptr<uint32_t>(c->offs), rect, rec, cams, (int)c->n, fp.tile_w, fp.tile_h,
+                          fp.tile_test, st, keys[0], vals[0], emit_blocks, s);
+    if (cudaPeekAtLastError() != cudaSuccess) return -1;
+    ++launches;
+    SEELE_MARK_EXT(c, SEELE_STAGE_TILE_SORT);
+    uint32_t* run = ptr<uint32_t>(c->ranges);
+    const uint64_t units = f.units_total;
+    const int fin = radix_sort_pairs<KeyT>(keys, vals, n_inst, (uint32_t)cap, f.tile_bits, false, scnt, soff, lb,
+                                           c->epoch, st, 6, launches, s, run, run + units, f.blocks ? masks : nullptr);
+    if (fin < 0) return -1;
+    SEELE_MARK_EXT(c, SEELE_STAGE_RANGES);
+    if (f.blocks) {
+        launch_mask_summary(masks[fin], st, ptr<uint32_t>(c->msum), (uint32_t)(cap / 32 + 1), s);
+        launch_block_order(run, run + units, (uint32_t)units, ptr<uint32_t>(c->border), s);
+        if (cudaPeekAtLastError() != cudaSuccess) return -1;
+        launches += 2;
+    }
+    return fin;
+}
 
 bool tile_supported(int w, int h) { return (w == 16 && h == 16) || (w == 32 && h == 8) || (w == 32 && h == 16); }
 
@@ -248,14 +266,18 @@ seele_status check_options(seele_ctx* c, const seele_options* opt) {
     if (opt->n_neighbors < 0) return fail(c, SEELE_ERR_ARG, "n_neighbors must be >= 0");
     if (opt->tile_test != SEELE_TILES_RECT && opt->tile_test != SEELE_TILES_ELLIPSE)
         return fail(c, SEELE_ERR_ARG, "bad tile_test");
+    if (opt->binning != SEELE_BIN_TILES && opt->binning != SEELE_BIN_BLOCKS)
+        return fail(c, SEELE_ERR_ARG, "bad binning");
     return SEELE_OK;
 }
 
 // Camera constants for the options' tile size (host only).
-void build_cameras(seele_ctx* c, const seele_options* opt, uint64_t& tiles_total, uint64_t& pix_total) {
+void build_cameras(seele_ctx* c, const seele_options* opt, uint64_t& tiles_total, uint64_t& blocks_total,
+                   uint64_t& pix_total) {
     const int ncam = (int)c->cams.size();
     c->camdev.resize(ncam);
     tiles_total = 0;
+    blocks_total = 0;
     pix_total = 0;
     for (int i = 0; i < ncam; ++i) {
         const seele_camera& k = c->cams[i];
@@ -282,6 +304,9 @@ void build_cameras(seele_ctx* c, const seele_options* opt, uint64_t& tiles_total
         d.tile_offset = (uint32_t)tiles_total;
         d.pix_offset = (uint32_t)pix_total;
         d.sel_bits = opt->cluster_filter ? select_clusters(c, k, opt->n_neighbors) : 0xffffffffu;
+        d.blocks_x = (d.tiles_x + kBlockW - 1) / kBlockW;
+        d.block_offset = (uint32_t)blocks_total;
+        blocks_total += (uint64_t)d.blocks_x * ((d.tiles_y + kBlockH - 1) / kBlockH);
         tiles_total += (uint64_t)d.tiles_x * d.tiles_y;
         pix_total += (uint64_t)k.width * k.height;
     }
@@ -297,6 +322,7 @@ void fill_params(seele_ctx* c, const seele_options* opt, FrameInfo& f) {
     fp.tile_h = opt->tile_h;
     fp.opacity_filter = opt->opacity_filter ? 1 : 0;
     fp.tile_test = opt->tile_test == SEELE_TILES_ELLIPSE ? 1 : 0;
+    fp.binning = opt->binning == SEELE_BIN_BLOCKS ? 1 : 0;
     fp.use_mask = opt->cluster_filter ? 1 : 0;
     fp.alpha_min = opt->alpha_min;
     fp.alpha_max = opt->alpha_max;
@@ -319,9 +345,15 @@ seele_status size_frame(seele_ctx* c, FrameInfo& f) {
         SEELE_CUDA(c, ensure(c->visv[i], 4 * R));
         SEELE_CUDA(c, ensure(c->instk[i], 4 * cap));
         SEELE_CUDA(c, ensure(c->instv[i], 4 * cap));
+        if (f.blocks) SEELE_CUDA(c, ensure(c->instm[i], 4 * (cap + 32)));  // whole 32-entry groups
+    }
+    if (f.blocks) {
+        SEELE_CUDA(c, ensure(c->blocks, 4 * R));
+        SEELE_CUDA(c, ensure(c->msum, 4 * (cap / 32 + 2)));
+        SEELE_CUDA(c, ensure(c->border, 4 * f.blocks_total));
     }
     SEELE_CUDA(c, ensure(c->offs, 4 * R));
-    SEELE_CUDA(c, ensure(c->ranges, 8 * f.tiles_total));  // starts[n_tiles], then ends[n_tiles]
+    SEELE_CUDA(c, ensure(c->ranges, 8 * f.units_total));  // starts[n_units], then ends[n_units]
     SEELE_CUDA(c, ensure(c->status, sizeof(DeviceStatus)));
     SEELE_CUDA(c, ensure(c->T, 4 * f.pix_total));
     SEELE_CUDA(c, ensure(c->nc, 4 * f.pix_total));
@@ -331,7 +363,7 @@ seele_status size_frame(seele_ctx* c, FrameInfo& f) {
     SEELE_CUDA(c, ensure(c->sortcnt, 8ull * f.cnt_words));
     // look-back status words of the scans of one frame (cleared every frame)
     const uint32_t items = scan_tiles_per_launch();
-    f.lb_entries = (std::max<uint64_t>(R, f.cnt_words) + items - 1) / items + 1;
+    f.lb_entries = (std::max<uint64_t>(std::max<uint64_t>(R, f.cnt_words), f.tiles_total) + items - 1) / items + 1;
     SEELE_CUDA(c, ensure(c->lookback, 8 * f.lb_entries));
     return SEELE_OK;
 }
@@ -375,6 +407,7 @@ std::vector<uint64_t> graph_key(const seele_ctx* c, const seele_options* opt, co
     k.push_back((uint64_t)(uintptr_t)T_copy);
     k.push_back((uint64_t)(uintptr_t)c->rec.p);
     k.push_back((uint64_t)(uintptr_t)c->instk[0].p);
+    k.push_back((uint64_t)(uintptr_t)c->instm[0].p);
     return k;
 }
 
@@ -382,7 +415,7 @@ std::vector<uint64_t> graph_key(const seele_ctx* c, const seele_options* opt, co
 // read-back.  Allocates nothing and never waits, so it can be captured.
 seele_status enqueue_frame(seele_ctx* c, const seele_options* opt, const FrameInfo& f, float* rgb_target,
                            float* T_copy, bool count, int& launches, int& fin) {
-    const uint64_t R = f.R, cap = f.cap, tiles_total = f.tiles_total;
+    const uint64_t R = f.R, cap = f.cap, tiles_total = f.tiles_total, units_total = f.units_total;
     const int ncam = f.ncam;
     cudaStream_t s = c->stream;
     DeviceStatus* st = ptr<DeviceStatus>(c->status);
@@ -394,8 +427,8 @@ seele_status enqueue_frame(seele_ctx* c, const seele_options* opt, const FrameIn
     SEELE_CUDA(c, cudaMemsetAsync(st, 0, sizeof(DeviceStatus), s));
     SEELE_CUDA(c, cudaMemsetAsync(lb, 0, 8 * f.lb_entries, s));
     SEELE_CUDA(c, cudaMemsetAsync(c->viewt.p, 0, 12ull * ncam + 8, s));
-    SEELE_CUDA(c, cudaMemsetAsync(c->ranges.p, 0xff, 4 * tiles_total, s));
-    SEELE_CUDA(c, cudaMemsetAsync(ptr<uint32_t>(c->ranges) + tiles_total, 0, 4 * tiles_total, s));
+    SEELE_CUDA(c, cudaMemsetAsync(c->ranges.p, 0xff, 4 * units_total, s));
+    SEELE_CUDA(c, cudaMemsetAsync(ptr<uint32_t>(c->ranges) + units_total, 0, 4 * units_total, s));
     SEELE_MARK(SEELE_STAGE_PREPROCESS);
     if (c->scene_flags == SEELE_SCENE_BORROW) {
         const seele_scene_desc& b = c->borrowed;
@@ -415,7 +448,8 @@ seele_status enqueue_frame(seele_ctx* c, const seele_options* opt, const FrameIn
                                                                   : ptr<const uint32_t>(c->mask))
                           : nullptr;
     unsigned long long* vt = ptr<unsigned long long>(c->viewt);
-    ProjOut po{ptr<float4>(c->rec), ptr<uint2>(c->rect), ptr<uint32_t>(c->tiles), ptr<float>(c->depth), vt};
+    ProjOut po{ptr<float4>(c->rec), ptr<uint2>(c->rect), ptr<uint32_t>(c->tiles),
+               f.blocks ? ptr<uint32_t>(c->blocks) : nullptr, ptr<float>(c->depth), vt};
     const CamDev* cams = ptr<const CamDev>(c->cams_dev);
     launch_preprocess(sc, cams, f.fp, po, s);
     SEELE_LAUNCHED(c);
@@ -442,25 +476,29 @@ seele_status enqueue_frame(seele_ctx* c, const seele_options* opt, const FrameIn
     // sorted ids are back in buffer 0 after an even number of passes
     const uint32_t* order = ptr<uint32_t>(c->visv[0]);
     SEELE_MARK(SEELE_STAGE_TILE_SCAN);
-    launch_scan_tiles(po.tiles, order, (uint32_t)R, ptr<uint32_t>(c->offs), lb, c->epoch++, st, 1,
-                      (uint32_t)std::min<uint64_t>(cap, 0xffffffffu), s);
+    launch_scan_tiles(f.blocks ? po.blocks : po.tiles, order, (uint32_t)R, ptr<uint32_t>(c->offs), lb, c->epoch++,
+                      st, 1, (uint32_t)std::min<uint64_t>(cap, 0xffffffffu), s);
     SEELE_LAUNCHED(c);
     ++launches;
     const int emit_blocks = (int)std::max<uint64_t>(std::min<uint64_t>((R + 255) / 256, 8 * 152), 1);
     SEELE_MARK(SEELE_STAGE_EMIT);
     const uint32_t* n_inst = &st->n_inst_valid;
     if (f.short_keys)
-        fin = enqueue_tile_sort<uint16_t>(c, order, po.rect, po.rec, cams, f.fp, st, n_inst, (uint32_t)tiles_total, f.tile_bits, cap,
-                                          emit_blocks, lb, scnt, soff, launches, s);
+        fin = enqueue_tile_sort<uint16_t>(c, f, order, po.rect, po.rec, cams, st, n_inst, cap, emit_blocks, lb, scnt,
+                                          soff, launches, s);
     else
-        fin = enqueue_tile_sort<uint32_t>(c, order, po.rect, po.rec, cams, f.fp, st, n_inst, (uint32_t)tiles_total, f.tile_bits, cap,
-                                          emit_blocks, lb, scnt, soff, launches, s);
+        fin = enqueue_tile_sort<uint32_t>(c, f, order, po.rect, po.rec, cams, st, n_inst, cap, emit_blocks, lb, scnt,
+                                          soff, launches, s);
     if (fin < 0) return fail(c, SEELE_ERR_CUDA, "tile sort launch failed: %s", cudaGetErrorString(cudaGetLastError()));
 
     RasterArgs ra;
     ra.starts = ptr<uint32_t>(c->ranges);
-    ra.ends = ptr<uint32_t>(c->ranges) + tiles_total;
+    ra.ends = ptr<uint32_t>(c->ranges) + units_total;
     ra.inst_rec = ptr<uint32_t>(c->instv[fin]);
+    ra.inst_mask = f.blocks ? ptr<uint32_t>(c->instm[fin]) : nullptr;
+    ra.mask_summary = f.blocks ? ptr<uint32_t>(c->msum) : nullptr;
+    ra.block_order = f.blocks ? ptr<uint32_t>(c->border) : nullptr;
+    ra.n_blocks = (uint32_t)f.blocks_total;
     ra.rec = ptr<float4>(c->rec);
     ra.cams = cams;
     ra.n_cams = ncam;
@@ -505,6 +543,7 @@ void seele_default_options(seele_options* o) {
     o->t_stop = 1e-4f;
     o->flags = 0;
     o->tile_test = SEELE_TILES_ELLIPSE;
+    o->binning = SEELE_BIN_BLOCKS;
 }
 
 seele_status seele_create(seele_ctx** out, int device, void* cuda_stream) {
@@ -694,11 +733,13 @@ seele_status seele_render(seele_ctx* c, const seele_options* opt, float* out_rgb
     f.ncam = (int)c->cams.size();
     f.R = (uint64_t)c->n * f.ncam;
     if (f.R >= (1ull << 31)) return fail(c, SEELE_ERR_ARG, "cameras x Gaussians must be < 2^31");
-    build_cameras(c, opt, f.tiles_total, f.pix_total);
+    build_cameras(c, opt, f.tiles_total, f.blocks_total, f.pix_total);
     if (f.tiles_total >= (1ull << 31) || f.pix_total >= (1ull << 31))
         return fail(c, SEELE_ERR_ARG, "too many tiles or pixels in one render");
-    f.short_keys = f.tiles_total <= kShortKeyMaxTiles;
-    f.tile_bits = std::max(1, bits_for(f.tiles_total > 0 ? f.tiles_total - 1 : 0));
+    f.blocks = opt->binning == SEELE_BIN_BLOCKS;
+    f.units_total = f.blocks ? f.blocks_total : f.tiles_total;
+    f.short_keys = f.units_total <= kShortKeyMaxTiles;
+    f.tile_bits = std::max(1, bits_for(f.units_total > 0 ? f.units_total - 1 : 0));
     fill_params(c, opt, f);
     if (profile && !c->ev[0])
         for (cudaEvent_t& e : c->ev) SEELE_CUDA(c, cudaEventCreate(&e));
@@ -759,6 +800,7 @@ seele_status seele_render(seele_ctx* c, const seele_options* opt, float* out_rgb
         }
         c->inst_final = fin;
         c->n_tiles_total = (uint32_t)f.tiles_total;
+        c->n_units_total = (uint32_t)f.units_total;
         c->n_pix_total = f.pix_total;
         c->last_opt = *opt;
         c->last_fp = f.fp;
@@ -885,6 +927,16 @@ seele_status seele_render_backward(seele_ctx* c, const float* dL_drgb, const see
     const void* dev_ptrs[] = {dL_drgb, g->means, g->log_scales, g->quats, g->opacity_logits, g->sh};
     for (const void* p : dev_ptrs)
         if (!is_device_ptr(p)) return fail(c, SEELE_ERR_ARG, "backward buffers must be device memory");
+    if (c->last_opt.binning == SEELE_BIN_BLOCKS) {
+        // the backward walks per-tile lists: bin the same frame by tiles
+        // (same image, same per-pixel list positions) and continue from it
+        seele_options o = c->last_opt;
+        o.binning = SEELE_BIN_TILES;
+        o.flags = 0;
+        SEELE_CUDA(c, ensure(c->rgb_tmp, 12 * c->n_pix_total));
+        const seele_status r = seele_render(c, &o, ptr<float>(c->rgb_tmp), nullptr, nullptr);
+        if (r != SEELE_OK) return r;
+    }
     const int ncam = (int)c->cams.size();
     const uint64_t R = (uint64_t)c->n * ncam;
     SEELE_CUDA(c, ensure(c->grad_rec, 48 * R));
@@ -928,10 +980,12 @@ seele_status seele_get_debug_view(const seele_ctx* c, seele_debug_view* out) {
     out->n_records = (int64_t)c->n * (int64_t)c->cams.size();
     out->n_visible = c->h_status->n_visible;
     out->n_instances = c->h_status->n_inst_valid;
-    out->n_tiles = c->n_tiles_total;
+    const bool blk = c->last_opt.binning == SEELE_BIN_BLOCKS;
+    out->n_tiles = c->n_units_total;
     out->inst_record = ptr<const uint32_t>(m->instv[c->inst_final]);
     out->tile_start = ptr<const uint32_t>(m->ranges);
-    out->tile_end = ptr<const uint32_t>(m->ranges) + c->n_tiles_total;
+    out->tile_end = ptr<const uint32_t>(m->ranges) + c->n_units_total;
+    out->inst_mask = blk ? ptr<const uint32_t>(m->instm[c->inst_final]) : nullptr;
     out->tiles_touched = ptr<const uint32_t>(m->tiles);
     out->rect = ptr<const uint32_t>(m->rect);
     out->records = ptr<const float>(m->rec);

@@ -1,6 +1,8 @@
 // binning.cu -- tile instances (Sec. 3.1: "the preprocessing stage ...
 // identifies the intersection between Gaussians and rendering tiles") and
 // per-tile ranges into the sorted instance list.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "tiletest.cuh"
@@ -141,6 +143,202 @@ __global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ 
     }
 }
 
+// Block binning: the same walk over depth-ordered records, but the units
+// are (record, block row) pairs -- a block row being kBlockH tile rows -- and
+// each output is one tile block with the 32-bit mask of its tiles that the
+// record's tile-row spans cover.  The count per pair is the number of blocks
+// spanned by the union of its rows' spans, exactly as preprocessing counted.
+template <typename KeyT>
+__global__ void __launch_bounds__(256) emit_blocks_kernel(const uint32_t* __restrict__ order,
+                                                          const uint32_t* __restrict__ offsets,
+                                                          const uint2* __restrict__ rect,
+                                                          const float4* __restrict__ rec,
+                                                          const CamDev* __restrict__ cams, int n_gauss, int tile_w,
+                                                          int tile_h, int ellipse, DeviceStatus* st,
+                                                          KeyT* __restrict__ inst_block,
+                                                          uint32_t* __restrict__ inst_rec,
+                                                          uint32_t* __restrict__ inst_mask) {
+    if (st->error != kOk) return;
+    const uint32_t n = st->n_visible;
+    const uint32_t n_inst = st->n_instances;
+    const int lane = threadIdx.x & 31;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t wb = warp * 32; wb < n; wb += nwarps * 32) {
+        const uint32_t j = wb + lane;
+        uint32_t r = 0, x0 = 0, x1 = 0, y0 = 0, y1 = 0, prs = 0, boff = 0, bx_n = 0;
+        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
+        if (j < n) {
+            r = __ldg(order + j);
+            const uint2 b = __ldg(rect + r);
+            x0 = b.x & 0xffffu;
+            y0 = b.x >> 16;
+            x1 = b.y & 0xffffu;
+            y1 = b.y >> 16;
+            prs = y1 / kBlockH - y0 / kBlockH + 1;
+            const CamDev& C = cams[r / (uint32_t)n_gauss];
+            boff = C.block_offset;
+            bx_n = (uint32_t)C.blocks_x;
+            if (ellipse) {
+                r0 = __ldg(rec + 3 * (size_t)r);
+                r1 = __ldg(rec + 3 * (size_t)r + 1);
+            }
+        }
+        const uint32_t pincl = warp_incl_scan(prs, lane);
+        const uint32_t pexcl = pincl - prs;
+        const uint32_t ptotal = __shfl_sync(0xffffffffu, pincl, 31);
+        const uint32_t base = __shfl_sync(0xffffffffu, j < n ? __ldg(offsets + j) : 0u, 0);
+        const uint32_t end = wb + 32 < n ? __ldg(offsets + wb + 32) : n_inst;
+        uint32_t pos = base;
+        for (uint32_t c0 = 0; c0 < ptotal; c0 += 32) {
+            const uint32_t po = c0 + lane;
+            const int s = warp_search(pexcl, po);
+            const uint32_t rs = __shfl_sync(0xffffffffu, r, s);
+            const uint32_t es = __shfl_sync(0xffffffffu, pexcl, s);
+            const int xs0 = (int)__shfl_sync(0xffffffffu, x0, s);
+            const int xs1 = (int)__shfl_sync(0xffffffffu, x1, s);
+            const int ys0 = (int)__shfl_sync(0xffffffffu, y0, s);
+            const int ys1 = (int)__shfl_sync(0xffffffffu, y1, s);
+            const uint32_t os = __shfl_sync(0xffffffffu, boff, s);
+            const uint32_t ns = __shfl_sync(0xffffffffu, bx_n, s);
+            float4 q0, q1;
+            q0.x = __shfl_sync(0xffffffffu, r0.x, s);
+            q0.y = __shfl_sync(0xffffffffu, r0.y, s);
+            q0.z = __shfl_sync(0xffffffffu, r0.z, s);
+            q0.w = __shfl_sync(0xffffffffu, r0.w, s);
+            q1.x = __shfl_sync(0xffffffffu, r1.x, s);
+            q1.w = __shfl_sync(0xffffffffu, r1.w, s);
+            q1.y = q1.z = 0.f;
+            // the pair's (up to kBlockH) tile-row spans, packed lo | hi << 16;
+            // an empty row is lo = 0xffff > hi = 0
+            uint32_t span[kBlockH];
+            int blo = 1 << 30, bhi = -1;
+            uint32_t by = 0;
+#pragma unroll
+            for (int q = 0; q < kBlockH; ++q) span[q] = 0x0000ffffu;
+            if (po < ptotal) {
+                by = (uint32_t)(ys0 / kBlockH) + (po - es);
+                const Ellipse E = make_ellipse(q0, q1);
+#pragma unroll
+                for (int q = 0; q < kBlockH; ++q) {
+                    const int ty = (int)by * kBlockH + q;
+                    if (ty < ys0 || ty > ys1) continue;
+                    int l = xs0, h = xs1;
+                    const bool any = ellipse ? row_span(E, ty, tile_w, tile_h, xs0, xs1, &l, &h) : true;
+                    if (!any) continue;
+                    span[q] = (uint32_t)l | ((uint32_t)h << 16);
+                    blo = min(blo, l);
+                    bhi = max(bhi, h);
+                }
+            }
+            const uint32_t cnt = bhi >= blo ? (uint32_t)(bhi / kBlockW - blo / kBlockW + 1) : 0u;
+            const uint32_t cincl = warp_incl_scan(cnt, lane);
+            const uint32_t cexcl = cincl - cnt;
+            const uint32_t ctotal = __shfl_sync(0xffffffffu, cincl, 31);
+            const uint32_t first_bx = bhi >= blo ? (uint32_t)(blo / kBlockW) : 0u;
+            const uint32_t row_base = os + by * ns;  // global id of block (0, by) of the camera
+            for (uint32_t o0 = 0; o0 < ctotal; o0 += 32) {
+                const uint32_t o = o0 + lane;
+                const int t = warp_search(cexcl, o);
+                const uint32_t et = __shfl_sync(0xffffffffu, cexcl, t);
+                const uint32_t fb = __shfl_sync(0xffffffffu, first_bx, t);
+                const uint32_t rb = __shfl_sync(0xffffffffu, row_base, t);
+                const uint32_t rt = __shfl_sync(0xffffffffu, rs, t);
+                uint32_t sp[kBlockH];
+#pragma unroll
+                for (int q = 0; q < kBlockH; ++q) sp[q] = __shfl_sync(0xffffffffu, span[q], t);
+                const uint32_t p = pos + o;
+                if (o < ctotal && p < end) {
+                    const int bx = (int)(fb + (o - et));
+                    const int c0x = bx * kBlockW, c1x = c0x + kBlockW - 1;
+                    uint32_t mask = 0;
+#pragma unroll
+                    for (int q = 0; q < kBlockH; ++q) {
+                        const int a = max((int)(sp[q] & 0xffffu), c0x), b = min((int)(sp[q] >> 16), c1x);
+                        if (a <= b) mask |= ((0xffu >> (kBlockW - 1 - (b - a))) << (a - c0x)) << (kBlockW * q);
+                    }
+                    inst_block[p] = (KeyT)(rb + (uint32_t)bx);
+                    inst_rec[p] = rt;
+                    inst_mask[p] = mask;
+                }
+            }
+            pos += ctotal;
+        }
+        if (pos != end) {
+            if (lane == 0) record_error(st, kErrInternal, 8);
+            const uint32_t b0 = __shfl_sync(0xffffffffu, boff, 0), rr0 = __shfl_sync(0xffffffffu, r, 0);
+            for (uint32_t p = pos + lane; p < end; p += 32) {
+                inst_block[p] = (KeyT)b0;
+                inst_rec[p] = rr0;
+                inst_mask[p] = 0u;
+            }
+        }
+    }
+}
+
+// After the block sort: the OR of the tile masks of every 32 consecutive
+// entries (aligned to the list array), so a tile's rasterizer can skip 32
+// entries of its block list with one load when none of them reaches it.
+__global__ void mask_summary_kernel(const uint32_t* __restrict__ mask, const DeviceStatus* __restrict__ st,
+                                    uint32_t* __restrict__ summary, uint32_t max_groups) {
+    const uint32_t n = st->error == kOk ? st->n_inst_valid : 0u;
+    const uint32_t groups = (n + 31) / 32;
+    const int lane = threadIdx.x & 31;
+    for (uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < groups && g < max_groups;
+         g += (gridDim.x * blockDim.x) >> 5) {
+        const uint32_t j = 32 * g + lane;
+        const uint32_t m = j < n ? __ldg(mask + j) : 0u;
+        const uint32_t o = __reduce_or_sync(0xffffffffu, m);
+        if (lane == 0) summary[g] = o;
+    }
+}
+
+void launch_mask_summary(const uint32_t* mask, const DeviceStatus* st, uint32_t* summary, uint32_t max_groups,
+                         cudaStream_t s) {
+    const uint32_t blocks = std::max<uint32_t>(1u, std::min<uint32_t>((max_groups + 7) / 8, 152u * 16u));
+    mask_summary_kernel<<<blocks, 256, 0, s>>>(mask, st, summary, max_groups);
+}
+
+// Longest lists first: the raster grid walks tile blocks in decreasing order
+// of their list length (a counting sort on a log-scale bucket of the length,
+// one CTA), so the longest-running tiles start early and no straggler is
+// left for the end of the kernel.  Order within a bucket is free.
+constexpr int kOrderBuckets = 64;
+
+__global__ void __launch_bounds__(1024) block_order_kernel(const uint32_t* __restrict__ bstart,
+                                                           const uint32_t* __restrict__ bend, uint32_t n_blocks,
+                                                           uint32_t* __restrict__ order) {
+    __shared__ uint32_t s_hist[kOrderBuckets];
+    __shared__ uint32_t s_pos[kOrderBuckets];
+    auto bucket = [&](uint32_t b) -> int {
+        const uint32_t s = __ldg(bstart + b), e = __ldg(bend + b);
+        const uint32_t len = s < e ? e - s : 0u;
+        // 4 buckets per octave, longest lists in bucket 0
+        const uint32_t v = len + 1u;
+        const int lg = 31 - __clz(v);
+        const int frac = lg >= 2 ? (int)((v >> (lg - 2)) & 3u) : (int)((v << (2 - lg)) & 3u);
+        return kOrderBuckets - 1 - min(kOrderBuckets - 1, lg * 4 + frac);
+    };
+    for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x) s_hist[i] = 0;
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b < n_blocks; b += blockDim.x) atomicAdd(&s_hist[bucket(b)], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int i = 0; i < kOrderBuckets; ++i) {
+            s_pos[i] = run;
+            run += s_hist[i];
+        }
+    }
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b < n_blocks; b += blockDim.x) order[atomicAdd(&s_pos[bucket(b)], 1u)] = b;
+}
+
+void launch_block_order(const uint32_t* bstart, const uint32_t* bend, uint32_t n_blocks, uint32_t* order,
+                        cudaStream_t s) {
+    block_order_kernel<<<1, 1024, 0, s>>>(bstart, bend, n_blocks, order);
+}
+
 template <typename KeyT>
 void launch_emit(const uint32_t* order, const uint32_t* offsets, const uint2* rect, const float4* rec,
                  const CamDev* cams, int n_gauss, int tile_w, int tile_h, int ellipse, DeviceStatus* st,
@@ -149,6 +347,20 @@ void launch_emit(const uint32_t* order, const uint32_t* offsets, const uint2* re
                                              inst_tile, inst_rec);
 }
 
+template <typename KeyT>
+void launch_emit_blocks(const uint32_t* order, const uint32_t* offsets, const uint2* rect, const float4* rec,
+                        const CamDev* cams, int n_gauss, int tile_w, int tile_h, int ellipse, DeviceStatus* st,
+                        KeyT* inst_block, uint32_t* inst_rec, uint32_t* inst_mask, int blocks, cudaStream_t s) {
+    emit_blocks_kernel<KeyT><<<blocks, 256, 0, s>>>(order, offsets, rect, rec, cams, n_gauss, tile_w, tile_h, ellipse,
+                                                    st, inst_block, inst_rec, inst_mask);
+}
+
+template void launch_emit_blocks<uint16_t>(const uint32_t*, const uint32_t*, const uint2*, const float4*,
+                                           const CamDev*, int, int, int, int, DeviceStatus*, uint16_t*, uint32_t*,
+                                           uint32_t*, int, cudaStream_t);
+template void launch_emit_blocks<uint32_t>(const uint32_t*, const uint32_t*, const uint2*, const float4*,
+                                           const CamDev*, int, int, int, int, DeviceStatus*, uint32_t*, uint32_t*,
+                                           uint32_t*, int, cudaStream_t);
 template void launch_emit<uint16_t>(const uint32_t*, const uint32_t*, const uint2*, const float4*, const CamDev*,
                                     int, int, int, int, DeviceStatus*, uint16_t*, uint32_t*, int, cudaStream_t);
 template void launch_emit<uint32_t>(const uint32_t*, const uint32_t*, const uint2*, const float4*, const CamDev*,

@@ -29,7 +29,7 @@ struct DeviceStatus {
     uint32_t capacity;       // instance capacity the scan compared K against
     uint32_t n_inst_valid;   // K if it fits the capacity, else 0 (what the tile sort reads)
     uint32_t timeout_site;   // which wait gave up (diagnostics)
-    uint32_t pad[2];
+    uint32_t pad[3];
     uint32_t ticket[16];     // dynamic block tickets of the look-back kernels
     unsigned long long work[4];  // rasterizer work counters (counting variant only)
 };
@@ -47,8 +47,17 @@ struct CamDev {
     uint32_t tile_offset;    // first global tile id of this camera
     uint32_t pix_offset;     // sum of W*H of the previous cameras
     uint32_t sel_bits;       // selected view clusters
-    uint32_t pad;
+    uint32_t block_offset;   // first global tile-block id of this camera (block binning)
+    int32_t blocks_x;        // tile blocks per row: ceil(tiles_x / kBlockW)
+    int32_t pad[3];
 };
+
+// Block binning: a tile block is kBlockW x kBlockH tiles; its instances carry a
+// 32-bit mask of the block's tiles that the Gaussian reaches (bit j * kBlockW + i
+// for tile (i, j) of the block).
+constexpr int kBlockW = 8;
+constexpr int kBlockH = 4;
+static_assert(kBlockW * kBlockH == 32, "one mask word per block instance");
 
 struct FrameParams {
     int32_t n;               // Gaussians
@@ -57,6 +66,7 @@ struct FrameParams {
     int32_t tile_w, tile_h;
     int32_t opacity_filter;
     int32_t tile_test;       // 1: ellipse tile test, 0: every tile of the rect
+    int32_t binning;         // 0: tile instances, 1: tile-block instances with tile masks
     int32_t use_mask;
     float alpha_min, alpha_max, t_stop;
     float dilation;
@@ -78,6 +88,7 @@ struct ProjOut {
     float4* rec;               // [3 * R]: (u, v, cA, cB), (cC, log2 o, e_thr, T_tile), (r, g, b, 0)
     uint2* rect;               // [R] tile box x0 | y0 << 16, x1 | y1 << 16
     uint32_t* tiles;           // [R] tiles touched (0 = culled)
+    uint32_t* blocks;          // [R] tile-block instances (block binning only, else unused)
     float* depth;              // [R] camera-space Z
     unsigned long long* t_frame;  // receives the frame's start time (%globaltimer, ns)
 };

@@ -38,22 +38,41 @@ uint32_t radix_count_words(uint32_t max_n);
 // digits; returns the index of the buffer pair holding the result, or -1 on a
 // launch error.  With run_start / run_end (cleared to all-ones / zero, one
 // word per key value) the last pass also records [first, last + 1) of every
-// key value present -- the per-tile ranges.
+// key value present -- the per-tile ranges.  With aux (two buffers, like vals)
+// a second 32-bit payload is permuted with the values.
 template <typename KeyT>
 int radix_sort_pairs(KeyT* keys[2], uint32_t* vals[2], const uint32_t* count_ptr, uint32_t max_n, int key_bits,
                      bool keys_after_last, uint32_t* counts, uint32_t* offsets, uint64_t* lookback,
                      uint32_t& epoch, DeviceStatus* st, int ticket, int& launches, cudaStream_t s,
-                     uint32_t* run_start = nullptr, uint32_t* run_end = nullptr);
+                     uint32_t* run_start = nullptr, uint32_t* run_end = nullptr, uint32_t* const* aux = nullptr);
 
 template <typename KeyT>
 void launch_emit(const uint32_t* order, const uint32_t* offsets, const uint2* rect, const float4* rec,
                  const CamDev* cams, int n_gauss, int tile_w, int tile_h, int ellipse, DeviceStatus* st,
                  KeyT* inst_tile, uint32_t* inst_rec, int blocks, cudaStream_t s);
 
+template <typename KeyT>
+void launch_emit_blocks(const uint32_t* order, const uint32_t* offsets, const uint2* rect, const float4* rec,
+                        const CamDev* cams, int n_gauss, int tile_w, int tile_h, int ellipse, DeviceStatus* st,
+                        KeyT* inst_block, uint32_t* inst_rec, uint32_t* inst_mask, int blocks, cudaStream_t s);
+
+// Block binning: OR of the tile masks of every 32 list entries, and the
+// order in which the rasterizer visits tile blocks (longest lists first).
+void launch_mask_summary(const uint32_t* mask, const DeviceStatus* st, uint32_t* summary, uint32_t max_groups,
+                         cudaStream_t s);
+void launch_block_order(const uint32_t* bstart, const uint32_t* bend, uint32_t n_blocks, uint32_t* order,
+                        cudaStream_t s);
+
 struct RasterArgs {
-    const uint32_t* starts;     // [n_tiles]: tile t's list is [starts[t], ends[t]) (empty if start >= end)
-    const uint32_t* ends;
+    const uint32_t* starts;     // [n_units]: unit u's list is [starts[u], ends[u]) (empty if start >= end);
+    const uint32_t* ends;       //   units are tiles, or tile blocks with block binning
     const uint32_t* inst_rec;
+    // block binning (else nullptr): per entry the tiles of its block it reaches,
+    // per 32 entries the OR of those masks, and the block visiting order
+    const uint32_t* inst_mask;
+    const uint32_t* mask_summary;
+    const uint32_t* block_order;
+    uint32_t n_blocks;
     const float4* rec;
     const CamDev* cams;
     int n_cams;

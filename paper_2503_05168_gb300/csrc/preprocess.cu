@@ -177,16 +177,33 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev sc, const CamD
         const float4 rec0 = make_float4(u, v, -0.5f * kLog2e * c * inv, kLog2e * b * inv);
         const float4 rec1 = make_float4(-0.5f * kLog2e * a * inv, lo, thr,
                                         __fmul_rn(tg, 0.5f * kLog2e * (1.f + kTileInflate)));
+        // tiles touched, and for block binning the tile-block instances: per
+        // block row, the blocks spanned by the union of its tile rows' spans
+        uint32_t nblocks = 0;
         if (fp.tile_test) {
             const Ellipse E = make_ellipse(rec0, rec1);
+            int cur = ty0 / kBlockH, blo = 1 << 30, bhi = -1;
             for (int ty = ty0; ty <= ty1; ++ty) {
+                if (ty / kBlockH != cur) {
+                    if (bhi >= blo) nblocks += (uint32_t)(bhi / kBlockW - blo / kBlockW + 1);
+                    cur = ty / kBlockH;
+                    blo = 1 << 30;
+                    bhi = -1;
+                }
                 int l, h;
-                if (row_span(E, ty, fp.tile_w, fp.tile_h, tx0, tx1, &l, &h)) ntiles += (uint32_t)(h - l + 1);
+                if (row_span(E, ty, fp.tile_w, fp.tile_h, tx0, tx1, &l, &h)) {
+                    ntiles += (uint32_t)(h - l + 1);
+                    blo = min(blo, l);
+                    bhi = max(bhi, h);
+                }
             }
+            if (bhi >= blo) nblocks += (uint32_t)(bhi / kBlockW - blo / kBlockW + 1);
             if (ntiles == 0) break;
         } else {
             ntiles = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+            nblocks = (uint32_t)((tx1 / kBlockW - tx0 / kBlockW + 1) * (ty1 / kBlockH - ty0 / kBlockH + 1));
         }
+        if (fp.binning) out.blocks[rid] = nblocks;
 
         // colour: SH in the direction from the camera centre to the mean
         float dxw = pl.x - C.campos[0], dyw = pl.y - C.campos[1], dzw = pl.z - C.campos[2];

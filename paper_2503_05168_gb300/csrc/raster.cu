@@ -23,10 +23,16 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
-template <int TW, int TH, int PW, int PH, int GW, int GH, bool CR, bool COUNT>
+// BLOCKS (block binning): CTA i rasterizes tile i % 32 of the tile block
+// block_order[i / 32].  Its list is the block's list filtered by the tile's
+// mask bit: a window of 32 * NT entries at a time, one 32-entry group per
+// thread, skipped with one load when the group's OR-summary lacks the bit.
+// The kept entries, in list order, are exactly the tile's own list.
+template <int TW, int TH, int PW, int PH, int GW, int GH, bool CR, bool COUNT, bool BLOCKS>
 __global__ void __launch_bounds__((TW / PW) * (TH / PH))
     raster_fwd_kernel(const uint32_t* __restrict__ starts, const uint32_t* __restrict__ ends,
-                      const uint32_t* __restrict__ inst_rec,
+                      const uint32_t* __restrict__ inst_rec, const uint32_t* __restrict__ inst_mask,
+                      const uint32_t* __restrict__ mask_summary, const uint32_t* __restrict__ block_order,
                       const float4* __restrict__ rec, const CamDev* __restrict__ cams, int n_cams, FrameParams fp,
                       float* __restrict__ out_rgb, float* __restrict__ out_T, uint32_t* __restrict__ out_nc,
                       DeviceStatus* __restrict__ counters, unsigned long long* __restrict__ view_end,
@@ -34,18 +40,43 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
     constexpr int NT = (TW / PW) * (TH / PH);
     constexpr int NP = PW * PH;
     constexpr int TXN = TW / PW;
+    constexpr int WIN = BLOCKS ? 32 * NT : 1;  // list entries filtered per window
     static_assert(PW % GW == 0 && PH % GH == 0, "groups must tile the thread block");
+    static_assert(NT % 32 == 0 && kBlockW * kBlockH == 32, "whole warps; one mask word per block entry");
     __shared__ float4 s0[NT], s1[NT], s2[NT];
+    __shared__ uint32_t s_idx[WIN];          // block binning: list indices of the window's tile entries
+    __shared__ uint32_t s_wsum[NT / 32];
 
-    const uint32_t gtile = blockIdx.x;
-    int lo = 0, hi = n_cams - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (cams[mid].tile_offset <= gtile) lo = mid; else hi = mid - 1;
+    uint32_t gtile, unit, bit = 0;
+    int lo = 0, tx, ty;
+    if (BLOCKS) {
+        const uint32_t b = __ldg(block_order + (blockIdx.x >> 5));
+        bit = blockIdx.x & 31u;
+        int hi = n_cams - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (cams[mid].block_offset <= b) lo = mid; else hi = mid - 1;
+        }
+        const CamDev& Cb = cams[lo];
+        const uint32_t lb = b - Cb.block_offset;
+        tx = (int)(lb % (uint32_t)Cb.blocks_x) * kBlockW + (int)(bit % kBlockW);
+        ty = (int)(lb / (uint32_t)Cb.blocks_x) * kBlockH + (int)(bit / kBlockW);
+        if (tx >= Cb.tiles_x || ty >= Cb.tiles_y) return;  // padding tile of a partial block
+        gtile = Cb.tile_offset + (uint32_t)(ty * Cb.tiles_x + tx);
+        unit = b;
+    } else {
+        gtile = blockIdx.x;
+        int hi = n_cams - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (cams[mid].tile_offset <= gtile) lo = mid; else hi = mid - 1;
+        }
+        const uint32_t lt = gtile - cams[lo].tile_offset;
+        tx = (int)(lt % (uint32_t)cams[lo].tiles_x);
+        ty = (int)(lt / (uint32_t)cams[lo].tiles_x);
+        unit = gtile;
     }
     const CamDev& C = cams[lo];
-    const uint32_t lt = gtile - C.tile_offset;
-    const int tx = (int)(lt % (uint32_t)C.tiles_x), ty = (int)(lt / (uint32_t)C.tiles_x);
     const int t = threadIdx.x;
     const int bx = tx * TW + (t % TXN) * PW, by = ty * TH + (t / TXN) * PH;
 
@@ -59,23 +90,88 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
         nc[p] = 0;
         if (bx + p % PW < C.W && by + p / PW < C.H) live |= 1u << p;
     }
-    uint2 rg = make_uint2(__ldg(starts + gtile), __ldg(ends + gtile));
-    if (rg.x >= rg.y) rg = make_uint2(0u, 0u);  // tile without instances
+    uint2 rg = make_uint2(__ldg(starts + unit), __ldg(ends + unit));
+    if (rg.x >= rg.y) rg = make_uint2(0u, 0u);  // no instances
     const float fx0 = (float)bx + 0.5f, fy0 = (float)by + 0.5f;
     const float amax = fp.alpha_max, tstop = fp.t_stop;
     uint32_t n_lead = 0, n_eval = 0, n_blend = 0;  // counting variant only
 
-    for (uint32_t base = rg.x; base < rg.y; base += NT) {
+    uint32_t cursor = BLOCKS ? rg.x >> 5 : rg.x;  // next list entry (tiles) or 32-entry group (blocks)
+    const uint32_t cursor_end = BLOCKS ? (rg.y + 31u) >> 5 : rg.y;
+    uint32_t pos0 = 0;           // tile-list position of staged entry 0
+    int n_idx = 0, idx_pos = 0;  // block binning: window entries kept / staged
+    while (true) {
         if (__syncthreads_and(live == 0u)) break;
-        const uint32_t j = base + t;
-        if (j < rg.y) {
-            const uint32_t r = __ldg(inst_rec + j);
-            s0[t] = __ldg(rec + 3 * (size_t)r);
-            s1[t] = __ldg(rec + 3 * (size_t)r + 1);
-            s2[t] = __ldg(rec + 3 * (size_t)r + 2);
+        int cnt;
+        if (!BLOCKS) {
+            if (cursor >= cursor_end) break;
+            const uint32_t j = cursor + t;
+            if (j < rg.y) {
+                const uint32_t r = __ldg(inst_rec + j);
+                s0[t] = __ldg(rec + 3 * (size_t)r);
+                s1[t] = __ldg(rec + 3 * (size_t)r + 1);
+                s2[t] = __ldg(rec + 3 * (size_t)r + 2);
+            }
+            cnt = (int)min((uint32_t)NT, rg.y - cursor);
+            cursor += NT;
+            __syncthreads();
+        } else {
+            if (idx_pos == n_idx) {
+                if (cursor >= cursor_end) break;
+                // thread t filters group cursor + t; group order is list order
+                const uint32_t g = cursor + (uint32_t)t;
+                uint32_t hits = 0;
+                if (g < cursor_end && ((__ldg(mask_summary + g) >> bit) & 1u)) {
+                    const uint4* mg = reinterpret_cast<const uint4*>(inst_mask + 32 * (size_t)g);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const uint4 v = __ldg(mg + q);
+                        hits |= (((v.x >> bit) & 1u) | (((v.y >> bit) & 1u) << 1) | (((v.z >> bit) & 1u) << 2) |
+                                 (((v.w >> bit) & 1u) << 3)) << (4 * q);
+                    }
+                    // entries of neighbouring lists share the edge groups
+                    const uint32_t e0 = 32 * g;
+                    if (e0 < rg.x) hits &= 0xffffffffu << (rg.x - e0);
+                    if (e0 + 32 > rg.y) hits &= 0xffffffffu >> (e0 + 32 - rg.y);
+                }
+                const uint32_t c = __popc(hits);
+                uint32_t incl = c;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if ((t & 31) >= o) incl += y;
+                }
+                if ((t & 31) == 31) s_wsum[t >> 5] = incl;
+                __syncthreads();
+                uint32_t off = incl - c, total = 0;
+#pragma unroll
+                for (int ww = 0; ww < NT / 32; ++ww) {
+                    const uint32_t v = s_wsum[ww];
+                    off += ww < (t >> 5) ? v : 0u;
+                    total += v;
+                }
+                while (hits) {
+                    const int q = __ffs(hits) - 1;
+                    hits &= hits - 1u;
+                    s_idx[off++] = 32 * g + (uint32_t)q;
+                }
+                n_idx = (int)total;
+                idx_pos = 0;
+                cursor += NT;
+                __syncthreads();
+                if (n_idx == 0) continue;
+            }
+            cnt = min(NT, n_idx - idx_pos);
+            if (t < cnt) {
+                const uint32_t r = __ldg(inst_rec + s_idx[idx_pos + t]);
+                s0[t] = __ldg(rec + 3 * (size_t)r);
+                s1[t] = __ldg(rec + 3 * (size_t)r + 1);
+                s2[t] = __ldg(rec + 3 * (size_t)r + 2);
+            }
+            idx_pos += cnt;
+            __syncthreads();
         }
-        __syncthreads();
-        const int cnt = min((uint32_t)NT, rg.y - base);
+        do {
         if (CR && GW == PW && GH == PH) {
             // Alg. 1 with one group per thread.  Phase 1: the leader (pixel 0)
             // tests every staged Gaussian -- independent of the blending state,
@@ -101,7 +197,7 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
                 const float4 B = s1[k];
                 const float4 Cc = s2[k];
                 const float dx = fx0 - A.x, dy = fy0 - A.y;
-                const uint32_t pos1 = base + (uint32_t)k - rg.x + 1u;
+                const uint32_t pos1 = pos0 + (uint32_t)k + 1u;
 #pragma unroll
                 for (int jj = 0; jj < PH; ++jj) {
                     const float ddy = dy + (float)jj;
@@ -138,7 +234,7 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
             const float4 A = s0[k];
             const float4 B = s1[k];
             const float dx = fx0 - A.x, dy = fy0 - A.y;
-            const uint32_t pos1 = base + (uint32_t)k - rg.x + 1u;
+            const uint32_t pos1 = pos0 + (uint32_t)k + 1u;
             // exponent of alpha = 2^e at pixel offset (i, j) of this thread
             auto expo = [&](int i, int jj) {
                 const float ddx = dx + (float)i, ddy = dy + (float)jj;
@@ -193,6 +289,8 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
                     if (live >> p & 1u) blend(p, expo(p % PW, p / PW));
             }
         }
+        } while (0);
+        pos0 += (uint32_t)cnt;
     }
 
     if (COUNT) {
@@ -222,17 +320,25 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
     }
 }
 
+template <int TW, int TH, int PW, int PH, int GW, int GH, bool CR, bool COUNT, bool BLOCKS>
+static void launch_variant(const RasterArgs& a, cudaStream_t s) {
+    constexpr int NT = (TW / PW) * (TH / PH);
+    const uint32_t grid = BLOCKS ? 32 * a.n_blocks : a.n_tiles;
+    raster_fwd_kernel<TW, TH, PW, PH, GW, GH, CR, COUNT, BLOCKS><<<grid, NT, 0, s>>>(
+        a.starts, a.ends, a.inst_rec, a.inst_mask, a.mask_summary, a.block_order, a.rec, a.cams, a.n_cams, a.fp,
+        a.out_rgb, a.out_T, a.out_nc, COUNT ? a.count_into : nullptr, a.view_end, a.view_done);
+}
+
 template <int TW, int TH, int PW, int PH, int GW, int GH, bool CR>
 static void launch_one(const RasterArgs& a, cudaStream_t s) {
-    constexpr int NT = (TW / PW) * (TH / PH);
-    if (a.count_into)
-        raster_fwd_kernel<TW, TH, PW, PH, GW, GH, CR, true><<<a.n_tiles, NT, 0, s>>>(
-            a.starts, a.ends, a.inst_rec, a.rec, a.cams, a.n_cams, a.fp, a.out_rgb, a.out_T, a.out_nc, a.count_into,
-            a.view_end, a.view_done);
-    else
-        raster_fwd_kernel<TW, TH, PW, PH, GW, GH, CR, false><<<a.n_tiles, NT, 0, s>>>(
-            a.starts, a.ends, a.inst_rec, a.rec, a.cams, a.n_cams, a.fp, a.out_rgb, a.out_T, a.out_nc, nullptr,
-            a.view_end, a.view_done);
+    const bool blocks = a.inst_mask != nullptr;
+    if (a.count_into) {
+        if (blocks) launch_variant<TW, TH, PW, PH, GW, GH, CR, true, true>(a, s);
+        else launch_variant<TW, TH, PW, PH, GW, GH, CR, true, false>(a, s);
+    } else {
+        if (blocks) launch_variant<TW, TH, PW, PH, GW, GH, CR, false, true>(a, s);
+        else launch_variant<TW, TH, PW, PH, GW, GH, CR, false, false>(a, s);
+    }
 }
 
 template <int TW, int TH>

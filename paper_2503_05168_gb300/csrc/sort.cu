@@ -66,7 +66,9 @@ __global__ void __launch_bounds__(kSortThreads) upsweep_kernel(const KeyT* __res
     counts[(size_t)d * stride + tile] = total;
 }
 
-template <typename KeyT, bool WRITE_KEYS>
+// AUX: a second 32-bit payload travels with each pair; it is staged through
+// the same shared buffer as the values after they have been written.
+template <typename KeyT, bool WRITE_KEYS, bool AUX>
 __global__ void __launch_bounds__(kSortThreads) downsweep_kernel(const KeyT* __restrict__ keys_in,
                                                                  const uint32_t* __restrict__ vals_in,
                                                                  KeyT* __restrict__ keys_out,
@@ -74,7 +76,9 @@ __global__ void __launch_bounds__(kSortThreads) downsweep_kernel(const KeyT* __r
                                                                  const uint32_t* __restrict__ count_ptr, int shift,
                                                                  int nbits, const uint32_t* __restrict__ offsets,
                                                                  uint32_t stride, uint32_t* __restrict__ run_start,
-                                                                 uint32_t* __restrict__ run_end) {
+                                                                 uint32_t* __restrict__ run_end,
+                                                                 const uint32_t* __restrict__ aux_in,
+                                                                 uint32_t* __restrict__ aux_out) {
     __shared__ KeyT s_keys[kSortTile];
     __shared__ uint32_t s_vals[kSortTile];
     __shared__ uint32_t s_wcount[kWarps][kRadix + 1];  // per-warp digit counters, then exclusive prefixes
@@ -96,13 +100,14 @@ __global__ void __launch_bounds__(kSortThreads) downsweep_kernel(const KeyT* __r
 
     // load warp-striped: item k of lane l is element wbase + 32 k + l, so the
     // order (k, lane) is the input order and ranking in that order is stable
-    uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+    uint32_t key[kSortItems], val[kSortItems], rank[kSortItems], aux[AUX ? kSortItems : 1];
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
         const uint32_t i = wbase + 32 * k + lane;
         const bool ok = i < n;
         key[k] = ok ? (uint32_t)__ldg(keys_in + i) : 0xffffffffu;
         val[k] = ok ? __ldg(vals_in + i) : 0u;
+        if (AUX) aux[AUX ? k : 0] = ok ? __ldg(aux_in + i) : 0u;
     }
     // lanes holding the same digit: one ballot per significant digit bit plus
     // one for validity (elements past n form their own group)
@@ -174,6 +179,22 @@ __global__ void __launch_bounds__(kSortThreads) downsweep_kernel(const KeyT* __r
             }
         }
     }
+    if (AUX) {
+        __syncthreads();  // every value has been read out of s_vals
+#pragma unroll
+        for (int k = 0; k < kSortItems; ++k) {
+            if (key[k] != 0xffffffffu) {
+                const uint32_t dg = (key[k] >> shift) & 0xffu;
+                s_vals[s_local_base[dg] + s_wcount[w][dg] + rank[k]] = aux[AUX ? k : 0];
+            }
+        }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < tile_n; i += kSortThreads) {
+            const uint32_t dg = ((uint32_t)s_keys[i] >> shift) & 0xffu;
+            const uint32_t o = s_global_base[dg] + (i - s_local_base[dg]);
+            if (o < n) aux_out[o] = s_vals[i];
+        }
+    }
 }
 
 uint32_t sort_tile_items() { return kSortTile; }
@@ -189,22 +210,33 @@ void launch_radix_downsweep_u32(const uint32_t* keys_in, const uint32_t* vals_in
                                 const uint32_t* offsets, uint32_t stride, uint32_t* run_start, uint32_t* run_end,
                                 cudaStream_t s) {
     if (keys_out)
-        downsweep_kernel<uint32_t, true><<<stride, kSortThreads, 0, s>>>(
-            keys_in, vals_in, keys_out, vals_out, count_ptr, shift, nbits, offsets, stride, run_start, run_end);
+        downsweep_kernel<uint32_t, true, false><<<stride, kSortThreads, 0, s>>>(
+            keys_in, vals_in, keys_out, vals_out, count_ptr, shift, nbits, offsets, stride, run_start, run_end,
+            nullptr, nullptr);
     else
-        downsweep_kernel<uint32_t, false><<<stride, kSortThreads, 0, s>>>(
-            keys_in, vals_in, keys_out, vals_out, count_ptr, shift, nbits, offsets, stride, run_start, run_end);
+        downsweep_kernel<uint32_t, false, false><<<stride, kSortThreads, 0, s>>>(
+            keys_in, vals_in, keys_out, vals_out, count_ptr, shift, nbits, offsets, stride, run_start, run_end,
+            nullptr, nullptr);
 }
 
 uint32_t radix_count_words(uint32_t max_n) {
     return kRadix * std::max<uint32_t>((max_n + kSortTile - 1) / kSortTile, 1u);
 }
 
+template <typename KeyT, bool WK, bool AUX>
+static void launch_downsweep(KeyT* keys[2], uint32_t* vals[2], uint32_t* const* aux, int a, int b,
+                             const uint32_t* count_ptr, int shift, int nbits, const uint32_t* offsets, uint32_t stride,
+                             uint32_t* rs, uint32_t* re, cudaStream_t s) {
+    downsweep_kernel<KeyT, WK, AUX><<<stride, kSortThreads, 0, s>>>(
+        keys[a], vals[a], keys[b], vals[b], count_ptr, shift, nbits, offsets, stride, rs, re,
+        AUX ? aux[a] : nullptr, AUX ? aux[b] : nullptr);
+}
+
 template <typename KeyT>
 int radix_sort_pairs(KeyT* keys[2], uint32_t* vals[2], const uint32_t* count_ptr, uint32_t max_n, int key_bits,
                      bool keys_after_last, uint32_t* counts, uint32_t* offsets, uint64_t* lookback,
                      uint32_t& epoch, DeviceStatus* st, int ticket, int& launches, cudaStream_t s,
-                     uint32_t* run_start, uint32_t* run_end) {
+                     uint32_t* run_start, uint32_t* run_end, uint32_t* const* aux) {
     const uint32_t stride = std::max<uint32_t>((max_n + kSortTile - 1) / kSortTile, 1u);
     const int passes = std::max(1, (key_bits + 7) / 8);
     for (int p = 0; p < passes; ++p) {
@@ -215,12 +247,18 @@ int radix_sort_pairs(KeyT* keys[2], uint32_t* vals[2], const uint32_t* count_ptr
         uint32_t* re = last ? run_end : nullptr;
         upsweep_kernel<KeyT><<<stride, kSortThreads, 0, s>>>(keys[a], count_ptr, 8 * p, counts, stride);
         launch_exclusive_scan(counts, kRadix * stride, offsets, lookback, epoch++, st, ticket + p, s);
-        if (!last || keys_after_last)
-            downsweep_kernel<KeyT, true><<<stride, kSortThreads, 0, s>>>(
-                keys[a], vals[a], keys[b], vals[b], count_ptr, 8 * p, nbits, offsets, stride, rs, re);
-        else
-            downsweep_kernel<KeyT, false><<<stride, kSortThreads, 0, s>>>(
-                keys[a], vals[a], keys[b], vals[b], count_ptr, 8 * p, nbits, offsets, stride, rs, re);
+        const bool wk = !last || keys_after_last;
+        if (aux) {
+            if (wk) launch_downsweep<KeyT, true, true>(keys, vals, aux, a, b, count_ptr, 8 * p, nbits, offsets, stride,
+                                                        rs, re, s);
+            else launch_downsweep<KeyT, false, true>(keys, vals, aux, a, b, count_ptr, 8 * p, nbits, offsets, stride,
+                                                      rs, re, s);
+        } else {
+            if (wk) launch_downsweep<KeyT, true, false>(keys, vals, aux, a, b, count_ptr, 8 * p, nbits, offsets,
+                                                         stride, rs, re, s);
+            else launch_downsweep<KeyT, false, false>(keys, vals, aux, a, b, count_ptr, 8 * p, nbits, offsets,
+                                                       stride, rs, re, s);
+        }
         if (cudaPeekAtLastError() != cudaSuccess) return -1;
         launches += 3;
     }
@@ -228,9 +266,9 @@ int radix_sort_pairs(KeyT* keys[2], uint32_t* vals[2], const uint32_t* count_ptr
 }
 template int radix_sort_pairs<uint32_t>(uint32_t* [2], uint32_t* [2], const uint32_t*, uint32_t, int, bool,
                                         uint32_t*, uint32_t*, uint64_t*, uint32_t&, DeviceStatus*, int, int&,
-                                        cudaStream_t, uint32_t*, uint32_t*);
+                                        cudaStream_t, uint32_t*, uint32_t*, uint32_t* const*);
 template int radix_sort_pairs<uint16_t>(uint16_t* [2], uint32_t* [2], const uint32_t*, uint32_t, int, bool,
                                         uint32_t*, uint32_t*, uint64_t*, uint32_t&, DeviceStatus*, int, int&,
-                                        cudaStream_t, uint32_t*, uint32_t*);
+                                        cudaStream_t, uint32_t*, uint32_t*, uint32_t* const*);
 
 }  // namespace seele

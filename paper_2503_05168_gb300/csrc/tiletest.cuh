@@ -25,12 +25,27 @@ namespace seele {
 constexpr float kTileInflate = 1e-3f;
 constexpr float kTileSlack = 1.f / 256.f;
 
+// Hardware approximations (about one ulp); the slack above covers their error,
+// and both kernels issue the same instructions on the same inputs.
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 struct Ellipse {
     float u, v;        // centre (px)
     float a, b, c;     // Q = a dx^2 + 2 b dx dy + c dy^2
     float det;         // a c - b^2
+    float inv_a;       // 1 / a
     float xr, yr;      // half extents of Q <= T along x and y
-    float T;           // support bound on Q
+    float k;           // the rightmost point is at dy = -k, the leftmost at +k
 };
 
 __device__ __forceinline__ Ellipse make_ellipse(float4 r0, float4 r1) {
@@ -40,14 +55,17 @@ __device__ __forceinline__ Ellipse make_ellipse(float4 r0, float4 r1) {
     E.a = -r0.z;
     E.b = __fmul_rn(-0.5f, r0.w);
     E.c = -r1.x;
-    E.T = r1.w;
+    const float T = r1.w;
     // Kahan's a c - b^2 with one rounding error
     const float w = __fmul_rn(E.b, E.b);
     const float e = __fmaf_rn(-E.b, E.b, w);
     const float f = __fmaf_rn(E.a, E.c, -w);
     E.det = __fadd_rn(f, e);
-    E.xr = __fsqrt_rn(__fdiv_rn(__fmul_rn(E.T, E.c), E.det));
-    E.yr = __fsqrt_rn(__fdiv_rn(__fmul_rn(E.T, E.a), E.det));
+    E.inv_a = rcp_approx(E.a);
+    const float inv_det = rcp_approx(E.det);
+    E.xr = sqrt_approx(__fmul_rn(__fmul_rn(T, E.c), inv_det));
+    E.yr = sqrt_approx(__fmul_rn(__fmul_rn(T, E.a), inv_det));
+    E.k = __fmul_rn(__fmul_rn(E.b, E.xr), rcp_approx(E.c));
     return E;
 }
 
@@ -56,13 +74,14 @@ __device__ __forceinline__ Ellipse make_ellipse(float4 r0, float4 r1) {
 // without the cancellation of the expanded form.
 __device__ __forceinline__ float boundary_x(const Ellipse& E, float dy, float side) {
     const float s = __fmul_rn(E.det, __fmul_rn(__fsub_rn(E.yr, dy), __fadd_rn(E.yr, dy)));
-    const float root = __fsqrt_rn(fmaxf(s, 0.f));
-    return __fdiv_rn(__fmaf_rn(side, root, __fmul_rn(-E.b, dy)), E.a);
+    const float root = sqrt_approx(fmaxf(s, 0.f));
+    return __fmul_rn(__fmaf_rn(side, root, __fmul_rn(-E.b, dy)), E.inv_a);
 }
 
 // Tiles [*lo, *hi] of tile row ty within the rect columns [rx0, rx1]; false
 // when the row holds none.  A conic whose FP32 determinant is not positive (a
 // needle so thin that rounding swamps a c - b^2) keeps the whole rect row.
+// Tile sizes are powers of two, so multiplying by 1 / TW is exact.
 __device__ __forceinline__ bool row_span(const Ellipse& E, int ty, int TW, int TH, int rx0, int rx1, int* lo,
                                          int* hi) {
     if (!(E.det > 0.f && E.a > 0.f && E.c > 0.f)) {
@@ -70,17 +89,16 @@ __device__ __forceinline__ bool row_span(const Ellipse& E, int ty, int TW, int T
         *hi = rx1;
         return true;
     }
-    const float y0 = (float)(ty * TH), x_w = (float)TW;
+    const float y0 = (float)(ty * TH), x_w = (float)TW, inv_w = 1.f / (float)TW;
     const float ya = __fsub_rn(__fadd_rn(y0, 0.5f - kTileSlack), E.v);
     const float yb = __fsub_rn(__fadd_rn(y0, (float)TH - 0.5f + kTileSlack), E.v);
     const float blo = fmaxf(ya, -E.yr), bhi = fminf(yb, E.yr);
     if (blo > bhi) return false;
-    const float k = __fdiv_rn(__fmul_rn(E.b, E.xr), E.c);
-    const float dr = fminf(fmaxf(-k, blo), bhi), dl = fminf(fmaxf(k, blo), bhi);
+    const float dr = fminf(fmaxf(-E.k, blo), bhi), dl = fminf(fmaxf(E.k, blo), bhi);
     const float xR = __fadd_rn(E.u, boundary_x(E, dr, 1.f));
     const float xL = __fadd_rn(E.u, boundary_x(E, dl, -1.f));
-    const float fr = __fdiv_rn(__fadd_rn(xR, kTileSlack - 0.5f), x_w);
-    const float fl = __fdiv_rn(__fsub_rn(xL, x_w - 0.5f + kTileSlack), x_w);
+    const float fr = __fmul_rn(__fadd_rn(xR, kTileSlack - 0.5f), inv_w);
+    const float fl = __fmul_rn(__fsub_rn(xL, x_w - 0.5f + kTileSlack), inv_w);
     const int a = max(rx0, (int)ceilf(fmaxf(fl, -1.f)));
     const int b = min(rx1, (int)floorf(fminf(fr, 65536.f)));
     *lo = a;

@@ -86,11 +86,11 @@ def _is_clear(s, cam, n):
     return np.min(np.diff(d)) > 4
 
 
-def _clear_tiny_scene(seed, n=48, W=64, H=48):
+def _clear_tiny_scene(seed, n=48, W=64, H=48, f=50.0):
     """Random tiny scene and two cameras with every rect, cull and depth-order
     decision far from a rounding flip (re-drawn until so)."""
     rs = np.random.default_rng(seed)
-    cam = camera(f=50.0, width=W, height=H)
+    cam = camera(f=f, width=W, height=H)
     cam2 = dict(cam, world_to_cam=np.concatenate([np.eye(3), [[0.3], [0.1], [0.5]]], 1))
     for _ in range(500):
         means = rs.uniform(-1, 1, (n, 3)) * [1.0, 0.7, 1.0] + [0, 0, 4]
@@ -102,13 +102,16 @@ def _clear_tiny_scene(seed, n=48, W=64, H=48):
 
 
 @pytest.mark.parametrize("tile_test", ["ellipse", "rect"])
-@pytest.mark.parametrize("seed", [0, 1, 2, 3])
-def test_tile_lists_bit_exact(Renderer, seed, tile_test):
-    s, cams = _clear_tiny_scene(seed)
+@pytest.mark.parametrize("seed,size", [(0, (64, 48, 50.0)), (1, (64, 48, 50.0)), (2, (200, 120, 160.0)),
+                                       (3, (200, 120, 160.0))])
+def test_tile_lists_bit_exact(Renderer, seed, size, tile_test):
+    """Tile lists, their order and ranges equal the oracle's, bit for bit."""
+    W, H, f = size
+    s, cams = _clear_tiny_scene(seed, W=W, H=H, f=f)
     r = Renderer()
     r.load_scene(s)
     r.set_cameras(cams)
-    parity.gpu_render(r, tile_test=tile_test)
+    parity.gpu_render(r, tile_test=tile_test, binning="tiles")
     d = parity.debug_numpy(r)
     n = s["means"].shape[0]
     exp_tile, exp_rec, exp_rng = [], [], []
@@ -136,13 +139,66 @@ def test_tile_lists_bit_exact(Renderer, seed, tile_test):
     r.close()
 
 
+@pytest.mark.parametrize("seed", [2, 3])
+def test_block_lists_filtered_per_tile_are_the_tile_lists(Renderer, seed):
+    """Block binning: walking a tile's block list and keeping the entries whose
+    mask has the tile's bit gives exactly the oracle's tile list, in order
+    (the 200x120 frames span several 8x4-tile blocks each way)."""
+    s, cams = _clear_tiny_scene(seed, W=200, H=120, f=160.0)
+    r = Renderer()
+    r.load_scene(s)
+    r.set_cameras(cams)
+    parity.gpu_render(r, binning="blocks")
+    d = parity.debug_numpy(r)
+    n = s["means"].shape[0]
+    rng = d["tile_ranges"].astype(np.int64)
+    mask = d["inst_mask"].view(np.uint32)
+    blk_off = 0
+    for ci, c in enumerate(cams):
+        tx_n, ty_n = oracle.tile_grid(c, oracle.Options())
+        bx_n, by_n = -(-tx_n // 8), -(-ty_n // 4)
+        proj = oracle.preprocess(oracle.Scene64.from_scene(s), c, oracle.Options())
+        _, gid, ranges = oracle.instances(proj, c, oracle.Options())
+        for t in range(tx_n * ty_n):
+            tx, ty = t % tx_n, t // tx_n
+            b = blk_off + (ty // 4) * bx_n + tx // 8
+            bit = (ty % 4) * 8 + tx % 8
+            sel = slice(rng[b, 0], rng[b, 1])
+            keep = (mask[sel] >> bit) & 1 == 1
+            got = d["inst_record"][sel][keep].astype(np.int64)
+            np.testing.assert_array_equal(got, gid[ranges[t, 0]:ranges[t, 1]] + ci * n, err_msg=f"{ci} {t}")
+        blk_off += bx_n * by_n
+    assert blk_off == d["n_tiles"]
+    r.close()
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (32, 8), (32, 16)])
+def test_block_binning_renders_bit_identical_to_tile_binning(Renderer, tile):
+    sc, _ = scenegen.uniform_10k()
+    cams = [scenegen.look_at((0.5 * i, -0.2, -2.6), (0, 0, 0), w, h) for i, (w, h) in
+            enumerate([(256, 256), (100, 70), (33, 17), (517, 301)])]
+    r = Renderer()
+    r.load_scene(sc)
+    r.set_cameras(cams)
+    for kw in (dict(mode="plain"), dict(mode="cr"), dict(mode="cr", opacity_filter=True),
+               dict(mode="cr", group=(2, 4)), dict(mode="cr", group=(1, 1)), dict(mode="plain", tile_test="rect")):
+        a, ta = parity.gpu_render(r, tile=tile, binning="tiles", **kw)
+        nca = parity.debug_numpy(r)["n_contrib"]
+        b, tb = parity.gpu_render(r, tile=tile, binning="blocks", **kw)
+        ncb = parity.debug_numpy(r)["n_contrib"]
+        for x, y in zip(a + ta, b + tb):
+            np.testing.assert_array_equal(x, y, err_msg=str(kw))
+        np.testing.assert_array_equal(nca, ncb, err_msg=str(kw))
+    r.close()
+
+
 def test_tile_lists_at_scale_up_to_ambiguous_cases(Renderer):
     sc, cams = scenegen.uniform_10k()
     cam = cams[0]
     r = Renderer()
     r.load_scene(sc)
     r.set_cameras(cams)
-    parity.gpu_render(r)
+    parity.gpu_render(r, binning="tiles")
     d = parity.debug_numpy(r)
     proj = oracle.preprocess(oracle.Scene64.from_scene(sc), cam, oracle.Options())
     tile, gid, ranges = oracle.instances(proj, cam, oracle.Options())
@@ -218,9 +274,9 @@ def test_opacity_filter_keeps_image_and_cuts_instances(Renderer):
     r = Renderer()
     r.load_scene(sc)
     r.set_cameras(cams)
-    a, _ = parity.gpu_render(r, mode="plain")
+    a, _ = parity.gpu_render(r, mode="plain", binning="tiles")
     k0 = r.last_stats["n_instances"]
-    b, _ = parity.gpu_render(r, mode="plain", opacity_filter=True)
+    b, _ = parity.gpu_render(r, mode="plain", opacity_filter=True, binning="tiles")
     k1 = r.last_stats["n_instances"]
     assert k1 < k0
     diff = np.abs(a[0] - b[0])
@@ -238,9 +294,9 @@ def test_ellipse_tile_test_keeps_image_and_cuts_instances(Renderer, tile):
     r.load_scene(sc)
     r.set_cameras(cams)
     for kw in (dict(mode="plain"), dict(mode="cr", opacity_filter=True)):
-        a, ta = parity.gpu_render(r, tile=tile, tile_test="rect", **kw)
+        a, ta = parity.gpu_render(r, tile=tile, tile_test="rect", binning="tiles", **kw)
         k_rect = r.last_stats["n_instances"]
-        b, tb = parity.gpu_render(r, tile=tile, tile_test="ellipse", **kw)
+        b, tb = parity.gpu_render(r, tile=tile, tile_test="ellipse", binning="tiles", **kw)
         k_ell = r.last_stats["n_instances"]
         assert k_ell < 0.85 * k_rect, (k_ell, k_rect)
         for x, y in zip(a + ta, b + tb):
@@ -313,7 +369,7 @@ def test_capacity_growth_is_transparent(Renderer):
     r = Renderer()
     r.load_scene(s)
     r.set_cameras([cam])
-    imgs, _ = parity.gpu_render(r)
+    imgs, _ = parity.gpu_render(r, binning="tiles")
     assert r.last_stats["retries"] == 1 and r.last_stats["n_instances"] > (1 << 20)
     ref = oracle.render(oracle.Scene64.from_scene(s), cam, oracle.Options(), nthreads=8)[0]
     ok, rep = parity.compare_images(imgs[0], ref.rgb, ref.margin)

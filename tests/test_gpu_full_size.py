@@ -1,6 +1,8 @@
 """Parity at the benchmark's full size: 3M Gaussians (unbounded_3m) at
 1920x1080, in the launch configuration the benchmark times (asynchronous
-CR + opacity-aware filtering, 16x16 tiles, ellipse tile test).
+CR + opacity-aware filtering, 16x16 tiles, ellipse tile test, block
+binning), checked bit-identical to the same frame binned by tiles, whose
+tile lists are then compared.
 
 The oracle preprocesses every Gaussian, so per-Gaussian visibility and tile
 counts are compared for all 3M; binning and blending, too slow to run whole
@@ -46,6 +48,9 @@ def test_full_size_matches_oracle_on_sampled_tiles(Renderer, workload, view):
     r.render(out=out, mode="cr", opacity_filter=True, sync=False)
     r.synchronize()
     img = r.images(out)[0].cpu().numpy()
+    # the same frame binned by tiles: identical image, and the tile lists
+    img_t = r.images(r.render(mode="cr", opacity_filter=True, binning="tiles"))[0].cpu().numpy()
+    np.testing.assert_array_equal(img, img_t)
     d = parity.debug_numpy(r)
 
     opts = parity.oracle_options("cr", opacity_filter=True)

@@ -65,7 +65,7 @@ def test_noalloc_sort_matches_the_render_path_twice(Renderer, width, height):
     r = Renderer()
     r.load_scene(sc)
     r.set_cameras(cams)
-    r.render(mode="cr", opacity_filter=True)
+    r.render(mode="cr", opacity_filter=True, binning="tiles")
     torch.cuda.synchronize()
     d = {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in r.debug_view().items()}
     tiles_x = (width + 15) // 16
