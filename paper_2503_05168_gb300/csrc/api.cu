@@ -49,7 +49,7 @@ struct seele_ctx {
 
     // frame workspace
     DevBuf rec, rect, tiles, blocks, depth, visk[2], visv[2], offs, instk[2], instv[2], instm[2], ranges, msum,
-        border, status, hist, lookback, T, nc, rgb_tmp, sortcnt, grad_rec;
+        border, chunkv, chunks, status, hist, lookback, T, nc, rgb_tmp, sortcnt, grad_rec;
     size_t lookback_entries = 0;
     DeviceStatus* h_status = nullptr;  // pinned mirror of the device status
     cudaEvent_t ev[SEELE_NUM_STAGES + 1] = {};
@@ -353,6 +353,8 @@ seele_status size_frame(seele_ctx* c, FrameInfo& f) {
         SEELE_CUDA(c, ensure(c->border, 4 * f.blocks_total));
     }
     SEELE_CUDA(c, ensure(c->offs, 4 * R));
+    SEELE_CUDA(c, ensure(c->chunkv, 4 * (R / kChunkItems + 1)));
+    SEELE_CUDA(c, ensure(c->chunks, 4 * (R / kChunkItems + 1)));
     SEELE_CUDA(c, ensure(c->ranges, 8 * f.units_total));  // starts[n_units], then ends[n_units]
     SEELE_CUDA(c, ensure(c->status, sizeof(DeviceStatus)));
     SEELE_CUDA(c, ensure(c->T, 4 * f.pix_total));
@@ -425,6 +427,7 @@ seele_status enqueue_frame(seele_ctx* c, const seele_options* opt, const FrameIn
     if (c->profiling) SEELE_CUDA(c, cudaEventRecord(c->ev[k], s))
 
     SEELE_CUDA(c, cudaMemsetAsync(st, 0, sizeof(DeviceStatus), s));
+    SEELE_CUDA(c, cudaMemsetAsync(c->chunkv.p, 0, 4 * (R / kChunkItems + 1), s));
     SEELE_CUDA(c, cudaMemsetAsync(lb, 0, 8 * f.lb_entries, s));
     SEELE_CUDA(c, cudaMemsetAsync(c->viewt.p, 0, 12ull * ncam + 8, s));
     SEELE_CUDA(c, cudaMemsetAsync(c->ranges.p, 0xff, 4 * units_total, s));
@@ -449,7 +452,7 @@ seele_status enqueue_frame(seele_ctx* c, const seele_options* opt, const FrameIn
                           : nullptr;
     unsigned long long* vt = ptr<unsigned long long>(c->viewt);
     ProjOut po{ptr<float4>(c->rec), ptr<uint2>(c->rect), ptr<uint32_t>(c->tiles),
-               f.blocks ? ptr<uint32_t>(c->blocks) : nullptr, ptr<float>(c->depth), vt};
+               f.blocks ? ptr<uint32_t>(c->blocks) : nullptr, ptr<float>(c->depth), vt, ptr<uint32_t>(c->chunkv)};
     const CamDev* cams = ptr<const CamDev>(c->cams_dev);
     launch_preprocess(sc, cams, f.fp, po, s);
     SEELE_LAUNCHED(c);
@@ -457,8 +460,8 @@ seele_status enqueue_frame(seele_ctx* c, const seele_options* opt, const FrameIn
 
     // visible records -> (depth bits, id), then the stable depth sort
     SEELE_MARK(SEELE_STAGE_COMPACT);
-    launch_compact_visible(po.tiles, po.depth, (uint32_t)R, ptr<uint32_t>(c->visk[0]), ptr<uint32_t>(c->visv[0]), lb,
-                           c->epoch++, st, 0, s);
+    launch_compact_visible(po.tiles, po.depth, (uint32_t)R, po.chunk_vis, ptr<uint32_t>(c->visk[0]),
+                           ptr<uint32_t>(c->visv[0]), st, s);
     SEELE_LAUNCHED(c);
     ++launches;
     const uint32_t* n_vis = &st->n_visible;
@@ -476,10 +479,10 @@ seele_status enqueue_frame(seele_ctx* c, const seele_options* opt, const FrameIn
     // sorted ids are back in buffer 0 after an even number of passes
     const uint32_t* order = ptr<uint32_t>(c->visv[0]);
     SEELE_MARK(SEELE_STAGE_TILE_SCAN);
-    launch_scan_tiles(f.blocks ? po.blocks : po.tiles, order, (uint32_t)R, ptr<uint32_t>(c->offs), lb, c->epoch++,
-                      st, 1, (uint32_t)std::min<uint64_t>(cap, 0xffffffffu), s);
+    launch_scan_tiles(f.blocks ? po.blocks : po.tiles, order, (uint32_t)R, ptr<uint32_t>(c->chunks),
+                      ptr<uint32_t>(c->offs), st, (uint32_t)std::min<uint64_t>(cap, 0xffffffffu), s);
     SEELE_LAUNCHED(c);
-    ++launches;
+    launches += 2;
     const int emit_blocks = (int)std::max<uint64_t>(std::min<uint64_t>((R + 255) / 256, 8 * 152), 1);
     SEELE_MARK(SEELE_STAGE_EMIT);
     const uint32_t* n_inst = &st->n_inst_valid;

@@ -143,11 +143,12 @@ __global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ 
     }
 }
 
-// Block binning: the same walk over depth-ordered records, but the units
-// are (record, block row) pairs -- a block row being kBlockH tile rows -- and
-// each output is one tile block with the 32-bit mask of its tiles that the
-// record's tile-row spans cover.  The count per pair is the number of blocks
-// spanned by the union of its rows' spans, exactly as preprocessing counted.
+// Block binning: one thread per depth-ordered record writes its (block,
+// record, mask) entries at the record's scanned offset -- a record reaches
+// about two tile blocks on average, too few to be worth a warp.  Per block
+// row (kBlockH tile rows) it computes the rows' spans once, then emits the
+// blocks spanned by their union with the mask of the tiles each row covers
+// in that block; preprocessing counted the same blocks from the same spans.
 template <typename KeyT>
 __global__ void __launch_bounds__(256) emit_blocks_kernel(const uint32_t* __restrict__ order,
                                                           const uint32_t* __restrict__ offsets,
@@ -161,115 +162,58 @@ __global__ void __launch_bounds__(256) emit_blocks_kernel(const uint32_t* __rest
     if (st->error != kOk) return;
     const uint32_t n = st->n_visible;
     const uint32_t n_inst = st->n_instances;
-    const int lane = threadIdx.x & 31;
-    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t wb = warp * 32; wb < n; wb += nwarps * 32) {
-        const uint32_t j = wb + lane;
-        uint32_t r = 0, x0 = 0, x1 = 0, y0 = 0, y1 = 0, prs = 0, boff = 0, bx_n = 0;
-        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
-        if (j < n) {
-            r = __ldg(order + j);
-            const uint2 b = __ldg(rect + r);
-            x0 = b.x & 0xffffu;
-            y0 = b.x >> 16;
-            x1 = b.y & 0xffffu;
-            y1 = b.y >> 16;
-            prs = y1 / kBlockH - y0 / kBlockH + 1;
-            const CamDev& C = cams[r / (uint32_t)n_gauss];
-            boff = C.block_offset;
-            bx_n = (uint32_t)C.blocks_x;
-            if (ellipse) {
-                r0 = __ldg(rec + 3 * (size_t)r);
-                r1 = __ldg(rec + 3 * (size_t)r + 1);
-            }
-        }
-        const uint32_t pincl = warp_incl_scan(prs, lane);
-        const uint32_t pexcl = pincl - prs;
-        const uint32_t ptotal = __shfl_sync(0xffffffffu, pincl, 31);
-        const uint32_t base = __shfl_sync(0xffffffffu, j < n ? __ldg(offsets + j) : 0u, 0);
-        const uint32_t end = wb + 32 < n ? __ldg(offsets + wb + 32) : n_inst;
-        uint32_t pos = base;
-        for (uint32_t c0 = 0; c0 < ptotal; c0 += 32) {
-            const uint32_t po = c0 + lane;
-            const int s = warp_search(pexcl, po);
-            const uint32_t rs = __shfl_sync(0xffffffffu, r, s);
-            const uint32_t es = __shfl_sync(0xffffffffu, pexcl, s);
-            const int xs0 = (int)__shfl_sync(0xffffffffu, x0, s);
-            const int xs1 = (int)__shfl_sync(0xffffffffu, x1, s);
-            const int ys0 = (int)__shfl_sync(0xffffffffu, y0, s);
-            const int ys1 = (int)__shfl_sync(0xffffffffu, y1, s);
-            const uint32_t os = __shfl_sync(0xffffffffu, boff, s);
-            const uint32_t ns = __shfl_sync(0xffffffffu, bx_n, s);
-            float4 q0, q1;
-            q0.x = __shfl_sync(0xffffffffu, r0.x, s);
-            q0.y = __shfl_sync(0xffffffffu, r0.y, s);
-            q0.z = __shfl_sync(0xffffffffu, r0.z, s);
-            q0.w = __shfl_sync(0xffffffffu, r0.w, s);
-            q1.x = __shfl_sync(0xffffffffu, r1.x, s);
-            q1.w = __shfl_sync(0xffffffffu, r1.w, s);
-            q1.y = q1.z = 0.f;
-            // the pair's (up to kBlockH) tile-row spans, packed lo | hi << 16;
-            // an empty row is lo = 0xffff > hi = 0
-            uint32_t span[kBlockH];
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const uint32_t r = __ldg(order + j);
+        const uint2 bx2 = __ldg(rect + r);
+        const int x0 = (int)(bx2.x & 0xffffu), y0 = (int)(bx2.x >> 16);
+        const int x1 = (int)(bx2.y & 0xffffu), y1 = (int)(bx2.y >> 16);
+        const CamDev& C = cams[r / (uint32_t)n_gauss];
+        const uint32_t boff = C.block_offset, bx_n = (uint32_t)C.blocks_x;
+        Ellipse E;
+        if (ellipse) E = make_ellipse(__ldg(rec + 3 * (size_t)r), __ldg(rec + 3 * (size_t)r + 1));
+        uint32_t pos = __ldg(offsets + j);
+        const uint32_t end = j + 1 < n ? __ldg(offsets + j + 1) : n_inst;
+        for (int by = y0 / kBlockH; by <= y1 / kBlockH; ++by) {
+            int lo[kBlockH], hi[kBlockH];
             int blo = 1 << 30, bhi = -1;
-            uint32_t by = 0;
 #pragma unroll
-            for (int q = 0; q < kBlockH; ++q) span[q] = 0x0000ffffu;
-            if (po < ptotal) {
-                by = (uint32_t)(ys0 / kBlockH) + (po - es);
-                const Ellipse E = make_ellipse(q0, q1);
+            for (int q = 0; q < kBlockH; ++q) {
+                const int ty = by * kBlockH + q;
+                lo[q] = 1;
+                hi[q] = 0;
+                if (ty < y0 || ty > y1) continue;
+                int l = x0, h = x1;
+                if (ellipse && !row_span(E, ty, tile_w, tile_h, x0, x1, &l, &h)) continue;
+                lo[q] = l;
+                hi[q] = h;
+                blo = min(blo, l);
+                bhi = max(bhi, h);
+            }
+            if (bhi < blo) continue;
+            const uint32_t row_base = boff + (uint32_t)by * bx_n;
+            for (int bx = blo / kBlockW; bx <= bhi / kBlockW; ++bx) {
+                const int c0 = bx * kBlockW, c1 = c0 + kBlockW - 1;
+                uint32_t mask = 0;
 #pragma unroll
                 for (int q = 0; q < kBlockH; ++q) {
-                    const int ty = (int)by * kBlockH + q;
-                    if (ty < ys0 || ty > ys1) continue;
-                    int l = xs0, h = xs1;
-                    const bool any = ellipse ? row_span(E, ty, tile_w, tile_h, xs0, xs1, &l, &h) : true;
-                    if (!any) continue;
-                    span[q] = (uint32_t)l | ((uint32_t)h << 16);
-                    blo = min(blo, l);
-                    bhi = max(bhi, h);
+                    const int a = max(lo[q], c0), b = min(hi[q], c1);
+                    if (a <= b) mask |= ((0xffu >> (kBlockW - 1 - (b - a))) << (a - c0)) << (kBlockW * q);
                 }
-            }
-            const uint32_t cnt = bhi >= blo ? (uint32_t)(bhi / kBlockW - blo / kBlockW + 1) : 0u;
-            const uint32_t cincl = warp_incl_scan(cnt, lane);
-            const uint32_t cexcl = cincl - cnt;
-            const uint32_t ctotal = __shfl_sync(0xffffffffu, cincl, 31);
-            const uint32_t first_bx = bhi >= blo ? (uint32_t)(blo / kBlockW) : 0u;
-            const uint32_t row_base = os + by * ns;  // global id of block (0, by) of the camera
-            for (uint32_t o0 = 0; o0 < ctotal; o0 += 32) {
-                const uint32_t o = o0 + lane;
-                const int t = warp_search(cexcl, o);
-                const uint32_t et = __shfl_sync(0xffffffffu, cexcl, t);
-                const uint32_t fb = __shfl_sync(0xffffffffu, first_bx, t);
-                const uint32_t rb = __shfl_sync(0xffffffffu, row_base, t);
-                const uint32_t rt = __shfl_sync(0xffffffffu, rs, t);
-                uint32_t sp[kBlockH];
-#pragma unroll
-                for (int q = 0; q < kBlockH; ++q) sp[q] = __shfl_sync(0xffffffffu, span[q], t);
-                const uint32_t p = pos + o;
-                if (o < ctotal && p < end) {
-                    const int bx = (int)(fb + (o - et));
-                    const int c0x = bx * kBlockW, c1x = c0x + kBlockW - 1;
-                    uint32_t mask = 0;
-#pragma unroll
-                    for (int q = 0; q < kBlockH; ++q) {
-                        const int a = max((int)(sp[q] & 0xffffu), c0x), b = min((int)(sp[q] >> 16), c1x);
-                        if (a <= b) mask |= ((0xffu >> (kBlockW - 1 - (b - a))) << (a - c0x)) << (kBlockW * q);
-                    }
-                    inst_block[p] = (KeyT)(rb + (uint32_t)bx);
-                    inst_rec[p] = rt;
-                    inst_mask[p] = mask;
+                if (pos < end) {
+                    inst_block[pos] = (KeyT)(row_base + (uint32_t)bx);
+                    inst_rec[pos] = r;
+                    inst_mask[pos] = mask;
                 }
+                ++pos;
             }
-            pos += ctotal;
         }
         if (pos != end) {
-            if (lane == 0) record_error(st, kErrInternal, 8);
-            const uint32_t b0 = __shfl_sync(0xffffffffu, boff, 0), rr0 = __shfl_sync(0xffffffffu, r, 0);
-            for (uint32_t p = pos + lane; p < end; p += 32) {
-                inst_block[p] = (KeyT)b0;
-                inst_rec[p] = rr0;
+            // never expected: both counts come from the same row_span on the
+            // same stored floats.  Report it and keep every slot a valid entry.
+            record_error(st, kErrInternal, 8);
+            for (uint32_t p = pos; p < end; ++p) {
+                inst_block[p] = (KeyT)boff;
+                inst_rec[p] = r;
                 inst_mask[p] = 0u;
             }
         }

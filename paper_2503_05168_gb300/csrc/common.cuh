@@ -52,6 +52,10 @@ struct CamDev {
     int32_t pad[3];
 };
 
+// Records are counted in chunks of this many for the ordered compaction and
+// scans (a chunk is one CTA of those kernels).
+constexpr uint32_t kChunkItems = 4096;
+
 // Block binning: a tile block is kBlockW x kBlockH tiles; its instances carry a
 // 32-bit mask of the block's tiles that the Gaussian reaches (bit j * kBlockW + i
 // for tile (i, j) of the block).
@@ -91,6 +95,7 @@ struct ProjOut {
     uint32_t* blocks;          // [R] tile-block instances (block binning only, else unused)
     float* depth;              // [R] camera-space Z
     unsigned long long* t_frame;  // receives the frame's start time (%globaltimer, ns)
+    uint32_t* chunk_vis;       // [ceil(R / kChunkItems)] visible records per chunk (cleared per frame)
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {

@@ -16,11 +16,12 @@ void launch_preprocess(const SceneDev& sc, const CamDev* cams, const FrameParams
                        cudaStream_t s);
 
 uint32_t scan_tiles_per_launch();
-void launch_compact_visible(const uint32_t* tiles, const float* depth, uint32_t R, uint32_t* keys, uint32_t* vals,
-                            uint64_t* status, uint32_t epoch, DeviceStatus* st, int ticket, cudaStream_t s);
-void launch_scan_tiles(const uint32_t* tiles, const uint32_t* order, uint32_t max_n, uint32_t* offsets,
-                       uint64_t* status, uint32_t epoch, DeviceStatus* st, int ticket, uint32_t capacity,
-                       cudaStream_t s);
+void launch_compact_visible(const uint32_t* tiles, const float* depth, uint32_t R, const uint32_t* chunk_vis,
+                            uint32_t* keys, uint32_t* vals, DeviceStatus* st, cudaStream_t s);
+// Instance offsets of the depth-ordered records and K (capacity check);
+// chunk_sum: scratch of ceil(max_n / kChunkItems) words.
+void launch_scan_tiles(const uint32_t* cnt, const uint32_t* order, uint32_t max_n, uint32_t* chunk_sum,
+                       uint32_t* offsets, DeviceStatus* st, uint32_t capacity, cudaStream_t s);
 
 void launch_exclusive_scan(const uint32_t* in, uint32_t n, uint32_t* out, uint64_t* status, uint32_t epoch,
                            DeviceStatus* st, int ticket, cudaStream_t s);

@@ -232,6 +232,20 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev sc, const CamD
         out.depth[rid] = Z;
     } while (0);
     out.tiles[rid] = ntiles;
+    // visible records per 4096-record chunk (for the compaction); the valid
+    // lanes of a warp are a prefix and hold consecutive records, so they span
+    // at most two chunks
+    const int lane = threadIdx.x & 31;
+    const int valid = min(32, fp.n - (g - lane));
+    const uint32_t am = valid >= 32 ? 0xffffffffu : ((1u << valid) - 1u);
+    const uint32_t chunk = (uint32_t)(rid / kChunkItems);
+    const uint32_t c0 = __shfl_sync(am, chunk, 0);
+    const uint32_t vis = __ballot_sync(am, ntiles > 0u);
+    const uint32_t hi = __ballot_sync(am, ntiles > 0u && chunk != c0);
+    if (lane == 0) {
+        if (vis & ~hi) atomicAdd(out.chunk_vis + c0, (uint32_t)__popc(vis & ~hi));
+        if (hi) atomicAdd(out.chunk_vis + c0 + 1, (uint32_t)__popc(hi));
+    }
 }
 
 // Scene repack: caller layout (arrays of structures) -> library planes.

@@ -3,13 +3,20 @@
 //  compact_visible: ordered stream compaction of the visible records (tiles
 //                   touched > 0) into (depth bits, record id) pairs -- the input
 //                   of the depth sort, in record-id order so that the stable
-//                   sort breaks depth ties by id.
-//  scan_tiles:      exclusive scan of tiles touched in depth order, giving each
-//                   visible record the start of its tile instances and K.
-//
-// Each block takes a dynamic ticket (so every predecessor has already started
-// and will publish), reduces its tile, publishes the aggregate and walks back
-// over its predecessors one warp-width at a time.  Every wait is bounded.
+//                   sort breaks depth ties by id.  Preprocessing has counted
+//                   the visible records of each 4096-record chunk, so a CTA
+//                   adds up its predecessors' counts directly.
+//  scan_tiles:      exclusive scan of the instance counts in depth order,
+//                   giving each visible record the start of its instances and
+//                   K; chunk sums first, then the same direct prefix.
+//  exclusive_scan:  generic single-pass scan with decoupled look-back: each
+//                   block takes a dynamic ticket (so every predecessor has
+//                   already started and will publish), reduces its tile,
+//                   publishes the aggregate and walks back over its
+//                   predecessors one warp-width at a time.  Every wait is
+//                   bounded.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -18,6 +25,7 @@ namespace seele {
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;
 constexpr int kScanTile = kScanThreads * kScanItems;
+static_assert(kScanTile == kChunkItems, "scan tiles are the counting chunks");
 
 // Exclusive prefix of `aggregate` over the preceding tiles (all threads call).
 __device__ uint32_t lookback_prefix(uint64_t* status, uint32_t tile, uint32_t aggregate, uint32_t epoch,
@@ -98,67 +106,148 @@ __device__ __forceinline__ uint32_t take_ticket(uint32_t* counter) {
     return s_tile;
 }
 
-__global__ void __launch_bounds__(kScanThreads) compact_visible_kernel(const uint32_t* __restrict__ tiles,
-                                                                       const float* __restrict__ depth, uint32_t R,
-                                                                       uint32_t* keys, uint32_t* vals,
-                                                                       uint64_t* status, uint32_t epoch,
-                                                                       DeviceStatus* st, int ticket) {
-    const uint32_t tile = take_ticket(&st->ticket[ticket]);
-    const uint32_t ntiles = (R + kScanTile - 1) / kScanTile;
-    if (tile >= ntiles) return;
-    const uint32_t base = tile * kScanTile + threadIdx.x * kScanItems;
-    uint32_t flags = 0, cnt = 0;
+// Sum of counts[0, c) by the whole block (every thread gets it).  Chunk
+// counts are few (one per 4096 items), so each CTA adds up its predecessors
+// directly instead of waiting on them.
+__device__ __forceinline__ uint32_t chunk_prefix(const uint32_t* __restrict__ counts, uint32_t c) {
+    __shared__ uint32_t s_part[kScanThreads / 32];
+    uint32_t v = 0;
+    for (uint32_t i = threadIdx.x; i < c; i += kScanThreads) v += __ldg(counts + i);
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        const uint32_t i = base + k;
-        const bool vis = i < R && __ldg(tiles + i) > 0u;
-        flags |= (uint32_t)vis << k;
-        cnt += vis;
-    }
-    uint32_t total;
-    const uint32_t excl = block_exclusive_scan(cnt, &total);
-    const uint32_t prefix = lookback_prefix(status, tile, total, epoch, st, 1);
-    uint32_t pos = prefix + excl;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    uint32_t total = 0;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k)
-        if (flags >> k & 1u) {
-            keys[pos] = __float_as_uint(__ldg(depth + base + k));
-            vals[pos] = base + k;
-            ++pos;
-        }
-    if (tile == ntiles - 1 && threadIdx.x == 0) st->n_visible = prefix + total;
+    for (int w = 0; w < kScanThreads / 32; ++w) total += s_part[w];
+    __syncthreads();
+    return total;
 }
 
-__global__ void __launch_bounds__(kScanThreads) scan_tiles_kernel(const uint32_t* __restrict__ tiles,
-                                                                  const uint32_t* __restrict__ order,
-                                                                  uint32_t* offsets, uint64_t* status, uint32_t epoch,
-                                                                  DeviceStatus* st, int ticket, uint32_t capacity) {
-    const uint32_t tile = take_ticket(&st->ticket[ticket]);
-    const uint32_t n = st->n_visible;
-    const uint32_t ntiles = (n + kScanTile - 1) / kScanTile;
-    if (tile >= ntiles) {
-        if (n == 0 && tile == 0 && threadIdx.x == 0) st->n_instances = 0;
-        return;
+// Exclusive offsets of the block's warps from their totals (every thread).
+__device__ __forceinline__ uint32_t warp_offset(uint32_t warp_total, uint32_t* block_total) {
+    __shared__ uint32_t s_w[kScanThreads / 32];
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) s_w[w] = warp_total;
+    __syncthreads();
+    uint32_t before = 0, all = 0;
+#pragma unroll
+    for (int ww = 0; ww < kScanThreads / 32; ++ww) {
+        const uint32_t v = s_w[ww];
+        before += ww < w ? v : 0u;
+        all += v;
     }
-    const uint32_t base = tile * kScanTile + threadIdx.x * kScanItems;
-    uint32_t c[kScanItems];
-    uint32_t sum = 0;
+    *block_total = all;
+    return before;
+}
+
+// Ordered compaction of chunk c: items are warp-striped (item k of lane l of
+// warp w is c * 4096 + w * 512 + 32 k + l), ranked by one ballot per k, and
+// placed after the visible records of all earlier chunks.
+__global__ void __launch_bounds__(kScanThreads) compact_visible_kernel(const uint32_t* __restrict__ tiles,
+                                                                       const float* __restrict__ depth, uint32_t R,
+                                                                       const uint32_t* __restrict__ chunk_vis,
+                                                                       uint32_t* keys, uint32_t* vals,
+                                                                       DeviceStatus* st) {
+    const uint32_t c = blockIdx.x;
+    const uint32_t nchunks = (R + kChunkItems - 1) / kChunkItems;
+    const uint32_t prefix = chunk_prefix(chunk_vis, c);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t wbase = c * kChunkItems + (uint32_t)w * 32 * kScanItems;
+    uint32_t bal[kScanItems], wtot = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        const uint32_t j = base + k;
-        c[k] = j < n ? __ldg(tiles + __ldg(order + j)) : 0u;
-        sum += c[k];
+        const uint32_t i = wbase + 32 * k + lane;
+        bal[k] = __ballot_sync(0xffffffffu, i < R && __ldg(tiles + i) > 0u);
+        wtot += __popc(bal[k]);
     }
     uint32_t total;
-    const uint32_t excl = block_exclusive_scan(sum, &total);
-    const uint32_t prefix = lookback_prefix(status, tile, total, epoch, st, 2);
-    uint32_t pos = prefix + excl;
+    uint32_t pos = prefix + warp_offset(wtot, &total);
+    const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        if (base + k < n) offsets[base + k] = pos;
-        pos += c[k];
+        const uint32_t i = wbase + 32 * k + lane;
+        if ((bal[k] >> lane) & 1u) {
+            const uint32_t o = pos + __popc(bal[k] & lt);
+            keys[o] = __float_as_uint(__ldg(depth + i));
+            vals[o] = i;
+        }
+        pos += __popc(bal[k]);
     }
-    if (tile == ntiles - 1 && threadIdx.x == 0) {
+    if (c == nchunks - 1 && threadIdx.x == 0) st->n_visible = prefix + total;
+}
+
+// Per chunk of 4096 depth-ordered records: the sum of their counts.
+__global__ void __launch_bounds__(kScanThreads) chunk_sums_kernel(const uint32_t* __restrict__ cnt,
+                                                                  const uint32_t* __restrict__ order,
+                                                                  const DeviceStatus* __restrict__ st,
+                                                                  uint32_t* __restrict__ chunk_sum) {
+    __shared__ uint32_t s_part[kScanThreads / 32];
+    const uint32_t n = st->n_visible;
+    const uint32_t base = blockIdx.x * kChunkItems;
+    if (base >= n) return;
+    uint32_t v = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const uint32_t j = base + k * kScanThreads + threadIdx.x;
+        if (j < n) v += __ldg(cnt + __ldg(order + j));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < kScanThreads / 32; ++w) t += s_part[w];
+        chunk_sum[blockIdx.x] = t;
+    }
+}
+
+// Exclusive scan of the counts of the depth-ordered records (their instance
+// offsets), chunk by chunk after the sums of the earlier chunks; the last
+// chunk sets K and compares it with the capacity.
+__global__ void __launch_bounds__(kScanThreads) scan_tiles_kernel(const uint32_t* __restrict__ cnt,
+                                                                  const uint32_t* __restrict__ order,
+                                                                  const uint32_t* __restrict__ chunk_sum,
+                                                                  uint32_t* offsets, DeviceStatus* st,
+                                                                  uint32_t capacity) {
+    const uint32_t n = st->n_visible;
+    const uint32_t nchunks = (n + kChunkItems - 1) / kChunkItems;
+    const uint32_t c = blockIdx.x;
+    if (c >= nchunks) {
+        if (n == 0 && c == 0 && threadIdx.x == 0) {
+            st->n_instances = 0;
+            st->capacity = capacity;
+        }
+        return;
+    }
+    const uint32_t prefix = chunk_prefix(chunk_sum, c);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t wbase = c * kChunkItems + (uint32_t)w * 32 * kScanItems;
+    uint32_t v[kScanItems], wtot = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const uint32_t j = wbase + 32 * k + lane;
+        v[k] = j < n ? __ldg(cnt + __ldg(order + j)) : 0u;
+        wtot += v[k];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wtot += __shfl_xor_sync(0xffffffffu, wtot, o);
+    uint32_t total;
+    uint32_t pos = prefix + warp_offset(wtot, &total);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        uint32_t incl = v[k];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t j = wbase + 32 * k + lane;
+        if (j < n) offsets[j] = pos + incl - v[k];
+        pos += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (c == nchunks - 1 && threadIdx.x == 0) {
         const uint32_t K = prefix + total;
         st->n_instances = K;
         st->capacity = capacity;
@@ -212,19 +301,18 @@ void launch_exclusive_scan(const uint32_t* in, uint32_t n, uint32_t* out, uint64
 
 uint32_t scan_tiles_per_launch() { return kScanTile; }
 
-void launch_compact_visible(const uint32_t* tiles, const float* depth, uint32_t R, uint32_t* keys, uint32_t* vals,
-                            uint64_t* status, uint32_t epoch, DeviceStatus* st, int ticket, cudaStream_t s) {
-    const uint32_t blocks = (R + kScanTile - 1) / kScanTile;
-    compact_visible_kernel<<<blocks > 0 ? blocks : 1, kScanThreads, 0, s>>>(tiles, depth, R, keys, vals, status,
-                                                                            epoch, st, ticket);
+void launch_compact_visible(const uint32_t* tiles, const float* depth, uint32_t R, const uint32_t* chunk_vis,
+                            uint32_t* keys, uint32_t* vals, DeviceStatus* st, cudaStream_t s) {
+    const uint32_t blocks = (R + kChunkItems - 1) / kChunkItems;
+    compact_visible_kernel<<<blocks > 0 ? blocks : 1, kScanThreads, 0, s>>>(tiles, depth, R, chunk_vis, keys, vals,
+                                                                            st);
 }
 
-void launch_scan_tiles(const uint32_t* tiles, const uint32_t* order, uint32_t max_n, uint32_t* offsets,
-                       uint64_t* status, uint32_t epoch, DeviceStatus* st, int ticket, uint32_t capacity,
-                       cudaStream_t s) {
-    const uint32_t blocks = (max_n + kScanTile - 1) / kScanTile;
-    scan_tiles_kernel<<<blocks > 0 ? blocks : 1, kScanThreads, 0, s>>>(tiles, order, offsets, status, epoch, st,
-                                                                       ticket, capacity);
+void launch_scan_tiles(const uint32_t* cnt, const uint32_t* order, uint32_t max_n, uint32_t* chunk_sum,
+                       uint32_t* offsets, DeviceStatus* st, uint32_t capacity, cudaStream_t s) {
+    const uint32_t blocks = std::max<uint32_t>((max_n + kChunkItems - 1) / kChunkItems, 1u);
+    chunk_sums_kernel<<<blocks, kScanThreads, 0, s>>>(cnt, order, st, chunk_sum);
+    scan_tiles_kernel<<<blocks, kScanThreads, 0, s>>>(cnt, order, chunk_sum, offsets, st, capacity);
 }
 
 }  // namespace seele
