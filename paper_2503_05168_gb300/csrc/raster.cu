@@ -10,8 +10,8 @@
 // outright when every group it holds rejects it -- the divergence-free skip of
 // Sec. 3.4 "GPU Parallelism".
 //
-// Work per (pixel, Gaussian) pair: ~11 FP32-pipe instructions and one MUFU
-// ex2; the kernel is bound by FP32 issue, not by memory.
+// Work per (pixel, Gaussian) pair: ~10 FP32-pipe instructions and one MUFU
+// ex2; the kernel is bound by instruction issue, not by memory.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -178,21 +178,23 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
             // so the tests run back to back.  Phase 2: only the Gaussians the
             // leader kept are blended, in list order, by the group's pixels.
             if (live == 0u) continue;
-            for (int c0 = 0; c0 < cnt && live != 0u; c0 += 64) {
-            const int c1 = min(cnt, c0 + 64);
-            uint64_t pass = 0;
-#pragma unroll 8
-            for (int k = c0; k < c1; ++k) {
-                const float4 A = s0[k];
-                const float4 B = s1[k];
-                const float dx = fx0 - A.x, dy = fy0 - A.y;
-                const float e0 = fmaf(fmaf(A.z, dx, A.w * dy), dx, fmaf(B.x * dy, dy, B.y));
-                if (COUNT) ++n_lead;
-                pass |= (uint64_t)(e0 >= B.z) << (k - c0);
+            for (int c0 = 0; c0 < cnt && live != 0u; c0 += 32) {
+            const int n32 = min(32, cnt - c0);
+            uint32_t pass = 0;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                if (i < n32) {
+                    const float4 A = s0[c0 + i];
+                    const float4 B = s1[c0 + i];
+                    const float dx = fx0 - A.x, dy = fy0 - A.y;
+                    const float e0 = fmaf(fmaf(A.z, dx, A.w * dy), dx, fmaf(B.x * dy, dy, B.y));
+                    if (COUNT) ++n_lead;
+                    pass |= e0 >= B.z ? 1u << i : 0u;
+                }
             }
-            while (pass != 0ull && live != 0u) {
-                const int k = c0 + __ffsll((long long)pass) - 1;
-                pass &= pass - 1ull;
+            while (pass != 0u && live != 0u) {
+                const int k = c0 + __ffs(pass) - 1;
+                pass &= pass - 1u;
                 const float4 A = s0[k];
                 const float4 B = s1[k];
                 const float4 Cc = s2[k];
@@ -211,12 +213,12 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
                         const float e = fmaf(fmaf(A.z, ddx, rb), ddx, rc);
                         if (e < B.z) continue;  // per-pixel alpha_theta / support rule
                         const float al = fminf(amax, ex2_approx(e));
-                        const float Tn = T[p] * (1.f - al);
+                        const float wgt = al * T[p];
+                        const float Tn = T[p] - wgt;  // T (1 - alpha)
                         if (Tn < tstop) {
                             live &= ~(1u << p);
                             continue;
                         }
-                        const float wgt = al * T[p];
                         cr[p] = fmaf(wgt, Cc.x, cr[p]);
                         cg[p] = fmaf(wgt, Cc.y, cg[p]);
                         cb[p] = fmaf(wgt, Cc.z, cb[p]);
@@ -244,13 +246,13 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
                 if (COUNT) ++n_eval;
                 if (e < B.z) return;  // outside the support or alpha < alpha_theta
                 const float al = fminf(amax, ex2_approx(e));
-                const float Tn = T[p] * (1.f - al);
+                const float wgt = al * T[p];
+                const float Tn = T[p] - wgt;  // T (1 - alpha)
                 if (Tn < tstop) {     // stop before crossing Gamma_theta
                     live &= ~(1u << p);
                     return;
                 }
                 const float4 Cc = s2[k];
-                const float wgt = al * T[p];
                 cr[p] = fmaf(wgt, Cc.x, cr[p]);
                 cg[p] = fmaf(wgt, Cc.y, cg[p]);
                 cb[p] = fmaf(wgt, Cc.z, cb[p]);

@@ -100,14 +100,13 @@ __global__ void __launch_bounds__(kSortThreads) downsweep_kernel(const KeyT* __r
 
     // load warp-striped: item k of lane l is element wbase + 32 k + l, so the
     // order (k, lane) is the input order and ranking in that order is stable
-    uint32_t key[kSortItems], val[kSortItems], rank[kSortItems], aux[AUX ? kSortItems : 1];
+    uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
         const uint32_t i = wbase + 32 * k + lane;
         const bool ok = i < n;
         key[k] = ok ? (uint32_t)__ldg(keys_in + i) : 0xffffffffu;
         val[k] = ok ? __ldg(vals_in + i) : 0u;
-        if (AUX) aux[AUX ? k : 0] = ok ? __ldg(aux_in + i) : 0u;
     }
     // lanes holding the same digit: one ballot per significant digit bit plus
     // one for validity (elements past n form their own group)
@@ -180,12 +179,19 @@ __global__ void __launch_bounds__(kSortThreads) downsweep_kernel(const KeyT* __r
         }
     }
     if (AUX) {
+        // read again here rather than held in registers through the ranking
+        uint32_t aux[kSortItems];
+#pragma unroll
+        for (int k = 0; k < kSortItems; ++k) {
+            const uint32_t i = wbase + 32 * k + lane;
+            aux[k] = key[k] != 0xffffffffu ? __ldg(aux_in + i) : 0u;
+        }
         __syncthreads();  // every value has been read out of s_vals
 #pragma unroll
         for (int k = 0; k < kSortItems; ++k) {
             if (key[k] != 0xffffffffu) {
                 const uint32_t dg = (key[k] >> shift) & 0xffu;
-                s_vals[s_local_base[dg] + s_wcount[w][dg] + rank[k]] = aux[AUX ? k : 0];
+                s_vals[s_local_base[dg] + s_wcount[w][dg] + rank[k]] = aux[k];
             }
         }
         __syncthreads();
