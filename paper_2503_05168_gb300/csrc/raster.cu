@@ -204,27 +204,29 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
                 for (int jj = 0; jj < PH; ++jj) {
                     const float ddy = dy + (float)jj;
                     const float rb = A.w * ddy, rc = fmaf(B.x * ddy, ddy, B.y);
+                    // branch-free over the group's pixels (almost every pixel
+                    // of a kept Gaussian blends), so their chains interleave
 #pragma unroll
                     for (int i = 0; i < PW; ++i) {
                         const int p = jj * PW + i;
-                        if (!(live >> p & 1u)) continue;
-                        if (COUNT) ++n_eval;
+                        const bool alive = (live >> p) & 1u;
+                        if (COUNT) n_eval += alive;
                         const float ddx = dx + (float)i;
                         const float e = fmaf(fmaf(A.z, ddx, rb), ddx, rc);
-                        if (e < B.z) continue;  // per-pixel alpha_theta / support rule
+                        const bool on = alive && e >= B.z;  // per-pixel alpha_theta / support rule
                         const float al = fminf(amax, ex2_approx(e));
                         const float wgt = al * T[p];
                         const float Tn = T[p] - wgt;  // T (1 - alpha)
-                        if (Tn < tstop) {
-                            live &= ~(1u << p);
-                            continue;
-                        }
-                        cr[p] = fmaf(wgt, Cc.x, cr[p]);
-                        cg[p] = fmaf(wgt, Cc.y, cg[p]);
-                        cb[p] = fmaf(wgt, Cc.z, cb[p]);
-                        T[p] = Tn;
-                        nc[p] = pos1;
-                        if (COUNT) ++n_blend;
+                        const bool stop = on && Tn < tstop;
+                        const bool take = on && !stop;
+                        live &= stop ? ~(1u << p) : 0xffffffffu;
+                        const float w = take ? wgt : 0.f;
+                        cr[p] = fmaf(w, Cc.x, cr[p]);
+                        cg[p] = fmaf(w, Cc.y, cg[p]);
+                        cb[p] = fmaf(w, Cc.z, cb[p]);
+                        T[p] = take ? Tn : T[p];
+                        nc[p] = take ? pos1 : nc[p];
+                        if (COUNT) n_blend += take;
                     }
                 }
             }
