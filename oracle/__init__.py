@@ -99,6 +99,12 @@ def _L():
         lib.oc_select_clusters.argtypes = [I32, P, ctypes.c_double, P, I32]
         lib.oc_select_clusters.restype = ctypes.c_uint32
         lib.oc_sh_eval.argtypes = [I32, I64, P, P, P]
+        lib.oc_pose_feature.argtypes = [P, ctypes.c_double, P]
+        lib.oc_pose_feature.restype = None
+        lib.oc_kmeans.argtypes = [I32, I32, P, I32, P, I32, P, P]
+        lib.oc_kmeans.restype = I32
+        lib.oc_topk_contributors.argtypes = [P, P, P, I32, I32, P, I32, P, P, P, P, I32]
+        lib.oc_topk_contributors.restype = None
         lib.oc_sh_eval.restype = None
         _lib = lib
     return _lib
@@ -310,3 +316,75 @@ def sh_eval(lmax: int, dirs: np.ndarray, grad: bool = False):
     g = np.zeros((d.shape[0], nc, 3)) if grad else None
     _L().oc_sh_eval(lmax, d.shape[0], _p(d), _p(y), _p(g))
     return (y, g) if grad else y
+
+
+# ------------------------------------------------------------------------------
+# Offline view-dependent representation (Sec. 3.3 "Offline Clustering")
+# ------------------------------------------------------------------------------
+
+def pose_features(poses, pos_scale: float) -> np.ndarray:
+    """(x / s, v) per pose: camera centre over the position scale and the unit
+    viewing direction (beta = 1)."""
+    out = np.zeros((len(poses), 6))
+    for i, cam in enumerate(poses):
+        f = np.zeros(6)
+        _L().oc_pose_feature(_p(camera_struct(cam)), float(pos_scale), _p(f))
+        out[i] = f
+    return out
+
+
+def position_scale(poses) -> float:
+    """s = the largest camera distance from the origin over the samples."""
+    f = pose_features(poses, 1.0)
+    return float(np.max(np.linalg.norm(f[:, :3], axis=1)))
+
+
+def kmeans(x: np.ndarray, k: int, u: np.ndarray, max_iter: int = 100):
+    """k-means++ seeded by the uniforms u[0..k), then Lloyd iterations (see
+    oc_kmeans).  Returns (centroids [k, dim], assignment [n], updates)."""
+    x = _f64(x, (x.shape[0], -1))
+    u = _f64(u, (-1,))
+    assert u.shape[0] >= k and x.shape[0] >= 1
+    cent = np.zeros((k, x.shape[1]))
+    assign = np.zeros(x.shape[0], np.int32)
+    it = _L().oc_kmeans(x.shape[0], x.shape[1], _p(x), k, _p(u), int(max_iter), _p(cent), _p(assign))
+    return cent, assign, int(it)
+
+
+def topk_contributors(proj, gid, ranges, cam, opts: Options, k: int, nthreads: int = 1):
+    """Per-pixel top-k contributors (Gamma alpha) of a plain render: ids and
+    contributions [H, W, k] (-1 / 0 when unused), counts [H, W] and the
+    per-pixel decision margin including the k-th / (k+1)-th gap."""
+    W, H = int(cam["width"]), int(cam["height"])
+    ids = np.zeros((H, W, k), np.int32)
+    w = np.zeros((H, W, k))
+    cnt = np.zeros((H, W), np.int32)
+    margin = np.zeros((H, W))
+    o = opts.to_struct()
+    gid = np.ascontiguousarray(gid, np.int32)
+    ranges = np.ascontiguousarray(ranges, np.int64)
+    _L().oc_topk_contributors(_p(proj), _p(gid) if gid.size else None, _p(ranges), W, H, _p(o), int(k), _p(ids),
+                              _p(w), _p(cnt), _p(margin), nthreads)
+    return ids, w, cnt, margin
+
+
+def view_masks(scene: Scene64, poses, assign: np.ndarray, k: int, opts: Options | None = None,
+               nthreads: int = 1):
+    """Cluster bit mask per Gaussian: bit c is set when the Gaussian is among
+    the top-k contributors of some pixel of some pose assigned to cluster c
+    (Gaussians of every cluster are the shared ones; a zero mask drops the
+    Gaussian).  Also returns, per Gaussian, the smallest margin of a pixel
+    that made it a member (for decision-aware comparisons)."""
+    opts = opts or Options()
+    mask = np.zeros(scene.n, np.uint32)
+    gmargin = np.full(scene.n, np.inf)
+    for cam, c in zip(poses, assign):
+        proj = preprocess(scene, cam, opts, nthreads)
+        _, gid, ranges = instances(proj, cam, opts)
+        ids, _, _, margin = topk_contributors(proj, gid, ranges, cam, opts, k, nthreads)
+        sel = ids >= 0
+        g = ids[sel]
+        mask[g] |= np.uint32(1) << np.uint32(c)
+        m = np.broadcast_to(margin[..., None], ids.shape)[sel]
+        np.minimum.at(gmargin, g, m)
+    return mask, gmargin

@@ -972,3 +972,165 @@ uint32_t oc_select_clusters(int nclusters, const double* centroids, double pos_s
     }
     return bits;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Offline view-dependent representation (Sec. 3.3 "Offline Clustering").    */
+/* Sampled camera poses are clustered on the feature (x / s, v); for every    */
+/* pixel of every pose the Gaussians with the k largest contributions         */
+/* Gamma_i alpha_i are found, and a Gaussian belongs to cluster c when it is  */
+/* such a top contributor for some pose of c.  (Readings: k-means with        */
+/* beta = 1, s = the largest camera distance of the samples; shared = the     */
+/* Gaussians of every cluster; a Gaussian of no cluster is dropped.)          */
+/* ------------------------------------------------------------------------ */
+
+/* Pose feature: camera centre over the position scale, then the unit viewing
+   direction (the camera's +z axis in world coordinates). */
+void oc_pose_feature(const oc_camera* cam, double pos_scale, double* f) {
+    double c[3];
+    camera_centre(cam, c);
+    for (int i = 0; i < 3; ++i) f[i] = c[i] / pos_scale;
+    for (int i = 0; i < 3; ++i) f[3 + i] = cam->R[6 + i];
+}
+
+static double sqdist(const double* a, const double* b, int dim) {
+    double d = 0.0;
+    for (int i = 0; i < dim; ++i) d += (a[i] - b[i]) * (a[i] - b[i]);
+    return d;
+}
+
+/* k-means of n points of `dim` coordinates into k clusters.  Seeding is
+   k-means++ driven by the uniforms u[0..k): the first centre is point
+   floor(u[0] n); centre j is the first point at which the running sum of the
+   squared distances to the nearest chosen centre exceeds u[j] times their
+   total (floor(u[j] n) if that total is zero).  Lloyd iterations then assign
+   every point to its nearest centre (ties to the lower index) and move every
+   centre to the mean of its points (an empty cluster keeps its centre),
+   stopping once an assignment step changes nothing or after max_iter
+   updates.  Returns the number of updates made. */
+int oc_kmeans(int n, int dim, const double* x, int k, const double* u, int max_iter, double* cent,
+              int32_t* assign) {
+    double* d2 = (double*)malloc((size_t)n * sizeof(double));
+    int first = (int)floor(u[0] * n);
+    if (first >= n) first = n - 1;
+    memcpy(cent, x + (size_t)first * dim, (size_t)dim * sizeof(double));
+    for (int i = 0; i < n; ++i) d2[i] = sqdist(x + (size_t)i * dim, cent, dim);
+    for (int j = 1; j < k; ++j) {
+        double total = 0.0;
+        for (int i = 0; i < n; ++i) total += d2[i];
+        int pick = n - 1;
+        if (total > 0.0) {
+            const double target = u[j] * total;
+            double run = 0.0;
+            for (int i = 0; i < n; ++i) {
+                run += d2[i];
+                if (run > target) { pick = i; break; }
+            }
+        } else {
+            pick = (int)floor(u[j] * n);
+            if (pick >= n) pick = n - 1;
+        }
+        memcpy(cent + (size_t)j * dim, x + (size_t)pick * dim, (size_t)dim * sizeof(double));
+        for (int i = 0; i < n; ++i) {
+            const double d = sqdist(x + (size_t)i * dim, cent + (size_t)j * dim, dim);
+            if (d < d2[i]) d2[i] = d;
+        }
+    }
+    free(d2);
+    for (int i = 0; i < n; ++i) assign[i] = -1;
+    double* sum = (double*)malloc((size_t)k * dim * sizeof(double));
+    int* cnt = (int*)malloc((size_t)k * sizeof(int));
+    int it = 0;
+    for (; it < max_iter; ++it) {
+        int changed = 0;
+        for (int i = 0; i < n; ++i) {
+            int best = 0;
+            double bd = sqdist(x + (size_t)i * dim, cent, dim);
+            for (int j = 1; j < k; ++j) {
+                const double d = sqdist(x + (size_t)i * dim, cent + (size_t)j * dim, dim);
+                if (d < bd) { bd = d; best = j; }
+            }
+            if (assign[i] != best) { assign[i] = best; changed = 1; }
+        }
+        if (!changed) break;
+        memset(sum, 0, (size_t)k * dim * sizeof(double));
+        memset(cnt, 0, (size_t)k * sizeof(int));
+        for (int i = 0; i < n; ++i) {
+            for (int c = 0; c < dim; ++c) sum[(size_t)assign[i] * dim + c] += x[(size_t)i * dim + c];
+            cnt[assign[i]]++;
+        }
+        for (int j = 0; j < k; ++j)
+            if (cnt[j] > 0)
+                for (int c = 0; c < dim; ++c) cent[(size_t)j * dim + c] = sum[(size_t)j * dim + c] / cnt[j];
+    }
+    free(sum);
+    free(cnt);
+    return it;
+}
+
+typedef struct {
+    double w;
+    int32_t g;
+} oc_contrib;
+
+static int contrib_cmp(const void* a, const void* b) {
+    const oc_contrib* x = (const oc_contrib*)a;
+    const oc_contrib* y = (const oc_contrib*)b;
+    if (x->w != y->w) return x->w > y->w ? -1 : 1;
+    return (x->g > y->g) - (x->g < y->g);
+}
+
+/* Per-pixel top-k contributors of a plain render (Sec. 3.3): every pixel
+   walks its tile list under the rules of px_blend; a blended Gaussian
+   contributes Gamma_i alpha_i = T alpha (T before it).  The k largest, ties
+   to the lower Gaussian index, descending: out_ids / out_w [H W][k] (unused
+   slots -1 / 0), out_count [H W], and out_margin [H W] = the smaller of the
+   pixel's decision margin and the relative gap between the k-th and
+   (k+1)-th contribution (INFINITY with k or fewer contributors). */
+void oc_topk_contributors(const oc_proj* proj, const int32_t* gid, const int64_t* ranges, int W, int H,
+                          const oc_options* opt, int k, int32_t* out_ids, double* out_w, int32_t* out_count,
+                          double* out_margin, int nthreads) {
+    int tw = opt->tile_w, th = opt->tile_h;
+    int tiles_x = (W + tw - 1) / tw, tiles_y = (H + th - 1) / th;
+    int64_t ntiles = (int64_t)tiles_x * tiles_y;
+    int nt = nthreads > 0 ? nthreads : 1;
+    (void)nt;
+#ifdef _OPENMP
+    #pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+#endif
+    for (int64_t t = 0; t < ntiles; ++t) {
+        int64_t cnt[OC_NCOUNT] = {0};
+        int tx = (int)(t % tiles_x), ty = (int)(t / tiles_x);
+        int64_t start = ranges[2 * t], end = ranges[2 * t + 1];
+        oc_contrib* buf = (oc_contrib*)malloc((size_t)(end > start ? end - start : 1) * sizeof(oc_contrib));
+        for (int y = ty * th; y < ty * th + th && y < H; ++y)
+            for (int x = tx * tw; x < tx * tw + tw && x < W; ++x) {
+                px_state s;
+                px_init(&s);
+                int m = 0;
+                for (int64_t i = start; i < end && !s.done; ++i) {
+                    const double T = s.T;
+                    const oc_proj* P = proj + gid[i];
+                    if (px_blend(&s, P, opt, x + 0.5, y + 0.5, i - start, cnt)) {
+                        buf[m].w = T * alpha_of_q(P, opt, quad_at(P, x + 0.5, y + 0.5));
+                        buf[m].g = gid[i];
+                        ++m;
+                    }
+                }
+                qsort(buf, (size_t)m, sizeof(oc_contrib), contrib_cmp);
+                const int64_t p = (int64_t)y * W + x;
+                const int c = m < k ? m : k;
+                for (int j = 0; j < k; ++j) {
+                    out_ids[p * k + j] = j < c ? buf[j].g : -1;
+                    out_w[p * k + j] = j < c ? buf[j].w : 0.0;
+                }
+                out_count[p] = c;
+                double mg = s.margin;
+                if (m > k) {
+                    const double gap = (buf[k - 1].w - buf[k].w) / buf[k - 1].w;
+                    if (gap < mg) mg = gap;
+                }
+                out_margin[p] = mg;
+            }
+        free(buf);
+    }
+}

@@ -141,6 +141,24 @@ def view_clusters(means: np.ndarray, n_clusters: int, radius: float, r: np.rando
     return mask, centroids, float(radius)
 
 
+def sample_poses(n: int, radius: float, width: int, height: int, r: np.random.Generator,
+                 elevation_deg: float = 30.0, fov_y_deg: float = 60.0) -> list:
+    """n random camera poses on a sphere of the given radius looking at the
+    origin: azimuth U[0, 2 pi), elevation U[-elevation, elevation]."""
+    az = r.uniform(0.0, 2 * math.pi, n)
+    el = np.radians(r.uniform(-elevation_deg, elevation_deg, n))
+    cams = []
+    for a, e in zip(az, el):
+        eye = (radius * math.cos(a) * math.cos(e), -radius * math.sin(e), radius * math.sin(a) * math.cos(e))
+        cams.append(look_at(eye, (0.0, 0.0, 0.0), width, height, fov_y_deg))
+    return cams
+
+
+def kmeans_uniforms(k: int, r: np.random.Generator) -> np.ndarray:
+    """The k uniforms in [0, 1) that drive k-means++ seeding."""
+    return r.random(k)
+
+
 # -------------------------------------------------------------- workloads --
 
 def uniform_10k(seed: int = 0, n: int = 10_000, width: int = 256, height: int = 256) -> tuple[dict, list]:
