@@ -272,6 +272,35 @@ seele_status seele_get_view_times(const seele_ctx* ctx, float* out_ms, int32_t n
  * *best_ms (nullable).  Leaves no render state behind. */
 seele_status seele_autotune(seele_ctx* ctx, seele_options* inout, float* best_ms);
 
+/* Builds the offline view-dependent representation of the loaded scene
+ * (Sec. 3.3 "Offline Clustering").
+ *   poses        host, [n_poses] sampled cameras (any image sizes)
+ *   n_clusters   N of Sec. 3.3, 1..32;  n_poses >= n_clusters
+ *   top_k        k of Sec. 3.3 (32), 1..64
+ *   uniforms     host, [n_clusters] draws in [0, 1) that drive k-means++
+ *   max_iter     Lloyd updates at most (100)
+ * Poses are clustered by k-means on the feature (x / s, v) -- camera centre
+ * over s = the largest camera distance of the samples, and the unit viewing
+ * direction (beta = 1): seeding picks point floor(u_0 n), then the first point
+ * whose running sum of squared distances to the chosen centres exceeds
+ * u_j times their total; Lloyd iterations assign to the nearest centre (ties
+ * to the lower index) and move centres to the means, until nothing changes.
+ * Every pose is then rendered plainly (t_g = 9, no filters) and, per pixel,
+ * the k Gaussians with the largest contribution Gamma_i alpha_i (ties to the
+ * lower index) are found; a Gaussian gets bit c of its mask when it is such a
+ * contributor for some pose of cluster c.  Gaussians of every cluster are the
+ * shared ones; a zero mask drops the Gaussian.
+ *   out_centroids  host, [n_clusters][6] (the seele_scene_desc layout)
+ *   out_pos_scale  host, s (the seele_scene_desc position scale)
+ *   out_mask       host or device, [n] (the seele_scene_desc cluster mask)
+ *   out_assign     host or NULL, [n_poses] cluster of each pose
+ * Synchronous; leaves the context's cameras as they were and no render
+ * state behind. */
+seele_status seele_build_view_clusters(seele_ctx* ctx, const seele_camera* poses, int32_t n_poses,
+                                       int32_t n_clusters, int32_t top_k, const double* uniforms,
+                                       int32_t max_iter, float* out_centroids, float* out_pos_scale,
+                                       uint32_t* out_mask, int32_t* out_assign);
+
 /* Message of the last failed call on this context (library-owned). */
 const char* seele_last_error(const seele_ctx* ctx);
 

@@ -141,7 +141,8 @@ class Renderer:
         self.n = n
         self.sh_degree = d.sh_degree
 
-    def set_cameras(self, cams):
+    @staticmethod
+    def _camera_array(cams):
         arr = (_abi.Camera * len(cams))()
         for i, c in enumerate(cams):
             w2c = np.asarray(c["world_to_cam"], dtype=np.float64).reshape(3, 4)
@@ -150,6 +151,10 @@ class Renderer:
             arr[i].cx, arr[i].cy = float(c["cx"]), float(c["cy"])
             arr[i].width, arr[i].height = int(c["width"]), int(c["height"])
             arr[i].near_z = float(c.get("near", 0.2))
+        return arr
+
+    def set_cameras(self, cams):
+        arr = self._camera_array(cams)
         self._check(lib().seele_set_cameras(self._h, arr, len(cams)))
         self.cameras = [dict(width=int(c["width"]), height=int(c["height"])) for c in cams]
 
@@ -244,6 +249,28 @@ class Renderer:
             res.append(flat[off:off + k].reshape(3, c["height"], c["width"]))
             off += k
         return res
+
+    def build_view_clusters(self, poses, n_clusters: int = 16, top_k: int = 32, uniforms=None, seed: int = 0,
+                            max_iter: int = 100):
+        """Offline view-dependent representation of the loaded scene (Sec. 3.3):
+        k-means of the poses on (x / s, v) and per-Gaussian cluster bits from the
+        per-pixel top-k contributors.  ``uniforms`` drive k-means++ (default:
+        ``n_clusters`` draws of numpy's PCG64 with ``seed``).  Returns
+        dict(mask uint32 [n], centroids [C, 6], pos_scale, assign [n_poses])."""
+        if uniforms is None:
+            uniforms = np.random.default_rng(seed).random(n_clusters)
+        u = np.ascontiguousarray(uniforms, np.float64)
+        cams = self._camera_array(poses)
+        cent = np.zeros((n_clusters, 6), np.float32)
+        scale = ctypes.c_float()
+        mask = np.zeros(self.n, np.uint32)
+        assign = np.zeros(len(poses), np.int32)
+        self._sync_stream()
+        self._check(lib().seele_build_view_clusters(
+            self._h, cams, len(poses), int(n_clusters), int(top_k), ctypes.c_void_p(u.ctypes.data), int(max_iter),
+            ctypes.c_void_p(cent.ctypes.data), ctypes.byref(scale), ctypes.c_void_p(mask.ctypes.data),
+            ctypes.c_void_p(assign.ctypes.data)))
+        return dict(mask=mask, centroids=cent, pos_scale=float(scale.value), assign=assign)
 
     def debug_view(self) -> dict:
         """Copies of the last render's intermediates (CUDA tensors)."""

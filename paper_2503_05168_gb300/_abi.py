@@ -81,6 +81,8 @@ PROTOTYPES = {
     "seele_get_view_times": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_float), ctypes.c_int32]),
     "seele_autotune": (ctypes.c_int, [P, ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_float)]),
     "seele_sort_tile_instances_noalloc": (ctypes.c_int, [P, P, ctypes.c_uint32, ctypes.c_uint32, P, P, P, P]),
+    "seele_build_view_clusters": (ctypes.c_int, [P, ctypes.POINTER(Camera), ctypes.c_int32, ctypes.c_int32,
+                                                 ctypes.c_int32, P, ctypes.c_int32, P, P, P, P]),
 }
 NOALLOC_MAX_INSTANCES = 1 << 20
 NOALLOC_MAX_TILES = 1 << 16

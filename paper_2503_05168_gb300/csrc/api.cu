@@ -49,7 +49,7 @@ struct seele_ctx {
 
     // frame workspace
     DevBuf rec, rect, tiles, blocks, depth, visk[2], visv[2], offs, instk[2], instv[2], instm[2], ranges, msum,
-        border, chunkv, chunks, status, hist, lookback, T, nc, rgb_tmp, sortcnt, grad_rec;
+        border, chunkv, chunks, vbuf, status, hist, lookback, T, nc, rgb_tmp, sortcnt, grad_rec;
     size_t lookback_entries = 0;
     DeviceStatus* h_status = nullptr;  // pinned mirror of the device status
     cudaEvent_t ev[SEELE_NUM_STAGES + 1] = {};
@@ -85,6 +85,12 @@ struct seele_ctx {
     uint32_t n_units_total = 0;   // list units: tiles, or tile blocks with block binning
     uint64_t n_pix_total = 0;
     FrameParams last_fp{};
+
+    // view-representation builder: while set, frames end in the top-k
+    // contributor pass instead of the rasterizer
+    int topk_k = 0;
+    const int* topk_cluster = nullptr;   // device, cluster of each camera of the frame
+    uint32_t* topk_mask = nullptr;       // device, [n]
 };
 
 namespace {
@@ -517,7 +523,13 @@ seele_status enqueue_frame(seele_ctx* c, const seele_options* opt, const FrameIn
     ra.view_end = vt + 1;
     ra.view_done = reinterpret_cast<uint32_t*>(vt + 1 + ncam);
     SEELE_MARK(SEELE_STAGE_RASTER);
-    if (!launch_raster_fwd(ra, s)) return fail(c, SEELE_ERR_ARG, "no rasterizer for these options");
+    if (c->topk_k > 0) {
+        if (!launch_topk(ra.starts, ra.ends, ra.inst_rec, ra.rec, cams, ncam, ra.n_tiles, f.fp, c->topk_k,
+                         c->topk_cluster, c->topk_mask, s))
+            return fail(c, SEELE_ERR_ARG, "no top-k pass for these options");
+    } else if (!launch_raster_fwd(ra, s)) {
+        return fail(c, SEELE_ERR_ARG, "no rasterizer for these options");
+    }
     SEELE_LAUNCHED(c);
     ++launches;
     SEELE_MARK(SEELE_NUM_STAGES);
@@ -579,7 +591,9 @@ void seele_destroy(seele_ctx* c) {
     DevBuf* all[] = {&c->pos_logit, &c->quat, &c->log_scale, &c->sh, &c->mask, &c->staging, &c->cams_dev,
                      &c->rec, &c->rect, &c->tiles, &c->depth, &c->visk[0], &c->visk[1], &c->visv[0],
                      &c->visv[1], &c->offs, &c->instk[0], &c->instk[1], &c->instv[0], &c->instv[1],
-                     &c->ranges, &c->status, &c->hist, &c->lookback, &c->T, &c->nc, &c->rgb_tmp, &c->sortcnt, &c->grad_rec};
+                     &c->ranges, &c->status, &c->hist, &c->lookback, &c->T, &c->nc, &c->rgb_tmp, &c->sortcnt,
+                     &c->grad_rec, &c->blocks, &c->instm[0], &c->instm[1], &c->msum, &c->border, &c->chunkv,
+                     &c->chunks, &c->vbuf};
     for (DevBuf* b : all) release(*b);
     release(c->viewt);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -994,6 +1008,96 @@ seele_status seele_get_debug_view(const seele_ctx* c, seele_debug_view* out) {
     out->records = ptr<const float>(m->rec);
     out->depth = ptr<const float>(m->depth);
     out->n_contrib = ptr<const uint32_t>(m->nc);
+    return SEELE_OK;
+}
+
+seele_status seele_build_view_clusters(seele_ctx* c, const seele_camera* poses, int32_t n_poses, int32_t n_clusters,
+                                       int32_t top_k, const double* uniforms, int32_t max_iter, float* out_centroids,
+                                       float* out_pos_scale, uint32_t* out_mask, int32_t* out_assign) {
+    if (!c) return SEELE_ERR_ARG;
+    if (!c->has_scene) return fail(c, SEELE_ERR_STATE, "no scene loaded");
+    if (!poses || !uniforms || !out_centroids || !out_pos_scale || !out_mask)
+        return fail(c, SEELE_ERR_ARG, "poses, uniforms and the outputs are required");
+    if (n_clusters < 1 || n_clusters > 32 || n_poses < n_clusters)
+        return fail(c, SEELE_ERR_ARG, "need 1 <= n_clusters <= 32 and n_poses >= n_clusters");
+    if (top_k < 1 || top_k > 64) return fail(c, SEELE_ERR_ARG, "top_k must be in [1, 64]");
+    if (max_iter < 0) return fail(c, SEELE_ERR_ARG, "max_iter must be >= 0");
+    for (int j = 0; j < n_clusters; ++j)
+        if (!(uniforms[j] >= 0.0 && uniforms[j] < 1.0)) return fail(c, SEELE_ERR_ARG, "uniforms must lie in [0, 1)");
+    for (int i = 0; i < n_poses; ++i)
+        if (poses[i].width < 1 || poses[i].height < 1 || poses[i].width > 16384 || poses[i].height > 16384)
+            return fail(c, SEELE_ERR_ARG, "pose %d: bad image size", i);
+    SEELE_CUDA(c, cudaSetDevice(c->device));
+    cudaStream_t s = c->stream;
+
+    // pose features (x / s, v), s = the largest camera distance of the samples
+    std::vector<double> feat(6 * (size_t)n_poses);
+    double scale = 0.0;
+    for (int i = 0; i < n_poses; ++i) {
+        const float* w = poses[i].world_to_cam;
+        const double R[9] = {w[0], w[1], w[2], w[4], w[5], w[6], w[8], w[9], w[10]};
+        const double t[3] = {w[3], w[7], w[11]};
+        for (int a = 0; a < 3; ++a) feat[6 * i + a] = -(R[a] * t[0] + R[3 + a] * t[1] + R[6 + a] * t[2]);
+        for (int a = 0; a < 3; ++a) feat[6 * i + 3 + a] = R[6 + a];
+        scale = std::max(scale, std::sqrt(feat[6 * i] * feat[6 * i] + feat[6 * i + 1] * feat[6 * i + 1] +
+                                          feat[6 * i + 2] * feat[6 * i + 2]));
+    }
+    if (!(scale > 0.0)) return fail(c, SEELE_ERR_ARG, "every pose sits at the origin");
+    for (int i = 0; i < n_poses; ++i)
+        for (int a = 0; a < 3; ++a) feat[6 * i + a] /= scale;
+
+    // device layout: features, uniforms, centroids, assignment, seeding scratch,
+    // iteration count, then the per-camera clusters of a batch and the mask
+    const size_t nf = 6 * (size_t)n_poses, nk = (size_t)n_clusters;
+    const size_t off_u = 8 * nf, off_c = off_u + 8 * nk, off_a = off_c + 48 * nk;
+    const size_t off_d = off_a + 8 * (size_t)n_poses, off_it = off_d + 8 * (size_t)n_poses;
+    const size_t off_cl = off_it + 16, off_m = off_cl + 4 * (size_t)kMaxCams + 256;
+    SEELE_CUDA(c, ensure(c->vbuf, off_m + 4 * (size_t)c->n + 16));
+    unsigned char* vb = static_cast<unsigned char*>(c->vbuf.p);
+    SEELE_CUDA(c, cudaMemcpyAsync(vb, feat.data(), 8 * nf, cudaMemcpyHostToDevice, s));
+    SEELE_CUDA(c, cudaMemcpyAsync(vb + off_u, uniforms, 8 * nk, cudaMemcpyHostToDevice, s));
+    launch_kmeans(reinterpret_cast<double*>(vb), n_poses, n_clusters, reinterpret_cast<double*>(vb + off_u),
+                  max_iter, reinterpret_cast<double*>(vb + off_c), reinterpret_cast<int*>(vb + off_a),
+                  reinterpret_cast<double*>(vb + off_d), reinterpret_cast<int*>(vb + off_it), s);
+    SEELE_LAUNCHED(c);
+    std::vector<double> cent(6 * nk);
+    std::vector<int> assign(n_poses);
+    SEELE_CUDA(c, cudaMemcpyAsync(cent.data(), vb + off_c, 48 * nk, cudaMemcpyDeviceToHost, s));
+    SEELE_CUDA(c, cudaMemcpyAsync(assign.data(), vb + off_a, 4 * (size_t)n_poses, cudaMemcpyDeviceToHost, s));
+    SEELE_CUDA(c, cudaStreamSynchronize(s));
+
+    // top-k contributors of every pose, a batch of cameras per frame
+    uint32_t* mask = reinterpret_cast<uint32_t*>(vb + off_m);
+    int* cl = reinterpret_cast<int*>(vb + off_cl);
+    SEELE_CUDA(c, cudaMemsetAsync(mask, 0, 4 * (size_t)c->n, s));
+    std::vector<seele_camera> saved = c->cams;
+    seele_options o;
+    seele_default_options(&o);
+    o.binning = SEELE_BIN_TILES;
+    seele_status result = SEELE_OK;
+    const int batch = 32;
+    for (int b0 = 0; b0 < n_poses && result == SEELE_OK; b0 += batch) {
+        const int nb = std::min(batch, n_poses - b0);
+        c->cams.assign(poses + b0, poses + b0 + nb);
+        uint64_t pix = 0;
+        for (int i = 0; i < nb; ++i) pix += (uint64_t)poses[b0 + i].width * poses[b0 + i].height;
+        SEELE_CUDA(c, cudaMemcpyAsync(cl, assign.data() + b0, 4 * (size_t)nb, cudaMemcpyHostToDevice, s));
+        SEELE_CUDA(c, ensure(c->rgb_tmp, 12 * pix));
+        c->topk_k = top_k;
+        c->topk_cluster = cl;
+        c->topk_mask = mask;
+        result = seele_render(c, &o, ptr<float>(c->rgb_tmp), nullptr, nullptr);
+        c->topk_k = 0;
+    }
+    c->cams = saved;
+    c->rendered = false;
+    if (result != SEELE_OK) return result;
+    SEELE_CUDA(c, cudaMemcpyAsync(out_mask, mask, 4 * (size_t)c->n, cudaMemcpyDefault, s));
+    SEELE_CUDA(c, cudaStreamSynchronize(s));
+    for (size_t i = 0; i < 6 * nk; ++i) out_centroids[i] = (float)cent[i];
+    *out_pos_scale = (float)scale;
+    if (out_assign)
+        for (int i = 0; i < n_poses; ++i) out_assign[i] = assign[i];
     return SEELE_OK;
 }
 

@@ -64,6 +64,15 @@ void launch_mask_summary(const uint32_t* mask, const DeviceStatus* st, uint32_t*
 void launch_block_order(const uint32_t* bstart, const uint32_t* bend, uint32_t n_blocks, uint32_t* order,
                         cudaStream_t s);
 
+// Offline view-dependent representation (views.cu).  k-means of n 6-D
+// double points (one CTA); top-k contributors of a frame's tile lists ORed
+// into the per-Gaussian cluster mask.
+void launch_kmeans(const double* x, int n, int k, const double* u, int max_iter, double* cent, int* assign,
+                   double* scratch, int* iters, cudaStream_t s);
+bool launch_topk(const uint32_t* starts, const uint32_t* ends, const uint32_t* inst_rec, const float4* rec,
+                 const CamDev* cams, int n_cams, uint32_t n_tiles, const FrameParams& fp, int k,
+                 const int* cam_cluster, uint32_t* mask, cudaStream_t s);
+
 struct RasterArgs {
     const uint32_t* starts;     // [n_units]: unit u's list is [starts[u], ends[u]) (empty if start >= end);
     const uint32_t* ends;       //   units are tiles, or tile blocks with block binning

@@ -1,0 +1,117 @@
+"""The offline view-dependent representation on the GPU
+(seele_build_view_clusters) against the FP64 oracle: k-means of the pose
+features, the per-Gaussian cluster masks from per-pixel top-k contributors,
+and a render that consumes the built representation (Sec. 3.3)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import scenegen
+from tests import parity
+from tests.scene_helpers import scene
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Renderer():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2503_05168_gb300 import Renderer as R
+    return R
+
+
+def _narrow_views(seed=5, n=90):
+    rs = np.random.default_rng(seed)
+    s = scene(rs.uniform(-1, 1, (n, 3)) * [2.0, 0.5, 0.5] + [0, 0, 4],
+              log_scales=rs.normal(math.log(0.12), 0.3, (n, 3)), quats=rs.standard_normal((n, 4)),
+              opacity=rs.uniform(0.1, 0.95, n), dc=rs.uniform(-1, 1, (n, 3)))
+    s = {k: (v.astype(np.float32) if isinstance(v, np.ndarray) and v.dtype == np.float64 else v) for k, v in s.items()}
+    poses = [scenegen.look_at(rs.normal(0, 0.05, 3), (tx, 0, 4), 24, 20, fov_y_deg=25.0)
+             for tx in (-1.5, -1.2, -0.9, 0.0, 0.3, 0.6, 0.9, 1.2, 1.5)]
+    return s, poses
+
+
+def test_kmeans_matches_oracle(Renderer):
+    s, _ = _narrow_views()
+    poses = scenegen.sample_poses(96, 4.0, 16, 12, np.random.default_rng(3))
+    u = scenegen.kmeans_uniforms(6, np.random.default_rng(4))
+    r = Renderer()
+    r.load_scene(s)
+    out = r.build_view_clusters(poses, n_clusters=6, top_k=8, uniforms=u)
+    scale = oracle.position_scale(poses)
+    assert abs(out["pos_scale"] - scale) <= 1e-6 * scale
+    cent, assign, _ = oracle.kmeans(oracle.pose_features(poses, scale), 6, u)
+    np.testing.assert_array_equal(out["assign"], assign)
+    np.testing.assert_allclose(out["centroids"], cent, rtol=0, atol=1e-6)  # returned as float32
+    r.close()
+
+
+@pytest.mark.parametrize("k", [4, 64])
+def test_cluster_masks_match_oracle(Renderer, k):
+    s, poses = _narrow_views()
+    assign = np.array([0, 0, 0, 1, 1, 1, 2, 2, 2], np.int32)
+    r = Renderer()
+    r.load_scene(s)
+    # fixed seeds on well separated poses make the clustering the expected one
+    feats = oracle.pose_features(poses, oracle.position_scale(poses))
+    u = np.array([0.05, 0.5, 0.95])
+    cent, a_or, _ = oracle.kmeans(feats, 3, u)
+    out = r.build_view_clusters(poses, n_clusters=3, top_k=k, uniforms=u)
+    np.testing.assert_array_equal(out["assign"], a_or)
+    mask, gmargin = oracle.view_masks(oracle.Scene64.from_scene(s), poses, a_or, k)
+    diff = out["mask"] != mask
+    # a Gaussian may flip only where its membership rests on an FP32 decision
+    # or a top-k tie within 1e-4 of the FP64 one
+    assert np.all(gmargin[diff] < 1e-4), (np.nonzero(diff)[0], gmargin[diff])
+    assert diff.mean() <= 0.02
+    assert np.count_nonzero(mask) > 0
+    r.close()
+
+
+def test_built_representation_drives_the_cluster_filter(Renderer):
+    """Clusters built from 64 sampled poses of a 20k-Gaussian clustered scene
+    (8 clusters, k = 32): the masks agree with the oracle's, and rendering an
+    orbit view through them matches the oracle's render of the same
+    representation."""
+    sc, cams = scenegen.clusters_500k(n=20_000, width=160, height=90, n_cams=2)
+    for key in ("cluster_mask", "centroids", "pos_scale"):
+        sc.pop(key)
+    poses = scenegen.sample_poses(64, 4.0, 80, 45, np.random.default_rng(11))
+    u = scenegen.kmeans_uniforms(8, np.random.default_rng(12))
+    r = Renderer()
+    r.load_scene(sc)
+    out = r.build_view_clusters(poses, n_clusters=8, top_k=32, uniforms=u)
+    s64 = oracle.Scene64.from_scene(sc)
+    mask, gmargin = oracle.view_masks(s64, poses, out["assign"], 32, nthreads=8)
+    diff = out["mask"] != mask
+    assert diff.mean() <= 2e-3 and np.all(gmargin[diff] < 1e-3), (diff.sum(), np.sort(gmargin[diff])[-5:])
+    assert 0 < np.count_nonzero(out["mask"]) < sc["means"].shape[0]
+    rep = dict(sc, cluster_mask=out["mask"], centroids=out["centroids"], pos_scale=out["pos_scale"])
+    r.load_scene(rep)
+    r.set_cameras(cams)
+    imgs, _ = parity.gpu_render(r, mode="cr", cluster_filter=True, opacity_filter=True)
+    rep64 = oracle.Scene64.from_scene(rep)
+    for ci, cam in enumerate(cams):
+        sel = oracle.select_clusters(rep64.centroids, rep64.pos_scale, cam, 3)
+        ref = oracle.render(rep64, cam, parity.oracle_options("cr", opacity_filter=True, cluster_filter=True,
+                                                              sel_bits=sel), nthreads=8)[0]
+        ok, rep_ = parity.compare_images(imgs[ci], ref.rgb, ref.margin)
+        assert ok, (ci, rep_)
+    r.close()
+
+
+def test_builder_rejects_bad_arguments(Renderer):
+    from paper_2503_05168_gb300 import SeeleError
+    s, poses = _narrow_views()
+    r = Renderer()
+    r.load_scene(s)
+    for kw in (dict(n_clusters=0), dict(n_clusters=33), dict(top_k=0), dict(top_k=65),
+               dict(n_clusters=3, uniforms=[0.1, 1.0, 0.2])):
+        with pytest.raises(SeeleError):
+            r.build_view_clusters(poses, **kw)
+    with pytest.raises(SeeleError):
+        r.build_view_clusters(poses[:2], n_clusters=3)
+    r.close()
