@@ -176,6 +176,21 @@ def cpu_baseline(scene, cams, bands=4, nthreads=None):
                       f"{bands} horizontal bands by the FP64 C oracle with OpenMP; {total:.1f} s"}
 
 
+def cpu_baseline_views(n_gauss: int, poses: int = 2):
+    """The FP64 oracle building the view representation's masks for a bounded
+    sample of the poses the GPU builder processes (same scene, same 320x180
+    poses), in seconds per pose on all host cores."""
+    import oracle
+    import scenegen
+    scene, _ = scenegen.clusters_500k(n=n_gauss)
+    s64 = oracle.Scene64.from_scene(scene)
+    sample = scenegen.sample_poses(512, 4.0, 320, 180, scenegen.rng(7))[:poses]
+    t0 = time.perf_counter()
+    oracle.view_masks(s64, sample, np.zeros(poses, np.int32), 32, nthreads=os.cpu_count())
+    return {"s_per_pose": (time.perf_counter() - t0) / poses, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{poses} of the 512 poses (320x180, top-32 contributors), {n_gauss} Gaussians"}
+
+
 def run_reference(args):
     rank, _, ws, dist = _dist()
     if rank != 0:
@@ -319,17 +334,6 @@ def _ablation(args, device):
         "kept_fraction": float(np.count_nonzero(rep["mask"]) / n),
         "shared_fraction": float(np.count_nonzero((rep["mask"] & full_bits) == full_bits) / n),
         "what": "seele_build_view_clusters: pose k-means + per-pixel top-k contributor pass over all poses"}
-    # the oracle doing the same for a bounded sample of the poses
-    try:
-        import oracle
-        s64 = oracle.Scene64.from_scene(scene)
-        t0 = time.perf_counter()
-        oracle.view_masks(s64, poses[:2], rep["assign"][:2], 32, nthreads=os.cpu_count())
-        representation["oracle_s_per_pose"] = (time.perf_counter() - t0) / 2
-        representation["oracle_cores"] = os.cpu_count()
-    except Exception as exc:  # the CPU oracle is optional context here
-        representation["oracle_s_per_pose"] = None
-        representation["oracle_error"] = str(exc)[:120]
     scene.update(cluster_mask=rep["mask"], centroids=rep["centroids"], pos_scale=rep["pos_scale"])
     r.load_scene(scene)
     variants = {
@@ -371,6 +375,63 @@ def _ablation(args, device):
                        f"GPU from 512 sampled poses (nearest + 3 neighbours at render time), 8 orbit cameras at r 4, "
                        f"1280x720, mean over the cameras")
     out["representation"] = representation
+    r.close()
+    return out
+
+
+def _sensitivity(args, device):
+    """Sensitivity sweeps of Sec. 4.4 on the clustered scene: number of view
+    clusters x cluster neighbours M, and the number of primary contributors k
+    of the offline representation (each point rebuilt on the GPU); frames/s
+    of the full path (CR + both filters) and PSNR against the plain render of
+    all Gaussians, mean over the 8 orbit cameras."""
+    import torch
+
+    import scenegen
+    from paper_2503_05168_gb300 import Renderer
+
+    scene, cams = scenegen.clusters_500k(n=args.ablation_n)
+    for key in ("cluster_mask", "centroids", "pos_scale"):
+        scene.pop(key)
+    r = Renderer(device)
+    r.load_scene(scene)
+    refs = []
+    for c in cams:
+        r.set_cameras([c])
+        refs.append(r.render(mode="plain").clone())
+    poses = scenegen.sample_poses(512, 4.0, 320, 180, scenegen.rng(7))
+
+    def point(n_clusters, k, M):
+        rep = r.build_view_clusters(poses, n_clusters=n_clusters, top_k=k,
+                                    uniforms=scenegen.kmeans_uniforms(n_clusters, scenegen.rng(8)))
+        r.load_scene(dict(scene, cluster_mask=rep["mask"], centroids=rep["centroids"], pos_scale=rep["pos_scale"]))
+        kw = dict(mode="cr", opacity_filter=True, cluster_filter=True, n_neighbors=M)
+        imgs = []
+        for c in cams:
+            r.set_cameras([c])
+            imgs.append(r.render(**kw).clone())
+        mse = float(np.mean([torch.mean((a - b) ** 2).item() for a, b in zip(imgs, refs)]))
+        opts = r.make_options(sync=False, **kw)
+        reps = 4
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        for i in range(reps * len(cams)):
+            r.set_cameras([cams[i % len(cams)]])
+            r.render(options=opts)
+        e.record()
+        r.synchronize()
+        return {"fps": 1000.0 * reps * len(cams) / s.elapsed_time(e),
+                "psnr_vs_plain_db": 10 * math.log10(1.0 / mse) if mse > 0 else None,
+                "kept_fraction": float(np.count_nonzero(rep["mask"]) / scene["means"].shape[0])}
+
+    out = {"clusters_x_neighbours": {}, "top_k": {}}
+    for n_clusters in (8, 16, 24):
+        for M in (1, 3):
+            out["clusters_x_neighbours"][f"{n_clusters}x{M}"] = point(n_clusters, 32, M)
+    for k in (8, 16, 32, 64):
+        out["top_k"][str(k)] = point(16, k, 3)
+    out["workload"] = (f"clusters_500k: {args.ablation_n} Gaussians, 512 sampled poses at 320x180 per build, "
+                       f"8 orbit cameras at 1280x720; full path (CR + opacity and cluster filters)")
     r.close()
     return out
 
@@ -583,6 +644,7 @@ def run_gpu(args):
     fwd_bwd = _fwd_bwd(args, local)
     multiview = _multiview(args, local) if args.multiview_n > 0 else None
     ablation = _ablation(args, local) if args.ablation_n > 0 else None
+    sensitivity = _sensitivity(args, local) if args.ablation_n > 0 else None
 
     line = {
         "metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -599,7 +661,7 @@ def run_gpu(args):
         "stage_ms_plain": {k: round(v, 4) for k, v in stage_plain.items()},
         "n_visible": n_vis, "n_block_instances": K, "n_tile_instances": K_tiles, "raster_work": work,
         "roofline": roof, "stage_roofline_hbm": stage_roof,
-        "e2e": e2e, "fwd_bwd": fwd_bwd, "multiview": multiview, "ablation": ablation,
+        "e2e": e2e, "fwd_bwd": fwd_bwd, "multiview": multiview, "ablation": ablation, "sensitivity": sensitivity,
         "async_fps": fps_async,
         "gpu_launches": int(kernels_per_frame * args.steps),
         "clocks": clock_info,
@@ -610,6 +672,8 @@ def run_gpu(args):
                                       f"shell), SH degree 3, 1920x1080, 16x16 tiles, 8 orbit cameras at r 5, seed 0")
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(scene, cams)
+        if args.ablation_n > 0:
+            line["cpu_baseline"]["view_representation"] = cpu_baseline_views(args.ablation_n)
     if rank == 0:
         print(json.dumps(line), flush=True)
     r.close()
