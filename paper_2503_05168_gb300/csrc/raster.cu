@@ -178,7 +178,18 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
             // so the tests run back to back.  Phase 2: only the Gaussians the
             // leader kept are blended, in list order, by the group's pixels.
             if (live == 0u) continue;
-            for (int c0 = 0; c0 < cnt && live != 0u; c0 += 32) {
+            // the group's pixels' live flags as separate predicates for the
+            // blend loop (no bit extraction per pixel), folded back after it
+            bool alive[NP];
+#pragma unroll
+            for (int p = 0; p < NP; ++p) alive[p] = (live >> p) & 1u;
+            auto any_alive = [&]() {
+                bool a = false;
+#pragma unroll
+                for (int p = 0; p < NP; ++p) a = a || alive[p];
+                return a;
+            };
+            for (int c0 = 0; c0 < cnt && any_alive(); c0 += 32) {
             const int n32 = min(32, cnt - c0);
             uint32_t pass = 0;
 #pragma unroll
@@ -192,7 +203,7 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
                     pass |= e0 >= B.z ? 1u << i : 0u;
                 }
             }
-            while (pass != 0u && live != 0u) {
+            while (pass != 0u && any_alive()) {
                 const int k = c0 + __ffs(pass) - 1;
                 pass &= pass - 1u;
                 const float4 A = s0[k];
@@ -209,28 +220,30 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
 #pragma unroll
                     for (int i = 0; i < PW; ++i) {
                         const int p = jj * PW + i;
-                        const bool alive = (live >> p) & 1u;
-                        if (COUNT) n_eval += alive;
+                        if (COUNT) n_eval += alive[p];
                         const float ddx = dx + (float)i;
                         const float e = fmaf(fmaf(A.z, ddx, rb), ddx, rc);
-                        const bool on = alive && e >= B.z;  // per-pixel alpha_theta / support rule
+                        const bool on = alive[p] && e >= B.z;  // per-pixel alpha_theta / support rule
                         const float al = fminf(amax, ex2_approx(e));
                         const float wgt = al * T[p];
                         const float Tn = T[p] - wgt;  // T (1 - alpha)
                         const bool stop = on && Tn < tstop;
                         const bool take = on && !stop;
-                        live &= stop ? ~(1u << p) : 0xffffffffu;
+                        alive[p] = alive[p] && !stop;
                         const float w = take ? wgt : 0.f;
                         cr[p] = fmaf(w, Cc.x, cr[p]);
                         cg[p] = fmaf(w, Cc.y, cg[p]);
                         cb[p] = fmaf(w, Cc.z, cb[p]);
-                        T[p] = take ? Tn : T[p];
+                        T[p] = T[p] - w;  // Tn when taken (same rounding), else T
                         nc[p] = take ? pos1 : nc[p];
                         if (COUNT) n_blend += take;
                     }
                 }
             }
             }
+            live = 0u;
+#pragma unroll
+            for (int p = 0; p < NP; ++p) live |= (uint32_t)alive[p] << p;
             continue;
         }
         for (int k = 0; k < cnt; ++k) {
