@@ -331,6 +331,8 @@ void fill_params(seele_ctx* c, const seele_options* opt, FrameInfo& f) {
     fp.binning = opt->binning == SEELE_BIN_BLOCKS ? 1 : 0;
     fp.use_mask = opt->cluster_filter ? 1 : 0;
     fp.alpha_min = opt->alpha_min;
+    fp.log_alpha_min = std::log(opt->alpha_min);
+    fp.log2_alpha_min = std::log2(opt->alpha_min);
     fp.alpha_max = opt->alpha_max;
     fp.t_stop = opt->t_stop;
     fp.dilation = 0.3f;

@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ 
             y0 = b.x >> 16;
             x1 = b.y & 0xffffu;
             rows = (b.y >> 16) - y0 + 1;
-            const CamDev& C = cams[r / (uint32_t)n_gauss];
+            const CamDev& C = cams[r < (uint32_t)n_gauss ? 0u : r / (uint32_t)n_gauss];
             tx_n = (uint32_t)C.tiles_x;
             row0 = C.tile_offset;
             if (ellipse) {
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(256) emit_blocks_kernel(const uint32_t* __rest
         const uint2 bx2 = __ldg(rect + r);
         const int x0 = (int)(bx2.x & 0xffffu), y0 = (int)(bx2.x >> 16);
         const int x1 = (int)(bx2.y & 0xffffu), y1 = (int)(bx2.y >> 16);
-        const CamDev& C = cams[r / (uint32_t)n_gauss];
+        const CamDev& C = cams[r < (uint32_t)n_gauss ? 0u : r / (uint32_t)n_gauss];
         const uint32_t boff = C.block_offset, bx_n = (uint32_t)C.blocks_x;
         Ellipse E;
         if (ellipse) E = make_ellipse(__ldg(rec + 3 * (size_t)r), __ldg(rec + 3 * (size_t)r + 1));

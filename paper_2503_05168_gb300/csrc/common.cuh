@@ -73,6 +73,7 @@ struct FrameParams {
     int32_t binning;         // 0: tile instances, 1: tile-block instances with tile masks
     int32_t use_mask;
     float alpha_min, alpha_max, t_stop;
+    float log_alpha_min, log2_alpha_min;  // ln and log2 of alpha_min
     float dilation;
     float frustum_slack;
     uint32_t n_tiles_total;

@@ -105,15 +105,17 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev sc, const CamD
         const float Y = fmaf(C.R[3], pl.x, fmaf(C.R[4], pl.y, fmaf(C.R[5], pl.z, C.t[1])));
         const float Z = fmaf(C.R[6], pl.x, fmaf(C.R[7], pl.y, fmaf(C.R[8], pl.z, C.t[2])));
         if (!(Z > C.near_z)) break;
-        const float xz = X / Z, yz = Y / Z;
+        const float iz = __frcp_rn(Z);
+        const float xz = X * iz, yz = Y * iz;
         if (fabsf(xz) > C.lim_x || fabsf(yz) > C.lim_y) break;
 
         // opacity and the support threshold t_g (Eqn. 3, or Eqn. 5 when filtering)
-        const float o = 1.f / (1.f + expf(-pl.w));
+        // (hardware exp/log/reciprocal: a few ulp, inside the FP32 margins)
+        const float o = __frcp_rn(1.f + __expf(-pl.w));
         float tg = 9.f;
         if (fp.opacity_filter) {
             if (!(o > fp.alpha_min)) break;
-            tg = fminf(2.f * logf(o / fp.alpha_min), 9.f);
+            tg = fminf(2.f * (__logf(o) - fp.log_alpha_min), 9.f);
         }
 
         // Sigma' = J W R S (J W R S)^T + dilation: build N = J W R S (2x3)
@@ -121,7 +123,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev sc, const CamD
         const float qinv = rsqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
         const float qw = q4.x * qinv, qx = q4.y * qinv, qy = q4.z * qinv, qz = q4.w * qinv;
         const float4 ls = __ldg(sc.log_scale + g);
-        const float s0 = expf(ls.x), s1 = expf(ls.y), s2 = expf(ls.z);
+        const float s0 = __expf(ls.x), s1 = __expf(ls.y), s2 = __expf(ls.z);
         float M[9];  // R(q) diag(s)
         M[0] = (1.f - 2.f * (qy * qy + qz * qz)) * s0;
         M[1] = 2.f * (qx * qy - qw * qz) * s1;
@@ -138,7 +140,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev sc, const CamD
 #pragma unroll
             for (int j = 0; j < 3; ++j)
                 WM[3 * i + j] = fmaf(C.R[3 * i + 0], M[j], fmaf(C.R[3 * i + 1], M[3 + j], C.R[3 * i + 2] * M[6 + j]));
-        const float jx = C.fx / Z, jy = C.fy / Z;
+        const float jx = C.fx * iz, jy = C.fy * iz;
         float N0[3], N1[3];
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
@@ -150,7 +152,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev sc, const CamD
         const float c = fmaf(N1[0], N1[0], fmaf(N1[1], N1[1], N1[2] * N1[2])) + fp.dilation;
         const float det = det2_sym(a, b, c);
         if (!(det > 0.f)) break;
-        const float inv = 1.f / det;
+        const float inv = __frcp_rn(det);
 
         const float u = fmaf(C.fx, xz, C.cx);
         const float v = fmaf(C.fy, yz, C.cy);
@@ -166,14 +168,15 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev sc, const CamD
         fx1 = fminf(fx1, (float)(C.W - 1));
         fy1 = fminf(fy1, (float)(C.H - 1));
         if (fx0 > fx1 || fy0 > fy1) break;
-        const int tx0 = (int)fx0 / fp.tile_w, tx1 = (int)fx1 / fp.tile_w;
-        const int ty0 = (int)fy0 / fp.tile_h, ty1 = (int)fy1 / fp.tile_h;
+        const int sw = __ffs(fp.tile_w) - 1, sh = __ffs(fp.tile_h) - 1;  // tile sizes are powers of two
+        const int tx0 = (int)fx0 >> sw, tx1 = (int)fx1 >> sw;
+        const int ty0 = (int)fy0 >> sh, ty1 = (int)fy1 >> sh;
 
         // raster record: exponent e = log2(o) - q log2(e) / 2 and one threshold
         // for "inside the support and alpha >= alpha_theta" (both are e >= bound);
         // the last slot holds the tile test's bound on -(cA dx^2 + cB dx dy + cC dy^2)
-        const float lo = log2f(o);
-        const float thr = fmaxf(fmaf(-0.5f * kLog2e, tg, lo), log2f(fp.alpha_min));
+        const float lo = __log2f(o);
+        const float thr = fmaxf(fmaf(-0.5f * kLog2e, tg, lo), fp.log2_alpha_min);
         const float4 rec0 = make_float4(u, v, -0.5f * kLog2e * c * inv, kLog2e * b * inv);
         const float4 rec1 = make_float4(-0.5f * kLog2e * a * inv, lo, thr,
                                         __fmul_rn(tg, 0.5f * kLog2e * (1.f + kTileInflate)));
