@@ -111,3 +111,34 @@ def test_view_times_and_autotune(Renderer):
     t = r.view_times()
     assert len(t) == len(cams) and all(v > 0 for v in t) and max(t) < 1000
     r.close()
+
+
+@pytest.mark.parametrize("binning", ["blocks", "tiles"])
+def test_wide_batches_take_32_bit_unit_keys(Renderer, binning):
+    """520 cameras of 16384x16 make 532,480 tiles and 66,560 tile blocks in one
+    frame: unit ids no longer fit 16-bit keys and the unit sort takes 3 passes.
+    Sampled cameras of the batch equal their single-camera renders (16-bit
+    keys, one or two passes) bit for bit."""
+    import torch
+    sc, _ = scenegen.uniform_10k(n=4000)
+    rs = np.random.default_rng(9)
+    cams = []
+    for i in range(520):
+        eye = (rs.uniform(-0.5, 0.5), rs.uniform(-0.3, 0.3), -3.0)
+        c = scenegen.look_at(eye, (0, 0, 0), 16384, 16)
+        c["fx"] = c["fy"] = 4000.0
+        cams.append(c)
+    r = Renderer()
+    r.load_scene(sc)
+    r.set_cameras(cams)
+    flat = r.render(mode="cr", binning=binning)
+    torch.cuda.synchronize()
+    assert r.last_stats["n_instances"] > 0
+    per = 3 * 16384 * 16
+    for i in (0, 259, 519):
+        batch = flat[i * per:(i + 1) * per].cpu().numpy()
+        r.set_cameras([cams[i]])
+        single = r.render(mode="cr", binning=binning).cpu().numpy()
+        np.testing.assert_array_equal(batch, single)
+        assert np.count_nonzero(single) > 0
+    r.close()
