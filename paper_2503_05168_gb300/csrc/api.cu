@@ -49,7 +49,7 @@ struct seele_ctx {
 
     // frame workspace
     DevBuf rec, rect, tiles, blocks, depth, visk[2], visv[2], offs, instk[2], instv[2], instm[2], ranges, msum,
-        border, chunkv, chunks, vbuf, status, hist, lookback, T, nc, rgb_tmp, sortcnt, grad_rec;
+        border, chunkv, chunks, vbuf, status, hist, lookback, T, nc, rgb_tmp, sortcnt, grad_rec, cnts;
     size_t lookback_entries = 0;
     DeviceStatus* h_status = nullptr;  // pinned mirror of the device status
     cudaEvent_t ev[SEELE_NUM_STAGES + 1] = {};
@@ -361,6 +361,7 @@ seele_status size_frame(seele_ctx* c, FrameInfo& f) {
         SEELE_CUDA(c, ensure(c->border, 4 * f.blocks_total));
     }
     SEELE_CUDA(c, ensure(c->offs, 4 * R));
+    SEELE_CUDA(c, ensure(c->cnts, 4 * R));
     SEELE_CUDA(c, ensure(c->chunkv, 4 * (R / kChunkItems + 1)));
     SEELE_CUDA(c, ensure(c->chunks, 4 * (R / kChunkItems + 1)));
     SEELE_CUDA(c, ensure(c->ranges, 8 * f.units_total));  // starts[n_units], then ends[n_units]
@@ -468,7 +469,10 @@ seele_status enqueue_frame(seele_ctx* c, const seele_options* opt, const FrameIn
 
     // visible records -> (depth bits, id), then the stable depth sort
     SEELE_MARK(SEELE_STAGE_COMPACT);
-    launch_compact_visible(po.tiles, po.depth, (uint32_t)R, po.chunk_vis, ptr<uint32_t>(c->visk[0]),
+    // with ids below 2^24 the sort values also carry the instance counts
+    const uint32_t* cnt_src = f.blocks ? po.blocks : po.tiles;
+    const bool packed = R <= (1ull << kPackedIdBits);
+    launch_compact_visible(cnt_src, packed, po.depth, (uint32_t)R, po.chunk_vis, ptr<uint32_t>(c->visk[0]),
                            ptr<uint32_t>(c->visv[0]), st, s);
     SEELE_LAUNCHED(c);
     ++launches;
@@ -479,16 +483,22 @@ seele_status enqueue_frame(seele_ctx* c, const seele_options* opt, const FrameIn
     {
         uint32_t* vk[2] = {ptr<uint32_t>(c->visk[0]), ptr<uint32_t>(c->visk[1])};
         uint32_t* vv[2] = {ptr<uint32_t>(c->visv[0]), ptr<uint32_t>(c->visv[1])};
-        // positive fp32 depths order like their bit patterns, sign bit clear: 31 bits
+        // positive fp32 depths order like their bit patterns, sign bit clear:
+        // 31 bits; the last pass also lays the records' instance counts out
+        // in depth order
+        SortGather gather;
+        gather.src = cnt_src;
+        gather.out = ptr<uint32_t>(c->cnts);
+        gather.packed = packed;
         if (radix_sort_pairs<uint32_t>(vk, vv, n_vis, (uint32_t)R, 31, false, scnt, soff, lb, c->epoch, st, 2,
-                                       launches, s) != 0)
+                                       launches, s, nullptr, nullptr, nullptr, &gather) != 0)
             return fail(c, SEELE_ERR_CUDA, "depth sort launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     }
     // sorted ids are back in buffer 0 after an even number of passes
     const uint32_t* order = ptr<uint32_t>(c->visv[0]);
     SEELE_MARK(SEELE_STAGE_TILE_SCAN);
-    launch_scan_tiles(f.blocks ? po.blocks : po.tiles, order, (uint32_t)R, ptr<uint32_t>(c->chunks),
-                      ptr<uint32_t>(c->offs), st, (uint32_t)std::min<uint64_t>(cap, 0xffffffffu), s);
+    launch_scan_tiles(ptr<uint32_t>(c->cnts), ptr<uint32_t>(c->chunks), (uint32_t)R, ptr<uint32_t>(c->offs), st,
+                      (uint32_t)std::min<uint64_t>(cap, 0xffffffffu), s);
     SEELE_LAUNCHED(c);
     launches += 2;
     const int emit_blocks = (int)std::max<uint64_t>(std::min<uint64_t>((R + 255) / 256, 8 * 152), 1);
@@ -595,7 +605,7 @@ void seele_destroy(seele_ctx* c) {
                      &c->visv[1], &c->offs, &c->instk[0], &c->instk[1], &c->instv[0], &c->instv[1],
                      &c->ranges, &c->status, &c->hist, &c->lookback, &c->T, &c->nc, &c->rgb_tmp, &c->sortcnt,
                      &c->grad_rec, &c->blocks, &c->instm[0], &c->instm[1], &c->msum, &c->border, &c->chunkv,
-                     &c->chunks, &c->vbuf};
+                     &c->chunks, &c->vbuf, &c->cnts};
     for (DevBuf* b : all) release(*b);
     release(c->viewt);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);

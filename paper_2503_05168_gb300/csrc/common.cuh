@@ -55,6 +55,10 @@ struct CamDev {
 // Records are counted in chunks of this many for the ordered compaction and
 // scans (a chunk is one CTA of those kernels).
 constexpr uint32_t kChunkItems = 4096;
+// Packed (record id, instance count) sort values: ids below 2^kPackedIdBits,
+// counts saturated at kPackedCountMax (the true count is then read again).
+constexpr int kPackedIdBits = 24;
+constexpr uint32_t kPackedCountMax = 255u;
 
 // Block binning: a tile block is kBlockW x kBlockH tiles; its instances carry a
 // 32-bit mask of the block's tiles that the Gaussian reaches (bit j * kBlockW + i
@@ -93,7 +97,7 @@ struct ProjOut {
     float4* rec;               // [3 * R]: (u, v, cA, cB), (cC, log2 o, e_thr, T_tile), (r, g, b, 0)
     uint2* rect;               // [R] tile box x0 | y0 << 16, x1 | y1 << 16
     uint32_t* tiles;           // [R] tiles touched (0 = culled)
-    uint32_t* blocks;          // [R] tile-block instances (block binning only, else unused)
+    uint32_t* blocks;          // [R] tile-block instances (0 = culled; block binning only, else unused)
     float* depth;              // [R] camera-space Z
     unsigned long long* t_frame;  // receives the frame's start time (%globaltimer, ns)
     uint32_t* chunk_vis;       // [ceil(R / kChunkItems)] visible records per chunk (cleared per frame)

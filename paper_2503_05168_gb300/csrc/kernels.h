@@ -16,12 +16,16 @@ void launch_preprocess(const SceneDev& sc, const CamDev* cams, const FrameParams
                        cudaStream_t s);
 
 uint32_t scan_tiles_per_launch();
-void launch_compact_visible(const uint32_t* tiles, const float* depth, uint32_t R, const uint32_t* chunk_vis,
-                            uint32_t* keys, uint32_t* vals, DeviceStatus* st, cudaStream_t s);
-// Instance offsets of the depth-ordered records and K (capacity check);
+// cnt: per-record instance counts (0 = culled); pack: carry them in the
+// values' top bits (R <= 2^24).
+void launch_compact_visible(const uint32_t* cnt, bool pack, const float* depth, uint32_t R,
+                            const uint32_t* chunk_vis, uint32_t* keys, uint32_t* vals, DeviceStatus* st,
+                            cudaStream_t s);
+// Instance offsets of the depth-ordered records and K (capacity check):
+// cnt_sorted[j] is the instance count of the j-th record in depth order;
 // chunk_sum: scratch of ceil(max_n / kChunkItems) words.
-void launch_scan_tiles(const uint32_t* cnt, const uint32_t* order, uint32_t max_n, uint32_t* chunk_sum,
-                       uint32_t* offsets, DeviceStatus* st, uint32_t capacity, cudaStream_t s);
+void launch_scan_tiles(const uint32_t* cnt_sorted, uint32_t* chunk_sum, uint32_t max_n, uint32_t* offsets,
+                       DeviceStatus* st, uint32_t capacity, cudaStream_t s);
 
 void launch_exclusive_scan(const uint32_t* in, uint32_t n, uint32_t* out, uint64_t* status, uint32_t epoch,
                            DeviceStatus* st, int ticket, cudaStream_t s);
@@ -35,17 +39,29 @@ void launch_radix_downsweep_u32(const uint32_t* keys_in, const uint32_t* vals_in
                                 const uint32_t* offsets, uint32_t stride, uint32_t* run_start, uint32_t* run_end,
                                 cudaStream_t s);
 uint32_t radix_count_words(uint32_t max_n);
+// Last-pass counts: out[o] = the instance count of sorted record o.  packed:
+// the values carry the count in their top bits (kPackedIdBits; saturated
+// counts are read from src) and the pass writes bare record ids; otherwise
+// the count is src[value].
+struct SortGather {
+    const uint32_t* src = nullptr;
+    uint32_t* out = nullptr;
+    bool packed = false;
+};
 // Stable LSD sort of (keys[0], vals[0]) by their low `key_bits` bits in 8-bit
 // digits; returns the index of the buffer pair holding the result, or -1 on a
 // launch error.  With run_start / run_end (cleared to all-ones / zero, one
 // word per key value) the last pass also records [first, last + 1) of every
 // key value present -- the per-tile ranges.  With aux (two buffers, like vals)
-// a second 32-bit payload is permuted with the values.
+// a second 32-bit payload is permuted with the values.  With gather (and no
+// aux) the last pass also lays out the records' instance counts in sorted
+// order (SortGather).
 template <typename KeyT>
 int radix_sort_pairs(KeyT* keys[2], uint32_t* vals[2], const uint32_t* count_ptr, uint32_t max_n, int key_bits,
                      bool keys_after_last, uint32_t* counts, uint32_t* offsets, uint64_t* lookback,
                      uint32_t& epoch, DeviceStatus* st, int ticket, int& launches, cudaStream_t s,
-                     uint32_t* run_start = nullptr, uint32_t* run_end = nullptr, uint32_t* const* aux = nullptr);
+                     uint32_t* run_start = nullptr, uint32_t* run_end = nullptr, uint32_t* const* aux = nullptr,
+                     const SortGather* gather = nullptr);
 
 template <typename KeyT>
 void launch_emit(const uint32_t* order, const uint32_t* offsets, const uint2* rect, const float4* rec,

@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev sc, const CamD
     if (g >= fp.n) return;
     const size_t rid = (size_t)ci * fp.n + g;
     const CamDev& C = cams[ci];
-    uint32_t ntiles = 0;
+    uint32_t ntiles = 0, nblocks = 0;
     do {
         // view-cluster filter: selected clusters plus shared Gaussians (Sec. 3.3)
         if (fp.use_mask && (__ldg(sc.mask + g) & C.sel_bits) == 0u) break;
@@ -182,7 +182,6 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev sc, const CamD
                                         __fmul_rn(tg, 0.5f * kLog2e * (1.f + kTileInflate)));
         // tiles touched, and for block binning the tile-block instances: per
         // block row, the blocks spanned by the union of its tile rows' spans
-        uint32_t nblocks = 0;
         if (fp.tile_test) {
             const Ellipse E = make_ellipse(rec0, rec1);
             int cur = ty0 / kBlockH, blo = 1 << 30, bhi = -1;
@@ -206,7 +205,6 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev sc, const CamD
             ntiles = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
             nblocks = (uint32_t)((tx1 / kBlockW - tx0 / kBlockW + 1) * (ty1 / kBlockH - ty0 / kBlockH + 1));
         }
-        if (fp.binning) out.blocks[rid] = nblocks;
 
         // colour: SH in the direction from the camera centre to the mean
         float dxw = pl.x - C.campos[0], dyw = pl.y - C.campos[1], dzw = pl.z - C.campos[2];
@@ -235,6 +233,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev sc, const CamD
         out.depth[rid] = Z;
     } while (0);
     out.tiles[rid] = ntiles;
+    if (fp.binning) out.blocks[rid] = nblocks;  // > 0 exactly when ntiles > 0
     // visible records per 4096-record chunk (for the compaction); the valid
     // lanes of a warp are a prefix and hold consecutive records, so they span
     // at most two chunks

@@ -8,7 +8,9 @@
 //                   adds up its predecessors' counts directly.
 //  scan_tiles:      exclusive scan of the instance counts in depth order,
 //                   giving each visible record the start of its instances and
-//                   K; chunk sums first, then the same direct prefix.
+//                   K; the depth sort's last pass has laid the counts out in
+//                   depth order; chunk sums first, then each CTA adds up its
+//                   predecessors' sums directly.
 //  exclusive_scan:  generic single-pass scan with decoupled look-back: each
 //                   block takes a dynamic ticket (so every predecessor has
 //                   already started and will publish), reduces its tile,
@@ -143,8 +145,10 @@ __device__ __forceinline__ uint32_t warp_offset(uint32_t warp_total, uint32_t* b
 
 // Ordered compaction of chunk c: items are warp-striped (item k of lane l of
 // warp w is c * 4096 + w * 512 + 32 k + l), ranked by one ballot per k, and
-// placed after the visible records of all earlier chunks.
-__global__ void __launch_bounds__(kScanThreads) compact_visible_kernel(const uint32_t* __restrict__ tiles,
+// placed after the visible records of all earlier chunks.  A record is
+// visible when its instance count cnt[i] is not zero; with pack, each value
+// carries min(cnt[i], 255) in its top 8 bits (record ids < 2^24).
+__global__ void __launch_bounds__(kScanThreads) compact_visible_kernel(const uint32_t* __restrict__ cnt, int pack,
                                                                        const float* __restrict__ depth, uint32_t R,
                                                                        const uint32_t* __restrict__ chunk_vis,
                                                                        uint32_t* keys, uint32_t* vals,
@@ -154,11 +158,12 @@ __global__ void __launch_bounds__(kScanThreads) compact_visible_kernel(const uin
     const uint32_t prefix = chunk_prefix(chunk_vis, c);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t wbase = c * kChunkItems + (uint32_t)w * 32 * kScanItems;
-    uint32_t bal[kScanItems], wtot = 0;
+    uint32_t bal[kScanItems], cv[kScanItems], wtot = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
         const uint32_t i = wbase + 32 * k + lane;
-        bal[k] = __ballot_sync(0xffffffffu, i < R && __ldg(tiles + i) > 0u);
+        cv[k] = i < R ? __ldg(cnt + i) : 0u;
+        bal[k] = __ballot_sync(0xffffffffu, cv[k] > 0u);
         wtot += __popc(bal[k]);
     }
     uint32_t total;
@@ -170,7 +175,7 @@ __global__ void __launch_bounds__(kScanThreads) compact_visible_kernel(const uin
         if ((bal[k] >> lane) & 1u) {
             const uint32_t o = pos + __popc(bal[k] & lt);
             keys[o] = __float_as_uint(__ldg(depth + i));
-            vals[o] = i;
+            vals[o] = pack ? (i | (min(cv[k], kPackedCountMax) << kPackedIdBits)) : i;
         }
         pos += __popc(bal[k]);
     }
@@ -179,7 +184,6 @@ __global__ void __launch_bounds__(kScanThreads) compact_visible_kernel(const uin
 
 // Per chunk of 4096 depth-ordered records: the sum of their counts.
 __global__ void __launch_bounds__(kScanThreads) chunk_sums_kernel(const uint32_t* __restrict__ cnt,
-                                                                  const uint32_t* __restrict__ order,
                                                                   const DeviceStatus* __restrict__ st,
                                                                   uint32_t* __restrict__ chunk_sum) {
     __shared__ uint32_t s_part[kScanThreads / 32];
@@ -187,10 +191,15 @@ __global__ void __launch_bounds__(kScanThreads) chunk_sums_kernel(const uint32_t
     const uint32_t base = blockIdx.x * kChunkItems;
     if (base >= n) return;
     uint32_t v = 0;
+    if (base + kChunkItems <= n) {
+        const uint4* p4 = reinterpret_cast<const uint4*>(cnt + base) + threadIdx.x;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        const uint32_t j = base + k * kScanThreads + threadIdx.x;
-        if (j < n) v += __ldg(cnt + __ldg(order + j));
+        for (int q = 0; q < kScanItems / 4; ++q) {
+            const uint4 x = __ldg(p4 + q * kScanThreads);
+            v += x.x + x.y + x.z + x.w;
+        }
+    } else {
+        for (uint32_t j = base + threadIdx.x; j < n; j += kScanThreads) v += __ldg(cnt + j);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -207,7 +216,6 @@ __global__ void __launch_bounds__(kScanThreads) chunk_sums_kernel(const uint32_t
 // offsets), chunk by chunk after the sums of the earlier chunks; the last
 // chunk sets K and compares it with the capacity.
 __global__ void __launch_bounds__(kScanThreads) scan_tiles_kernel(const uint32_t* __restrict__ cnt,
-                                                                  const uint32_t* __restrict__ order,
                                                                   const uint32_t* __restrict__ chunk_sum,
                                                                   uint32_t* offsets, DeviceStatus* st,
                                                                   uint32_t capacity) {
@@ -228,7 +236,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_tiles_kernel(const uint32_t
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
         const uint32_t j = wbase + 32 * k + lane;
-        v[k] = j < n ? __ldg(cnt + __ldg(order + j)) : 0u;
+        v[k] = j < n ? __ldg(cnt + j) : 0u;
         wtot += v[k];
     }
 #pragma unroll
@@ -301,18 +309,19 @@ void launch_exclusive_scan(const uint32_t* in, uint32_t n, uint32_t* out, uint64
 
 uint32_t scan_tiles_per_launch() { return kScanTile; }
 
-void launch_compact_visible(const uint32_t* tiles, const float* depth, uint32_t R, const uint32_t* chunk_vis,
-                            uint32_t* keys, uint32_t* vals, DeviceStatus* st, cudaStream_t s) {
+void launch_compact_visible(const uint32_t* cnt, bool pack, const float* depth, uint32_t R,
+                            const uint32_t* chunk_vis, uint32_t* keys, uint32_t* vals, DeviceStatus* st,
+                            cudaStream_t s) {
     const uint32_t blocks = (R + kChunkItems - 1) / kChunkItems;
-    compact_visible_kernel<<<blocks > 0 ? blocks : 1, kScanThreads, 0, s>>>(tiles, depth, R, chunk_vis, keys, vals,
-                                                                            st);
+    compact_visible_kernel<<<blocks > 0 ? blocks : 1, kScanThreads, 0, s>>>(cnt, pack ? 1 : 0, depth, R, chunk_vis,
+                                                                            keys, vals, st);
 }
 
-void launch_scan_tiles(const uint32_t* cnt, const uint32_t* order, uint32_t max_n, uint32_t* chunk_sum,
-                       uint32_t* offsets, DeviceStatus* st, uint32_t capacity, cudaStream_t s) {
+void launch_scan_tiles(const uint32_t* cnt_sorted, uint32_t* chunk_sum, uint32_t max_n, uint32_t* offsets,
+                       DeviceStatus* st, uint32_t capacity, cudaStream_t s) {
     const uint32_t blocks = std::max<uint32_t>((max_n + kChunkItems - 1) / kChunkItems, 1u);
-    chunk_sums_kernel<<<blocks, kScanThreads, 0, s>>>(cnt, order, st, chunk_sum);
-    scan_tiles_kernel<<<blocks, kScanThreads, 0, s>>>(cnt, order, chunk_sum, offsets, st, capacity);
+    chunk_sums_kernel<<<blocks, kScanThreads, 0, s>>>(cnt_sorted, st, chunk_sum);
+    scan_tiles_kernel<<<blocks, kScanThreads, 0, s>>>(cnt_sorted, chunk_sum, offsets, st, capacity);
 }
 
 }  // namespace seele

@@ -7,12 +7,14 @@
 //   downsweep: each tile ranks its elements stably (warp match + per-warp
 //              counters), stages them in shared memory by digit and writes
 //              each digit's run contiguously.
-// No block waits on another inside the sort.  Ranking uses one warp ballot per
-// significant digit bit.  Used twice per frame: on the visible records keyed
-// by fp32 depth bits (31 bits, 4 passes) and on the tile instances keyed by
-// global tile id (16-bit keys when the frame has <= 65536 tiles); the last
-// pass of each writes values only.  Stability is what makes the two sorts
-// compose into the (tile, depth, record id) order of Sec. 3.1 "Sorting".
+// No block waits on another inside the sort.
+// Ranking uses one warp ballot per significant digit bit.  Used twice per
+// frame: on the visible records keyed by fp32 depth bits (31 bits, 4 passes)
+// and on the tile instances keyed by global tile id (16-bit keys when the
+// frame has <= 65536 tiles); the last pass of each writes values only.
+// Stability is what makes the two sorts compose into the (tile, depth,
+// record id) order of Sec. 3.1 "Sorting".  The depth sort's last pass also
+// lays out each record's instance count in depth order (SortGather).
 //
 // Element counts live on the device (they are produced by the previous
 // kernel), so grids are sized for the capacity and surplus tiles write
@@ -78,7 +80,8 @@ __global__ void __launch_bounds__(kSortThreads) downsweep_kernel(const KeyT* __r
                                                                  uint32_t stride, uint32_t* __restrict__ run_start,
                                                                  uint32_t* __restrict__ run_end,
                                                                  const uint32_t* __restrict__ aux_in,
-                                                                 uint32_t* __restrict__ aux_out) {
+                                                                 uint32_t* __restrict__ aux_out,
+                                                                 SortGather gather) {
     __shared__ KeyT s_keys[kSortTile];
     __shared__ uint32_t s_vals[kSortTile];
     __shared__ uint32_t s_wcount[kWarps][kRadix + 1];  // per-warp digit counters, then exclusive prefixes
@@ -162,13 +165,23 @@ __global__ void __launch_bounds__(kSortThreads) downsweep_kernel(const KeyT* __r
     }
     __syncthreads();
     const uint32_t tile_n = min((uint32_t)kSortTile, n - tile * kSortTile);
+    const bool counts = !AUX && gather.src != nullptr;
+    const bool packed = counts && gather.packed;
+    const uint32_t vmask = packed ? (1u << kPackedIdBits) - 1u : 0xffffffffu;
     for (uint32_t i = threadIdx.x; i < tile_n; i += kSortThreads) {
         const uint32_t k = s_keys[i];
         const uint32_t dg = (k >> shift) & 0xffu;
         const uint32_t o = s_global_base[dg] + (i - s_local_base[dg]);
         if (o < n) {
             if (WRITE_KEYS) keys_out[o] = (KeyT)k;
-            vals_out[o] = s_vals[i];
+            const uint32_t v = s_vals[i];
+            vals_out[o] = v & vmask;
+            if (counts) {
+                // the record's instance count: carried in the value, or read
+                uint32_t c = packed ? v >> kPackedIdBits : kPackedCountMax;
+                if (c == kPackedCountMax) c = __ldg(gather.src + (v & vmask));
+                gather.out[o] = c;
+            }
             // last pass: within a digit run the staged keys are in the lower
             // digits' sorted order, so equal whole keys are adjacent; each
             // block reports where its runs of a key begin and end
@@ -218,11 +231,11 @@ void launch_radix_downsweep_u32(const uint32_t* keys_in, const uint32_t* vals_in
     if (keys_out)
         downsweep_kernel<uint32_t, true, false><<<stride, kSortThreads, 0, s>>>(
             keys_in, vals_in, keys_out, vals_out, count_ptr, shift, nbits, offsets, stride, run_start, run_end,
-            nullptr, nullptr);
+            nullptr, nullptr, SortGather{});
     else
         downsweep_kernel<uint32_t, false, false><<<stride, kSortThreads, 0, s>>>(
             keys_in, vals_in, keys_out, vals_out, count_ptr, shift, nbits, offsets, stride, run_start, run_end,
-            nullptr, nullptr);
+            nullptr, nullptr, SortGather{});
 }
 
 uint32_t radix_count_words(uint32_t max_n) {
@@ -232,17 +245,17 @@ uint32_t radix_count_words(uint32_t max_n) {
 template <typename KeyT, bool WK, bool AUX>
 static void launch_downsweep(KeyT* keys[2], uint32_t* vals[2], uint32_t* const* aux, int a, int b,
                              const uint32_t* count_ptr, int shift, int nbits, const uint32_t* offsets, uint32_t stride,
-                             uint32_t* rs, uint32_t* re, cudaStream_t s) {
+                             uint32_t* rs, uint32_t* re, const SortGather& gather, cudaStream_t s) {
     downsweep_kernel<KeyT, WK, AUX><<<stride, kSortThreads, 0, s>>>(
         keys[a], vals[a], keys[b], vals[b], count_ptr, shift, nbits, offsets, stride, rs, re,
-        AUX ? aux[a] : nullptr, AUX ? aux[b] : nullptr);
+        AUX ? aux[a] : nullptr, AUX ? aux[b] : nullptr, gather);
 }
 
 template <typename KeyT>
 int radix_sort_pairs(KeyT* keys[2], uint32_t* vals[2], const uint32_t* count_ptr, uint32_t max_n, int key_bits,
                      bool keys_after_last, uint32_t* counts, uint32_t* offsets, uint64_t* lookback,
                      uint32_t& epoch, DeviceStatus* st, int ticket, int& launches, cudaStream_t s,
-                     uint32_t* run_start, uint32_t* run_end, uint32_t* const* aux) {
+                     uint32_t* run_start, uint32_t* run_end, uint32_t* const* aux, const SortGather* gather) {
     const uint32_t stride = std::max<uint32_t>((max_n + kSortTile - 1) / kSortTile, 1u);
     const int passes = std::max(1, (key_bits + 7) / 8);
     for (int p = 0; p < passes; ++p) {
@@ -251,19 +264,20 @@ int radix_sort_pairs(KeyT* keys[2], uint32_t* vals[2], const uint32_t* count_ptr
         const bool last = p == passes - 1;
         uint32_t* rs = last ? run_start : nullptr;
         uint32_t* re = last ? run_end : nullptr;
+        const SortGather g = (last && gather) ? *gather : SortGather{};
         upsweep_kernel<KeyT><<<stride, kSortThreads, 0, s>>>(keys[a], count_ptr, 8 * p, counts, stride);
         launch_exclusive_scan(counts, kRadix * stride, offsets, lookback, epoch++, st, ticket + p, s);
         const bool wk = !last || keys_after_last;
         if (aux) {
             if (wk) launch_downsweep<KeyT, true, true>(keys, vals, aux, a, b, count_ptr, 8 * p, nbits, offsets, stride,
-                                                        rs, re, s);
+                                                        rs, re, g, s);
             else launch_downsweep<KeyT, false, true>(keys, vals, aux, a, b, count_ptr, 8 * p, nbits, offsets, stride,
-                                                      rs, re, s);
+                                                      rs, re, g, s);
         } else {
             if (wk) launch_downsweep<KeyT, true, false>(keys, vals, aux, a, b, count_ptr, 8 * p, nbits, offsets,
-                                                         stride, rs, re, s);
+                                                         stride, rs, re, g, s);
             else launch_downsweep<KeyT, false, false>(keys, vals, aux, a, b, count_ptr, 8 * p, nbits, offsets,
-                                                       stride, rs, re, s);
+                                                       stride, rs, re, g, s);
         }
         if (cudaPeekAtLastError() != cudaSuccess) return -1;
         launches += 3;
@@ -272,9 +286,9 @@ int radix_sort_pairs(KeyT* keys[2], uint32_t* vals[2], const uint32_t* count_ptr
 }
 template int radix_sort_pairs<uint32_t>(uint32_t* [2], uint32_t* [2], const uint32_t*, uint32_t, int, bool,
                                         uint32_t*, uint32_t*, uint64_t*, uint32_t&, DeviceStatus*, int, int&,
-                                        cudaStream_t, uint32_t*, uint32_t*, uint32_t* const*);
+                                        cudaStream_t, uint32_t*, uint32_t*, uint32_t* const*, const SortGather*);
 template int radix_sort_pairs<uint16_t>(uint16_t* [2], uint32_t* [2], const uint32_t*, uint32_t, int, bool,
                                         uint32_t*, uint32_t*, uint64_t*, uint32_t&, DeviceStatus*, int, int&,
-                                        cudaStream_t, uint32_t*, uint32_t*, uint32_t* const*);
+                                        cudaStream_t, uint32_t*, uint32_t*, uint32_t* const*, const SortGather*);
 
 }  // namespace seele

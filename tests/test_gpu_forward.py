@@ -86,15 +86,19 @@ def _is_clear(s, cam, n):
     return np.min(np.diff(d)) > 4
 
 
-def _clear_tiny_scene(seed, n=48, W=64, H=48, f=50.0):
+def _clear_tiny_scene(seed, n=48, W=64, H=48, f=50.0, n_big=0):
     """Random tiny scene and two cameras with every rect, cull and depth-order
-    decision far from a rounding flip (re-drawn until so)."""
+    decision far from a rounding flip (re-drawn until so).  The first n_big
+    Gaussians are wide ones near the middle of the view."""
     rs = np.random.default_rng(seed)
     cam = camera(f=f, width=W, height=H)
     cam2 = dict(cam, world_to_cam=np.concatenate([np.eye(3), [[0.3], [0.1], [0.5]]], 1))
     for _ in range(500):
         means = rs.uniform(-1, 1, (n, 3)) * [1.0, 0.7, 1.0] + [0, 0, 4]
-        s = _f32(scene(means, log_scales=rs.normal(math.log(0.08), 0.4, (n, 3)), quats=rs.standard_normal((n, 4)),
+        log_scales = rs.normal(math.log(0.08), 0.4, (n, 3))
+        means[:n_big, :2] *= 0.2
+        log_scales[:n_big] = rs.normal(math.log(0.5), 0.1, (n_big, 3))
+        s = _f32(scene(means, log_scales=log_scales, quats=rs.standard_normal((n, 4)),
                        opacity=rs.uniform(0.05, 0.95, n), dc=rs.uniform(-1, 1, (n, 3))))
         if _is_clear(s, cam, n) and _is_clear(s, cam2, n):
             return s, [cam, cam2]
@@ -102,12 +106,15 @@ def _clear_tiny_scene(seed, n=48, W=64, H=48, f=50.0):
 
 
 @pytest.mark.parametrize("tile_test", ["ellipse", "rect"])
-@pytest.mark.parametrize("seed,size", [(0, (64, 48, 50.0)), (1, (64, 48, 50.0)), (2, (200, 120, 160.0)),
-                                       (3, (200, 120, 160.0))])
-def test_tile_lists_bit_exact(Renderer, seed, size, tile_test):
-    """Tile lists, their order and ranges equal the oracle's, bit for bit."""
+@pytest.mark.parametrize("seed,size,n_big", [(0, (64, 48, 50.0), 0), (1, (64, 48, 50.0), 0),
+                                             (2, (200, 120, 160.0), 0), (3, (200, 120, 160.0), 0),
+                                             (4, (480, 320, 400.0), 3)])
+def test_tile_lists_bit_exact(Renderer, seed, size, n_big, tile_test):
+    """Tile lists, their order and ranges equal the oracle's, bit for bit.  The
+    480x320 frames hold Gaussians spanning more than 255 tiles, whose counts
+    do not fit the count byte the depth sort carries with each record id."""
     W, H, f = size
-    s, cams = _clear_tiny_scene(seed, W=W, H=H, f=f)
+    s, cams = _clear_tiny_scene(seed, W=W, H=H, f=f, n_big=n_big)
     r = Renderer()
     r.load_scene(s)
     r.set_cameras(cams)
@@ -128,6 +135,8 @@ def test_tile_lists_bit_exact(Renderer, seed, size, tile_test):
         exp_rng.append(rr)
         tile_off += ranges.shape[0]
         k_off += tile.size
+    if n_big:
+        assert d["tiles_touched"].max() > 255
     np.testing.assert_array_equal(d["inst_tile"], np.concatenate(exp_tile))
     np.testing.assert_array_equal(d["inst_record"], np.concatenate(exp_rec))
     # an empty tile's range may start anywhere; non-empty ones are exact
