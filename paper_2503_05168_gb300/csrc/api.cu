@@ -49,8 +49,7 @@ struct seele_ctx {
 
     // frame workspace
     DevBuf rec, rect, tiles, blocks, depth, visk[2], visv[2], offs, instk[2], instv[2], instm[2], ranges, msum,
-        border, chunkv, chunks, vbuf, status, hist, lookback, T, nc, rgb_tmp, sortcnt, grad_rec, cnts;
-    size_t lookback_entries = 0;
+        border, chunkv, chunks, vbuf, status, hist, digtot, T, nc, rgb_tmp, sortcnt, grad_rec, cnts;
     DeviceStatus* h_status = nullptr;  // pinned mirror of the device status
     cudaEvent_t ev[SEELE_NUM_STAGES + 1] = {};
     bool profiling = false;
@@ -74,7 +73,6 @@ struct seele_ctx {
     int g_launches = 0, g_fin = 0;
     uint64_t scene_gen = 0;
     uint64_t capacity = 0;
-    uint32_t epoch = 1;
     bool status_pending = false;
 
     // last render
@@ -207,6 +205,11 @@ int bits_for(uint64_t v) {
     return b;
 }
 
+// Digit totals of the sorts' passes, 256 words per pass: the depth sort's
+// four, then up to four of the tile sort.
+constexpr uint32_t kDepthSortTotals = 4 * 256;
+constexpr uint32_t kDigitTotalWords = 8 * 256;
+
 struct FrameInfo {
     int ncam = 0;
     uint64_t R = 0, tiles_total = 0, blocks_total = 0, pix_total = 0, cap = 0;
@@ -214,7 +217,6 @@ struct FrameInfo {
     bool blocks = false, short_keys = false, rgb_dev = true, T_dev = true;
     int tile_bits = 1;         // key bits of a list unit id
     uint32_t cnt_words = 0;
-    size_t lb_entries = 0;
     FrameParams fp{};
 };
 
@@ -227,7 +229,7 @@ struct FrameInfo {
 template <typename KeyT>
 int enqueue_tile_sort(seele_ctx* c, const FrameInfo& f, const uint32_t* order, const uint2* rect, const float4* rec,
                       const CamDev* cams, DeviceStatus* st, const uint32_t* n_inst, uint64_t cap, int emit_blocks,
-                      uint64_t* lb, uint32_t* scnt, uint32_t* soff, int& launches, cudaStream_t s) {
+                      uint32_t* dtot, uint32_t* scnt, uint32_t* soff, int& launches, cudaStream_t s) {
     const FrameParams& fp = f.fp;
     KeyT* keys[2] = {ptr<KeyT>(c->instk[0]), ptr<KeyT>(c->instk[1])};
     uint32_t* vals[2] = {ptr<uint32_t>(c->instv[0]), ptr<uint32_t>(c->instv[1])};
@@ -243,8 +245,8 @@ int enqueue_tile_sort(seele_ctx* c, const FrameInfo& f, const uint32_t* order, c
     SEELE_MARK_EXT(c, SEELE_STAGE_TILE_SORT);
     uint32_t* run = ptr<uint32_t>(c->ranges);
     const uint64_t units = f.units_total;
-    const int fin = radix_sort_pairs<KeyT>(keys, vals, n_inst, (uint32_t)cap, f.tile_bits, false, scnt, soff, lb,
-                                           c->epoch, st, 6, launches, s, run, run + units, f.blocks ? masks : nullptr);
+    const int fin = radix_sort_pairs<KeyT>(keys, vals, n_inst, (uint32_t)cap, f.tile_bits, false, scnt, soff, dtot,
+                                           launches, s, run, run + units, f.blocks ? masks : nullptr);
     if (fin < 0) return -1;
     SEELE_MARK_EXT(c, SEELE_STAGE_RANGES);
     if (f.blocks) {
@@ -372,10 +374,8 @@ seele_status size_frame(seele_ctx* c, FrameInfo& f) {
     if (!f.rgb_dev) SEELE_CUDA(c, ensure(c->rgb_tmp, 12 * f.pix_total));
     f.cnt_words = radix_count_words((uint32_t)std::max<uint64_t>(R, cap));
     SEELE_CUDA(c, ensure(c->sortcnt, 8ull * f.cnt_words));
-    // look-back status words of the scans of one frame (cleared every frame)
-    const uint32_t items = scan_tiles_per_launch();
-    f.lb_entries = (std::max<uint64_t>(std::max<uint64_t>(R, f.cnt_words), f.tiles_total) + items - 1) / items + 1;
-    SEELE_CUDA(c, ensure(c->lookback, 8 * f.lb_entries));
+    // digit totals of the sorts' passes (cleared every frame)
+    SEELE_CUDA(c, ensure(c->digtot, 4 * kDigitTotalWords));
     return SEELE_OK;
 }
 
@@ -430,14 +430,14 @@ seele_status enqueue_frame(seele_ctx* c, const seele_options* opt, const FrameIn
     const int ncam = f.ncam;
     cudaStream_t s = c->stream;
     DeviceStatus* st = ptr<DeviceStatus>(c->status);
-    uint64_t* lb = ptr<uint64_t>(c->lookback);
+    uint32_t* dtot = ptr<uint32_t>(c->digtot);
     launches = 0;
 #define SEELE_MARK(k) \
     if (c->profiling) SEELE_CUDA(c, cudaEventRecord(c->ev[k], s))
 
     SEELE_CUDA(c, cudaMemsetAsync(st, 0, sizeof(DeviceStatus), s));
     SEELE_CUDA(c, cudaMemsetAsync(c->chunkv.p, 0, 4 * (R / kChunkItems + 1), s));
-    SEELE_CUDA(c, cudaMemsetAsync(lb, 0, 8 * f.lb_entries, s));
+    SEELE_CUDA(c, cudaMemsetAsync(dtot, 0, 4 * kDigitTotalWords, s));
     SEELE_CUDA(c, cudaMemsetAsync(c->viewt.p, 0, 12ull * ncam + 8, s));
     SEELE_CUDA(c, cudaMemsetAsync(c->ranges.p, 0xff, 4 * units_total, s));
     SEELE_CUDA(c, cudaMemsetAsync(ptr<uint32_t>(c->ranges) + units_total, 0, 4 * units_total, s));
@@ -490,8 +490,8 @@ seele_status enqueue_frame(seele_ctx* c, const seele_options* opt, const FrameIn
         gather.src = cnt_src;
         gather.out = ptr<uint32_t>(c->cnts);
         gather.packed = packed;
-        if (radix_sort_pairs<uint32_t>(vk, vv, n_vis, (uint32_t)R, 31, false, scnt, soff, lb, c->epoch, st, 2,
-                                       launches, s, nullptr, nullptr, nullptr, &gather) != 0)
+        if (radix_sort_pairs<uint32_t>(vk, vv, n_vis, (uint32_t)R, 31, false, scnt, soff, dtot, launches, s, nullptr,
+                                       nullptr, nullptr, &gather) != 0)
             return fail(c, SEELE_ERR_CUDA, "depth sort launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     }
     // sorted ids are back in buffer 0 after an even number of passes
@@ -505,11 +505,11 @@ seele_status enqueue_frame(seele_ctx* c, const seele_options* opt, const FrameIn
     SEELE_MARK(SEELE_STAGE_EMIT);
     const uint32_t* n_inst = &st->n_inst_valid;
     if (f.short_keys)
-        fin = enqueue_tile_sort<uint16_t>(c, f, order, po.rect, po.rec, cams, st, n_inst, cap, emit_blocks, lb, scnt,
-                                          soff, launches, s);
+        fin = enqueue_tile_sort<uint16_t>(c, f, order, po.rect, po.rec, cams, st, n_inst, cap, emit_blocks,
+                                          dtot + kDepthSortTotals, scnt, soff, launches, s);
     else
-        fin = enqueue_tile_sort<uint32_t>(c, f, order, po.rect, po.rec, cams, st, n_inst, cap, emit_blocks, lb, scnt,
-                                          soff, launches, s);
+        fin = enqueue_tile_sort<uint32_t>(c, f, order, po.rect, po.rec, cams, st, n_inst, cap, emit_blocks,
+                                          dtot + kDepthSortTotals, scnt, soff, launches, s);
     if (fin < 0) return fail(c, SEELE_ERR_CUDA, "tile sort launch failed: %s", cudaGetErrorString(cudaGetLastError()));
 
     RasterArgs ra;
@@ -603,7 +603,7 @@ void seele_destroy(seele_ctx* c) {
     DevBuf* all[] = {&c->pos_logit, &c->quat, &c->log_scale, &c->sh, &c->mask, &c->staging, &c->cams_dev,
                      &c->rec, &c->rect, &c->tiles, &c->depth, &c->visk[0], &c->visk[1], &c->visv[0],
                      &c->visv[1], &c->offs, &c->instk[0], &c->instk[1], &c->instv[0], &c->instv[1],
-                     &c->ranges, &c->status, &c->hist, &c->lookback, &c->T, &c->nc, &c->rgb_tmp, &c->sortcnt,
+                     &c->ranges, &c->status, &c->hist, &c->digtot, &c->T, &c->nc, &c->rgb_tmp, &c->sortcnt,
                      &c->grad_rec, &c->blocks, &c->instm[0], &c->instm[1], &c->msum, &c->border, &c->chunkv,
                      &c->chunks, &c->vbuf, &c->cnts};
     for (DevBuf* b : all) release(*b);

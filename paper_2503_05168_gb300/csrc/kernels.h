@@ -27,6 +27,10 @@ void launch_compact_visible(const uint32_t* cnt, bool pack, const float* depth, 
 void launch_scan_tiles(const uint32_t* cnt_sorted, uint32_t* chunk_sum, uint32_t max_n, uint32_t* offsets,
                        DeviceStatus* st, uint32_t capacity, cudaStream_t s);
 
+// Exclusive scan of a 256 x stride digit-major count matrix given its row
+// totals (no look-back).
+void launch_digit_scan(const uint32_t* in, uint32_t stride, const uint32_t* row_total, uint32_t* out,
+                       cudaStream_t s);
 void launch_exclusive_scan(const uint32_t* in, uint32_t n, uint32_t* out, uint64_t* status, uint32_t epoch,
                            DeviceStatus* st, int ticket, cudaStream_t s);
 
@@ -56,12 +60,12 @@ struct SortGather {
 // a second 32-bit payload is permuted with the values.  With gather (and no
 // aux) the last pass also lays out the records' instance counts in sorted
 // order (SortGather).
+// digit_totals: 256 words per pass, cleared by the caller.
 template <typename KeyT>
 int radix_sort_pairs(KeyT* keys[2], uint32_t* vals[2], const uint32_t* count_ptr, uint32_t max_n, int key_bits,
-                     bool keys_after_last, uint32_t* counts, uint32_t* offsets, uint64_t* lookback,
-                     uint32_t& epoch, DeviceStatus* st, int ticket, int& launches, cudaStream_t s,
-                     uint32_t* run_start = nullptr, uint32_t* run_end = nullptr, uint32_t* const* aux = nullptr,
-                     const SortGather* gather = nullptr);
+                     bool keys_after_last, uint32_t* counts, uint32_t* offsets, uint32_t* digit_totals,
+                     int& launches, cudaStream_t s, uint32_t* run_start = nullptr, uint32_t* run_end = nullptr,
+                     uint32_t* const* aux = nullptr, const SortGather* gather = nullptr);
 
 template <typename KeyT>
 void launch_emit(const uint32_t* order, const uint32_t* offsets, const uint2* rect, const float4* rec,

@@ -11,6 +11,8 @@
 //                   K; the depth sort's last pass has laid the counts out in
 //                   depth order; chunk sums first, then each CTA adds up its
 //                   predecessors' sums directly.
+//  digit_scan:      exclusive scan of a radix sort's digit-major count matrix
+//                   from its row totals, without look-back.
 //  exclusive_scan:  generic single-pass scan with decoupled look-back: each
 //                   block takes a dynamic ticket (so every predecessor has
 //                   already started and will publish), reduces its tile,
@@ -264,6 +266,55 @@ __global__ void __launch_bounds__(kScanThreads) scan_tiles_kernel(const uint32_t
     }
 }
 
+// Exclusive scan of the digit-major count matrix in[d * stride + t] (256 rows
+// of stride) given its row totals: the elements before scan tile s are the
+// whole rows d < d0 and the first t0 entries of row d0, so each block adds
+// those up itself and no block waits on another.
+__global__ void __launch_bounds__(kScanThreads) digit_scan_kernel(const uint32_t* __restrict__ in, uint32_t stride,
+                                                                  const uint32_t* __restrict__ row_total,
+                                                                  uint32_t* __restrict__ out) {
+    __shared__ uint32_t s_part[kScanThreads / 32];
+    const uint32_t n = 256u * stride;
+    const uint32_t first = blockIdx.x * kScanTile;
+    const uint32_t base = first + threadIdx.x * kScanItems;
+    uint32_t c[kScanItems];
+    if (base + kScanItems <= n) {
+        const uint4* p4 = reinterpret_cast<const uint4*>(in + base);
+#pragma unroll
+        for (int q = 0; q < kScanItems / 4; ++q) {
+            const uint4 v = __ldg(p4 + q);
+            c[4 * q] = v.x;
+            c[4 * q + 1] = v.y;
+            c[4 * q + 2] = v.z;
+            c[4 * q + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) c[k] = base + k < n ? __ldg(in + base + k) : 0u;
+    }
+    const uint32_t d0 = first / stride, t0 = first - d0 * stride;
+    uint32_t part = threadIdx.x < d0 ? __ldg(row_total + threadIdx.x) : 0u;
+    const uint32_t* row = in + (size_t)d0 * stride;
+    for (uint32_t t = threadIdx.x; t < t0; t += kScanThreads) part += __ldg(row + t);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = part;
+    __syncthreads();
+    uint32_t prefix = 0;
+#pragma unroll
+    for (int w = 0; w < kScanThreads / 32; ++w) prefix += s_part[w];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) sum += c[k];
+    uint32_t total;
+    uint32_t pos = prefix + block_exclusive_scan(sum, &total);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n) out[base + k] = pos;
+        pos += c[k];
+    }
+}
+
 // Exclusive scan of n uint32 values (n known on the host).
 __global__ void __launch_bounds__(kScanThreads) exclusive_scan_kernel(const uint32_t* __restrict__ in, uint32_t n,
                                                                       uint32_t* __restrict__ out, uint64_t* status,
@@ -299,6 +350,12 @@ __global__ void __launch_bounds__(kScanThreads) exclusive_scan_kernel(const uint
         if (base + k < n) out[base + k] = pos;
         pos += c[k];
     }
+}
+
+void launch_digit_scan(const uint32_t* in, uint32_t stride, const uint32_t* row_total, uint32_t* out,
+                       cudaStream_t s) {
+    const uint32_t blocks = (256u * stride + kScanTile - 1) / kScanTile;
+    digit_scan_kernel<<<blocks, kScanThreads, 0, s>>>(in, stride, row_total, out);
 }
 
 void launch_exclusive_scan(const uint32_t* in, uint32_t n, uint32_t* out, uint64_t* status, uint32_t epoch,

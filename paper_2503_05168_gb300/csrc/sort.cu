@@ -3,7 +3,9 @@
 //   upsweep:   each tile of 4096 elements counts its digits into a
 //              digit-major matrix counts[d * stride + tile];
 //   scan:      one device-wide exclusive scan of that matrix gives, for every
-//              (digit, tile), where the tile's run of that digit starts;
+//              (digit, tile), where the tile's run of that digit starts (the
+//              upsweep also adds up each digit's total, so every scan block
+//              finds the sum of the elements before it directly);
 //   downsweep: each tile ranks its elements stably (warp match + per-warp
 //              counters), stages them in shared memory by digit and writes
 //              each digit's run contiguously.
@@ -38,7 +40,8 @@ constexpr int kWarps = kSortThreads / 32;
 template <typename KeyT>
 __global__ void __launch_bounds__(kSortThreads) upsweep_kernel(const KeyT* __restrict__ keys,
                                                                const uint32_t* __restrict__ count_ptr, int shift,
-                                                               uint32_t* __restrict__ counts, uint32_t stride) {
+                                                               uint32_t* __restrict__ counts, uint32_t stride,
+                                                               uint32_t* __restrict__ row_total) {
     static_assert(kSortItems * sizeof(KeyT) % 16 == 0, "vector loads");
     __shared__ uint32_t s_w[kWarps][kRadix];
     const uint32_t tile = blockIdx.x;
@@ -66,6 +69,7 @@ __global__ void __launch_bounds__(kSortThreads) upsweep_kernel(const KeyT* __res
 #pragma unroll
     for (int ww = 0; ww < kWarps; ++ww) total += s_w[ww][d];
     counts[(size_t)d * stride + tile] = total;
+    if (row_total != nullptr && total != 0u) atomicAdd(row_total + d, total);
 }
 
 // AUX: a second 32-bit payload travels with each pair; it is staged through
@@ -221,7 +225,7 @@ uint32_t sort_tile_items() { return kSortTile; }
 // Single passes of the sort, for callers that manage their own buffers.
 void launch_radix_upsweep_u32(const uint32_t* keys, const uint32_t* count_ptr, int shift, uint32_t* counts,
                               uint32_t stride, cudaStream_t s) {
-    upsweep_kernel<uint32_t><<<stride, kSortThreads, 0, s>>>(keys, count_ptr, shift, counts, stride);
+    upsweep_kernel<uint32_t><<<stride, kSortThreads, 0, s>>>(keys, count_ptr, shift, counts, stride, nullptr);
 }
 
 void launch_radix_downsweep_u32(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
@@ -253,9 +257,9 @@ static void launch_downsweep(KeyT* keys[2], uint32_t* vals[2], uint32_t* const* 
 
 template <typename KeyT>
 int radix_sort_pairs(KeyT* keys[2], uint32_t* vals[2], const uint32_t* count_ptr, uint32_t max_n, int key_bits,
-                     bool keys_after_last, uint32_t* counts, uint32_t* offsets, uint64_t* lookback,
-                     uint32_t& epoch, DeviceStatus* st, int ticket, int& launches, cudaStream_t s,
-                     uint32_t* run_start, uint32_t* run_end, uint32_t* const* aux, const SortGather* gather) {
+                     bool keys_after_last, uint32_t* counts, uint32_t* offsets, uint32_t* digit_totals,
+                     int& launches, cudaStream_t s, uint32_t* run_start, uint32_t* run_end, uint32_t* const* aux,
+                     const SortGather* gather) {
     const uint32_t stride = std::max<uint32_t>((max_n + kSortTile - 1) / kSortTile, 1u);
     const int passes = std::max(1, (key_bits + 7) / 8);
     for (int p = 0; p < passes; ++p) {
@@ -265,8 +269,9 @@ int radix_sort_pairs(KeyT* keys[2], uint32_t* vals[2], const uint32_t* count_ptr
         uint32_t* rs = last ? run_start : nullptr;
         uint32_t* re = last ? run_end : nullptr;
         const SortGather g = (last && gather) ? *gather : SortGather{};
-        upsweep_kernel<KeyT><<<stride, kSortThreads, 0, s>>>(keys[a], count_ptr, 8 * p, counts, stride);
-        launch_exclusive_scan(counts, kRadix * stride, offsets, lookback, epoch++, st, ticket + p, s);
+        uint32_t* totals = digit_totals + (size_t)p * kRadix;
+        upsweep_kernel<KeyT><<<stride, kSortThreads, 0, s>>>(keys[a], count_ptr, 8 * p, counts, stride, totals);
+        launch_digit_scan(counts, stride, totals, offsets, s);
         const bool wk = !last || keys_after_last;
         if (aux) {
             if (wk) launch_downsweep<KeyT, true, true>(keys, vals, aux, a, b, count_ptr, 8 * p, nbits, offsets, stride,
@@ -285,10 +290,10 @@ int radix_sort_pairs(KeyT* keys[2], uint32_t* vals[2], const uint32_t* count_ptr
     return passes & 1;
 }
 template int radix_sort_pairs<uint32_t>(uint32_t* [2], uint32_t* [2], const uint32_t*, uint32_t, int, bool,
-                                        uint32_t*, uint32_t*, uint64_t*, uint32_t&, DeviceStatus*, int, int&,
-                                        cudaStream_t, uint32_t*, uint32_t*, uint32_t* const*, const SortGather*);
+                                        uint32_t*, uint32_t*, uint32_t*, int&, cudaStream_t, uint32_t*,
+                                        uint32_t*, uint32_t* const*, const SortGather*);
 template int radix_sort_pairs<uint16_t>(uint16_t* [2], uint32_t* [2], const uint32_t*, uint32_t, int, bool,
-                                        uint32_t*, uint32_t*, uint64_t*, uint32_t&, DeviceStatus*, int, int&,
-                                        cudaStream_t, uint32_t*, uint32_t*, uint32_t* const*, const SortGather*);
+                                        uint32_t*, uint32_t*, uint32_t*, int&, cudaStream_t, uint32_t*,
+                                        uint32_t*, uint32_t* const*, const SortGather*);
 
 }  // namespace seele
