@@ -607,12 +607,13 @@ def run_gpu(args):
     n_blocks = 15 * 17
     block_passes = max(1, math.ceil(max(1, (n_blocks - 1).bit_length()) / 8))
     stage_bytes = {
-        # position/logit of every Gaussian, count out; quat, scale, 48 SH floats in and
-        # 48 B record + 8 B rect + 4 B depth + 4 B block count out per visible one
-        "preprocess": 16 * n_gauss + 4 * n_gauss + (32 + 192 + 64) * work_vis,
+        # position/logit in and tile + block counts out for every Gaussian; quat, scale,
+        # 48 SH floats in and the 64 B record + 4 B depth out per visible one
+        "preprocess": 16 * n_gauss + 8 * n_gauss + (32 + 192 + 68) * work_vis,
         "compact": 4 * n_gauss + 12 * work_vis,
         "depth_sort": 4 * 20 * work_vis,
         "tile_scan": 12 * work_vis,
+        # order + offset + the record's ellipse and tile box in, 10 B per entry out
         "emit": 48 * work_vis + 10 * work_K,
         "tile_sort": block_passes * 22 * work_K,
         "ranges": 4 * work_K,

@@ -243,13 +243,14 @@ typedef struct {
                                      tile_start >= tile_end */
     const uint32_t* tile_end;     /* [n_tiles] */
     const uint32_t* tiles_touched;/* [n_records] 0 = culled */
-    const uint32_t* rect;         /* [n_records][2] tile box, packed x | y << 16 */
-    const float* records;         /* [n_records][12] raster record: u, v,
+    const float* records;         /* [n_records][16] raster record (64 bytes): u, v,
                                      -A/2*log2e, -B*log2e, -C/2*log2e (conic
                                      [[A,B],[B,C]] = Sigma'^-1), log2 o, e_thr,
-                                     0, r, g, b, 0; a pixel at offset (dx, dy)
-                                     takes the Gaussian iff
-                                     e = cA dx^2 + cB dx dy + cC dy^2 + log2 o
+                                     the tile test's bound on -(cA dx^2 + cB dx dy
+                                     + cC dy^2), r, g, b, 0, then the tile box as
+                                     two uint32 x0 | y0 << 16, x1 | y1 << 16, 0, 0;
+                                     a pixel at offset (dx, dy) takes the Gaussian
+                                     iff e = cA dx^2 + cB dx dy + cC dy^2 + log2 o
                                      >= e_thr, with alpha = min(clamp, 2^e) */
     const float* depth;           /* [n_records] camera-space Z */
     const uint32_t* n_contrib;    /* [sum W*H] 1 + last blended position in the

@@ -297,12 +297,13 @@ class Renderer:
         ranges = torch.stack([torch.where(empty, 0, start), torch.where(empty, 0, end)], 1).to(i32)
         counts = (ranges[:, 1] - ranges[:, 0]).to(torch.int64)
         inst_tile = torch.repeat_interleave(torch.arange(T, device=self.device, dtype=i32), counts)
+        records = dev(v.records, 16 * R, torch.float32).reshape(R, 16)
         return dict(
             n_records=R, n_visible=v.n_visible, n_instances=K, n_tiles=T,
             inst_tile=inst_tile, inst_record=dev(v.inst_record, K, i32),
             tile_ranges=ranges,
-            tiles_touched=dev(v.tiles_touched, R, i32), rect=dev(v.rect, 2 * R, i32).reshape(R, 2),
-            records=dev(v.records, 12 * R, torch.float32).reshape(R, 12), depth=dev(v.depth, R, torch.float32),
+            tiles_touched=dev(v.tiles_touched, R, i32), rect=records[:, 12:14].contiguous().view(i32),
+            records=records[:, :12].contiguous(), depth=dev(v.depth, R, torch.float32),
             n_contrib=dev(v.n_contrib, self.n_pixels, i32),
             inst_mask=dev(v.inst_mask, K, i32) if v.inst_mask else None,
         )

@@ -61,7 +61,7 @@ class Grads(ctypes.Structure):
 class DebugView(ctypes.Structure):
     _fields_ = [("n_records", ctypes.c_int64), ("n_visible", ctypes.c_int64), ("n_instances", ctypes.c_int64),
                 ("n_tiles", ctypes.c_int64), ("inst_record", P), ("tile_start", P), ("tile_end", P),
-                ("tiles_touched", P), ("rect", P), ("records", P), ("depth", P), ("n_contrib", P),
+                ("tiles_touched", P), ("records", P), ("depth", P), ("n_contrib", P),
                 ("inst_mask", P)]
 
 

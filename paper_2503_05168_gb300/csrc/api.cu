@@ -48,7 +48,7 @@ struct seele_ctx {
     DevBuf cams_dev;
 
     // frame workspace
-    DevBuf rec, rect, tiles, blocks, depth, visk[2], visv[2], offs, instk[2], instv[2], instm[2], ranges, msum,
+    DevBuf rec, tiles, blocks, depth, visk[2], visv[2], offs, instk[2], instv[2], instm[2], ranges, msum,
         border, chunkv, chunks, vbuf, status, hist, digtot, T, nc, rgb_tmp, sortcnt, grad_rec, cnts;
     DeviceStatus* h_status = nullptr;  // pinned mirror of the device status
     cudaEvent_t ev[SEELE_NUM_STAGES + 1] = {};
@@ -227,7 +227,7 @@ struct FrameInfo {
 // Returns the ping-pong buffer holding the sorted lists, or -1 on a launch
 // error.
 template <typename KeyT>
-int enqueue_tile_sort(seele_ctx* c, const FrameInfo& f, const uint32_t* order, const uint2* rect, const float4* rec,
+int enqueue_tile_sort(seele_ctx* c, const FrameInfo& f, const uint32_t* order, const float4* rec,
                       const CamDev* cams, DeviceStatus* st, const uint32_t* n_inst, uint64_t cap, int emit_blocks,
                       uint32_t* dtot, uint32_t* scnt, uint32_t* soff, int& launches, cudaStream_t s) {
     const FrameParams& fp = f.fp;
@@ -235,10 +235,10 @@ int enqueue_tile_sort(seele_ctx* c, const FrameInfo& f, const uint32_t* order, c
     uint32_t* vals[2] = {ptr<uint32_t>(c->instv[0]), ptr<uint32_t>(c->instv[1])};
     uint32_t* masks[2] = {ptr<uint32_t>(c->instm[0]), ptr<uint32_t>(c->instm[1])};
     if (f.blocks)
-        launch_emit_blocks<KeyT>(order, ptr<uint32_t>(c->offs), rect, rec, cams, (int)c->n, fp.tile_w, fp.tile_h,
+        launch_emit_blocks<KeyT>(order, ptr<uint32_t>(c->offs), rec, cams, (int)c->n, fp.tile_w, fp.tile_h,
                                  fp.tile_test, st, keys[0], vals[0], masks[0], emit_blocks, s);
     else
-        launch_emit<KeyT>(order, ptr<uint32_t>(c->offs), rect, rec, cams, (int)c->n, fp.tile_w, fp.tile_h,
+        launch_emit<KeyT>(order, ptr<uint32_t>(c->offs), rec, cams, (int)c->n, fp.tile_w, fp.tile_h,
                           fp.tile_test, st, keys[0], vals[0], emit_blocks, s);
     if (cudaPeekAtLastError() != cudaSuccess) return -1;
     ++launches;
@@ -346,8 +346,7 @@ void fill_params(seele_ctx* c, const seele_options* opt, FrameInfo& f) {
 seele_status size_frame(seele_ctx* c, FrameInfo& f) {
     const uint64_t R = f.R, cap = f.cap;
     SEELE_CUDA(c, ensure(c->cams_dev, sizeof(CamDev) * f.ncam));
-    SEELE_CUDA(c, ensure(c->rec, 48 * R));
-    SEELE_CUDA(c, ensure(c->rect, 8 * R));
+    SEELE_CUDA(c, ensure(c->rec, 16ull * kRecF4 * R));
     SEELE_CUDA(c, ensure(c->tiles, 4 * R));
     SEELE_CUDA(c, ensure(c->depth, 4 * R));
     for (int i = 0; i < 2; ++i) {
@@ -460,7 +459,7 @@ seele_status enqueue_frame(seele_ctx* c, const seele_options* opt, const FrameIn
                                                                   : ptr<const uint32_t>(c->mask))
                           : nullptr;
     unsigned long long* vt = ptr<unsigned long long>(c->viewt);
-    ProjOut po{ptr<float4>(c->rec), ptr<uint2>(c->rect), ptr<uint32_t>(c->tiles),
+    ProjOut po{ptr<float4>(c->rec), ptr<uint32_t>(c->tiles),
                f.blocks ? ptr<uint32_t>(c->blocks) : nullptr, ptr<float>(c->depth), vt, ptr<uint32_t>(c->chunkv)};
     const CamDev* cams = ptr<const CamDev>(c->cams_dev);
     launch_preprocess(sc, cams, f.fp, po, s);
@@ -505,10 +504,10 @@ seele_status enqueue_frame(seele_ctx* c, const seele_options* opt, const FrameIn
     SEELE_MARK(SEELE_STAGE_EMIT);
     const uint32_t* n_inst = &st->n_inst_valid;
     if (f.short_keys)
-        fin = enqueue_tile_sort<uint16_t>(c, f, order, po.rect, po.rec, cams, st, n_inst, cap, emit_blocks,
+        fin = enqueue_tile_sort<uint16_t>(c, f, order, po.rec, cams, st, n_inst, cap, emit_blocks,
                                           dtot + kDepthSortTotals, scnt, soff, launches, s);
     else
-        fin = enqueue_tile_sort<uint32_t>(c, f, order, po.rect, po.rec, cams, st, n_inst, cap, emit_blocks,
+        fin = enqueue_tile_sort<uint32_t>(c, f, order, po.rec, cams, st, n_inst, cap, emit_blocks,
                                           dtot + kDepthSortTotals, scnt, soff, launches, s);
     if (fin < 0) return fail(c, SEELE_ERR_CUDA, "tile sort launch failed: %s", cudaGetErrorString(cudaGetLastError()));
 
@@ -601,7 +600,7 @@ void seele_destroy(seele_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
     DevBuf* all[] = {&c->pos_logit, &c->quat, &c->log_scale, &c->sh, &c->mask, &c->staging, &c->cams_dev,
-                     &c->rec, &c->rect, &c->tiles, &c->depth, &c->visk[0], &c->visk[1], &c->visv[0],
+                     &c->rec, &c->tiles, &c->depth, &c->visk[0], &c->visk[1], &c->visv[0],
                      &c->visv[1], &c->offs, &c->instk[0], &c->instk[1], &c->instv[0], &c->instv[1],
                      &c->ranges, &c->status, &c->hist, &c->digtot, &c->T, &c->nc, &c->rgb_tmp, &c->sortcnt,
                      &c->grad_rec, &c->blocks, &c->instm[0], &c->instm[1], &c->msum, &c->border, &c->chunkv,
@@ -1016,7 +1015,6 @@ seele_status seele_get_debug_view(const seele_ctx* c, seele_debug_view* out) {
     out->tile_end = ptr<const uint32_t>(m->ranges) + c->n_units_total;
     out->inst_mask = blk ? ptr<const uint32_t>(m->instm[c->inst_final]) : nullptr;
     out->tiles_touched = ptr<const uint32_t>(m->tiles);
-    out->rect = ptr<const uint32_t>(m->rect);
     out->records = ptr<const float>(m->rec);
     out->depth = ptr<const float>(m->depth);
     out->n_contrib = ptr<const uint32_t>(m->nc);

@@ -90,9 +90,9 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
         if (t < b1 - b0) {
             const uint32_t r = __ldg(inst_rec + start + b0 + t);
             s_r[t] = r;
-            s0[t] = __ldg(rec + 3 * (size_t)r);
-            s1[t] = __ldg(rec + 3 * (size_t)r + 1);
-            s2[t] = __ldg(rec + 3 * (size_t)r + 2);
+            s0[t] = __ldg(rec + (size_t)kRecF4 * r);
+            s1[t] = __ldg(rec + (size_t)kRecF4 * r + 1);
+            s2[t] = __ldg(rec + (size_t)kRecF4 * r + 2);
         }
         __syncthreads();
         for (int k = b1 - b0 - 1; k >= 0; --k) {

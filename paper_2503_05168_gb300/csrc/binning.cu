@@ -43,7 +43,7 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
 template <typename KeyT>
 __global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ order,
                                                    const uint32_t* __restrict__ offsets,
-                                                   const uint2* __restrict__ rect, const float4* __restrict__ rec,
+                                                   const float4* __restrict__ rec,
                                                    const CamDev* __restrict__ cams, int n_gauss, int tile_w,
                                                    int tile_h, int ellipse, DeviceStatus* st,
                                                    KeyT* __restrict__ inst_tile, uint32_t* __restrict__ inst_rec) {
@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ 
         float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
         if (j < n) {
             r = __ldg(order + j);
-            const uint2 b = __ldg(rect + r);
+            const uint2 b = rec_tile_box(rec, r);
             x0 = b.x & 0xffffu;
             y0 = b.x >> 16;
             x1 = b.y & 0xffffu;
@@ -68,8 +68,8 @@ __global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ 
             tx_n = (uint32_t)C.tiles_x;
             row0 = C.tile_offset;
             if (ellipse) {
-                r0 = __ldg(rec + 3 * (size_t)r);
-                r1 = __ldg(rec + 3 * (size_t)r + 1);
+                r0 = __ldg(rec + (size_t)kRecF4 * r);
+                r1 = __ldg(rec + (size_t)kRecF4 * r + 1);
             }
         }
         const uint32_t rincl = warp_incl_scan(rows, lane);
@@ -152,7 +152,6 @@ __global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ 
 template <typename KeyT>
 __global__ void __launch_bounds__(256) emit_blocks_kernel(const uint32_t* __restrict__ order,
                                                           const uint32_t* __restrict__ offsets,
-                                                          const uint2* __restrict__ rect,
                                                           const float4* __restrict__ rec,
                                                           const CamDev* __restrict__ cams, int n_gauss, int tile_w,
                                                           int tile_h, int ellipse, DeviceStatus* st,
@@ -164,13 +163,13 @@ __global__ void __launch_bounds__(256) emit_blocks_kernel(const uint32_t* __rest
     const uint32_t n_inst = st->n_instances;
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
         const uint32_t r = __ldg(order + j);
-        const uint2 bx2 = __ldg(rect + r);
+        const uint2 bx2 = rec_tile_box(rec, r);
         const int x0 = (int)(bx2.x & 0xffffu), y0 = (int)(bx2.x >> 16);
         const int x1 = (int)(bx2.y & 0xffffu), y1 = (int)(bx2.y >> 16);
         const CamDev& C = cams[r < (uint32_t)n_gauss ? 0u : r / (uint32_t)n_gauss];
         const uint32_t boff = C.block_offset, bx_n = (uint32_t)C.blocks_x;
         Ellipse E;
-        if (ellipse) E = make_ellipse(__ldg(rec + 3 * (size_t)r), __ldg(rec + 3 * (size_t)r + 1));
+        if (ellipse) E = make_ellipse(__ldg(rec + (size_t)kRecF4 * r), __ldg(rec + (size_t)kRecF4 * r + 1));
         uint32_t pos = __ldg(offsets + j);
         const uint32_t end = j + 1 < n ? __ldg(offsets + j + 1) : n_inst;
         for (int by = y0 / kBlockH; by <= y1 / kBlockH; ++by) {
@@ -284,30 +283,30 @@ void launch_block_order(const uint32_t* bstart, const uint32_t* bend, uint32_t n
 }
 
 template <typename KeyT>
-void launch_emit(const uint32_t* order, const uint32_t* offsets, const uint2* rect, const float4* rec,
+void launch_emit(const uint32_t* order, const uint32_t* offsets, const float4* rec,
                  const CamDev* cams, int n_gauss, int tile_w, int tile_h, int ellipse, DeviceStatus* st,
                  KeyT* inst_tile, uint32_t* inst_rec, int blocks, cudaStream_t s) {
-    emit_kernel<KeyT><<<blocks, 256, 0, s>>>(order, offsets, rect, rec, cams, n_gauss, tile_w, tile_h, ellipse, st,
+    emit_kernel<KeyT><<<blocks, 256, 0, s>>>(order, offsets, rec, cams, n_gauss, tile_w, tile_h, ellipse, st,
                                              inst_tile, inst_rec);
 }
 
 template <typename KeyT>
-void launch_emit_blocks(const uint32_t* order, const uint32_t* offsets, const uint2* rect, const float4* rec,
+void launch_emit_blocks(const uint32_t* order, const uint32_t* offsets, const float4* rec,
                         const CamDev* cams, int n_gauss, int tile_w, int tile_h, int ellipse, DeviceStatus* st,
                         KeyT* inst_block, uint32_t* inst_rec, uint32_t* inst_mask, int blocks, cudaStream_t s) {
-    emit_blocks_kernel<KeyT><<<blocks, 256, 0, s>>>(order, offsets, rect, rec, cams, n_gauss, tile_w, tile_h, ellipse,
+    emit_blocks_kernel<KeyT><<<blocks, 256, 0, s>>>(order, offsets, rec, cams, n_gauss, tile_w, tile_h, ellipse,
                                                     st, inst_block, inst_rec, inst_mask);
 }
 
-template void launch_emit_blocks<uint16_t>(const uint32_t*, const uint32_t*, const uint2*, const float4*,
+template void launch_emit_blocks<uint16_t>(const uint32_t*, const uint32_t*, const float4*,
                                            const CamDev*, int, int, int, int, DeviceStatus*, uint16_t*, uint32_t*,
                                            uint32_t*, int, cudaStream_t);
-template void launch_emit_blocks<uint32_t>(const uint32_t*, const uint32_t*, const uint2*, const float4*,
+template void launch_emit_blocks<uint32_t>(const uint32_t*, const uint32_t*, const float4*,
                                            const CamDev*, int, int, int, int, DeviceStatus*, uint32_t*, uint32_t*,
                                            uint32_t*, int, cudaStream_t);
-template void launch_emit<uint16_t>(const uint32_t*, const uint32_t*, const uint2*, const float4*, const CamDev*,
+template void launch_emit<uint16_t>(const uint32_t*, const uint32_t*, const float4*, const CamDev*,
                                     int, int, int, int, DeviceStatus*, uint16_t*, uint32_t*, int, cudaStream_t);
-template void launch_emit<uint32_t>(const uint32_t*, const uint32_t*, const uint2*, const float4*, const CamDev*,
+template void launch_emit<uint32_t>(const uint32_t*, const uint32_t*, const float4*, const CamDev*,
                                     int, int, int, int, DeviceStatus*, uint32_t*, uint32_t*, int, cudaStream_t);
 
 }  // namespace seele

@@ -92,10 +92,19 @@ struct SceneDev {
     const uint32_t* mask;      // [n] or nullptr
 };
 
+// Raster record: kRecF4 float4 per record, one 64-byte line:
+//   (u, v, cA, cB), (cC, log2 o, e_thr, T_tile), (r, g, b, 0),
+//   (tile box x0 | y0 << 16, x1 | y1 << 16, 0, 0) as integer bits.
+constexpr int kRecF4 = 4;
+
+__device__ __forceinline__ uint2 rec_tile_box(const float4* rec, uint32_t r) {
+    const float4 b = __ldg(rec + (size_t)kRecF4 * r + 3);
+    return make_uint2(__float_as_uint(b.x), __float_as_uint(b.y));
+}
+
 // Per-record outputs of preprocessing.
 struct ProjOut {
-    float4* rec;               // [3 * R]: (u, v, cA, cB), (cC, log2 o, e_thr, T_tile), (r, g, b, 0)
-    uint2* rect;               // [R] tile box x0 | y0 << 16, x1 | y1 << 16
+    float4* rec;               // [kRecF4 * R] raster records
     uint32_t* tiles;           // [R] tiles touched (0 = culled)
     uint32_t* blocks;          // [R] tile-block instances (0 = culled; block binning only, else unused)
     float* depth;              // [R] camera-space Z

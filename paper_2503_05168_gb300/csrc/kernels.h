@@ -68,12 +68,12 @@ int radix_sort_pairs(KeyT* keys[2], uint32_t* vals[2], const uint32_t* count_ptr
                      uint32_t* const* aux = nullptr, const SortGather* gather = nullptr);
 
 template <typename KeyT>
-void launch_emit(const uint32_t* order, const uint32_t* offsets, const uint2* rect, const float4* rec,
+void launch_emit(const uint32_t* order, const uint32_t* offsets, const float4* rec,
                  const CamDev* cams, int n_gauss, int tile_w, int tile_h, int ellipse, DeviceStatus* st,
                  KeyT* inst_tile, uint32_t* inst_rec, int blocks, cudaStream_t s);
 
 template <typename KeyT>
-void launch_emit_blocks(const uint32_t* order, const uint32_t* offsets, const uint2* rect, const float4* rec,
+void launch_emit_blocks(const uint32_t* order, const uint32_t* offsets, const float4* rec,
                         const CamDev* cams, int n_gauss, int tile_w, int tile_h, int ellipse, DeviceStatus* st,
                         KeyT* inst_block, uint32_t* inst_rec, uint32_t* inst_mask, int blocks, cudaStream_t s);
 

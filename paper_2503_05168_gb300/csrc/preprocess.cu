@@ -226,10 +226,12 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev sc, const CamD
             rgb[ch] = fmaxf(s, 0.f);
         }
 
-        out.rec[3 * rid + 0] = rec0;
-        out.rec[3 * rid + 1] = rec1;
-        out.rec[3 * rid + 2] = make_float4(rgb[0], rgb[1], rgb[2], 0.f);
-        out.rect[rid] = make_uint2((uint32_t)tx0 | ((uint32_t)ty0 << 16), (uint32_t)tx1 | ((uint32_t)ty1 << 16));
+        float4* ro = out.rec + (size_t)kRecF4 * rid;
+        ro[0] = rec0;
+        ro[1] = rec1;
+        ro[2] = make_float4(rgb[0], rgb[1], rgb[2], 0.f);
+        ro[3] = make_float4(__uint_as_float((uint32_t)tx0 | ((uint32_t)ty0 << 16)),
+                            __uint_as_float((uint32_t)tx1 | ((uint32_t)ty1 << 16)), 0.f, 0.f);
         out.depth[rid] = Z;
     } while (0);
     out.tiles[rid] = ntiles;

@@ -108,9 +108,9 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
             const uint32_t j = cursor + t;
             if (j < rg.y) {
                 const uint32_t r = __ldg(inst_rec + j);
-                s0[t] = __ldg(rec + 3 * (size_t)r);
-                s1[t] = __ldg(rec + 3 * (size_t)r + 1);
-                s2[t] = __ldg(rec + 3 * (size_t)r + 2);
+                s0[t] = __ldg(rec + (size_t)kRecF4 * r);
+                s1[t] = __ldg(rec + (size_t)kRecF4 * r + 1);
+                s2[t] = __ldg(rec + (size_t)kRecF4 * r + 2);
             }
             cnt = (int)min((uint32_t)NT, rg.y - cursor);
             cursor += NT;
@@ -164,9 +164,9 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
             cnt = min(NT, n_idx - idx_pos);
             if (t < cnt) {
                 const uint32_t r = __ldg(inst_rec + s_idx[idx_pos + t]);
-                s0[t] = __ldg(rec + 3 * (size_t)r);
-                s1[t] = __ldg(rec + 3 * (size_t)r + 1);
-                s2[t] = __ldg(rec + 3 * (size_t)r + 2);
+                s0[t] = __ldg(rec + (size_t)kRecF4 * r);
+                s1[t] = __ldg(rec + (size_t)kRecF4 * r + 1);
+                s2[t] = __ldg(rec + (size_t)kRecF4 * r + 2);
             }
             idx_pos += cnt;
             __syncthreads();

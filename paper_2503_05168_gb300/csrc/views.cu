@@ -176,8 +176,8 @@ __global__ void __launch_bounds__(TW * TH) topk_kernel(const uint32_t* __restric
         if (j < rg.y) {
             const uint32_t r = __ldg(inst_rec + j);
             s_r[t] = r;
-            s0[t] = __ldg(rec + 3 * (size_t)r);
-            s1[t] = __ldg(rec + 3 * (size_t)r + 1);
+            s0[t] = __ldg(rec + (size_t)kRecF4 * r);
+            s1[t] = __ldg(rec + (size_t)kRecF4 * r + 1);
         }
         __syncthreads();
         const int cnt = (int)min((uint32_t)NT, rg.y - base);
