@@ -148,12 +148,15 @@ def test_tile_lists_bit_exact(Renderer, seed, size, n_big, tile_test):
     r.close()
 
 
-@pytest.mark.parametrize("seed", [2, 3])
-def test_block_lists_filtered_per_tile_are_the_tile_lists(Renderer, seed):
+@pytest.mark.parametrize("seed,size,n_big", [(2, (200, 120, 160.0), 0), (3, (200, 120, 160.0), 0),
+                                             (4, (480, 320, 400.0), 3)])
+def test_block_lists_filtered_per_tile_are_the_tile_lists(Renderer, seed, size, n_big):
     """Block binning: walking a tile's block list and keeping the entries whose
     mask has the tile's bit gives exactly the oracle's tile list, in order
-    (the 200x120 frames span several 8x4-tile blocks each way)."""
-    s, cams = _clear_tiny_scene(seed, W=200, H=120, f=160.0)
+    (the 200x120 frames span several 8x4-tile blocks each way; the 480x320
+    ones hold records up to 20 tile rows tall across many blocks)."""
+    W, H, f = size
+    s, cams = _clear_tiny_scene(seed, W=W, H=H, f=f, n_big=n_big)
     r = Renderer()
     r.load_scene(s)
     r.set_cameras(cams)
