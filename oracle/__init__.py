@@ -105,6 +105,8 @@ def _L():
         lib.oc_kmeans.restype = I32
         lib.oc_topk_contributors.argtypes = [P, P, P, I32, I32, P, I32, P, P, P, P, I32]
         lib.oc_topk_contributors.restype = None
+        lib.oc_contribution_skew.argtypes = [P, P, P, I32, I32, P, ctypes.c_double, P, P, P, P, P, I32]
+        lib.oc_contribution_skew.restype = None
         lib.oc_sh_eval.restype = None
         _lib = lib
     return _lib
@@ -366,6 +368,25 @@ def topk_contributors(proj, gid, ranges, cam, opts: Options, k: int, nthreads: i
     _L().oc_topk_contributors(_p(proj), _p(gid) if gid.size else None, _p(ranges), W, H, _p(o), int(k), _p(ids),
                               _p(w), _p(cnt), _p(margin), nthreads)
     return ids, w, cnt, margin
+
+
+def contribution_skew(proj, gid, ranges, cam, opts: Options, frac: float = 0.99, nthreads: int = 1):
+    """Per pixel of a plain render (Sec. 1, Sec. 3.4 "Motivation"): the
+    smallest number m of its largest contributions Gamma alpha that sum to
+    frac of their total, the number of contributions, the list entries it
+    walked, the total, and the decision margin (see oc_contribution_skew)."""
+    W, H = int(cam["width"]), int(cam["height"])
+    m = np.zeros((H, W), np.int32)
+    blended = np.zeros((H, W), np.int32)
+    walked = np.zeros((H, W), np.int32)
+    total = np.zeros((H, W))
+    margin = np.zeros((H, W))
+    o = opts.to_struct()
+    gid = np.ascontiguousarray(gid, np.int32)
+    ranges = np.ascontiguousarray(ranges, np.int64)
+    _L().oc_contribution_skew(_p(proj), _p(gid) if gid.size else None, _p(ranges), W, H, _p(o), float(frac), _p(m),
+                              _p(blended), _p(walked), _p(total), _p(margin), nthreads)
+    return dict(m=m, blended=blended, walked=walked, total=total, margin=margin)
 
 
 def view_masks(scene: Scene64, poses, assign: np.ndarray, k: int, opts: Options | None = None,

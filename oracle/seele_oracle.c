@@ -1134,3 +1134,75 @@ void oc_topk_contributors(const oc_proj* proj, const int32_t* gid, const int64_t
         free(buf);
     }
 }
+
+/* Contribution skew (Sec. 1 "Rendering Inefficiency", Sec. 3.4 "Motivation"):
+   every pixel walks its tile list under the plain rules of px_blend, the
+   contributions Gamma_i alpha_i of the blended Gaussians are sorted in
+   descending order, and out_m [H W] is the smallest number of them whose sum
+   reaches frac times their total (0 for a pixel nothing blends into).  Also
+   out_blended (contributions), out_walked (list entries the pixel examined:
+   up to and including the one whose blending would have crossed T_stop, else
+   the whole list), out_total (the sum), and out_margin = the smaller of the
+   pixel's decision margin and the relative distance of frac * total from the
+   two prefix sums that bracket it. */
+void oc_contribution_skew(const oc_proj* proj, const int32_t* gid, const int64_t* ranges, int W, int H,
+                          const oc_options* opt, double frac, int32_t* out_m, int32_t* out_blended,
+                          int32_t* out_walked, double* out_total, double* out_margin, int nthreads) {
+    int tw = opt->tile_w, th = opt->tile_h;
+    int tiles_x = (W + tw - 1) / tw, tiles_y = (H + th - 1) / th;
+    int64_t ntiles = (int64_t)tiles_x * tiles_y;
+    int nt = nthreads > 0 ? nthreads : 1;
+    (void)nt;
+#ifdef _OPENMP
+    #pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+#endif
+    for (int64_t t = 0; t < ntiles; ++t) {
+        int64_t cnt[OC_NCOUNT] = {0};
+        int tx = (int)(t % tiles_x), ty = (int)(t / tiles_x);
+        int64_t start = ranges[2 * t], end = ranges[2 * t + 1];
+        oc_contrib* buf = (oc_contrib*)malloc((size_t)(end > start ? end - start : 1) * sizeof(oc_contrib));
+        for (int y = ty * th; y < ty * th + th && y < H; ++y)
+            for (int x = tx * tw; x < tx * tw + tw && x < W; ++x) {
+                px_state s;
+                px_init(&s);
+                int m = 0;
+                int64_t walked = 0;
+                for (int64_t i = start; i < end && !s.done; ++i) {
+                    const double T = s.T;
+                    const oc_proj* P = proj + gid[i];
+                    ++walked;
+                    if (px_blend(&s, P, opt, x + 0.5, y + 0.5, i - start, cnt)) {
+                        buf[m].w = T * alpha_of_q(P, opt, quad_at(P, x + 0.5, y + 0.5));
+                        buf[m].g = gid[i];
+                        ++m;
+                    }
+                }
+                qsort(buf, (size_t)m, sizeof(oc_contrib), contrib_cmp);
+                double total = 0.0;
+                for (int j = 0; j < m; ++j) total += buf[j].w;
+                const double target = frac * total;
+                int need = 0;
+                double before = 0.0, upto = 0.0;
+                if (m > 0) {
+                    while (need < m && upto < target) {
+                        before = upto;
+                        upto += buf[need].w;
+                        ++need;
+                    }
+                }
+                const int64_t p = (int64_t)y * W + x;
+                out_m[p] = need;
+                out_blended[p] = m;
+                out_walked[p] = (int32_t)walked;
+                out_total[p] = total;
+                double mg = s.margin;
+                if (m > 0 && total > 0.0) {
+                    const double above = (upto - target) / total, below = (target - before) / total;
+                    if (above < mg) mg = above;
+                    if (need > 1 && below < mg) mg = below;
+                }
+                out_margin[p] = mg;
+            }
+        free(buf);
+    }
+}
