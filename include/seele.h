@@ -297,6 +297,28 @@ seele_status seele_autotune(seele_ctx* ctx, seele_options* inout, float* best_ms
  *   out_assign     host or NULL, [n_poses] cluster of each pose
  * Synchronous; leaves the context's cameras as they were and no render
  * state behind. */
+/* Contribution skew of the current cameras (Sec. 1 "Rendering
+ * Inefficiency", Sec. 3.4 "Motivation"): the cameras are rendered with the
+ * plain rules (Sec. 3.1; no opacity or cluster filter, tile lists) and, per
+ * pixel, the contributions Gamma_i alpha_i of the Gaussians it blends are
+ * ranked in descending order.
+ *   opt          tile size, tile test, alpha_min / alpha_max / t_stop (NULL:
+ *                defaults); its mode, filters, binning and flags are ignored
+ *   frac         the share of the pixel's total to reach, 0 < frac <= 1 (0.99)
+ *   out_m        [sum W*H] smallest number of the largest contributions whose
+ *                sum reaches frac of their total (ties at the cut all count;
+ *                0 where nothing blends)
+ *   out_blended  [sum W*H] number of contributions
+ *   out_walked   [sum W*H] tile-list entries the pixel examined (up to and
+ *                including the one that would have crossed t_stop, else all)
+ *   out_total    [sum W*H] sum of the contributions (1 - final T)
+ *   out_listed   [sum W*H] or NULL: length of the pixel's tile list
+ * Outputs are host or device memory, each camera's pixels row-major after the
+ * previous camera's.  Synchronous; leaves no render state behind. */
+seele_status seele_contribution_skew(seele_ctx* ctx, const seele_options* opt, float frac, uint32_t* out_m,
+                                     uint32_t* out_blended, uint32_t* out_walked, float* out_total,
+                                     uint32_t* out_listed);
+
 seele_status seele_build_view_clusters(seele_ctx* ctx, const seele_camera* poses, int32_t n_poses,
                                        int32_t n_clusters, int32_t top_k, const double* uniforms,
                                        int32_t max_iter, float* out_centroids, float* out_pos_scale,

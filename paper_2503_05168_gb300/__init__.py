@@ -272,6 +272,34 @@ class Renderer:
             ctypes.c_void_p(assign.ctypes.data)))
         return dict(mask=mask, centroids=cent, pos_scale=float(scale.value), assign=assign)
 
+    def contribution_skew(self, frac: float = 0.99, tile=(16, 16), tile_test="ellipse", **kw):
+        """Contribution skew of a plain render of the current cameras (Sec. 1,
+        Sec. 3.4): per camera, dict(m, blended, walked, total, listed) as
+        [H, W] numpy arrays -- m the smallest number of a pixel's largest
+        contributions Gamma alpha that sum to ``frac`` of their total, listed
+        the length of its tile list."""
+        o = self.make_options(mode="plain", tile=tile, tile_test=tile_test, binning="tiles", **kw)
+        P = self.n_pixels
+        m = np.zeros(P, np.uint32)
+        blended = np.zeros(P, np.uint32)
+        walked = np.zeros(P, np.uint32)
+        total = np.zeros(P, np.float32)
+        listed = np.zeros(P, np.uint32)
+        self._sync_stream()
+        self._check(lib().seele_contribution_skew(
+            self._h, ctypes.byref(o), ctypes.c_float(frac), ctypes.c_void_p(m.ctypes.data),
+            ctypes.c_void_p(blended.ctypes.data), ctypes.c_void_p(walked.ctypes.data),
+            ctypes.c_void_p(total.ctypes.data), ctypes.c_void_p(listed.ctypes.data)))
+        out, off = [], 0
+        for c in self.cameras:
+            W, H = c["width"], c["height"]
+            sl = slice(off, off + W * H)
+            out.append(dict(m=m[sl].reshape(H, W), blended=blended[sl].reshape(H, W),
+                            walked=walked[sl].reshape(H, W), total=total[sl].reshape(H, W),
+                            listed=listed[sl].reshape(H, W)))
+            off += W * H
+        return out
+
     def debug_view(self) -> dict:
         """Copies of the last render's intermediates (CUDA tensors)."""
         torch = self._torch

@@ -83,6 +83,7 @@ PROTOTYPES = {
     "seele_sort_tile_instances_noalloc": (ctypes.c_int, [P, P, ctypes.c_uint32, ctypes.c_uint32, P, P, P, P]),
     "seele_build_view_clusters": (ctypes.c_int, [P, ctypes.POINTER(Camera), ctypes.c_int32, ctypes.c_int32,
                                                  ctypes.c_int32, P, ctypes.c_int32, P, P, P, P]),
+    "seele_contribution_skew": (ctypes.c_int, [P, ctypes.POINTER(Options), ctypes.c_float, P, P, P, P, P]),
 }
 NOALLOC_MAX_INSTANCES = 1 << 20
 NOALLOC_MAX_TILES = 1 << 16

@@ -89,6 +89,11 @@ struct seele_ctx {
     int topk_k = 0;
     const int* topk_cluster = nullptr;   // device, cluster of each camera of the frame
     uint32_t* topk_mask = nullptr;       // device, [n]
+    // contribution-skew statistic: while skew_frac > 0, frames end in the
+    // skew pass, writing [pixels] m, blended, walked (u32), total (f32) and
+    // listed (u32)
+    double skew_frac = 0.0;
+    DevBuf skew;
 };
 
 namespace {
@@ -534,7 +539,13 @@ seele_status enqueue_frame(seele_ctx* c, const seele_options* opt, const FrameIn
     ra.view_end = vt + 1;
     ra.view_done = reinterpret_cast<uint32_t*>(vt + 1 + ncam);
     SEELE_MARK(SEELE_STAGE_RASTER);
-    if (c->topk_k > 0) {
+    if (c->skew_frac > 0.0) {
+        uint32_t* sk = ptr<uint32_t>(c->skew);
+        if (!launch_skew(ra.starts, ra.ends, ra.inst_rec, ra.rec, cams, ncam, ra.n_tiles, f.fp, c->skew_frac, sk,
+                         sk + f.pix_total, sk + 2 * f.pix_total, reinterpret_cast<float*>(sk + 3 * f.pix_total),
+                         sk + 4 * f.pix_total, s))
+            return fail(c, SEELE_ERR_ARG, "no skew pass for these options");
+    } else if (c->topk_k > 0) {
         if (!launch_topk(ra.starts, ra.ends, ra.inst_rec, ra.rec, cams, ncam, ra.n_tiles, f.fp, c->topk_k,
                          c->topk_cluster, c->topk_mask, s))
             return fail(c, SEELE_ERR_ARG, "no top-k pass for these options");
@@ -604,7 +615,7 @@ void seele_destroy(seele_ctx* c) {
                      &c->visv[1], &c->offs, &c->instk[0], &c->instk[1], &c->instv[0], &c->instv[1],
                      &c->ranges, &c->status, &c->hist, &c->digtot, &c->T, &c->nc, &c->rgb_tmp, &c->sortcnt,
                      &c->grad_rec, &c->blocks, &c->instm[0], &c->instm[1], &c->msum, &c->border, &c->chunkv,
-                     &c->chunks, &c->vbuf, &c->cnts};
+                     &c->chunks, &c->vbuf, &c->cnts, &c->skew};
     for (DevBuf* b : all) release(*b);
     release(c->viewt);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -1018,6 +1029,43 @@ seele_status seele_get_debug_view(const seele_ctx* c, seele_debug_view* out) {
     out->records = ptr<const float>(m->rec);
     out->depth = ptr<const float>(m->depth);
     out->n_contrib = ptr<const uint32_t>(m->nc);
+    return SEELE_OK;
+}
+
+seele_status seele_contribution_skew(seele_ctx* c, const seele_options* opt, float frac, uint32_t* out_m,
+                                     uint32_t* out_blended, uint32_t* out_walked, float* out_total,
+                                     uint32_t* out_listed) {
+    if (!c) return SEELE_ERR_ARG;
+    if (!c->has_scene) return fail(c, SEELE_ERR_STATE, "no scene loaded");
+    if (c->cams.empty()) return fail(c, SEELE_ERR_STATE, "no cameras");
+    if (!(frac > 0.f && frac <= 1.f)) return fail(c, SEELE_ERR_ARG, "frac must be in (0, 1]");
+    if (!out_m || !out_blended || !out_walked || !out_total) return fail(c, SEELE_ERR_ARG, "every output is required");
+    SEELE_CUDA(c, cudaSetDevice(c->device));
+    seele_options o;
+    if (opt) o = *opt;
+    else seele_default_options(&o);
+    o.mode = SEELE_MODE_PLAIN;
+    o.opacity_filter = 0;
+    o.cluster_filter = 0;
+    o.binning = SEELE_BIN_TILES;
+    o.flags = 0;
+    uint64_t pix = 0;
+    for (const auto& cam : c->cams) pix += (uint64_t)cam.width * cam.height;
+    SEELE_CUDA(c, ensure(c->skew, 20 * pix));
+    SEELE_CUDA(c, ensure(c->rgb_tmp, 12 * pix));
+    c->skew_frac = frac;
+    const seele_status r = seele_render(c, &o, ptr<float>(c->rgb_tmp), nullptr, nullptr);
+    c->skew_frac = 0.0;
+    c->rendered = false;
+    if (r != SEELE_OK) return r;
+    cudaStream_t s = c->stream;
+    const uint32_t* sk = ptr<uint32_t>(c->skew);
+    SEELE_CUDA(c, cudaMemcpyAsync(out_m, sk, 4 * pix, cudaMemcpyDefault, s));
+    SEELE_CUDA(c, cudaMemcpyAsync(out_blended, sk + pix, 4 * pix, cudaMemcpyDefault, s));
+    SEELE_CUDA(c, cudaMemcpyAsync(out_walked, sk + 2 * pix, 4 * pix, cudaMemcpyDefault, s));
+    SEELE_CUDA(c, cudaMemcpyAsync(out_total, sk + 3 * pix, 4 * pix, cudaMemcpyDefault, s));
+    if (out_listed) SEELE_CUDA(c, cudaMemcpyAsync(out_listed, sk + 4 * pix, 4 * pix, cudaMemcpyDefault, s));
+    SEELE_CUDA(c, cudaStreamSynchronize(s));
     return SEELE_OK;
 }
 

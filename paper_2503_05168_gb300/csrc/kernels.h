@@ -89,6 +89,12 @@ void launch_block_order(const uint32_t* bstart, const uint32_t* bend, uint32_t n
 // into the per-Gaussian cluster mask.
 void launch_kmeans(const double* x, int n, int k, const double* u, int max_iter, double* cent, int* assign,
                    double* scratch, int* iters, cudaStream_t s);
+// Contribution skew per pixel over the tile lists (seele_contribution_skew).
+bool launch_skew(const uint32_t* starts, const uint32_t* ends, const uint32_t* inst_rec, const float4* rec,
+                 const CamDev* cams, int n_cams, uint32_t n_tiles, const FrameParams& fp, double frac,
+                 uint32_t* out_m, uint32_t* out_blended, uint32_t* out_walked, float* out_total,
+                 uint32_t* out_listed, cudaStream_t s);
+
 bool launch_topk(const uint32_t* starts, const uint32_t* ends, const uint32_t* inst_rec, const float4* rec,
                  const CamDev* cams, int n_cams, uint32_t n_tiles, const FrameParams& fp, int k,
                  const int* cam_cluster, uint32_t* mask, cudaStream_t s);
