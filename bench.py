@@ -344,6 +344,8 @@ def _ablation(args, device):
         "full": dict(mode="cr", opacity_filter=True, cluster_filter=True),
         "cr_group_1x1": dict(mode="cr", group=(1, 1)),
         "cr_group_2x4": dict(mode="cr", group=(2, 4)),
+        "cr_group_4x4": dict(mode="cr", group=(4, 4)),
+        "cr_group_4x8": dict(mode="cr", group=(4, 8)),
     }
     refs = []
     for c in cams:

@@ -142,7 +142,7 @@ enum {
 /* Render options.  seele_default_options fills the paper's constants. */
 typedef struct {
     int32_t mode;                 /* PLAIN (Sec. 3.1) or CR (Alg. 1) */
-    int32_t group_w, group_h;     /* CR pixel group: 2x2 (default), 1x1, 2x4 */
+    int32_t group_w, group_h;     /* CR pixel group: 2x2 (default), 1x1, 2x4, 4x4, 4x8 */
     int32_t tile_w, tile_h;       /* 16x16 (default), 32x8 or 32x16 */
     int32_t opacity_filter;       /* 1: support min(2 ln(o/alpha_theta), 9) (Eqn. 5) */
     int32_t cluster_filter;       /* 1: render only the selected view clusters (Sec. 3.3) */

@@ -198,7 +198,8 @@ uint32_t select_clusters(const seele_ctx* c, const seele_camera& cam, int M) {
 }
 
 bool group_supported(int gw, int gh) {
-    return (gw == 2 && gh == 2) || (gw == 1 && gh == 1) || (gw == 2 && gh == 4);
+    return (gw == 2 && gh == 2) || (gw == 1 && gh == 1) || (gw == 2 && gh == 4) || (gw == 4 && gh == 4) ||
+           (gw == 4 && gh == 8);
 }
 
 int bits_for(uint64_t v) {
@@ -270,7 +271,7 @@ seele_status check_options(seele_ctx* c, const seele_options* opt) {
     if (!tile_supported(opt->tile_w, opt->tile_h))
         return fail(c, SEELE_ERR_ARG, "tile size %dx%d not supported (16x16, 32x8, 32x16)", opt->tile_w, opt->tile_h);
     if (opt->mode == SEELE_MODE_CR && !group_supported(opt->group_w, opt->group_h))
-        return fail(c, SEELE_ERR_ARG, "pixel group %dx%d not supported (1x1, 2x2, 2x4)", opt->group_w, opt->group_h);
+        return fail(c, SEELE_ERR_ARG, "pixel group %dx%d not supported (1x1, 2x2, 2x4, 4x4, 4x8)", opt->group_w, opt->group_h);
     if (!(opt->alpha_min > 0 && opt->alpha_min < opt->alpha_max && opt->alpha_max <= 1.0f))
         return fail(c, SEELE_ERR_ARG, "need 0 < alpha_min < alpha_max <= 1");
     if (!(opt->t_stop > 0 && opt->t_stop < 1)) return fail(c, SEELE_ERR_ARG, "need 0 < t_stop < 1");

@@ -36,6 +36,10 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
     constexpr int NT = (TW / PW) * (TH / PH);
     constexpr int NP = PW * PH;
     constexpr int TXN = TW / PW;
+    // a group is a sub-block of the thread's pixels, or one or more whole
+    // thread blocks (the forward pass's rule); GWL x GHL is its part here
+    constexpr bool WHOLE = GW % PW == 0 && GH % PH == 0;
+    constexpr int GWL = WHOLE ? PW : GW, GHL = WHOLE ? PH : GH;
     __shared__ float4 s0[NT], s1[NT], s2[NT];
     __shared__ uint32_t s_r[NT];
     __shared__ uint32_t s_max;
@@ -82,6 +86,7 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
     __syncthreads();
     const uint32_t lmax = min(s_max, end - start);
     const float fx0 = (float)bx + 0.5f, fy0 = (float)by + 0.5f;
+    const float lx0 = (float)(bx / GW * GW) + 0.5f, ly0 = (float)(by / GH * GH) + 0.5f;  // the group's leader
     const float amax = fp.alpha_max;
 
     for (int b1 = (int)lmax; b1 > 0; b1 -= NT) {
@@ -109,25 +114,30 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
             float du = 0.f, dv = 0.f, dcA = 0.f, dcB = 0.f, dcC = 0.f, dlo = 0.f, dr = 0.f, dg = 0.f, db = 0.f;
             bool any = false;
 #pragma unroll
-            for (int gy = 0; gy < PH / GH; ++gy)
+            for (int gy = 0; gy < PH / GHL; ++gy)
 #pragma unroll
-                for (int gx = 0; gx < PW / GW; ++gx) {
+                for (int gx = 0; gx < PW / GWL; ++gx) {
                     bool lead = true;
                     if (CR) {
                         bool need = false;
 #pragma unroll
-                        for (int jj = 0; jj < GH; ++jj)
+                        for (int jj = 0; jj < GHL; ++jj)
 #pragma unroll
-                            for (int i = 0; i < GW; ++i) need |= j < last[(gy * GH + jj) * PW + gx * GW + i];
+                            for (int i = 0; i < GWL; ++i) need |= j < last[(gy * GHL + jj) * PW + gx * GWL + i];
                         if (!need) continue;
-                        lead = expo(gx * GW, gy * GH) >= B.z;
+                        if (WHOLE) {
+                            const float lx = lx0 - A.x, ly = ly0 - A.y;
+                            lead = fmaf(fmaf(A.z, lx, A.w * ly), lx, fmaf(B.x * ly, ly, B.y)) >= B.z;
+                        } else {
+                            lead = expo(gx * GW, gy * GH) >= B.z;
+                        }
                     }
                     if (!lead) continue;
 #pragma unroll
-                    for (int jj = 0; jj < GH; ++jj)
+                    for (int jj = 0; jj < GHL; ++jj)
 #pragma unroll
-                        for (int i = 0; i < GW; ++i) {
-                            const int pi = gx * GW + i, pj = gy * GH + jj;
+                        for (int i = 0; i < GWL; ++i) {
+                            const int pi = gx * GWL + i, pj = gy * GHL + jj;
                             const int p = pj * PW + pi;
                             if (!(j < last[p])) continue;
                             const float e = expo(pi, pj);
@@ -416,6 +426,8 @@ static bool launch_bwd_shape(const RasterBwdArgs& a, cudaStream_t s) {
     else if (a.group_w == 2 && a.group_h == 2) launch_bwd_one<TW, TH, 2, 2, 2, 2, true>(a, s);
     else if (a.group_w == 1 && a.group_h == 1) launch_bwd_one<TW, TH, 2, 2, 1, 1, true>(a, s);
     else if (a.group_w == 2 && a.group_h == 4) launch_bwd_one<TW, TH, 2, 4, 2, 4, true>(a, s);
+    else if (a.group_w == 4 && a.group_h == 4) launch_bwd_one<TW, TH, 2, 2, 4, 4, true>(a, s);
+    else if (a.group_w == 4 && a.group_h == 8) launch_bwd_one<TW, TH, 2, 4, 4, 8, true>(a, s);
     else return false;
     return true;
 }

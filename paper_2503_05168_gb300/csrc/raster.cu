@@ -4,9 +4,11 @@
 // One CTA per tile; each thread owns a PW x PH block of pixels, so a Gaussian
 // staged in shared memory is loaded once per 4 (or 8) pixels and the pixels of
 // a thread give four independent dependency chains.  Pixel groups of Alg. 1
-// are GW x GH sub-blocks of a thread's block with the top-left pixel as
-// leader (Sec. 4.1): the leader's exponent decides for its group, the
-// remaining pixels then apply the per-pixel rules.  A warp skips a Gaussian
+// are GW x GH sub-blocks of a thread's block, or unions of whole thread
+// blocks, with the top-left pixel as leader (Sec. 4.1): the leader's exponent
+// decides for its group, the remaining pixels then apply the per-pixel rules.
+// A group spanning several threads has each of them evaluate the leader's
+// exponent itself (the same FP32 operations on the same inputs).  A warp skips a Gaussian
 // outright when every group it holds rejects it -- the divergence-free skip of
 // Sec. 3.4 "GPU Parallelism".
 //
@@ -41,7 +43,9 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
     constexpr int NP = PW * PH;
     constexpr int TXN = TW / PW;
     constexpr int WIN = BLOCKS ? 32 * NT : 1;  // list entries filtered per window
-    static_assert(PW % GW == 0 && PH % GH == 0, "groups must tile the thread block");
+    static_assert((PW % GW == 0 && PH % GH == 0) || (GW % PW == 0 && GH % PH == 0),
+                  "groups tile the thread block or are tiled by thread blocks");
+    constexpr bool WHOLE = GW % PW == 0 && GH % PH == 0;  // a group is one or more whole thread blocks
     static_assert(NT % 32 == 0 && kBlockW * kBlockH == 32, "whole warps; one mask word per block entry");
     __shared__ float4 s0[NT], s1[NT], s2[NT];
     __shared__ uint32_t s_idx[WIN];          // block binning: list indices of the window's tile entries
@@ -93,6 +97,8 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
     uint2 rg = make_uint2(__ldg(starts + unit), __ldg(ends + unit));
     if (rg.x >= rg.y) rg = make_uint2(0u, 0u);  // no instances
     const float fx0 = (float)bx + 0.5f, fy0 = (float)by + 0.5f;
+    // the leader pixel of the group holding this thread's block (WHOLE groups)
+    const float lx0 = (float)(bx / GW * GW) + 0.5f, ly0 = (float)(by / GH * GH) + 0.5f;
     const float amax = fp.alpha_max, tstop = fp.t_stop;
     uint32_t n_lead = 0, n_eval = 0, n_blend = 0;  // counting variant only
 
@@ -172,11 +178,12 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
             __syncthreads();
         }
         do {
-        if (CR && GW == PW && GH == PH) {
-            // Alg. 1 with one group per thread.  Phase 1: the leader (pixel 0)
-            // tests every staged Gaussian -- independent of the blending state,
-            // so the tests run back to back.  Phase 2: only the Gaussians the
-            // leader kept are blended, in list order, by the group's pixels.
+        if (CR && WHOLE) {
+            // Alg. 1 with the thread's pixels inside one group.  Phase 1: the
+            // group's leader tests every staged Gaussian -- independent of the
+            // blending state, so the tests run back to back.  Phase 2: only the
+            // Gaussians the leader kept are blended, in list order, by the
+            // thread's pixels.
             if (live == 0u) continue;
             // the group's pixels' live flags as separate predicates for the
             // blend loop (no bit extraction per pixel), folded back after it
@@ -197,7 +204,7 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
                 if (i < n32) {
                     const float4 A = s0[c0 + i];
                     const float4 B = s1[c0 + i];
-                    const float dx = fx0 - A.x, dy = fy0 - A.y;
+                    const float dx = lx0 - A.x, dy = ly0 - A.y;
                     const float e0 = fmaf(fmaf(A.z, dx, A.w * dy), dx, fmaf(B.x * dy, dy, B.y));
                     if (COUNT) ++n_lead;
                     pass |= e0 >= B.z ? 1u << i : 0u;
@@ -275,8 +282,8 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
                 nc[p] = pos1;
                 if (COUNT) ++n_blend;
             };
-            if (CR && GW == PW && GH == PH) {
-                // handled by the two-phase path below
+            if (CR && WHOLE) {
+                // handled by the two-phase path above
             } else if (CR) {
 #pragma unroll
                 for (int gy = 0; gy < PH / GH; ++gy)
@@ -364,6 +371,8 @@ static bool launch_shape(const RasterArgs& a, cudaStream_t s) {
     else if (a.group_w == 2 && a.group_h == 2) launch_one<TW, TH, 2, 2, 2, 2, true>(a, s);
     else if (a.group_w == 1 && a.group_h == 1) launch_one<TW, TH, 2, 2, 1, 1, true>(a, s);
     else if (a.group_w == 2 && a.group_h == 4) launch_one<TW, TH, 2, 4, 2, 4, true>(a, s);
+    else if (a.group_w == 4 && a.group_h == 4) launch_one<TW, TH, 2, 2, 4, 4, true>(a, s);
+    else if (a.group_w == 4 && a.group_h == 8) launch_one<TW, TH, 2, 4, 4, 8, true>(a, s);
     else return false;
     return true;
 }

@@ -193,7 +193,8 @@ def test_block_binning_renders_bit_identical_to_tile_binning(Renderer, tile):
     r.load_scene(sc)
     r.set_cameras(cams)
     for kw in (dict(mode="plain"), dict(mode="cr"), dict(mode="cr", opacity_filter=True),
-               dict(mode="cr", group=(2, 4)), dict(mode="cr", group=(1, 1)), dict(mode="plain", tile_test="rect")):
+               dict(mode="cr", group=(2, 4)), dict(mode="cr", group=(1, 1)), dict(mode="cr", group=(4, 4)),
+               dict(mode="cr", group=(4, 8)), dict(mode="plain", tile_test="rect")):
         a, ta = parity.gpu_render(r, tile=tile, binning="tiles", **kw)
         nca = parity.debug_numpy(r)["n_contrib"]
         b, tb = parity.gpu_render(r, tile=tile, binning="blocks", **kw)
@@ -246,6 +247,8 @@ CASES = [
     dict(mode="cr", opacity_filter=True),
     dict(mode="cr", group=(1, 1)),
     dict(mode="cr", group=(2, 4)),
+    dict(mode="cr", group=(4, 4)),
+    dict(mode="cr", group=(4, 8)),
 ]
 
 
