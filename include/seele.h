@@ -198,6 +198,43 @@ seele_status seele_set_stream(seele_ctx* ctx, void* cuda_stream);
  * Invalidates any previous render state. */
 seele_status seele_load_scene(seele_ctx* ctx, const seele_scene_desc* scene);
 
+/* Streamed scene (Sec. 3.3 "Scene Prefetching").  Like seele_load_scene
+ * (COPY, host memory only) with view clusters, but the device holds only the
+ * shared Gaussians (mask with every cluster bit) and n_slots (1..64) slots of
+ * slot_gaussians Gaussians (0: the largest cluster's size); every cluster's
+ * Gaussians stay in pinned host memory (a Gaussian of several clusters is
+ * copied into each), cut into chunks of at most slot_gaussians, one per slot.
+ * Renders need the cluster filter, and the chunks of the clusters a frame's
+ * cameras select must fit the slots.  Before a frame, those chunks are loaded
+ * into slots on the render stream if not resident (the least recently used
+ * slot is refilled); a Gaussian held by several selected
+ * clusters' slots is drawn from the lowest cluster's, so the frame renders the
+ * same Gaussians as the whole scene with the cluster filter.  After a frame,
+ * each camera's position and viewing direction are extrapolated linearly
+ * `ahead` (>= 1) frames from its last two frames, and the clusters selected
+ * for that pose are prefetched (their chunks) into slots the frame does not read, on a
+ * separate copy stream that waits only for the last frame reading the slot;
+ * the next frame waits for a prefetched slot only when it needs it.
+ * Gradients, the view builder and the skew statistic need seele_load_scene. */
+seele_status seele_load_scene_streamed(seele_ctx* ctx, const seele_scene_desc* scene, int32_t n_slots,
+                                       int64_t slot_gaussians, int32_t ahead);
+
+typedef struct {
+    int64_t resident_bytes;    /* device bytes of the resident Gaussians (attributes and masks) */
+    int64_t full_bytes;        /* the same for the whole scene resident */
+    int64_t n_shared;          /* resident shared Gaussians */
+    int64_t slot_capacity;     /* Gaussians per slot */
+    int64_t n_slots;
+    int64_t n_chunks;          /* chunks the clusters are cut into */
+    int64_t frames;            /* frames rendered since the load */
+    int64_t loads_sync;        /* chunks a frame had to load itself */
+    int64_t loads_prefetched;  /* chunks loaded ahead on the copy stream */
+    int64_t prefetch_hits;     /* prefetched chunks a later frame used */
+    int64_t resident_hits;     /* needed chunks already resident from earlier frames */
+} seele_stream_stats;
+
+seele_status seele_get_stream_stats(const seele_ctx* ctx, seele_stream_stats* out);
+
 /* Sets n >= 1 cameras (host array, copied).  With view clusters loaded, also
  * runs the runtime cluster selection of Sec. 3.3 on the host: the nearest
  * centroid to the camera feature (position / s, view direction) and the

@@ -102,12 +102,16 @@ class Renderer:
             pass
 
     # -- scene and cameras ----------------------------------------------------
-    def load_scene(self, scene: dict, borrow: bool = False):
+    def load_scene(self, scene: dict, borrow: bool = False, streamed_slots: int = 0, slot_gaussians: int = 0,
+                   ahead: int = 1):
         """``scene``: means [n,3], log_scales [n,3], quats [n,4], opacity_logits [n],
         sh [n,nc,3] (float32), sh_degree, optional cluster_mask [n] uint32,
         centroids [C,6], pos_scale.  numpy arrays are host memory, torch CUDA
         tensors device memory.  ``borrow`` keeps references instead of copying
-        (device tensors only)."""
+        (device tensors only).  ``streamed_slots`` > 0 loads a streamed scene
+        (seele_load_scene_streamed: host arrays with view clusters; the shared
+        Gaussians and that many slots of ``slot_gaussians`` (0: the largest
+        cluster) resident, prefetching ``ahead`` frames)."""
         torch = self._torch
 
         def prep(a, dtype):
@@ -136,7 +140,11 @@ class Renderer:
         d.pos_scale = float(scene.get("pos_scale", 1.0))
         d.centroids = _ptr(cen)
         self._sync_stream()
-        self._check(lib().seele_load_scene(self._h, ctypes.byref(d)))
+        if streamed_slots > 0:
+            self._check(lib().seele_load_scene_streamed(self._h, ctypes.byref(d), int(streamed_slots),
+                                                        int(slot_gaussians), int(ahead)))
+        else:
+            self._check(lib().seele_load_scene(self._h, ctypes.byref(d)))
         self._keep = [arrs, mask, cen] if borrow else []
         self.n = n
         self.sh_degree = d.sh_degree
@@ -271,6 +279,12 @@ class Renderer:
             ctypes.c_void_p(cent.ctypes.data), ctypes.byref(scale), ctypes.c_void_p(mask.ctypes.data),
             ctypes.c_void_p(assign.ctypes.data)))
         return dict(mask=mask, centroids=cent, pos_scale=float(scale.value), assign=assign)
+
+    def stream_stats(self) -> dict:
+        """Residency and prefetch counters of a streamed scene."""
+        st = _abi.StreamStats()
+        self._check(lib().seele_get_stream_stats(self._h, ctypes.byref(st)))
+        return {k: int(getattr(st, k)) for k, _ in _abi.StreamStats._fields_}
 
     def contribution_skew(self, frac: float = 0.99, tile=(16, 16), tile_test="ellipse", **kw):
         """Contribution skew of a plain render of the current cameras (Sec. 1,

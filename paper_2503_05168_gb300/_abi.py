@@ -54,6 +54,12 @@ class Stats(ctypes.Structure):
                 ("pairs_blended", ctypes.c_int64)]
 
 
+class StreamStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("resident_bytes", "full_bytes", "n_shared", "slot_capacity", "n_slots",
+                                              "n_chunks", "frames", "loads_sync", "loads_prefetched",
+                                              "prefetch_hits", "resident_hits")]
+
+
 class Grads(ctypes.Structure):
     _fields_ = [("means", P), ("log_scales", P), ("quats", P), ("opacity_logits", P), ("sh", P)]
 
@@ -84,6 +90,9 @@ PROTOTYPES = {
     "seele_build_view_clusters": (ctypes.c_int, [P, ctypes.POINTER(Camera), ctypes.c_int32, ctypes.c_int32,
                                                  ctypes.c_int32, P, ctypes.c_int32, P, P, P, P]),
     "seele_contribution_skew": (ctypes.c_int, [P, ctypes.POINTER(Options), ctypes.c_float, P, P, P, P, P]),
+    "seele_load_scene_streamed": (ctypes.c_int, [P, ctypes.POINTER(SceneDesc), ctypes.c_int32, ctypes.c_int64,
+                                                 ctypes.c_int32]),
+    "seele_get_stream_stats": (ctypes.c_int, [P, ctypes.POINTER(StreamStats)]),
 }
 NOALLOC_MAX_INSTANCES = 1 << 20
 NOALLOC_MAX_TILES = 1 << 16

@@ -36,7 +36,7 @@ struct seele_ctx {
     int sh_degree = 0;
     int scene_flags = 0;
     seele_scene_desc borrowed{};
-    DevBuf pos_logit, quat, log_scale, sh, mask, staging;
+    DevBuf pos_logit, quat, log_scale, sh, mask, staging, veto;
     bool has_mask = false;
     int n_clusters = 0;
     std::vector<double> centroids;
@@ -94,6 +94,37 @@ struct seele_ctx {
     // listed (u32)
     double skew_frac = 0.0;
     DevBuf skew;
+
+    // Streamed scene (Sec. 3.3 "Scene Prefetching"): every view cluster's
+    // Gaussians stay in pinned host memory, cut into chunks of at most
+    // slot_cap; the device holds the shared Gaussians and n_slots slots of
+    // slot_cap Gaussians, each holding one chunk.  A frame loads the chunks of
+    // the clusters its cameras select that are not resident (on its own
+    // stream); after it, the chunks of the clusters selected for the cameras'
+    // linearly extrapolated poses are prefetched on the copy stream.
+    struct Streamed {
+        bool on = false;
+        int n_slots = 0, ahead = 1, planes = 0;   // planes: float4 per Gaussian
+        uint32_t n_shared = 0, cap = 0;
+        int64_t n_full = 0;                       // Gaussians of the whole scene
+        float4* host = nullptr;                   // pinned, [planes][copies]
+        uint32_t* host_mask = nullptr;            // pinned, [copies]: the copy's cluster bit
+        uint32_t* host_veto = nullptr;            // pinned, [copies]: the Gaussian's lower clusters
+        size_t copies = 0;
+        std::vector<size_t> seg;                  // [C + 2]: cluster c is [seg[c], seg[c + 1]), shared last
+        std::vector<int> chunk_begin;             // [C + 1]: cluster c's chunks are [chunk_begin[c], ..[c + 1])
+        std::vector<int> chunk_cluster;           // per chunk
+        std::vector<size_t> chunk_at;             // per chunk: first copy
+        std::vector<uint32_t> chunk_n;            // per chunk: copies
+        std::vector<int> slot_cluster;            // per slot: the chunk it holds, -1: empty
+        std::vector<bool> slot_async;             // filled on the copy stream, not yet waited for
+        std::vector<uint64_t> slot_stamp;         // last frame that used or filled it
+        std::vector<cudaEvent_t> slot_ready, slot_used;
+        cudaStream_t copy = nullptr;
+        uint64_t frame = 0;
+        std::vector<std::vector<double>> prev;    // per camera: position and view direction last frame
+        int64_t loads_sync = 0, loads_prefetch = 0, prefetch_hits = 0, resident_hits = 0;
+    } st;
 };
 
 namespace {
@@ -154,17 +185,21 @@ T* ptr(DevBuf& b) {
 #define SEELE_MARK_EXT(ctx, k) \
     if ((ctx)->profiling) cudaEventRecord((ctx)->ev[k], (ctx)->stream)
 
+// Camera centre and unit viewing direction (the third row of R).
+void camera_pose(const seele_camera& cam, double pos[3], double dir[3]) {
+    const float* w = cam.world_to_cam;
+    const double R[9] = {w[0], w[1], w[2], w[4], w[5], w[6], w[8], w[9], w[10]};
+    const double t[3] = {w[3], w[7], w[11]};
+    for (int i = 0; i < 3; ++i) pos[i] = -(R[i] * t[0] + R[3 + i] * t[1] + R[6 + i] * t[2]);
+    for (int i = 0; i < 3; ++i) dir[i] = R[6 + i];
+}
+
 // Runtime cluster selection (Sec. 3.3 "Algorithm"): nearest centroid to the
 // camera feature (position / s, unit viewing direction), then the M centroids
 // nearest to that centroid; ties go to the lower index.
-uint32_t select_clusters(const seele_ctx* c, const seele_camera& cam, int M) {
+uint32_t select_clusters_at(const seele_ctx* c, const double pos[3], const double dir[3], int M) {
     if (c->n_clusters <= 0) return 0xffffffffu;
-    const float* w = cam.world_to_cam;
-    double R[9] = {w[0], w[1], w[2], w[4], w[5], w[6], w[8], w[9], w[10]};
-    double t[3] = {w[3], w[7], w[11]};
-    double pos[3];
-    for (int i = 0; i < 3; ++i) pos[i] = -(R[i] * t[0] + R[3 + i] * t[1] + R[6 + i] * t[2]);
-    double f[6] = {pos[0] / c->pos_scale, pos[1] / c->pos_scale, pos[2] / c->pos_scale, R[6], R[7], R[8]};
+    double f[6] = {pos[0] / c->pos_scale, pos[1] / c->pos_scale, pos[2] / c->pos_scale, dir[0], dir[1], dir[2]};
     const int C = c->n_clusters;
     auto dist2 = [&](const double* a, const double* b) {
         double s = 0;
@@ -195,6 +230,170 @@ uint32_t select_clusters(const seele_ctx* c, const seele_camera& cam, int M) {
         bits |= 1u << arg;
     }
     return bits;
+}
+
+uint32_t select_clusters(const seele_ctx* c, const seele_camera& cam, int M) {
+    double pos[3], dir[3];
+    camera_pose(cam, pos, dir);
+    return select_clusters_at(c, pos, dir, M);
+}
+
+// ------------------------------------------------------- streamed scene --
+
+void stream_release(seele_ctx* c) {
+    auto& S = c->st;
+    if (S.copy) cudaStreamSynchronize(S.copy);
+    for (cudaEvent_t e : S.slot_ready)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : S.slot_used)
+        if (e) cudaEventDestroy(e);
+    if (S.copy) cudaStreamDestroy(S.copy);
+    if (S.host) cudaFreeHost(S.host);
+    if (S.host_mask) cudaFreeHost(S.host_mask);
+    if (S.host_veto) cudaFreeHost(S.host_veto);
+    S = seele_ctx::Streamed{};
+}
+
+// Copies m Gaussians from pool position b to resident position `at`, and
+// clears the rest of a slot of `room`.
+seele_status stream_copy(seele_ctx* c, size_t b, size_t m, uint32_t at, uint32_t room, cudaStream_t s) {
+    auto& S = c->st;
+    const size_t n = (size_t)c->n;
+    float4* planes[3] = {ptr<float4>(c->pos_logit), ptr<float4>(c->quat), ptr<float4>(c->log_scale)};
+    for (int p = 0; p < S.planes; ++p) {
+        float4* dst = p < 3 ? planes[p] + at : ptr<float4>(c->sh) + (size_t)(p - 3) * n + at;
+        if (m) SEELE_CUDA(c, cudaMemcpyAsync(dst, S.host + (size_t)p * S.copies + b, 16 * m, cudaMemcpyHostToDevice, s));
+    }
+    if (m) {
+        SEELE_CUDA(c, cudaMemcpyAsync(ptr<uint32_t>(c->mask) + at, S.host_mask + b, 4 * m, cudaMemcpyHostToDevice, s));
+        SEELE_CUDA(c, cudaMemcpyAsync(ptr<uint32_t>(c->veto) + at, S.host_veto + b, 4 * m, cudaMemcpyHostToDevice, s));
+    }
+    if (room > m) SEELE_CUDA(c, cudaMemsetAsync(ptr<uint32_t>(c->mask) + at + m, 0, 4 * (room - m), s));
+    return SEELE_OK;
+}
+
+// A slot to (re)fill: empty first, else the least recently used one whose
+// chunk's cluster is not in `keep`.
+int stream_victim(const seele_ctx* c, uint32_t keep) {
+    const auto& S = c->st;
+    int best = -1;
+    for (int s = 0; s < S.n_slots; ++s) {
+        const int ch = S.slot_cluster[s];
+        if (ch >= 0 && ((keep >> S.chunk_cluster[ch]) & 1u)) continue;
+        if (ch < 0) return s;
+        if (best < 0 || S.slot_stamp[s] < S.slot_stamp[best]) best = s;
+    }
+    return best;
+}
+
+int stream_slot_of(const seele_ctx* c, int ch) {
+    for (int s = 0; s < c->st.n_slots; ++s)
+        if (c->st.slot_cluster[s] == ch) return s;
+    return -1;
+}
+
+int stream_chunks(const seele_ctx* c, uint32_t clusters) {
+    int n = 0;
+    for (int k = 0; k < c->n_clusters; ++k)
+        if ((clusters >> k) & 1u) n += c->st.chunk_begin[k + 1] - c->st.chunk_begin[k];
+    return n;
+}
+
+// Before a frame: every cluster the cameras select is made resident (loaded
+// on the frame's stream when it is not), the frame waits for slots the copy
+// stream filled, and each camera learns which slots it may read.
+seele_status stream_prepare(seele_ctx* c) {
+    auto& S = c->st;
+    uint32_t need = 0;
+    for (const CamDev& d : c->camdev) need |= d.sel_bits;
+    need &= c->n_clusters >= 32 ? 0xffffffffu : ((1u << c->n_clusters) - 1u);
+    if (stream_chunks(c, need) > S.n_slots)
+        return fail(c, SEELE_ERR_ARG, "the cameras select %d clusters in %d chunks, more than the %d slots",
+                    __builtin_popcount(need), stream_chunks(c, need), S.n_slots);
+    ++S.frame;
+    for (int ch = 0; ch < (int)S.chunk_cluster.size(); ++ch) {
+        if (!((need >> S.chunk_cluster[ch]) & 1u)) continue;
+        int s = stream_slot_of(c, ch);
+        if (s >= 0) {
+            if (S.slot_async[s]) {
+                SEELE_CUDA(c, cudaStreamWaitEvent(c->stream, S.slot_ready[s], 0));
+                S.slot_async[s] = false;
+                ++S.prefetch_hits;
+            } else {
+                ++S.resident_hits;
+            }
+        } else {
+            s = stream_victim(c, need);
+            if (S.slot_async[s]) SEELE_CUDA(c, cudaStreamWaitEvent(c->stream, S.slot_ready[s], 0));
+            S.slot_async[s] = false;
+            const seele_status r =
+                stream_copy(c, S.chunk_at[ch], S.chunk_n[ch], S.n_shared + (uint32_t)s * S.cap, S.cap, c->stream);
+            if (r != SEELE_OK) return r;
+            S.slot_cluster[s] = ch;
+            ++S.loads_sync;
+        }
+        S.slot_stamp[s] = S.frame;
+    }
+    for (CamDev& d : c->camdev) {
+        d.slot_ok[0] = d.slot_ok[1] = 0;
+        for (int s = 0; s < S.n_slots; ++s) {
+            const int ch = S.slot_cluster[s];
+            if (ch >= 0 && ((d.sel_bits >> S.chunk_cluster[ch]) & 1u)) d.slot_ok[s >> 5] |= 1u << (s & 31);
+        }
+    }
+    return SEELE_OK;
+}
+
+// After a frame is enqueued: mark the slots it reads as used by it, then
+// prefetch the clusters selected for each camera's pose extrapolated
+// `ahead` frames (position and viewing direction, linearly from the last two
+// frames) into slots the frame does not read, on the copy stream.
+seele_status stream_prefetch(seele_ctx* c, int M) {
+    auto& S = c->st;
+    uint32_t used[2] = {0u, 0u};
+    for (const CamDev& d : c->camdev) {
+        used[0] |= d.slot_ok[0];
+        used[1] |= d.slot_ok[1];
+    }
+    for (int s = 0; s < S.n_slots; ++s)
+        if ((used[s >> 5] >> (s & 31)) & 1u) SEELE_CUDA(c, cudaEventRecord(S.slot_used[s], c->stream));
+    uint32_t now = 0, want = 0;
+    for (const CamDev& d : c->camdev) now |= d.sel_bits;
+    if (S.prev.size() != c->cams.size()) S.prev.assign(c->cams.size(), std::vector<double>());
+    for (size_t i = 0; i < c->cams.size(); ++i) {
+        double pos[3], dir[3];
+        camera_pose(c->cams[i], pos, dir);
+        if (S.prev[i].size() == 6) {
+            double p[3], v[3], len = 0;
+            for (int j = 0; j < 3; ++j) {
+                p[j] = pos[j] + S.ahead * (pos[j] - S.prev[i][j]);
+                v[j] = dir[j] + S.ahead * (dir[j] - S.prev[i][3 + j]);
+                len += v[j] * v[j];
+            }
+            len = std::sqrt(len);
+            if (len > 0)
+                for (int j = 0; j < 3; ++j) v[j] /= len;
+            want |= select_clusters_at(c, p, v, M);
+        }
+        S.prev[i] = {pos[0], pos[1], pos[2], dir[0], dir[1], dir[2]};
+    }
+    want &= ~now;
+    for (int ch = 0; ch < (int)S.chunk_cluster.size(); ++ch) {
+        if (!((want >> S.chunk_cluster[ch]) & 1u) || stream_slot_of(c, ch) >= 0) continue;
+        const int s = stream_victim(c, now | want);
+        if (s < 0) break;
+        // the copy waits for the last frame that read the slot
+        SEELE_CUDA(c, cudaStreamWaitEvent(S.copy, S.slot_used[s], 0));
+        const seele_status r =
+            stream_copy(c, S.chunk_at[ch], S.chunk_n[ch], S.n_shared + (uint32_t)s * S.cap, S.cap, S.copy);
+        if (r != SEELE_OK) return r;
+        SEELE_CUDA(c, cudaEventRecord(S.slot_ready[s], S.copy));
+        S.slot_cluster[s] = ch;
+        S.slot_async[s] = true;
+        S.slot_stamp[s] = S.frame;
+        ++S.loads_prefetch;
+    }
+    return SEELE_OK;
 }
 
 bool group_supported(int gw, int gh) {
@@ -346,6 +545,8 @@ void fill_params(seele_ctx* c, const seele_options* opt, FrameInfo& f) {
     fp.dilation = 0.3f;
     fp.frustum_slack = 1.3f;
     fp.n_tiles_total = (uint32_t)f.tiles_total;
+    fp.n_shared = c->st.on ? c->st.n_shared : 0u;
+    fp.slot_cap = c->st.on ? c->st.cap : 0u;
 }
 
 // Sizes every buffer of a frame at the current capacity (may allocate).
@@ -464,6 +665,7 @@ seele_status enqueue_frame(seele_ctx* c, const seele_options* opt, const FrameIn
     sc.mask = c->has_mask ? (c->scene_flags == SEELE_SCENE_BORROW ? c->borrowed.cluster_mask
                                                                   : ptr<const uint32_t>(c->mask))
                           : nullptr;
+    sc.veto = c->st.on ? ptr<const uint32_t>(c->veto) : nullptr;
     unsigned long long* vt = ptr<unsigned long long>(c->viewt);
     ProjOut po{ptr<float4>(c->rec), ptr<uint32_t>(c->tiles),
                f.blocks ? ptr<uint32_t>(c->blocks) : nullptr, ptr<float>(c->depth), vt, ptr<uint32_t>(c->chunkv)};
@@ -616,8 +818,9 @@ void seele_destroy(seele_ctx* c) {
                      &c->visv[1], &c->offs, &c->instk[0], &c->instk[1], &c->instv[0], &c->instv[1],
                      &c->ranges, &c->status, &c->hist, &c->digtot, &c->T, &c->nc, &c->rgb_tmp, &c->sortcnt,
                      &c->grad_rec, &c->blocks, &c->instm[0], &c->instm[1], &c->msum, &c->border, &c->chunkv,
-                     &c->chunks, &c->vbuf, &c->cnts, &c->skew};
+                     &c->chunks, &c->vbuf, &c->cnts, &c->skew, &c->veto};
     for (DevBuf* b : all) release(*b);
+    stream_release(c);
     release(c->viewt);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -656,6 +859,7 @@ seele_status seele_load_scene(seele_ctx* c, const seele_scene_desc* d) {
     c->has_scene = false;
     c->rendered = false;
     ++c->scene_gen;
+    stream_release(c);
     const int64_t n = d->n;
     const int nc = (d->sh_degree + 1) * (d->sh_degree + 1);
     const int planes = (3 * nc + 3) / 4;
@@ -710,6 +914,143 @@ seele_status seele_load_scene(seele_ctx* c, const seele_scene_desc* d) {
     c->pos_scale = d->pos_scale;
     c->centroids.assign(d->centroids ? d->centroids : nullptr, d->centroids ? d->centroids + 6 * d->n_clusters : nullptr);
     c->has_scene = true;
+    return SEELE_OK;
+}
+
+seele_status seele_load_scene_streamed(seele_ctx* c, const seele_scene_desc* d, int32_t n_slots,
+                                       int64_t slot_gaussians, int32_t ahead) {
+    if (!c) return SEELE_ERR_ARG;
+    if (!d) return fail(c, SEELE_ERR_ARG, "scene descriptor is NULL");
+    if (d->flags != SEELE_SCENE_COPY) return fail(c, SEELE_ERR_ARG, "a streamed scene is copied (COPY)");
+    if (d->n < 1 || d->n > (int64_t)65535 * 256)
+        return fail(c, SEELE_ERR_ARG, "n = %lld out of range (1 .. 16776960)", (long long)d->n);
+    if (d->sh_degree < 0 || d->sh_degree > 3) return fail(c, SEELE_ERR_ARG, "sh_degree must be 0..3");
+    if (d->n_clusters < 1 || d->n_clusters > 32 || !d->cluster_mask || !d->centroids || !(d->pos_scale > 0))
+        return fail(c, SEELE_ERR_ARG, "a streamed scene needs 1..32 view clusters, masks, centroids and pos_scale");
+    if (n_slots < 1 || n_slots > 64) return fail(c, SEELE_ERR_ARG, "n_slots must be 1..64");
+    if (slot_gaussians < 0) return fail(c, SEELE_ERR_ARG, "slot_gaussians must be >= 0");
+    if (ahead < 1) return fail(c, SEELE_ERR_ARG, "ahead must be >= 1");
+    const void* hp[] = {d->means, d->log_scales, d->quats, d->opacity_logits, d->sh, d->cluster_mask};
+    for (const void* q : hp)
+        if (!q || is_device_ptr(q)) return fail(c, SEELE_ERR_ARG, "a streamed scene is read from host memory");
+    SEELE_CUDA(c, cudaSetDevice(c->device));
+    SEELE_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->has_scene = false;
+    c->rendered = false;
+    ++c->scene_gen;
+    stream_release(c);
+    auto& S = c->st;
+    const int64_t n = d->n;
+    const int C = d->n_clusters, nc = (d->sh_degree + 1) * (d->sh_degree + 1), np = (3 * nc + 3) / 4;
+    const uint32_t all = C >= 32 ? 0xffffffffu : ((1u << C) - 1u);
+    // segments: cluster k holds every Gaussian with bit k (a Gaussian of
+    // several clusters is copied into each), the shared ones (every bit) last
+    std::vector<std::vector<uint32_t>> seg(C + 1);
+    for (int64_t g = 0; g < n; ++g) {
+        const uint32_t m = d->cluster_mask[g] & all;
+        if (m == 0u) continue;
+        if (m == all) {
+            seg[C].push_back((uint32_t)g);
+            continue;
+        }
+        for (int k = 0; k < C; ++k)
+            if ((m >> k) & 1u) seg[k].push_back((uint32_t)g);
+    }
+    S.planes = 3 + np;
+    S.seg.assign(C + 2, 0);
+    for (int k = 0; k <= C; ++k) S.seg[k + 1] = S.seg[k] + seg[k].size();
+    S.copies = S.seg[C + 1];
+    S.n_shared = (uint32_t)seg[C].size();
+    // slot size: as asked, else the largest cluster (one chunk per cluster)
+    uint64_t largest = 1;
+    for (int k = 0; k < C; ++k) largest = std::max<uint64_t>(largest, seg[k].size());
+    S.cap = (uint32_t)std::min<uint64_t>(slot_gaussians > 0 ? (uint64_t)slot_gaussians : largest, largest);
+    S.chunk_begin.assign(C + 1, 0);
+    for (int k = 0; k < C; ++k) {
+        S.chunk_begin[k] = (int)S.chunk_cluster.size();
+        for (size_t b = 0; b < seg[k].size(); b += S.cap) {
+            S.chunk_cluster.push_back(k);
+            S.chunk_at.push_back(S.seg[k] + b);
+            S.chunk_n.push_back((uint32_t)std::min<size_t>(S.cap, seg[k].size() - b));
+        }
+    }
+    S.chunk_begin[C] = (int)S.chunk_cluster.size();
+    S.n_slots = n_slots;
+    S.ahead = ahead;
+    S.n_full = n;
+    const uint64_t n_res = (uint64_t)S.n_shared + (uint64_t)n_slots * S.cap;
+    SEELE_CUDA(c, cudaMallocHost(&S.host, 16 * (size_t)S.planes * std::max<size_t>(S.copies, 1)));
+    SEELE_CUDA(c, cudaMallocHost(&S.host_mask, 4 * std::max<size_t>(S.copies, 1)));
+    SEELE_CUDA(c, cudaMallocHost(&S.host_veto, 4 * std::max<size_t>(S.copies, 1)));
+    // plane-major copies in the library's layout (planes of float4)
+    for (int k = 0; k <= C; ++k)
+        for (size_t i = 0; i < seg[k].size(); ++i) {
+            const size_t at = S.seg[k] + i, g = seg[k][i];
+            float4* H = S.host;
+            H[at] = make_float4(d->means[3 * g], d->means[3 * g + 1], d->means[3 * g + 2], d->opacity_logits[g]);
+            H[S.copies + at] = make_float4(d->quats[4 * g], d->quats[4 * g + 1], d->quats[4 * g + 2], d->quats[4 * g + 3]);
+            H[2 * S.copies + at] =
+                make_float4(d->log_scales[3 * g], d->log_scales[3 * g + 1], d->log_scales[3 * g + 2], 0.f);
+            const float* sh = d->sh + g * 3 * nc;
+            for (int j = 0; j < np; ++j) {
+                float v[4];
+                for (int q = 0; q < 4; ++q) v[q] = 4 * j + q < 3 * nc ? sh[4 * j + q] : 0.f;
+                H[(size_t)(3 + j) * S.copies + at] = make_float4(v[0], v[1], v[2], v[3]);
+            }
+            const uint32_t m = d->cluster_mask[g] & all;
+            S.host_mask[at] = k == C ? 0xffffffffu : (1u << k);
+            S.host_veto[at] = k == C ? 0u : (m & ((1u << k) - 1u));
+        }
+    c->n = (int64_t)n_res;
+    SEELE_CUDA(c, ensure(c->pos_logit, 16 * n_res));
+    SEELE_CUDA(c, ensure(c->quat, 16 * n_res));
+    SEELE_CUDA(c, ensure(c->log_scale, 16 * n_res));
+    SEELE_CUDA(c, ensure(c->sh, 16 * n_res * np));
+    SEELE_CUDA(c, ensure(c->mask, 4 * n_res));
+    SEELE_CUDA(c, ensure(c->veto, 4 * n_res));
+    SEELE_CUDA(c, cudaMemsetAsync(c->mask.p, 0, 4 * n_res, c->stream));
+    SEELE_CUDA(c, cudaMemsetAsync(c->veto.p, 0, 4 * n_res, c->stream));
+    const seele_status r = stream_copy(c, S.seg[C], S.n_shared, 0, S.n_shared, c->stream);
+    if (r != SEELE_OK) return r;
+    S.slot_cluster.assign(n_slots, -1);
+    S.slot_async.assign(n_slots, false);
+    S.slot_stamp.assign(n_slots, 0);
+    S.slot_ready.assign(n_slots, nullptr);
+    S.slot_used.assign(n_slots, nullptr);
+    for (int s = 0; s < n_slots; ++s) {
+        SEELE_CUDA(c, cudaEventCreateWithFlags(&S.slot_ready[s], cudaEventDisableTiming));
+        SEELE_CUDA(c, cudaEventCreateWithFlags(&S.slot_used[s], cudaEventDisableTiming));
+    }
+    SEELE_CUDA(c, cudaStreamCreateWithFlags(&S.copy, cudaStreamNonBlocking));
+    SEELE_CUDA(c, cudaStreamSynchronize(c->stream));
+    S.on = true;
+    c->sh_degree = d->sh_degree;
+    c->scene_flags = SEELE_SCENE_COPY;
+    c->has_mask = true;
+    c->n_clusters = C;
+    c->pos_scale = d->pos_scale;
+    c->centroids.assign(d->centroids, d->centroids + 6 * C);
+    c->has_scene = true;
+    return SEELE_OK;
+}
+
+seele_status seele_get_stream_stats(const seele_ctx* c, seele_stream_stats* out) {
+    if (!c || !out) return SEELE_ERR_ARG;
+    seele_ctx* m = const_cast<seele_ctx*>(c);
+    if (!c->st.on) return fail(m, SEELE_ERR_STATE, "no streamed scene loaded");
+    const auto& S = c->st;
+    const int64_t per = 16 * S.planes + 4;  // attribute planes and the cluster mask
+    out->full_bytes = per * S.n_full;
+    out->resident_bytes = (per + 4) * c->n;  // plus the precedence mask
+    out->n_shared = S.n_shared;
+    out->slot_capacity = S.cap;
+    out->n_slots = S.n_slots;
+    out->n_chunks = (int64_t)S.chunk_cluster.size();
+    out->frames = (int64_t)S.frame;
+    out->loads_sync = S.loads_sync;
+    out->loads_prefetched = S.loads_prefetch;
+    out->prefetch_hits = S.prefetch_hits;
+    out->resident_hits = S.resident_hits;
     return SEELE_OK;
 }
 
@@ -776,6 +1117,11 @@ seele_status seele_render(seele_ctx* c, const seele_options* opt, float* out_rgb
     build_cameras(c, opt, f.tiles_total, f.blocks_total, f.pix_total);
     if (f.tiles_total >= (1ull << 31) || f.pix_total >= (1ull << 31))
         return fail(c, SEELE_ERR_ARG, "too many tiles or pixels in one render");
+    if (c->st.on) {
+        if (!opt->cluster_filter) return fail(c, SEELE_ERR_ARG, "a streamed scene renders with the cluster filter");
+        const seele_status sp = stream_prepare(c);
+        if (sp != SEELE_OK) return sp;
+    }
     f.blocks = opt->binning == SEELE_BIN_BLOCKS;
     f.units_total = f.blocks ? f.blocks_total : f.tiles_total;
     f.short_keys = f.units_total <= kShortKeyMaxTiles;
@@ -864,6 +1210,10 @@ seele_status seele_render(seele_ctx* c, const seele_options* opt, float* out_rgb
         break;
     }
 
+    if (c->st.on) {
+        const seele_status sp = stream_prefetch(c, opt->n_neighbors);
+        if (sp != SEELE_OK) return sp;
+    }
     if (!f.rgb_dev)
         SEELE_CUDA(c, cudaMemcpyAsync(out_rgb, c->rgb_tmp.p, 12 * f.pix_total, cudaMemcpyDeviceToHost, c->stream));
     if (out_T && !f.T_dev)
@@ -961,6 +1311,7 @@ seele_status seele_autotune(seele_ctx* c, seele_options* inout, float* best_ms) 
 seele_status seele_render_backward(seele_ctx* c, const float* dL_drgb, const seele_grads* g) {
     if (!c) return SEELE_ERR_ARG;
     if (!c->rendered) return fail(c, SEELE_ERR_STATE, "no render to differentiate");
+    if (c->st.on) return fail(c, SEELE_ERR_STATE, "gradients need the whole scene resident (seele_load_scene)");
     if (!dL_drgb || !g || !g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh)
         return fail(c, SEELE_ERR_ARG, "dL_drgb and every gradient buffer are required");
     SEELE_CUDA(c, cudaSetDevice(c->device));
@@ -1038,6 +1389,7 @@ seele_status seele_contribution_skew(seele_ctx* c, const seele_options* opt, flo
                                      uint32_t* out_listed) {
     if (!c) return SEELE_ERR_ARG;
     if (!c->has_scene) return fail(c, SEELE_ERR_STATE, "no scene loaded");
+    if (c->st.on) return fail(c, SEELE_ERR_STATE, "the skew statistic needs the whole scene resident");
     if (c->cams.empty()) return fail(c, SEELE_ERR_STATE, "no cameras");
     if (!(frac > 0.f && frac <= 1.f)) return fail(c, SEELE_ERR_ARG, "frac must be in (0, 1]");
     if (!out_m || !out_blended || !out_walked || !out_total) return fail(c, SEELE_ERR_ARG, "every output is required");
@@ -1075,6 +1427,7 @@ seele_status seele_build_view_clusters(seele_ctx* c, const seele_camera* poses, 
                                        float* out_pos_scale, uint32_t* out_mask, int32_t* out_assign) {
     if (!c) return SEELE_ERR_ARG;
     if (!c->has_scene) return fail(c, SEELE_ERR_STATE, "no scene loaded");
+    if (c->st.on) return fail(c, SEELE_ERR_STATE, "the builder needs the whole scene resident");
     if (!poses || !uniforms || !out_centroids || !out_pos_scale || !out_mask)
         return fail(c, SEELE_ERR_ARG, "poses, uniforms and the outputs are required");
     if (n_clusters < 1 || n_clusters > 32 || n_poses < n_clusters)

@@ -49,7 +49,9 @@ struct CamDev {
     uint32_t sel_bits;       // selected view clusters
     uint32_t block_offset;   // first global tile-block id of this camera (block binning)
     int32_t blocks_x;        // tile blocks per row: ceil(tiles_x / kBlockW)
-    int32_t pad[3];
+    uint32_t slot_ok[2];     // streamed scene: slots (bit s of word s / 32) ready to read that
+                             // hold part of a selected cluster
+    int32_t pad;
 };
 
 // Records are counted in chunks of this many for the ordered compaction and
@@ -81,6 +83,8 @@ struct FrameParams {
     float dilation;
     float frustum_slack;
     uint32_t n_tiles_total;
+    uint32_t n_shared;       // streamed scene: resident shared Gaussians, then slots of slot_cap
+    uint32_t slot_cap;       // 0: the whole scene is resident
 };
 
 // Scene in the library's layout (structure of arrays, 16-byte aligned).
@@ -90,6 +94,7 @@ struct SceneDev {
     const float4* log_scale;   // (lx, ly, lz, 0)
     const float4* sh;          // plane-major: sh[j * n + g], j < ceil(3 nc / 4)
     const uint32_t* mask;      // [n] or nullptr
+    const uint32_t* veto;      // streamed scene: [n] clusters that take precedence, or nullptr
 };
 
 // Raster record: kRecF4 float4 per record, one 64-byte line:

@@ -98,8 +98,18 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev sc, const CamD
     const CamDev& C = cams[ci];
     uint32_t ntiles = 0, nblocks = 0;
     do {
-        // view-cluster filter: selected clusters plus shared Gaussians (Sec. 3.3)
-        if (fp.use_mask && (__ldg(sc.mask + g) & C.sel_bits) == 0u) break;
+        // view-cluster filter: selected clusters plus shared Gaussians (Sec. 3.3);
+        // a streamed scene's slot is read only when it holds a selected cluster
+        // and is ready, and a Gaussian held by several selected clusters' slots
+        // is kept in the slot of the lowest one (veto: the lower clusters)
+        if (fp.use_mask) {
+            if (fp.slot_cap != 0u && (uint32_t)g >= fp.n_shared) {
+                const uint32_t slot = ((uint32_t)g - fp.n_shared) / fp.slot_cap;
+                if (!((C.slot_ok[slot >> 5] >> (slot & 31u)) & 1u)) break;
+            }
+            if ((__ldg(sc.mask + g) & C.sel_bits) == 0u) break;
+            if (sc.veto != nullptr && (__ldg(sc.veto + g) & C.sel_bits) != 0u) break;
+        }
         const float4 pl = __ldg(sc.pos_logit + g);
         const float X = fmaf(C.R[0], pl.x, fmaf(C.R[1], pl.y, fmaf(C.R[2], pl.z, C.t[0])));
         const float Y = fmaf(C.R[3], pl.x, fmaf(C.R[4], pl.y, fmaf(C.R[5], pl.z, C.t[1])));
