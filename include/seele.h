@@ -61,17 +61,24 @@ typedef enum {
     SEELE_ERR_INTERNAL = 7   /* a device consistency check failed (outputs undefined) */
 } seele_status;
 
-enum { SEELE_SCENE_COPY = 0, SEELE_SCENE_BORROW = 1 };
+enum { SEELE_SCENE_COPY = 0, SEELE_SCENE_BORROW = 1, SEELE_SCENE_SPATIAL = 2 };
 
 /* Scene description.  COPY: the library copies the attributes (host or device
  * pointers) into its own layout and owns that copy.  BORROW: the pointers are
  * device memory owned by the caller, must stay valid and unchanged in size
  * until the next seele_load_scene or seele_destroy, and are re-read by every
- * render (their contents may change between renders, as in training). */
+ * render (their contents may change between renders, as in training).
+ * COPY | SPATIAL also stores the Gaussians in Morton order of their means
+ * (computed on the device at load), so that Gaussians culled together are
+ * stored together and preprocessing reads less of the scene.  Images are the
+ * same up to Gaussians at exactly equal depth (ties break by stored index);
+ * gradients and view-builder masks come back in the caller's order, while
+ * record ids in seele_debug_view follow the stored order (its scene_order maps
+ * them back). */
 typedef struct {
     int64_t n;                    /* number of Gaussians, 1 <= n <= 16776960, n * cameras < 2^31 */
     int32_t sh_degree;            /* 0..3 */
-    int32_t flags;                /* SEELE_SCENE_COPY or SEELE_SCENE_BORROW */
+    int32_t flags;                /* SEELE_SCENE_COPY or SEELE_SCENE_BORROW, optionally | SEELE_SCENE_SPATIAL */
     const float* means;           /* [n][3] */
     const float* log_scales;      /* [n][3] */
     const float* quats;           /* [n][4] */
@@ -294,6 +301,8 @@ typedef struct {
                                      pixel's tile list */
     const uint32_t* inst_mask;    /* SEELE_BIN_BLOCKS: [n_instances] tiles of the block the
                                      entry reaches, bit j*8 + i for tile (i, j); else NULL */
+    const uint32_t* scene_order;  /* SEELE_SCENE_SPATIAL: [n] the caller's index of stored
+                                     Gaussian g (record id = camera * n + g); else NULL */
 } seele_debug_view;
 
 seele_status seele_get_debug_view(const seele_ctx* ctx, seele_debug_view* out);

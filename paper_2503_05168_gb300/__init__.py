@@ -103,7 +103,7 @@ class Renderer:
 
     # -- scene and cameras ----------------------------------------------------
     def load_scene(self, scene: dict, borrow: bool = False, streamed_slots: int = 0, slot_gaussians: int = 0,
-                   ahead: int = 1):
+                   ahead: int = 1, spatial: bool = False):
         """``scene``: means [n,3], log_scales [n,3], quats [n,4], opacity_logits [n],
         sh [n,nc,3] (float32), sh_degree, optional cluster_mask [n] uint32,
         centroids [C,6], pos_scale.  numpy arrays are host memory, torch CUDA
@@ -111,7 +111,8 @@ class Renderer:
         (device tensors only).  ``streamed_slots`` > 0 loads a streamed scene
         (seele_load_scene_streamed: host arrays with view clusters; the shared
         Gaussians and that many slots of ``slot_gaussians`` (0: the largest
-        cluster) resident, prefetching ``ahead`` frames)."""
+        cluster) resident, prefetching ``ahead`` frames).  ``spatial`` stores
+        the Gaussians in Morton order of their means (SEELE_SCENE_SPATIAL)."""
         torch = self._torch
 
         def prep(a, dtype):
@@ -132,7 +133,7 @@ class Renderer:
         d = _abi.SceneDesc()
         d.n = n
         d.sh_degree = int(scene["sh_degree"])
-        d.flags = _abi.SCENE_BORROW if borrow else _abi.SCENE_COPY
+        d.flags = (_abi.SCENE_BORROW if borrow else _abi.SCENE_COPY) | (_abi.SCENE_SPATIAL if spatial else 0)
         d.means, d.log_scales, d.quats = _ptr(arrs["means"]), _ptr(arrs["log_scales"]), _ptr(arrs["quats"])
         d.opacity_logits, d.sh = _ptr(arrs["opacity_logits"]), _ptr(arrs["sh"])
         d.cluster_mask = _ptr(mask)
@@ -348,6 +349,7 @@ class Renderer:
             records=records[:, :12].contiguous(), depth=dev(v.depth, R, torch.float32),
             n_contrib=dev(v.n_contrib, self.n_pixels, i32),
             inst_mask=dev(v.inst_mask, K, i32) if v.inst_mask else None,
+            scene_order=dev(v.scene_order, R // max(1, len(self.cameras)), i32) if v.scene_order else None,
         )
 
 

@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(HERE, "libseele.so")
 SEELE_OK = 0
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_STATE", 3: "ERR_CUDA", 4: "ERR_CAPACITY", 5: "ERR_TIMEOUT",
                 6: "ERR_OOM", 7: "ERR_INTERNAL"}
-SCENE_COPY, SCENE_BORROW = 0, 1
+SCENE_COPY, SCENE_BORROW, SCENE_SPATIAL = 0, 1, 2
 MODE_PLAIN, MODE_CR = 0, 1
 TILES_RECT, TILES_ELLIPSE = 0, 1
 BIN_TILES, BIN_BLOCKS = 0, 1
@@ -68,7 +68,7 @@ class DebugView(ctypes.Structure):
     _fields_ = [("n_records", ctypes.c_int64), ("n_visible", ctypes.c_int64), ("n_instances", ctypes.c_int64),
                 ("n_tiles", ctypes.c_int64), ("inst_record", P), ("tile_start", P), ("tile_end", P),
                 ("tiles_touched", P), ("records", P), ("depth", P), ("n_contrib", P),
-                ("inst_mask", P)]
+                ("inst_mask", P), ("scene_order", P)]
 
 
 # name -> (restype, argtypes); the ABI test checks this table against the header

@@ -37,6 +37,10 @@ struct seele_ctx {
     int scene_flags = 0;
     seele_scene_desc borrowed{};
     DevBuf pos_logit, quat, log_scale, sh, mask, staging, veto;
+    // spatial order (SEELE_SCENE_SPATIAL): caller index of each resident
+    // Gaussian, the planes before the gather, a few words of scratch
+    DevBuf order, unordered, order_scratch;
+    bool spatial = false;
     bool has_mask = false;
     int n_clusters = 0;
     std::vector<double> centroids;
@@ -238,6 +242,49 @@ uint32_t select_clusters(const seele_ctx* c, const seele_camera& cam, int M) {
     return select_clusters_at(c, pos, dir, M);
 }
 
+// Digit totals of the sorts' passes, 256 words per pass: the depth sort's
+// four, then up to four of the tile sort.
+constexpr uint32_t kDepthSortTotals = 4 * 256;
+constexpr uint32_t kDigitTotalWords = 8 * 256;
+
+// ------------------------------------------------------- spatial order --
+
+// Reorders the planes built in c->unordered (and the cluster mask) into
+// Morton order of the means; c->order keeps each one's caller index.
+seele_status spatial_order(seele_ctx* c, int64_t n, int planes) {
+    cudaStream_t s = c->stream;
+    SEELE_CUDA(c, ensure(c->order, 4 * n));
+    SEELE_CUDA(c, ensure(c->order_scratch, 64));
+    for (int i = 0; i < 2; ++i) {
+        SEELE_CUDA(c, ensure(c->visk[i], 4 * n));
+        SEELE_CUDA(c, ensure(c->visv[i], 4 * n));
+    }
+    const uint32_t words = radix_count_words((uint32_t)n);
+    SEELE_CUDA(c, ensure(c->sortcnt, 8ull * words));
+    SEELE_CUDA(c, ensure(c->digtot, 4 * kDigitTotalWords));
+    uint32_t* bb = ptr<uint32_t>(c->order_scratch);
+    const uint32_t count = (uint32_t)n;
+    SEELE_CUDA(c, cudaMemcpy(bb + 6, &count, 4, cudaMemcpyHostToDevice));
+    uint32_t* keys[2] = {ptr<uint32_t>(c->visk[0]), ptr<uint32_t>(c->visk[1])};
+    uint32_t* vals[2] = {ptr<uint32_t>(c->visv[0]), ptr<uint32_t>(c->visv[1])};
+    const float4* P0 = ptr<float4>(c->unordered);
+    const int fin = launch_spatial_order(P0, (int)n, bb, keys, vals, bb + 6, ptr<uint32_t>(c->sortcnt),
+                                         ptr<uint32_t>(c->sortcnt) + words, ptr<uint32_t>(c->digtot), s);
+    if (fin < 0) return fail(c, SEELE_ERR_CUDA, "spatial order: %s", cudaGetErrorString(cudaGetLastError()));
+    const uint32_t* ord = vals[fin];
+    SEELE_CUDA(c, cudaMemcpyAsync(c->order.p, ord, 4 * n, cudaMemcpyDeviceToDevice, s));
+    launch_gather_planes(P0, ptr<float4>(c->pos_logit), (int)n, 1, ord, s);
+    launch_gather_planes(P0 + n, ptr<float4>(c->quat), (int)n, 1, ord, s);
+    launch_gather_planes(P0 + 2 * n, ptr<float4>(c->log_scale), (int)n, 1, ord, s);
+    launch_gather_planes(P0 + 3 * n, ptr<float4>(c->sh), (int)n, planes, ord, s);
+    if (c->has_mask) {
+        SEELE_CUDA(c, cudaMemcpyAsync(keys[1], c->mask.p, 4 * n, cudaMemcpyDeviceToDevice, s));
+        launch_gather_u32(keys[1], ptr<uint32_t>(c->mask), (int)n, ord, s);
+    }
+    SEELE_LAUNCHED(c);
+    return SEELE_OK;
+}
+
 // ------------------------------------------------------- streamed scene --
 
 void stream_release(seele_ctx* c) {
@@ -409,11 +456,6 @@ int bits_for(uint64_t v) {
     }
     return b;
 }
-
-// Digit totals of the sorts' passes, 256 words per pass: the depth sort's
-// four, then up to four of the tile sort.
-constexpr uint32_t kDepthSortTotals = 4 * 256;
-constexpr uint32_t kDigitTotalWords = 8 * 256;
 
 struct FrameInfo {
     int ncam = 0;
@@ -818,7 +860,8 @@ void seele_destroy(seele_ctx* c) {
                      &c->visv[1], &c->offs, &c->instk[0], &c->instk[1], &c->instv[0], &c->instv[1],
                      &c->ranges, &c->status, &c->hist, &c->digtot, &c->T, &c->nc, &c->rgb_tmp, &c->sortcnt,
                      &c->grad_rec, &c->blocks, &c->instm[0], &c->instm[1], &c->msum, &c->border, &c->chunkv,
-                     &c->chunks, &c->vbuf, &c->cnts, &c->skew, &c->veto};
+                     &c->chunks, &c->vbuf, &c->cnts, &c->skew, &c->veto, &c->order, &c->unordered,
+                     &c->order_scratch};
     for (DevBuf* b : all) release(*b);
     stream_release(c);
     release(c->viewt);
@@ -850,8 +893,11 @@ seele_status seele_load_scene(seele_ctx* c, const seele_scene_desc* d) {
     if (d->sh_degree < 0 || d->sh_degree > 3) return fail(c, SEELE_ERR_ARG, "sh_degree must be 0..3");
     if (!d->means || !d->log_scales || !d->quats || !d->opacity_logits || !d->sh)
         return fail(c, SEELE_ERR_ARG, "scene attribute pointer is NULL");
-    if (d->flags != SEELE_SCENE_COPY && d->flags != SEELE_SCENE_BORROW)
-        return fail(c, SEELE_ERR_ARG, "flags must be COPY or BORROW");
+    const bool spatial = (d->flags & SEELE_SCENE_SPATIAL) != 0;
+    const int32_t mode = d->flags & ~SEELE_SCENE_SPATIAL;
+    if (mode != SEELE_SCENE_COPY && mode != SEELE_SCENE_BORROW)
+        return fail(c, SEELE_ERR_ARG, "flags must be COPY or BORROW, optionally with SPATIAL");
+    if (spatial && mode == SEELE_SCENE_BORROW) return fail(c, SEELE_ERR_ARG, "SPATIAL needs a COPY scene");
     if (d->n_clusters < 0 || d->n_clusters > 32) return fail(c, SEELE_ERR_ARG, "n_clusters must be 0..32");
     if (d->n_clusters > 0 && (!d->centroids || !(d->pos_scale > 0)))
         return fail(c, SEELE_ERR_ARG, "centroids and a positive pos_scale are required with clusters");
@@ -868,7 +914,8 @@ seele_status seele_load_scene(seele_ctx* c, const seele_scene_desc* d) {
     SEELE_CUDA(c, ensure(c->log_scale, 16 * n));
     SEELE_CUDA(c, ensure(c->sh, 16 * n * planes));
     c->has_mask = d->cluster_mask != nullptr;
-    if (d->flags == SEELE_SCENE_BORROW) {
+    c->spatial = false;
+    if (mode == SEELE_SCENE_BORROW) {
         const void* ps[] = {d->means, d->log_scales, d->quats, d->opacity_logits, d->sh};
         for (const void* p : ps)
             if (!is_device_ptr(p)) return fail(c, SEELE_ERR_ARG, "BORROW needs device pointers");
@@ -898,18 +945,29 @@ seele_status seele_load_scene(seele_ctx* c, const seele_scene_desc* d) {
                 off += cnt[i];
             }
         }
-        launch_repack((int)n, nc, use[0], use[1], use[2], use[3], use[4], ptr<float4>(c->pos_logit),
-                      ptr<float4>(c->quat), ptr<float4>(c->log_scale), ptr<float4>(c->sh), c->stream);
+        // with SPATIAL the planes are built aside, then gathered in Morton order
+        if (spatial) SEELE_CUDA(c, ensure(c->unordered, 16ull * n * (3 + planes)));
+        float4* P0 = spatial ? ptr<float4>(c->unordered) : ptr<float4>(c->pos_logit);
+        float4* P1 = spatial ? P0 + n : ptr<float4>(c->quat);
+        float4* P2 = spatial ? P0 + 2 * n : ptr<float4>(c->log_scale);
+        float4* P3 = spatial ? P0 + 3 * n : ptr<float4>(c->sh);
+        launch_repack((int)n, nc, use[0], use[1], use[2], use[3], use[4], P0, P1, P2, P3, c->stream);
         SEELE_LAUNCHED(c);
         if (c->has_mask) {
             SEELE_CUDA(c, ensure(c->mask, 4 * n));
             SEELE_CUDA(c, cudaMemcpyAsync(c->mask.p, d->cluster_mask, 4 * n, cudaMemcpyDefault, c->stream));
         }
+        if (spatial) {
+            const seele_status r = spatial_order(c, n, planes);
+            if (r != SEELE_OK) return r;
+        }
         SEELE_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (spatial) release(c->unordered);
+        c->spatial = spatial;
     }
     c->n = n;
     c->sh_degree = d->sh_degree;
-    c->scene_flags = d->flags;
+    c->scene_flags = mode;
     c->n_clusters = d->n_clusters;
     c->pos_scale = d->pos_scale;
     c->centroids.assign(d->centroids ? d->centroids : nullptr, d->centroids ? d->centroids + 6 * d->n_clusters : nullptr);
@@ -1024,6 +1082,7 @@ seele_status seele_load_scene_streamed(seele_ctx* c, const seele_scene_desc* d, 
     SEELE_CUDA(c, cudaStreamCreateWithFlags(&S.copy, cudaStreamNonBlocking));
     SEELE_CUDA(c, cudaStreamSynchronize(c->stream));
     S.on = true;
+    c->spatial = false;
     c->sh_degree = d->sh_degree;
     c->scene_flags = SEELE_SCENE_COPY;
     c->has_mask = true;
@@ -1358,7 +1417,8 @@ seele_status seele_render_backward(seele_ctx* c, const float* dL_drgb, const see
     sc.sh = ptr<float4>(c->sh);
     sc.mask = nullptr;
     launch_preprocess_bwd(sc, a.cams, c->last_fp, ptr<uint32_t>(c->tiles), a.grad_rec, g->means, g->log_scales,
-                          g->quats, g->opacity_logits, g->sh, s);
+                          g->quats, g->opacity_logits, g->sh, c->spatial ? ptr<const uint32_t>(c->order) : nullptr,
+                          s);
     SEELE_LAUNCHED(c);
     return SEELE_OK;
 }
@@ -1381,6 +1441,7 @@ seele_status seele_get_debug_view(const seele_ctx* c, seele_debug_view* out) {
     out->records = ptr<const float>(m->rec);
     out->depth = ptr<const float>(m->depth);
     out->n_contrib = ptr<const uint32_t>(m->nc);
+    out->scene_order = c->spatial ? ptr<const uint32_t>(m->order) : nullptr;
     return SEELE_OK;
 }
 
@@ -1504,7 +1565,15 @@ seele_status seele_build_view_clusters(seele_ctx* c, const seele_camera* poses, 
     c->cams = saved;
     c->rendered = false;
     if (result != SEELE_OK) return result;
-    SEELE_CUDA(c, cudaMemcpyAsync(out_mask, mask, 4 * (size_t)c->n, cudaMemcpyDefault, s));
+    const uint32_t* mask_out = mask;
+    if (c->spatial) {
+        // back to the caller's order of the Gaussians
+        SEELE_CUDA(c, ensure(c->visk[1], 4 * (size_t)c->n));
+        launch_scatter_u32(mask, ptr<uint32_t>(c->visk[1]), (int)c->n, ptr<const uint32_t>(c->order), s);
+        SEELE_LAUNCHED(c);
+        mask_out = ptr<const uint32_t>(c->visk[1]);
+    }
+    SEELE_CUDA(c, cudaMemcpyAsync(out_mask, mask_out, 4 * (size_t)c->n, cudaMemcpyDefault, s));
     SEELE_CUDA(c, cudaStreamSynchronize(s));
     for (size_t i = 0; i < 6 * nk; ++i) out_centroids[i] = (float)cent[i];
     *out_pos_scale = (float)scale;

@@ -235,7 +235,8 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(SceneDev sc, const 
                                                              const float* __restrict__ grad_rec,
                                                              float* __restrict__ d_means, float* __restrict__ d_ls,
                                                              float* __restrict__ d_quat, float* __restrict__ d_logit,
-                                                             float* __restrict__ d_sh) {
+                                                             float* __restrict__ d_sh,
+                                                             const uint32_t* __restrict__ order) {
     constexpr int NC = (DEG + 1) * (DEG + 1);
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= fp.n) return;
@@ -400,16 +401,18 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(SceneDev sc, const 
 #pragma unroll
         for (int i = 0; i < 3; ++i) gm[i] += (gdir[i] - dd[i] * dot) * rn;
     }
+    // gradients go to the caller's index of the Gaussian
+    const size_t go = order != nullptr ? (size_t)__ldg(order + g) : (size_t)g;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        d_means[3 * (size_t)g + i] = gm[i];
-        d_ls[3 * (size_t)g + i] = gls[i];
+        d_means[3 * go + i] = gm[i];
+        d_ls[3 * go + i] = gls[i];
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) d_quat[4 * (size_t)g + i] = gq[i];
-    d_logit[g] = glogit;
+    for (int i = 0; i < 4; ++i) d_quat[4 * go + i] = gq[i];
+    d_logit[go] = glogit;
 #pragma unroll
-    for (int i = 0; i < 3 * NC; ++i) d_sh[(size_t)g * 3 * NC + i] = gsh[i];
+    for (int i = 0; i < 3 * NC; ++i) d_sh[go * 3 * NC + i] = gsh[i];
 }
 
 template <int TW, int TH, int PW, int PH, int GW, int GH, bool CR>
@@ -442,13 +445,13 @@ bool launch_raster_bwd(const RasterBwdArgs& a, cudaStream_t s) {
 
 void launch_preprocess_bwd(const SceneDev& sc, const CamDev* cams, const FrameParams& fp, const uint32_t* tiles,
                            const float* grad_rec, float* d_means, float* d_ls, float* d_quat, float* d_logit,
-                           float* d_sh, cudaStream_t s) {
+                           float* d_sh, const uint32_t* order, cudaStream_t s) {
     const int blocks = (fp.n + 127) / 128;
     switch (fp.sh_degree) {
-        case 0: preprocess_bwd_kernel<0><<<blocks, 128, 0, s>>>(sc, cams, fp, tiles, grad_rec, d_means, d_ls, d_quat, d_logit, d_sh); break;
-        case 1: preprocess_bwd_kernel<1><<<blocks, 128, 0, s>>>(sc, cams, fp, tiles, grad_rec, d_means, d_ls, d_quat, d_logit, d_sh); break;
-        case 2: preprocess_bwd_kernel<2><<<blocks, 128, 0, s>>>(sc, cams, fp, tiles, grad_rec, d_means, d_ls, d_quat, d_logit, d_sh); break;
-        default: preprocess_bwd_kernel<3><<<blocks, 128, 0, s>>>(sc, cams, fp, tiles, grad_rec, d_means, d_ls, d_quat, d_logit, d_sh); break;
+        case 0: preprocess_bwd_kernel<0><<<blocks, 128, 0, s>>>(sc, cams, fp, tiles, grad_rec, d_means, d_ls, d_quat, d_logit, d_sh, order); break;
+        case 1: preprocess_bwd_kernel<1><<<blocks, 128, 0, s>>>(sc, cams, fp, tiles, grad_rec, d_means, d_ls, d_quat, d_logit, d_sh, order); break;
+        case 2: preprocess_bwd_kernel<2><<<blocks, 128, 0, s>>>(sc, cams, fp, tiles, grad_rec, d_means, d_ls, d_quat, d_logit, d_sh, order); break;
+        default: preprocess_bwd_kernel<3><<<blocks, 128, 0, s>>>(sc, cams, fp, tiles, grad_rec, d_means, d_ls, d_quat, d_logit, d_sh, order); break;
     }
 }
 

@@ -34,6 +34,16 @@ void launch_digit_scan(const uint32_t* in, uint32_t stride, const uint32_t* row_
 void launch_exclusive_scan(const uint32_t* in, uint32_t n, uint32_t* out, uint64_t* status, uint32_t epoch,
                            DeviceStatus* st, int ticket, cudaStream_t s);
 
+// Spatial order of a scene (order.cu): Morton order of the means, stable;
+// returns the ping-pong index holding the order in vals (0), or -1.
+// bb: 6 words of scratch; count_ptr: device word holding n.
+int launch_spatial_order(const float4* pos, int n, uint32_t* bb, uint32_t* keys[2], uint32_t* vals[2],
+                         const uint32_t* count_ptr, uint32_t* counts, uint32_t* offsets, uint32_t* digit_totals,
+                         cudaStream_t s);
+void launch_gather_planes(const float4* src, float4* dst, int n, int planes, const uint32_t* order, cudaStream_t s);
+void launch_gather_u32(const uint32_t* src, uint32_t* dst, int n, const uint32_t* order, cudaStream_t s);
+void launch_scatter_u32(const uint32_t* src, uint32_t* dst, int n, const uint32_t* order, cudaStream_t s);
+
 uint32_t sort_tile_items();
 void launch_radix_upsweep_u32(const uint32_t* keys, const uint32_t* count_ptr, int shift, uint32_t* counts,
                               uint32_t stride, cudaStream_t s);
@@ -142,8 +152,9 @@ struct RasterBwdArgs {
     float* grad_rec;            // [R][12]: d(u, v, cA, cB, cC, log2 o, r, g, b), zeroed by the caller
 };
 bool launch_raster_bwd(const RasterBwdArgs& a, cudaStream_t s);
+// order (nullable): caller index of each resident Gaussian (spatial order)
 void launch_preprocess_bwd(const SceneDev& sc, const CamDev* cams, const FrameParams& fp, const uint32_t* tiles,
                            const float* grad_rec, float* d_means, float* d_ls, float* d_quat, float* d_logit,
-                           float* d_sh, cudaStream_t s);
+                           float* d_sh, const uint32_t* order, cudaStream_t s);
 
 }  // namespace seele
