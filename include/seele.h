@@ -150,7 +150,7 @@ enum {
 typedef struct {
     int32_t mode;                 /* PLAIN (Sec. 3.1) or CR (Alg. 1) */
     int32_t group_w, group_h;     /* CR pixel group: 2x2 (default), 1x1, 2x4, 4x4, 4x8 */
-    int32_t tile_w, tile_h;       /* 16x16 (default), 32x8 or 32x16 */
+    int32_t tile_w, tile_h;       /* 16x16 (default), 32x8, 32x16 or 8x8 */
     int32_t opacity_filter;       /* 1: support min(2 ln(o/alpha_theta), 9) (Eqn. 5) */
     int32_t cluster_filter;       /* 1: render only the selected view clusters (Sec. 3.3) */
     int32_t n_neighbors;          /* M of Sec. 3.3 (3) */
@@ -313,7 +313,7 @@ seele_status seele_get_debug_view(const seele_ctx* ctx, seele_debug_view* out);
  * the stream. */
 seele_status seele_get_view_times(const seele_ctx* ctx, float* out_ms, int32_t n);
 
-/* Chooses the tile shape (16x16, 32x8 or 32x16) that renders the current
+/* Chooses the tile shape (16x16, 32x8, 32x16 or 8x8) that renders the current
  * scene and cameras fastest with *inout's other options, by timing a few
  * renders of each; writes it into *inout and the time per render into
  * *best_ms (nullable).  Leaves no render state behind. */

@@ -505,12 +505,14 @@ int enqueue_tile_sort(seele_ctx* c, const FrameInfo& f, const uint32_t* order, c
     return fin;
 }
 
-bool tile_supported(int w, int h) { return (w == 16 && h == 16) || (w == 32 && h == 8) || (w == 32 && h == 16); }
+bool tile_supported(int w, int h) {
+    return (w == 8 && h == 8) || (w == 16 && h == 16) || (w == 32 && h == 8) || (w == 32 && h == 16);
+}
 
 seele_status check_options(seele_ctx* c, const seele_options* opt) {
     if (opt->mode != SEELE_MODE_PLAIN && opt->mode != SEELE_MODE_CR) return fail(c, SEELE_ERR_ARG, "bad mode");
     if (!tile_supported(opt->tile_w, opt->tile_h))
-        return fail(c, SEELE_ERR_ARG, "tile size %dx%d not supported (16x16, 32x8, 32x16)", opt->tile_w, opt->tile_h);
+        return fail(c, SEELE_ERR_ARG, "tile size %dx%d not supported (8x8, 16x16, 32x8, 32x16)", opt->tile_w, opt->tile_h);
     if (opt->mode == SEELE_MODE_CR && !group_supported(opt->group_w, opt->group_h))
         return fail(c, SEELE_ERR_ARG, "pixel group %dx%d not supported (1x1, 2x2, 2x4, 4x4, 4x8)", opt->group_w, opt->group_h);
     if (!(opt->alpha_min > 0 && opt->alpha_min < opt->alpha_max && opt->alpha_max <= 1.0f))
@@ -1312,7 +1314,7 @@ seele_status seele_get_view_times(const seele_ctx* c, float* out_ms, int32_t n) 
 seele_status seele_autotune(seele_ctx* c, seele_options* inout, float* best_ms) {
     if (!c || !inout) return SEELE_ERR_ARG;
     if (!c->has_scene || c->cams.empty()) return fail(c, SEELE_ERR_STATE, "autotune needs a scene and cameras");
-    static const int shapes[][2] = {{16, 16}, {32, 8}, {32, 16}};
+    static const int shapes[][2] = {{16, 16}, {32, 8}, {32, 16}, {8, 8}};
     std::vector<float> out;
     size_t pix = 0;
     for (const auto& k : c->cams) pix += (size_t)k.width * k.height;

@@ -377,8 +377,21 @@ static bool launch_shape(const RasterArgs& a, cudaStream_t s) {
     return true;
 }
 
+// 8x8 tiles: one pixel per thread (two warps); every group spans threads
+static bool launch_shape_8x8(const RasterArgs& a, cudaStream_t s) {
+    if (!a.cr) launch_one<8, 8, 1, 1, 1, 1, false>(a, s);
+    else if (a.group_w == 2 && a.group_h == 2) launch_one<8, 8, 1, 1, 2, 2, true>(a, s);
+    else if (a.group_w == 1 && a.group_h == 1) launch_one<8, 8, 1, 1, 1, 1, true>(a, s);
+    else if (a.group_w == 2 && a.group_h == 4) launch_one<8, 8, 1, 1, 2, 4, true>(a, s);
+    else if (a.group_w == 4 && a.group_h == 4) launch_one<8, 8, 1, 1, 4, 4, true>(a, s);
+    else if (a.group_w == 4 && a.group_h == 8) launch_one<8, 8, 1, 1, 4, 8, true>(a, s);
+    else return false;
+    return true;
+}
+
 bool launch_raster_fwd(const RasterArgs& a, cudaStream_t s) {
     if (a.n_tiles == 0) return true;
+    if (a.fp.tile_w == 8 && a.fp.tile_h == 8) return launch_shape_8x8(a, s);
     if (a.fp.tile_w == 16 && a.fp.tile_h == 16) return launch_shape<16, 16>(a, s);
     if (a.fp.tile_w == 32 && a.fp.tile_h == 8) return launch_shape<32, 8>(a, s);
     if (a.fp.tile_w == 32 && a.fp.tile_h == 16) return launch_shape<32, 16>(a, s);

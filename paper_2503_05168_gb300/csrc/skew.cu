@@ -142,7 +142,10 @@ bool launch_skew(const uint32_t* starts, const uint32_t* ends, const uint32_t* i
                  uint32_t* out_m, uint32_t* out_blended, uint32_t* out_walked, float* out_total,
                  uint32_t* out_listed, cudaStream_t s) {
     if (n_tiles == 0) return true;
-    if (fp.tile_w == 16 && fp.tile_h == 16)
+    if (fp.tile_w == 8 && fp.tile_h == 8)
+        skew_kernel<8, 8><<<n_tiles, 64, 0, s>>>(starts, ends, inst_rec, rec, cams, n_cams, fp, frac, out_m,
+                                                 out_blended, out_walked, out_total, out_listed);
+    else if (fp.tile_w == 16 && fp.tile_h == 16)
         skew_kernel<16, 16><<<n_tiles, 256, 0, s>>>(starts, ends, inst_rec, rec, cams, n_cams, fp, frac, out_m,
                                                     out_blended, out_walked, out_total, out_listed);
     else if (fp.tile_w == 32 && fp.tile_h == 8)

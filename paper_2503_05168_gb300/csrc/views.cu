@@ -231,6 +231,7 @@ bool launch_topk(const uint32_t* starts, const uint32_t* ends, const uint32_t* i
         kernel<<<n_tiles, nt, dyn, s>>>(starts, ends, inst_rec, rec, cams, n_cams, fp, k, cam_cluster, mask);
         return true;
     };
+    if (fp.tile_w == 8 && fp.tile_h == 8) return run(topk_kernel<8, 8>, 64);
     if (fp.tile_w == 16 && fp.tile_h == 16) return run(topk_kernel<16, 16>, 256);
     if (fp.tile_w == 32 && fp.tile_h == 8) return run(topk_kernel<32, 8>, 256);
     return false;

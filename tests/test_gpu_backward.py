@@ -43,21 +43,23 @@ def _compare(gpu, ref):
     return ok, rep
 
 
-@pytest.mark.parametrize("mode,group", [("plain", (2, 2)), ("cr", (2, 2)), ("cr", (4, 4))])
-def test_backward_matches_oracle_analytic(Renderer, mode, group):
+@pytest.mark.parametrize("mode,group,tile", [("plain", (2, 2), (16, 16)), ("cr", (2, 2), (16, 16)),
+                                             ("cr", (4, 4), (16, 16)), ("cr", (2, 2), (8, 8))])
+def test_backward_matches_oracle_analytic(Renderer, mode, group, tile):
     import torch
     sc, cams = scenegen.uniform_10k()
     r = Renderer()
     r.load_scene(sc)
     r.set_cameras(cams)
-    r.render(mode=mode, group=group)
+    r.render(mode=mode, group=group, tile=tile)
     rs = np.random.default_rng(7)
     w = rs.standard_normal((3, 256, 256))
     g = r.render_backward(torch.from_numpy(w.reshape(-1).astype(np.float32)).cuda())
     torch.cuda.synchronize()
     gpu = {k: v.cpu().numpy() for k, v in g.items()}
     ref = oracle.backward(oracle.Scene64.from_scene(sc), cams[0],
-                          oracle.Options(cr=(mode == "cr"), group_w=group[0], group_h=group[1]), w)
+                          oracle.Options(cr=(mode == "cr"), group_w=group[0], group_h=group[1], tile_w=tile[0],
+                                         tile_h=tile[1]), w)
     ok, rep = _compare(gpu, ref)
     print(mode, rep)
     assert ok, rep

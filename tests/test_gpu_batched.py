@@ -106,7 +106,7 @@ def test_view_times_and_autotune(Renderer):
     r.load_scene(sc)
     r.set_cameras(cams)
     opts, ms = r.autotune(mode="cr", opacity_filter=True)
-    assert (opts.tile_w, opts.tile_h) in {(16, 16), (32, 8), (32, 16)} and ms > 0
+    assert (opts.tile_w, opts.tile_h) in {(16, 16), (32, 8), (32, 16), (8, 8)} and ms > 0
     r.render(options=opts)
     t = r.view_times()
     assert len(t) == len(cams) and all(v > 0 for v in t) and max(t) < 1000

@@ -184,7 +184,7 @@ def test_block_lists_filtered_per_tile_are_the_tile_lists(Renderer, seed, size, 
     r.close()
 
 
-@pytest.mark.parametrize("tile", [(16, 16), (32, 8), (32, 16)])
+@pytest.mark.parametrize("tile", [(16, 16), (32, 8), (32, 16), (8, 8)])
 def test_block_binning_renders_bit_identical_to_tile_binning(Renderer, tile):
     sc, _ = scenegen.uniform_10k()
     cams = [scenegen.look_at((0.5 * i, -0.2, -2.6), (0, 0, 0), w, h) for i, (w, h) in
@@ -270,6 +270,24 @@ def test_render_matches_oracle(Renderer, case, where):
     assert ok, rep
     clear = ref.margin >= parity.MARGIN
     assert np.max(np.abs(Ts[0] - ref.T)[clear]) <= parity.RGB_MAX_ABS
+    r.close()
+
+
+@pytest.mark.parametrize("case", [dict(mode="plain"), dict(mode="cr"), dict(mode="cr", group=(4, 4))],
+                         ids=lambda c: "-".join(f"{k}={v}" for k, v in c.items()))
+def test_eight_by_eight_tiles_match_oracle(Renderer, case):
+    """8x8 tiles (one pixel per thread, groups spanning threads) against the
+    oracle run on 8x8 tiles."""
+    sc, cams = scenegen.uniform_10k()
+    r = Renderer()
+    r.load_scene(sc)
+    r.set_cameras(cams)
+    imgs, Ts = parity.gpu_render(r, tile=(8, 8), **case)
+    g = case.get("group", (2, 2))
+    oo = oracle.Options(cr=case["mode"] == "cr", group_w=g[0], group_h=g[1], tile_w=8, tile_h=8)
+    ref = oracle.render(oracle.Scene64.from_scene(sc), cams[0], oo, nthreads=8)[0]
+    ok, rep = parity.compare_images(imgs[0], ref.rgb, ref.margin)
+    assert ok, rep
     r.close()
 
 
@@ -440,7 +458,7 @@ def test_argument_and_state_errors(Renderer):
     with pytest.raises(SeeleError, match="ERR_ARG"):
         r.render(mode="cr", group=(3, 3))
     with pytest.raises(SeeleError, match="ERR_ARG"):
-        r.render(tile=(8, 8))
+        r.render(tile=(16, 8))
     with pytest.raises(SeeleError, match="ERR_STATE"):
         r.render(cluster_filter=True)
     with pytest.raises(SeeleError, match="ERR_ARG"):
