@@ -47,6 +47,7 @@ __global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ 
                                                    const CamDev* __restrict__ cams, int n_gauss, int tile_w,
                                                    int tile_h, int ellipse, DeviceStatus* st,
                                                    KeyT* __restrict__ inst_tile, uint32_t* __restrict__ inst_rec) {
+    pdl_enter();
     if (st->error != kOk) return;  // capacity overflow: nothing fits, outputs undefined
     const uint32_t n = st->n_visible;
     const uint32_t n_inst = st->n_instances;
@@ -158,6 +159,7 @@ __global__ void __launch_bounds__(256) emit_blocks_kernel(const uint32_t* __rest
                                                           KeyT* __restrict__ inst_block,
                                                           uint32_t* __restrict__ inst_rec,
                                                           uint32_t* __restrict__ inst_mask) {
+    pdl_enter();
     if (st->error != kOk) return;
     const uint32_t n = st->n_visible;
     const uint32_t n_inst = st->n_instances;
@@ -224,6 +226,7 @@ __global__ void __launch_bounds__(256) emit_blocks_kernel(const uint32_t* __rest
 // entries of its block list with one load when none of them reaches it.
 __global__ void mask_summary_kernel(const uint32_t* __restrict__ mask, const DeviceStatus* __restrict__ st,
                                     uint32_t* __restrict__ summary, uint32_t max_groups) {
+    pdl_enter();
     const uint32_t n = st->error == kOk ? st->n_inst_valid : 0u;
     const uint32_t groups = (n + 31) / 32;
     const int lane = threadIdx.x & 31;
@@ -239,7 +242,7 @@ __global__ void mask_summary_kernel(const uint32_t* __restrict__ mask, const Dev
 void launch_mask_summary(const uint32_t* mask, const DeviceStatus* st, uint32_t* summary, uint32_t max_groups,
                          cudaStream_t s) {
     const uint32_t blocks = std::max<uint32_t>(1u, std::min<uint32_t>((max_groups + 7) / 8, 152u * 16u));
-    mask_summary_kernel<<<blocks, 256, 0, s>>>(mask, st, summary, max_groups);
+    launch_pdl(mask_summary_kernel, dim3(blocks), dim3(256), 0, s, mask, st, summary, max_groups);
 }
 
 // Longest lists first: the raster grid walks tile blocks in decreasing order
@@ -253,6 +256,7 @@ __global__ void __launch_bounds__(1024) block_order_kernel(const uint32_t* __res
                                                            uint32_t* __restrict__ order) {
     __shared__ uint32_t s_hist[kOrderBuckets];
     __shared__ uint32_t s_pos[kOrderBuckets];
+    pdl_enter();
     auto bucket = [&](uint32_t b) -> int {
         const uint32_t s = __ldg(bstart + b), e = __ldg(bend + b);
         const uint32_t len = s < e ? e - s : 0u;
@@ -279,23 +283,23 @@ __global__ void __launch_bounds__(1024) block_order_kernel(const uint32_t* __res
 
 void launch_block_order(const uint32_t* bstart, const uint32_t* bend, uint32_t n_blocks, uint32_t* order,
                         cudaStream_t s) {
-    block_order_kernel<<<1, 1024, 0, s>>>(bstart, bend, n_blocks, order);
+    launch_pdl(block_order_kernel, dim3(1), dim3(1024), 0, s, bstart, bend, n_blocks, order);
 }
 
 template <typename KeyT>
 void launch_emit(const uint32_t* order, const uint32_t* offsets, const float4* rec,
                  const CamDev* cams, int n_gauss, int tile_w, int tile_h, int ellipse, DeviceStatus* st,
                  KeyT* inst_tile, uint32_t* inst_rec, int blocks, cudaStream_t s) {
-    emit_kernel<KeyT><<<blocks, 256, 0, s>>>(order, offsets, rec, cams, n_gauss, tile_w, tile_h, ellipse, st,
-                                             inst_tile, inst_rec);
+    launch_pdl(emit_kernel<KeyT>, dim3(blocks), dim3(256), 0, s, order, offsets, rec, cams, n_gauss, tile_w, tile_h,
+               ellipse, st, inst_tile, inst_rec);
 }
 
 template <typename KeyT>
 void launch_emit_blocks(const uint32_t* order, const uint32_t* offsets, const float4* rec,
                         const CamDev* cams, int n_gauss, int tile_w, int tile_h, int ellipse, DeviceStatus* st,
                         KeyT* inst_block, uint32_t* inst_rec, uint32_t* inst_mask, int blocks, cudaStream_t s) {
-    emit_blocks_kernel<KeyT><<<blocks, 256, 0, s>>>(order, offsets, rec, cams, n_gauss, tile_w, tile_h, ellipse,
-                                                    st, inst_block, inst_rec, inst_mask);
+    launch_pdl(emit_blocks_kernel<KeyT>, dim3(blocks), dim3(256), 0, s, order, offsets, rec, cams, n_gauss, tile_w,
+               tile_h, ellipse, st, inst_block, inst_rec, inst_mask);
 }
 
 template void launch_emit_blocks<uint16_t>(const uint32_t*, const uint32_t*, const float4*,

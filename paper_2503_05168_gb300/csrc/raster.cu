@@ -51,6 +51,7 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
     __shared__ uint32_t s_idx[WIN];          // block binning: list indices of the window's tile entries
     __shared__ uint32_t s_wsum[NT / 32];
 
+    pdl_enter();
     uint32_t gtile, unit, bit = 0;
     int lo = 0, tx, ty;
     if (BLOCKS) {
@@ -348,9 +349,9 @@ template <int TW, int TH, int PW, int PH, int GW, int GH, bool CR, bool COUNT, b
 static void launch_variant(const RasterArgs& a, cudaStream_t s) {
     constexpr int NT = (TW / PW) * (TH / PH);
     const uint32_t grid = BLOCKS ? 32 * a.n_blocks : a.n_tiles;
-    raster_fwd_kernel<TW, TH, PW, PH, GW, GH, CR, COUNT, BLOCKS><<<grid, NT, 0, s>>>(
-        a.starts, a.ends, a.inst_rec, a.inst_mask, a.mask_summary, a.block_order, a.rec, a.cams, a.n_cams, a.fp,
-        a.out_rgb, a.out_T, a.out_nc, COUNT ? a.count_into : nullptr, a.view_end, a.view_done);
+    launch_pdl(raster_fwd_kernel<TW, TH, PW, PH, GW, GH, CR, COUNT, BLOCKS>, dim3(grid), dim3(NT), 0, s,
+               a.starts, a.ends, a.inst_rec, a.inst_mask, a.mask_summary, a.block_order, a.rec, a.cams, a.n_cams,
+               a.fp, a.out_rgb, a.out_T, a.out_nc, COUNT ? a.count_into : nullptr, a.view_end, a.view_done);
 }
 
 template <int TW, int TH, int PW, int PH, int GW, int GH, bool CR>

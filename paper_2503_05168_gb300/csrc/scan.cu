@@ -155,6 +155,7 @@ __global__ void __launch_bounds__(kScanThreads) compact_visible_kernel(const uin
                                                                        const uint32_t* __restrict__ chunk_vis,
                                                                        uint32_t* keys, uint32_t* vals,
                                                                        DeviceStatus* st) {
+    pdl_enter();
     const uint32_t c = blockIdx.x;
     const uint32_t nchunks = (R + kChunkItems - 1) / kChunkItems;
     const uint32_t prefix = chunk_prefix(chunk_vis, c);
@@ -189,6 +190,7 @@ __global__ void __launch_bounds__(kScanThreads) chunk_sums_kernel(const uint32_t
                                                                   const DeviceStatus* __restrict__ st,
                                                                   uint32_t* __restrict__ chunk_sum) {
     __shared__ uint32_t s_part[kScanThreads / 32];
+    pdl_enter();
     const uint32_t n = st->n_visible;
     const uint32_t base = blockIdx.x * kChunkItems;
     if (base >= n) return;
@@ -221,6 +223,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_tiles_kernel(const uint32_t
                                                                   const uint32_t* __restrict__ chunk_sum,
                                                                   uint32_t* offsets, DeviceStatus* st,
                                                                   uint32_t capacity) {
+    pdl_enter();
     const uint32_t n = st->n_visible;
     const uint32_t nchunks = (n + kChunkItems - 1) / kChunkItems;
     const uint32_t c = blockIdx.x;
@@ -274,6 +277,7 @@ __global__ void __launch_bounds__(kScanThreads) digit_scan_kernel(const uint32_t
                                                                   const uint32_t* __restrict__ row_total,
                                                                   uint32_t* __restrict__ out) {
     __shared__ uint32_t s_part[kScanThreads / 32];
+    pdl_enter();
     const uint32_t n = 256u * stride;
     const uint32_t first = blockIdx.x * kScanTile;
     const uint32_t base = first + threadIdx.x * kScanItems;
@@ -355,7 +359,7 @@ __global__ void __launch_bounds__(kScanThreads) exclusive_scan_kernel(const uint
 void launch_digit_scan(const uint32_t* in, uint32_t stride, const uint32_t* row_total, uint32_t* out,
                        cudaStream_t s) {
     const uint32_t blocks = (256u * stride + kScanTile - 1) / kScanTile;
-    digit_scan_kernel<<<blocks, kScanThreads, 0, s>>>(in, stride, row_total, out);
+    launch_pdl(digit_scan_kernel, dim3(blocks), dim3(kScanThreads), 0, s, in, stride, row_total, out);
 }
 
 void launch_exclusive_scan(const uint32_t* in, uint32_t n, uint32_t* out, uint64_t* status, uint32_t epoch,
@@ -370,15 +374,16 @@ void launch_compact_visible(const uint32_t* cnt, bool pack, const float* depth, 
                             const uint32_t* chunk_vis, uint32_t* keys, uint32_t* vals, DeviceStatus* st,
                             cudaStream_t s) {
     const uint32_t blocks = (R + kChunkItems - 1) / kChunkItems;
-    compact_visible_kernel<<<blocks > 0 ? blocks : 1, kScanThreads, 0, s>>>(cnt, pack ? 1 : 0, depth, R, chunk_vis,
-                                                                            keys, vals, st);
+    launch_pdl(compact_visible_kernel, dim3(blocks > 0 ? blocks : 1), dim3(kScanThreads), 0, s, cnt, pack ? 1 : 0,
+               depth, R, chunk_vis, keys, vals, st);
 }
 
 void launch_scan_tiles(const uint32_t* cnt_sorted, uint32_t* chunk_sum, uint32_t max_n, uint32_t* offsets,
                        DeviceStatus* st, uint32_t capacity, cudaStream_t s) {
     const uint32_t blocks = std::max<uint32_t>((max_n + kChunkItems - 1) / kChunkItems, 1u);
-    chunk_sums_kernel<<<blocks, kScanThreads, 0, s>>>(cnt_sorted, st, chunk_sum);
-    scan_tiles_kernel<<<blocks, kScanThreads, 0, s>>>(cnt_sorted, chunk_sum, offsets, st, capacity);
+    launch_pdl(chunk_sums_kernel, dim3(blocks), dim3(kScanThreads), 0, s, cnt_sorted, st, chunk_sum);
+    launch_pdl(scan_tiles_kernel, dim3(blocks), dim3(kScanThreads), 0, s, cnt_sorted, chunk_sum, offsets, st,
+               capacity);
 }
 
 }  // namespace seele

@@ -44,6 +44,7 @@ __global__ void __launch_bounds__(kSortThreads) upsweep_kernel(const KeyT* __res
                                                                uint32_t* __restrict__ row_total) {
     static_assert(kSortItems * sizeof(KeyT) % 16 == 0, "vector loads");
     __shared__ uint32_t s_w[kWarps][kRadix];
+    pdl_enter();
     const uint32_t tile = blockIdx.x;
     const uint32_t n = *count_ptr;
     const int w = threadIdx.x >> 5;
@@ -93,6 +94,7 @@ __global__ void __launch_bounds__(kSortThreads) downsweep_kernel(const KeyT* __r
     __shared__ uint32_t s_global_base[kRadix];         // digit start in the output for this tile
     __shared__ uint32_t s_scan[kWarps];
 
+    pdl_enter();
     const uint32_t tile = blockIdx.x;
     const uint32_t n = *count_ptr;
     if (tile * (uint32_t)kSortTile >= n) return;
@@ -250,9 +252,9 @@ template <typename KeyT, bool WK, bool AUX>
 static void launch_downsweep(KeyT* keys[2], uint32_t* vals[2], uint32_t* const* aux, int a, int b,
                              const uint32_t* count_ptr, int shift, int nbits, const uint32_t* offsets, uint32_t stride,
                              uint32_t* rs, uint32_t* re, const SortGather& gather, cudaStream_t s) {
-    downsweep_kernel<KeyT, WK, AUX><<<stride, kSortThreads, 0, s>>>(
-        keys[a], vals[a], keys[b], vals[b], count_ptr, shift, nbits, offsets, stride, rs, re,
-        AUX ? aux[a] : nullptr, AUX ? aux[b] : nullptr, gather);
+    launch_pdl(downsweep_kernel<KeyT, WK, AUX>, dim3(stride), dim3(kSortThreads), 0, s, keys[a], vals[a], keys[b],
+               vals[b], count_ptr, shift, nbits, offsets, stride, rs, re, AUX ? aux[a] : nullptr,
+               AUX ? aux[b] : nullptr, gather);
 }
 
 template <typename KeyT>
@@ -270,7 +272,8 @@ int radix_sort_pairs(KeyT* keys[2], uint32_t* vals[2], const uint32_t* count_ptr
         uint32_t* re = last ? run_end : nullptr;
         const SortGather g = (last && gather) ? *gather : SortGather{};
         uint32_t* totals = digit_totals + (size_t)p * kRadix;
-        upsweep_kernel<KeyT><<<stride, kSortThreads, 0, s>>>(keys[a], count_ptr, 8 * p, counts, stride, totals);
+        launch_pdl(upsweep_kernel<KeyT>, dim3(stride), dim3(kSortThreads), 0, s, keys[a], count_ptr, 8 * p, counts,
+                   stride, totals);
         launch_digit_scan(counts, stride, totals, offsets, s);
         const bool wk = !last || keys_after_last;
         if (aux) {
