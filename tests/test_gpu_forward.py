@@ -391,6 +391,39 @@ def test_degenerate_scenes(Renderer):
     r.close()
 
 
+@pytest.mark.parametrize("case", [dict(mode="plain"), dict(mode="cr"), dict(mode="cr", opacity_filter=True)],
+                         ids=lambda c: "-".join(f"{k}={v}" for k, v in c.items()))
+def test_extreme_attributes_match_oracle(Renderer, case):
+    """Opacities above the 0.99 alpha clamp, sub-pixel scales (the 0.3 px^2
+    dilation dominates the footprint), Gaussians larger than the image and
+    elongated ones, mixed in one frame."""
+    rs = np.random.default_rng(21)
+    n = 400
+    means = rs.uniform(-1, 1, (n, 3)) * [1.2, 0.9, 1.0] + [0, 0, 5]
+    ls = rs.normal(math.log(0.05), 0.4, (n, 3))
+    ls[:80] = math.log(1e-4)                        # far below a pixel
+    ls[80:90] = math.log(2.5)                       # larger than the view
+    ls[90:150, 0] = math.log(0.6)                   # needles: one long axis
+    ls[90:150, 1:] = math.log(0.004)
+    op = rs.uniform(0.05, 0.9, n)
+    op[150:260] = 1.0 - rs.uniform(1e-6, 5e-3, 110)  # alpha clamps at the centre
+    s = _f32(scene(means, log_scales=ls, quats=rs.standard_normal((n, 4)), opacity=op,
+                   dc=rs.uniform(-1, 1, (n, 3))))
+    cam = camera(f=120.0, width=160, height=128)
+    r = Renderer()
+    r.load_scene(s)
+    r.set_cameras([cam])
+    imgs, Ts = parity.gpu_render(r, **case)
+    oo = parity.oracle_options(case["mode"], (2, 2), case.get("opacity_filter", False))
+    ref = oracle.render(oracle.Scene64.from_scene(s), cam, oo, nthreads=8)[0]
+    ok, rep = parity.compare_images(imgs[0], ref.rgb, ref.margin)
+    assert ok, rep
+    clear = ref.margin >= parity.MARGIN
+    assert clear.mean() > 0.9
+    assert np.max(np.abs(Ts[0] - ref.T)[clear]) <= parity.RGB_MAX_ABS
+    r.close()
+
+
 def test_capacity_growth_is_transparent(Renderer):
     # a few huge Gaussians touch every tile: K = n * tiles >> 4 n, so the first
     # attempt overflows the initial capacity and the call grows and re-renders
