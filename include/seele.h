@@ -226,6 +226,28 @@ seele_status seele_load_scene(seele_ctx* ctx, const seele_scene_desc* scene);
 seele_status seele_load_scene_streamed(seele_ctx* ctx, const seele_scene_desc* scene, int32_t n_slots,
                                        int64_t slot_gaussians, int32_t ahead);
 
+/* Makes dst render the scene src holds, without a copy: dst keeps its own
+ * stream, cameras, frame workspace and captured graph, so frames of the two
+ * contexts may be in flight at once on their streams (one frame's
+ * rasterization overlapping the next frame's preprocessing and sorting).
+ * The device memory of a COPY scene is reference counted: it stays valid
+ * until every context sharing it has loaded another scene or been destroyed,
+ * so either context may later reload or be destroyed; the others keep
+ * rendering the scene as it was shared.  A BORROW scene is referenced by dst
+ * as by src (the caller keeps its arrays alive and unchanged); dst repacks
+ * it into its own planes each frame.  View clusters, the spatial order and
+ * the cluster mask come along; every call that reads the scene works on dst,
+ * and none writes it.
+ *   dst, src  contexts on the same device; src holds a scene loaded by
+ *             seele_load_scene (or shared into it); dst may hold any state,
+ *             which is dropped as by seele_load_scene.
+ * Errors: SEELE_ERR_ARG for NULL, dst == src or different devices;
+ * SEELE_ERR_STATE when src has no scene or a streamed one (its slots change
+ * every frame).  Contexts sharing a scene may be used from different host
+ * threads; loading, sharing and destroying contexts are not thread safe
+ * with respect to each other. */
+seele_status seele_share_scene(seele_ctx* dst, const seele_ctx* src);
+
 typedef struct {
     int64_t resident_bytes;    /* device bytes of the resident Gaussians (attributes and masks) */
     int64_t full_bytes;        /* the same for the whole scene resident */

@@ -63,15 +63,18 @@ def _ptr(x):
 
 
 class Renderer:
-    """One library context on one CUDA device."""
+    """One library context on one CUDA device.  Calls enqueue on ``stream``
+    (a torch.cuda.Stream) if given, else on the current stream at each call."""
 
-    def __init__(self, device: int = 0):
+    def __init__(self, device: int = 0, stream=None):
         import torch
         self._torch = torch
         self.device = torch.device("cuda", device)
         torch.cuda.init()
+        self._stream = stream
         h = ctypes.c_void_p()
-        st = lib().seele_create(ctypes.byref(h), device, ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream))
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        st = lib().seele_create(ctypes.byref(h), device, ctypes.c_void_p(s.cuda_stream))
         if st != 0:
             raise SeeleError(st, "seele_create failed")
         self._h = h
@@ -86,8 +89,11 @@ class Renderer:
         if st != 0:
             raise SeeleError(st, lib().seele_last_error(self._h).decode(errors="replace"))
 
+    def _stream_now(self):
+        return self._stream if self._stream is not None else self._torch.cuda.current_stream(self.device)
+
     def _sync_stream(self):
-        s = self._torch.cuda.current_stream(self.device).cuda_stream
+        s = self._stream_now().cuda_stream
         self._check(lib().seele_set_stream(self._h, ctypes.c_void_p(s)))
 
     def close(self):
@@ -149,6 +155,16 @@ class Renderer:
         self._keep = [arrs, mask, cen] if borrow else []
         self.n = n
         self.sh_degree = d.sh_degree
+
+    def share_scene(self, other: "Renderer"):
+        """Renders ``other``'s scene without a copy (seele_share_scene); this
+        renderer keeps its own stream, cameras and frame workspace, so frames
+        of both can be in flight at once."""
+        self._sync_stream()
+        self._check(lib().seele_share_scene(self._h, other._h))
+        self._keep = list(other._keep)
+        self.n = other.n
+        self.sh_degree = other.sh_degree
 
     @staticmethod
     def _camera_array(cams):
@@ -325,7 +341,7 @@ class Renderer:
             if count == 0:
                 return torch.empty(0, dtype=dtype, device=self.device)
             out = torch.empty(count, dtype=dtype, device=self.device)
-            torch.cuda.current_stream(self.device).synchronize()
+            self._stream_now().synchronize()
             res = _cudart().cudaMemcpy(ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(ptr),
                                        ctypes.c_size_t(count * out.element_size()), 3)  # device to device
             if int(res) != 0:

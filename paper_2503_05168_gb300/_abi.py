@@ -93,6 +93,7 @@ PROTOTYPES = {
     "seele_load_scene_streamed": (ctypes.c_int, [P, ctypes.POINTER(SceneDesc), ctypes.c_int32, ctypes.c_int64,
                                                  ctypes.c_int32]),
     "seele_get_stream_stats": (ctypes.c_int, [P, ctypes.POINTER(StreamStats)]),
+    "seele_share_scene": (ctypes.c_int, [P, P]),
 }
 NOALLOC_MAX_INSTANCES = 1 << 20
 NOALLOC_MAX_TILES = 1 << 16

@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -18,6 +19,22 @@ namespace {
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
+};
+
+// Device memory of a COPY scene that several contexts render
+// (seele_share_scene): the planes, the cluster mask and the spatial order,
+// freed when the last context lets go.
+struct SharedScene {
+    int device = 0;
+    void* p[6] = {};
+    ~SharedScene() {
+        int prev = 0;
+        const bool had = cudaGetDevice(&prev) == cudaSuccess;
+        cudaSetDevice(device);
+        for (void* q : p)
+            if (q) cudaFree(q);
+        if (had) cudaSetDevice(prev);
+    }
 };
 
 constexpr int kMaxCams = 4096;
@@ -41,6 +58,9 @@ struct seele_ctx {
     // Gaussian, the planes before the gather, a few words of scratch
     DevBuf order, unordered, order_scratch;
     bool spatial = false;
+    // set while the scene's memory is shared: pos_logit, quat, log_scale,
+    // sh, mask and order are then views of it, not owned
+    std::shared_ptr<SharedScene> shared;
     bool has_mask = false;
     int n_clusters = 0;
     std::vector<double> centroids;
@@ -283,6 +303,21 @@ seele_status spatial_order(seele_ctx* c, int64_t n, int planes) {
     }
     SEELE_LAUNCHED(c);
     return SEELE_OK;
+}
+
+// ------------------------------------------------------- shared scene --
+
+DevBuf* scene_bufs(seele_ctx* c, int i) {
+    DevBuf* b[6] = {&c->pos_logit, &c->quat, &c->log_scale, &c->sh, &c->mask, &c->order};
+    return b[i];
+}
+
+// Lets go of a shared scene's memory (freed here if this was the last
+// context holding it); the scene buffers start empty again.
+void scene_unshare(seele_ctx* c) {
+    if (!c->shared) return;
+    for (int i = 0; i < 6; ++i) *scene_bufs(c, i) = DevBuf{};
+    c->shared.reset();
 }
 
 // ------------------------------------------------------- streamed scene --
@@ -857,6 +892,7 @@ void seele_destroy(seele_ctx* c) {
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
+    scene_unshare(c);
     DevBuf* all[] = {&c->pos_logit, &c->quat, &c->log_scale, &c->sh, &c->mask, &c->staging, &c->cams_dev,
                      &c->rec, &c->tiles, &c->depth, &c->visk[0], &c->visk[1], &c->visv[0],
                      &c->visv[1], &c->offs, &c->instk[0], &c->instk[1], &c->instv[0], &c->instv[1],
@@ -908,6 +944,7 @@ seele_status seele_load_scene(seele_ctx* c, const seele_scene_desc* d) {
     c->rendered = false;
     ++c->scene_gen;
     stream_release(c);
+    scene_unshare(c);
     const int64_t n = d->n;
     const int nc = (d->sh_degree + 1) * (d->sh_degree + 1);
     const int planes = (3 * nc + 3) / 4;
@@ -999,6 +1036,7 @@ seele_status seele_load_scene_streamed(seele_ctx* c, const seele_scene_desc* d, 
     c->rendered = false;
     ++c->scene_gen;
     stream_release(c);
+    scene_unshare(c);
     auto& S = c->st;
     const int64_t n = d->n;
     const int C = d->n_clusters, nc = (d->sh_degree + 1) * (d->sh_degree + 1), np = (3 * nc + 3) / 4;
@@ -1092,6 +1130,54 @@ seele_status seele_load_scene_streamed(seele_ctx* c, const seele_scene_desc* d, 
     c->pos_scale = d->pos_scale;
     c->centroids.assign(d->centroids, d->centroids + 6 * C);
     c->has_scene = true;
+    return SEELE_OK;
+}
+
+seele_status seele_share_scene(seele_ctx* dst, const seele_ctx* src_c) {
+    if (!dst) return SEELE_ERR_ARG;
+    if (!src_c || src_c == dst) return fail(dst, SEELE_ERR_ARG, "src must be another context");
+    seele_ctx* src = const_cast<seele_ctx*>(src_c);   // only its ownership record changes
+    if (src->device != dst->device) return fail(dst, SEELE_ERR_ARG, "src and dst are on different devices");
+    if (!src->has_scene) return fail(dst, SEELE_ERR_STATE, "src holds no scene");
+    if (src->st.on) return fail(dst, SEELE_ERR_STATE, "a streamed scene cannot be shared: its slots change every frame");
+    SEELE_CUDA(dst, cudaSetDevice(dst->device));
+    SEELE_CUDA(dst, dst->stream ? cudaStreamSynchronize(dst->stream) : cudaDeviceSynchronize());
+    dst->has_scene = false;
+    dst->rendered = false;
+    ++dst->scene_gen;
+    stream_release(dst);
+    scene_unshare(dst);
+    const int64_t n = src->n;
+    if (src->scene_flags == SEELE_SCENE_COPY) {
+        if (!src->shared) {
+            auto h = std::make_shared<SharedScene>();
+            h->device = src->device;
+            for (int i = 0; i < 6; ++i) h->p[i] = scene_bufs(src, i)->p;
+            src->shared = h;
+        }
+        for (int i = 0; i < 6; ++i) {
+            release(*scene_bufs(dst, i));
+            *scene_bufs(dst, i) = *scene_bufs(src, i);
+        }
+        dst->shared = src->shared;
+    } else {
+        // BORROW: the caller's arrays, repacked into dst's own planes per frame
+        const int planes = (3 * (src->sh_degree + 1) * (src->sh_degree + 1) + 3) / 4;
+        SEELE_CUDA(dst, ensure(dst->pos_logit, 16 * n));
+        SEELE_CUDA(dst, ensure(dst->quat, 16 * n));
+        SEELE_CUDA(dst, ensure(dst->log_scale, 16 * n));
+        SEELE_CUDA(dst, ensure(dst->sh, 16 * n * planes));
+        dst->borrowed = src->borrowed;
+    }
+    dst->n = n;
+    dst->sh_degree = src->sh_degree;
+    dst->scene_flags = src->scene_flags;
+    dst->spatial = src->spatial;
+    dst->has_mask = src->has_mask;
+    dst->n_clusters = src->n_clusters;
+    dst->pos_scale = src->pos_scale;
+    dst->centroids = src->centroids;
+    dst->has_scene = true;
     return SEELE_OK;
 }
 
