@@ -68,6 +68,10 @@ enum { SEELE_SCENE_COPY = 0, SEELE_SCENE_BORROW = 1, SEELE_SCENE_SPATIAL = 2 };
  * device memory owned by the caller, must stay valid and unchanged in size
  * until the next seele_load_scene or seele_destroy, and are re-read by every
  * render (their contents may change between renders, as in training).
+ * COPY reads device and page-locked host arrays (cudaMallocHost,
+ * cudaHostRegister) in place, the latter over the host link in the same pass
+ * that repacks them; other host arrays are first copied to a device staging
+ * area.
  * COPY | SPATIAL also stores the Gaussians in Morton order of their means
  * (computed on the device at load), so that Gaussians culled together are
  * stored together and preprocessing reads less of the scene.  Images are the
@@ -130,7 +134,7 @@ enum {
                                      replay it while the camera count and resolutions, the
                                      options, the instance capacity, the scene and the
                                      output pointers stay the same; camera poses may change
-                                     between replays.  Device outputs only */
+                                     between replays.  Device or page-locked host outputs */
 };
 
 /* Stages timed by SEELE_RENDER_PROFILE, in launch order. */
@@ -276,10 +280,12 @@ seele_status seele_set_cameras(seele_ctx* ctx, const seele_camera* cams, int32_t
  *   stats    host or NULL
  * Without SEELE_RENDER_ASYNC the call synchronises the stream, grows the
  * instance capacity and re-renders when it was exceeded, and returns the
- * device status.  With SEELE_RENDER_ASYNC it returns after enqueueing (device
- * output pointers only); a capacity overflow then leaves the outputs
- * undefined and is reported by seele_synchronize, after which the next render
- * uses the grown capacity. */
+ * device status.  With SEELE_RENDER_ASYNC it returns after enqueueing; the
+ * outputs must then be device or page-locked host memory, and a host output
+ * is written by a copy enqueued after the frame on the same stream.  A
+ * capacity overflow then leaves the outputs undefined and is reported by
+ * seele_synchronize, after which the next render uses the grown capacity.
+ * SEELE_RENDER_GRAPH takes the same outputs. */
 seele_status seele_render(seele_ctx* ctx, const seele_options* opt, float* out_rgb, float* out_T,
                           seele_stats* stats);
 

@@ -201,6 +201,18 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Device address of page-locked host memory (cudaMallocHost,
+// cudaHostRegister), which kernels read and write over the host link; NULL
+// for any other pointer.
+const void* mapped_host(const void* p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 template <class T>
 T* ptr(DevBuf& b) {
     return static_cast<T*>(b.p);
@@ -962,21 +974,22 @@ seele_status seele_load_scene(seele_ctx* c, const seele_scene_desc* d) {
             return fail(c, SEELE_ERR_ARG, "BORROW needs a device cluster_mask");
         c->borrowed = *d;
     } else {
-        // attributes that live on the host go through one device staging area
+        // the repack reads device and page-locked host attributes where they
+        // are; other host attributes go through one device staging area
         const float* src[5] = {d->means, d->log_scales, d->quats, d->opacity_logits, d->sh};
         const size_t cnt[5] = {(size_t)n * 3, (size_t)n * 3, (size_t)n * 4, (size_t)n, (size_t)n * nc * 3};
         size_t stage_floats = 0;
-        bool dev[5];
+        const float* direct[5];
         for (int i = 0; i < 5; ++i) {
-            dev[i] = is_device_ptr(src[i]);
-            if (!dev[i]) stage_floats += cnt[i];
+            direct[i] = is_device_ptr(src[i]) ? src[i] : static_cast<const float*>(mapped_host(src[i]));
+            if (!direct[i]) stage_floats += cnt[i];
         }
-        SEELE_CUDA(c, ensure(c->staging, stage_floats * 4));
+        if (stage_floats) SEELE_CUDA(c, ensure(c->staging, stage_floats * 4));
         const float* use[5];
         size_t off = 0;
         for (int i = 0; i < 5; ++i) {
-            if (dev[i]) {
-                use[i] = src[i];
+            if (direct[i]) {
+                use[i] = direct[i];
             } else {
                 float* dst = ptr<float>(c->staging) + off;
                 SEELE_CUDA(c, cudaMemcpyAsync(dst, src[i], cnt[i] * 4, cudaMemcpyHostToDevice, c->stream));
@@ -1256,8 +1269,10 @@ seele_status seele_render(seele_ctx* c, const seele_options* opt, float* out_rgb
     FrameInfo f;
     f.rgb_dev = is_device_ptr(out_rgb);
     f.T_dev = out_T ? is_device_ptr(out_T) : true;
-    if ((async || graph) && (!f.rgb_dev || !f.T_dev))
-        return fail(c, SEELE_ERR_ARG, "ASYNC and GRAPH renders need device outputs");
+    // host outputs are read back on the stream after the frame; only
+    // page-locked ones asynchronously
+    if ((async || graph) && ((!f.rgb_dev && !mapped_host(out_rgb)) || (!f.T_dev && !mapped_host(out_T))))
+        return fail(c, SEELE_ERR_ARG, "ASYNC and GRAPH renders need device or page-locked host outputs");
     f.ncam = (int)c->cams.size();
     f.R = (uint64_t)c->n * f.ncam;
     if (f.R >= (1ull << 31)) return fail(c, SEELE_ERR_ARG, "cameras x Gaussians must be < 2^31");
@@ -1337,6 +1352,10 @@ seele_status seele_render(seele_ctx* c, const seele_options* opt, float* out_rgb
         c->n_pix_total = f.pix_total;
         c->last_opt = *opt;
         c->last_fp = f.fp;
+        if (!f.rgb_dev)
+            SEELE_CUDA(c, cudaMemcpyAsync(out_rgb, c->rgb_tmp.p, 12 * f.pix_total, cudaMemcpyDeviceToHost, c->stream));
+        if (out_T && !f.T_dev)
+            SEELE_CUDA(c, cudaMemcpyAsync(out_T, c->T.p, 4 * f.pix_total, cudaMemcpyDeviceToHost, c->stream));
         if (async) {
             c->status_pending = true;
             c->rendered = true;
@@ -1361,11 +1380,6 @@ seele_status seele_render(seele_ctx* c, const seele_options* opt, float* out_rgb
         const seele_status sp = stream_prefetch(c, opt->n_neighbors);
         if (sp != SEELE_OK) return sp;
     }
-    if (!f.rgb_dev)
-        SEELE_CUDA(c, cudaMemcpyAsync(out_rgb, c->rgb_tmp.p, 12 * f.pix_total, cudaMemcpyDeviceToHost, c->stream));
-    if (out_T && !f.T_dev)
-        SEELE_CUDA(c, cudaMemcpyAsync(out_T, c->T.p, 4 * f.pix_total, cudaMemcpyDeviceToHost, c->stream));
-    if (!f.rgb_dev || !f.T_dev) SEELE_CUDA(c, cudaStreamSynchronize(c->stream));
     if (stats) {
         std::memset(stats->stage_ms, 0, sizeof stats->stage_ms);
         if (profile)

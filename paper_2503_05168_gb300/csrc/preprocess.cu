@@ -262,23 +262,51 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev sc, const CamD
     }
 }
 
-// Scene repack: caller layout (arrays of structures) -> library planes.
-__global__ void repack_kernel(int n, int nc, const float* __restrict__ means, const float* __restrict__ log_scales,
-                              const float* __restrict__ quats, const float* __restrict__ logits,
-                              const float* __restrict__ sh, float4* pos_logit, float4* quat, float4* log_scale,
-                              float4* shp) {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n) return;
-    pos_logit[g] = make_float4(means[3 * g], means[3 * g + 1], means[3 * g + 2], logits[g]);
-    quat[g] = make_float4(quats[4 * g], quats[4 * g + 1], quats[4 * g + 2], quats[4 * g + 3]);
-    log_scale[g] = make_float4(log_scales[3 * g], log_scales[3 * g + 1], log_scales[3 * g + 2], 0.f);
-    const int nf = 3 * nc, np = (nf + 3) / 4;
-    const float* src = sh + (size_t)g * nf;
-    for (int j = 0; j < np; ++j) {
+// Scene repack: caller layout (arrays of structures) -> library planes.  A
+// block takes kRepackG consecutive Gaussians: it reads their contiguous
+// spans of every input array with consecutive threads on consecutive words
+// (also when the inputs are page-locked host memory read over the
+// host link), parks them in shared memory (SH rows padded to an odd
+// stride, so a warp reading one column hits 32 banks), then writes the
+// float4 planes, one Gaussian per thread.
+constexpr int kRepackG = 128;
+
+template <int NC>
+__global__ void __launch_bounds__(256) repack_kernel(int n, const float* __restrict__ means,
+                                                     const float* __restrict__ log_scales,
+                                                     const float* __restrict__ quats,
+                                                     const float* __restrict__ logits,
+                                                     const float* __restrict__ sh, float4* __restrict__ pos_logit,
+                                                     float4* __restrict__ quat, float4* __restrict__ log_scale,
+                                                     float4* __restrict__ shp) {
+    constexpr int NF = 3 * NC, NP = (NF + 3) / 4, RS = NF | 1;
+    __shared__ float4 s_q[kRepackG];
+    __shared__ float s_sh[kRepackG * RS], s_m[3 * kRepackG], s_s[3 * kRepackG], s_o[kRepackG];
+    const size_t g0 = (size_t)blockIdx.x * kRepackG;
+    const int cnt = (int)min((size_t)kRepackG, (size_t)n - g0);
+    const int t = threadIdx.x;
+    for (int i = t; i < cnt * NF; i += 256) s_sh[(i / NF) * RS + i % NF] = __ldg(sh + g0 * NF + i);
+    for (int i = t; i < cnt * 3; i += 256) {
+        s_m[i] = __ldg(means + g0 * 3 + i);
+        s_s[i] = __ldg(log_scales + g0 * 3 + i);
+    }
+    float* q = reinterpret_cast<float*>(s_q);
+    for (int i = t; i < cnt * 4; i += 256) q[i] = __ldg(quats + g0 * 4 + i);
+    for (int i = t; i < cnt; i += 256) s_o[i] = __ldg(logits + g0 + i);
+    __syncthreads();
+    if (t < cnt) {
+        pos_logit[g0 + t] = make_float4(s_m[3 * t], s_m[3 * t + 1], s_m[3 * t + 2], s_o[t]);
+        quat[g0 + t] = s_q[t];
+        log_scale[g0 + t] = make_float4(s_s[3 * t], s_s[3 * t + 1], s_s[3 * t + 2], 0.f);
+    }
+    for (int k = t; k < NP * kRepackG; k += 256) {
+        const int j = k / kRepackG, gl = k % kRepackG;
+        if (gl >= cnt) continue;
+        const float* row = s_sh + gl * RS + 4 * j;
         float v[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) v[i] = (4 * j + i < nf) ? src[4 * j + i] : 0.f;
-        shp[(size_t)j * n + g] = make_float4(v[0], v[1], v[2], v[3]);
+        for (int i = 0; i < 4; ++i) v[i] = (4 * j + i < NF) ? row[i] : 0.f;
+        shp[(size_t)j * n + g0 + gl] = make_float4(v[0], v[1], v[2], v[3]);
     }
 }
 
@@ -296,8 +324,17 @@ void launch_preprocess(const SceneDev& sc, const CamDev* cams, const FrameParams
 void launch_repack(int n, int nc, const float* means, const float* log_scales, const float* quats,
                    const float* logits, const float* sh, float4* pos_logit, float4* quat, float4* log_scale,
                    float4* shp, cudaStream_t s) {
-    repack_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, nc, means, log_scales, quats, logits, sh, pos_logit, quat,
-                                                   log_scale, shp);
+    const int blocks = (n + kRepackG - 1) / kRepackG;
+    switch (nc) {
+        case 1: repack_kernel<1><<<blocks, 256, 0, s>>>(n, means, log_scales, quats, logits, sh, pos_logit, quat,
+                                                        log_scale, shp); break;
+        case 4: repack_kernel<4><<<blocks, 256, 0, s>>>(n, means, log_scales, quats, logits, sh, pos_logit, quat,
+                                                        log_scale, shp); break;
+        case 9: repack_kernel<9><<<blocks, 256, 0, s>>>(n, means, log_scales, quats, logits, sh, pos_logit, quat,
+                                                        log_scale, shp); break;
+        default: repack_kernel<16><<<blocks, 256, 0, s>>>(n, means, log_scales, quats, logits, sh, pos_logit,
+                                                          quat, log_scale, shp); break;
+    }
 }
 
 }  // namespace seele
