@@ -428,3 +428,87 @@ def test_cluster_selection_brute_force():
         order = np.argsort(d, kind="stable")
         assert order[0] == near
         assert sel == sum(1 << int(k) for k in order[:4])
+
+
+# ------------------------------------------- transmittance along the list --
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_transmittance_is_monotone_along_the_list(seed):
+    """Eqn. 1 composites front to back: adding the next Gaussian in depth
+    order can only lower a pixel's transmittance and raise its colour (SH
+    colours are clamped at 0), and the stopping rule keeps T >= Gamma_theta.
+    The oracle renders the j nearest Gaussians for every j, as a black box."""
+    sc, cams = scenegen.uniform_10k(seed=seed, n=40, width=24, height=24)
+    # opaque, wide Gaussians, so that pixels reach Gamma_theta
+    sc["opacity_logits"] = sc["opacity_logits"] + np.float32(4.0)
+    sc["log_scales"] = sc["log_scales"] + np.float32(3.0)
+    cam = cams[0]
+    opts = oracle.Options()
+    proj = oracle.preprocess(oracle.Scene64.from_scene(sc), cam, opts)
+    vis = np.nonzero(proj["visible"] == 1)[0]
+    order = vis[np.lexsort((vis, proj["depth32"][vis]))]
+    assert order.size > 30
+    prev_T = np.ones((24, 24))
+    prev_C = np.zeros((3, 24, 24))
+    changed = 0
+    for j in range(order.size + 1):
+        sub = proj.copy()
+        sub["visible"] = 0
+        sub["visible"][order[:j]] = 1
+        C, T = oracle.render_bruteforce(sub, cam, opts)
+        assert np.all(T <= prev_T) and np.all(C >= prev_C), j
+        assert np.all(T >= opts.t_stop) and np.all(T <= 1.0)
+        changed += int(np.any(T < prev_T))
+        prev_T, prev_C = T, C
+    assert changed > order.size // 2
+    full = oracle.render(oracle.Scene64.from_scene(sc), cam, opts)[0]
+    np.testing.assert_array_equal(full.T, prev_T)
+    assert full.counters["terminated"] > 100
+
+
+# ---------------------------------------------- CR error against plain ----
+
+@pytest.mark.parametrize("group", [(2, 2), (2, 4), (4, 4)])
+@pytest.mark.parametrize("seed", [3, 4])
+def test_cr_differs_from_plain_by_at_most_its_skipped_alphas(seed, group):
+    """Alg. 1 blends at pixel p exactly the Gaussians plain blends there
+    whose test at the group's top-left pixel passes.  Removing one layer g
+    from an over-composite changes it by T_front alpha_g (c_g - C_behind),
+    at most alpha_g c_max per channel, and stopping at Gamma_theta leaves
+    out at most T_final c_max; so per pixel and channel
+        |C_plain - C_CR| <= c_max (sum of alpha_g,p over the skipped g
+                                   + T_final of each run that stopped).
+    The skipped set is computed here from the leader rule; the two images
+    are the oracle's."""
+    sc, cams = scenegen.uniform_10k(seed=seed, n=300, width=48, height=48)
+    cam = cams[0]
+    s64 = oracle.Scene64.from_scene(sc)
+    plain = oracle.render(s64, cam, oracle.Options())[0]
+    cr = oracle.render(s64, cam, oracle.Options(cr=True, group_w=group[0], group_h=group[1]))[0]
+    proj = oracle.preprocess(s64, cam, oracle.Options())
+    P = proj[proj["visible"] == 1]
+    cmax = P["rgb"].max(axis=0)
+    a_min, a_max = 1.0 / 255.0, 0.99
+
+    def alpha_on(x, y):
+        dx, dy = x - P["uv"][:, 0], y - P["uv"][:, 1]
+        q = P["conic"][:, 0] * dx * dx + 2.0 * P["conic"][:, 1] * dx * dy + P["conic"][:, 2] * dy * dy
+        al = np.minimum(a_max, P["opacity"] * np.exp(-0.5 * q))
+        return al, (q <= P["tg"]) & (al >= a_min)
+
+    checked = differ = 0
+    for py in range(48):
+        for px in range(48):
+            if min(plain.margin[py, px], cr.margin[py, px]) < 1e-9:
+                continue
+            al, on = alpha_on(px + 0.5, py + 0.5)
+            _, lead = alpha_on(px - px % group[0] + 0.5, py - py % group[1] + 0.5)
+            skipped = al[on & ~lead].sum()
+            stop = sum(t for t in (plain.T[py, px], cr.T[py, px]) if t < 0.01)
+            d = np.abs(plain.rgb[:, py, px] - cr.rgb[:, py, px])
+            assert np.all(d <= cmax * (skipped + stop) + 1e-12), (px, py, d, skipped, stop)
+            if skipped == 0 and stop == 0:
+                assert np.all(d == 0)   # no skip and no stop: the same layers
+            checked += 1
+            differ += int(np.any(d > 0))
+    assert checked > 0.99 * 48 * 48 and differ > 50
