@@ -297,6 +297,20 @@ def _fwd_bwd(args, device):
         e.record()
         torch.cuda.synchronize()
         out[f"{mode}_ms"] = s.elapsed_time(e) / k
+        # the backward alone on the last frame, and the frame's counted work
+        img = r.render(options=opts)
+        g = torch.sign(img - tgt) / img.numel()
+        r.render_backward(g)
+        torch.cuda.synchronize()
+        s.record()
+        for _ in range(k):
+            r.render_backward(g)
+        e.record()
+        torch.cuda.synchronize()
+        out[f"{mode}_bwd_ms"] = s.elapsed_time(e) / k
+        r.render(mode=mode, opacity_filter=(mode == "cr"), binning="tiles", count=True)
+        out[f"{mode}_work"] = {kk: r.last_stats[kk] for kk in ("n_visible", "n_instances", "leader_tests",
+                                                                "pairs_evaluated", "pairs_blended")}
     out["workload"] = (f"clusters_1m: {args.fwd_bwd_n} Gaussians in 64 clusters, 1280x720, L1 loss vs a target "
                        f"rendered from attributes + N(0, 0.01); gradients for all attributes; CR path with the "
                        f"opacity filter, plain path without; tile binning")
@@ -547,6 +561,10 @@ def run_gpu(args):
         __graft_entry__.build()
     _barrier(dist)
     torch.cuda.set_device(local)
+    if args.fwd_bwd_only:
+        if rank == 0:
+            print(json.dumps({"fwd_bwd": _fwd_bwd(args, local)}), flush=True)
+        return
     scene, cams = scenegen.unbounded_3m(n=args.n_gauss)
     r = Renderer(local)
     # stored in Morton order of the means (SEELE_SCENE_SPATIAL, computed at load)
@@ -904,6 +922,8 @@ def main():
     ap.add_argument("--impl", default="seele", choices=["seele", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fwd-bwd-n", type=int, default=1_000_000)
+    ap.add_argument("--fwd-bwd-only", action="store_true",
+                    help="time only the forward + backward step (for profiling captures of the backward kernels)")
     ap.add_argument("--multiview-n", type=int, default=2_000_000, help="0 skips the multi-view measurement")
     ap.add_argument("--ablation-n", type=int, default=500_000, help="0 skips the ablation")
     ap.add_argument("--n-gauss", type=int, default=3_000_000,

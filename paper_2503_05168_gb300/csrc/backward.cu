@@ -26,6 +26,38 @@ __device__ __forceinline__ float ex2_approx_b(float x) {
     return y;
 }
 
+// Warp totals of nine per-lane values.  Values 0..7 are reduced by
+// recursive halving: at each exchange a lane sends the half of its values
+// that its partner keeps and adds the half it keeps, so after the exchanges
+// over lane bits 4, 3 and 2 (then 1 and 0 on the one value left) lane l
+// holds the total of value (l >> 2) & 7 -- 9 shuffles instead of 40.  Value
+// 8 takes a plain butterfly.  Returns (total of value (l >> 2) & 7, total of
+// value 8).
+__device__ __forceinline__ float2 warp_sum9(const float (&v)[9], int lane) {
+    constexpr unsigned kAll = 0xffffffffu;
+    float a[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const bool hi = lane & 16;
+        a[i] = (hi ? v[i + 4] : v[i]) + __shfl_xor_sync(kAll, hi ? v[i] : v[i + 4], 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const bool hi = lane & 8;
+        a[i] = (hi ? a[i + 2] : a[i]) + __shfl_xor_sync(kAll, hi ? a[i] : a[i + 2], 8);
+    }
+    {
+        const bool hi = lane & 4;
+        a[0] = (hi ? a[1] : a[0]) + __shfl_xor_sync(kAll, hi ? a[0] : a[1], 4);
+    }
+    a[0] += __shfl_xor_sync(kAll, a[0], 2);
+    a[0] += __shfl_xor_sync(kAll, a[0], 1);
+    float w = v[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(kAll, w, o);
+    return make_float2(a[0], w);
+}
+
 template <int TW, int TH, int PW, int PH, int GW, int GH, bool CR>
 __global__ void __launch_bounds__((TW / PW) * (TH / PH))
     raster_bwd_kernel(const uint32_t* __restrict__ starts, const uint32_t* __restrict__ ends,
@@ -143,11 +175,13 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
                             const float e = expo(pi, pj);
                             if (e < B.z) continue;  // skipped in the forward pass too
                             const float al = fminf(amax, ex2_approx_b(e));
-                            const float om = 1.f - al;
-                            const float Tb = T[p] / om;  // transmittance before this entry
+                            // one correctly rounded reciprocal instead of four
+                            // divisions (1 - alpha >= 0.01 at the clamp)
+                            const float inv = __frcp_rn(1.f - al);
+                            const float Tb = T[p] * inv;  // transmittance before this entry
                             const float wgt = Tb * al;
-                            const float dal = g0[p] * (Tb * Cc.x - S0[p] / om) + g1[p] * (Tb * Cc.y - S1[p] / om) +
-                                              g2[p] * (Tb * Cc.z - S2[p] / om);
+                            const float dal = g0[p] * (Tb * Cc.x - S0[p] * inv) + g1[p] * (Tb * Cc.y - S1[p] * inv) +
+                                              g2[p] * (Tb * Cc.z - S2[p] * inv);
                             dr = fmaf(wgt, g0[p], dr);
                             dg = fmaf(wgt, g1[p], dg);
                             db = fmaf(wgt, g2[p], db);
@@ -169,17 +203,11 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
                         }
                 }
             if (__any_sync(0xffffffffu, any)) {
-                float v[9] = {du, dv, dcA, dcB, dcC, dlo, dr, dg, db};
-#pragma unroll
-                for (int q = 0; q < 9; ++q)
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
-                if (lane == 0) {
-                    float* G = grad_rec + 12 * (size_t)s_r[k];
-#pragma unroll
-                    for (int q = 0; q < 9; ++q)
-                        if (v[q] != 0.f) atomicAdd(G + q, v[q]);
-                }
+                const float v[9] = {du, dv, dcA, dcB, dcC, dlo, dr, dg, db};
+                const float2 tot = warp_sum9(v, lane);
+                float* G = grad_rec + 12 * (size_t)s_r[k];
+                if ((lane & 3) == 0 && tot.x != 0.f) atomicAdd(G + (lane >> 2), tot.x);
+                if (lane == 1 && tot.y != 0.f) atomicAdd(G + 8, tot.y);
             }
         }
     }
