@@ -73,7 +73,7 @@ struct seele_ctx {
 
     // frame workspace
     DevBuf rec, tiles, blocks, depth, visk[2], visv[2], offs, instk[2], instv[2], instm[2], ranges, msum,
-        border, chunkv, chunks, vbuf, status, hist, digtot, T, nc, rgb_tmp, sortcnt, grad_rec, cnts;
+        border, chunkv, chunks, vbuf, status, hist, digtot, T, nc, rgb_tmp, sortcnt, grad_rec, cnts, torder;
     DeviceStatus* h_status = nullptr;  // pinned mirror of the device status
     cudaEvent_t ev[SEELE_NUM_STAGES + 1] = {};
     bool profiling = false;
@@ -911,7 +911,7 @@ void seele_destroy(seele_ctx* c) {
                      &c->ranges, &c->status, &c->hist, &c->digtot, &c->T, &c->nc, &c->rgb_tmp, &c->sortcnt,
                      &c->grad_rec, &c->blocks, &c->instm[0], &c->instm[1], &c->msum, &c->border, &c->chunkv,
                      &c->chunks, &c->vbuf, &c->cnts, &c->skew, &c->veto, &c->order, &c->unordered,
-                     &c->order_scratch};
+                     &c->order_scratch, &c->torder};
     for (DevBuf* b : all) release(*b);
     stream_release(c);
     release(c->viewt);
@@ -1510,6 +1510,11 @@ seele_status seele_render_backward(seele_ctx* c, const float* dL_drgb, const see
     a.T_final = ptr<float>(c->T);
     a.n_contrib = ptr<uint32_t>(c->nc);
     a.grad_rec = ptr<float>(c->grad_rec);
+    // tiles with the longest lists first, as in the forward pass
+    SEELE_CUDA(c, ensure(c->torder, 4ull * c->n_tiles_total));
+    launch_block_order(a.starts, a.ends, c->n_tiles_total, ptr<uint32_t>(c->torder), s);
+    SEELE_LAUNCHED(c);
+    a.tile_order = ptr<const uint32_t>(c->torder);
     if (!launch_raster_bwd(a, s)) return fail(c, SEELE_ERR_ARG, "no backward rasterizer for these options");
     SEELE_LAUNCHED(c);
     SceneDev sc;

@@ -64,7 +64,7 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
                       const uint32_t* __restrict__ inst_rec, const float4* __restrict__ rec,
                       const CamDev* __restrict__ cams, int n_cams, FrameParams fp, const float* __restrict__ dL_drgb,
                       const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
-                      float* __restrict__ grad_rec) {
+                      float* __restrict__ grad_rec, const uint32_t* __restrict__ tile_order) {
     constexpr int NT = (TW / PW) * (TH / PH);
     constexpr int NP = PW * PH;
     constexpr int TXN = TW / PW;
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
     __shared__ uint32_t s_r[NT];
     __shared__ uint32_t s_max;
 
-    const uint32_t gtile = blockIdx.x;
+    const uint32_t gtile = tile_order ? __ldg(tile_order + blockIdx.x) : blockIdx.x;
     int lo = 0, hi = n_cams - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -257,7 +257,10 @@ __device__ __forceinline__ void sh_basis_grad(float x, float y, float z, float* 
     }
 }
 
-template <int DEG>
+// ONE: a single camera (the training step).  Its SH gradients are written
+// once, so they go through shared memory and leave as whole rows; with
+// several cameras they are summed in registers over the cameras.
+template <int DEG, bool ONE>
 __global__ void __launch_bounds__(128) preprocess_bwd_kernel(SceneDev sc, const CamDev* __restrict__ cams,
                                                              FrameParams fp, const uint32_t* __restrict__ tiles,
                                                              const float* __restrict__ grad_rec,
@@ -266,22 +269,31 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(SceneDev sc, const 
                                                              float* __restrict__ d_sh,
                                                              const uint32_t* __restrict__ order) {
     constexpr int NC = (DEG + 1) * (DEG + 1);
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= fp.n) return;
+    constexpr int NF = 3 * NC, RS = NF | 1;  // SH gradient row, padded to an odd stride
+    __shared__ float s_sh[ONE ? 128 * RS : 1];
+    const int t = threadIdx.x;
+    const int g = blockIdx.x * blockDim.x + t;
+    bool wrote = false;
+    if (g < fp.n) {
     float gm[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, glogit = 0.f;
-    float gsh[3 * NC];
+    float gsh[ONE ? 1 : NF];
+    if constexpr (!ONE) {
 #pragma unroll
-    for (int i = 0; i < 3 * NC; ++i) gsh[i] = 0.f;
+        for (int i = 0; i < NF; ++i) gsh[i] = 0.f;
+    }
     const float4 pl = __ldg(sc.pos_logit + g);
     const float4 q4 = __ldg(sc.quat + g);
     const float4 ls = __ldg(sc.log_scale + g);
 
-    for (int ci = 0; ci < fp.n_cams; ++ci) {
+    for (int ci = 0; ci < (ONE ? 1 : fp.n_cams); ++ci) {
         const size_t rid = (size_t)ci * fp.n + g;
         if (__ldg(tiles + rid) == 0u) continue;
+        // the record's 9 gradients, 48-byte aligned: two 16-byte loads and one word
         const float* G = grad_rec + 12 * rid;
-        const float gu = G[0], gv = G[1], gcA = G[2], gcB = G[3], gcC = G[4], glo = G[5];
-        const float grgb[3] = {G[6], G[7], G[8]};
+        const float4 G0 = __ldg(reinterpret_cast<const float4*>(G));
+        const float4 G1 = __ldg(reinterpret_cast<const float4*>(G) + 1);
+        const float gu = G0.x, gv = G0.y, gcA = G0.z, gcB = G0.w, gcC = G1.x, glo = G1.y;
+        const float grgb[3] = {G1.z, G1.w, __ldg(G + 8)};
         const CamDev& C = cams[ci];
 
         // ---- recompute the forward quantities
@@ -398,32 +410,46 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(SceneDev sc, const 
         dd[2] *= rn;
         float Yb[NC], dY[NC][3];
         sh_basis_grad<DEG>(dd[0], dd[1], dd[2], Yb, dY);
-        float gdir[3] = {0.f, 0.f, 0.f};
-        constexpr int NPL = (3 * NC + 3) / 4;
-        float shf[4 * NPL];
+        // the coefficients stream in twice (the second time from L1):
+        // first the raw colour, then w_k = sum_c gc_c sh_kc, so that the
+        // direction gradient is sum_k w_k grad Y_k
+        constexpr int NPL = (NF + 3) / 4;
+        float raw[3] = {0.5f, 0.5f, 0.5f};
 #pragma unroll
         for (int jp = 0; jp < NPL; ++jp) {
             const float4 vv = __ldg(sc.sh + (size_t)jp * fp.n + g);
-            shf[4 * jp] = vv.x;
-            shf[4 * jp + 1] = vv.y;
-            shf[4 * jp + 2] = vv.z;
-            shf[4 * jp + 3] = vv.w;
+            const float e4[4] = {vv.x, vv.y, vv.z, vv.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (4 * jp + i < NF) raw[(4 * jp + i) % 3] = fmaf(e4[i], Yb[(4 * jp + i) / 3], raw[(4 * jp + i) % 3]);
         }
+        const float gc[3] = {raw[0] > 0.f ? grgb[0] : 0.f, raw[1] > 0.f ? grgb[1] : 0.f,
+                             raw[2] > 0.f ? grgb[2] : 0.f};
+        float w[NC];
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            float raw = 0.5f;
+        for (int k = 0; k < NC; ++k) w[k] = 0.f;
 #pragma unroll
-            for (int k = 0; k < NC; ++k) raw = fmaf(shf[3 * k + ch], Yb[k], raw);
-            const float gc = raw > 0.f ? grgb[ch] : 0.f;
-            if (gc == 0.f) continue;
+        for (int jp = 0; jp < NPL; ++jp) {
+            const float4 vv = __ldg(sc.sh + (size_t)jp * fp.n + g);
+            const float e4[4] = {vv.x, vv.y, vv.z, vv.w};
 #pragma unroll
-            for (int k = 0; k < NC; ++k) {
-                gsh[3 * k + ch] = fmaf(Yb[k], gc, gsh[3 * k + ch]);
-                const float w = shf[3 * k + ch] * gc;
-                gdir[0] = fmaf(w, dY[k][0], gdir[0]);
-                gdir[1] = fmaf(w, dY[k][1], gdir[1]);
-                gdir[2] = fmaf(w, dY[k][2], gdir[2]);
-            }
+            for (int i = 0; i < 4; ++i)
+                if (4 * jp + i < NF) w[(4 * jp + i) / 3] = fmaf(e4[i], gc[(4 * jp + i) % 3], w[(4 * jp + i) / 3]);
+        }
+        if constexpr (ONE) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) s_sh[t * RS + f] = Yb[f / 3] * gc[f % 3];
+            wrote = true;
+        } else {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) gsh[f] = fmaf(Yb[f / 3], gc[f % 3], gsh[f]);
+        }
+        float gdir[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            gdir[0] = fmaf(w[k], dY[k][0], gdir[0]);
+            gdir[1] = fmaf(w[k], dY[k][1], gdir[1]);
+            gdir[2] = fmaf(w[k], dY[k][2], gdir[2]);
         }
         const float dot = dd[0] * gdir[0] + dd[1] * gdir[1] + dd[2] * gdir[2];
 #pragma unroll
@@ -439,8 +465,29 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(SceneDev sc, const 
 #pragma unroll
     for (int i = 0; i < 4; ++i) d_quat[4 * go + i] = gq[i];
     d_logit[go] = glogit;
+    if constexpr (!ONE) {
 #pragma unroll
-    for (int i = 0; i < 3 * NC; ++i) d_sh[go * 3 * NC + i] = gsh[i];
+        for (int i = 0; i < NF; ++i) d_sh[go * NF + i] = gsh[i];
+    }
+    }  // g < n
+    if constexpr (ONE) {
+        if (!wrote)
+            for (int f = 0; f < NF; ++f) s_sh[t * RS + f] = 0.f;
+        __syncthreads();
+        const size_t g0 = (size_t)blockIdx.x * blockDim.x;
+        const int cnt = (int)min((size_t)blockDim.x, (size_t)fp.n - g0);
+        if (order == nullptr) {
+            // the block's rows are one contiguous span of the output
+            for (int i = t; i < cnt * NF; i += blockDim.x) d_sh[g0 * NF + i] = s_sh[(i / NF) * RS + i % NF];
+        } else {
+            // rows at the caller's indices: one warp per row
+            const int lane = t & 31;
+            for (int r = t >> 5; r < cnt; r += (int)(blockDim.x >> 5)) {
+                float* dst = d_sh + (size_t)__ldg(order + g0 + r) * NF;
+                for (int f = lane; f < NF; f += 32) dst[f] = s_sh[r * RS + f];
+            }
+        }
+    }
 }
 
 template <int TW, int TH, int PW, int PH, int GW, int GH, bool CR>
@@ -448,7 +495,7 @@ static void launch_bwd_one(const RasterBwdArgs& a, cudaStream_t s) {
     constexpr int NT = (TW / PW) * (TH / PH);
     raster_bwd_kernel<TW, TH, PW, PH, GW, GH, CR><<<a.n_tiles, NT, 0, s>>>(
         a.starts, a.ends, a.inst_rec, a.rec, a.cams, a.n_cams, a.fp, a.dL_drgb, a.T_final, a.n_contrib,
-        a.grad_rec);
+        a.grad_rec, a.tile_order);
 }
 
 template <int TW, int TH>
@@ -487,11 +534,20 @@ void launch_preprocess_bwd(const SceneDev& sc, const CamDev* cams, const FramePa
                            const float* grad_rec, float* d_means, float* d_ls, float* d_quat, float* d_logit,
                            float* d_sh, const uint32_t* order, cudaStream_t s) {
     const int blocks = (fp.n + 127) / 128;
+    if (fp.n_cams == 1) {
+        switch (fp.sh_degree) {
+            case 0: preprocess_bwd_kernel<0, true><<<blocks, 128, 0, s>>>(sc, cams, fp, tiles, grad_rec, d_means, d_ls, d_quat, d_logit, d_sh, order); break;
+            case 1: preprocess_bwd_kernel<1, true><<<blocks, 128, 0, s>>>(sc, cams, fp, tiles, grad_rec, d_means, d_ls, d_quat, d_logit, d_sh, order); break;
+            case 2: preprocess_bwd_kernel<2, true><<<blocks, 128, 0, s>>>(sc, cams, fp, tiles, grad_rec, d_means, d_ls, d_quat, d_logit, d_sh, order); break;
+            default: preprocess_bwd_kernel<3, true><<<blocks, 128, 0, s>>>(sc, cams, fp, tiles, grad_rec, d_means, d_ls, d_quat, d_logit, d_sh, order); break;
+        }
+        return;
+    }
     switch (fp.sh_degree) {
-        case 0: preprocess_bwd_kernel<0><<<blocks, 128, 0, s>>>(sc, cams, fp, tiles, grad_rec, d_means, d_ls, d_quat, d_logit, d_sh, order); break;
-        case 1: preprocess_bwd_kernel<1><<<blocks, 128, 0, s>>>(sc, cams, fp, tiles, grad_rec, d_means, d_ls, d_quat, d_logit, d_sh, order); break;
-        case 2: preprocess_bwd_kernel<2><<<blocks, 128, 0, s>>>(sc, cams, fp, tiles, grad_rec, d_means, d_ls, d_quat, d_logit, d_sh, order); break;
-        default: preprocess_bwd_kernel<3><<<blocks, 128, 0, s>>>(sc, cams, fp, tiles, grad_rec, d_means, d_ls, d_quat, d_logit, d_sh, order); break;
+        case 0: preprocess_bwd_kernel<0, false><<<blocks, 128, 0, s>>>(sc, cams, fp, tiles, grad_rec, d_means, d_ls, d_quat, d_logit, d_sh, order); break;
+        case 1: preprocess_bwd_kernel<1, false><<<blocks, 128, 0, s>>>(sc, cams, fp, tiles, grad_rec, d_means, d_ls, d_quat, d_logit, d_sh, order); break;
+        case 2: preprocess_bwd_kernel<2, false><<<blocks, 128, 0, s>>>(sc, cams, fp, tiles, grad_rec, d_means, d_ls, d_quat, d_logit, d_sh, order); break;
+        default: preprocess_bwd_kernel<3, false><<<blocks, 128, 0, s>>>(sc, cams, fp, tiles, grad_rec, d_means, d_ls, d_quat, d_logit, d_sh, order); break;
     }
 }
 

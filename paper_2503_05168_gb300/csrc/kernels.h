@@ -150,6 +150,7 @@ struct RasterBwdArgs {
     const float* T_final;
     const uint32_t* n_contrib;
     float* grad_rec;            // [R][12]: d(u, v, cA, cB, cC, log2 o, r, g, b), zeroed by the caller
+    const uint32_t* tile_order; // nullable: CTA i walks tile tile_order[i] (longest lists first)
 };
 bool launch_raster_bwd(const RasterBwdArgs& a, cudaStream_t s);
 // order (nullable): caller index of each resident Gaussian (spatial order)
