@@ -73,7 +73,11 @@ struct seele_ctx {
 
     // frame workspace
     DevBuf rec, tiles, blocks, depth, visk[2], visv[2], offs, instk[2], instv[2], instm[2], ranges, msum,
-        border, chunkv, chunks, vbuf, status, hist, digtot, T, nc, rgb_tmp, sortcnt, grad_rec, cnts, torder;
+        border, chunkv, chunks, vbuf, status, hist, digtot, T, nc, rgb_tmp, sortcnt, grad_rec, cnts, torder,
+        ckpt, cfin, bmap;
+    // the last render wrote transmittance checkpoints for ckpt_slots slots
+    bool ckpt_valid = false;
+    uint64_t ckpt_slots = 0;
     DeviceStatus* h_status = nullptr;  // pinned mirror of the device status
     cudaEvent_t ev[SEELE_NUM_STAGES + 1] = {};
     bool profiling = false;
@@ -669,6 +673,11 @@ seele_status size_frame(seele_ctx* c, FrameInfo& f) {
     SEELE_CUDA(c, ensure(c->nc, 4 * f.pix_total));
     SEELE_CUDA(c, ensure(c->viewt, 12ull * f.ncam + 8));
     if (!f.rgb_dev) SEELE_CUDA(c, ensure(c->rgb_tmp, 12 * f.pix_total));
+    if (!f.blocks) {
+        // transmittance checkpoints for the backward pass (tile binning)
+        SEELE_CUDA(c, ensure(c->ckpt, 16ull * ((cap >> kCkptShift) + 2) * (uint64_t)f.fp.tile_w * f.fp.tile_h));
+        SEELE_CUDA(c, ensure(c->cfin, 16 * f.pix_total));
+    }
     f.cnt_words = radix_count_words((uint32_t)std::max<uint64_t>(R, cap));
     SEELE_CUDA(c, ensure(c->sortcnt, 8ull * f.cnt_words));
     // digit totals of the sorts' passes (cleared every frame)
@@ -716,6 +725,8 @@ std::vector<uint64_t> graph_key(const seele_ctx* c, const seele_options* opt, co
     k.push_back((uint64_t)(uintptr_t)c->rec.p);
     k.push_back((uint64_t)(uintptr_t)c->instk[0].p);
     k.push_back((uint64_t)(uintptr_t)c->instm[0].p);
+    k.push_back((uint64_t)(uintptr_t)c->ckpt.p);
+    k.push_back((uint64_t)(uintptr_t)c->cfin.p);
     return k;
 }
 
@@ -832,6 +843,9 @@ seele_status enqueue_frame(seele_ctx* c, const seele_options* opt, const FrameIn
     ra.count_into = count ? st : nullptr;
     ra.view_end = vt + 1;
     ra.view_done = reinterpret_cast<uint32_t*>(vt + 1 + ncam);
+    const bool ckpt = !f.blocks && !count && c->skew_frac <= 0.0 && c->topk_k <= 0;
+    ra.ckpt = ckpt ? ptr<float4>(c->ckpt) : nullptr;
+    ra.cfin = ckpt ? ptr<float4>(c->cfin) : nullptr;
     SEELE_MARK(SEELE_STAGE_RASTER);
     if (c->skew_frac > 0.0) {
         uint32_t* sk = ptr<uint32_t>(c->skew);
@@ -911,7 +925,7 @@ void seele_destroy(seele_ctx* c) {
                      &c->ranges, &c->status, &c->hist, &c->digtot, &c->T, &c->nc, &c->rgb_tmp, &c->sortcnt,
                      &c->grad_rec, &c->blocks, &c->instm[0], &c->instm[1], &c->msum, &c->border, &c->chunkv,
                      &c->chunks, &c->vbuf, &c->cnts, &c->skew, &c->veto, &c->order, &c->unordered,
-                     &c->order_scratch, &c->torder};
+                     &c->order_scratch, &c->torder, &c->ckpt, &c->cfin, &c->bmap};
     for (DevBuf* b : all) release(*b);
     stream_release(c);
     release(c->viewt);
@@ -1352,6 +1366,9 @@ seele_status seele_render(seele_ctx* c, const seele_options* opt, float* out_rgb
         c->n_pix_total = f.pix_total;
         c->last_opt = *opt;
         c->last_fp = f.fp;
+        // the frame (enqueued or replayed) wrote checkpoints for the backward pass
+        c->ckpt_valid = !f.blocks && !count && c->skew_frac <= 0.0 && c->topk_k <= 0;
+        c->ckpt_slots = (f.cap >> kCkptShift) + 2;
         if (!f.rgb_dev)
             SEELE_CUDA(c, cudaMemcpyAsync(out_rgb, c->rgb_tmp.p, 12 * f.pix_total, cudaMemcpyDeviceToHost, c->stream));
         if (out_T && !f.T_dev)
@@ -1515,6 +1532,22 @@ seele_status seele_render_backward(seele_ctx* c, const float* dL_drgb, const see
     launch_block_order(a.starts, a.ends, c->n_tiles_total, ptr<uint32_t>(c->torder), s);
     SEELE_LAUNCHED(c);
     a.tile_order = ptr<const uint32_t>(c->torder);
+    // long lists are walked in kCkptL-entry chunks from the forward pass's
+    // checkpoints, one CTA each
+    a.ckpt = nullptr;
+    a.cfin = nullptr;
+    a.chunk_map = nullptr;
+    a.n_map = 0;
+    if (c->ckpt_valid) {
+        a.n_map = (uint32_t)c->ckpt_slots;
+        SEELE_CUDA(c, ensure(c->bmap, 4ull * a.n_map));
+        SEELE_CUDA(c, cudaMemsetAsync(c->bmap.p, 0xff, 4ull * a.n_map, s));
+        launch_chunk_map(a.starts, a.ends, c->n_tiles_total, ptr<uint32_t>(c->bmap), a.n_map, s);
+        SEELE_LAUNCHED(c);
+        a.ckpt = ptr<const float4>(c->ckpt);
+        a.cfin = ptr<const float4>(c->cfin);
+        a.chunk_map = ptr<const uint32_t>(c->bmap);
+    }
     if (!launch_raster_bwd(a, s)) return fail(c, SEELE_ERR_ARG, "no backward rasterizer for these options");
     SEELE_LAUNCHED(c);
     SceneDev sc;

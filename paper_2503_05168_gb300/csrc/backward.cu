@@ -64,7 +64,9 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
                       const uint32_t* __restrict__ inst_rec, const float4* __restrict__ rec,
                       const CamDev* __restrict__ cams, int n_cams, FrameParams fp, const float* __restrict__ dL_drgb,
                       const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
-                      float* __restrict__ grad_rec, const uint32_t* __restrict__ tile_order) {
+                      float* __restrict__ grad_rec, const uint32_t* __restrict__ tile_order,
+                      const float4* __restrict__ ckpt, const float4* __restrict__ cfin,
+                      const uint32_t* __restrict__ chunk_map, uint32_t n_tiles) {
     constexpr int NT = (TW / PW) * (TH / PH);
     constexpr int NP = PW * PH;
     constexpr int TXN = TW / PW;
@@ -76,7 +78,16 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
     __shared__ uint32_t s_r[NT];
     __shared__ uint32_t s_max;
 
-    const uint32_t gtile = tile_order ? __ldg(tile_order + blockIdx.x) : blockIdx.x;
+    // CTA -> (tile, chunk): the first n_tiles CTAs take chunk 0 of every
+    // tile, the others the later chunks of long lists (see kCkptShift)
+    uint32_t gtile, chunk = 0;
+    if (blockIdx.x < n_tiles) {
+        gtile = tile_order ? __ldg(tile_order + blockIdx.x) : blockIdx.x;
+    } else {
+        gtile = __ldg(chunk_map + (blockIdx.x - n_tiles));
+        if (gtile == 0xffffffffu) return;
+        chunk = (blockIdx.x - n_tiles) - (__ldg(starts + gtile) >> kCkptShift);
+    }
     int lo = 0, hi = n_cams - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -117,12 +128,33 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
     atomicMax(&s_max, my_max);
     __syncthreads();
     const uint32_t lmax = min(s_max, end - start);
+    // this CTA's part of the list; with checkpoints, chunk [c L, (c + 1) L)
+    const uint32_t wlo = ckpt ? chunk * kCkptL : 0u;
+    const uint32_t whi = ckpt ? min(lmax, (chunk + 1u) * kCkptL) : lmax;
+    if (wlo >= whi) return;
+    if (whi < lmax) {
+        // start from the state the forward pass saved at the chunk's end:
+        // T there, and the colour behind it = final colour - colour so far
+        const float4* slot = ckpt + (size_t)((start >> kCkptShift) + chunk + 1u) * (TW * TH);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            const int x = bx + p % PW, y = by + p / PW;
+            if (x < C.W && y < C.H) {
+                const float4 k = __ldg(slot + (y - ty * TH) * TW + (x - tx * TW));
+                const float4 f = __ldg(cfin + C.pix_offset + (size_t)y * C.W + x);
+                T[p] = k.x;
+                S0[p] = f.y - k.y;
+                S1[p] = f.z - k.z;
+                S2[p] = f.w - k.w;
+            }
+        }
+    }
     const float fx0 = (float)bx + 0.5f, fy0 = (float)by + 0.5f;
     const float lx0 = (float)(bx / GW * GW) + 0.5f, ly0 = (float)(by / GH * GH) + 0.5f;  // the group's leader
     const float amax = fp.alpha_max;
 
-    for (int b1 = (int)lmax; b1 > 0; b1 -= NT) {
-        const int b0 = max(0, b1 - NT);
+    for (int b1 = (int)whi; b1 > (int)wlo; b1 -= NT) {
+        const int b0 = max((int)wlo, b1 - NT);
         __syncthreads();
         if (t < b1 - b0) {
             const uint32_t r = __ldg(inst_rec + start + b0 + t);
@@ -493,9 +525,9 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(SceneDev sc, const 
 template <int TW, int TH, int PW, int PH, int GW, int GH, bool CR>
 static void launch_bwd_one(const RasterBwdArgs& a, cudaStream_t s) {
     constexpr int NT = (TW / PW) * (TH / PH);
-    raster_bwd_kernel<TW, TH, PW, PH, GW, GH, CR><<<a.n_tiles, NT, 0, s>>>(
+    raster_bwd_kernel<TW, TH, PW, PH, GW, GH, CR><<<a.n_tiles + (a.ckpt ? a.n_map : 0u), NT, 0, s>>>(
         a.starts, a.ends, a.inst_rec, a.rec, a.cams, a.n_cams, a.fp, a.dL_drgb, a.T_final, a.n_contrib,
-        a.grad_rec, a.tile_order);
+        a.grad_rec, a.tile_order, a.ckpt, a.cfin, a.chunk_map, a.n_tiles);
 }
 
 template <int TW, int TH>
@@ -528,6 +560,29 @@ bool launch_raster_bwd(const RasterBwdArgs& a, cudaStream_t s) {
     if (a.fp.tile_w == 32 && a.fp.tile_h == 8) return launch_bwd_shape<32, 8>(a, s);
     if (a.fp.tile_w == 32 && a.fp.tile_h == 16) return launch_bwd_shape<32, 16>(a, s);
     return false;
+}
+
+// Chunk map of the backward pass: slot (start_t >> kCkptShift) + c -> t for
+// the chunks c >= 1 of every list longer than kCkptL (slots of different
+// lists never collide; unused slots stay all-ones).
+__global__ void chunk_map_kernel(const uint32_t* __restrict__ starts, const uint32_t* __restrict__ ends,
+                                 uint32_t n_tiles, uint32_t* __restrict__ map, uint32_t n_map) {
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x) {
+        const uint32_t s = __ldg(starts + t), e = __ldg(ends + t);
+        if (s >= e) continue;
+        const uint32_t n = (e - s + kCkptL - 1u) >> kCkptShift;
+        for (uint32_t c = 1; c < n; ++c) {
+            const uint32_t i = (s >> kCkptShift) + c;
+            if (i < n_map) map[i] = t;
+        }
+    }
+}
+
+void launch_chunk_map(const uint32_t* starts, const uint32_t* ends, uint32_t n_tiles, uint32_t* map, uint32_t n_map,
+                      cudaStream_t s) {
+    if (n_tiles == 0) return;
+    chunk_map_kernel<<<std::min<uint32_t>((n_tiles + 255) / 256, 152u * 4u), 256, 0, s>>>(starts, ends, n_tiles, map,
+                                                                                         n_map);
 }
 
 void launch_preprocess_bwd(const SceneDev& sc, const CamDev* cams, const FrameParams& fp, const uint32_t* tiles,

@@ -61,6 +61,14 @@ constexpr uint32_t kChunkItems = 4096;
 // counts saturated at kPackedCountMax (the true count is then read again).
 constexpr int kPackedIdBits = 24;
 constexpr uint32_t kPackedCountMax = 255u;
+// Transmittance checkpoints of tile-binned renders: every kCkptL entries of
+// a tile's list, each pixel's (T, r, g, b) so far.  Tile t's checkpoint c
+// (c >= 1, at list position c * kCkptL < its length) is slot
+// (start_t >> kCkptShift) + c: lists are disjoint, so slots never collide
+// and there are at most capacity / kCkptL + 2 of them.  The backward pass
+// walks each kCkptL-entry chunk of a list in a CTA of its own from them.
+constexpr uint32_t kCkptShift = 8;
+constexpr uint32_t kCkptL = 1u << kCkptShift;
 
 // Block binning: a tile block is kBlockW x kBlockH tiles; its instances carry a
 // 32-bit mask of the block's tiles that the Gaussian reaches (bit j * kBlockW + i

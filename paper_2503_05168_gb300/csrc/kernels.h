@@ -132,6 +132,10 @@ struct RasterArgs {
     DeviceStatus* count_into;   // non-null: run the counting variant
     unsigned long long* view_end;  // [n_cams] time the camera's last tile finished (%globaltimer)
     uint32_t* view_done;        // [n_cams] finished tiles, cleared per frame
+    // tile binning (else nullptr): transmittance checkpoints, [slots][tile pixels]
+    // (see kCkptShift), and every pixel's final (T, r, g, b)
+    float4* ckpt;
+    float4* cfin;
 };
 bool launch_raster_fwd(const RasterArgs& a, cudaStream_t s);
 
@@ -151,7 +155,15 @@ struct RasterBwdArgs {
     const uint32_t* n_contrib;
     float* grad_rec;            // [R][12]: d(u, v, cA, cB, cC, log2 o, r, g, b), zeroed by the caller
     const uint32_t* tile_order; // nullable: CTA i walks tile tile_order[i] (longest lists first)
+    // checkpoints of the forward pass (nullptr: each CTA walks a whole list):
+    // CTAs n_tiles + i walk chunk i - (start >> kCkptShift) of tile chunk_map[i]
+    const float4* ckpt;
+    const float4* cfin;
+    const uint32_t* chunk_map;
+    uint32_t n_map;
 };
+void launch_chunk_map(const uint32_t* starts, const uint32_t* ends, uint32_t n_tiles, uint32_t* map, uint32_t n_map,
+                      cudaStream_t s);
 bool launch_raster_bwd(const RasterBwdArgs& a, cudaStream_t s);
 // order (nullable): caller index of each resident Gaussian (spatial order)
 void launch_preprocess_bwd(const SceneDev& sc, const CamDev* cams, const FrameParams& fp, const uint32_t* tiles,

@@ -38,7 +38,7 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
                       const float4* __restrict__ rec, const CamDev* __restrict__ cams, int n_cams, FrameParams fp,
                       float* __restrict__ out_rgb, float* __restrict__ out_T, uint32_t* __restrict__ out_nc,
                       DeviceStatus* __restrict__ counters, unsigned long long* __restrict__ view_end,
-                      uint32_t* __restrict__ view_done) {
+                      uint32_t* __restrict__ view_done, float4* __restrict__ ckpt, float4* __restrict__ cfin) {
     constexpr int NT = (TW / PW) * (TH / PH);
     constexpr int NP = PW * PH;
     constexpr int TXN = TW / PW;
@@ -316,6 +316,13 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
         }
         } while (0);
         pos0 += (uint32_t)cnt;
+        if (!BLOCKS && ckpt != nullptr && (pos0 & (kCkptL - 1u)) == 0u && pos0 < rg.y - rg.x) {
+            float4* slot = ckpt + (size_t)((rg.x >> kCkptShift) + (pos0 >> kCkptShift)) * (TW * TH);
+#pragma unroll
+            for (int p = 0; p < NP; ++p)
+                if (bx + p % PW < C.W && by + p / PW < C.H)
+                    slot[(by - ty * TH + p / PW) * TW + (bx - tx * TW + p % PW)] = make_float4(T[p], cr[p], cg[p], cb[p]);
+        }
     }
 
     if (COUNT) {
@@ -335,6 +342,7 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
             img[2 * plane + o] = cb[p];
             out_T[C.pix_offset + o] = T[p];
             out_nc[C.pix_offset + o] = nc[p];
+            if (cfin != nullptr) cfin[C.pix_offset + o] = make_float4(T[p], cr[p], cg[p], cb[p]);
         }
     }
     // the CTA that finishes a camera's last tile stamps the view's end time
@@ -351,7 +359,8 @@ static void launch_variant(const RasterArgs& a, cudaStream_t s) {
     const uint32_t grid = BLOCKS ? 32 * a.n_blocks : a.n_tiles;
     launch_pdl(raster_fwd_kernel<TW, TH, PW, PH, GW, GH, CR, COUNT, BLOCKS>, dim3(grid), dim3(NT), 0, s,
                a.starts, a.ends, a.inst_rec, a.inst_mask, a.mask_summary, a.block_order, a.rec, a.cams, a.n_cams,
-               a.fp, a.out_rgb, a.out_T, a.out_nc, COUNT ? a.count_into : nullptr, a.view_end, a.view_done);
+               a.fp, a.out_rgb, a.out_T, a.out_nc, COUNT ? a.count_into : nullptr, a.view_end, a.view_done,
+               (COUNT || BLOCKS) ? nullptr : a.ckpt, (COUNT || BLOCKS) ? nullptr : a.cfin);
 }
 
 template <int TW, int TH, int PW, int PH, int GW, int GH, bool CR>
