@@ -549,10 +549,12 @@ int enqueue_tile_sort(seele_ctx* c, const FrameInfo& f, const uint32_t* order, c
     SEELE_MARK_EXT(c, SEELE_STAGE_RANGES);
     if (f.blocks) {
         launch_mask_summary(masks[fin], st, ptr<uint32_t>(c->msum), (uint32_t)(cap / 32 + 1), s);
-        launch_block_order(run, run + units, (uint32_t)units, ptr<uint32_t>(c->border), s);
-        if (cudaPeekAtLastError() != cudaSuccess) return -1;
-        launches += 2;
+        ++launches;
     }
+    // CTAs take the units with the longest lists first
+    launch_block_order(run, run + units, (uint32_t)units, ptr<uint32_t>(c->border), s);
+    if (cudaPeekAtLastError() != cudaSuccess) return -1;
+    ++launches;
     return fin;
 }
 
@@ -661,8 +663,8 @@ seele_status size_frame(seele_ctx* c, FrameInfo& f) {
     if (f.blocks) {
         SEELE_CUDA(c, ensure(c->blocks, 4 * R));
         SEELE_CUDA(c, ensure(c->msum, 4 * (cap / 32 + 2)));
-        SEELE_CUDA(c, ensure(c->border, 4 * f.blocks_total));
     }
+    SEELE_CUDA(c, ensure(c->border, 4 * f.units_total));
     SEELE_CUDA(c, ensure(c->offs, 4 * R));
     SEELE_CUDA(c, ensure(c->cnts, 4 * R));
     SEELE_CUDA(c, ensure(c->chunkv, 4 * (R / kChunkItems + 1)));
@@ -725,6 +727,7 @@ std::vector<uint64_t> graph_key(const seele_ctx* c, const seele_options* opt, co
     k.push_back((uint64_t)(uintptr_t)c->rec.p);
     k.push_back((uint64_t)(uintptr_t)c->instk[0].p);
     k.push_back((uint64_t)(uintptr_t)c->instm[0].p);
+    k.push_back((uint64_t)(uintptr_t)c->border.p);
     k.push_back((uint64_t)(uintptr_t)c->ckpt.p);
     k.push_back((uint64_t)(uintptr_t)c->cfin.p);
     return k;
@@ -827,7 +830,7 @@ seele_status enqueue_frame(seele_ctx* c, const seele_options* opt, const FrameIn
     ra.inst_rec = ptr<uint32_t>(c->instv[fin]);
     ra.inst_mask = f.blocks ? ptr<uint32_t>(c->instm[fin]) : nullptr;
     ra.mask_summary = f.blocks ? ptr<uint32_t>(c->msum) : nullptr;
-    ra.block_order = f.blocks ? ptr<uint32_t>(c->border) : nullptr;
+    ra.block_order = ptr<uint32_t>(c->border);
     ra.n_blocks = (uint32_t)f.blocks_total;
     ra.rec = ptr<float4>(c->rec);
     ra.cams = cams;

@@ -114,7 +114,8 @@ struct RasterArgs {
     const uint32_t* ends;       //   units are tiles, or tile blocks with block binning
     const uint32_t* inst_rec;
     // block binning (else nullptr): per entry the tiles of its block it reaches,
-    // per 32 entries the OR of those masks, and the block visiting order
+    // and per 32 entries the OR of those masks; block_order: the order CTAs
+    // visit the units (blocks, or tiles with tile binning) in
     const uint32_t* inst_mask;
     const uint32_t* mask_summary;
     const uint32_t* block_order;

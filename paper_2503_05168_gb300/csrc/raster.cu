@@ -70,7 +70,7 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
         gtile = Cb.tile_offset + (uint32_t)(ty * Cb.tiles_x + tx);
         unit = b;
     } else {
-        gtile = blockIdx.x;
+        gtile = block_order ? __ldg(block_order + blockIdx.x) : blockIdx.x;  // longest lists first
         int hi = n_cams - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
