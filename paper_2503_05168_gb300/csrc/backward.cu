@@ -2,11 +2,13 @@
 // CR "do not participate in gradient descent": every skip and stop decision
 // of the forward pass is replayed and held fixed).
 //
-// raster_bwd_kernel: one CTA per tile, the same 2x2-pixels-per-thread layout
-//   as the forward pass.  Each pixel walks its list back to front from its
-//   last blended entry; the transmittance before an entry is recomputed from
-//   the stored final T by T_j = T_{j+1} / (1 - alpha_j) (not stored per
-//   entry), and S, the colour accumulated behind entry j, gives
+// raster_bwd_kernel: one CTA per 256-entry chunk of a tile's list (one per
+//   tile for lists that short), the same 2x2-pixels-per-thread layout as
+//   the forward pass.  Each pixel walks its chunk back to front from its
+//   last blended entry; the transmittance before an entry is recomputed by
+//   T_j = T_{j+1} / (1 - alpha_j) from the state at the chunk's end (the
+//   final T, or the forward pass's checkpoint there), and S, the colour
+//   accumulated behind entry j, gives
 //     dC/dc_j = T_j alpha_j,   dC/dalpha_j = T_j c_j - S / (1 - alpha_j).
 //   Gradients w.r.t. the record (u, v, cA, cB, cC, log2 o, r, g, b) are
 //   summed over the warp's pixels and added with one atomic per value.
