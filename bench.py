@@ -275,28 +275,40 @@ def _fwd_bwd(args, device):
     params = {k: torch.from_numpy(np.ascontiguousarray(scene[k])).cuda(device)
               for k in ("means", "log_scales", "quats", "opacity_logits", "sh")}
     out = {}
-    for mode in ("cr", "plain"):
-        # training bins by tiles: the backward walks per-tile lists
-        opts = r.make_options(mode=mode, opacity_filter=(mode == "cr"), binning="tiles")
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
 
-        def step():
-            r.load_scene(dict(params, sh_degree=3), borrow=True)
-            img = r.render(options=opts)
-            g = torch.sign(img - tgt) / img.numel()      # d(mean |img - target|)
-            return r.render_backward(g)
-
+    def timed(step, k):
         for _ in range(3):
             step()
         torch.cuda.synchronize()
-        s = torch.cuda.Event(enable_timing=True)
-        e = torch.cuda.Event(enable_timing=True)
-        k = max(3, min(args.steps, 20))
         s.record()
         for _ in range(k):
             step()
         e.record()
         torch.cuda.synchronize()
-        out[f"{mode}_ms"] = s.elapsed_time(e) / k
+        return s.elapsed_time(e) / k
+
+    for mode in ("cr", "plain"):
+        def make_step(tile):
+            # training bins by tiles: the backward walks per-tile lists
+            opts = r.make_options(mode=mode, opacity_filter=(mode == "cr"), binning="tiles", tile=tile)
+
+            def step():
+                r.load_scene(dict(params, sh_degree=3), borrow=True)
+                img = r.render(options=opts)
+                g = torch.sign(img - tgt) / img.numel()      # d(mean |img - target|)
+                return r.render_backward(g)
+            return opts, step
+
+        # the tile shape is tuned for the whole step (a few timed steps each)
+        tune = {tile: timed(make_step(tile)[1], 5) for tile in ((16, 16), (8, 8), (32, 8))}
+        tile = min(tune, key=tune.get)
+        opts, step = make_step(tile)
+        k = max(3, min(args.steps, 20))
+        out[f"{mode}_ms"] = timed(step, k)
+        out[f"{mode}_tile"] = list(tile)
+        out[f"{mode}_tuning_ms"] = {f"{a}x{b}": round(v, 4) for (a, b), v in tune.items()}
         # the backward alone on the last frame, and the frame's counted work
         img = r.render(options=opts)
         g = torch.sign(img - tgt) / img.numel()
@@ -308,12 +320,13 @@ def _fwd_bwd(args, device):
         e.record()
         torch.cuda.synchronize()
         out[f"{mode}_bwd_ms"] = s.elapsed_time(e) / k
-        r.render(mode=mode, opacity_filter=(mode == "cr"), binning="tiles", count=True)
+        r.render(mode=mode, opacity_filter=(mode == "cr"), binning="tiles", tile=tile, count=True)
         out[f"{mode}_work"] = {kk: r.last_stats[kk] for kk in ("n_visible", "n_instances", "leader_tests",
                                                                 "pairs_evaluated", "pairs_blended")}
     out["workload"] = (f"clusters_1m: {args.fwd_bwd_n} Gaussians in 64 clusters, 1280x720, L1 loss vs a target "
                        f"rendered from attributes + N(0, 0.01); gradients for all attributes; CR path with the "
-                       f"opacity filter, plain path without; tile binning")
+                       f"opacity filter, plain path without; tile binning, tile shape tuned per mode over "
+                       f"16x16, 8x8 and 32x8 by timing the step")
     r.close()
     return out
 
