@@ -191,13 +191,20 @@ def cpu_baseline_views(n_gauss: int, poses: int = 2):
             "sample": f"{poses} of the 512 poses (320x180, top-32 contributors), {n_gauss} Gaussians"}
 
 
+def _workload(n_gauss: int) -> str:
+    if n_gauss == 3_000_000:
+        return WORKLOAD
+    return (f"unbounded, {n_gauss} Gaussians (80% in 64 clusters, 20% on a r 30-50 shell), SH degree 3, "
+            f"1920x1080, 16x16 tiles, 8 orbit cameras at r 5, seed 0")
+
+
 def run_reference(args):
     rank, _, ws, dist = _dist()
     if rank != 0:
         return
     import scenegen
     import oracle
-    scene, cams = scenegen.unbounded_3m()
+    scene, cams = scenegen.unbounded_3m(n=args.n_gauss)
     s64 = oracle.Scene64.from_scene(scene)
     opts = oracle.Options(cr=True, opacity_filter=True)
     nthreads = os.cpu_count()
@@ -218,7 +225,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "path": "CR 2x2 + opacity-aware filter",
+            "data": "synthetic", "config": {"workload": _workload(args.n_gauss), "path": "CR 2x2 + opacity-aware filter",
                                             "step": "one horizontal quarter band of a frame"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle",
                              "sample": f"each step renders one 1920x270 band of a frame; {args.steps} bands"},
@@ -913,9 +920,7 @@ def run_gpu(args):
         "clocks": clock_info,
     }
     # the CPU oracle as it stands, rank 0 at N = 1 only
-    if args.n_gauss != 3_000_000:
-        line["config"]["workload"] = (f"unbounded, {args.n_gauss} Gaussians (80% in 64 clusters, 20% on a r 30-50 "
-                                      f"shell), SH degree 3, 1920x1080, 16x16 tiles, 8 orbit cameras at r 5, seed 0")
+    line["config"]["workload"] = _workload(args.n_gauss)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(scene, cams)
         if args.ablation_n > 0:
