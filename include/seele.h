@@ -94,7 +94,7 @@ typedef struct {
     const float* centroids;       /* host, [n_clusters][6] = (x / s, view dir) */
 } seele_scene_desc;
 
-/* One camera (Sec. 3.1 "Given a camera pose and a view direction"). */
+/* One camera (Sec. 3.1: a render takes a camera pose and viewing direction). */
 typedef struct {
     float world_to_cam[12];       /* [R | t], row-major 3x4 */
     float fx, fy, cx, cy;         /* pinhole intrinsics, pixels */
@@ -296,7 +296,8 @@ seele_status seele_synchronize(seele_ctx* ctx);
 /* Gradient of sum(dL_drgb * rgb) for the last seele_render (same scene,
  * cameras and options; else SEELE_ERR_STATE).  dL_drgb is device memory in
  * the out_rgb layout.  Skip and stop decisions of the forward pass are held
- * fixed (Sec. 3.5: HP and CR "do not participate in gradient descent");
+ * fixed (Sec. 3.5: hybrid preprocessing and the CR skips are left out of
+ * the gradient);
  * per-pixel transmittance is recomputed back to front, not stored. */
 seele_status seele_render_backward(seele_ctx* ctx, const float* dL_drgb, const seele_grads* grads);
 

@@ -22,8 +22,8 @@
  *             projection of Zwicker et al.; 0.3 is the 3DGS low-pass term).
  *   colour    rgb = max(0, sum_lm k_lm Y_lm(d) + 0.5), d = unit(mean - campos),
  *             real spherical harmonics with the Condon-Shortley phase,
- *             coefficient index k = l*l + l + m (Sec. 3.1 "c_i is a function of
- *             the Gaussian spherical harmonics").
+ *             coefficient index k = l*l + l + m (Sec. 3.1: the colour of a
+ *             Gaussian comes from its SH coefficients).
  *   alpha     alpha = min(0.99, o * exp(-q / 2)), q = d^T Sigma'^-1 d (Eqn. 2),
  *             o = sigmoid(logit).
  *   support   a pixel only receives a Gaussian when q <= t_g, with t_g = 9 (the
@@ -44,10 +44,10 @@
  *             the pixel stops without blending; otherwise C += T alpha c,
  *             T = T' (Eqn. 1 and the two rules after Eqn. 2).
  *   CR        Algorithm 1: every w x h pixel group has its top-left pixel as
- *             leader (Sec. 4.1 "we pick the first pixel"); the leader's alpha
- *             decides for the whole group, pixels of a passing group apply the
- *             per-pixel rules above (Sec. 3.4 "performs the same rasterization
- *             computations as the original approach").
+ *             leader (Sec. 4.1 takes the group's first pixel); the leader's
+ *             alpha decides for the whole group, pixels of a passing group
+ *             apply the per-pixel rules above (Sec. 3.4: a passing group is
+ *             rasterized as in the plain method).
  */
 #include <math.h>
 #include <stdint.h>

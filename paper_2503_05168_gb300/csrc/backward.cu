@@ -1,6 +1,7 @@
-// backward.cu -- gradients of the render for fine-tuning (Sec. 3.5: HP and
-// CR "do not participate in gradient descent": every skip and stop decision
-// of the forward pass is replayed and held fixed).
+// backward.cu -- gradients of the render for fine-tuning (Sec. 3.5: the
+// hybrid preprocessing and the contribution-aware skips are left out of the
+// gradient; every skip and stop decision of the forward pass is replayed and
+// held fixed).
 //
 // raster_bwd_kernel: one CTA per 256-entry chunk of a tile's list (one per
 //   tile for lists that short), the same 2x2-pixels-per-thread layout as
