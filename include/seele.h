@@ -67,7 +67,11 @@ enum { SEELE_SCENE_COPY = 0, SEELE_SCENE_BORROW = 1, SEELE_SCENE_SPATIAL = 2 };
  * pointers) into its own layout and owns that copy.  BORROW: the pointers are
  * device memory owned by the caller, must stay valid and unchanged in size
  * until the next seele_load_scene or seele_destroy, and are re-read by every
- * render (their contents may change between renders, as in training).
+ * render (their contents may change between renders, as in training) and by
+ * seele_render_backward, which needs them as the render it differentiates
+ * read them.  When quats and sh are 16-byte aligned the kernels read the
+ * arrays in place; otherwise every render first repacks them into the
+ * library's layout.
  * COPY reads device and page-locked host arrays (cudaMallocHost,
  * cudaHostRegister) in place, the latter over the host link in the same pass
  * that repacks them; other host arrays are first copied to a device staging

@@ -321,6 +321,28 @@ seele_status spatial_order(seele_ctx* c, int64_t n, int planes) {
     return SEELE_OK;
 }
 
+// The scene as the kernels read it: the planes, or a BORROW scene's own
+// arrays in place when quats and sh are 16-byte aligned (else the frame
+// repacks them into the planes first).
+SceneDev scene_dev(seele_ctx* c) {
+    SceneDev sc;
+    sc.pos_logit = ptr<float4>(c->pos_logit);
+    sc.quat = ptr<float4>(c->quat);
+    sc.log_scale = ptr<float4>(c->log_scale);
+    sc.sh = ptr<float4>(c->sh);
+    if (c->scene_flags == SEELE_SCENE_BORROW) {
+        const seele_scene_desc& b = c->borrowed;
+        if (((uintptr_t)b.quats & 15u) == 0 && ((uintptr_t)b.sh & 15u) == 0) {
+            sc.means = b.means;
+            sc.log_scales = b.log_scales;
+            sc.quats = b.quats;
+            sc.logits = b.opacity_logits;
+            sc.shc = b.sh;
+        }
+    }
+    return sc;
+}
+
 // ------------------------------------------------------- shared scene --
 
 DevBuf* scene_bufs(seele_ctx* c, int i) {
@@ -753,7 +775,8 @@ seele_status enqueue_frame(seele_ctx* c, const seele_options* opt, const FrameIn
     SEELE_CUDA(c, cudaMemsetAsync(c->ranges.p, 0xff, 4 * units_total, s));
     SEELE_CUDA(c, cudaMemsetAsync(ptr<uint32_t>(c->ranges) + units_total, 0, 4 * units_total, s));
     SEELE_MARK(SEELE_STAGE_PREPROCESS);
-    if (c->scene_flags == SEELE_SCENE_BORROW) {
+    SceneDev sc = scene_dev(c);
+    if (c->scene_flags == SEELE_SCENE_BORROW && sc.means == nullptr) {
         const seele_scene_desc& b = c->borrowed;
         const int ncoef = (c->sh_degree + 1) * (c->sh_degree + 1);
         launch_repack((int)c->n, ncoef, b.means, b.log_scales, b.quats, b.opacity_logits, b.sh,
@@ -762,11 +785,6 @@ seele_status enqueue_frame(seele_ctx* c, const seele_options* opt, const FrameIn
         SEELE_LAUNCHED(c);
         ++launches;
     }
-    SceneDev sc;
-    sc.pos_logit = ptr<float4>(c->pos_logit);
-    sc.quat = ptr<float4>(c->quat);
-    sc.log_scale = ptr<float4>(c->log_scale);
-    sc.sh = ptr<float4>(c->sh);
     sc.mask = c->has_mask ? (c->scene_flags == SEELE_SCENE_BORROW ? c->borrowed.cluster_mask
                                                                   : ptr<const uint32_t>(c->mask))
                           : nullptr;
@@ -1553,11 +1571,7 @@ seele_status seele_render_backward(seele_ctx* c, const float* dL_drgb, const see
     }
     if (!launch_raster_bwd(a, s)) return fail(c, SEELE_ERR_ARG, "no backward rasterizer for these options");
     SEELE_LAUNCHED(c);
-    SceneDev sc;
-    sc.pos_logit = ptr<float4>(c->pos_logit);
-    sc.quat = ptr<float4>(c->quat);
-    sc.log_scale = ptr<float4>(c->log_scale);
-    sc.sh = ptr<float4>(c->sh);
+    SceneDev sc = scene_dev(c);
     sc.mask = nullptr;
     launch_preprocess_bwd(sc, a.cams, c->last_fp, ptr<uint32_t>(c->tiles), a.grad_rec, g->means, g->log_scales,
                           g->quats, g->opacity_logits, g->sh, c->spatial ? ptr<const uint32_t>(c->order) : nullptr,

@@ -316,9 +316,10 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(SceneDev sc, const 
 #pragma unroll
         for (int i = 0; i < NF; ++i) gsh[i] = 0.f;
     }
-    const float4 pl = __ldg(sc.pos_logit + g);
-    const float4 q4 = __ldg(sc.quat + g);
-    const float4 ls = __ldg(sc.log_scale + g);
+    const bool aos = sc.means != nullptr;  // a BORROW scene read in place
+    const float4 pl = aos ? scene_pos_logit<true>(sc, g) : scene_pos_logit<false>(sc, g);
+    const float4 q4 = aos ? scene_quat<true>(sc, g) : scene_quat<false>(sc, g);
+    const float4 ls = aos ? scene_log_scale<true>(sc, g) : scene_log_scale<false>(sc, g);
 
     for (int ci = 0; ci < (ONE ? 1 : fp.n_cams); ++ci) {
         const size_t rid = (size_t)ci * fp.n + g;
@@ -452,7 +453,8 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(SceneDev sc, const 
         float raw[3] = {0.5f, 0.5f, 0.5f};
 #pragma unroll
         for (int jp = 0; jp < NPL; ++jp) {
-            const float4 vv = __ldg(sc.sh + (size_t)jp * fp.n + g);
+            const float4 vv = aos ? scene_sh4<true, NC>(sc, fp.n, g, jp)
+                                  : scene_sh4<false, NC>(sc, fp.n, g, jp);
             const float e4[4] = {vv.x, vv.y, vv.z, vv.w};
 #pragma unroll
             for (int i = 0; i < 4; ++i)
@@ -465,7 +467,8 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(SceneDev sc, const 
         for (int k = 0; k < NC; ++k) w[k] = 0.f;
 #pragma unroll
         for (int jp = 0; jp < NPL; ++jp) {
-            const float4 vv = __ldg(sc.sh + (size_t)jp * fp.n + g);
+            const float4 vv = aos ? scene_sh4<true, NC>(sc, fp.n, g, jp)
+                                  : scene_sh4<false, NC>(sc, fp.n, g, jp);
             const float e4[4] = {vv.x, vv.y, vv.z, vv.w};
 #pragma unroll
             for (int i = 0; i < 4; ++i)

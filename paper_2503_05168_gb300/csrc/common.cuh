@@ -97,13 +97,65 @@ struct FrameParams {
 
 // Scene in the library's layout (structure of arrays, 16-byte aligned).
 struct SceneDev {
-    const float4* pos_logit;   // (x, y, z, opacity logit)
-    const float4* quat;        // (w, x, y, z)
-    const float4* log_scale;   // (lx, ly, lz, 0)
-    const float4* sh;          // plane-major: sh[j * n + g], j < ceil(3 nc / 4)
-    const uint32_t* mask;      // [n] or nullptr
-    const uint32_t* veto;      // streamed scene: [n] clusters that take precedence, or nullptr
+    const float4* pos_logit = nullptr;   // (x, y, z, opacity logit)
+    const float4* quat = nullptr;        // (w, x, y, z)
+    const float4* log_scale = nullptr;   // (lx, ly, lz, 0)
+    const float4* sh = nullptr;          // plane-major: sh[j * n + g], j < ceil(3 nc / 4)
+    const uint32_t* mask = nullptr;      // [n] or nullptr
+    const uint32_t* veto = nullptr;      // streamed scene: [n] clusters that take precedence, or nullptr
+    // a BORROW scene read in place (else nullptr): the caller's arrays in the
+    // layout of seele_scene_desc, quats and sh 16-byte aligned
+    const float* means = nullptr;        // [n][3]
+    const float* log_scales = nullptr;   // [n][3]
+    const float* quats = nullptr;        // [n][4]
+    const float* logits = nullptr;       // [n]
+    const float* shc = nullptr;          // [n][nc][3]
 };
+
+// One Gaussian's attributes from the planes, or (AOS) from the caller's arrays.
+template <bool AOS>
+__device__ __forceinline__ float4 scene_pos_logit(const SceneDev& sc, int g) {
+    if constexpr (AOS)
+        return make_float4(__ldg(sc.means + 3 * (size_t)g), __ldg(sc.means + 3 * (size_t)g + 1),
+                           __ldg(sc.means + 3 * (size_t)g + 2), __ldg(sc.logits + g));
+    else
+        return __ldg(sc.pos_logit + g);
+}
+
+template <bool AOS>
+__device__ __forceinline__ float4 scene_quat(const SceneDev& sc, int g) {
+    if constexpr (AOS)
+        return __ldg(reinterpret_cast<const float4*>(sc.quats) + g);
+    else
+        return __ldg(sc.quat + g);
+}
+
+template <bool AOS>
+__device__ __forceinline__ float4 scene_log_scale(const SceneDev& sc, int g) {
+    if constexpr (AOS)
+        return make_float4(__ldg(sc.log_scales + 3 * (size_t)g), __ldg(sc.log_scales + 3 * (size_t)g + 1),
+                           __ldg(sc.log_scales + 3 * (size_t)g + 2), 0.f);
+    else
+        return __ldg(sc.log_scale + g);
+}
+
+// SH coefficients 4j .. 4j + 3 of Gaussian g (zero past 3 nc), the j-th plane
+template <bool AOS, int NC>
+__device__ __forceinline__ float4 scene_sh4(const SceneDev& sc, int n, int g, int j) {
+    if constexpr (AOS) {
+        const float* row = sc.shc + (size_t)g * (3 * NC);
+        if constexpr ((3 * NC) % 4 == 0) {
+            return __ldg(reinterpret_cast<const float4*>(row) + j);  // 16-byte rows
+        } else {
+            float v[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) v[i] = 4 * j + i < 3 * NC ? __ldg(row + 4 * j + i) : 0.f;
+            return make_float4(v[0], v[1], v[2], v[3]);
+        }
+    } else {
+        return __ldg(sc.sh + (size_t)j * n + g);
+    }
+}
 
 // Raster record: kRecF4 float4 per record, one 64-byte line:
 //   (u, v, cA, cB), (cC, log2 o, e_thr, T_tile), (r, g, b, 0),

@@ -62,13 +62,13 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, float* Y) {
     }
 }
 
-template <int DEG>
-__device__ __forceinline__ void load_sh(const float4* __restrict__ sh, int n, int g, float* f) {
+template <int DEG, bool AOS>
+__device__ __forceinline__ void load_sh(const SceneDev& sc, int n, int g, float* f) {
     constexpr int NC = (DEG + 1) * (DEG + 1);
     constexpr int NP = (3 * NC + 3) / 4;
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
-        float4 v = __ldg(sh + (size_t)j * n + g);
+        const float4 v = scene_sh4<AOS, NC>(sc, n, g, j);
         f[4 * j + 0] = v.x;
         f[4 * j + 1] = v.y;
         f[4 * j + 2] = v.z;
@@ -85,7 +85,7 @@ __device__ __forceinline__ float det2_sym(float a, float b, float c) {
     return f + e;
 }
 
-template <int DEG>
+template <int DEG, bool AOS>
 __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev sc, const CamDev* __restrict__ cams,
                                                          FrameParams fp, ProjOut out) {
     // cameras vary fastest over the grid, so the blocks that read one slice
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev sc, const CamD
             if ((__ldg(sc.mask + g) & C.sel_bits) == 0u) break;
             if (sc.veto != nullptr && (__ldg(sc.veto + g) & C.sel_bits) != 0u) break;
         }
-        const float4 pl = __ldg(sc.pos_logit + g);
+        const float4 pl = scene_pos_logit<AOS>(sc, g);
         const float X = fmaf(C.R[0], pl.x, fmaf(C.R[1], pl.y, fmaf(C.R[2], pl.z, C.t[0])));
         const float Y = fmaf(C.R[3], pl.x, fmaf(C.R[4], pl.y, fmaf(C.R[5], pl.z, C.t[1])));
         const float Z = fmaf(C.R[6], pl.x, fmaf(C.R[7], pl.y, fmaf(C.R[8], pl.z, C.t[2])));
@@ -129,10 +129,10 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev sc, const CamD
         }
 
         // Sigma' = J W R S (J W R S)^T + dilation: build N = J W R S (2x3)
-        const float4 q4 = __ldg(sc.quat + g);
+        const float4 q4 = scene_quat<AOS>(sc, g);
         const float qinv = rsqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
         const float qw = q4.x * qinv, qx = q4.y * qinv, qy = q4.z * qinv, qz = q4.w * qinv;
-        const float4 ls = __ldg(sc.log_scale + g);
+        const float4 ls = scene_log_scale<AOS>(sc, g);
         const float s0 = __expf(ls.x), s1 = __expf(ls.y), s2 = __expf(ls.z);
         float M[9];  // R(q) diag(s)
         M[0] = (1.f - 2.f * (qy * qy + qz * qz)) * s0;
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev sc, const CamD
         float Yb[NC];
         sh_basis<DEG>(dxw, dyw, dzw, Yb);
         float shf[((3 * NC + 3) / 4) * 4];
-        load_sh<DEG>(sc.sh, fp.n, g, shf);
+        load_sh<DEG, AOS>(sc, fp.n, g, shf);
         float rgb[3];
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
@@ -313,11 +313,24 @@ __global__ void __launch_bounds__(256) repack_kernel(int n, const float* __restr
 void launch_preprocess(const SceneDev& sc, const CamDev* cams, const FrameParams& fp, const ProjOut& out,
                        cudaStream_t s) {
     dim3 grid(fp.n_cams, (fp.n + 255) / 256);
+    const bool aos = sc.means != nullptr;
     switch (fp.sh_degree) {
-        case 0: preprocess_kernel<0><<<grid, 256, 0, s>>>(sc, cams, fp, out); break;
-        case 1: preprocess_kernel<1><<<grid, 256, 0, s>>>(sc, cams, fp, out); break;
-        case 2: preprocess_kernel<2><<<grid, 256, 0, s>>>(sc, cams, fp, out); break;
-        default: preprocess_kernel<3><<<grid, 256, 0, s>>>(sc, cams, fp, out); break;
+        case 0:
+            if (aos) preprocess_kernel<0, true><<<grid, 256, 0, s>>>(sc, cams, fp, out);
+            else preprocess_kernel<0, false><<<grid, 256, 0, s>>>(sc, cams, fp, out);
+            break;
+        case 1:
+            if (aos) preprocess_kernel<1, true><<<grid, 256, 0, s>>>(sc, cams, fp, out);
+            else preprocess_kernel<1, false><<<grid, 256, 0, s>>>(sc, cams, fp, out);
+            break;
+        case 2:
+            if (aos) preprocess_kernel<2, true><<<grid, 256, 0, s>>>(sc, cams, fp, out);
+            else preprocess_kernel<2, false><<<grid, 256, 0, s>>>(sc, cams, fp, out);
+            break;
+        default:
+            if (aos) preprocess_kernel<3, true><<<grid, 256, 0, s>>>(sc, cams, fp, out);
+            else preprocess_kernel<3, false><<<grid, 256, 0, s>>>(sc, cams, fp, out);
+            break;
     }
 }
 

@@ -34,6 +34,8 @@ def _source(sc, kind):
     import torch
     if kind == "numpy":
         return sc
+    if kind == "borrow":   # device arrays read in place
+        return _source(sc, "device")
     out = {}
     for k, v in sc.items():
         if k in ("means", "log_scales", "quats", "opacity_logits", "sh", "cluster_mask"):
@@ -44,12 +46,12 @@ def _source(sc, kind):
     return out
 
 
-@pytest.mark.parametrize("kind", ["numpy", "pinned", "device"])
+@pytest.mark.parametrize("kind", ["numpy", "pinned", "device", "borrow"])
 @pytest.mark.parametrize("deg", [0, 1, 2, 3])
 def test_records_match_oracle_at_every_sh_degree(Renderer, deg, kind):
     sc, cams = _scene(deg)
     r = Renderer()
-    r.load_scene(_source(sc, kind))
+    r.load_scene(_source(sc, kind), borrow=(kind == "borrow"))
     r.set_cameras(cams)
     parity.gpu_render(r)
     d = parity.debug_numpy(r)
@@ -124,3 +126,39 @@ def test_async_and_graph_renders_into_page_locked_host(Renderer):
     r.render(out=pageable, mode="cr", opacity_filter=True)   # synchronous: fine
     assert np.array_equal(pageable.view(np.uint32), refs[-1][0].numpy().view(np.uint32))
     r.close()
+
+
+@pytest.mark.parametrize("deg", [1, 3])
+def test_borrowed_arrays_in_place_or_repacked(Renderer, deg):
+    """A BORROW scene is read in place when its quaternion and SH arrays are
+    16-byte aligned and repacked first when they are not: the same bits as
+    the copied scene either way, forward and backward."""
+    import torch
+    sc, cams = _scene(deg, n=5001)
+    ref = Renderer()
+    ref.load_scene(sc)
+    ref.set_cameras(cams)
+    img_ref, _ = parity.gpu_render(ref, mode="cr")
+    w = torch.from_numpy(np.random.default_rng(5).standard_normal(3 * 256 * 256).astype(np.float32)).cuda()
+    g_ref = {k: v.cpu().numpy() for k, v in ref.render_backward(w).items()}
+    dev = _source(sc, "device")
+    # the same arrays one float into a larger buffer: 4-byte aligned only
+    shifted = dict(dev)
+    for k in ("quats", "sh"):
+        buf = torch.zeros(dev[k].numel() + 1, device="cuda")
+        buf[1:] = dev[k].reshape(-1)
+        shifted[k] = buf[1:].view(dev[k].shape)
+        assert shifted[k].data_ptr() % 16 == 4
+    for arrays in (dev, shifted):
+        r = Renderer()
+        r.load_scene(arrays, borrow=True)
+        r.set_cameras(cams)
+        img, _ = parity.gpu_render(r, mode="cr")
+        for x, y in zip(img, img_ref):
+            assert np.array_equal(x.view(np.uint32), y.view(np.uint32))
+        g = {k: v.cpu().numpy() for k, v in r.render_backward(w).items()}
+        for k in g_ref:
+            # float atomics add the per-pixel terms in any order
+            assert np.max(np.abs(g[k] - g_ref[k])) <= 1e-5 * (np.abs(g_ref[k]).max() + 1e-30), k
+        r.close()
+    ref.close()
