@@ -16,6 +16,9 @@ What each entry point follows in the paper:
                        order.
 * ``render_tiled``     Sec. 3.1 "Rasterization", Eqns. 1-2 and the alpha_theta
                        / Gamma_theta rules; with ``cr`` Algorithm 1 (Sec. 3.4).
+* ``pixel_outcomes``   the outcomes of a pixel of ``render_tiled`` when any
+                       decision near its threshold goes the other way (the
+                       decision-aware comparison with an FP32 render).
 * ``render_bruteforce`` the same rules without tiles: every pixel walks every
                        visible Gaussian in global depth order.
 * ``backward_*``       the chain rule through the above (Sec. 3.5 fine-tuning;
@@ -90,6 +93,8 @@ def _L():
         lib.oc_build_instances.restype = None
         lib.oc_render_tiled.argtypes = [P, P, P, I32, I32, P, P, P, P, P, P, I32]
         lib.oc_render_tiled.restype = None
+        lib.oc_pixel_outcomes.argtypes = [P, P, P, I32, I32, P, P, I64, ctypes.c_double, I32, P, P, I32]
+        lib.oc_pixel_outcomes.restype = None
         lib.oc_render_bruteforce.argtypes = [I64, P, I32, I32, P, P, P, P, I32]
         lib.oc_render_bruteforce.restype = None
         lib.oc_backward_raster.argtypes = [I64, P, P, P, I32, I32, P, P, P]
@@ -257,6 +262,27 @@ def render_tiled(proj, gid, ranges, cam, opts: Options, nthreads: int = 1) -> Re
     counters["visible"] = int(proj["visible"].sum())
     counters["instances"] = int(gid.size)
     return Render(rgb, T, nc, margin, counters)
+
+
+def pixel_outcomes(proj, gid, ranges, cam, opts: Options, pixels, tol: float = 1e-3, max_out: int = 256,
+                   nthreads: int = 1):
+    """Every outcome (r, g, b, T) a pixel of the tiled render can reach when
+    any decision taken within ``tol`` (relative) of its threshold goes the
+    other way (see oc_pixel_outcomes).  ``pixels``: flat indices y * W + x.
+    Returns (outcomes [npix, max_out, 4], counts [npix]); outcome 0 is the
+    ordinary render's pixel, a count of -1 means more than ``max_out``."""
+    W, H = int(cam["width"]), int(cam["height"])
+    pix = np.ascontiguousarray(pixels, np.int64).reshape(-1)
+    out = np.zeros((pix.size, max_out, 4))
+    n = np.zeros(pix.size, np.int32)
+    if pix.size == 0:
+        return out, n
+    o = opts.to_struct()
+    gid = np.ascontiguousarray(gid, np.int32)
+    ranges = np.ascontiguousarray(ranges, np.int64)
+    _L().oc_pixel_outcomes(_p(proj), _p(gid) if gid.size else None, _p(ranges), W, H, _p(o), _p(pix), pix.size,
+                           float(tol), int(max_out), _p(out), _p(n), nthreads)
+    return out, n
 
 
 def render(scene: Scene64, cam, opts: Options, nthreads: int = 1):

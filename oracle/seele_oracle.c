@@ -647,6 +647,149 @@ void oc_render_tiled(const oc_proj* proj, const int32_t* gid, const int64_t* ran
 }
 
 /* ------------------------------------------------------------------------ */
+/* Outcomes of a pixel under near-threshold decisions                        */
+/* ------------------------------------------------------------------------ */
+
+/* A decision that double precision takes within a relative distance `tol` of
+   its threshold may go the other way in a single-precision render.  For one
+   pixel, every outcome (C, T) reachable by taking either branch of any such
+   decision is enumerated by a depth-first walk of the pixel's tile list: both
+   branches are followed at a near decision, the double-precision branch
+   everywhere else.  The decisions are the pixel rule's (support q <= t_g and
+   alpha >= alpha_theta, taken together as one test; the stop test on
+   T (1 - alpha)) and, under Algorithm 1, the group leader's test.  A leader
+   pixel's own support and alpha test is the leader test on the same sample
+   point and is not branched a second time.  The double-precision branch is
+   always followed first, so outcome 0 is the ordinary render's pixel. */
+
+typedef struct {
+    const oc_proj* proj;
+    const int32_t* gid;
+    int64_t end;
+    const oc_options* opt;
+    double px, py;        /* the pixel's sample point */
+    double lx, ly;        /* its group leader's sample point (Algorithm 1) */
+    int is_leader;
+    double tol;
+    int max_out;
+    int n_out;            /* outcomes written; max_out + 1 once there are more */
+    double* out;          /* [max_out][4]: r, g, b, T */
+} po_walk;
+
+/* The values "q <= t_g and alpha >= alpha_theta" at (x, y) can take when
+   either near component may flip: bit 0 set = false reachable, bit 1 = true
+   reachable.  *base = the double-precision value. */
+static int po_on(const po_walk* w, const oc_proj* P, double x, double y, int* base) {
+    double q = quad_at(P, x, y);
+    double al = alpha_of_q(P, w->opt, q);
+    int s = q <= P->tg, a = al >= w->opt->alpha_min;
+    int s_near = fabs(q - P->tg) / P->tg < w->tol;
+    int a_near = fabs(al - w->opt->alpha_min) / w->opt->alpha_min < w->tol;
+    *base = s && a;
+    int vals = 0;
+    for (int fs = 0; fs <= s_near; ++fs)
+        for (int fa = 0; fa <= a_near; ++fa) vals |= 1 << ((fs ? !s : s) && (fa ? !a : a));
+    return vals;
+}
+
+static void po_leaf(po_walk* w, const double* C, double T) {
+    if (w->n_out >= w->max_out) { w->n_out = w->max_out + 1; return; }
+    double* o = w->out + 4 * (int64_t)w->n_out;
+    o[0] = C[0]; o[1] = C[1]; o[2] = C[2]; o[3] = T;
+    w->n_out++;
+}
+
+/* Continue at list entry i, at stage `stage` of that entry's decisions:
+   0 the leader test (Algorithm 1 only), 1 the pixel's support and alpha
+   test, 2 the stop test and the blend. */
+static void po_walk_from(po_walk* w, int64_t i, int stage, const double* C0, double T) {
+    double C[3] = {C0[0], C0[1], C0[2]};
+    while (i < w->end) {
+        if (w->n_out > w->max_out) return;
+        const oc_proj* P = w->proj + w->gid[i];
+        int base, v;
+        if (stage == 0) {
+            if (w->opt->cr) {
+                v = po_on(w, P, w->lx, w->ly, &base);
+                if (v == 3) {
+                    if (base) { po_walk_from(w, i, 1, C, T); po_walk_from(w, i + 1, 0, C, T); }
+                    else { po_walk_from(w, i + 1, 0, C, T); po_walk_from(w, i, 1, C, T); }
+                    return;
+                }
+                if (!base) { ++i; continue; }     /* the whole group skips entry i */
+            }
+            stage = 1;
+        }
+        if (stage == 1) {
+            if (!(w->opt->cr && w->is_leader)) {
+                v = po_on(w, P, w->px, w->py, &base);
+                if (v == 3) {
+                    if (base) { po_walk_from(w, i, 2, C, T); po_walk_from(w, i + 1, 0, C, T); }
+                    else { po_walk_from(w, i + 1, 0, C, T); po_walk_from(w, i, 2, C, T); }
+                    return;
+                }
+                if (!base) { ++i; stage = 0; continue; }
+            }
+            stage = 2;
+        }
+        double al = alpha_of_q(P, w->opt, quad_at(P, w->px, w->py));
+        double Tn = T * (1.0 - al);
+        int stop = Tn < w->opt->t_stop;
+        double Cn[3];
+        for (int ch = 0; ch < 3; ++ch) Cn[ch] = C[ch] + T * al * P->rgb[ch];
+        if (fabs(Tn - w->opt->t_stop) / w->opt->t_stop < w->tol) {
+            if (stop) { po_leaf(w, C, T); po_walk_from(w, i + 1, 0, Cn, Tn); }
+            else { po_walk_from(w, i + 1, 0, Cn, Tn); po_leaf(w, C, T); }
+            return;
+        }
+        if (stop) { po_leaf(w, C, T); return; }
+        C[0] = Cn[0]; C[1] = Cn[1]; C[2] = Cn[2];
+        T = Tn;
+        ++i;
+        stage = 0;
+    }
+    po_leaf(w, C, T);
+}
+
+/* Outcomes of the pixels pix[k] = y * W + x of a tiled render (the lists and
+   ranges of oc_build_instances): out[k][j][0..3] = (r, g, b, T) of outcome j,
+   n_out[k] = the number of outcomes, or -1 when there are more than max_out. */
+void oc_pixel_outcomes(const oc_proj* proj, const int32_t* gid, const int64_t* ranges, int W, int H,
+                       const oc_options* opt, const int64_t* pix, int64_t npix, double tol, int max_out,
+                       double* out, int32_t* n_out, int nthreads) {
+    int tw = opt->tile_w, th = opt->tile_h;
+    int tiles_x = (W + tw - 1) / tw;
+    int gw = opt->cr ? opt->group_w : 1, gh = opt->cr ? opt->group_h : 1;
+    (void)H;
+#ifdef _OPENMP
+    #pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+    for (int64_t k = 0; k < npix; ++k) {
+        int x = (int)(pix[k] % W), y = (int)(pix[k] / W);
+        int tx = x / tw, ty = y / th;
+        int64_t t = (int64_t)ty * tiles_x + tx;
+        int x0 = tx * tw, y0 = ty * th;
+        int gx = x0 + (x - x0) / gw * gw, gy = y0 + (y - y0) / gh * gh;
+        po_walk w;
+        w.proj = proj;
+        w.gid = gid;
+        w.end = ranges[2 * t + 1];
+        w.opt = opt;
+        w.px = x + 0.5; w.py = y + 0.5;
+        w.lx = gx + 0.5; w.ly = gy + 0.5;
+        w.is_leader = gx == x && gy == y;
+        w.tol = tol;
+        w.max_out = max_out;
+        w.n_out = 0;
+        w.out = out + (int64_t)4 * max_out * k;
+        double C0[3] = {0.0, 0.0, 0.0};
+        if (ranges[2 * t] < ranges[2 * t + 1]) po_walk_from(&w, ranges[2 * t], 0, C0, 1.0);
+        else po_leaf(&w, C0, 1.0);
+        n_out[k] = w.n_out > max_out ? -1 : w.n_out;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Brute-force render: no tiles, no rects.  Every pixel walks every visible  */
 /* Gaussian in global (fp32 depth, index) order under the same rules.        */
 /* ------------------------------------------------------------------------ */
