@@ -38,10 +38,6 @@ METRIC = "1080p frames/s at 3M Gaussians vs plain path; fwd+bwd ms; % of rooflin
 UNIT = "frames/s"
 WORKLOAD = ("unbounded_3m: 3M Gaussians (2.4M in 64 clusters sigma 0.15 in [-3,3]^3 + 0.6M on a r 30-50 shell), "
             "SH degree 3, 1920x1080, 16x16 tiles, 8 orbit cameras at r 5, seed 0")
-FP32_LANES_PER_SM = 128
-N_SM = 152
-
-
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -585,6 +581,10 @@ def run_gpu(args):
         if rank == 0:
             print(json.dumps({"fwd_bwd": _fwd_bwd(args, local)}), flush=True)
         return
+    import paper_2503_05168_gb300 as seele
+    # issue rates of the FMA, MUFU and ALU pipes on this device (the
+    # denominators of the blending's roofline), and its SM count
+    pipe_peaks = seele.measure_peaks(local)
     scene, cams = scenegen.unbounded_3m(n=args.n_gauss)
     r = Renderer(local)
     # stored in Morton order of the means (SEELE_SCENE_SPATIAL, computed at load)
@@ -716,6 +716,9 @@ def run_gpu(args):
     r.render(mode="cr", opacity_filter=True, binning="tiles")
     K_tiles = r.last_stats["n_instances"]
 
+    raster_event_ms = stage["raster"]
+    raster_traffic = _traffic("raster_fwd", _source_hash("raster.cu"))
+
     # quality: CR vs plain on the same frame
     img_cr = r.render(mode="cr", opacity_filter=True).cpu().numpy().astype(np.float64)
     img_pl = r.render(mode="plain").cpu().numpy().astype(np.float64)
@@ -727,7 +730,6 @@ def run_gpu(args):
     dom = max(stage, key=stage.get)
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     n_gauss = int(scene["means"].shape[0])
     # algorithmic bytes per stage (block binning, one 1920x1080 camera:
     # 15 x 17 = 255 tile blocks, so the block sort is one 8-bit pass)
@@ -748,20 +750,39 @@ def run_gpu(args):
     stage_roof = {k: {"GB_s": round(v / (stage[k] / 1000.0) / 1e9, 1),
                       "frac": round(v / (stage[k] / 1000.0) / 1e9 / hbm, 3)}
                   for k, v in stage_bytes.items() if stage.get(k, 0) > 0}
-    if dom == "raster":
-        ops = 8 * (work["pairs_evaluated"] + work["leader_tests"]) + 7 * work["pairs_blended"]
-        achieved = ops / (stage[dom] / 1000.0) / 1e12
-        peak = N_SM * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": _traffic("raster_fwd", _source_hash("raster.cu")),
-                "kernel": "raster_fwd_kernel (CR 2x2)",
-                "note": f"FP32-pipe ops = 8 per exponent evaluation (leader tests and pixel pairs) + 7 per blended "
-                        f"pair; peak = {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz"}
-    else:
-        b = stage_bytes.get(dom, 0)
-        achieved = b / (stage[dom] / 1000.0) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "kernel": dom, "note": f"peak of {peak_src} (MEASURED_PEAKS hbm_gbs)"}
+    pipes = pipe_peaks
+    raster_s = raster_event_ms / 1000.0
+    # counted work of the blending: 8 FP32 ops per exponent evaluation
+    # (leader tests and pixel pairs) + 7 per blended pair; one ex2 per pixel
+    # pair; one threshold compare per exponent and one stop compare per pair
+    fp32_ops = 8 * (work["pairs_evaluated"] + work["leader_tests"]) + 7 * work["pairs_blended"]
+    sfu_ops = work["pairs_evaluated"]
+    alu_ops = work["pairs_evaluated"] + work["leader_tests"] + work["pairs_evaluated"]
+    raster_bytes = raster_traffic if raster_traffic else 0
+    floors = {"fp32": fp32_ops / (pipes["fp32_tops"] * 1e12), "sfu": sfu_ops / (pipes["sfu_tops"] * 1e12),
+              "alu": alu_ops / (max(pipes["alu_fmnmx_tops"], pipes["alu_lop3_tops"]) * 1e12),
+              "hbm": raster_bytes / (hbm * 1e9)}
+    binding = max(floors, key=floors.get)
+    sustained = float(peaks.get("clocks_under_load", {}).get("sm_mhz_median", 0.0) or 0.0)
+    clk_max = float(pipes.get("sm_clock_max_mhz") or peaks.get("sm_max_mhz", 2070.0))
+    achieved = fp32_ops / raster_s / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": pipes["fp32_tops"], "unit": "TFLOP/s",
+            "frac": achieved / pipes["fp32_tops"],
+            "traffic": raster_traffic, "kernel": "raster_fwd_kernel (CR 2x2)",
+            "binding_pipe": binding,
+            "frac_of_floor": {k: round(v / raster_s, 4) for k, v in floors.items()},
+            "frac_sustained_clock": (achieved / (pipes["fp32_tops"] * sustained / clk_max)
+                                     if sustained > 0 else None),
+            "launch_ms": raster_event_ms,
+            "note": f"achieved = counted FP32 ops of the blending ({fp32_ops / 1e9:.3f} G: 8 per exponent "
+                    f"evaluation, leader tests and pixel pairs, + 7 per blended pair) / the kernel's mean CUDA-event "
+                    f"time; peak = the FMA rate measured by seele_measure_peaks on this device "
+                    f"({pipes['sm_count']} SMs; of measured); frac_of_floor: each pipe's counted work over its "
+                    f"measured rate (sfu: {sfu_ops / 1e9:.3f} G ex2; alu: {alu_ops / 1e9:.3f} G compares), and the "
+                    f"kernel's DRAM bytes over {hbm:.0f} GB/s; frac_sustained_clock: the FMA peak scaled to the "
+                    f"{sustained:.0f} MHz median SM clock under sustained load"}
+    if dom != "raster":
+        roof["note"] += f"; the stage with most time is {dom}"
 
     # end to end through the public API with host buffers: scene upload from
     # pinned host memory (read in place by the load's repack kernel), render,
@@ -894,38 +915,56 @@ def run_gpu(args):
     ablation = _ablation(args, local) if args.ablation_n > 0 else None
     sensitivity = _sensitivity(args, local) if args.ablation_n > 0 else None
 
+    config = {"workload": _workload(args.n_gauss),
+              "path": "contribution-aware (Alg. 1, 2x2 groups) + opacity-aware filter; ellipse tile test; block "
+                      "binning (8x4-tile blocks with tile masks)",
+              "launch": "one CUDA-graph replay of the whole frame per step (pose updated per step)",
+              "l2": "inputs larger than L2 (720 MB of Gaussian attributes per frame)",
+              "scene_order": "Morton order of the means, computed by the library at load (SEELE_SCENE_SPATIAL)",
+              "parallelism": f"replicas x{ws} (cameras sharded, no collective)"}
+    fb = fwd_bwd
     line = {
         "metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * t_cr_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "path": "contribution-aware (Alg. 1, 2x2 groups) + opacity-aware filter; "
-                                                 "ellipse tile test; block binning (8x4-tile blocks with tile masks)",
-                   "launch": "one CUDA-graph replay of the whole frame per step (pose updated per step); "
-                             "async_fps: the same frames as plain stream launches; two_stream_fps: the same "
-                             "frames alternating between two contexts sharing the scene, each on its own stream "
-                             "(two frames in flight)",
-                   "l2": "inputs larger than L2 (720 MB of Gaussian attributes per frame)",
-                   "scene_order": "Morton order of the means, computed by the library at load "
-                                  "(SEELE_SCENE_SPATIAL); the per-frame upload leg of e2e loads in the generated order",
-                   "parallelism": f"replicas x{ws} (cameras sharded, no collective)"},
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
         "plain_fps": fps_plain, "speedup_vs_plain": fps / fps_plain, "psnr_cr_vs_plain_db": psnr,
+        "fwd_bwd": {"cr_ms": fb["cr_ms"], "plain_ms": fb["plain_ms"], "cr_bwd_ms": fb["cr_bwd_ms"],
+                    "plain_bwd_ms": fb["plain_bwd_ms"], "speedup_vs_plain": fb["plain_ms"] / fb["cr_ms"],
+                    "workload": f"clusters_1m, {args.fwd_bwd_n} Gaussians, 1280x720, L1 loss, all gradients"},
         "stage_ms": {k: round(v, 4) for k, v in stage.items()},
-        "stage_ms_plain": {k: round(v, 4) for k, v in stage_plain.items()},
-        "n_visible": n_vis, "n_block_instances": K, "n_tile_instances": K_tiles, "raster_work": work,
-        "roofline": roof, "stage_roofline_hbm": stage_roof,
-        "e2e": e2e, "fwd_bwd": fwd_bwd, "multiview": multiview, "ablation": ablation, "sensitivity": sensitivity,
-        "contribution_skew": skew,
+        "roofline": roof,
+        "e2e": {k: e2e[k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step")},
+        "e2e_resident_scene_fps": e2e["resident_scene"]["value"],
         "async_fps": fps_async, "batch8_fps": fps_batch8, "two_stream_fps": fps_two_streams,
+        "multiview": ({k: multiview[k] for k in ("views_per_s", "view_ms_p50", "view_ms_p99")}
+                      if multiview else None),
+        "peaks": {k: (round(v, 3) if isinstance(v, float) else v) for k, v in pipe_peaks.items()},
         "gpu_launches": int(kernels_per_frame * args.steps),
         "clocks": clock_info,
     }
+    details = {
+        "stage_ms_plain": {k: round(v, 4) for k, v in stage_plain.items()},
+        "n_visible": n_vis, "n_block_instances": K, "n_tile_instances": K_tiles, "raster_work": work,
+        "stage_roofline_hbm": stage_roof, "e2e": e2e, "fwd_bwd": fwd_bwd, "multiview": multiview,
+        "ablation": ablation, "sensitivity": sensitivity, "contribution_skew": skew,
+        "launch_kinds": {"async_fps": "the same frames as plain stream launches",
+                         "two_stream_fps": "the same frames alternating between two contexts sharing the scene, "
+                                           "each on its own stream (two frames in flight)",
+                         "batch8_fps": "the 8 orbit views as one batched call per step"},
+    }
     # the CPU oracle as it stands, rank 0 at N = 1 only
-    line["config"]["workload"] = _workload(args.n_gauss)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(scene, cams)
         if args.ablation_n > 0:
-            line["cpu_baseline"]["view_representation"] = cpu_baseline_views(args.ablation_n)
+            details["cpu_baseline_view_representation"] = cpu_baseline_views(args.ablation_n)
     if rank == 0:
+        # the long-form results go to stderr (and to --details): the JSON line
+        # on stdout stays short enough to be read whole
+        blob = json.dumps({"details": details})
+        print(blob, file=sys.stderr, flush=True)
+        if args.details:
+            with open(args.details, "w") as fh:
+                fh.write(blob + "\n")
         print(json.dumps(line), flush=True)
     r.close()
     if dist is not None:
@@ -944,6 +983,7 @@ def main():
                     help="time only the forward + backward step (for profiling captures of the backward kernels)")
     ap.add_argument("--multiview-n", type=int, default=2_000_000, help="0 skips the multi-view measurement")
     ap.add_argument("--ablation-n", type=int, default=500_000, help="0 skips the ablation")
+    ap.add_argument("--details", default=None, help="also write the long-form results (JSON) to this file")
     ap.add_argument("--n-gauss", type=int, default=3_000_000,
                     help="scene size (3M is the benchmark; smaller sizes are for profiling captures)")
     args = ap.parse_args()

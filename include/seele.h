@@ -324,7 +324,9 @@ typedef struct {
                                      -A/2*log2e, -B*log2e, -C/2*log2e (conic
                                      [[A,B],[B,C]] = Sigma'^-1), log2 o, e_thr,
                                      the tile test's bound on -(cA dx^2 + cB dx dy
-                                     + cC dy^2), r, g, b, 0, then the tile box as
+                                     + cC dy^2), r, g, b, clamp flag (1 when
+                                     log2 o is within 1e-4 of log2 of the alpha
+                                     clamp, else 0), then the tile box as
                                      two uint32 x0 | y0 << 16, x1 | y1 << 16, 0, 0;
                                      a pixel at offset (dx, dy) takes the Gaussian
                                      iff e = cA dx^2 + cB dx dy + cC dy^2 + log2 o
@@ -406,6 +408,46 @@ seele_status seele_build_view_clusters(seele_ctx* ctx, const seele_camera* poses
 /* Message of the last failed call on this context (library-owned). */
 const char* seele_last_error(const seele_ctx* ctx);
 
+/* Measured issue rates of the pipes the blending runs on (Sec. 3.1 Eqns.
+ * 1-2, Alg. 1), the denominators of its roofline: every SM of `device` is
+ * filled with independent chains of one instruction kind and each rate is
+ * lane-operations per second from CUDA-event times (best of 3, after a
+ * warm-up), at whatever SM clock the device runs.  Takes a few milliseconds
+ * per kernel on `cuda_stream`; allocates 256 bytes; synchronous.
+ *   fp32: fused multiply-add (one op per FMA), sfu: ex2.approx, alu: float
+ *   min/max and three-input integer logic. */
+typedef struct {
+    int32_t sm_count;             /* cudaDevAttrMultiProcessorCount */
+    int32_t sm_clock_max_mhz;     /* cudaDevAttrClockRate / 1000 */
+    double fp32_tops;             /* 1e12 lane-ops/s */
+    double sfu_tops;
+    double alu_fmnmx_tops;
+    double alu_lop3_tops;
+    float fp32_ms, sfu_ms, alu_fmnmx_ms, alu_lop3_ms;  /* timed launch of each */
+} seele_peaks;
+
+seele_status seele_measure_peaks(int device, void* cuda_stream, seele_peaks* out);
+
+/* Exclusive prefix sum out[i] = in[0] + ... + in[i-1] (mod 2^32) by the
+ * single-pass decoupled look-back scan that seele_sort_tile_instances_noalloc
+ * runs, on caller memory, with a test hook for its bounded wait.  The paper
+ * has no counterpart (a service of the library).
+ *   in, out         device, [n]; in 16-byte aligned
+ *   scratch         device, seele_scan_scratch_bytes(n) bytes, 256-byte
+ *                   aligned, any contents (cleared by the call)
+ *   withhold_block  test hook: the scan block that takes this ticket (blocks
+ *                   of 4096 elements, in launch order) publishes nothing, so
+ *                   its successor's wait runs out; UINT32_MAX for none
+ *   spin_limit      polls of a predecessor before a waiting block gives up,
+ *                   records a timeout and goes on as if that predecessor's
+ *                   prefix were zero (0: the library's limit, about a second)
+ * Returns after the stream has finished: SEELE_OK, SEELE_ERR_TIMEOUT when a
+ * wait gave up (out is then wrong from that block on), SEELE_ERR_ARG for NULL
+ * or misaligned pointers. */
+size_t seele_scan_scratch_bytes(uint32_t n);
+seele_status seele_exclusive_scan(const uint32_t* in, uint32_t n, uint32_t* out, void* scratch,
+                                  uint32_t withhold_block, uint32_t spin_limit, void* cuda_stream);
+
 /* Sorting tile instances without allocating.  The paper has no counterpart:
  * this is a service of the library, not a step of the method.
  *
@@ -419,7 +461,8 @@ const char* seele_last_error(const seele_ctx* ctx);
  *
  *   inst_tile[i], inst_record[i]  device, [n_instances]: tile id (< n_tiles)
  *                                 and payload of instance i, in the order the
- *                                 lists must keep (stable)
+ *                                 lists must keep (stable); inst_tile must be
+ *                                 16-byte aligned (it is read as vectors)
  *   sorted_record                 device, [n_instances]: payloads grouped by
  *                                 tile, in input order within a tile
  *   tile_start, tile_end          device, [n_tiles]: tile t's list is
@@ -427,10 +470,12 @@ const char* seele_last_error(const seele_ctx* ctx);
  *                                 an empty tile has tile_start >= tile_end
  *   cuda_stream                   the stream to run on (NULL: legacy default)
  * Limits: n_instances <= SEELE_NOALLOC_MAX_INSTANCES, 1 <= n_tiles <=
- * SEELE_NOALLOC_MAX_TILES; larger sizes return SEELE_ERR_ARG before any GPU
- * work.  The call runs on the current CUDA device and returns after the
- * stream has finished the sort (SEELE_ERR_TIMEOUT if a bounded device wait
- * gave up).  The first call on a device also looks up the array's device
+ * SEELE_NOALLOC_MAX_TILES; larger sizes, a NULL or misaligned pointer return
+ * SEELE_ERR_ARG before any GPU work.  A tile id >= n_tiles is found on the
+ * device: nothing is sorted, every list is left empty and the call returns
+ * SEELE_ERR_ARG.  The call runs on the current CUDA device and returns after
+ * the stream has finished the sort (SEELE_ERR_TIMEOUT if a bounded device
+ * wait gave up, SEELE_ERR_INTERNAL for any other device error).  The first call on a device also looks up the array's device
  * address; make that first call before any stream capture.  Every call
  * shares the one array and it keeps the last call's contents: calls that
  * overlap on the GPU (other streams or threads) race on it. */

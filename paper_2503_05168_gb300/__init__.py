@@ -19,7 +19,8 @@ import numpy as np
 from . import _abi
 from ._abi import SeeleError, lib
 
-__all__ = ["Renderer", "SeeleError", "SeeleRender", "render", "lib", "default_options", "build"]
+__all__ = ["Renderer", "SeeleError", "SeeleRender", "render", "lib", "default_options", "build", "measure_peaks",
+           "exclusive_scan"]
 
 
 def build(force: bool = False) -> str:
@@ -413,3 +414,32 @@ def render(renderer: "Renderer", means, log_scales, quats, opacity_logits, sh, s
     options.setdefault("binning", "tiles")
     o = renderer.make_options(**options)
     return fn.apply(renderer, o, sh_degree, means, log_scales, quats, opacity_logits, sh)
+
+
+def measure_peaks(device: int = 0) -> dict:
+    """seele_measure_peaks: measured FP32 (FMA), SFU (ex2) and ALU (float
+    min/max, integer logic) lane-op rates of ``device`` in 1e12 per second,
+    its SM count and maximum SM clock (MHz), on the current stream."""
+    import torch
+    s = torch.cuda.current_stream(torch.device("cuda", device)).cuda_stream
+    p = _abi.Peaks()
+    st = lib().seele_measure_peaks(device, ctypes.c_void_p(s), ctypes.byref(p))
+    if st != 0:
+        raise SeeleError(st, "seele_measure_peaks failed")
+    return {f: getattr(p, f) for f, _ in _abi.Peaks._fields_}
+
+
+def exclusive_scan(x, withhold_block: int | None = None, spin_limit: int = 0):
+    """seele_exclusive_scan of a 1-D int32/uint32 CUDA tensor (16-byte
+    aligned); returns (status, out).  ``withhold_block`` and ``spin_limit`` are
+    the call's test hook for the bounded look-back wait."""
+    import torch
+    n = int(x.numel())
+    out = torch.empty_like(x)
+    scratch = torch.empty(int(lib().seele_scan_scratch_bytes(n)) + 256, dtype=torch.uint8, device=x.device)
+    base = (scratch.data_ptr() + 255) // 256 * 256
+    s = torch.cuda.current_stream(x.device).cuda_stream
+    st = lib().seele_exclusive_scan(ctypes.c_void_p(x.data_ptr()), n, ctypes.c_void_p(out.data_ptr()),
+                                    ctypes.c_void_p(base), 0xFFFFFFFF if withhold_block is None else withhold_block,
+                                    spin_limit, ctypes.c_void_p(s))
+    return st, out

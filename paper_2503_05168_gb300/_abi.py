@@ -60,6 +60,13 @@ class StreamStats(ctypes.Structure):
                                               "prefetch_hits", "resident_hits")]
 
 
+class Peaks(ctypes.Structure):
+    _fields_ = [("sm_count", ctypes.c_int32), ("sm_clock_max_mhz", ctypes.c_int32), ("fp32_tops", ctypes.c_double),
+                ("sfu_tops", ctypes.c_double), ("alu_fmnmx_tops", ctypes.c_double),
+                ("alu_lop3_tops", ctypes.c_double), ("fp32_ms", ctypes.c_float), ("sfu_ms", ctypes.c_float),
+                ("alu_fmnmx_ms", ctypes.c_float), ("alu_lop3_ms", ctypes.c_float)]
+
+
 class Grads(ctypes.Structure):
     _fields_ = [("means", P), ("log_scales", P), ("quats", P), ("opacity_logits", P), ("sh", P)]
 
@@ -94,6 +101,9 @@ PROTOTYPES = {
                                                  ctypes.c_int32]),
     "seele_get_stream_stats": (ctypes.c_int, [P, ctypes.POINTER(StreamStats)]),
     "seele_share_scene": (ctypes.c_int, [P, P]),
+    "seele_measure_peaks": (ctypes.c_int, [ctypes.c_int, P, ctypes.POINTER(Peaks)]),
+    "seele_scan_scratch_bytes": (ctypes.c_size_t, [ctypes.c_uint32]),
+    "seele_exclusive_scan": (ctypes.c_int, [P, ctypes.c_uint32, P, P, ctypes.c_uint32, ctypes.c_uint32, P]),
 }
 NOALLOC_MAX_INSTANCES = 1 << 20
 NOALLOC_MAX_TILES = 1 << 16

@@ -20,7 +20,7 @@ namespace seele {
 constexpr float kLog2e = 1.4426950408889634f;
 
 // Device status word: the first error a kernel meets is kept.
-enum : int32_t { kOk = 0, kErrCapacity = 4, kErrTimeout = 5, kErrInternal = 7 };
+enum : int32_t { kOk = 0, kErrArg = 1, kErrCapacity = 4, kErrTimeout = 5, kErrInternal = 7 };
 
 struct DeviceStatus {
     int32_t error;
@@ -158,7 +158,7 @@ __device__ __forceinline__ float4 scene_sh4(const SceneDev& sc, int n, int g, in
 }
 
 // Raster record: kRecF4 float4 per record, one 64-byte line:
-//   (u, v, cA, cB), (cC, log2 o, e_thr, T_tile), (r, g, b, 0),
+//   (u, v, cA, cB), (cC, log2 o, e_thr, T_tile), (r, g, b, clamp flag),
 //   (tile box x0 | y0 << 16, x1 | y1 << 16, 0, 0) as integer bits.
 constexpr int kRecF4 = 4;
 

@@ -31,8 +31,15 @@ void launch_scan_tiles(const uint32_t* cnt_sorted, uint32_t* chunk_sum, uint32_t
 // totals (no look-back).
 void launch_digit_scan(const uint32_t* in, uint32_t stride, const uint32_t* row_total, uint32_t* out,
                        cudaStream_t s);
+// Single-pass scan with decoupled look-back (in 16-byte aligned).  status:
+// one word per block (exclusive_scan_blocks), entries of other epochs read as
+// unpublished; st->ticket[ticket] must be zero.  spin_limit: polls of a
+// predecessor before giving up (0: kSpinLimit); withhold: a test hook, the
+// block with this ticket publishes nothing (UINT32_MAX: none).
 void launch_exclusive_scan(const uint32_t* in, uint32_t n, uint32_t* out, uint64_t* status, uint32_t epoch,
-                           DeviceStatus* st, int ticket, cudaStream_t s);
+                           DeviceStatus* st, int ticket, cudaStream_t s, uint32_t spin_limit = 0,
+                           uint32_t withhold = 0xffffffffu);
+uint32_t exclusive_scan_blocks(uint32_t n);
 
 // Spatial order of a scene (order.cu): Morton order of the means, stable;
 // returns the ping-pong index holding the order in vals (0), or -1.

@@ -50,6 +50,21 @@ __global__ void noalloc_prepare_kernel(uint32_t n) {
     if (threadIdx.x == 0) *reinterpret_cast<uint32_t*>(g_scratch + kOffCount) = n;
 }
 
+// Tile ids must be below n_tiles: the sort ranks only the bits such ids have
+// and indexes the range arrays with them.  An id outside that range zeroes the
+// element count the sort kernels read (so they touch nothing) and records an
+// argument error.
+__global__ void noalloc_check_kernel(const uint32_t* __restrict__ tile, uint32_t n, uint32_t n_tiles) {
+    uint32_t bad = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        bad |= __ldg(tile + i) >= n_tiles ? 1u : 0u;
+    if (__syncthreads_or(bad) && threadIdx.x == 0) {
+        DeviceStatus* st = reinterpret_cast<DeviceStatus*>(g_scratch + kOffStatus);
+        atomicCAS(&st->error, kOk, kErrArg);
+        atomicExch(reinterpret_cast<uint32_t*>(g_scratch + kOffCount), 0u);
+    }
+}
+
 // Host code must not take &g_scratch (that is a host-side stand-in): the
 // device address comes from cudaGetSymbolAddress, once per device, with that
 // device current.
@@ -92,6 +107,8 @@ extern "C" seele_status seele_sort_tile_instances_noalloc(const uint32_t* inst_t
     if (n_instances > SEELE_NOALLOC_MAX_INSTANCES) return SEELE_ERR_ARG;
     if (!tile_start || !tile_end) return SEELE_ERR_ARG;
     if (n_instances > 0 && (!inst_tile || !inst_record || !sorted_record)) return SEELE_ERR_ARG;
+    // the first pass reads the tile ids as 16-byte vectors
+    if (reinterpret_cast<uintptr_t>(inst_tile) & 15u) return SEELE_ERR_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         (void)cudaGetLastError();
@@ -111,6 +128,10 @@ extern "C" seele_status seele_sort_tile_instances_noalloc(const uint32_t* inst_t
     uint64_t* lookback = reinterpret_cast<uint64_t*>(base + kOffLookback);
 
     noalloc_prepare_kernel<<<1, 64, 0, s>>>(n_instances);
+    if (n_instances > 0) {
+        const uint32_t blocks = (n_instances + 255) / 256 < 1216 ? (n_instances + 255) / 256 : 1216;
+        noalloc_check_kernel<<<blocks, 256, 0, s>>>(inst_tile, n_instances, n_tiles);
+    }
     if (cudaMemsetAsync(tile_start, 0xff, 4ull * n_tiles, s) != cudaSuccess ||
         cudaMemsetAsync(tile_end, 0, 4ull * n_tiles, s) != cudaSuccess) {
         (void)cudaGetLastError();
@@ -141,5 +162,8 @@ extern "C" seele_status seele_sort_tile_instances_noalloc(const uint32_t* inst_t
         (void)cudaGetLastError();
         return SEELE_ERR_CUDA;
     }
-    return err == kErrTimeout ? SEELE_ERR_TIMEOUT : SEELE_OK;
+    if (err == kOk) return SEELE_OK;
+    if (err == kErrTimeout) return SEELE_ERR_TIMEOUT;
+    if (err == kErrArg) return SEELE_ERR_ARG;
+    return SEELE_ERR_INTERNAL;
 }

@@ -32,12 +32,17 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 static_assert(kScanTile == kChunkItems, "scan tiles are the counting chunks");
 
 // Exclusive prefix of `aggregate` over the preceding tiles (all threads call).
+// A predecessor is polled at most spin_limit times; then the wait records a
+// timeout and takes that predecessor as an inclusive zero.  publish = false
+// (a test hook) makes this tile keep its sums to itself, so that its
+// successor's wait runs out.
 __device__ uint32_t lookback_prefix(uint64_t* status, uint32_t tile, uint32_t aggregate, uint32_t epoch,
-                                    DeviceStatus* st, uint32_t site) {
+                                    DeviceStatus* st, uint32_t site, uint32_t spin_limit, bool publish) {
     __shared__ uint32_t s_prefix;
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
-        if (lane == 0) st_release_u64(status + tile, pack_status(epoch, tile == 0 ? kFlagInclusive : kFlagAggregate, aggregate));
+        if (lane == 0 && publish)
+            st_release_u64(status + tile, pack_status(epoch, tile == 0 ? kFlagInclusive : kFlagAggregate, aggregate));
         uint32_t prefix = 0;
         int64_t window = (int64_t)tile - 1;
         while (window >= 0) {
@@ -49,7 +54,7 @@ __device__ uint32_t lookback_prefix(uint64_t* status, uint32_t tile, uint32_t ag
                 do {
                     s = ld_acquire_u64(status + idx);
                     flag = status_flag(s, epoch);
-                } while (flag == 0 && ++spins < kSpinLimit);
+                } while (flag == 0 && ++spins < spin_limit);
                 if (flag == 0) {
                     record_error(st, kErrTimeout, site);
                     flag = kFlagInclusive;
@@ -67,7 +72,7 @@ __device__ uint32_t lookback_prefix(uint64_t* status, uint32_t tile, uint32_t ag
             window -= 32;
         }
         if (lane == 0) {
-            if (tile > 0) st_release_u64(status + tile, pack_status(epoch, kFlagInclusive, prefix + aggregate));
+            if (tile > 0 && publish) st_release_u64(status + tile, pack_status(epoch, kFlagInclusive, prefix + aggregate));
             s_prefix = prefix;
         }
     }
@@ -322,7 +327,8 @@ __global__ void __launch_bounds__(kScanThreads) digit_scan_kernel(const uint32_t
 // Exclusive scan of n uint32 values (n known on the host).
 __global__ void __launch_bounds__(kScanThreads) exclusive_scan_kernel(const uint32_t* __restrict__ in, uint32_t n,
                                                                       uint32_t* __restrict__ out, uint64_t* status,
-                                                                      uint32_t epoch, DeviceStatus* st, int ticket) {
+                                                                      uint32_t epoch, DeviceStatus* st, int ticket,
+                                                                      uint32_t spin_limit, uint32_t withhold) {
     const uint32_t tile = take_ticket(&st->ticket[ticket]);
     const uint32_t ntiles = (n + kScanTile - 1) / kScanTile;
     if (tile >= ntiles) return;
@@ -347,7 +353,7 @@ __global__ void __launch_bounds__(kScanThreads) exclusive_scan_kernel(const uint
     for (int k = 0; k < kScanItems; ++k) sum += c[k];
     uint32_t total;
     const uint32_t excl = block_exclusive_scan(sum, &total);
-    const uint32_t prefix = lookback_prefix(status, tile, total, epoch, st, 4);
+    const uint32_t prefix = lookback_prefix(status, tile, total, epoch, st, 4, spin_limit, tile != withhold);
     uint32_t pos = prefix + excl;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
@@ -363,10 +369,14 @@ void launch_digit_scan(const uint32_t* in, uint32_t stride, const uint32_t* row_
 }
 
 void launch_exclusive_scan(const uint32_t* in, uint32_t n, uint32_t* out, uint64_t* status, uint32_t epoch,
-                           DeviceStatus* st, int ticket, cudaStream_t s) {
+                           DeviceStatus* st, int ticket, cudaStream_t s, uint32_t spin_limit, uint32_t withhold) {
     const uint32_t blocks = (n + kScanTile - 1) / kScanTile;
-    exclusive_scan_kernel<<<blocks > 0 ? blocks : 1, kScanThreads, 0, s>>>(in, n, out, status, epoch, st, ticket);
+    exclusive_scan_kernel<<<blocks > 0 ? blocks : 1, kScanThreads, 0, s>>>(in, n, out, status, epoch, st, ticket,
+                                                                            spin_limit ? spin_limit : kSpinLimit,
+                                                                            withhold);
 }
+
+uint32_t exclusive_scan_blocks(uint32_t n) { return std::max<uint32_t>((n + kScanTile - 1) / kScanTile, 1u); }
 
 uint32_t scan_tiles_per_launch() { return kScanTile; }
 

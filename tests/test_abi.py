@@ -57,6 +57,7 @@ def test_create_without_device_is_an_argument_error(lib):
 STRUCTS = {
     "seele_scene_desc": _abi.SceneDesc, "seele_camera": _abi.Camera, "seele_options": _abi.Options,
     "seele_stats": _abi.Stats, "seele_grads": _abi.Grads, "seele_debug_view": _abi.DebugView,
+    "seele_peaks": _abi.Peaks,
 }
 
 
@@ -77,3 +78,20 @@ def test_ctypes_layouts_match_the_header():
         assert int(got[cname]) == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert int(got[f"{cname}.{f}"]) == getattr(py, f).offset, (cname, f)
+
+
+def test_argument_checks_come_before_any_gpu_work(lib):
+    """Calls that must refuse their arguments do so without touching memory
+    or a device (the pointers below are never dereferenced)."""
+    L = _abi.lib()
+    fake = [ctypes.c_void_p(0x100000 + 0x1000 * i) for i in range(5)]
+    # no-alloc sort: the tile ids are read as 16-byte vectors
+    mis = ctypes.c_void_p(0x100004)
+    assert L.seele_sort_tile_instances_noalloc(mis, fake[1], 8, 4, fake[2], fake[3], fake[4], None) == 1
+    assert L.seele_sort_tile_instances_noalloc(fake[0], fake[1], 8, 4, fake[2], None, fake[4], None) == 1
+    # scan: misaligned scratch or input, NULL pointers
+    assert L.seele_exclusive_scan(fake[0], 8, fake[1], ctypes.c_void_p(0x100010), 0xFFFFFFFF, 0, None) == 1
+    assert L.seele_exclusive_scan(mis, 8, fake[1], fake[2], 0xFFFFFFFF, 0, None) == 1
+    assert L.seele_exclusive_scan(None, 8, fake[1], fake[2], 0xFFFFFFFF, 0, None) == 1
+    assert L.seele_measure_peaks(0, None, None) == 1
+    assert L.seele_scan_scratch_bytes(4096 * 16) == 256 + 8 * 16

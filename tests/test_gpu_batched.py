@@ -91,11 +91,11 @@ def test_tile_shapes_render_the_same_image(Renderer, tile):
             d = np.abs(x - y)
             assert d.max() <= parity.RGB_MAX_ABS and (d == 0).mean() > 0.999
     # and against the oracle with that tile shape
-    ref = oracle.render(oracle.Scene64.from_scene(sc), cams[0],
-                        oracle.Options(cr=True, tile_w=tile[0], tile_h=tile[1]), nthreads=8)[0]
-    imgs, _ = parity.gpu_render(r, mode="cr", tile=tile)
-    ok, rep = parity.compare_images(imgs[0], ref.rgb, ref.margin)
-    assert ok, rep
+    oo = oracle.Options(cr=True, tile_w=tile[0], tile_h=tile[1])
+    ref, proj, _, gid, ranges = oracle.render(oracle.Scene64.from_scene(sc), cams[0], oo, nthreads=8)
+    imgs, Ts = parity.gpu_render(r, mode="cr", tile=tile)
+    rep = parity.check_render(imgs[0], Ts[0], ref, proj, gid, ranges, cams[0], oo)
+    assert rep["ok"], str(rep)
     r.close()
 
 

@@ -265,11 +265,9 @@ def test_render_matches_oracle(Renderer, case, where):
     r.set_cameras(cams)
     imgs, Ts = parity.gpu_render(r, **case)
     oo = parity.oracle_options(case["mode"], case.get("group", (2, 2)), case.get("opacity_filter", False))
-    ref = oracle.render(oracle.Scene64.from_scene(sc), cams[0], oo, nthreads=8)[0]
-    ok, rep = parity.compare_images(imgs[0], ref.rgb, ref.margin)
-    assert ok, rep
-    clear = ref.margin >= parity.MARGIN
-    assert np.max(np.abs(Ts[0] - ref.T)[clear]) <= parity.RGB_MAX_ABS
+    ref, proj, _, gid, ranges = oracle.render(oracle.Scene64.from_scene(sc), cams[0], oo, nthreads=8)
+    rep = parity.check_render(imgs[0], Ts[0], ref, proj, gid, ranges, cams[0], oo)
+    assert rep["ok"], str(rep)
     r.close()
 
 
@@ -285,9 +283,9 @@ def test_eight_by_eight_tiles_match_oracle(Renderer, case):
     imgs, Ts = parity.gpu_render(r, tile=(8, 8), **case)
     g = case.get("group", (2, 2))
     oo = oracle.Options(cr=case["mode"] == "cr", group_w=g[0], group_h=g[1], tile_w=8, tile_h=8)
-    ref = oracle.render(oracle.Scene64.from_scene(sc), cams[0], oo, nthreads=8)[0]
-    ok, rep = parity.compare_images(imgs[0], ref.rgb, ref.margin)
-    assert ok, rep
+    ref, proj, _, gid, ranges = oracle.render(oracle.Scene64.from_scene(sc), cams[0], oo, nthreads=8)
+    rep = parity.check_render(imgs[0], Ts[0], ref, proj, gid, ranges, cams[0], oo)
+    assert rep["ok"], str(rep)
     r.close()
 
 
@@ -342,14 +340,14 @@ def test_cluster_filter_matches_oracle(Renderer):
     r = Renderer()
     r.load_scene(sc)
     r.set_cameras(cams)
-    imgs, _ = parity.gpu_render(r, mode="cr", cluster_filter=True, opacity_filter=True)
+    imgs, Ts = parity.gpu_render(r, mode="cr", cluster_filter=True, opacity_filter=True)
     s64 = oracle.Scene64.from_scene(sc)
     for ci, cam in enumerate(cams):
         sel = oracle.select_clusters(s64.centroids, s64.pos_scale, cam, 3)
-        ref = oracle.render(s64, cam, parity.oracle_options("cr", opacity_filter=True, cluster_filter=True,
-                                                            sel_bits=sel), nthreads=8)[0]
-        ok, rep = parity.compare_images(imgs[ci], ref.rgb, ref.margin)
-        assert ok, (ci, rep)
+        oo = parity.oracle_options("cr", opacity_filter=True, cluster_filter=True, sel_bits=sel)
+        ref, proj, _, gid, ranges = oracle.render(s64, cam, oo, nthreads=8)
+        rep = parity.check_render(imgs[ci], Ts[ci], ref, proj, gid, ranges, cam, oo)
+        assert rep["ok"], str((ci, rep))
     r.close()
 
 
@@ -415,12 +413,9 @@ def test_extreme_attributes_match_oracle(Renderer, case):
     r.set_cameras([cam])
     imgs, Ts = parity.gpu_render(r, **case)
     oo = parity.oracle_options(case["mode"], (2, 2), case.get("opacity_filter", False))
-    ref = oracle.render(oracle.Scene64.from_scene(s), cam, oo, nthreads=8)[0]
-    ok, rep = parity.compare_images(imgs[0], ref.rgb, ref.margin)
-    assert ok, rep
-    clear = ref.margin >= parity.MARGIN
-    assert clear.mean() > 0.9
-    assert np.max(np.abs(Ts[0] - ref.T)[clear]) <= parity.RGB_MAX_ABS
+    ref, proj, _, gid, ranges = oracle.render(oracle.Scene64.from_scene(s), cam, oo, nthreads=8)
+    rep = parity.check_render(imgs[0], Ts[0], ref, proj, gid, ranges, cam, oo)
+    assert rep["ok"], str(rep)
     r.close()
 
 
@@ -435,11 +430,12 @@ def test_capacity_growth_is_transparent(Renderer):
     r = Renderer()
     r.load_scene(s)
     r.set_cameras([cam])
-    imgs, _ = parity.gpu_render(r, binning="tiles")
+    imgs, Ts = parity.gpu_render(r, binning="tiles")
     assert r.last_stats["retries"] == 1 and r.last_stats["n_instances"] > (1 << 20)
-    ref = oracle.render(oracle.Scene64.from_scene(s), cam, oracle.Options(), nthreads=8)[0]
-    ok, rep = parity.compare_images(imgs[0], ref.rgb, ref.margin)
-    assert ok, rep
+    oo = oracle.Options()
+    ref, proj, _, gid, ranges = oracle.render(oracle.Scene64.from_scene(s), cam, oo, nthreads=8)
+    rep = parity.check_render(imgs[0], Ts[0], ref, proj, gid, ranges, cam, oo)
+    assert rep["ok"], str(rep)
     r.close()
 
 

@@ -92,14 +92,14 @@ def test_built_representation_drives_the_cluster_filter(Renderer):
     rep = dict(sc, cluster_mask=out["mask"], centroids=out["centroids"], pos_scale=out["pos_scale"])
     r.load_scene(rep)
     r.set_cameras(cams)
-    imgs, _ = parity.gpu_render(r, mode="cr", cluster_filter=True, opacity_filter=True)
+    imgs, Ts = parity.gpu_render(r, mode="cr", cluster_filter=True, opacity_filter=True)
     rep64 = oracle.Scene64.from_scene(rep)
     for ci, cam in enumerate(cams):
         sel = oracle.select_clusters(rep64.centroids, rep64.pos_scale, cam, 3)
-        ref = oracle.render(rep64, cam, parity.oracle_options("cr", opacity_filter=True, cluster_filter=True,
-                                                              sel_bits=sel), nthreads=8)[0]
-        ok, rep_ = parity.compare_images(imgs[ci], ref.rgb, ref.margin)
-        assert ok, (ci, rep_)
+        oo = parity.oracle_options("cr", opacity_filter=True, cluster_filter=True, sel_bits=sel)
+        ref, proj, _, gid, ranges = oracle.render(rep64, cam, oo, nthreads=8)
+        rep_ = parity.check_render(imgs[ci], Ts[ci], ref, proj, gid, ranges, cam, oo)
+        assert rep_["ok"], str((ci, rep_))
     r.close()
 
 

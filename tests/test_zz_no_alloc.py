@@ -87,6 +87,62 @@ def test_noalloc_sort_matches_the_render_path_twice(Renderer, width, height):
     r.close()
 
 
+def _stable_reference(tiles, recs, n_tiles):
+    order = np.argsort(tiles, kind="stable")
+    counts = np.bincount(tiles, minlength=n_tiles)
+    start = np.concatenate([[0], np.cumsum(counts)[:-1]])
+    return recs[order], start, start + counts, counts > 0
+
+
+@pytest.mark.parametrize("n,n_tiles", [(1 << 20, 1 << 16), (300_007, 8160), (0, 17), (5000, 200)])
+def test_noalloc_sort_matches_a_stable_argsort_twice(Renderer, n, n_tiles):
+    """Random tile ids at the limits (2^20 instances over 2^16 tiles: 16 scan
+    blocks, two radix passes), a mid size, a single pass and no instances at
+    all, each sorted twice in a row so that look-back entries left by the
+    previous call are met too."""
+    import torch
+    from paper_2503_05168_gb300 import lib
+    rs = np.random.default_rng(n + n_tiles)
+    tiles = rs.integers(0, n_tiles, n).astype(np.uint32)
+    recs = rs.integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32)
+    exp_rec, exp_start, exp_end, nonempty = _stable_reference(tiles, recs, n_tiles)
+    stream = torch.cuda.current_stream().cuda_stream
+    for _ in range(2):
+        st, got, start, end = _call(lib(), stream, tiles, recs, n_tiles)
+        assert st == 0
+        np.testing.assert_array_equal(got, exp_rec)
+        np.testing.assert_array_equal(start[nonempty], exp_start[nonempty])
+        np.testing.assert_array_equal(end[nonempty], exp_end[nonempty])
+        assert np.all(start[~nonempty].astype(np.int64) >= end[~nonempty])
+
+
+def test_noalloc_sort_refuses_bad_tile_ids_and_misaligned_input(Renderer):
+    """A tile id >= n_tiles is found on the device: nothing is sorted, every
+    list stays empty and the call returns SEELE_ERR_ARG; a tile-id pointer
+    that is not 16-byte aligned is refused before any GPU work."""
+    import torch
+    from paper_2503_05168_gb300 import lib
+    stream = torch.cuda.current_stream().cuda_stream
+    tiles = np.arange(1000, dtype=np.uint32) % 64
+    tiles[617] = 64
+    recs = np.arange(1000, dtype=np.uint32)
+    st, got, start, end = _call(lib(), stream, tiles, recs, 64)
+    assert st == 1
+    assert np.all(start.astype(np.int64) >= end) and np.all(got == np.uint32(0xFFFFFFF9))
+    t = torch.from_numpy((tiles % 64).view(np.int32)).cuda()
+    r = torch.from_numpy(recs.view(np.int32)).cuda()
+    out = torch.zeros(1000, dtype=torch.int32, device="cuda")
+    se = torch.zeros(64, dtype=torch.int32, device="cuda")
+    st = lib().seele_sort_tile_instances_noalloc(
+        ctypes.c_void_p(t[1:].data_ptr()), ctypes.c_void_p(r.data_ptr()), 999, 64, ctypes.c_void_p(out.data_ptr()),
+        ctypes.c_void_p(se.data_ptr()), ctypes.c_void_p(se.data_ptr()), ctypes.c_void_p(stream))
+    assert st == 1
+    # and the next ordinary call works
+    st, got, start, end = _call(lib(), stream, tiles % 64, recs, 64)
+    assert st == 0
+    np.testing.assert_array_equal(got, _stable_reference(tiles % 64, recs, 64)[0])
+
+
 def test_noalloc_sort_rejects_sizes_beyond_its_limits():
     import torch
     from paper_2503_05168_gb300 import _abi, lib
