@@ -286,6 +286,105 @@ void launch_block_order(const uint32_t* bstart, const uint32_t* bend, uint32_t n
     launch_pdl(block_order_kernel, dim3(1), dim3(1024), 0, s, bstart, bend, n_blocks, order);
 }
 
+// Cameras in groups for the persistent rasterizer (Sec. 3.1's tiles of many
+// views from one queue): the cameras are ranked by their total list length,
+// least first, and cut into groups of `depth`; the queue takes group after
+// group, each with its longest lists first, so the views of an early group
+// finish before later groups start (per-view latency) while each group still
+// balances its own tiles.  depth 0 (or >= n_cams): one group, the plain
+// longest-lists-first order.  One CTA: a counting sort on (group, bucket).
+constexpr int kOrderGroups = 64;
+
+__global__ void __launch_bounds__(1024) view_order_kernel(const uint32_t* __restrict__ bstart,
+                                                          const uint32_t* __restrict__ bend, uint32_t n_units,
+                                                          const CamDev* __restrict__ cams, int n_cams, int blocks,
+                                                          int depth, uint32_t* __restrict__ order) {
+    __shared__ uint32_t s_tot[kViewOrderMaxCams];
+    __shared__ uint8_t s_group[kViewOrderMaxCams];
+    __shared__ uint32_t s_hist[kOrderGroups * kOrderBuckets];
+    __shared__ uint32_t s_warp[32];
+    pdl_enter();
+    const int t = threadIdx.x;
+    auto cam_of = [&](uint32_t u) {
+        int lo = 0, hi = n_cams - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            const uint32_t off = blocks ? cams[mid].block_offset : cams[mid].tile_offset;
+            if (off <= u) lo = mid; else hi = mid - 1;
+        }
+        return lo;
+    };
+    auto length = [&](uint32_t u) {
+        const uint32_t s = __ldg(bstart + u), e = __ldg(bend + u);
+        return s < e ? e - s : 0u;
+    };
+    auto bucket = [&](uint32_t len) {  // 4 buckets per octave, longest lists in bucket 0
+        const uint32_t v = len + 1u;
+        const int lg = 31 - __clz(v);
+        const int frac = lg >= 2 ? (int)((v >> (lg - 2)) & 3u) : (int)((v << (2 - lg)) & 3u);
+        return kOrderBuckets - 1 - min(kOrderBuckets - 1, lg * 4 + frac);
+    };
+    for (int i = t; i < n_cams; i += blockDim.x) s_tot[i] = 0;
+    for (int i = t; i < kOrderGroups * kOrderBuckets; i += blockDim.x) s_hist[i] = 0;
+    __syncthreads();
+    for (uint32_t u = t; u < n_units; u += blockDim.x) atomicAdd(&s_tot[cam_of(u)], length(u));
+    __syncthreads();
+    // rank by total (ties to the lower index), then the group of the rank
+    const int d = (depth <= 0 || depth >= n_cams) ? n_cams : max(depth, (n_cams + kOrderGroups - 1) / kOrderGroups);
+    for (int c = t; c < n_cams; c += blockDim.x) {
+        const uint32_t mine = s_tot[c];
+        int rank = 0;
+        for (int o = 0; o < n_cams; ++o) rank += (s_tot[o] < mine || (s_tot[o] == mine && o < c)) ? 1 : 0;
+        s_group[c] = (uint8_t)(rank / d);
+    }
+    __syncthreads();
+    for (uint32_t u = t; u < n_units; u += blockDim.x)
+        atomicAdd(&s_hist[s_group[cam_of(u)] * kOrderBuckets + bucket(length(u))], 1u);
+    __syncthreads();
+    // exclusive scan of the histogram: four entries per thread
+    constexpr int kPer = kOrderGroups * kOrderBuckets / 1024;
+    uint32_t v[kPer], sum = 0;
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        v[i] = s_hist[t * kPer + i];
+        sum += v[i];
+    }
+    const int lane = t & 31, w = t >> 5;
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_warp[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t x = s_warp[lane], xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, xi, o);
+            if (lane >= o) xi += y;
+        }
+        s_warp[lane] = xi - x;
+    }
+    __syncthreads();
+    uint32_t run = s_warp[w] + incl - sum;
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        s_hist[t * kPer + i] = run;
+        run += v[i];
+    }
+    __syncthreads();
+    for (uint32_t u = t; u < n_units; u += blockDim.x)
+        order[atomicAdd(&s_hist[s_group[cam_of(u)] * kOrderBuckets + bucket(length(u))], 1u)] = u;
+}
+
+void launch_view_order(const uint32_t* bstart, const uint32_t* bend, uint32_t n_units, const CamDev* cams, int n_cams,
+                       bool blocks, int depth, uint32_t* order, cudaStream_t s) {
+    launch_pdl(view_order_kernel, dim3(1), dim3(1024), 0, s, bstart, bend, n_units, cams, n_cams, blocks ? 1 : 0,
+               depth, order);
+}
+
 template <typename KeyT>
 void launch_emit(const uint32_t* order, const uint32_t* offsets, const float4* rec,
                  const CamDev* cams, int n_gauss, int tile_w, int tile_h, int ellipse, DeviceStatus* st,

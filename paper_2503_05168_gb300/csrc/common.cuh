@@ -29,7 +29,8 @@ struct DeviceStatus {
     uint32_t capacity;       // instance capacity the scan compared K against
     uint32_t n_inst_valid;   // K if it fits the capacity, else 0 (what the tile sort reads)
     uint32_t timeout_site;   // which wait gave up (diagnostics)
-    uint32_t pad[3];
+    uint32_t queue;          // list units taken by the persistent rasterizer
+    uint32_t pad[2];
     uint32_t ticket[16];     // dynamic block tickets of the look-back kernels
     unsigned long long work[4];  // rasterizer work counters (counting variant only)
 };

@@ -100,6 +100,12 @@ void launch_mask_summary(const uint32_t* mask, const DeviceStatus* st, uint32_t*
                          cudaStream_t s);
 void launch_block_order(const uint32_t* bstart, const uint32_t* bend, uint32_t n_blocks, uint32_t* order,
                         cudaStream_t s);
+// The unit order for the persistent rasterizer: cameras in groups of `depth`
+// (least total work first; 0: one group of all), longest lists first within
+// a group.  Needs n_cams <= kViewOrderMaxCams.
+constexpr int kViewOrderMaxCams = 1024;
+void launch_view_order(const uint32_t* bstart, const uint32_t* bend, uint32_t n_units, const CamDev* cams, int n_cams,
+                       bool blocks, int depth, uint32_t* order, cudaStream_t s);
 
 // Offline view-dependent representation (views.cu).  k-means of n 6-D
 // double points (one CTA); top-k contributors of a frame's tile lists ORed
@@ -144,6 +150,10 @@ struct RasterArgs {
     // (see kCkptShift), and every pixel's final (T, r, g, b)
     float4* ckpt;
     float4* cfin;
+    // non-null: the persistent rasterizer, taking units in block_order's order
+    // through this counter (zero at the frame's start); the counting variant
+    // always runs one CTA per unit
+    uint32_t* queue = nullptr;
 };
 bool launch_raster_fwd(const RasterArgs& a, cudaStream_t s);
 

@@ -239,7 +239,10 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev sc, const CamD
         float4* ro = out.rec + (size_t)kRecF4 * rid;
         ro[0] = rec0;
         ro[1] = rec1;
-        ro[2] = make_float4(rgb[0], rgb[1], rgb[2], 0.f);
+        // the last slot flags the Gaussians whose alpha can reach the clamp
+        // (o within 1e-4 in log2 of alpha_max): only their blends need the
+        // min(), for every other one 2^e < alpha_max wherever e <= log2 o
+        ro[2] = make_float4(rgb[0], rgb[1], rgb[2], lo > __log2f(fp.alpha_max) - 1e-4f ? 1.f : 0.f);
         ro[3] = make_float4(__uint_as_float((uint32_t)tx0 | ((uint32_t)ty0 << 16)),
                             __uint_as_float((uint32_t)tx1 | ((uint32_t)ty1 << 16)), 0.f, 0.f);
         out.depth[rid] = Z;

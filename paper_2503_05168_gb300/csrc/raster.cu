@@ -1,361 +1,16 @@
-// raster.cu -- tile rasterization, forward (Sec. 3.1 "Rasterization",
-// Eqns. 1-2) and contribution-aware (Sec. 3.4, Algorithm 1).
-//
-// One CTA per tile; each thread owns a PW x PH block of pixels, so a Gaussian
-// staged in shared memory is loaded once per 4 (or 8) pixels and the pixels of
-// a thread give four independent dependency chains.  Pixel groups of Alg. 1
-// are GW x GH sub-blocks of a thread's block, or unions of whole thread
-// blocks, with the top-left pixel as leader (Sec. 4.1): the leader's exponent
-// decides for its group, the remaining pixels then apply the per-pixel rules.
-// A group spanning several threads has each of them evaluate the leader's
-// exponent itself (the same FP32 operations on the same inputs).  A warp skips a Gaussian
-// outright when every group it holds rejects it -- the divergence-free skip of
-// Sec. 3.4 "GPU Parallelism".
-//
-// Work per (pixel, Gaussian) pair: ~10 FP32-pipe instructions and one MUFU
-// ex2; the kernel is bound by instruction issue, not by memory.
-#include "common.cuh"
-#include "kernels.h"
+// raster.cu -- launches of the tile rasterizer (raster_impl.cuh): one CTA per
+// list unit, or the persistent queue kernels of raster_queue.cu.
+#include "raster_impl.cuh"
 
 namespace seele {
-
-__device__ __forceinline__ float ex2_approx(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// BLOCKS (block binning): CTA i rasterizes tile i % 32 of the tile block
-// block_order[i / 32].  Its list is the block's list filtered by the tile's
-// mask bit: a window of 32 * NT entries at a time, one 32-entry group per
-// thread, skipped with one load when the group's OR-summary lacks the bit.
-// The kept entries, in list order, are exactly the tile's own list.
-template <int TW, int TH, int PW, int PH, int GW, int GH, bool CR, bool COUNT, bool BLOCKS>
-__global__ void __launch_bounds__((TW / PW) * (TH / PH))
-    raster_fwd_kernel(const uint32_t* __restrict__ starts, const uint32_t* __restrict__ ends,
-                      const uint32_t* __restrict__ inst_rec, const uint32_t* __restrict__ inst_mask,
-                      const uint32_t* __restrict__ mask_summary, const uint32_t* __restrict__ block_order,
-                      const float4* __restrict__ rec, const CamDev* __restrict__ cams, int n_cams, FrameParams fp,
-                      float* __restrict__ out_rgb, float* __restrict__ out_T, uint32_t* __restrict__ out_nc,
-                      DeviceStatus* __restrict__ counters, unsigned long long* __restrict__ view_end,
-                      uint32_t* __restrict__ view_done, float4* __restrict__ ckpt, float4* __restrict__ cfin) {
-    constexpr int NT = (TW / PW) * (TH / PH);
-    constexpr int NP = PW * PH;
-    constexpr int TXN = TW / PW;
-    constexpr int WIN = BLOCKS ? 32 * NT : 1;  // list entries filtered per window
-    static_assert((PW % GW == 0 && PH % GH == 0) || (GW % PW == 0 && GH % PH == 0),
-                  "groups tile the thread block or are tiled by thread blocks");
-    constexpr bool WHOLE = GW % PW == 0 && GH % PH == 0;  // a group is one or more whole thread blocks
-    static_assert(NT % 32 == 0 && kBlockW * kBlockH == 32, "whole warps; one mask word per block entry");
-    __shared__ float4 s0[NT], s1[NT], s2[NT];
-    __shared__ uint32_t s_idx[WIN];          // block binning: list indices of the window's tile entries
-    __shared__ uint32_t s_wsum[NT / 32];
-
-    pdl_enter();
-    uint32_t gtile, unit, bit = 0;
-    int lo = 0, tx, ty;
-    if (BLOCKS) {
-        const uint32_t b = __ldg(block_order + (blockIdx.x >> 5));
-        bit = blockIdx.x & 31u;
-        int hi = n_cams - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (cams[mid].block_offset <= b) lo = mid; else hi = mid - 1;
-        }
-        const CamDev& Cb = cams[lo];
-        const uint32_t lb = b - Cb.block_offset;
-        tx = (int)(lb % (uint32_t)Cb.blocks_x) * kBlockW + (int)(bit % kBlockW);
-        ty = (int)(lb / (uint32_t)Cb.blocks_x) * kBlockH + (int)(bit / kBlockW);
-        if (tx >= Cb.tiles_x || ty >= Cb.tiles_y) return;  // padding tile of a partial block
-        gtile = Cb.tile_offset + (uint32_t)(ty * Cb.tiles_x + tx);
-        unit = b;
-    } else {
-        gtile = block_order ? __ldg(block_order + blockIdx.x) : blockIdx.x;  // longest lists first
-        int hi = n_cams - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (cams[mid].tile_offset <= gtile) lo = mid; else hi = mid - 1;
-        }
-        const uint32_t lt = gtile - cams[lo].tile_offset;
-        tx = (int)(lt % (uint32_t)cams[lo].tiles_x);
-        ty = (int)(lt / (uint32_t)cams[lo].tiles_x);
-        unit = gtile;
-    }
-    const CamDev& C = cams[lo];
-    const int t = threadIdx.x;
-    const int bx = tx * TW + (t % TXN) * PW, by = ty * TH + (t / TXN) * PH;
-
-    float T[NP], cr[NP], cg[NP], cb[NP];
-    uint32_t nc[NP];
-    uint32_t live = 0;
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-        T[p] = 1.f;
-        cr[p] = cg[p] = cb[p] = 0.f;
-        nc[p] = 0;
-        if (bx + p % PW < C.W && by + p / PW < C.H) live |= 1u << p;
-    }
-    uint2 rg = make_uint2(__ldg(starts + unit), __ldg(ends + unit));
-    if (rg.x >= rg.y) rg = make_uint2(0u, 0u);  // no instances
-    const float fx0 = (float)bx + 0.5f, fy0 = (float)by + 0.5f;
-    // the leader pixel of the group holding this thread's block (WHOLE groups)
-    const float lx0 = (float)(bx / GW * GW) + 0.5f, ly0 = (float)(by / GH * GH) + 0.5f;
-    const float amax = fp.alpha_max, tstop = fp.t_stop;
-    uint32_t n_lead = 0, n_eval = 0, n_blend = 0;  // counting variant only
-
-    uint32_t cursor = BLOCKS ? rg.x >> 5 : rg.x;  // next list entry (tiles) or 32-entry group (blocks)
-    const uint32_t cursor_end = BLOCKS ? (rg.y + 31u) >> 5 : rg.y;
-    uint32_t pos0 = 0;           // tile-list position of staged entry 0
-    int n_idx = 0, idx_pos = 0;  // block binning: window entries kept / staged
-    while (true) {
-        if (__syncthreads_and(live == 0u)) break;
-        int cnt;
-        if (!BLOCKS) {
-            if (cursor >= cursor_end) break;
-            const uint32_t j = cursor + t;
-            if (j < rg.y) {
-                const uint32_t r = __ldg(inst_rec + j);
-                s0[t] = __ldg(rec + (size_t)kRecF4 * r);
-                s1[t] = __ldg(rec + (size_t)kRecF4 * r + 1);
-                s2[t] = __ldg(rec + (size_t)kRecF4 * r + 2);
-            }
-            cnt = (int)min((uint32_t)NT, rg.y - cursor);
-            cursor += NT;
-            __syncthreads();
-        } else {
-            if (idx_pos == n_idx) {
-                if (cursor >= cursor_end) break;
-                // thread t filters group cursor + t; group order is list order
-                const uint32_t g = cursor + (uint32_t)t;
-                uint32_t hits = 0;
-                if (g < cursor_end && ((__ldg(mask_summary + g) >> bit) & 1u)) {
-                    const uint4* mg = reinterpret_cast<const uint4*>(inst_mask + 32 * (size_t)g);
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const uint4 v = __ldg(mg + q);
-                        hits |= (((v.x >> bit) & 1u) | (((v.y >> bit) & 1u) << 1) | (((v.z >> bit) & 1u) << 2) |
-                                 (((v.w >> bit) & 1u) << 3)) << (4 * q);
-                    }
-                    // entries of neighbouring lists share the edge groups
-                    const uint32_t e0 = 32 * g;
-                    if (e0 < rg.x) hits &= 0xffffffffu << (rg.x - e0);
-                    if (e0 + 32 > rg.y) hits &= 0xffffffffu >> (e0 + 32 - rg.y);
-                }
-                const uint32_t c = __popc(hits);
-                uint32_t incl = c;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                    if ((t & 31) >= o) incl += y;
-                }
-                if ((t & 31) == 31) s_wsum[t >> 5] = incl;
-                __syncthreads();
-                uint32_t off = incl - c, total = 0;
-#pragma unroll
-                for (int ww = 0; ww < NT / 32; ++ww) {
-                    const uint32_t v = s_wsum[ww];
-                    off += ww < (t >> 5) ? v : 0u;
-                    total += v;
-                }
-                while (hits) {
-                    const int q = __ffs(hits) - 1;
-                    hits &= hits - 1u;
-                    s_idx[off++] = 32 * g + (uint32_t)q;
-                }
-                n_idx = (int)total;
-                idx_pos = 0;
-                cursor += NT;
-                __syncthreads();
-                if (n_idx == 0) continue;
-            }
-            cnt = min(NT, n_idx - idx_pos);
-            if (t < cnt) {
-                const uint32_t r = __ldg(inst_rec + s_idx[idx_pos + t]);
-                s0[t] = __ldg(rec + (size_t)kRecF4 * r);
-                s1[t] = __ldg(rec + (size_t)kRecF4 * r + 1);
-                s2[t] = __ldg(rec + (size_t)kRecF4 * r + 2);
-            }
-            idx_pos += cnt;
-            __syncthreads();
-        }
-        do {
-        if (CR && WHOLE) {
-            // Alg. 1 with the thread's pixels inside one group.  Phase 1: the
-            // group's leader tests every staged Gaussian -- independent of the
-            // blending state, so the tests run back to back.  Phase 2: only the
-            // Gaussians the leader kept are blended, in list order, by the
-            // thread's pixels.
-            if (live == 0u) continue;
-            // the group's pixels' live flags as separate predicates for the
-            // blend loop (no bit extraction per pixel), folded back after it
-            bool alive[NP];
-#pragma unroll
-            for (int p = 0; p < NP; ++p) alive[p] = (live >> p) & 1u;
-            auto any_alive = [&]() {
-                bool a = false;
-#pragma unroll
-                for (int p = 0; p < NP; ++p) a = a || alive[p];
-                return a;
-            };
-            for (int c0 = 0; c0 < cnt && any_alive(); c0 += 32) {
-            const int n32 = min(32, cnt - c0);
-            uint32_t pass = 0;
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                if (i < n32) {
-                    const float4 A = s0[c0 + i];
-                    const float4 B = s1[c0 + i];
-                    const float dx = lx0 - A.x, dy = ly0 - A.y;
-                    const float e0 = fmaf(fmaf(A.z, dx, A.w * dy), dx, fmaf(B.x * dy, dy, B.y));
-                    if (COUNT) ++n_lead;
-                    pass |= e0 >= B.z ? 1u << i : 0u;
-                }
-            }
-            while (pass != 0u && any_alive()) {
-                const int k = c0 + __ffs(pass) - 1;
-                pass &= pass - 1u;
-                const float4 A = s0[k];
-                const float4 B = s1[k];
-                const float4 Cc = s2[k];
-                const float dx = fx0 - A.x, dy = fy0 - A.y;
-                const uint32_t pos1 = pos0 + (uint32_t)k + 1u;
-#pragma unroll
-                for (int jj = 0; jj < PH; ++jj) {
-                    const float ddy = dy + (float)jj;
-                    const float rb = A.w * ddy, rc = fmaf(B.x * ddy, ddy, B.y);
-                    // branch-free over the group's pixels (almost every pixel
-                    // of a kept Gaussian blends), so their chains interleave
-#pragma unroll
-                    for (int i = 0; i < PW; ++i) {
-                        const int p = jj * PW + i;
-                        if (COUNT) n_eval += alive[p];
-                        const float ddx = dx + (float)i;
-                        const float e = fmaf(fmaf(A.z, ddx, rb), ddx, rc);
-                        const bool on = alive[p] && e >= B.z;  // per-pixel alpha_theta / support rule
-                        const float al = fminf(amax, ex2_approx(e));
-                        const float wgt = al * T[p];
-                        const float Tn = T[p] - wgt;  // T (1 - alpha)
-                        const bool stop = on && Tn < tstop;
-                        const bool take = on && !stop;
-                        alive[p] = alive[p] && !stop;
-                        const float w = take ? wgt : 0.f;
-                        cr[p] = fmaf(w, Cc.x, cr[p]);
-                        cg[p] = fmaf(w, Cc.y, cg[p]);
-                        cb[p] = fmaf(w, Cc.z, cb[p]);
-                        T[p] = T[p] - w;  // Tn when taken (same rounding), else T
-                        nc[p] = take ? pos1 : nc[p];
-                        if (COUNT) n_blend += take;
-                    }
-                }
-            }
-            }
-            live = 0u;
-#pragma unroll
-            for (int p = 0; p < NP; ++p) live |= (uint32_t)alive[p] << p;
-            continue;
-        }
-        for (int k = 0; k < cnt; ++k) {
-            if (live == 0u) break;
-            const float4 A = s0[k];
-            const float4 B = s1[k];
-            const float dx = fx0 - A.x, dy = fy0 - A.y;
-            const uint32_t pos1 = pos0 + (uint32_t)k + 1u;
-            // exponent of alpha = 2^e at pixel offset (i, j) of this thread
-            auto expo = [&](int i, int jj) {
-                const float ddx = dx + (float)i, ddy = dy + (float)jj;
-                return fmaf(fmaf(A.z, ddx, A.w * ddy), ddx, fmaf(B.x * ddy, ddy, B.y));
-            };
-            auto blend = [&](int p, float e) {
-                if (COUNT) ++n_eval;
-                if (e < B.z) return;  // outside the support or alpha < alpha_theta
-                const float al = fminf(amax, ex2_approx(e));
-                const float wgt = al * T[p];
-                const float Tn = T[p] - wgt;  // T (1 - alpha)
-                if (Tn < tstop) {     // stop before crossing Gamma_theta
-                    live &= ~(1u << p);
-                    return;
-                }
-                const float4 Cc = s2[k];
-                cr[p] = fmaf(wgt, Cc.x, cr[p]);
-                cg[p] = fmaf(wgt, Cc.y, cg[p]);
-                cb[p] = fmaf(wgt, Cc.z, cb[p]);
-                T[p] = Tn;
-                nc[p] = pos1;
-                if (COUNT) ++n_blend;
-            };
-            if (CR && WHOLE) {
-                // handled by the two-phase path above
-            } else if (CR) {
-#pragma unroll
-                for (int gy = 0; gy < PH / GH; ++gy)
-#pragma unroll
-                    for (int gx = 0; gx < PW / GW; ++gx) {
-                        uint32_t gmask = 0;
-#pragma unroll
-                        for (int jj = 0; jj < GH; ++jj)
-#pragma unroll
-                            for (int i = 0; i < GW; ++i) gmask |= 1u << ((gy * GH + jj) * PW + gx * GW + i);
-                        if ((live & gmask) == 0u) continue;
-                        if (COUNT) ++n_lead;
-                        const float e0 = expo(gx * GW, gy * GH);
-                        if (e0 < B.z) continue;  // leader rejects: the whole group skips g
-#pragma unroll
-                        for (int jj = 0; jj < GH; ++jj)
-#pragma unroll
-                            for (int i = 0; i < GW; ++i) {
-                                const int p = (gy * GH + jj) * PW + gx * GW + i;
-                                if (!(live >> p & 1u)) continue;
-                                blend(p, (i == 0 && jj == 0) ? e0 : expo(gx * GW + i, gy * GH + jj));
-                            }
-                    }
-            } else {
-#pragma unroll
-                for (int p = 0; p < NP; ++p)
-                    if (live >> p & 1u) blend(p, expo(p % PW, p / PW));
-            }
-        }
-        } while (0);
-        pos0 += (uint32_t)cnt;
-        if (!BLOCKS && ckpt != nullptr && (pos0 & (kCkptL - 1u)) == 0u && pos0 < rg.y - rg.x) {
-            float4* slot = ckpt + (size_t)((rg.x >> kCkptShift) + (pos0 >> kCkptShift)) * (TW * TH);
-#pragma unroll
-            for (int p = 0; p < NP; ++p)
-                if (bx + p % PW < C.W && by + p / PW < C.H)
-                    slot[(by - ty * TH + p / PW) * TW + (bx - tx * TW + p % PW)] = make_float4(T[p], cr[p], cg[p], cb[p]);
-        }
-    }
-
-    if (COUNT) {
-        atomicAdd(&counters->work[0], (unsigned long long)n_lead);
-        atomicAdd(&counters->work[1], (unsigned long long)n_eval);
-        atomicAdd(&counters->work[2], (unsigned long long)n_blend);
-    }
-    const size_t plane = (size_t)C.W * C.H;
-    float* img = out_rgb + 3 * (size_t)C.pix_offset;
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-        const int x = bx + p % PW, y = by + p / PW;
-        if (x < C.W && y < C.H) {
-            const size_t o = (size_t)y * C.W + x;
-            img[o] = cr[p];
-            img[plane + o] = cg[p];
-            img[2 * plane + o] = cb[p];
-            out_T[C.pix_offset + o] = T[p];
-            out_nc[C.pix_offset + o] = nc[p];
-            if (cfin != nullptr) cfin[C.pix_offset + o] = make_float4(T[p], cr[p], cg[p], cb[p]);
-        }
-    }
-    // the CTA that finishes a camera's last tile stamps the view's end time
-    if (view_done) {
-        __syncthreads();
-        if (t == 0 && atomicAdd(view_done + lo, 1u) + 1u == (uint32_t)(C.tiles_x * C.tiles_y))
-            view_end[lo] = global_ns();
-    }
-}
 
 template <int TW, int TH, int PW, int PH, int GW, int GH, bool CR, bool COUNT, bool BLOCKS>
 static void launch_variant(const RasterArgs& a, cudaStream_t s) {
     constexpr int NT = (TW / PW) * (TH / PH);
+    if (!COUNT && a.queue != nullptr) {
+        launch_raster_queue<TW, TH, PW, PH, GW, GH, CR, BLOCKS>(a, s);
+        return;
+    }
     const uint32_t grid = BLOCKS ? 32 * a.n_blocks : a.n_tiles;
     launch_pdl(raster_fwd_kernel<TW, TH, PW, PH, GW, GH, CR, COUNT, BLOCKS>, dim3(grid), dim3(NT), 0, s,
                a.starts, a.ends, a.inst_rec, a.inst_mask, a.mask_summary, a.block_order, a.rec, a.cams, a.n_cams,
