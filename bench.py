@@ -520,8 +520,11 @@ def _sensitivity(args, device):
     return out
 
 
-def _multiview(args, device):
-    """64 cameras of mixed resolution rendered in one graph launch per batch."""
+def _multiview(args, device, pipe_peaks):
+    """64 cameras of mixed resolution rendered in one CUDA-graph launch per
+    batch.  The batched autotuner (seele_autotune_ex) picks the tile shape,
+    then the rasterizer schedule and batch depth, once for throughput and once
+    for the median per-view latency; both choices are timed."""
     import torch
 
     import scenegen
@@ -531,36 +534,64 @@ def _multiview(args, device):
     r = Renderer(device)
     r.load_scene(scene, spatial=True)
     r.set_cameras(cams)
-    opts, tune_ms = r.autotune(mode="cr", opacity_filter=True)
-    r.render(options=opts)                       # sizes the instance buffers
-    out = torch.empty(3 * r.n_pixels, device=r.device)
-    gopts = r.make_options(mode="cr", opacity_filter=True, tile=(opts.tile_w, opts.tile_h), graph=True, sync=False)
-    for _ in range(3):
-        r.render(out=out, options=gopts)
-    r.synchronize()
-    k = max(3, min(args.steps, 10))
-    s = torch.cuda.Event(enable_timing=True)
-    e = torch.cuda.Event(enable_timing=True)
-    s.record()
-    for _ in range(k):
-        r.render(out=out, options=gopts)
-    e.record()
-    r.synchronize()
-    ms = s.elapsed_time(e) / k
-    per_view = []
-    for _ in range(3):
-        r.render(out=out, options=r.make_options(mode="cr", opacity_filter=True, tile=(opts.tile_w, opts.tile_h),
-                                                 graph=True))
-        per_view += r.view_times()
     n_views = len(cams)
-    res = {"views_per_s": n_views * 1000.0 / ms, "ms_per_batch": ms, "views": n_views,
-           "tile": [opts.tile_w, opts.tile_h], "autotune_ms": tune_ms,
-           "view_ms_p50": float(np.percentile(per_view, 50)), "view_ms_p99": float(np.percentile(per_view, 99)),
-           "instances": r.last_stats["n_instances"] if r.last_stats else None,
-           "workload": (f"multiview_2m: {args.multiview_n} Gaussians (unbounded-style), {n_views} cameras with "
-                        f"resolutions from {{640x360, 1280x720, 1920x1080}} at radius 3-6, one CUDA-graph launch "
-                        f"per batch, CR + opacity filter, scene in spatial order; per-view ms = start of "
-                        f"preprocessing to the view's last tile")}
+    out = torch.empty(3 * r.n_pixels, device=r.device)
+    t0 = time.perf_counter()
+    o_thr, tune_thr = r.autotune_ex(objective="batch", cache=args.tune_cache, mode="cr", opacity_filter=True)
+    o_lat, tune_lat = r.autotune_ex(objective="p50", cache=args.tune_cache, mode="cr", opacity_filter=True)
+    tune_s = time.perf_counter() - t0
+
+    def timed(o):
+        kw = dict(mode="cr", opacity_filter=True, tile=(o.tile_w, o.tile_h),
+                  schedule="queue" if o.schedule else "grid", batch_depth=o.batch_depth)
+        r.render(**kw)                                # sizes the instance buffers
+        gopts = r.make_options(graph=True, sync=False, **kw)
+        for _ in range(3):
+            r.render(out=out, options=gopts)
+        r.synchronize()
+        k = max(3, min(args.steps, 10))
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        for _ in range(k):
+            r.render(out=out, options=gopts)
+        e.record()
+        r.synchronize()
+        ms = s.elapsed_time(e) / k
+        per_view = []
+        for _ in range(3):
+            r.render(out=out, options=r.make_options(graph=True, **kw))
+            per_view += r.view_times()
+        return kw, {"views_per_s": n_views * 1000.0 / ms, "ms_per_batch": ms,
+                    "view_ms_p50": float(np.percentile(per_view, 50)),
+                    "view_ms_p99": float(np.percentile(per_view, 99)),
+                    "tile": [o.tile_w, o.tile_h], "schedule": "queue" if o.schedule else "grid",
+                    "batch_depth": int(o.batch_depth)}
+
+    kw_thr, thr = timed(o_thr)
+    _, lat = timed(o_lat)
+    # roofline of the batch's rasterizer: counted FP32 work over its event time
+    stage = {}
+    for _ in range(3):
+        r.render(profile=True, **kw_thr)
+        for kk, v in r.last_stats["stage_ms"].items():
+            stage[kk] = stage.get(kk, 0.0) + v / 3
+    r.render(count=True, **kw_thr)
+    work = {kk: r.last_stats[kk] for kk in ("leader_tests", "pairs_evaluated", "pairs_blended")}
+    ops = 8 * (work["pairs_evaluated"] + work["leader_tests"]) + 7 * work["pairs_blended"]
+    achieved = ops / (stage["raster"] / 1000.0) / 1e12
+    res = dict(thr)
+    res.update({
+        "latency_tuned": lat, "autotune": {"throughput": tune_thr, "latency": tune_lat, "seconds": tune_s},
+        "views": n_views, "instances": r.last_stats["n_instances"] if r.last_stats else None,
+        "stage_ms": {kk: round(v, 4) for kk, v in stage.items()},
+        "roofline": {"bound": "alu", "kernel": "raster_fwd (CR 2x2, all views of the batch)", "unit": "TFLOP/s",
+                     "achieved": achieved, "peak": pipe_peaks["fp32_tops"],
+                     "frac": achieved / pipe_peaks["fp32_tops"], "raster_ms": stage["raster"],
+                     "ops": ops, "work": work},
+        "workload": (f"multiview_2m: {args.multiview_n} Gaussians (unbounded-style), {n_views} cameras with "
+                     f"resolutions from {{640x360, 1280x720, 1920x1080}} at radius 3-6, one CUDA-graph launch "
+                     f"per batch, CR + opacity filter, scene in spatial order; per-view ms = start of "
+                     f"preprocessing to the view's last tile; configuration from seele_autotune_ex")})
     r.close()
     return res
 
@@ -911,7 +942,7 @@ def run_gpu(args):
     # 1M Gaussians shaped as the clustered scene, 1280x720, target rendered
     # from attributes perturbed by N(0, 0.01)
     fwd_bwd = _fwd_bwd(args, local)
-    multiview = _multiview(args, local) if args.multiview_n > 0 else None
+    multiview = _multiview(args, local, pipe_peaks) if args.multiview_n > 0 else None
     ablation = _ablation(args, local) if args.ablation_n > 0 else None
     sensitivity = _sensitivity(args, local) if args.ablation_n > 0 else None
 
@@ -936,8 +967,11 @@ def run_gpu(args):
         "e2e": {k: e2e[k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step")},
         "e2e_resident_scene_fps": e2e["resident_scene"]["value"],
         "async_fps": fps_async, "batch8_fps": fps_batch8, "two_stream_fps": fps_two_streams,
-        "multiview": ({k: multiview[k] for k in ("views_per_s", "view_ms_p50", "view_ms_p99")}
-                      if multiview else None),
+        "multiview": ({**{k: multiview[k] for k in ("views_per_s", "view_ms_p50", "view_ms_p99", "tile",
+                                                     "schedule", "batch_depth")},
+                       "latency_tuned": {k: multiview["latency_tuned"][k] for k in
+                                         ("views_per_s", "view_ms_p50", "view_ms_p99", "schedule", "batch_depth")},
+                       "raster_frac": round(multiview["roofline"]["frac"], 4)} if multiview else None),
         "peaks": {k: (round(v, 3) if isinstance(v, float) else v) for k, v in pipe_peaks.items()},
         "gpu_launches": int(kernels_per_frame * args.steps),
         "clocks": clock_info,
@@ -984,6 +1018,7 @@ def main():
     ap.add_argument("--multiview-n", type=int, default=2_000_000, help="0 skips the multi-view measurement")
     ap.add_argument("--ablation-n", type=int, default=500_000, help="0 skips the ablation")
     ap.add_argument("--details", default=None, help="also write the long-form results (JSON) to this file")
+    ap.add_argument("--tune-cache", default=None, help="JSON cache file of the batched autotuner")
     ap.add_argument("--n-gauss", type=int, default=3_000_000,
                     help="scene size (3M is the benchmark; smaller sizes are for profiling captures)")
     args = ap.parse_args()

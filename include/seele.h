@@ -127,6 +127,17 @@ enum { SEELE_TILES_RECT = 0, SEELE_TILES_ELLIPSE = 1 };
  * A backward pass after a BLOCKS render first re-bins the frame by tiles. */
 enum { SEELE_BIN_TILES = 0, SEELE_BIN_BLOCKS = 1 };
 
+/* Rasterizer schedule (not in the paper: how many cameras' tiles share the
+ * GPU).  GRID: one CTA per list unit, launched longest lists first.  QUEUE:
+ * one resident wave of CTAs that pull units from an atomic queue; the queue
+ * takes the cameras in groups of batch_depth (the cameras with the least
+ * rasterization work first: list lengths times the tiles that walk them),
+ * each group's units longest lists first, so that the views of
+ * an early group are finished before the next group starts -- per-view
+ * latency falls while each group still balances its own tiles.  batch_depth
+ * 0 puts every camera in one group (then QUEUE orders like GRID). */
+enum { SEELE_SCHEDULE_GRID = 0, SEELE_SCHEDULE_QUEUE = 1 };
+
 /* Render flags */
 enum {
     SEELE_RENDER_ASYNC = 1,       /* do not synchronise; see seele_render */
@@ -168,6 +179,8 @@ typedef struct {
     int32_t flags;                /* SEELE_RENDER_* */
     int32_t tile_test;            /* SEELE_TILES_ELLIPSE (default) or SEELE_TILES_RECT */
     int32_t binning;              /* SEELE_BIN_BLOCKS (default) or SEELE_BIN_TILES */
+    int32_t schedule;             /* SEELE_SCHEDULE_GRID (default) or SEELE_SCHEDULE_QUEUE */
+    int32_t batch_depth;          /* QUEUE: cameras per group, 0 = all (default) */
 } seele_options;
 
 /* Per-render statistics (all cameras of the call). */
@@ -195,12 +208,15 @@ typedef struct {
 
 /* Fills *opt with: PLAIN, 2x2 group, 16x16 tiles, filters off, M = 3,
  * alpha_theta = 1/255 (Sec. 3.1), clamp 0.99, Gamma_theta = 1e-4, flags 0,
- * ellipse tile test, block binning. */
+ * ellipse tile test, block binning, grid schedule. */
 void seele_default_options(seele_options* opt);
 
 /* Creates a context on CUDA device `device` that enqueues on `cuda_stream`
  * (a cudaStream_t; NULL = legacy default stream).  *out receives the context,
- * owned by the caller and released with seele_destroy. */
+ * owned by the caller and released with seele_destroy.  (The paper's renderer
+ * state: the trained model and the per-frame buffers of Sec. 3.1's three
+ * steps live in the context.)  Errors: SEELE_ERR_ARG for a NULL out or a
+ * device that does not exist (no device at all included). */
 seele_status seele_create(seele_ctx** out, int device, void* cuda_stream);
 
 /* Releases every device buffer of the context.  NULL is ignored. */
@@ -278,7 +294,10 @@ seele_status seele_get_stream_stats(const seele_ctx* ctx, seele_stream_stats* ou
  * opt-independent M = n_neighbors(3) centroids nearest to it. */
 seele_status seele_set_cameras(seele_ctx* ctx, const seele_camera* cams, int32_t n);
 
-/* Renders every camera set by seele_set_cameras.
+/* Renders every camera set by seele_set_cameras: Sec. 3.1's preprocessing,
+ * sorting and tile rasterization (Eqns. 1-2), with the options' hybrid
+ * preprocessing (Sec. 3.3, Eqns. 3-5) and contribution-aware rasterization
+ * (Sec. 3.4, Algorithm 1).
  *   out_rgb  host or device, [sum_j 3 W_j H_j] planar per camera (see top)
  *   out_T    host, device or NULL, [sum_j W_j H_j] final transmittance
  *   stats    host or NULL
@@ -298,7 +317,8 @@ seele_status seele_render(seele_ctx* ctx, const seele_options* opt, float* out_r
 seele_status seele_synchronize(seele_ctx* ctx);
 
 /* Gradient of sum(dL_drgb * rgb) for the last seele_render (same scene,
- * cameras and options; else SEELE_ERR_STATE).  dL_drgb is device memory in
+ * cameras and options; else SEELE_ERR_STATE), for the fine-tuning of
+ * Sec. 3.5.  dL_drgb is device memory in
  * the out_rgb layout.  Skip and stop decisions of the forward pass are held
  * fixed (Sec. 3.5: hybrid preprocessing and the CR skips are left out of
  * the gradient);
@@ -348,11 +368,41 @@ seele_status seele_get_debug_view(const seele_ctx* ctx, seele_debug_view* out);
  * the stream. */
 seele_status seele_get_view_times(const seele_ctx* ctx, float* out_ms, int32_t n);
 
-/* Chooses the tile shape (16x16, 32x8, 32x16 or 8x8) that renders the current
- * scene and cameras fastest with *inout's other options, by timing a few
+/* Chooses the tile shape (16x16, 32x8, 32x16 or 8x8; Sec. 3.1 renders
+ * "tile by tile", the tile size is the renderer's choice) that renders the
+ * current scene and cameras fastest with *inout's other options, by timing a few
  * renders of each; writes it into *inout and the time per render into
- * *best_ms (nullable).  Leaves no render state behind. */
+ * *best_ms (nullable).  Leaves no render state behind.  (Batched multi-view
+ * frames are not in the paper; its renders are one camera at a time.) */
 seele_status seele_autotune(seele_ctx* ctx, seele_options* inout, float* best_ms);
+
+/* What seele_autotune_ex minimises over the renders it times. */
+enum { SEELE_TUNE_BATCH_MS = 0, SEELE_TUNE_VIEW_P50 = 1, SEELE_TUNE_VIEW_P99 = 2 };
+
+typedef struct {
+    float batch_ms;               /* device time of one render of all cameras */
+    float view_p50_ms;            /* per-view completion times (seele_get_view_times) over */
+    float view_p99_ms;            /*   the cameras of the timed renders: median, 99th pct. */
+    int32_t from_cache;           /* 1: the choice came from the cache, nothing was timed */
+    int32_t candidates;           /* configurations timed */
+} seele_tune_result;
+
+/* The batched multi-view autotuner (not in the paper): tile shape, then
+ * schedule and batch depth.  Stage 1 times the four tile shapes with the
+ * GRID schedule (batch time); stage 2, with the best shape, times GRID and
+ * QUEUE with batch_depth 0 and n/2, n/4, ... 1 (at most 8 depths) and keeps
+ * the configuration with the least `objective`.  Each candidate: two
+ * warm-up renders, five timed CUDA-graph renders (batch time), and the view
+ * times of those renders.
+ *   cache_path  NULL, or a JSON file of earlier choices keyed by the device
+ *               (name, SM count), the scene size (ceil log2 n), the cameras'
+ *               resolutions, the render options that shape the work and the
+ *               objective; a hit is returned without timing, a miss is timed
+ *               and written back (the file is replaced atomically).
+ * Writes the choice into *inout (tile_w, tile_h, schedule, batch_depth) and
+ * the measurements into *result (nullable).  Leaves no render state behind. */
+seele_status seele_autotune_ex(seele_ctx* ctx, seele_options* inout, int32_t objective, const char* cache_path,
+                               seele_tune_result* result);
 
 /* Builds the offline view-dependent representation of the loaded scene
  * (Sec. 3.3 "Offline Clustering").
@@ -378,6 +428,11 @@ seele_status seele_autotune(seele_ctx* ctx, seele_options* inout, float* best_ms
  *   out_assign     host or NULL, [n_poses] cluster of each pose
  * Synchronous; leaves the context's cameras as they were and no render
  * state behind. */
+seele_status seele_build_view_clusters(seele_ctx* ctx, const seele_camera* poses, int32_t n_poses,
+                                       int32_t n_clusters, int32_t top_k, const double* uniforms,
+                                       int32_t max_iter, float* out_centroids, float* out_pos_scale,
+                                       uint32_t* out_mask, int32_t* out_assign);
+
 /* Contribution skew of the current cameras (Sec. 1 "Rendering
  * Inefficiency", Sec. 3.4 "Motivation"): the cameras are rendered with the
  * plain rules (Sec. 3.1; no opacity or cluster filter, tile lists) and, per
@@ -400,10 +455,6 @@ seele_status seele_contribution_skew(seele_ctx* ctx, const seele_options* opt, f
                                      uint32_t* out_blended, uint32_t* out_walked, float* out_total,
                                      uint32_t* out_listed);
 
-seele_status seele_build_view_clusters(seele_ctx* ctx, const seele_camera* poses, int32_t n_poses,
-                                       int32_t n_clusters, int32_t top_k, const double* uniforms,
-                                       int32_t max_iter, float* out_centroids, float* out_pos_scale,
-                                       uint32_t* out_mask, int32_t* out_assign);
 
 /* Message of the last failed call on this context (library-owned). */
 const char* seele_last_error(const seele_ctx* ctx);

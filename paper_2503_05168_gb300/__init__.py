@@ -192,12 +192,16 @@ class Renderer:
     @staticmethod
     def make_options(mode="plain", group=(2, 2), tile=(16, 16), opacity_filter=False, cluster_filter=False,
                      n_neighbors=3, sync=True, profile=False, count=False, graph=False, tile_test="ellipse",
-                     binning="blocks", **kw) -> _abi.Options:
+                     binning="blocks", schedule="grid", batch_depth=0, **kw) -> _abi.Options:
         o = default_options()
         if tile_test not in ("ellipse", "rect"):
             raise ValueError("tile_test must be 'ellipse' or 'rect'")
         if binning not in ("blocks", "tiles"):
             raise ValueError("binning must be 'blocks' or 'tiles'")
+        if schedule not in ("grid", "queue"):
+            raise ValueError("schedule must be 'grid' or 'queue'")
+        o.schedule = _abi.SCHEDULE_QUEUE if schedule == "queue" else _abi.SCHEDULE_GRID
+        o.batch_depth = int(batch_depth)
         o.tile_test = _abi.TILES_ELLIPSE if tile_test == "ellipse" else _abi.TILES_RECT
         o.binning = _abi.BIN_BLOCKS if binning == "blocks" else _abi.BIN_TILES
         o.mode = _abi.MODE_CR if mode == "cr" else _abi.MODE_PLAIN
@@ -250,6 +254,19 @@ class Renderer:
         self._sync_stream()
         self._check(lib().seele_autotune(self._h, ctypes.byref(o), ctypes.byref(ms)))
         return o, ms.value
+
+    def autotune_ex(self, objective: str = "batch", cache: str | None = None,
+                    options: _abi.Options | None = None, **kw):
+        """seele_autotune_ex: tile shape, then schedule and batch depth for
+        ``objective`` ("batch", "p50" or "p99"), through the JSON ``cache``
+        file if given.  Returns (options, result dict)."""
+        objs = {"batch": _abi.TUNE_BATCH_MS, "p50": _abi.TUNE_VIEW_P50, "p99": _abi.TUNE_VIEW_P99}
+        o = options if options is not None else self.make_options(**kw)
+        res = _abi.TuneResult()
+        self._sync_stream()
+        self._check(lib().seele_autotune_ex(self._h, ctypes.byref(o), objs[objective],
+                                            None if cache is None else str(cache).encode(), ctypes.byref(res)))
+        return o, {f: getattr(res, f) for f, _ in _abi.TuneResult._fields_}
 
     def render_backward(self, dL_drgb) -> dict:
         """Gradients of sum(dL_drgb * rgb) for the last render (CUDA tensors in

@@ -17,6 +17,8 @@ SCENE_COPY, SCENE_BORROW, SCENE_SPATIAL = 0, 1, 2
 MODE_PLAIN, MODE_CR = 0, 1
 TILES_RECT, TILES_ELLIPSE = 0, 1
 BIN_TILES, BIN_BLOCKS = 0, 1
+SCHEDULE_GRID, SCHEDULE_QUEUE = 0, 1
+TUNE_BATCH_MS, TUNE_VIEW_P50, TUNE_VIEW_P99 = 0, 1, 2
 RENDER_ASYNC = 1
 RENDER_PROFILE = 2
 RENDER_COUNT = 4
@@ -44,7 +46,8 @@ class Options(ctypes.Structure):
                 ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("opacity_filter", ctypes.c_int32),
                 ("cluster_filter", ctypes.c_int32), ("n_neighbors", ctypes.c_int32),
                 ("alpha_min", ctypes.c_float), ("alpha_max", ctypes.c_float), ("t_stop", ctypes.c_float),
-                ("flags", ctypes.c_int32), ("tile_test", ctypes.c_int32), ("binning", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("tile_test", ctypes.c_int32), ("binning", ctypes.c_int32),
+                ("schedule", ctypes.c_int32), ("batch_depth", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -58,6 +61,11 @@ class StreamStats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in ("resident_bytes", "full_bytes", "n_shared", "slot_capacity", "n_slots",
                                               "n_chunks", "frames", "loads_sync", "loads_prefetched",
                                               "prefetch_hits", "resident_hits")]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("batch_ms", ctypes.c_float), ("view_p50_ms", ctypes.c_float), ("view_p99_ms", ctypes.c_float),
+                ("from_cache", ctypes.c_int32), ("candidates", ctypes.c_int32)]
 
 
 class Peaks(ctypes.Structure):
@@ -93,6 +101,8 @@ PROTOTYPES = {
     "seele_last_error": (ctypes.c_char_p, [P]),
     "seele_get_view_times": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_float), ctypes.c_int32]),
     "seele_autotune": (ctypes.c_int, [P, ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_float)]),
+    "seele_autotune_ex": (ctypes.c_int, [P, ctypes.POINTER(Options), ctypes.c_int32, ctypes.c_char_p,
+                                         ctypes.POINTER(TuneResult)]),
     "seele_sort_tile_instances_noalloc": (ctypes.c_int, [P, P, ctypes.c_uint32, ctypes.c_uint32, P, P, P, P]),
     "seele_build_view_clusters": (ctypes.c_int, [P, ctypes.POINTER(Camera), ctypes.c_int32, ctypes.c_int32,
                                                  ctypes.c_int32, P, ctypes.c_int32, P, P, P, P]),

@@ -537,6 +537,8 @@ struct FrameInfo {
     bool blocks = false, short_keys = false, rgb_dev = true, T_dev = true;
     int tile_bits = 1;         // key bits of a list unit id
     uint32_t cnt_words = 0;
+    bool queue = false;        // the persistent rasterizer, units in camera groups
+    int batch_depth = 0;
     FrameParams fp{};
 };
 
@@ -573,8 +575,13 @@ int enqueue_tile_sort(seele_ctx* c, const FrameInfo& f, const uint32_t* order, c
         launch_mask_summary(masks[fin], st, ptr<uint32_t>(c->msum), (uint32_t)(cap / 32 + 1), s);
         ++launches;
     }
-    // CTAs take the units with the longest lists first
-    launch_block_order(run, run + units, (uint32_t)units, ptr<uint32_t>(c->border), s);
+    // CTAs take the units with the longest lists first (the persistent
+    // rasterizer: camera group by camera group)
+    if (f.queue)
+        launch_view_order(run, run + units, (uint32_t)units, cams, f.ncam, f.blocks, f.batch_depth,
+                          ptr<uint32_t>(c->border), s);
+    else
+        launch_block_order(run, run + units, (uint32_t)units, ptr<uint32_t>(c->border), s);
     if (cudaPeekAtLastError() != cudaSuccess) return -1;
     ++launches;
     return fin;
@@ -600,6 +607,9 @@ seele_status check_options(seele_ctx* c, const seele_options* opt) {
         return fail(c, SEELE_ERR_ARG, "bad tile_test");
     if (opt->binning != SEELE_BIN_TILES && opt->binning != SEELE_BIN_BLOCKS)
         return fail(c, SEELE_ERR_ARG, "bad binning");
+    if (opt->schedule != SEELE_SCHEDULE_GRID && opt->schedule != SEELE_SCHEDULE_QUEUE)
+        return fail(c, SEELE_ERR_ARG, "bad schedule");
+    if (opt->batch_depth < 0) return fail(c, SEELE_ERR_ARG, "batch_depth must be >= 0");
     return SEELE_OK;
 }
 
@@ -867,6 +877,7 @@ seele_status enqueue_frame(seele_ctx* c, const seele_options* opt, const FrameIn
     const bool ckpt = !f.blocks && !count && c->skew_frac <= 0.0 && c->topk_k <= 0;
     ra.ckpt = ckpt ? ptr<float4>(c->ckpt) : nullptr;
     ra.cfin = ckpt ? ptr<float4>(c->cfin) : nullptr;
+    ra.queue = (f.queue && !count) ? &st->queue : nullptr;
     SEELE_MARK(SEELE_STAGE_RASTER);
     if (c->skew_frac > 0.0) {
         uint32_t* sk = ptr<uint32_t>(c->skew);
@@ -910,6 +921,8 @@ void seele_default_options(seele_options* o) {
     o->flags = 0;
     o->tile_test = SEELE_TILES_ELLIPSE;
     o->binning = SEELE_BIN_BLOCKS;
+    o->schedule = SEELE_SCHEDULE_GRID;
+    o->batch_depth = 0;
 }
 
 seele_status seele_create(seele_ctx** out, int device, void* cuda_stream) {
@@ -1320,6 +1333,8 @@ seele_status seele_render(seele_ctx* c, const seele_options* opt, float* out_rgb
         if (sp != SEELE_OK) return sp;
     }
     f.blocks = opt->binning == SEELE_BIN_BLOCKS;
+    f.queue = opt->schedule == SEELE_SCHEDULE_QUEUE && f.ncam <= kViewOrderMaxCams;
+    f.batch_depth = opt->batch_depth;
     f.units_total = f.blocks ? f.blocks_total : f.tiles_total;
     f.short_keys = f.units_total <= kShortKeyMaxTiles;
     f.tile_bits = std::max(1, bits_for(f.units_total > 0 ? f.units_total - 1 : 0));
@@ -1504,6 +1519,166 @@ seele_status seele_autotune(seele_ctx* c, seele_options* inout, float* best_ms) 
     inout->tile_h = bh;
     if (best_ms) *best_ms = best;
     c->rendered = false;
+    return SEELE_OK;
+}
+
+// The batched multi-view autotuner: tile shape (GRID, batch time), then
+// schedule and batch depth for the objective; see seele.h.
+seele_status seele_autotune_ex(seele_ctx* c, seele_options* inout, int32_t objective, const char* cache_path,
+                               seele_tune_result* result) {
+    if (!c || !inout) return SEELE_ERR_ARG;
+    if (objective < SEELE_TUNE_BATCH_MS || objective > SEELE_TUNE_VIEW_P99)
+        return fail(c, SEELE_ERR_ARG, "bad objective");
+    if (!c->has_scene || c->cams.empty()) return fail(c, SEELE_ERR_STATE, "autotune needs a scene and cameras");
+    seele_status st0 = check_options(c, inout);
+    if (st0 != SEELE_OK) return st0;
+    SEELE_CUDA(c, cudaSetDevice(c->device));
+    const int ncam = (int)c->cams.size();
+    // cache key: device, scene size bucket, resolutions, work-shaping options, objective
+    std::string key;
+    {
+        cudaDeviceProp prop{};
+        SEELE_CUDA(c, cudaGetDeviceProperties(&prop, c->device));
+        std::string name = prop.name;
+        for (char& ch : name)
+            if (ch == '"' || ch == '\\' || ch == ' ') ch = '_';
+        int lg = 0;
+        while ((1ll << lg) < c->n) ++lg;
+        std::vector<std::pair<int, int>> res;
+        for (const auto& k : c->cams) res.push_back({k.width, k.height});
+        std::sort(res.begin(), res.end());
+        char buf[256];
+        std::snprintf(buf, sizeof buf, "%s|sm%d|n2^%d|deg%d|mode%d|g%dx%d|op%d|cl%d|bin%d|tt%d|obj%d|cams", name.c_str(),
+                      prop.multiProcessorCount, lg, c->sh_degree, inout->mode, inout->group_w, inout->group_h,
+                      inout->opacity_filter, inout->cluster_filter, inout->binning, inout->tile_test, objective);
+        key = buf;
+        for (size_t i = 0; i < res.size();) {
+            size_t j = i;
+            while (j < res.size() && res[j] == res[i]) ++j;
+            std::snprintf(buf, sizeof buf, ":%dx%dx%d", (int)(j - i), res[i].first, res[i].second);
+            key += buf;
+            i = j;
+        }
+    }
+    seele_tune_result r{};
+    TuneEntry hit;
+    if (tune_cache_lookup(cache_path, key, &hit)) {
+        inout->tile_w = hit.tile_w;
+        inout->tile_h = hit.tile_h;
+        inout->schedule = hit.schedule;
+        inout->batch_depth = hit.batch_depth;
+        r.batch_ms = hit.batch_ms;
+        r.view_p50_ms = hit.p50_ms;
+        r.view_p99_ms = hit.p99_ms;
+        r.from_cache = 1;
+        if (result) *result = r;
+        return SEELE_OK;
+    }
+    size_t pix = 0;
+    for (const auto& k : c->cams) pix += (size_t)k.width * k.height;
+    float* dev_out = nullptr;
+    if (cudaMalloc(&dev_out, 12 * pix) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(c, SEELE_ERR_OOM, "autotune output buffer");
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    struct Measured {
+        float batch = INFINITY, p50 = INFINITY, p99 = INFINITY;
+        float score(int obj) const { return obj == SEELE_TUNE_VIEW_P50 ? p50 : obj == SEELE_TUNE_VIEW_P99 ? p99 : batch; }
+    };
+    std::vector<float> views(ncam);
+    auto measure = [&](seele_options o, Measured* m) -> seele_status {
+        o.flags = 0;
+        seele_status st = SEELE_OK;
+        for (int w = 0; w < 2 && st == SEELE_OK; ++w) st = seele_render(c, &o, dev_out, nullptr, nullptr);
+        o.flags = SEELE_RENDER_ASYNC | SEELE_RENDER_GRAPH;
+        if (st == SEELE_OK) st = seele_render(c, &o, dev_out, nullptr, nullptr);  // captures the graph
+        if (st == SEELE_OK) st = seele_synchronize(c);
+        if (st != SEELE_OK) return st;
+        cudaEventRecord(e0, c->stream);
+        for (int k = 0; k < 5 && st == SEELE_OK; ++k) st = seele_render(c, &o, dev_out, nullptr, nullptr);
+        cudaEventRecord(e1, c->stream);
+        if (st == SEELE_OK) st = seele_synchronize(c);
+        if (st != SEELE_OK) return st;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        m->batch = ms / 5.f;
+        std::vector<float> all;
+        for (int k = 0; k < 3 && st == SEELE_OK; ++k) {
+            st = seele_render(c, &o, dev_out, nullptr, nullptr);
+            if (st == SEELE_OK) st = seele_get_view_times(c, views.data(), ncam);
+            all.insert(all.end(), views.begin(), views.end());
+        }
+        if (st != SEELE_OK) return st;
+        std::sort(all.begin(), all.end());
+        m->p50 = all[all.size() / 2];
+        m->p99 = all[std::min(all.size() - 1, (size_t)std::ceil(0.99 * all.size()) - 1)];
+        ++r.candidates;
+        return SEELE_OK;
+    };
+    seele_status status = SEELE_OK;
+    seele_options best = *inout;
+    Measured bm;
+    // stage 1: the tile shape, GRID schedule, batch time
+    static const int shapes[][2] = {{16, 16}, {32, 8}, {32, 16}, {8, 8}};
+    for (const auto& sh : shapes) {
+        seele_options o = *inout;
+        o.tile_w = sh[0];
+        o.tile_h = sh[1];
+        o.schedule = SEELE_SCHEDULE_GRID;
+        o.batch_depth = 0;
+        Measured m;
+        status = measure(o, &m);
+        if (status != SEELE_OK) break;
+        if (m.batch < bm.batch) {
+            bm = m;
+            best = o;
+        }
+    }
+    // stage 2: schedule and batch depth with that shape, for the objective
+    if (status == SEELE_OK && ncam <= kViewOrderMaxCams) {
+        std::vector<int> depths = {0};
+        for (int d = ncam / 2; d >= 1 && depths.size() < 8; d /= 2) depths.push_back(d);
+        const seele_options base = best;
+        for (int d : depths) {
+            seele_options o = base;
+            o.schedule = SEELE_SCHEDULE_QUEUE;
+            o.batch_depth = d;
+            Measured m;
+            status = measure(o, &m);
+            if (status != SEELE_OK) break;
+            if (m.score(objective) < bm.score(objective)) {
+                bm = m;
+                best = o;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(dev_out);
+    c->rendered = false;
+    if (status != SEELE_OK) return status;
+    inout->tile_w = best.tile_w;
+    inout->tile_h = best.tile_h;
+    inout->schedule = best.schedule;
+    inout->batch_depth = best.batch_depth;
+    r.batch_ms = bm.batch;
+    r.view_p50_ms = bm.p50;
+    r.view_p99_ms = bm.p99;
+    if (result) *result = r;
+    if (cache_path) {
+        TuneEntry e;
+        e.tile_w = best.tile_w;
+        e.tile_h = best.tile_h;
+        e.schedule = best.schedule;
+        e.batch_depth = best.batch_depth;
+        e.batch_ms = bm.batch;
+        e.p50_ms = bm.p50;
+        e.p99_ms = bm.p99;
+        if (!tune_cache_store(cache_path, key, e)) return fail(c, SEELE_ERR_ARG, "cannot write the cache file");
+    }
     return SEELE_OK;
 }
 

@@ -12,7 +12,8 @@
 //   accumulated behind entry j, gives
 //     dC/dc_j = T_j alpha_j,   dC/dalpha_j = T_j c_j - S / (1 - alpha_j).
 //   Gradients w.r.t. the record (u, v, cA, cB, cC, log2 o, r, g, b) are
-//   summed over the warp's pixels and added with one atomic per value.
+//   summed over the warp's pixels and added with one atomic per value.  The
+//   pixels of a thread run branch-free under a per-pixel predicate.
 // preprocess_bwd_kernel: one thread per Gaussian, summing over cameras, runs
 //   the chain rule back through the raster record, the conic, the EWA
 //   projection, the covariance, the quaternion and the SH colour.
@@ -26,6 +27,12 @@ constexpr float kLn2 = 0.69314718055994531f;
 __device__ __forceinline__ float ex2_approx_b(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rcp_approx_b(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
 
@@ -180,6 +187,42 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
             };
             float du = 0.f, dv = 0.f, dcA = 0.f, dcB = 0.f, dcC = 0.f, dlo = 0.f, dr = 0.f, dg = 0.f, db = 0.f;
             bool any = false;
+            const bool clampable = Cc.w != 0.f;  // the record's alpha can reach alpha_max
+            // One pixel of an entry, branch-free: `m` says whether the forward
+            // pass blended the entry into the pixel (before its last blend,
+            // inside the support, alpha >= alpha_theta, its group kept the
+            // entry); for the others every update below adds zero or keeps
+            // the value, so the 2x2 pixels of a thread never diverge.
+            auto pixel = [&](int p, int pi, int pj, bool lead) {
+                const float e = expo(pi, pj);
+                const bool m = lead && j < last[p] && e >= B.z;
+                float al = ex2_approx_b(e);
+                if (clampable) al = fminf(amax, al);
+                // 1 - alpha >= 0.01 (the clamp): the approximate reciprocal
+                // keeps T_before within a few ulp per entry
+                const float inv = rcp_approx_b(1.f - al);
+                const float Tb = T[p] * inv;  // transmittance before this entry
+                const float wgt = m ? Tb * al : 0.f;
+                const float dal = g0[p] * (Tb * Cc.x - S0[p] * inv) + g1[p] * (Tb * Cc.y - S1[p] * inv) +
+                                  g2[p] * (Tb * Cc.z - S2[p] * inv);
+                dr = fmaf(wgt, g0[p], dr);
+                dg = fmaf(wgt, g1[p], dg);
+                db = fmaf(wgt, g2[p], db);
+                S0[p] = fmaf(wgt, Cc.x, S0[p]);
+                S1[p] = fmaf(wgt, Cc.y, S1[p]);
+                S2[p] = fmaf(wgt, Cc.z, S2[p]);
+                T[p] = m ? Tb : T[p];
+                any |= m;
+                // at the clamp alpha is constant: no gradient through e
+                const float de = (m && (!clampable || al < amax)) ? dal * al * kLn2 : 0.f;
+                const float ddx = dx + (float)pi, ddy = dy + (float)pj;
+                du -= de * (2.f * A.z * ddx + A.w * ddy);
+                dv -= de * (A.w * ddx + 2.f * B.x * ddy);
+                dcA = fmaf(de, ddx * ddx, dcA);
+                dcB = fmaf(de, ddx * ddy, dcB);
+                dcC = fmaf(de, ddy * ddy, dcC);
+                dlo += de;
+            };
 #pragma unroll
             for (int gy = 0; gy < PH / GHL; ++gy)
 #pragma unroll
@@ -205,36 +248,7 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
 #pragma unroll
                         for (int i = 0; i < GWL; ++i) {
                             const int pi = gx * GWL + i, pj = gy * GHL + jj;
-                            const int p = pj * PW + pi;
-                            if (!(j < last[p])) continue;
-                            const float e = expo(pi, pj);
-                            if (e < B.z) continue;  // skipped in the forward pass too
-                            const float al = fminf(amax, ex2_approx_b(e));
-                            // one correctly rounded reciprocal instead of four
-                            // divisions (1 - alpha >= 0.01 at the clamp)
-                            const float inv = __frcp_rn(1.f - al);
-                            const float Tb = T[p] * inv;  // transmittance before this entry
-                            const float wgt = Tb * al;
-                            const float dal = g0[p] * (Tb * Cc.x - S0[p] * inv) + g1[p] * (Tb * Cc.y - S1[p] * inv) +
-                                              g2[p] * (Tb * Cc.z - S2[p] * inv);
-                            dr = fmaf(wgt, g0[p], dr);
-                            dg = fmaf(wgt, g1[p], dg);
-                            db = fmaf(wgt, g2[p], db);
-                            S0[p] = fmaf(wgt, Cc.x, S0[p]);
-                            S1[p] = fmaf(wgt, Cc.y, S1[p]);
-                            S2[p] = fmaf(wgt, Cc.z, S2[p]);
-                            T[p] = Tb;
-                            any = true;
-                            if (al < amax) {  // at the clamp alpha is constant
-                                const float de = dal * al * kLn2;
-                                const float ddx = dx + (float)pi, ddy = dy + (float)pj;
-                                du -= de * (2.f * A.z * ddx + A.w * ddy);
-                                dv -= de * (A.w * ddx + 2.f * B.x * ddy);
-                                dcA = fmaf(de, ddx * ddx, dcA);
-                                dcB = fmaf(de, ddx * ddy, dcB);
-                                dcC = fmaf(de, ddy * ddy, dcC);
-                                dlo += de;
-                            }
+                            pixel(pj * PW + pi, pi, pj, true);
                         }
                 }
             if (__any_sync(0xffffffffu, any)) {

@@ -287,8 +287,10 @@ void launch_block_order(const uint32_t* bstart, const uint32_t* bend, uint32_t n
 }
 
 // Cameras in groups for the persistent rasterizer (Sec. 3.1's tiles of many
-// views from one queue): the cameras are ranked by their total list length,
-// least first, and cut into groups of `depth`; the queue takes group after
+// views from one queue): the cameras are ranked by their rasterization work,
+// least first -- the list length of each unit times the tiles that walk it
+// (one for a tile, the image's tiles of a tile block) -- and cut into groups
+// of `depth`; the queue takes group after
 // group, each with its longest lists first, so the views of an early group
 // finish before later groups start (per-view latency) while each group still
 // balances its own tiles.  depth 0 (or >= n_cams): one group, the plain
@@ -299,7 +301,7 @@ __global__ void __launch_bounds__(1024) view_order_kernel(const uint32_t* __rest
                                                           const uint32_t* __restrict__ bend, uint32_t n_units,
                                                           const CamDev* __restrict__ cams, int n_cams, int blocks,
                                                           int depth, uint32_t* __restrict__ order) {
-    __shared__ uint32_t s_tot[kViewOrderMaxCams];
+    __shared__ unsigned long long s_tot[kViewOrderMaxCams];
     __shared__ uint8_t s_group[kViewOrderMaxCams];
     __shared__ uint32_t s_hist[kOrderGroups * kOrderBuckets];
     __shared__ uint32_t s_warp[32];
@@ -324,15 +326,26 @@ __global__ void __launch_bounds__(1024) view_order_kernel(const uint32_t* __rest
         const int frac = lg >= 2 ? (int)((v >> (lg - 2)) & 3u) : (int)((v << (2 - lg)) & 3u);
         return kOrderBuckets - 1 - min(kOrderBuckets - 1, lg * 4 + frac);
     };
+    // tiles that walk unit u's list
+    auto walkers = [&](uint32_t u, int c) -> uint32_t {
+        if (!blocks) return 1u;
+        const CamDev& C = cams[c];
+        const uint32_t lb = u - C.block_offset;
+        const int bx = (int)(lb % (uint32_t)C.blocks_x) * kBlockW, by = (int)(lb / (uint32_t)C.blocks_x) * kBlockH;
+        return (uint32_t)(min(kBlockW, C.tiles_x - bx) * min(kBlockH, C.tiles_y - by));
+    };
     for (int i = t; i < n_cams; i += blockDim.x) s_tot[i] = 0;
     for (int i = t; i < kOrderGroups * kOrderBuckets; i += blockDim.x) s_hist[i] = 0;
     __syncthreads();
-    for (uint32_t u = t; u < n_units; u += blockDim.x) atomicAdd(&s_tot[cam_of(u)], length(u));
+    for (uint32_t u = t; u < n_units; u += blockDim.x) {
+        const int c = cam_of(u);
+        atomicAdd(&s_tot[c], (unsigned long long)length(u) * walkers(u, c));
+    }
     __syncthreads();
     // rank by total (ties to the lower index), then the group of the rank
     const int d = (depth <= 0 || depth >= n_cams) ? n_cams : max(depth, (n_cams + kOrderGroups - 1) / kOrderGroups);
     for (int c = t; c < n_cams; c += blockDim.x) {
-        const uint32_t mine = s_tot[c];
+        const unsigned long long mine = s_tot[c];
         int rank = 0;
         for (int o = 0; o < n_cams; ++o) rank += (s_tot[o] < mine || (s_tot[o] == mine && o < c)) ? 1 : 0;
         s_group[c] = (uint8_t)(rank / d);

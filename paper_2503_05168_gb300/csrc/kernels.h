@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "common.cuh"
 
 namespace seele {
@@ -156,6 +158,14 @@ struct RasterArgs {
     uint32_t* queue = nullptr;
 };
 bool launch_raster_fwd(const RasterArgs& a, cudaStream_t s);
+
+// The multi-view autotuner's cache (tune_cache.cu): one configuration per key.
+struct TuneEntry {
+    int tile_w = 16, tile_h = 16, schedule = 0, batch_depth = 0;
+    float batch_ms = 0.f, p50_ms = 0.f, p99_ms = 0.f;
+};
+bool tune_cache_lookup(const char* path, const std::string& key, TuneEntry* out);
+bool tune_cache_store(const char* path, const std::string& key, const TuneEntry& e);
 
 struct RasterBwdArgs {
     const uint32_t* starts;

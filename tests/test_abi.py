@@ -57,7 +57,7 @@ def test_create_without_device_is_an_argument_error(lib):
 STRUCTS = {
     "seele_scene_desc": _abi.SceneDesc, "seele_camera": _abi.Camera, "seele_options": _abi.Options,
     "seele_stats": _abi.Stats, "seele_grads": _abi.Grads, "seele_debug_view": _abi.DebugView,
-    "seele_peaks": _abi.Peaks,
+    "seele_peaks": _abi.Peaks, "seele_tune_result": _abi.TuneResult,
 }
 
 

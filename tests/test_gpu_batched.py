@@ -142,3 +142,124 @@ def test_wide_batches_take_32_bit_unit_keys(Renderer, binning):
         np.testing.assert_array_equal(batch, single)
         assert np.count_nonzero(single) > 0
     r.close()
+
+
+# ------------------------------------------------- persistent queue schedule --
+
+MIXED = [(640, 360), (320, 180), (160, 90), (640, 360), (96, 96), (320, 180), (200, 120), (160, 90), (48, 32),
+         (320, 180)]
+
+
+def _mixed_scene():
+    # the unbounded-style scene of the batched workload, small: dense clusters
+    # and a far shell, cameras at radius 3-6 looking at the origin
+    sc, _ = scenegen.unbounded_3m(n=60_000)
+    rs = np.random.default_rng(17)
+    cams = []
+    for w, h in MIXED:
+        az, el, rad = rs.uniform(0, 2 * np.pi), rs.uniform(-0.5, 0.5), rs.uniform(3.0, 6.0)
+        eye = (rad * np.cos(az) * np.cos(el), -rad * np.sin(el), rad * np.sin(az) * np.cos(el))
+        cams.append(scenegen.look_at(eye, (0, 0, 0), w, h))
+    return sc, cams
+
+
+@pytest.mark.parametrize("mode", ["cr", "plain"])
+def test_mixed_resolution_batch_matches_oracle_per_camera(Renderer, mode):
+    """Ten cameras of five resolutions in one frame (grid and persistent queue
+    schedules, CUDA-graph replay): every camera against the oracle on sampled
+    tiles (the corner tiles, the ragged last row and column, the longest list
+    and random ones), decision-aware on every sampled pixel."""
+    import torch
+    sc, cams = _mixed_scene()
+    r = Renderer()
+    r.load_scene(sc)
+    r.set_cameras(cams)
+    kw = dict(mode=mode, opacity_filter=(mode == "cr"))
+    r.render(**kw)
+    out = torch.empty(3 * r.n_pixels, device="cuda")
+    r.render(out=out, schedule="queue", batch_depth=3, graph=True, sync=False, **kw)
+    r.render(out=out, schedule="queue", batch_depth=3, graph=True, sync=False, **kw)   # a replay
+    r.synchronize()
+    imgs = r.images(out)
+    grid_imgs = r.images(r.render(**kw))
+    s64 = oracle.Scene64.from_scene(sc)
+    oo = parity.oracle_options(mode, opacity_filter=(mode == "cr"))
+    rs = np.random.default_rng(5)
+    for ci, cam in enumerate(cams):
+        img = imgs[ci].cpu().numpy()
+        np.testing.assert_array_equal(img, grid_imgs[ci].cpu().numpy())
+        proj = oracle.preprocess(s64, cam, oo, nthreads=8)
+        tx_n, ty_n = oracle.tile_grid(cam, oo)
+        tiles = np.unique(np.concatenate([rs.choice(tx_n * ty_n, min(6, tx_n * ty_n), replace=False),
+                                          [0, tx_n - 1, (ty_n - 1) * tx_n, tx_n * ty_n - 1]]))
+        ref, _, (sub, gid, ranges) = parity.oracle_render_tiles(proj, cam, oo, tiles)
+        W, H = cam["width"], cam["height"]
+        pix = []
+        for t in tiles:
+            tx, ty = t % tx_n, t // tx_n
+            yy, xx = np.mgrid[16 * ty:min(16 * ty + 16, H), 16 * tx:min(16 * tx + 16, W)]
+            pix.append((yy * W + xx).reshape(-1))
+        rep = parity.check_render(img, None, ref, sub, gid, ranges, cam, oo, pixels=np.concatenate(pix))
+        assert rep["ok"], str((ci, rep))
+    r.close()
+
+
+@pytest.mark.parametrize("binning", ["blocks", "tiles"])
+@pytest.mark.parametrize("depth", [0, 1, 4])
+def test_queue_schedule_equals_grid_bit_for_bit(Renderer, binning, depth):
+    sc, _ = scenegen.uniform_10k()
+    cams = _cams(21, SIZES * 3)
+    r = Renderer()
+    r.load_scene(sc)
+    r.set_cameras(cams)
+    for mode in ("plain", "cr"):
+        a, ta = parity.gpu_render(r, mode=mode, binning=binning)
+        b, tb = parity.gpu_render(r, mode=mode, binning=binning, schedule="queue", batch_depth=depth)
+        for x, y in zip(a + ta, b + tb):
+            np.testing.assert_array_equal(x, y)
+    r.close()
+
+
+def test_queue_groups_finish_in_order(Renderer):
+    """batch_depth 1: cameras one at a time, least work first.  Six views that
+    see no Gaussian (empty tile lists) and six that see the scene, all
+    256x256: every empty view is finished before any loaded one; as one group
+    (batch_depth 0) the longest lists go first instead."""
+    sc, _ = scenegen.uniform_10k()
+    loaded = _cams(31, [(256, 256)] * 6)
+    empty = [scenegen.look_at((0.0, 0.0, -3.0 - 0.1 * i), (0.0, 0.0, -9.0), 256, 256) for i in range(6)]
+    cams = [c for pair in zip(loaded, empty) for c in pair]   # interleaved: loaded views at even indices
+    r = Renderer()
+    r.load_scene(sc)
+    r.set_cameras(cams)
+    r.render(mode="cr")
+    for _ in range(3):
+        r.render(mode="cr", schedule="queue", batch_depth=1)
+        t = np.asarray(r.view_times())
+        assert t[1::2].max() < t[0::2].min(), t
+    r.close()
+
+
+def test_autotune_ex_times_then_reads_its_cache(Renderer, tmp_path):
+    import json
+    sc, _ = scenegen.uniform_10k(n=5000)
+    cams = _cams(41, SIZES * 2)
+    r = Renderer()
+    r.load_scene(sc)
+    r.set_cameras(cams)
+    cache = tmp_path / "tune.json"
+    o1, res1 = r.autotune_ex(objective="p50", cache=cache, mode="cr", opacity_filter=True)
+    assert res1["from_cache"] == 0 and res1["candidates"] >= 5 and res1["batch_ms"] > 0
+    assert 0 < res1["view_p50_ms"] <= res1["view_p99_ms"]
+    assert (o1.tile_w, o1.tile_h) in {(16, 16), (32, 8), (32, 16), (8, 8)} and o1.schedule in (0, 1)
+    entries = json.loads(cache.read_text())
+    assert len(entries) == 1
+    o2, res2 = r.autotune_ex(objective="p50", cache=cache, mode="cr", opacity_filter=True)
+    assert res2["from_cache"] == 1
+    assert (o2.tile_w, o2.tile_h, o2.schedule, o2.batch_depth) == (o1.tile_w, o1.tile_h, o1.schedule, o1.batch_depth)
+    # another objective is another key
+    r.autotune_ex(objective="batch", cache=cache, mode="cr", opacity_filter=True)
+    assert len(json.loads(cache.read_text())) == 2
+    # the chosen options render
+    r.render(options=o2)
+    r.close()
