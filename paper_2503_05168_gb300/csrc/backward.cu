@@ -186,17 +186,47 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
                 return fmaf(fmaf(A.z, ddx, A.w * ddy), ddx, fmaf(B.x * ddy, ddy, B.y));
             };
             float du = 0.f, dv = 0.f, dcA = 0.f, dcB = 0.f, dcC = 0.f, dlo = 0.f, dr = 0.f, dg = 0.f, db = 0.f;
-            bool any = false;
             const bool clampable = Cc.w != 0.f;  // the record's alpha can reach alpha_max
-            // One pixel of an entry, branch-free: `m` says whether the forward
-            // pass blended the entry into the pixel (before its last blend,
-            // inside the support, alpha >= alpha_theta, its group kept the
-            // entry); for the others every update below adds zero or keeps
-            // the value, so the 2x2 pixels of a thread never diverge.
-            auto pixel = [&](int p, int pi, int pj, bool lead) {
-                const float e = expo(pi, pj);
-                const bool m = lead && j < last[p] && e >= B.z;
-                float al = ex2_approx_b(e);
+            // Which of the thread's pixels did the forward pass blend this
+            // entry into (before its last blend, inside the support, alpha >=
+            // alpha_theta, its group kept the entry)?  Cheap; the gradient
+            // terms below run only when some lane of the warp has one.
+            float ev[NP];
+            uint32_t mbits = 0;
+#pragma unroll
+            for (int gy = 0; gy < PH / GHL; ++gy)
+#pragma unroll
+                for (int gx = 0; gx < PW / GWL; ++gx) {
+                    bool need = false;
+#pragma unroll
+                    for (int jj = 0; jj < GHL; ++jj)
+#pragma unroll
+                        for (int i = 0; i < GWL; ++i) need |= j < last[(gy * GHL + jj) * PW + gx * GWL + i];
+                    bool lead = need;
+                    if (CR && need) {
+                        if (WHOLE) {
+                            const float lx = lx0 - A.x, ly = ly0 - A.y;
+                            lead = fmaf(fmaf(A.z, lx, A.w * ly), lx, fmaf(B.x * ly, ly, B.y)) >= B.z;
+                        } else {
+                            lead = expo(gx * GW, gy * GH) >= B.z;
+                        }
+                    }
+#pragma unroll
+                    for (int jj = 0; jj < GHL; ++jj)
+#pragma unroll
+                        for (int i = 0; i < GWL; ++i) {
+                            const int pi = gx * GWL + i, pj = gy * GHL + jj;
+                            const int p = pj * PW + pi;
+                            ev[p] = expo(pi, pj);
+                            mbits |= (lead && j < last[p] && ev[p] >= B.z) ? 1u << p : 0u;
+                        }
+                }
+            if (!__any_sync(0xffffffffu, mbits != 0u)) continue;
+            // One pixel of the entry, branch-free: for a pixel the entry was
+            // not blended into every update below adds zero or keeps the value.
+            auto pixel = [&](int p, int pi, int pj) {
+                const bool m = (mbits >> p) & 1u;
+                float al = ex2_approx_b(ev[p]);
                 if (clampable) al = fminf(amax, al);
                 // 1 - alpha >= 0.01 (the clamp): the approximate reciprocal
                 // keeps T_before within a few ulp per entry
@@ -212,7 +242,6 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
                 S1[p] = fmaf(wgt, Cc.y, S1[p]);
                 S2[p] = fmaf(wgt, Cc.z, S2[p]);
                 T[p] = m ? Tb : T[p];
-                any |= m;
                 // at the clamp alpha is constant: no gradient through e
                 const float de = (m && (!clampable || al < amax)) ? dal * al * kLn2 : 0.f;
                 const float ddx = dx + (float)pi, ddy = dy + (float)pj;
@@ -224,33 +253,10 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
                 dlo += de;
             };
 #pragma unroll
-            for (int gy = 0; gy < PH / GHL; ++gy)
+            for (int pj = 0; pj < PH; ++pj)
 #pragma unroll
-                for (int gx = 0; gx < PW / GWL; ++gx) {
-                    bool lead = true;
-                    if (CR) {
-                        bool need = false;
-#pragma unroll
-                        for (int jj = 0; jj < GHL; ++jj)
-#pragma unroll
-                            for (int i = 0; i < GWL; ++i) need |= j < last[(gy * GHL + jj) * PW + gx * GWL + i];
-                        if (!need) continue;
-                        if (WHOLE) {
-                            const float lx = lx0 - A.x, ly = ly0 - A.y;
-                            lead = fmaf(fmaf(A.z, lx, A.w * ly), lx, fmaf(B.x * ly, ly, B.y)) >= B.z;
-                        } else {
-                            lead = expo(gx * GW, gy * GH) >= B.z;
-                        }
-                    }
-                    if (!lead) continue;
-#pragma unroll
-                    for (int jj = 0; jj < GHL; ++jj)
-#pragma unroll
-                        for (int i = 0; i < GWL; ++i) {
-                            const int pi = gx * GWL + i, pj = gy * GHL + jj;
-                            pixel(pj * PW + pi, pi, pj, true);
-                        }
-                }
+                for (int pi = 0; pi < PW; ++pi) pixel(pj * PW + pi, pi, pj);
+            const bool any = mbits != 0u;
             if (__any_sync(0xffffffffu, any)) {
                 const float v[9] = {du, dv, dcA, dcB, dcC, dlo, dr, dg, db};
                 const float2 tot = warp_sum9(v, lane);
