@@ -748,7 +748,7 @@ def run_gpu(args):
     K_tiles = r.last_stats["n_instances"]
 
     raster_event_ms = stage["raster"]
-    raster_traffic = _traffic("raster_fwd", _source_hash("raster.cu"))
+    raster_traffic = _traffic("raster_fwd", _source_hash("raster.cu", "raster_impl.cuh", "raster_queue.cu"))
 
     # quality: CR vs plain on the same frame
     img_cr = r.render(mode="cr", opacity_filter=True).cpu().numpy().astype(np.float64)
