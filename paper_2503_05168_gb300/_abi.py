@@ -8,7 +8,8 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libseele.so")
+# SEELE_LIBRARY selects another build of the same ABI (the checked build)
+LIB_PATH = os.environ.get("SEELE_LIBRARY") or os.path.join(HERE, "libseele.so")
 
 SEELE_OK = 0
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_STATE", 3: "ERR_CUDA", 4: "ERR_CAPACITY", 5: "ERR_TIMEOUT",

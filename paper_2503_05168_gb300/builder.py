@@ -2,7 +2,10 @@
 
 Each translation unit is compiled by its own nvcc process in parallel, then
 linked into one shared library with the CUDA runtime linked statically.  The
-result exposes only the C ABI of include/seele.h.
+result exposes only the C ABI of include/seele.h.  build(checked=True) makes
+libseele_checked.so, the same library with the kernels' index checks compiled
+in (SEELE_CHECKED: a bad gather index records an internal error instead of
+being read).
 """
 from __future__ import annotations
 
@@ -17,6 +20,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libseele.so")
+CHECKED_BUILD_DIR = os.path.join(HERE, "_build_checked")
+CHECKED_LIB_PATH = os.path.join(HERE, "libseele_checked.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
@@ -36,18 +41,19 @@ def _stale(sources, target) -> bool:
     return any(os.path.getmtime(s) > t for s in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    if not force and not _stale(sources, LIB_PATH):
-        return LIB_PATH
-    os.makedirs(BUILD_DIR, exist_ok=True)
+    lib_path, build_dir = (CHECKED_LIB_PATH, CHECKED_BUILD_DIR) if checked else (LIB_PATH, BUILD_DIR)
+    if not force and not _stale(sources, lib_path):
+        return lib_path
+    os.makedirs(build_dir, exist_ok=True)
     nvcc = _nvcc()
     procs = []
     objs = []
     for src in sources:
-        obj = os.path.join(BUILD_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
-        cmd = [nvcc] + ARCH + NVCC_FLAGS + ["-c", src, "-o", obj]
+        cmd = [nvcc] + ARCH + NVCC_FLAGS + (["-DSEELE_CHECKED=1"] if checked else []) + ["-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -59,10 +65,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if failed:
         msg = "\n".join(f"--- {s}\n{o}" for s, o in failed)
         raise RuntimeError(f"nvcc failed:\n{msg}")
-    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     subprocess.check_call([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart_static", "-lrt", "-ldl", "-lpthread"])
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

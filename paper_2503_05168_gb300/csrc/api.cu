@@ -9,12 +9,34 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "seele.h"
 #include "kernels.h"
 
 using namespace seele;
 
 namespace {
+
+// NVTX ranges: one per public call, and within a frame's enqueue one per
+// stage (host-side, where each stage is issued; free when no tool listens).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+const char* const kStageNvtx[SEELE_NUM_STAGES] = {"preprocess", "compact", "depth_sort", "tile_scan",
+                                                   "emit", "tile_sort", "ranges", "raster"};
+struct NvtxStages {
+    bool open = false;
+    void next(int k) {
+        if (open) nvtxRangePop();
+        nvtxRangePushA(kStageNvtx[k]);
+        open = true;
+    }
+    ~NvtxStages() {
+        if (open) nvtxRangePop();
+    }
+};
 
 struct DevBuf {
     void* p = nullptr;
@@ -775,7 +797,9 @@ seele_status enqueue_frame(seele_ctx* c, const seele_options* opt, const FrameIn
     DeviceStatus* st = ptr<DeviceStatus>(c->status);
     uint32_t* dtot = ptr<uint32_t>(c->digtot);
     launches = 0;
-#define SEELE_MARK(k) \
+    NvtxStages nvtx_stages;
+#define SEELE_MARK(k)                                               \
+    if ((k) < SEELE_NUM_STAGES) nvtx_stages.next(k);                \
     if (c->profiling) SEELE_CUDA(c, cudaEventRecord(c->ev[k], s))
 
     SEELE_CUDA(c, cudaMemsetAsync(st, 0, sizeof(DeviceStatus), s));
@@ -872,6 +896,7 @@ seele_status enqueue_frame(seele_ctx* c, const seele_options* opt, const FrameIn
     ra.out_T = ptr<float>(c->T);
     ra.out_nc = ptr<uint32_t>(c->nc);
     ra.count_into = count ? st : nullptr;
+    ra.status = st;
     ra.view_end = vt + 1;
     ra.view_done = reinterpret_cast<uint32_t*>(vt + 1 + ncam);
     const bool ckpt = !f.blocks && !count && c->skew_frac <= 0.0 && c->topk_k <= 0;
@@ -984,6 +1009,7 @@ seele_status seele_set_stream(seele_ctx* c, void* cuda_stream) {
 const char* seele_last_error(const seele_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
 seele_status seele_load_scene(seele_ctx* c, const seele_scene_desc* d) {
+    const NvtxRange nvtx_call("seele_load_scene");
     if (!c) return SEELE_ERR_ARG;
     if (!d) return fail(c, SEELE_ERR_ARG, "scene descriptor is NULL");
     if (d->n < 1 || d->n > (int64_t)65535 * 256)
@@ -1301,6 +1327,7 @@ seele_status seele_synchronize(seele_ctx* c) {
 }
 
 seele_status seele_render(seele_ctx* c, const seele_options* opt, float* out_rgb, float* out_T, seele_stats* stats) {
+    const NvtxRange nvtx_call("seele_render");
     if (!c) return SEELE_ERR_ARG;
     if (!c->has_scene) return fail(c, SEELE_ERR_STATE, "no scene loaded");
     if (c->cams.empty()) return fail(c, SEELE_ERR_STATE, "no cameras set");
@@ -1465,6 +1492,7 @@ seele_status seele_get_view_times(const seele_ctx* c, float* out_ms, int32_t n) 
 }
 
 seele_status seele_autotune(seele_ctx* c, seele_options* inout, float* best_ms) {
+    const NvtxRange nvtx_call("seele_autotune");
     if (!c || !inout) return SEELE_ERR_ARG;
     if (!c->has_scene || c->cams.empty()) return fail(c, SEELE_ERR_STATE, "autotune needs a scene and cameras");
     static const int shapes[][2] = {{16, 16}, {32, 8}, {32, 16}, {8, 8}};
@@ -1526,6 +1554,7 @@ seele_status seele_autotune(seele_ctx* c, seele_options* inout, float* best_ms) 
 // schedule and batch depth for the objective; see seele.h.
 seele_status seele_autotune_ex(seele_ctx* c, seele_options* inout, int32_t objective, const char* cache_path,
                                seele_tune_result* result) {
+    const NvtxRange nvtx_call("seele_autotune_ex");
     if (!c || !inout) return SEELE_ERR_ARG;
     if (objective < SEELE_TUNE_BATCH_MS || objective > SEELE_TUNE_VIEW_P99)
         return fail(c, SEELE_ERR_ARG, "bad objective");
@@ -1683,6 +1712,7 @@ seele_status seele_autotune_ex(seele_ctx* c, seele_options* inout, int32_t objec
 }
 
 seele_status seele_render_backward(seele_ctx* c, const float* dL_drgb, const seele_grads* g) {
+    const NvtxRange nvtx_call("seele_render_backward");
     if (!c) return SEELE_ERR_ARG;
     if (!c->rendered) return fail(c, SEELE_ERR_STATE, "no render to differentiate");
     if (c->st.on) return fail(c, SEELE_ERR_STATE, "gradients need the whole scene resident (seele_load_scene)");
@@ -1780,6 +1810,7 @@ seele_status seele_get_debug_view(const seele_ctx* c, seele_debug_view* out) {
 seele_status seele_contribution_skew(seele_ctx* c, const seele_options* opt, float frac, uint32_t* out_m,
                                      uint32_t* out_blended, uint32_t* out_walked, float* out_total,
                                      uint32_t* out_listed) {
+    const NvtxRange nvtx_call("seele_contribution_skew");
     if (!c) return SEELE_ERR_ARG;
     if (!c->has_scene) return fail(c, SEELE_ERR_STATE, "no scene loaded");
     if (c->st.on) return fail(c, SEELE_ERR_STATE, "the skew statistic needs the whole scene resident");
@@ -1818,6 +1849,7 @@ seele_status seele_contribution_skew(seele_ctx* c, const seele_options* opt, flo
 seele_status seele_build_view_clusters(seele_ctx* c, const seele_camera* poses, int32_t n_poses, int32_t n_clusters,
                                        int32_t top_k, const double* uniforms, int32_t max_iter, float* out_centroids,
                                        float* out_pos_scale, uint32_t* out_mask, int32_t* out_assign) {
+    const NvtxRange nvtx_call("seele_build_view_clusters");
     if (!c) return SEELE_ERR_ARG;
     if (!c->has_scene) return fail(c, SEELE_ERR_STATE, "no scene loaded");
     if (c->st.on) return fail(c, SEELE_ERR_STATE, "the builder needs the whole scene resident");

@@ -217,6 +217,18 @@ __device__ __forceinline__ void record_error(DeviceStatus* st, int32_t code, uin
     if (atomicCAS(&st->error, kOk, code) == kOk) st->timeout_site = site;
 }
 
+// The checked build (SEELE_CHECKED, libseele_checked.so) validates every
+// index a kernel gathers with before the access; a bad one records
+// kErrInternal with the site below and is replaced by a valid one, so the
+// kernel stays in bounds and the host reports SEELE_ERR_INTERNAL.  The
+// ordinary build compiles the checks away.
+#ifdef SEELE_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+enum : uint32_t { kSiteRasterRange = 20, kSiteRasterRecord = 21, kSiteRasterBlock = 22 };
+
 __device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t* p) {
     uint64_t v;
     asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");

@@ -146,6 +146,7 @@ struct RasterArgs {
     float* out_T;
     uint32_t* out_nc;
     DeviceStatus* count_into;   // non-null: run the counting variant
+    DeviceStatus* status = nullptr;  // the frame's status word (checked build: index checks)
     unsigned long long* view_end;  // [n_cams] time the camera's last tile finished (%globaltimer)
     uint32_t* view_done;        // [n_cams] finished tiles, cleared per frame
     // tile binning (else nullptr): transmittance checkpoints, [slots][tile pixels]

@@ -14,7 +14,7 @@ static void launch_variant(const RasterArgs& a, cudaStream_t s) {
     const uint32_t grid = BLOCKS ? 32 * a.n_blocks : a.n_tiles;
     launch_pdl(raster_fwd_kernel<TW, TH, PW, PH, GW, GH, CR, COUNT, BLOCKS>, dim3(grid), dim3(NT), 0, s,
                a.starts, a.ends, a.inst_rec, a.inst_mask, a.mask_summary, a.block_order, a.rec, a.cams, a.n_cams,
-               a.fp, a.out_rgb, a.out_T, a.out_nc, COUNT ? a.count_into : nullptr, a.view_end, a.view_done,
+               a.fp, a.out_rgb, a.out_T, a.out_nc, COUNT ? a.count_into : a.status, a.view_end, a.view_done,
                (COUNT || BLOCKS) ? nullptr : a.ckpt, (COUNT || BLOCKS) ? nullptr : a.cfin);
 }
 

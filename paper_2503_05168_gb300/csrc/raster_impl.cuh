@@ -147,7 +147,12 @@ __device__ __forceinline__ void raster_unit(uint32_t item, const uint32_t* __res
     uint32_t gtile, unit, bit = 0;
     int lo = 0, tx, ty;
     if (BLOCKS) {
-        const uint32_t b = __ldg(block_order + (item >> 5));
+        uint32_t b = __ldg(block_order + (item >> 5));
+        if (kChecked && b >= cams[n_cams - 1].block_offset + (uint32_t)(cams[n_cams - 1].blocks_x *
+                                                                          ((cams[n_cams - 1].tiles_y + kBlockH - 1) / kBlockH))) {
+            if (threadIdx.x == 0) record_error(counters, kErrInternal, kSiteRasterBlock);
+            b = 0;
+        }
         bit = item & 31u;
         int hi = n_cams - 1;
         while (lo < hi) {
@@ -202,6 +207,20 @@ __device__ __forceinline__ void raster_unit(uint32_t item, const uint32_t* __res
     };
     uint2 rg = make_uint2(__ldg(starts + unit), __ldg(ends + unit));
     if (rg.x >= rg.y) rg = make_uint2(0u, 0u);  // no instances
+    if (kChecked && rg.y > counters->n_inst_valid) {
+        if (threadIdx.x == 0) record_error(counters, kErrInternal, kSiteRasterRange);
+        rg = make_uint2(0u, 0u);
+    }
+    const uint32_t n_records = (uint32_t)fp.n * (uint32_t)n_cams;
+    // a record id of the list, validated in the checked build
+    auto record_of = [&](uint32_t j) {
+        uint32_t r = __ldg(inst_rec + j);
+        if (kChecked && r >= n_records) {
+            record_error(counters, kErrInternal, kSiteRasterRecord);
+            r = 0;
+        }
+        return r;
+    };
     const float fx0 = (float)bx + 0.5f, fy0 = (float)by + 0.5f;
     // the leader pixel of the group holding this thread's block (WHOLE groups)
     const float lx0 = (float)(bx / GW * GW) + 0.5f, ly0 = (float)(by / GH * GH) + 0.5f;
@@ -219,7 +238,7 @@ __device__ __forceinline__ void raster_unit(uint32_t item, const uint32_t* __res
             if (cursor >= cursor_end) break;
             const uint32_t j = cursor + t;
             if (j < rg.y) {
-                const uint32_t r = __ldg(inst_rec + j);
+                const uint32_t r = record_of(j);
                 s0[t] = __ldg(rec + (size_t)kRecF4 * r);
                 s1[t] = __ldg(rec + (size_t)kRecF4 * r + 1);
                 s2[t] = __ldg(rec + (size_t)kRecF4 * r + 2);
@@ -275,7 +294,7 @@ __device__ __forceinline__ void raster_unit(uint32_t item, const uint32_t* __res
             }
             cnt = min(NT, n_idx - idx_pos);
             if (t < cnt) {
-                const uint32_t r = __ldg(inst_rec + s_idx[idx_pos + t]);
+                const uint32_t r = record_of(s_idx[idx_pos + t]);
                 s0[t] = __ldg(rec + (size_t)kRecF4 * r);
                 s1[t] = __ldg(rec + (size_t)kRecF4 * r + 1);
                 s2[t] = __ldg(rec + (size_t)kRecF4 * r + 2);

@@ -23,7 +23,7 @@ void launch_raster_queue(const RasterArgs& a, cudaStream_t s) {
     const uint32_t grid = std::min<uint32_t>(n_items, (uint32_t)(per_sm * sms));
     launch_pdl(kernel, dim3(std::max<uint32_t>(grid, 1u)), dim3(NT), 0, s, a.starts, a.ends, a.inst_rec, a.inst_mask,
                a.mask_summary, a.block_order, a.rec, a.cams, a.n_cams, a.fp, a.out_rgb, a.out_T, a.out_nc,
-               (DeviceStatus*)nullptr, a.view_end, a.view_done, BLOCKS ? nullptr : a.ckpt,
+               a.status, a.view_end, a.view_done, BLOCKS ? nullptr : a.ckpt,
                BLOCKS ? nullptr : a.cfin, n_items, a.queue);
 }
 
