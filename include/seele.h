@@ -358,6 +358,9 @@ typedef struct {
                                      entry reaches, bit j*8 + i for tile (i, j); else NULL */
     const uint32_t* scene_order;  /* SEELE_SCENE_SPATIAL: [n] the caller's index of stored
                                      Gaussian g (record id = camera * n + g); else NULL */
+    const uint32_t* mask_summary; /* SEELE_BIN_BLOCKS: [ceil(n_instances / 32)] OR of the
+                                     masks of inst_mask[32 g .. 32 g + 31] (entries below
+                                     n_instances); else NULL */
 } seele_debug_view;
 
 seele_status seele_get_debug_view(const seele_ctx* ctx, seele_debug_view* out);

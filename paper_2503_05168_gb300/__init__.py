@@ -384,6 +384,7 @@ class Renderer:
             n_contrib=dev(v.n_contrib, self.n_pixels, i32),
             inst_mask=dev(v.inst_mask, K, i32) if v.inst_mask else None,
             scene_order=dev(v.scene_order, R // max(1, len(self.cameras)), i32) if v.scene_order else None,
+            mask_summary=dev(v.mask_summary, (K + 31) // 32, i32) if v.mask_summary else None,
         )
 
 

@@ -84,7 +84,7 @@ class DebugView(ctypes.Structure):
     _fields_ = [("n_records", ctypes.c_int64), ("n_visible", ctypes.c_int64), ("n_instances", ctypes.c_int64),
                 ("n_tiles", ctypes.c_int64), ("inst_record", P), ("tile_start", P), ("tile_end", P),
                 ("tiles_touched", P), ("records", P), ("depth", P), ("n_contrib", P),
-                ("inst_mask", P), ("scene_order", P)]
+                ("inst_mask", P), ("scene_order", P), ("mask_summary", P)]
 
 
 # name -> (restype, argtypes); the ABI test checks this table against the header

@@ -1804,6 +1804,7 @@ seele_status seele_get_debug_view(const seele_ctx* c, seele_debug_view* out) {
     out->depth = ptr<const float>(m->depth);
     out->n_contrib = ptr<const uint32_t>(m->nc);
     out->scene_order = c->spatial ? ptr<const uint32_t>(m->order) : nullptr;
+    out->mask_summary = blk ? ptr<const uint32_t>(m->msum) : nullptr;
     return SEELE_OK;
 }
 

@@ -568,13 +568,15 @@ static bool launch_bwd_shape(const RasterBwdArgs& a, cudaStream_t s) {
     return true;
 }
 
+// 8x8 tiles: one warp per tile, two pixels (a row pair) per lane, so each
+// list entry is tested once per tile rather than once per half tile.
 static bool launch_bwd_shape_8x8(const RasterBwdArgs& a, cudaStream_t s) {
-    if (!a.cr) launch_bwd_one<8, 8, 1, 1, 1, 1, false>(a, s);
-    else if (a.group_w == 2 && a.group_h == 2) launch_bwd_one<8, 8, 1, 1, 2, 2, true>(a, s);
-    else if (a.group_w == 1 && a.group_h == 1) launch_bwd_one<8, 8, 1, 1, 1, 1, true>(a, s);
-    else if (a.group_w == 2 && a.group_h == 4) launch_bwd_one<8, 8, 1, 1, 2, 4, true>(a, s);
-    else if (a.group_w == 4 && a.group_h == 4) launch_bwd_one<8, 8, 1, 1, 4, 4, true>(a, s);
-    else if (a.group_w == 4 && a.group_h == 8) launch_bwd_one<8, 8, 1, 1, 4, 8, true>(a, s);
+    if (!a.cr) launch_bwd_one<8, 8, 2, 1, 1, 1, false>(a, s);
+    else if (a.group_w == 2 && a.group_h == 2) launch_bwd_one<8, 8, 2, 1, 2, 2, true>(a, s);
+    else if (a.group_w == 1 && a.group_h == 1) launch_bwd_one<8, 8, 2, 1, 1, 1, true>(a, s);
+    else if (a.group_w == 2 && a.group_h == 4) launch_bwd_one<8, 8, 2, 1, 2, 4, true>(a, s);
+    else if (a.group_w == 4 && a.group_h == 4) launch_bwd_one<8, 8, 2, 1, 4, 4, true>(a, s);
+    else if (a.group_w == 4 && a.group_h == 8) launch_bwd_one<8, 8, 2, 1, 4, 8, true>(a, s);
     else return false;
     return true;
 }

@@ -5,6 +5,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "blocks.cuh"
 #include "tiletest.cuh"
 
 namespace seele {
@@ -145,11 +146,8 @@ __global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ 
 }
 
 // Block binning: one thread per depth-ordered record writes its (block,
-// record, mask) entries at the record's scanned offset -- a record reaches
-// about two tile blocks on average, too few to be worth a warp.  Per block
-// row (kBlockH tile rows) it computes the rows' spans once, then emits the
-// blocks spanned by their union with the mask of the tiles each row covers
-// in that block; preprocessing counted the same blocks from the same spans.
+// record, mask) entries (blocks.cuh) at the record's scanned offset -- a
+// record reaches about two tile blocks on average, too few to be worth a warp.
 template <typename KeyT>
 __global__ void __launch_bounds__(256) emit_blocks_kernel(const uint32_t* __restrict__ order,
                                                           const uint32_t* __restrict__ offsets,
@@ -165,54 +163,22 @@ __global__ void __launch_bounds__(256) emit_blocks_kernel(const uint32_t* __rest
     const uint32_t n_inst = st->n_instances;
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
         const uint32_t r = __ldg(order + j);
-        const uint2 bx2 = rec_tile_box(rec, r);
-        const int x0 = (int)(bx2.x & 0xffffu), y0 = (int)(bx2.x >> 16);
-        const int x1 = (int)(bx2.y & 0xffffu), y1 = (int)(bx2.y >> 16);
-        const CamDev& C = cams[r < (uint32_t)n_gauss ? 0u : r / (uint32_t)n_gauss];
-        const uint32_t boff = C.block_offset, bx_n = (uint32_t)C.blocks_x;
-        Ellipse E;
-        if (ellipse) E = make_ellipse(__ldg(rec + (size_t)kRecF4 * r), __ldg(rec + (size_t)kRecF4 * r + 1));
-        uint32_t pos = __ldg(offsets + j);
+        const uint32_t pos = __ldg(offsets + j);
         const uint32_t end = j + 1 < n ? __ldg(offsets + j + 1) : n_inst;
-        for (int by = y0 / kBlockH; by <= y1 / kBlockH; ++by) {
-            int lo[kBlockH], hi[kBlockH];
-            int blo = 1 << 30, bhi = -1;
-#pragma unroll
-            for (int q = 0; q < kBlockH; ++q) {
-                const int ty = by * kBlockH + q;
-                lo[q] = 1;
-                hi[q] = 0;
-                if (ty < y0 || ty > y1) continue;
-                int l = x0, h = x1;
-                if (ellipse && !row_span(E, ty, tile_w, tile_h, x0, x1, &l, &h)) continue;
-                lo[q] = l;
-                hi[q] = h;
-                blo = min(blo, l);
-                bhi = max(bhi, h);
-            }
-            if (bhi < blo) continue;
-            const uint32_t row_base = boff + (uint32_t)by * bx_n;
-            for (int bx = blo / kBlockW; bx <= bhi / kBlockW; ++bx) {
-                const int c0 = bx * kBlockW, c1 = c0 + kBlockW - 1;
-                uint32_t mask = 0;
-#pragma unroll
-                for (int q = 0; q < kBlockH; ++q) {
-                    const int a = max(lo[q], c0), b = min(hi[q], c1);
-                    if (a <= b) mask |= ((0xffu >> (kBlockW - 1 - (b - a))) << (a - c0)) << (kBlockW * q);
-                }
-                if (pos < end) {
-                    inst_block[pos] = (KeyT)(row_base + (uint32_t)bx);
-                    inst_rec[pos] = r;
-                    inst_mask[pos] = mask;
-                }
-                ++pos;
-            }
-        }
-        if (pos != end) {
+        const uint32_t got = for_each_block(rec, r, cams, n_gauss, tile_w, tile_h, ellipse,
+                                            [&](uint32_t k, uint32_t unit, uint32_t mask) {
+                                                if (pos + k < end) {
+                                                    inst_block[pos + k] = (KeyT)unit;
+                                                    inst_rec[pos + k] = r;
+                                                    inst_mask[pos + k] = mask;
+                                                }
+                                            });
+        if (pos + got != end) {
             // never expected: both counts come from the same row_span on the
             // same stored floats.  Report it and keep every slot a valid entry.
             record_error(st, kErrInternal, 8);
-            for (uint32_t p = pos; p < end; ++p) {
+            const uint32_t boff = record_camera(cams, r, n_gauss).block_offset;
+            for (uint32_t p = pos + got; p < end; ++p) {
                 inst_block[p] = (KeyT)boff;
                 inst_rec[p] = r;
                 inst_mask[p] = 0u;

@@ -181,6 +181,12 @@ def test_block_lists_filtered_per_tile_are_the_tile_lists(Renderer, seed, size, 
             np.testing.assert_array_equal(got, gid[ranges[t, 0]:ranges[t, 1]] + ci * n, err_msg=f"{ci} {t}")
         blk_off += bx_n * by_n
     assert blk_off == d["n_tiles"]
+    # the rasterizer's group skip: summary g is the OR of the masks of entries 32 g .. 32 g + 31
+    K = d["n_instances"]
+    padded = np.zeros(-(-K // 32) * 32, np.uint32)
+    padded[:K] = mask[:K]
+    np.testing.assert_array_equal(d["mask_summary"].view(np.uint32),
+                                  np.bitwise_or.reduce(padded.reshape(-1, 32), axis=1))
     r.close()
 
 
