@@ -96,7 +96,7 @@ struct seele_ctx {
     // frame workspace
     DevBuf rec, tiles, blocks, depth, visk[2], visv[2], offs, instk[2], instv[2], instm[2], ranges, msum,
         border, chunkv, chunks, vbuf, status, hist, digtot, T, nc, rgb_tmp, sortcnt, grad_rec, cnts, torder,
-        ckpt, cfin, bmap;
+        ckpt, cfin, bmap, branges, tcnt, toff, emap, ecnt;
     // the last render wrote transmittance checkpoints for ckpt_slots slots
     bool ckpt_valid = false;
     uint64_t ckpt_slots = 0;
@@ -561,15 +561,18 @@ struct FrameInfo {
     uint32_t cnt_words = 0;
     bool queue = false;        // the persistent rasterizer, units in camera groups
     int batch_depth = 0;
+    bool expand = false;       // tile binning made by expanding the sorted block lists
+    int block_bits = 1;        // key bits of a tile-block id
     FrameParams fp{};
 };
 
-// Emission, stable radix sort by list unit and the unit ranges (from the last
-// pass).  Tile binning: (tile, record) instances sorted by tile.  Block
-// binning: (block, record, tile mask) instances sorted by block, then the
-// mask summaries and the order in which the rasterizer visits the blocks.
-// Returns the ping-pong buffer holding the sorted lists, or -1 on a launch
-// error.
+// Emission of (block, record, tile mask) instances in depth order, their
+// stable radix sort by block and the block ranges (from the last pass).
+// Block binning: then the mask summaries and the order in which the
+// rasterizer visits the blocks.  Tile binning: then the block lists expanded
+// into the tile lists (in tile order) and the tiles' ranges and visiting
+// order.  Returns the ping-pong buffer holding the final lists, or -1 on a
+// launch error.
 template <typename KeyT>
 int enqueue_tile_sort(seele_ctx* c, const FrameInfo& f, const uint32_t* order, const float4* rec,
                       const CamDev* cams, DeviceStatus* st, const uint32_t* n_inst, uint64_t cap, int emit_blocks,
@@ -578,12 +581,43 @@ int enqueue_tile_sort(seele_ctx* c, const FrameInfo& f, const uint32_t* order, c
     KeyT* keys[2] = {ptr<KeyT>(c->instk[0]), ptr<KeyT>(c->instk[1])};
     uint32_t* vals[2] = {ptr<uint32_t>(c->instv[0]), ptr<uint32_t>(c->instv[1])};
     uint32_t* masks[2] = {ptr<uint32_t>(c->instm[0]), ptr<uint32_t>(c->instm[1])};
-    if (f.blocks)
+    if (f.expand) {
+        // tile lists from the block lists: block instances, their stable sort
+        // by block, then each block's list split into its tiles' lists
         launch_emit_blocks<KeyT>(order, ptr<uint32_t>(c->offs), rec, cams, (int)c->n, fp.tile_w, fp.tile_h,
                                  fp.tile_test, st, keys[0], vals[0], masks[0], emit_blocks, s);
-    else
-        launch_emit<KeyT>(order, ptr<uint32_t>(c->offs), rec, cams, (int)c->n, fp.tile_w, fp.tile_h,
-                          fp.tile_test, st, keys[0], vals[0], emit_blocks, s);
+        if (cudaPeekAtLastError() != cudaSuccess) return -1;
+        ++launches;
+        SEELE_MARK_EXT(c, SEELE_STAGE_TILE_SORT);
+        const uint32_t B = (uint32_t)f.blocks_total;
+        uint32_t* brun = ptr<uint32_t>(c->branges);
+        const int bfin = radix_sort_pairs<KeyT>(keys, vals, n_inst, (uint32_t)cap, f.block_bits, false, scnt, soff,
+                                                dtot, launches, s, brun, brun + B, masks);
+        if (bfin < 0) return -1;
+        SEELE_MARK_EXT(c, SEELE_STAGE_RANGES);
+        const uint64_t tiles = f.tiles_total;
+        const uint32_t chunks = (uint32_t)((tiles + 31) / 32);
+        const uint32_t n_ids = expand_chunk_ids(cap, B);
+        uint32_t* Lt = ptr<uint32_t>(c->tcnt);
+        uint32_t* chunk_total = Lt + 32 * (size_t)chunks;
+        uint32_t* St = ptr<uint32_t>(c->toff);
+        uint32_t* C = ptr<uint32_t>(c->ecnt);
+        uint32_t* Co = C + 32 * (size_t)n_ids;
+        uint32_t* run = ptr<uint32_t>(c->ranges);
+        launch_tile_expand(vals[bfin], masks[bfin], brun, brun + B, B, cams, f.ncam, (uint32_t)tiles, n_ids,
+                           (uint32_t)std::min<uint64_t>(cap, 0xffffffffu), st, ptr<uint32_t>(c->emap), C, Co, Lt,
+                           chunk_total, St, vals[bfin ^ 1], run, s);
+        if (f.queue)
+            launch_view_order(run, run + tiles, (uint32_t)tiles, cams, f.ncam, 0, f.batch_depth,
+                              ptr<uint32_t>(c->border), s);
+        else
+            launch_block_order(run, run + tiles, (uint32_t)tiles, ptr<uint32_t>(c->border), s);
+        if (cudaPeekAtLastError() != cudaSuccess) return -1;
+        launches += 6;
+        return bfin ^ 1;
+    }
+    launch_emit_blocks<KeyT>(order, ptr<uint32_t>(c->offs), rec, cams, (int)c->n, fp.tile_w, fp.tile_h,
+                             fp.tile_test, st, keys[0], vals[0], masks[0], emit_blocks, s);
     if (cudaPeekAtLastError() != cudaSuccess) return -1;
     ++launches;
     SEELE_MARK_EXT(c, SEELE_STAGE_TILE_SORT);
@@ -686,7 +720,7 @@ void fill_params(seele_ctx* c, const seele_options* opt, FrameInfo& f) {
     fp.tile_h = opt->tile_h;
     fp.opacity_filter = opt->opacity_filter ? 1 : 0;
     fp.tile_test = opt->tile_test == SEELE_TILES_ELLIPSE ? 1 : 0;
-    fp.binning = opt->binning == SEELE_BIN_BLOCKS ? 1 : 0;
+    fp.binning = (f.blocks || f.expand) ? 1 : 0;  // preprocessing counts the block instances
     fp.use_mask = opt->cluster_filter ? 1 : 0;
     fp.alpha_min = opt->alpha_min;
     fp.log_alpha_min = std::log(opt->alpha_min);
@@ -712,7 +746,17 @@ seele_status size_frame(seele_ctx* c, FrameInfo& f) {
         SEELE_CUDA(c, ensure(c->visv[i], 4 * R));
         SEELE_CUDA(c, ensure(c->instk[i], 4 * cap));
         SEELE_CUDA(c, ensure(c->instv[i], 4 * cap));
-        if (f.blocks) SEELE_CUDA(c, ensure(c->instm[i], 4 * (cap + 32)));  // whole 32-entry groups
+        if (f.blocks || f.expand) SEELE_CUDA(c, ensure(c->instm[i], 4 * (cap + 32)));  // whole 32-entry groups
+    }
+    if (f.expand) {
+        SEELE_CUDA(c, ensure(c->blocks, 4 * R));
+        const uint64_t chunks = (f.tiles_total + 31) / 32;
+        SEELE_CUDA(c, ensure(c->branges, 8 * f.blocks_total));  // block list starts, then ends
+        const uint64_t ids = expand_chunk_ids(cap, f.blocks_total);
+        SEELE_CUDA(c, ensure(c->tcnt, 4 * 33 * chunks));        // tile counts (whole chunks), chunk totals
+        SEELE_CUDA(c, ensure(c->toff, 4 * 32 * chunks));        // tile list starts
+        SEELE_CUDA(c, ensure(c->emap, 4 * (ids - f.blocks_total)));  // later chunks -> block
+        SEELE_CUDA(c, ensure(c->ecnt, 8 * 32 * ids));           // per-chunk tile counts, then their offsets
     }
     if (f.blocks) {
         SEELE_CUDA(c, ensure(c->blocks, 4 * R));
@@ -808,6 +852,13 @@ seele_status enqueue_frame(seele_ctx* c, const seele_options* opt, const FrameIn
     SEELE_CUDA(c, cudaMemsetAsync(c->viewt.p, 0, 12ull * ncam + 8, s));
     SEELE_CUDA(c, cudaMemsetAsync(c->ranges.p, 0xff, 4 * units_total, s));
     SEELE_CUDA(c, cudaMemsetAsync(ptr<uint32_t>(c->ranges) + units_total, 0, 4 * units_total, s));
+    if (f.expand) {
+        SEELE_CUDA(c, cudaMemsetAsync(c->branges.p, 0xff, 4 * f.blocks_total, s));
+        SEELE_CUDA(c, cudaMemsetAsync(ptr<uint32_t>(c->branges) + f.blocks_total, 0, 4 * f.blocks_total, s));
+        SEELE_CUDA(c, cudaMemsetAsync(c->tcnt.p, 0, 4 * 33 * ((tiles_total + 31) / 32), s));
+        SEELE_CUDA(c, cudaMemsetAsync(c->emap.p, 0xff, 4 * (expand_chunk_ids(cap, f.blocks_total) - f.blocks_total),
+                                      s));
+    }
     SEELE_MARK(SEELE_STAGE_PREPROCESS);
     SceneDev sc = scene_dev(c);
     if (c->scene_flags == SEELE_SCENE_BORROW && sc.means == nullptr) {
@@ -825,7 +876,8 @@ seele_status enqueue_frame(seele_ctx* c, const seele_options* opt, const FrameIn
     sc.veto = c->st.on ? ptr<const uint32_t>(c->veto) : nullptr;
     unsigned long long* vt = ptr<unsigned long long>(c->viewt);
     ProjOut po{ptr<float4>(c->rec), ptr<uint32_t>(c->tiles),
-               f.blocks ? ptr<uint32_t>(c->blocks) : nullptr, ptr<float>(c->depth), vt, ptr<uint32_t>(c->chunkv)};
+               (f.blocks || f.expand) ? ptr<uint32_t>(c->blocks) : nullptr, ptr<float>(c->depth), vt,
+               ptr<uint32_t>(c->chunkv)};
     const CamDev* cams = ptr<const CamDev>(c->cams_dev);
     launch_preprocess(sc, cams, f.fp, po, s);
     SEELE_LAUNCHED(c);
@@ -834,7 +886,7 @@ seele_status enqueue_frame(seele_ctx* c, const seele_options* opt, const FrameIn
     // visible records -> (depth bits, id), then the stable depth sort
     SEELE_MARK(SEELE_STAGE_COMPACT);
     // with ids below 2^24 the sort values also carry the instance counts
-    const uint32_t* cnt_src = f.blocks ? po.blocks : po.tiles;
+    const uint32_t* cnt_src = (f.blocks || f.expand) ? po.blocks : po.tiles;
     const bool packed = R <= (1ull << kPackedIdBits);
     launch_compact_visible(cnt_src, packed, po.depth, (uint32_t)R, po.chunk_vis, ptr<uint32_t>(c->visk[0]),
                            ptr<uint32_t>(c->visv[0]), st, s);
@@ -984,7 +1036,7 @@ void seele_destroy(seele_ctx* c) {
                      &c->ranges, &c->status, &c->hist, &c->digtot, &c->T, &c->nc, &c->rgb_tmp, &c->sortcnt,
                      &c->grad_rec, &c->blocks, &c->instm[0], &c->instm[1], &c->msum, &c->border, &c->chunkv,
                      &c->chunks, &c->vbuf, &c->cnts, &c->skew, &c->veto, &c->order, &c->unordered,
-                     &c->order_scratch, &c->torder, &c->ckpt, &c->cfin, &c->bmap};
+                     &c->order_scratch, &c->torder, &c->ckpt, &c->cfin, &c->bmap, &c->branges, &c->tcnt, &c->toff, &c->emap, &c->ecnt};
     for (DevBuf* b : all) release(*b);
     stream_release(c);
     release(c->viewt);
@@ -1365,6 +1417,8 @@ seele_status seele_render(seele_ctx* c, const seele_options* opt, float* out_rgb
     f.units_total = f.blocks ? f.blocks_total : f.tiles_total;
     f.short_keys = f.units_total <= kShortKeyMaxTiles;
     f.tile_bits = std::max(1, bits_for(f.units_total > 0 ? f.units_total - 1 : 0));
+    f.expand = !f.blocks;
+    f.block_bits = std::max(1, bits_for(f.blocks_total > 0 ? f.blocks_total - 1 : 0));
     fill_params(c, opt, f);
     if (profile && !c->ev[0])
         for (cudaEvent_t& e : c->ev) SEELE_CUDA(c, cudaEventCreate(&e));
@@ -1443,8 +1497,11 @@ seele_status seele_render(seele_ctx* c, const seele_options* opt, float* out_rgb
         }
         SEELE_CUDA(c, cudaStreamSynchronize(c->stream));
         const DeviceStatus& h = *c->h_status;
-        if (h.error == kErrCapacity && attempt == 0) {
-            c->capacity = (uint64_t)h.n_instances + h.n_instances / 4 + 1024;
+        // grow to what the overflowing stage counted and render again; with
+        // tile binning the block instances and then the (more numerous) tile
+        // instances can each overflow once
+        if (h.error == kErrCapacity && attempt < 2) {
+            c->capacity = std::max<uint64_t>(c->capacity, (uint64_t)h.n_instances + h.n_instances / 4 + 1024);
             ++retries;
             continue;
         }

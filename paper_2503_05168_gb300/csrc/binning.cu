@@ -1,6 +1,7 @@
-// binning.cu -- tile instances (Sec. 3.1: "the preprocessing stage ...
-// identifies the intersection between Gaussians and rendering tiles") and
-// per-tile ranges into the sorted instance list.
+// binning.cu -- tile instances (Sec. 3.1: the tile intersections found in
+// preprocessing become per-tile lists) and their ranges: block instances
+// emitted in depth order, and -- for tile binning -- the sorted block lists
+// expanded into tile lists.
 #include <algorithm>
 
 #include "common.cuh"
@@ -9,141 +10,6 @@
 #include "tiletest.cuh"
 
 namespace seele {
-
-// A warp takes 32 consecutive visible records in depth order and writes all
-// their (global tile, record) instances as one contiguous, coalesced run.
-// The records' tile rows are expanded 32 at a time (lane -> (record, row) by a
-// binary search over the exclusive row counts); each row lane finds its span
-// of tiles with the ellipse test of tiletest.cuh (or takes the whole rect row),
-// and the warp then writes the rows' tiles cooperatively: lane l writes
-// outputs l, l + 32, ... and finds its row by a second binary search.
-// Emission in depth order means the later stable sort by tile leaves each
-// tile's list front to back; within one record tiles go row-major.  Every
-// write stays inside the warp's run [offsets[wb], offsets[wb + 32]); a span
-// sum that disagrees with the preprocessing count is reported as kErrInternal.
-__device__ __forceinline__ int warp_search(uint32_t excl, uint32_t o) {
-    // largest lane s with excl_s <= o (excl non-decreasing over the lanes)
-    int s = 0;
-#pragma unroll
-    for (int step = 16; step > 0; step >>= 1) {
-        const uint32_t e = __shfl_sync(0xffffffffu, excl, s + step);
-        if (e <= o) s += step;
-    }
-    return s;
-}
-
-__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    return x;
-}
-
-template <typename KeyT>
-__global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ order,
-                                                   const uint32_t* __restrict__ offsets,
-                                                   const float4* __restrict__ rec,
-                                                   const CamDev* __restrict__ cams, int n_gauss, int tile_w,
-                                                   int tile_h, int ellipse, DeviceStatus* st,
-                                                   KeyT* __restrict__ inst_tile, uint32_t* __restrict__ inst_rec) {
-    pdl_enter();
-    if (st->error != kOk) return;  // capacity overflow: nothing fits, outputs undefined
-    const uint32_t n = st->n_visible;
-    const uint32_t n_inst = st->n_instances;
-    const int lane = threadIdx.x & 31;
-    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t wb = warp * 32; wb < n; wb += nwarps * 32) {
-        const uint32_t j = wb + lane;
-        uint32_t r = 0, x0 = 0, x1 = 0, y0 = 0, rows = 0, row0 = 0, tx_n = 0;
-        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
-        if (j < n) {
-            r = __ldg(order + j);
-            const uint2 b = rec_tile_box(rec, r);
-            x0 = b.x & 0xffffu;
-            y0 = b.x >> 16;
-            x1 = b.y & 0xffffu;
-            rows = (b.y >> 16) - y0 + 1;
-            const CamDev& C = cams[r < (uint32_t)n_gauss ? 0u : r / (uint32_t)n_gauss];
-            tx_n = (uint32_t)C.tiles_x;
-            row0 = C.tile_offset;
-            if (ellipse) {
-                r0 = __ldg(rec + (size_t)kRecF4 * r);
-                r1 = __ldg(rec + (size_t)kRecF4 * r + 1);
-            }
-        }
-        const uint32_t rincl = warp_incl_scan(rows, lane);
-        const uint32_t rexcl = rincl - rows;
-        const uint32_t rtotal = __shfl_sync(0xffffffffu, rincl, 31);
-        const uint32_t base = __shfl_sync(0xffffffffu, j < n ? __ldg(offsets + j) : 0u, 0);
-        const uint32_t end = wb + 32 < n ? __ldg(offsets + wb + 32) : n_inst;
-        uint32_t pos = base;
-        // warp-uniform trip counts: every shuffle below has all 32 lanes present
-        for (uint32_t c0 = 0; c0 < rtotal; c0 += 32) {
-            const uint32_t ro = c0 + lane;
-            const int s = warp_search(rexcl, ro);
-            const uint32_t rs = __shfl_sync(0xffffffffu, r, s);
-            const uint32_t es = __shfl_sync(0xffffffffu, rexcl, s);
-            const int xs0 = (int)__shfl_sync(0xffffffffu, x0, s);
-            const int xs1 = (int)__shfl_sync(0xffffffffu, x1, s);
-            const uint32_t ys0 = __shfl_sync(0xffffffffu, y0, s);
-            const uint32_t ns = __shfl_sync(0xffffffffu, tx_n, s);
-            const uint32_t os = __shfl_sync(0xffffffffu, row0, s);
-            float4 q0, q1;
-            q0.x = __shfl_sync(0xffffffffu, r0.x, s);
-            q0.y = __shfl_sync(0xffffffffu, r0.y, s);
-            q0.z = __shfl_sync(0xffffffffu, r0.z, s);
-            q0.w = __shfl_sync(0xffffffffu, r0.w, s);
-            q1.x = __shfl_sync(0xffffffffu, r1.x, s);
-            q1.w = __shfl_sync(0xffffffffu, r1.w, s);
-            q1.y = q1.z = 0.f;
-            int lo = 0, hi = -1;
-            uint32_t ty = 0;
-            if (ro < rtotal) {
-                ty = ys0 + (ro - es);
-                if (ellipse) {
-                    const Ellipse E = make_ellipse(q0, q1);
-                    row_span(E, (int)ty, tile_w, tile_h, xs0, xs1, &lo, &hi);
-                } else {
-                    lo = xs0;
-                    hi = xs1;
-                }
-            }
-            const uint32_t cnt = hi >= lo ? (uint32_t)(hi - lo + 1) : 0u;
-            const uint32_t cincl = warp_incl_scan(cnt, lane);
-            const uint32_t cexcl = cincl - cnt;
-            const uint32_t ctotal = __shfl_sync(0xffffffffu, cincl, 31);
-            const uint32_t first = os + ty * ns + (uint32_t)lo;  // global id of the row's first kept tile
-            for (uint32_t o0 = 0; o0 < ctotal; o0 += 32) {
-                const uint32_t o = o0 + lane;
-                const int t = warp_search(cexcl, o);
-                const uint32_t et = __shfl_sync(0xffffffffu, cexcl, t);
-                const uint32_t ft = __shfl_sync(0xffffffffu, first, t);
-                const uint32_t rt = __shfl_sync(0xffffffffu, rs, t);
-                const uint32_t p = pos + o;
-                if (o < ctotal && p < end) {
-                    inst_tile[p] = (KeyT)(ft + (o - et));
-                    inst_rec[p] = rt;
-                }
-            }
-            pos += ctotal;
-        }
-        if (pos != end) {
-            // never expected: both counts come from the same row_span on the
-            // same stored floats.  Report it and keep every slot a valid
-            // (tile, record) pair so that the sort and the rasterizer stay in
-            // bounds.
-            if (lane == 0) record_error(st, kErrInternal, 7);
-            const uint32_t t0 = __shfl_sync(0xffffffffu, row0, 0), rr0 = __shfl_sync(0xffffffffu, r, 0);
-            for (uint32_t p = pos + lane; p < end; p += 32) {
-                inst_tile[p] = (KeyT)t0;
-                inst_rec[p] = rr0;
-            }
-        }
-    }
-}
 
 // Block binning: one thread per depth-ordered record writes its (block,
 // record, mask) entries (blocks.cuh) at the record's scanned offset -- a
@@ -187,6 +53,301 @@ __global__ void __launch_bounds__(256) emit_blocks_kernel(const uint32_t* __rest
     }
 }
 
+// Tile binning through the blocks: a tile's list is its block's list kept
+// where the entry's mask has the tile's bit, in order (the (tile, depth,
+// record) order of Sec. 3.1), so the tile lists are made by expanding the
+// sorted block lists -- about a quarter as many entries to sort as tile
+// instances.  A block's list is cut into chunks of kExpandChunk entries.
+// Chunk 0 of block b has id b; chunk i >= 1 has id n_blocks + (start_b >>
+// kExpandShift) + i, unique because the block lists are disjoint (the last
+// of these ids of a block lies below the first of the next block), so no
+// scan is needed to place them.
+//   expand_map:     id of a later chunk -> block;
+//   expand_count:   per chunk, the entries of each of its block's 32 tiles;
+//   expand_offsets: per block and tile bit, each chunk's start inside the
+//                   tile's list, the tile's count at its global tile id (Lt)
+//                   and its 32-tile chunk's total; an exclusive scan of Lt
+//                   then gives the list starts (St), so the lists lie in tile
+//                   order, as a sort by tile would leave them;
+//   expand_write:   per chunk, staged in shared memory, warp t keeps the
+//                   entries with bit t (tile t % 8, t / 8 of the block) and
+//                   writes them at their places; the block's first chunk
+//                   writes the tiles' ranges; K_t is checked against the
+//                   capacity.
+constexpr int kExpandShift = 11;
+constexpr uint32_t kExpandChunk = 1u << kExpandShift;
+constexpr int kExpandThreads = 1024;  // expand_write: one warp per tile bit
+static_assert(kExpandThreads == 32 * kBlockW * kBlockH, "a warp per tile of the block");
+static_assert(kExpandChunk == 2 * kExpandThreads, "two staged entries per thread");
+constexpr int kCountThreads = 256;    // expand_count: 8 entries per thread
+static_assert(kExpandChunk == 8 * kCountThreads, "eight counted entries per thread");
+
+// chunk ids: n_blocks first chunks, then the later-chunk slots
+uint32_t expand_chunk_ids(uint64_t capacity, uint64_t n_blocks) {
+    return (uint32_t)(n_blocks + (capacity >> kExpandShift) + 2);
+}
+
+// The global id of tile bit t of block b, or UINT32_MAX where the block
+// overhangs its camera's tile grid.
+__device__ __forceinline__ uint32_t block_tile(const CamDev* __restrict__ cams, int n_cams, uint32_t b, int t) {
+    int lo = 0, hi = n_cams - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (cams[mid].block_offset <= b) lo = mid; else hi = mid - 1;
+    }
+    const CamDev& C = cams[lo];
+    const uint32_t lb = b - C.block_offset;
+    const int tx = (int)(lb % (uint32_t)C.blocks_x) * kBlockW + t % kBlockW;
+    const int ty = (int)(lb / (uint32_t)C.blocks_x) * kBlockH + t / kBlockW;
+    if (tx >= C.tiles_x || ty >= C.tiles_y) return 0xffffffffu;
+    return C.tile_offset + (uint32_t)(ty * C.tiles_x + tx);
+}
+
+__device__ __forceinline__ uint2 block_range(const uint32_t* __restrict__ bstart, const uint32_t* __restrict__ bend,
+                                             uint32_t b) {
+    const uint32_t s = __ldg(bstart + b), e = __ldg(bend + b);
+    return s < e ? make_uint2(s, e) : make_uint2(0u, 0u);
+}
+
+// The chunk behind CTA id: its block (UINT32_MAX: none) and index.
+__device__ __forceinline__ uint32_t chunk_block(uint32_t id, uint32_t n_blocks, const uint32_t* __restrict__ map) {
+    return id < n_blocks ? id : __ldg(map + (id - n_blocks));
+}
+
+__device__ __forceinline__ uint32_t chunk_id(uint32_t b, uint32_t start, uint32_t i, uint32_t n_blocks) {
+    return i == 0 ? b : n_blocks + (start >> kExpandShift) + i;
+}
+
+// map[slot] = block for every chunk i >= 1 (slot = (start_b >> kExpandShift)
+// + i; the map is cleared to UINT32_MAX first).
+__global__ void expand_map_kernel(const uint32_t* __restrict__ bstart, const uint32_t* __restrict__ bend,
+                                  uint32_t n_blocks, const DeviceStatus* __restrict__ st, uint32_t n_slots,
+                                  uint32_t* __restrict__ map) {
+    pdl_enter();
+    if (st->error != kOk) return;
+    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < n_blocks; b += gridDim.x * blockDim.x) {
+        const uint2 r = block_range(bstart, bend, b);
+        const uint32_t n = (r.y - r.x + kExpandChunk - 1) >> kExpandShift;
+        for (uint32_t i = 1; i < n; ++i) {
+            const uint32_t slot = (r.x >> kExpandShift) + i;
+            if (slot < n_slots) map[slot] = b;
+        }
+    }
+}
+
+// 32 x 32 bit transpose across a warp: lane l brings word x (bit t = entry
+// l's tile bit t) and gets back the word whose bit e is bit l of lane e's
+// word -- for lane t, which of the warp's 32 entries reach tile t.  Five
+// exchanges, each swapping the off-diagonal sub-blocks of the next smaller
+// scale between lane pairs.  Every lane of the warp calls it together.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
+    constexpr uint32_t kM[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const int j = 16 >> k;
+        const uint32_t other = __shfl_xor_sync(0xffffffffu, x, j);
+        x = (lane & j) ? (x & ~kM[k]) | ((other >> j) & kM[k]) : (x & kM[k]) | ((other & kM[k]) << j);
+    }
+    return x;
+}
+
+// The chunk ids in use: the first chunks, then the later-chunk slots below
+// the block instances' end (K_b, on the device).
+__device__ __forceinline__ uint32_t chunk_ids_used(const DeviceStatus* st, uint32_t n_blocks, uint32_t n_ids) {
+    const uint32_t kb = *(volatile const int32_t*)&st->error == kOk ? *(volatile const uint32_t*)&st->n_inst_valid
+                                                                    : 0u;
+    return min(n_ids, n_blocks + (kb >> kExpandShift) + 2u);
+}
+
+__global__ void __launch_bounds__(kCountThreads) expand_count_kernel(const uint32_t* __restrict__ mask,
+                                                                     const uint32_t* __restrict__ bstart,
+                                                                     const uint32_t* __restrict__ bend,
+                                                                     uint32_t n_blocks, uint32_t n_ids,
+                                                                     const DeviceStatus* __restrict__ st,
+                                                                     const uint32_t* __restrict__ map,
+                                                                     uint32_t* __restrict__ C) {
+    __shared__ uint32_t s_c[32];
+    __shared__ uint32_t s_used;
+    pdl_enter();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_used = chunk_ids_used(st, n_blocks, n_ids);
+    __syncthreads();
+    const uint32_t used = s_used;
+    for (uint32_t id = blockIdx.x; id < used; id += gridDim.x) {
+        const uint32_t b = chunk_block(id, n_blocks, map);
+        if (b == 0xffffffffu) continue;
+        if (threadIdx.x < 32) s_c[threadIdx.x] = 0u;
+        __syncthreads();
+        const uint2 r = block_range(bstart, bend, b);
+        const uint32_t i = id < n_blocks ? 0u : id - n_blocks - (r.x >> kExpandShift);
+        const uint32_t c0 = r.x + i * kExpandChunk, c1 = min(r.y, c0 + kExpandChunk);
+        // lane t counts bit t over the warp's 8 groups of 32 entries
+        uint32_t m[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const uint32_t j = c0 + (uint32_t)(256 * w + 32 * q + lane);
+            m[q] = j < c1 ? __ldg(mask + j) : 0u;
+        }
+        uint32_t n = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) n += __popc(warp_transpose32(m[q], lane));
+        atomicAdd(&s_c[lane], n);
+        __syncthreads();
+        if (threadIdx.x < 32) C[(size_t)id * 32 + threadIdx.x] = s_c[threadIdx.x];
+        __syncthreads();
+    }
+}
+
+// One warp per block, lane t for tile bit t.
+__global__ void expand_offsets_kernel(const uint32_t* __restrict__ bstart, const uint32_t* __restrict__ bend,
+                                      uint32_t n_blocks, const CamDev* __restrict__ cams, int n_cams,
+                                      const DeviceStatus* __restrict__ st, const uint32_t* __restrict__ C,
+                                      uint32_t* __restrict__ Co, uint32_t* __restrict__ Lt,
+                                      uint32_t* __restrict__ chunk_total) {
+    pdl_enter();
+    if (st->error != kOk) return;
+    const int lane = threadIdx.x & 31;
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < n_blocks; b += warps) {
+        const uint2 r = block_range(bstart, bend, b);
+        const uint32_t n = (r.y - r.x + kExpandChunk - 1) >> kExpandShift;
+        uint32_t run = 0;
+        for (uint32_t i = 0; i < n; ++i) {
+            const size_t k = (size_t)chunk_id(b, r.x, i, n_blocks) * 32 + lane;
+            const uint32_t v = __ldg(C + k);
+            Co[k] = run;
+            run += v;
+        }
+        const uint32_t g = block_tile(cams, n_cams, b, lane);
+        if (g != 0xffffffffu) {
+            Lt[g] = run;
+            if (run != 0u) atomicAdd(chunk_total + (g >> 5), run);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kExpandThreads) expand_write_kernel(
+    const uint32_t* __restrict__ rec_ids, const uint32_t* __restrict__ mask, const uint32_t* __restrict__ bstart,
+    const uint32_t* __restrict__ bend, uint32_t n_blocks, uint32_t n_ids, const uint32_t* __restrict__ map,
+    const uint32_t* __restrict__ Co,
+    const uint32_t* __restrict__ Lt, const uint32_t* __restrict__ St, const CamDev* __restrict__ cams, int n_cams,
+    uint32_t n_tiles, uint32_t capacity, DeviceStatus* st, uint32_t* __restrict__ out_rec,
+    uint32_t* __restrict__ ranges) {
+    __shared__ uint32_t s_mask[kExpandChunk];
+    __shared__ uint32_t s_rec[kExpandChunk];
+    __shared__ uint32_t s_wc[kExpandThreads / 32][33];  // per warp and tile: count, then start
+    __shared__ int32_t s_err;
+    __shared__ uint32_t s_used;
+    pdl_enter();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // K_t = the last tile's start plus its count; every CTA checks it alike
+    const uint32_t K = __ldg(St + n_tiles - 1) + __ldg(Lt + n_tiles - 1);
+    // read once for the whole CTA: CTA 0 replaces the instance count below
+    // (a CTA that reads it afterwards only visits more empty chunk ids)
+    if (threadIdx.x == 0) {
+        s_err = *(volatile const int32_t*)&st->error;
+        s_used = chunk_ids_used(st, n_blocks, n_ids);
+    }
+    __syncthreads();
+    if (s_err != kOk) return;
+    if (K > capacity) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            st->n_instances = K;
+            st->capacity = capacity;
+            record_error(st, kErrCapacity, 11);
+        }
+        return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->n_instances = K;
+        st->capacity = capacity;
+        st->n_inst_valid = K;
+    }
+    const uint32_t used = s_used;
+    for (uint32_t id = blockIdx.x; id < used; id += gridDim.x) {
+        const uint32_t b = chunk_block(id, n_blocks, map);
+        if (b == 0xffffffffu) continue;
+        const uint2 r = block_range(bstart, bend, b);
+        const uint32_t i = id < n_blocks ? 0u : id - n_blocks - (r.x >> kExpandShift);
+        const uint32_t c0 = r.x + i * kExpandChunk, c1 = min(r.y, c0 + kExpandChunk), n = c1 - c0;
+        __syncthreads();  // the previous chunk's staging is no longer read
+        for (uint32_t k = threadIdx.x; k < n; k += kExpandThreads) {
+            s_mask[k] = __ldg(mask + c0 + k);
+            s_rec[k] = __ldg(rec_ids + c0 + k);
+        }
+        __syncthreads();
+        // warp w takes entries [64 w, 64 w + 64) of the chunk, two groups of
+        // 32; after the transpose lane t holds, per group, which of them reach
+        // tile t.  First each warp's count per tile, then, from the tiles' list
+        // starts, the warps' own starts, then lane t writes its tile's entries.
+        uint32_t col[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const uint32_t k = 64u * (uint32_t)w + 32u * (uint32_t)q + (uint32_t)lane;
+            col[q] = warp_transpose32(k < n ? s_mask[k] : 0u, lane);
+        }
+        s_wc[w][lane] = __popc(col[0]) + __popc(col[1]);
+        __syncthreads();
+        if (w == 0) {
+            const uint32_t g0 = block_tile(cams, n_cams, b, lane);
+            uint32_t run = g0 == 0xffffffffu ? 0u : __ldg(St + g0) + __ldg(Co + (size_t)id * 32 + lane);
+            if (g0 != 0xffffffffu && i == 0) {
+                ranges[g0] = __ldg(St + g0);
+                ranges[n_tiles + g0] = __ldg(St + g0) + __ldg(Lt + g0);
+            }
+            for (int ww = 0; ww < kExpandThreads / 32; ++ww) {
+                const uint32_t x = s_wc[ww][lane];
+                s_wc[ww][lane] = run;
+                run += x;
+            }
+        }
+        __syncthreads();
+        // the warp writes one tile's run at a time (coalesced): lane e stores
+        // its own entry when it reaches the tile
+        uint32_t pos = s_wc[w][lane];
+        const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const uint32_t k = 64u * (uint32_t)w + 32u * (uint32_t)q + (uint32_t)lane;
+            const uint32_t r = k < n ? s_rec[k] : 0u;
+            for (uint32_t busy = __ballot_sync(0xffffffffu, col[q] != 0u); busy != 0u; busy &= busy - 1u) {
+                const int tt = __ffs(busy) - 1;
+                const uint32_t c = __shfl_sync(0xffffffffu, col[q], tt);
+                const uint32_t p = __shfl_sync(0xffffffffu, pos, tt);
+                if ((c >> lane) & 1u) {
+                    const uint32_t o = p + __popc(c & lt);
+                    if (o < capacity) out_rec[o] = r;
+                }
+            }
+            pos += __popc(col[q]);
+        }
+    }
+}
+
+void launch_tile_expand(const uint32_t* rec_ids, const uint32_t* mask, const uint32_t* bstart, const uint32_t* bend,
+                        uint32_t n_blocks, const CamDev* cams, int n_cams, uint32_t n_tiles, uint32_t n_ids,
+                        uint32_t capacity, DeviceStatus* st, uint32_t* map, uint32_t* C, uint32_t* Co, uint32_t* Lt,
+                        uint32_t* chunk_total, uint32_t* St, uint32_t* out_rec, uint32_t* ranges, cudaStream_t s) {
+    const uint32_t nb = std::max<uint32_t>(n_blocks, 1u);
+    launch_pdl(expand_map_kernel, dim3(std::min<uint32_t>((nb + 255) / 256, 1024u)), dim3(256), 0, s, bstart, bend,
+               n_blocks, (const DeviceStatus*)st, n_ids - n_blocks, map);
+    int sms = 152;
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    launch_pdl(expand_count_kernel, dim3(std::min<uint32_t>(n_ids, 8u * (uint32_t)sms)), dim3(kCountThreads), 0, s,
+               mask, bstart, bend, n_blocks, n_ids, (const DeviceStatus*)st, (const uint32_t*)map, C);
+    launch_pdl(expand_offsets_kernel, dim3(std::min<uint32_t>((nb + 7) / 8, 2048u)), dim3(256), 0, s, bstart, bend,
+               n_blocks, cams, n_cams, (const DeviceStatus*)st, (const uint32_t*)C, Co, Lt, chunk_total);
+    const uint32_t chunks = (n_tiles + 31) / 32;
+    launch_digit_scan(Lt, 32, chunk_total, St, s, chunks);
+    launch_pdl(expand_write_kernel, dim3(std::min<uint32_t>(n_ids, 2u * (uint32_t)sms)), dim3(kExpandThreads), 0, s,
+               rec_ids, mask, bstart, bend, n_blocks, n_ids, (const uint32_t*)map, (const uint32_t*)Co, (const uint32_t*)Lt, (const uint32_t*)St, cams, n_cams,
+               n_tiles, capacity, st, out_rec, ranges);
+}
+
 // After the block sort: the OR of the tile masks of every 32 consecutive
 // entries (aligned to the list array), so a tile's rasterizer can skip 32
 // entries of its block list with one load when none of them reaches it.
@@ -217,11 +378,14 @@ void launch_mask_summary(const uint32_t* mask, const DeviceStatus* st, uint32_t*
 // left for the end of the kernel.  Order within a bucket is free.
 constexpr int kOrderBuckets = 64;
 
+constexpr uint32_t kOrderCache = 32768;  // units whose buckets stay in shared memory
+
 __global__ void __launch_bounds__(1024) block_order_kernel(const uint32_t* __restrict__ bstart,
                                                            const uint32_t* __restrict__ bend, uint32_t n_blocks,
                                                            uint32_t* __restrict__ order) {
     __shared__ uint32_t s_hist[kOrderBuckets];
     __shared__ uint32_t s_pos[kOrderBuckets];
+    __shared__ uint8_t s_bucket[kOrderCache];
     pdl_enter();
     auto bucket = [&](uint32_t b) -> int {
         const uint32_t s = __ldg(bstart + b), e = __ldg(bend + b);
@@ -234,7 +398,15 @@ __global__ void __launch_bounds__(1024) block_order_kernel(const uint32_t* __res
     };
     for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x) s_hist[i] = 0;
     __syncthreads();
-    for (uint32_t b = threadIdx.x; b < n_blocks; b += blockDim.x) atomicAdd(&s_hist[bucket(b)], 1u);
+    // the units' buckets, computed once (their loads in flight together) and
+    // kept in shared memory when they fit
+    const bool cached = n_blocks <= kOrderCache;
+#pragma unroll 4
+    for (uint32_t b = threadIdx.x; b < n_blocks; b += blockDim.x) {
+        const int k = bucket(b);
+        if (cached) s_bucket[b] = (uint8_t)k;
+        atomicAdd(&s_hist[k], 1u);
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         uint32_t run = 0;
@@ -244,7 +416,9 @@ __global__ void __launch_bounds__(1024) block_order_kernel(const uint32_t* __res
         }
     }
     __syncthreads();
-    for (uint32_t b = threadIdx.x; b < n_blocks; b += blockDim.x) order[atomicAdd(&s_pos[bucket(b)], 1u)] = b;
+#pragma unroll 4
+    for (uint32_t b = threadIdx.x; b < n_blocks; b += blockDim.x)
+        order[atomicAdd(&s_pos[cached ? (int)s_bucket[b] : bucket(b)], 1u)] = b;
 }
 
 void launch_block_order(const uint32_t* bstart, const uint32_t* bend, uint32_t n_blocks, uint32_t* order,
@@ -365,14 +539,6 @@ void launch_view_order(const uint32_t* bstart, const uint32_t* bend, uint32_t n_
 }
 
 template <typename KeyT>
-void launch_emit(const uint32_t* order, const uint32_t* offsets, const float4* rec,
-                 const CamDev* cams, int n_gauss, int tile_w, int tile_h, int ellipse, DeviceStatus* st,
-                 KeyT* inst_tile, uint32_t* inst_rec, int blocks, cudaStream_t s) {
-    launch_pdl(emit_kernel<KeyT>, dim3(blocks), dim3(256), 0, s, order, offsets, rec, cams, n_gauss, tile_w, tile_h,
-               ellipse, st, inst_tile, inst_rec);
-}
-
-template <typename KeyT>
 void launch_emit_blocks(const uint32_t* order, const uint32_t* offsets, const float4* rec,
                         const CamDev* cams, int n_gauss, int tile_w, int tile_h, int ellipse, DeviceStatus* st,
                         KeyT* inst_block, uint32_t* inst_rec, uint32_t* inst_mask, int blocks, cudaStream_t s) {
@@ -386,9 +552,5 @@ template void launch_emit_blocks<uint16_t>(const uint32_t*, const uint32_t*, con
 template void launch_emit_blocks<uint32_t>(const uint32_t*, const uint32_t*, const float4*,
                                            const CamDev*, int, int, int, int, DeviceStatus*, uint32_t*, uint32_t*,
                                            uint32_t*, int, cudaStream_t);
-template void launch_emit<uint16_t>(const uint32_t*, const uint32_t*, const float4*, const CamDev*,
-                                    int, int, int, int, DeviceStatus*, uint16_t*, uint32_t*, int, cudaStream_t);
-template void launch_emit<uint32_t>(const uint32_t*, const uint32_t*, const float4*, const CamDev*,
-                                    int, int, int, int, DeviceStatus*, uint32_t*, uint32_t*, int, cudaStream_t);
 
 }  // namespace seele

@@ -29,10 +29,10 @@ void launch_compact_visible(const uint32_t* cnt, bool pack, const float* depth, 
 void launch_scan_tiles(const uint32_t* cnt_sorted, uint32_t* chunk_sum, uint32_t max_n, uint32_t* offsets,
                        DeviceStatus* st, uint32_t capacity, cudaStream_t s);
 
-// Exclusive scan of a 256 x stride digit-major count matrix given its row
-// totals (no look-back).
+// Exclusive scan of a rows x stride row-major count matrix given its row
+// totals (no look-back); a radix pass has 256 rows, one per digit.
 void launch_digit_scan(const uint32_t* in, uint32_t stride, const uint32_t* row_total, uint32_t* out,
-                       cudaStream_t s);
+                       cudaStream_t s, uint32_t rows = 256);
 // Single-pass scan with decoupled look-back (in 16-byte aligned).  status:
 // one word per block (exclusive_scan_blocks), entries of other epochs read as
 // unpublished; st->ticket[ticket] must be zero.  spin_limit: polls of a
@@ -87,14 +87,23 @@ int radix_sort_pairs(KeyT* keys[2], uint32_t* vals[2], const uint32_t* count_ptr
                      uint32_t* const* aux = nullptr, const SortGather* gather = nullptr);
 
 template <typename KeyT>
-void launch_emit(const uint32_t* order, const uint32_t* offsets, const float4* rec,
-                 const CamDev* cams, int n_gauss, int tile_w, int tile_h, int ellipse, DeviceStatus* st,
-                 KeyT* inst_tile, uint32_t* inst_rec, int blocks, cudaStream_t s);
-
-template <typename KeyT>
 void launch_emit_blocks(const uint32_t* order, const uint32_t* offsets, const float4* rec,
                         const CamDev* cams, int n_gauss, int tile_w, int tile_h, int ellipse, DeviceStatus* st,
                         KeyT* inst_block, uint32_t* inst_rec, uint32_t* inst_mask, int blocks, cudaStream_t s);
+
+// Tile binning through the blocks (binning.cu): the tile lists in tile
+// order, made from the sorted block lists (each block's list filtered by
+// each tile's bit, in order), and the tiles' ranges (starts[n_tiles], then
+// ends), with K_t checked against the capacity.  Scratch: map (n_ids -
+// n_blocks words, cleared to all-ones), C and Co (32 n_ids words each), Lt
+// (32 ceil(n_tiles / 32) words, cleared), chunk_total (ceil(n_tiles / 32)
+// words, cleared), St (like Lt); n_ids = expand_chunk_ids(capacity,
+// n_blocks).
+uint32_t expand_chunk_ids(uint64_t capacity, uint64_t n_blocks);
+void launch_tile_expand(const uint32_t* rec_ids, const uint32_t* mask, const uint32_t* bstart, const uint32_t* bend,
+                        uint32_t n_blocks, const CamDev* cams, int n_cams, uint32_t n_tiles, uint32_t n_ids,
+                        uint32_t capacity, DeviceStatus* st, uint32_t* map, uint32_t* C, uint32_t* Co, uint32_t* Lt,
+                        uint32_t* chunk_total, uint32_t* St, uint32_t* out_rec, uint32_t* ranges, cudaStream_t s);
 
 // Block binning: OR of the tile masks of every 32 list entries, and the
 // order in which the rasterizer visits tile blocks (longest lists first).

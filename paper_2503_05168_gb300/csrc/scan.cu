@@ -274,16 +274,18 @@ __global__ void __launch_bounds__(kScanThreads) scan_tiles_kernel(const uint32_t
     }
 }
 
-// Exclusive scan of the digit-major count matrix in[d * stride + t] (256 rows
-// of stride) given its row totals: the elements before scan tile s are the
-// whole rows d < d0 and the first t0 entries of row d0, so each block adds
-// those up itself and no block waits on another.
+// Exclusive scan of the row-major count matrix in[d * stride + t] (rows of
+// stride: a radix pass's 256 digits, or the tile blocks of tile binning with
+// their 32 tiles each) given its row totals: the elements before scan tile s
+// are the whole rows d < d0 and the first t0 entries of row d0, so each
+// block adds those up itself and no block waits on another.
 __global__ void __launch_bounds__(kScanThreads) digit_scan_kernel(const uint32_t* __restrict__ in, uint32_t stride,
+                                                                  uint32_t rows,
                                                                   const uint32_t* __restrict__ row_total,
                                                                   uint32_t* __restrict__ out) {
     __shared__ uint32_t s_part[kScanThreads / 32];
     pdl_enter();
-    const uint32_t n = 256u * stride;
+    const uint32_t n = rows * stride;
     const uint32_t first = blockIdx.x * kScanTile;
     const uint32_t base = first + threadIdx.x * kScanItems;
     uint32_t c[kScanItems];
@@ -302,7 +304,8 @@ __global__ void __launch_bounds__(kScanThreads) digit_scan_kernel(const uint32_t
         for (int k = 0; k < kScanItems; ++k) c[k] = base + k < n ? __ldg(in + base + k) : 0u;
     }
     const uint32_t d0 = first / stride, t0 = first - d0 * stride;
-    uint32_t part = threadIdx.x < d0 ? __ldg(row_total + threadIdx.x) : 0u;
+    uint32_t part = 0;
+    for (uint32_t d = threadIdx.x; d < d0; d += kScanThreads) part += __ldg(row_total + d);
     const uint32_t* row = in + (size_t)d0 * stride;
     for (uint32_t t = threadIdx.x; t < t0; t += kScanThreads) part += __ldg(row + t);
 #pragma unroll
@@ -363,9 +366,9 @@ __global__ void __launch_bounds__(kScanThreads) exclusive_scan_kernel(const uint
 }
 
 void launch_digit_scan(const uint32_t* in, uint32_t stride, const uint32_t* row_total, uint32_t* out,
-                       cudaStream_t s) {
-    const uint32_t blocks = (256u * stride + kScanTile - 1) / kScanTile;
-    launch_pdl(digit_scan_kernel, dim3(blocks), dim3(kScanThreads), 0, s, in, stride, row_total, out);
+                       cudaStream_t s, uint32_t rows) {
+    const uint32_t blocks = std::max<uint32_t>((rows * stride + kScanTile - 1) / kScanTile, 1u);
+    launch_pdl(digit_scan_kernel, dim3(blocks), dim3(kScanThreads), 0, s, in, stride, rows, row_total, out);
 }
 
 void launch_exclusive_scan(const uint32_t* in, uint32_t n, uint32_t* out, uint64_t* status, uint32_t epoch,
