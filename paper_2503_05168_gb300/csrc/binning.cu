@@ -76,9 +76,9 @@ __global__ void __launch_bounds__(256) emit_blocks_kernel(const uint32_t* __rest
 //                   capacity.
 constexpr int kExpandShift = 11;
 constexpr uint32_t kExpandChunk = 1u << kExpandShift;
-constexpr int kExpandThreads = 1024;  // expand_write: one warp per tile bit
-static_assert(kExpandThreads == 32 * kBlockW * kBlockH, "a warp per tile of the block");
-static_assert(kExpandChunk == 2 * kExpandThreads, "two staged entries per thread");
+constexpr int kExpandThreads = 256;   // expand_write: 8 warps of 8 groups of 32 entries
+constexpr int kExpandGroups = kExpandChunk / kExpandThreads;
+static_assert(kExpandGroups == 8 && kBlockW * kBlockH == 32, "a lane per tile of the block");
 constexpr int kCountThreads = 256;    // expand_count: 8 entries per thread
 static_assert(kExpandChunk == 8 * kCountThreads, "eight counted entries per thread");
 
@@ -233,8 +233,6 @@ __global__ void __launch_bounds__(kExpandThreads) expand_write_kernel(
     const uint32_t* __restrict__ Lt, const uint32_t* __restrict__ St, const CamDev* __restrict__ cams, int n_cams,
     uint32_t n_tiles, uint32_t capacity, DeviceStatus* st, uint32_t* __restrict__ out_rec,
     uint32_t* __restrict__ ranges) {
-    __shared__ uint32_t s_mask[kExpandChunk];
-    __shared__ uint32_t s_rec[kExpandChunk];
     __shared__ uint32_t s_wc[kExpandThreads / 32][33];  // per warp and tile: count, then start
     __shared__ int32_t s_err;
     __shared__ uint32_t s_used;
@@ -270,23 +268,21 @@ __global__ void __launch_bounds__(kExpandThreads) expand_write_kernel(
         const uint2 r = block_range(bstart, bend, b);
         const uint32_t i = id < n_blocks ? 0u : id - n_blocks - (r.x >> kExpandShift);
         const uint32_t c0 = r.x + i * kExpandChunk, c1 = min(r.y, c0 + kExpandChunk), n = c1 - c0;
-        __syncthreads();  // the previous chunk's staging is no longer read
-        for (uint32_t k = threadIdx.x; k < n; k += kExpandThreads) {
-            s_mask[k] = __ldg(mask + c0 + k);
-            s_rec[k] = __ldg(rec_ids + c0 + k);
-        }
-        __syncthreads();
-        // warp w takes entries [64 w, 64 w + 64) of the chunk, two groups of
-        // 32; after the transpose lane t holds, per group, which of them reach
-        // tile t.  First each warp's count per tile, then, from the tiles' list
-        // starts, the warps' own starts, then lane t writes its tile's entries.
-        uint32_t col[2];
+        // warp w takes entries [256 w, 256 w + 256) of the chunk, 8 groups of
+        // 32, in registers; after the transpose lane t holds, per group,
+        // which of them reach tile t.  First each warp's count per tile, then,
+        // from the tiles' list starts, the warps' own starts, then the writes.
+        uint32_t col[kExpandGroups], rq[kExpandGroups], cnt = 0;
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const uint32_t k = 64u * (uint32_t)w + 32u * (uint32_t)q + (uint32_t)lane;
-            col[q] = warp_transpose32(k < n ? s_mask[k] : 0u, lane);
+        for (int q = 0; q < kExpandGroups; ++q) {
+            const uint32_t k = 32u * (kExpandGroups * (uint32_t)w + (uint32_t)q) + (uint32_t)lane;
+            const bool ok = k < n;
+            rq[q] = ok ? __ldg(rec_ids + c0 + k) : 0u;
+            col[q] = warp_transpose32(ok ? __ldg(mask + c0 + k) : 0u, lane);
+            cnt += __popc(col[q]);
         }
-        s_wc[w][lane] = __popc(col[0]) + __popc(col[1]);
+        __syncthreads();  // the previous chunk's starts have been read
+        s_wc[w][lane] = cnt;
         __syncthreads();
         if (w == 0) {
             const uint32_t g0 = block_tile(cams, n_cams, b, lane);
@@ -295,6 +291,7 @@ __global__ void __launch_bounds__(kExpandThreads) expand_write_kernel(
                 ranges[g0] = __ldg(St + g0);
                 ranges[n_tiles + g0] = __ldg(St + g0) + __ldg(Lt + g0);
             }
+#pragma unroll
             for (int ww = 0; ww < kExpandThreads / 32; ++ww) {
                 const uint32_t x = s_wc[ww][lane];
                 s_wc[ww][lane] = run;
@@ -303,23 +300,22 @@ __global__ void __launch_bounds__(kExpandThreads) expand_write_kernel(
         }
         __syncthreads();
         // the warp writes one tile's run at a time (coalesced): lane e stores
-        // its own entry when it reaches the tile
-        uint32_t pos = s_wc[w][lane];
+        // its own entry when it reaches the tile; every tile in turn,
+        // unrolled, so that the shuffles of different tiles overlap
+        const uint32_t pos = s_wc[w][lane];
         const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const uint32_t k = 64u * (uint32_t)w + 32u * (uint32_t)q + (uint32_t)lane;
-            const uint32_t r = k < n ? s_rec[k] : 0u;
-            for (uint32_t busy = __ballot_sync(0xffffffffu, col[q] != 0u); busy != 0u; busy &= busy - 1u) {
-                const int tt = __ffs(busy) - 1;
+        for (int tt = 0; tt < 32; ++tt) {
+            uint32_t p = __shfl_sync(0xffffffffu, pos, tt);
+#pragma unroll
+            for (int q = 0; q < kExpandGroups; ++q) {
                 const uint32_t c = __shfl_sync(0xffffffffu, col[q], tt);
-                const uint32_t p = __shfl_sync(0xffffffffu, pos, tt);
                 if ((c >> lane) & 1u) {
                     const uint32_t o = p + __popc(c & lt);
-                    if (o < capacity) out_rec[o] = r;
+                    if (o < capacity) out_rec[o] = rq[q];
                 }
+                p += __popc(c);
             }
-            pos += __popc(col[q]);
         }
     }
 }
@@ -343,7 +339,7 @@ void launch_tile_expand(const uint32_t* rec_ids, const uint32_t* mask, const uin
                n_blocks, cams, n_cams, (const DeviceStatus*)st, (const uint32_t*)C, Co, Lt, chunk_total);
     const uint32_t chunks = (n_tiles + 31) / 32;
     launch_digit_scan(Lt, 32, chunk_total, St, s, chunks);
-    launch_pdl(expand_write_kernel, dim3(std::min<uint32_t>(n_ids, 2u * (uint32_t)sms)), dim3(kExpandThreads), 0, s,
+    launch_pdl(expand_write_kernel, dim3(std::min<uint32_t>(n_ids, 8u * (uint32_t)sms)), dim3(kExpandThreads), 0, s,
                rec_ids, mask, bstart, bend, n_blocks, n_ids, (const uint32_t*)map, (const uint32_t*)Co, (const uint32_t*)Lt, (const uint32_t*)St, cams, n_cams,
                n_tiles, capacity, st, out_rec, ranges);
 }
@@ -387,8 +383,7 @@ __global__ void __launch_bounds__(1024) block_order_kernel(const uint32_t* __res
     __shared__ uint32_t s_pos[kOrderBuckets];
     __shared__ uint8_t s_bucket[kOrderCache];
     pdl_enter();
-    auto bucket = [&](uint32_t b) -> int {
-        const uint32_t s = __ldg(bstart + b), e = __ldg(bend + b);
+    auto bucket_of = [](uint32_t s, uint32_t e) -> int {
         const uint32_t len = s < e ? e - s : 0u;
         // 4 buckets per octave, longest lists in bucket 0
         const uint32_t v = len + 1u;
@@ -396,16 +391,30 @@ __global__ void __launch_bounds__(1024) block_order_kernel(const uint32_t* __res
         const int frac = lg >= 2 ? (int)((v >> (lg - 2)) & 3u) : (int)((v << (2 - lg)) & 3u);
         return kOrderBuckets - 1 - min(kOrderBuckets - 1, lg * 4 + frac);
     };
+    auto bucket = [&](uint32_t b) -> int { return bucket_of(__ldg(bstart + b), __ldg(bend + b)); };
     for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x) s_hist[i] = 0;
     __syncthreads();
-    // the units' buckets, computed once (their loads in flight together) and
-    // kept in shared memory when they fit
+    // the units' buckets, computed once and kept in shared memory when they
+    // fit; each thread issues the loads of 16 units before using any
     const bool cached = n_blocks <= kOrderCache;
-#pragma unroll 4
-    for (uint32_t b = threadIdx.x; b < n_blocks; b += blockDim.x) {
-        const int k = bucket(b);
-        if (cached) s_bucket[b] = (uint8_t)k;
-        atomicAdd(&s_hist[k], 1u);
+    constexpr int kPer = 16;
+    for (uint32_t base = 0; base < n_blocks; base += kPer * blockDim.x) {
+        uint32_t sv[kPer], ev[kPer];
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const uint32_t b = base + (uint32_t)q * blockDim.x + threadIdx.x;
+            sv[q] = b < n_blocks ? __ldg(bstart + b) : 0u;
+            ev[q] = b < n_blocks ? __ldg(bend + b) : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const uint32_t b = base + (uint32_t)q * blockDim.x + threadIdx.x;
+            if (b < n_blocks) {
+                const int k = bucket_of(sv[q], ev[q]);
+                if (cached) s_bucket[b] = (uint8_t)k;
+                atomicAdd(&s_hist[k], 1u);
+            }
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -416,7 +425,6 @@ __global__ void __launch_bounds__(1024) block_order_kernel(const uint32_t* __res
         }
     }
     __syncthreads();
-#pragma unroll 4
     for (uint32_t b = threadIdx.x; b < n_blocks; b += blockDim.x)
         order[atomicAdd(&s_pos[cached ? (int)s_bucket[b] : bucket(b)], 1u)] = b;
 }
