@@ -42,14 +42,15 @@ static bool launch_shape(const RasterArgs& a, cudaStream_t s) {
     return true;
 }
 
-// 8x8 tiles: one pixel per thread (two warps); every group spans threads
+// 8x8 tiles: a pair of pixels in a row per thread, one warp per tile; a group
+// of two or more columns is whole threads
 static bool launch_shape_8x8(const RasterArgs& a, cudaStream_t s) {
-    if (!a.cr) launch_one<8, 8, 1, 1, 1, 1, false>(a, s);
-    else if (a.group_w == 2 && a.group_h == 2) launch_one<8, 8, 1, 1, 2, 2, true>(a, s);
-    else if (a.group_w == 1 && a.group_h == 1) launch_one<8, 8, 1, 1, 1, 1, true>(a, s);
-    else if (a.group_w == 2 && a.group_h == 4) launch_one<8, 8, 1, 1, 2, 4, true>(a, s);
-    else if (a.group_w == 4 && a.group_h == 4) launch_one<8, 8, 1, 1, 4, 4, true>(a, s);
-    else if (a.group_w == 4 && a.group_h == 8) launch_one<8, 8, 1, 1, 4, 8, true>(a, s);
+    if (!a.cr) launch_one<8, 8, 2, 1, 1, 1, false>(a, s);
+    else if (a.group_w == 2 && a.group_h == 2) launch_one<8, 8, 2, 1, 2, 2, true>(a, s);
+    else if (a.group_w == 1 && a.group_h == 1) launch_one<8, 8, 2, 1, 1, 1, true>(a, s);
+    else if (a.group_w == 2 && a.group_h == 4) launch_one<8, 8, 2, 1, 2, 4, true>(a, s);
+    else if (a.group_w == 4 && a.group_h == 4) launch_one<8, 8, 2, 1, 4, 4, true>(a, s);
+    else if (a.group_w == 4 && a.group_h == 8) launch_one<8, 8, 2, 1, 4, 8, true>(a, s);
     else return false;
     return true;
 }

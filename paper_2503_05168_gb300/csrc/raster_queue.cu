@@ -37,7 +37,7 @@ void launch_raster_queue(const RasterArgs& a, cudaStream_t s) {
 SEELE_QUEUE_SHAPE(16, 16, 2, 2)
 SEELE_QUEUE_SHAPE(32, 8, 2, 2)
 SEELE_QUEUE_SHAPE(32, 16, 2, 2)
-SEELE_QUEUE_SHAPE(8, 8, 1, 1)
+SEELE_QUEUE_SHAPE(8, 8, 2, 1)
 #define SEELE_QUEUE_CR(TW, TH, PW, PH, GW, GH)                                                          \
     template void launch_raster_queue<TW, TH, PW, PH, GW, GH, true, false>(const RasterArgs&, cudaStream_t); \
     template void launch_raster_queue<TW, TH, PW, PH, GW, GH, true, true>(const RasterArgs&, cudaStream_t);
@@ -49,9 +49,9 @@ SEELE_QUEUE_SHAPE(8, 8, 1, 1)
 SEELE_QUEUE_CR_SHAPE(16, 16)
 SEELE_QUEUE_CR_SHAPE(32, 8)
 SEELE_QUEUE_CR_SHAPE(32, 16)
-SEELE_QUEUE_CR(8, 8, 1, 1, 2, 2)
-SEELE_QUEUE_CR(8, 8, 1, 1, 2, 4)
-SEELE_QUEUE_CR(8, 8, 1, 1, 4, 4)
-SEELE_QUEUE_CR(8, 8, 1, 1, 4, 8)
+SEELE_QUEUE_CR(8, 8, 2, 1, 2, 2)
+SEELE_QUEUE_CR(8, 8, 2, 1, 2, 4)
+SEELE_QUEUE_CR(8, 8, 2, 1, 4, 4)
+SEELE_QUEUE_CR(8, 8, 2, 1, 4, 8)
 
 }  // namespace seele
