@@ -11,9 +11,13 @@
 //   final T, or the forward pass's checkpoint there), and S, the colour
 //   accumulated behind entry j, gives
 //     dC/dc_j = T_j alpha_j,   dC/dalpha_j = T_j c_j - S / (1 - alpha_j).
-//   Gradients w.r.t. the record (u, v, cA, cB, cC, log2 o, r, g, b) are
-//   summed over the warp's pixels and added with one atomic per value.  The
-//   pixels of a thread run branch-free under a per-pixel predicate.
+//   Only g . dC/dalpha_j enters the gradient (g = dL/dC of the pixel), so a
+//   pixel keeps the scalar g . S instead of S.  Gradients w.r.t. the record
+//   (u, v, cA, cB, cC, log2 o, r, g, b) are summed over the warp's pixels and
+//   added with one atomic per value; the exponent's terms are summed as
+//   moments of the pixel offsets (sum de dx, de dy, de dx^2, ...) and turned
+//   into du, dv once per entry.  The pixels of a thread run branch-free under
+//   a per-pixel predicate.
 // preprocess_bwd_kernel: one thread per Gaussian, summing over cameras, runs
 //   the chain rule back through the raster record, the conic, the EWA
 //   projection, the covariance, the quaternion and the SH colour.
@@ -113,7 +117,7 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
 
     const size_t plane = (size_t)C.W * C.H;
     const float* gimg = dL_drgb + 3 * (size_t)C.pix_offset;
-    float T[NP], g0[NP], g1[NP], g2[NP], S0[NP], S1[NP], S2[NP];
+    float T[NP], g0[NP], g1[NP], g2[NP], gS[NP];  // gS = g . (colour behind)
     uint32_t last[NP];
     uint32_t my_max = 0;
 #pragma unroll
@@ -121,7 +125,7 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
         const int x = bx + p % PW, y = by + p / PW;
         T[p] = 1.f;
         g0[p] = g1[p] = g2[p] = 0.f;
-        S0[p] = S1[p] = S2[p] = 0.f;
+        gS[p] = 0.f;
         last[p] = 0;
         if (x < C.W && y < C.H) {
             const size_t o = (size_t)y * C.W + x;
@@ -153,9 +157,7 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
                 const float4 k = __ldg(slot + (y - ty * TH) * TW + (x - tx * TW));
                 const float4 f = __ldg(cfin + C.pix_offset + (size_t)y * C.W + x);
                 T[p] = k.x;
-                S0[p] = f.y - k.y;
-                S1[p] = f.z - k.z;
-                S2[p] = f.w - k.w;
+                gS[p] = g0[p] * (f.y - k.y) + g1[p] * (f.z - k.z) + g2[p] * (f.w - k.w);
             }
         }
     }
@@ -185,7 +187,9 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
                 const float ddx = dx + (float)i, ddy = dy + (float)jj;
                 return fmaf(fmaf(A.z, ddx, A.w * ddy), ddx, fmaf(B.x * ddy, ddy, B.y));
             };
-            float du = 0.f, dv = 0.f, dcA = 0.f, dcB = 0.f, dcC = 0.f, dlo = 0.f, dr = 0.f, dg = 0.f, db = 0.f;
+            // per lane: sums of de, de dx, de dy, de dx^2, de dx dy, de dy^2 and
+            // of the colour weights
+            float sde = 0.f, sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f, dr = 0.f, dg = 0.f, db = 0.f;
             const bool clampable = Cc.w != 0.f;  // the record's alpha can reach alpha_max
             // Which of the thread's pixels did the forward pass blend this
             // entry into (before its last blend, inside the support, alpha >=
@@ -233,37 +237,37 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
                 const float inv = rcp_approx_b(1.f - al);
                 const float Tb = T[p] * inv;  // transmittance before this entry
                 const float wgt = m ? Tb * al : 0.f;
-                const float dal = g0[p] * (Tb * Cc.x - S0[p] * inv) + g1[p] * (Tb * Cc.y - S1[p] * inv) +
-                                  g2[p] * (Tb * Cc.z - S2[p] * inv);
+                const float gc = fmaf(g2[p], Cc.z, fmaf(g1[p], Cc.y, g0[p] * Cc.x));
+                const float dal = fmaf(Tb, gc, -gS[p] * inv);
                 dr = fmaf(wgt, g0[p], dr);
                 dg = fmaf(wgt, g1[p], dg);
                 db = fmaf(wgt, g2[p], db);
-                S0[p] = fmaf(wgt, Cc.x, S0[p]);
-                S1[p] = fmaf(wgt, Cc.y, S1[p]);
-                S2[p] = fmaf(wgt, Cc.z, S2[p]);
+                gS[p] = fmaf(wgt, gc, gS[p]);
                 T[p] = m ? Tb : T[p];
                 // at the clamp alpha is constant: no gradient through e
                 const float de = (m && (!clampable || al < amax)) ? dal * al * kLn2 : 0.f;
                 const float ddx = dx + (float)pi, ddy = dy + (float)pj;
-                du -= de * (2.f * A.z * ddx + A.w * ddy);
-                dv -= de * (A.w * ddx + 2.f * B.x * ddy);
-                dcA = fmaf(de, ddx * ddx, dcA);
-                dcB = fmaf(de, ddx * ddy, dcB);
-                dcC = fmaf(de, ddy * ddy, dcC);
-                dlo += de;
+                const float ex = de * ddx, ey = de * ddy;
+                sde += de;
+                sx += ex;
+                sy += ey;
+                sxx = fmaf(ex, ddx, sxx);
+                sxy = fmaf(ex, ddy, sxy);
+                syy = fmaf(ey, ddy, syy);
             };
 #pragma unroll
             for (int pj = 0; pj < PH; ++pj)
 #pragma unroll
                 for (int pi = 0; pi < PW; ++pi) pixel(pj * PW + pi, pi, pj);
-            const bool any = mbits != 0u;
-            if (__any_sync(0xffffffffu, any)) {
-                const float v[9] = {du, dv, dcA, dcB, dcC, dlo, dr, dg, db};
-                const float2 tot = warp_sum9(v, lane);
-                float* G = grad_rec + 12 * (size_t)s_r[k];
-                if ((lane & 3) == 0 && tot.x != 0.f) atomicAdd(G + (lane >> 2), tot.x);
-                if (lane == 1 && tot.y != 0.f) atomicAdd(G + 8, tot.y);
-            }
+            // e = cA dx^2 + cB dx dy + cC dy^2 + log2 o with dx = x - u:
+            // de/du = -(2 cA dx + cB dy), de/dv = -(cB dx + 2 cC dy)
+            const float du = -fmaf(2.f * A.z, sx, A.w * sy);
+            const float dv = -fmaf(A.w, sx, 2.f * B.x * sy);
+            const float v[9] = {du, dv, sxx, sxy, syy, sde, dr, dg, db};
+            const float2 tot = warp_sum9(v, lane);
+            float* G = grad_rec + 12 * (size_t)s_r[k];
+            if ((lane & 3) == 0 && tot.x != 0.f) atomicAdd(G + (lane >> 2), tot.x);
+            if (lane == 1 && tot.y != 0.f) atomicAdd(G + 8, tot.y);
         }
     }
 }
