@@ -301,7 +301,8 @@ uint32_t select_clusters(const seele_ctx* c, const seele_camera& cam, int M) {
 }
 
 // Digit totals of the sorts' passes, 256 words per pass: the depth sort's
-// four, then up to four of the tile sort.
+// four, then up to four of the tile sort (or the 512 or 1024 of its one wide
+// pass).
 constexpr uint32_t kDepthSortTotals = 4 * 256;
 constexpr uint32_t kDigitTotalWords = 8 * 256;
 
@@ -778,7 +779,11 @@ seele_status size_frame(seele_ctx* c, FrameInfo& f) {
         SEELE_CUDA(c, ensure(c->ckpt, 16ull * ((cap >> kCkptShift) + 2) * (uint64_t)f.fp.tile_w * f.fp.tile_h));
         SEELE_CUDA(c, ensure(c->cfin, 16 * f.pix_total));
     }
-    f.cnt_words = radix_count_words((uint32_t)std::max<uint64_t>(R, cap));
+    // count matrices: the depth sort's 8-bit passes over R records, the tile
+    // or block sort's passes over cap instances (one wide pass at 257 to
+    // 1024 units with 16-bit keys)
+    const int wide = radix_last_bits(f.expand ? f.block_bits : f.tile_bits, f.short_keys ? 2 : 4);
+    f.cnt_words = std::max(radix_count_words((uint32_t)R), radix_count_words((uint32_t)cap, wide));
     SEELE_CUDA(c, ensure(c->sortcnt, 8ull * f.cnt_words));
     // digit totals of the sorts' passes (cleared every frame)
     SEELE_CUDA(c, ensure(c->digtot, 4 * kDigitTotalWords));

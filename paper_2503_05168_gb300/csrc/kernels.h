@@ -61,7 +61,13 @@ void launch_radix_downsweep_u32(const uint32_t* keys_in, const uint32_t* vals_in
                                 uint32_t* vals_out, const uint32_t* count_ptr, int shift, int nbits,
                                 const uint32_t* offsets, uint32_t stride, uint32_t* run_start, uint32_t* run_end,
                                 cudaStream_t s);
-uint32_t radix_count_words(uint32_t max_n);
+// Words of one count matrix for a pass over max_n elements with digits of
+// radix_bits bits.
+uint32_t radix_count_words(uint32_t max_n, int radix_bits = 8);
+// Digit width of the last pass of radix_sort_pairs for key_bits significant
+// bits of a key_bytes-byte key: 9 or 10 (one pass) for 16-bit keys of that
+// many bits, else 8.
+int radix_last_bits(int key_bits, int key_bytes);
 // Last-pass counts: out[o] = the instance count of sorted record o.  packed:
 // the values carry the count in their top bits (kPackedIdBits; saturated
 // counts are read from src) and the pass writes bare record ids; otherwise
@@ -72,14 +78,16 @@ struct SortGather {
     bool packed = false;
 };
 // Stable LSD sort of (keys[0], vals[0]) by their low `key_bits` bits in 8-bit
-// digits; returns the index of the buffer pair holding the result, or -1 on a
+// digits (one 9- or 10-bit digit for 16-bit keys of that many bits); returns the index of the buffer pair holding the result, or -1 on a
 // launch error.  With run_start / run_end (cleared to all-ones / zero, one
 // word per key value) the last pass also records [first, last + 1) of every
 // key value present -- the per-tile ranges.  With aux (two buffers, like vals)
 // a second 32-bit payload is permuted with the values.  With gather (and no
 // aux) the last pass also lays out the records' instance counts in sorted
 // order (SortGather).
-// digit_totals: 256 words per pass, cleared by the caller.
+// digit_totals: 256 words per pass (1 << radix_last_bits for a one-pass
+// wide sort), cleared by the caller; counts and offsets: radix_count_words
+// (max_n, radix_last_bits) words each.
 template <typename KeyT>
 int radix_sort_pairs(KeyT* keys[2], uint32_t* vals[2], const uint32_t* count_ptr, uint32_t max_n, int key_bits,
                      bool keys_after_last, uint32_t* counts, uint32_t* offsets, uint32_t* digit_totals,

@@ -14,6 +14,10 @@
 // frame: on the visible records keyed by fp32 depth bits (31 bits, 4 passes)
 // and on the tile instances keyed by global tile id (16-bit keys when the
 // frame has <= 65536 tiles); the last pass of each writes values only.
+// 16-bit keys of 9 or 10 significant bits (257 to 1024 tile blocks) take one
+// pass with 9- or 10-bit digits instead of an 8-bit pass and a 1- or 2-bit
+// one: the per-warp digit counters are 16-bit then, so the pass's shared
+// memory still fits a CTA's static 48 KB.
 // Stability is what makes the two sorts compose into the (tile, depth,
 // record id) order of Sec. 3.1 "Sorting".  The depth sort's last pass also
 // lays out each record's instance count in depth order (SortGather).
@@ -22,6 +26,7 @@
 // kernel), so grids are sized for the capacity and surplus tiles write
 // nothing but zero counts.
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -36,19 +41,21 @@ constexpr int kWarps = kSortThreads / 32;
 
 // Per-tile digit counts, digit-major.  Counting ignores order, so each thread
 // reads 16 consecutive keys with vector loads and adds them to its warp's
-// shared counters.
-template <typename KeyT>
+// shared counters.  RB: digit width in bits.
+template <typename KeyT, int RB>
 __global__ void __launch_bounds__(kSortThreads) upsweep_kernel(const KeyT* __restrict__ keys,
                                                                const uint32_t* __restrict__ count_ptr, int shift,
                                                                uint32_t* __restrict__ counts, uint32_t stride,
                                                                uint32_t* __restrict__ row_total) {
     static_assert(kSortItems * sizeof(KeyT) % 16 == 0, "vector loads");
-    __shared__ uint32_t s_w[kWarps][kRadix];
+    constexpr uint32_t R = 1u << RB;
+    static_assert(R % kSortThreads == 0, "whole digits per thread");
+    __shared__ uint32_t s_w[kWarps][R];
     pdl_enter();
     const uint32_t tile = blockIdx.x;
     const uint32_t n = *count_ptr;
     const int w = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < kWarps * kRadix; i += kSortThreads) (&s_w[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < kWarps * (int)R; i += kSortThreads) (&s_w[0][0])[i] = 0;
     __syncthreads();
     const uint32_t base = tile * kSortTile + threadIdx.x * kSortItems;
     if (base + kSortItems <= n) {
@@ -59,23 +66,27 @@ __global__ void __launch_bounds__(kSortThreads) upsweep_kernel(const KeyT* __res
         for (int q = 0; q < NV; ++q) v[q] = __ldg(p + q);
         const KeyT* kk = reinterpret_cast<const KeyT*>(v);
 #pragma unroll
-        for (int k = 0; k < kSortItems; ++k) atomicAdd(&s_w[w][((uint32_t)kk[k] >> shift) & 0xffu], 1u);
+        for (int k = 0; k < kSortItems; ++k) atomicAdd(&s_w[w][((uint32_t)kk[k] >> shift) & (R - 1u)], 1u);
     } else {
         for (int k = 0; k < kSortItems; ++k)
-            if (base + k < n) atomicAdd(&s_w[w][((uint32_t)__ldg(keys + base + k) >> shift) & 0xffu], 1u);
+            if (base + k < n) atomicAdd(&s_w[w][((uint32_t)__ldg(keys + base + k) >> shift) & (R - 1u)], 1u);
     }
     __syncthreads();
-    const uint32_t d = threadIdx.x;
-    uint32_t total = 0;
 #pragma unroll
-    for (int ww = 0; ww < kWarps; ++ww) total += s_w[ww][d];
-    counts[(size_t)d * stride + tile] = total;
-    if (row_total != nullptr && total != 0u) atomicAdd(row_total + d, total);
+    for (uint32_t q = 0; q < R / kSortThreads; ++q) {
+        const uint32_t d = threadIdx.x + q * kSortThreads;
+        uint32_t total = 0;
+#pragma unroll
+        for (int ww = 0; ww < kWarps; ++ww) total += s_w[ww][d];
+        counts[(size_t)d * stride + tile] = total;
+        if (row_total != nullptr && total != 0u) atomicAdd(row_total + d, total);
+    }
 }
 
 // AUX: a second 32-bit payload travels with each pair; it is staged through
 // the same shared buffer as the values after they have been written.
-template <typename KeyT, bool WRITE_KEYS, bool AUX>
+// RB: digit width in bits; thread t owns digits [t DPT, (t + 1) DPT).
+template <typename KeyT, bool WRITE_KEYS, bool AUX, int RB>
 __global__ void __launch_bounds__(kSortThreads) downsweep_kernel(const KeyT* __restrict__ keys_in,
                                                                  const uint32_t* __restrict__ vals_in,
                                                                  KeyT* __restrict__ keys_out,
@@ -87,20 +98,27 @@ __global__ void __launch_bounds__(kSortThreads) downsweep_kernel(const KeyT* __r
                                                                  const uint32_t* __restrict__ aux_in,
                                                                  uint32_t* __restrict__ aux_out,
                                                                  SortGather gather) {
+    constexpr uint32_t R = 1u << RB;
+    constexpr int DPT = (int)R / kSortThreads;
+    static_assert(DPT >= 1 && (int)R == DPT * kSortThreads, "whole digits per thread");
+    static_assert(RB == 8 || sizeof(KeyT) == 2, "wide digits only with 16-bit keys (shared memory)");
+    // counts inside a tile are <= 4096: 16-bit counters for the wide digits
+    using CntT = typename std::conditional<(RB > 8), uint16_t, uint32_t>::type;
     __shared__ KeyT s_keys[kSortTile];
     __shared__ uint32_t s_vals[kSortTile];
-    __shared__ uint32_t s_wcount[kWarps][kRadix + 1];  // per-warp digit counters, then exclusive prefixes
-    __shared__ uint32_t s_local_base[kRadix];          // digit start inside this tile
-    __shared__ uint32_t s_global_base[kRadix];         // digit start in the output for this tile
+    __shared__ CntT s_wcount[kWarps][R + 1];  // per-warp digit counters, then exclusive prefixes
+    __shared__ CntT s_local_base[R];          // digit start inside this tile
+    __shared__ uint32_t s_global_base[R];     // digit start in the output for this tile
     __shared__ uint32_t s_scan[kWarps];
 
     pdl_enter();
     const uint32_t tile = blockIdx.x;
     const uint32_t n = *count_ptr;
     if (tile * (uint32_t)kSortTile >= n) return;
-    const uint32_t d = threadIdx.x;  // kSortThreads == kRadix: thread d owns digit d
-    for (int i = threadIdx.x; i < kWarps * (kRadix + 1); i += kSortThreads) (&s_wcount[0][0])[i] = 0;
-    s_global_base[d] = __ldg(offsets + (size_t)d * stride + tile);
+    const uint32_t t0 = threadIdx.x * DPT;  // this thread's first digit
+    for (int i = threadIdx.x; i < kWarps * (int)(R + 1); i += kSortThreads) (&s_wcount[0][0])[i] = 0;
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) s_global_base[t0 + q] = __ldg(offsets + (size_t)(t0 + q) * stride + tile);
     __syncthreads();
 
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -123,7 +141,7 @@ __global__ void __launch_bounds__(kSortThreads) downsweep_kernel(const KeyT* __r
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
         const bool ok = key[k] != 0xffffffffu;
-        const uint32_t dg = ok ? (key[k] >> shift) & 0xffu : (uint32_t)kRadix;  // sentinel bucket
+        const uint32_t dg = ok ? (key[k] >> shift) & (R - 1u) : R;  // sentinel bucket
         const uint32_t okm = __ballot_sync(0xffffffffu, ok);
         uint32_t peers = ok ? okm : (valid_base & ~okm);
         for (int b = 0; b < nbits; ++b) {
@@ -132,19 +150,26 @@ __global__ void __launch_bounds__(kSortThreads) downsweep_kernel(const KeyT* __r
         }
         const uint32_t before = s_wcount[w][dg];
         __syncwarp();
-        if ((peers & lt_mask) == 0u) s_wcount[w][dg] = before + __popc(peers);
+        if ((peers & lt_mask) == 0u) s_wcount[w][dg] = (CntT)(before + __popc(peers));
         __syncwarp();
         rank[k] = before + __popc(peers & lt_mask);
     }
     __syncthreads();
 
     // per digit: per-warp exclusive offsets and the tile-local digit start
+    uint32_t tot[DPT];
     uint32_t total = 0;
 #pragma unroll
-    for (int ww = 0; ww < kWarps; ++ww) {
-        const uint32_t c = s_wcount[ww][d];
-        s_wcount[ww][d] = total;
-        total += c;
+    for (int q = 0; q < DPT; ++q) {
+        uint32_t acc = 0;
+#pragma unroll
+        for (int ww = 0; ww < kWarps; ++ww) {
+            const uint32_t c = s_wcount[ww][t0 + q];
+            s_wcount[ww][t0 + q] = (CntT)acc;
+            acc += c;
+        }
+        tot[q] = acc;
+        total += acc;
     }
     uint32_t incl = total;
 #pragma unroll
@@ -156,15 +181,20 @@ __global__ void __launch_bounds__(kSortThreads) downsweep_kernel(const KeyT* __r
     __syncthreads();
     uint32_t add = 0;
     for (int ww = 0; ww < w; ++ww) add += s_scan[ww];
-    s_local_base[d] = add + incl - total;
+    uint32_t lb = add + incl - total;
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+        s_local_base[t0 + q] = (CntT)lb;
+        lb += tot[q];
+    }
     __syncthreads();
 
     // stage the tile in shared memory sorted by digit, then write out runs
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
         if (key[k] != 0xffffffffu) {
-            const uint32_t dg = (key[k] >> shift) & 0xffu;
-            const uint32_t p = s_local_base[dg] + s_wcount[w][dg] + rank[k];
+            const uint32_t dg = (key[k] >> shift) & (R - 1u);
+            const uint32_t p = (uint32_t)s_local_base[dg] + s_wcount[w][dg] + rank[k];
             s_keys[p] = (KeyT)key[k];
             s_vals[p] = val[k];
         }
@@ -176,8 +206,8 @@ __global__ void __launch_bounds__(kSortThreads) downsweep_kernel(const KeyT* __r
     const uint32_t vmask = packed ? (1u << kPackedIdBits) - 1u : 0xffffffffu;
     for (uint32_t i = threadIdx.x; i < tile_n; i += kSortThreads) {
         const uint32_t k = s_keys[i];
-        const uint32_t dg = (k >> shift) & 0xffu;
-        const uint32_t o = s_global_base[dg] + (i - s_local_base[dg]);
+        const uint32_t dg = (k >> shift) & (R - 1u);
+        const uint32_t o = s_global_base[dg] + (i - (uint32_t)s_local_base[dg]);
         if (o < n) {
             if (WRITE_KEYS) keys_out[o] = (KeyT)k;
             const uint32_t v = s_vals[i];
@@ -209,14 +239,14 @@ __global__ void __launch_bounds__(kSortThreads) downsweep_kernel(const KeyT* __r
 #pragma unroll
         for (int k = 0; k < kSortItems; ++k) {
             if (key[k] != 0xffffffffu) {
-                const uint32_t dg = (key[k] >> shift) & 0xffu;
-                s_vals[s_local_base[dg] + s_wcount[w][dg] + rank[k]] = aux[k];
+                const uint32_t dg = (key[k] >> shift) & (R - 1u);
+                s_vals[(uint32_t)s_local_base[dg] + s_wcount[w][dg] + rank[k]] = aux[k];
             }
         }
         __syncthreads();
         for (uint32_t i = threadIdx.x; i < tile_n; i += kSortThreads) {
-            const uint32_t dg = ((uint32_t)s_keys[i] >> shift) & 0xffu;
-            const uint32_t o = s_global_base[dg] + (i - s_local_base[dg]);
+            const uint32_t dg = ((uint32_t)s_keys[i] >> shift) & (R - 1u);
+            const uint32_t o = s_global_base[dg] + (i - (uint32_t)s_local_base[dg]);
             if (o < n) aux_out[o] = s_vals[i];
         }
     }
@@ -227,7 +257,7 @@ uint32_t sort_tile_items() { return kSortTile; }
 // Single passes of the sort, for callers that manage their own buffers.
 void launch_radix_upsweep_u32(const uint32_t* keys, const uint32_t* count_ptr, int shift, uint32_t* counts,
                               uint32_t stride, cudaStream_t s) {
-    upsweep_kernel<uint32_t><<<stride, kSortThreads, 0, s>>>(keys, count_ptr, shift, counts, stride, nullptr);
+    upsweep_kernel<uint32_t, 8><<<stride, kSortThreads, 0, s>>>(keys, count_ptr, shift, counts, stride, nullptr);
 }
 
 void launch_radix_downsweep_u32(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
@@ -235,26 +265,51 @@ void launch_radix_downsweep_u32(const uint32_t* keys_in, const uint32_t* vals_in
                                 const uint32_t* offsets, uint32_t stride, uint32_t* run_start, uint32_t* run_end,
                                 cudaStream_t s) {
     if (keys_out)
-        downsweep_kernel<uint32_t, true, false><<<stride, kSortThreads, 0, s>>>(
+        downsweep_kernel<uint32_t, true, false, 8><<<stride, kSortThreads, 0, s>>>(
             keys_in, vals_in, keys_out, vals_out, count_ptr, shift, nbits, offsets, stride, run_start, run_end,
             nullptr, nullptr, SortGather{});
     else
-        downsweep_kernel<uint32_t, false, false><<<stride, kSortThreads, 0, s>>>(
+        downsweep_kernel<uint32_t, false, false, 8><<<stride, kSortThreads, 0, s>>>(
             keys_in, vals_in, keys_out, vals_out, count_ptr, shift, nbits, offsets, stride, run_start, run_end,
             nullptr, nullptr, SortGather{});
 }
 
-uint32_t radix_count_words(uint32_t max_n) {
-    return kRadix * std::max<uint32_t>((max_n + kSortTile - 1) / kSortTile, 1u);
+int radix_last_bits(int key_bits, int key_bytes) {
+    return (key_bytes == 2 && key_bits > 8 && key_bits <= 10) ? key_bits : 8;
 }
 
-template <typename KeyT, bool WK, bool AUX>
+uint32_t radix_count_words(uint32_t max_n, int radix_bits) {
+    return (1u << radix_bits) * std::max<uint32_t>((max_n + kSortTile - 1) / kSortTile, 1u);
+}
+
+template <typename KeyT, bool WK, bool AUX, int RB>
 static void launch_downsweep(KeyT* keys[2], uint32_t* vals[2], uint32_t* const* aux, int a, int b,
                              const uint32_t* count_ptr, int shift, int nbits, const uint32_t* offsets, uint32_t stride,
                              uint32_t* rs, uint32_t* re, const SortGather& gather, cudaStream_t s) {
-    launch_pdl(downsweep_kernel<KeyT, WK, AUX>, dim3(stride), dim3(kSortThreads), 0, s, keys[a], vals[a], keys[b],
+    launch_pdl(downsweep_kernel<KeyT, WK, AUX, RB>, dim3(stride), dim3(kSortThreads), 0, s, keys[a], vals[a], keys[b],
                vals[b], count_ptr, shift, nbits, offsets, stride, rs, re, AUX ? aux[a] : nullptr,
                AUX ? aux[b] : nullptr, gather);
+}
+
+template <typename KeyT, int RB>
+static void launch_pass(KeyT* keys[2], uint32_t* vals[2], uint32_t* const* aux, int a, int b, bool wk,
+                        const uint32_t* count_ptr, int shift, int nbits, uint32_t* counts, uint32_t* offsets,
+                        uint32_t* totals, uint32_t stride, uint32_t* rs, uint32_t* re, const SortGather& g,
+                        cudaStream_t s) {
+    launch_pdl(upsweep_kernel<KeyT, RB>, dim3(stride), dim3(kSortThreads), 0, s, keys[a], count_ptr, shift, counts,
+               stride, totals);
+    launch_digit_scan(counts, stride, totals, offsets, s, 1u << RB);
+    if (aux) {
+        if (wk) launch_downsweep<KeyT, true, true, RB>(keys, vals, aux, a, b, count_ptr, shift, nbits, offsets, stride,
+                                                        rs, re, g, s);
+        else launch_downsweep<KeyT, false, true, RB>(keys, vals, aux, a, b, count_ptr, shift, nbits, offsets, stride,
+                                                      rs, re, g, s);
+    } else {
+        if (wk) launch_downsweep<KeyT, true, false, RB>(keys, vals, aux, a, b, count_ptr, shift, nbits, offsets,
+                                                         stride, rs, re, g, s);
+        else launch_downsweep<KeyT, false, false, RB>(keys, vals, aux, a, b, count_ptr, shift, nbits, offsets,
+                                                       stride, rs, re, g, s);
+    }
 }
 
 template <typename KeyT>
@@ -263,29 +318,31 @@ int radix_sort_pairs(KeyT* keys[2], uint32_t* vals[2], const uint32_t* count_ptr
                      int& launches, cudaStream_t s, uint32_t* run_start, uint32_t* run_end, uint32_t* const* aux,
                      const SortGather* gather) {
     const uint32_t stride = std::max<uint32_t>((max_n + kSortTile - 1) / kSortTile, 1u);
-    const int passes = std::max(1, (key_bits + 7) / 8);
+    const int wide = radix_last_bits(key_bits, (int)sizeof(KeyT));  // digit width of the last pass
+    const int passes = wide > 8 ? 1 : std::max(1, (key_bits + 7) / 8);
     for (int p = 0; p < passes; ++p) {
         const int a = p & 1, b = a ^ 1;
-        const int nbits = std::max(1, std::min(8, key_bits - 8 * p));
+        const int nbits = wide > 8 ? wide : std::max(1, std::min(8, key_bits - 8 * p));
         const bool last = p == passes - 1;
         uint32_t* rs = last ? run_start : nullptr;
         uint32_t* re = last ? run_end : nullptr;
         const SortGather g = (last && gather) ? *gather : SortGather{};
         uint32_t* totals = digit_totals + (size_t)p * kRadix;
-        launch_pdl(upsweep_kernel<KeyT>, dim3(stride), dim3(kSortThreads), 0, s, keys[a], count_ptr, 8 * p, counts,
-                   stride, totals);
-        launch_digit_scan(counts, stride, totals, offsets, s);
         const bool wk = !last || keys_after_last;
-        if (aux) {
-            if (wk) launch_downsweep<KeyT, true, true>(keys, vals, aux, a, b, count_ptr, 8 * p, nbits, offsets, stride,
-                                                        rs, re, g, s);
-            else launch_downsweep<KeyT, false, true>(keys, vals, aux, a, b, count_ptr, 8 * p, nbits, offsets, stride,
-                                                      rs, re, g, s);
+        if constexpr (sizeof(KeyT) == 2) {
+            if (wide == 9) {
+                launch_pass<KeyT, 9>(keys, vals, aux, a, b, wk, count_ptr, 0, nbits, counts, offsets, totals, stride,
+                                     rs, re, g, s);
+            } else if (wide == 10) {
+                launch_pass<KeyT, 10>(keys, vals, aux, a, b, wk, count_ptr, 0, nbits, counts, offsets, totals, stride,
+                                      rs, re, g, s);
+            } else {
+                launch_pass<KeyT, 8>(keys, vals, aux, a, b, wk, count_ptr, 8 * p, nbits, counts, offsets, totals,
+                                     stride, rs, re, g, s);
+            }
         } else {
-            if (wk) launch_downsweep<KeyT, true, false>(keys, vals, aux, a, b, count_ptr, 8 * p, nbits, offsets,
-                                                         stride, rs, re, g, s);
-            else launch_downsweep<KeyT, false, false>(keys, vals, aux, a, b, count_ptr, 8 * p, nbits, offsets,
-                                                       stride, rs, re, g, s);
+            launch_pass<KeyT, 8>(keys, vals, aux, a, b, wk, count_ptr, 8 * p, nbits, counts, offsets, totals, stride,
+                                 rs, re, g, s);
         }
         if (cudaPeekAtLastError() != cudaSuccess) return -1;
         launches += 3;

@@ -73,8 +73,8 @@ def _f32(s):
             for k, v in s.items()}
 
 
-def _is_clear(s, cam, n):
-    proj = oracle.preprocess(oracle.Scene64.from_scene(s), cam, oracle.Options())
+def _is_clear(s, cam, n, opts=None):
+    proj = oracle.preprocess(oracle.Scene64.from_scene(s), cam, opts or oracle.Options())
     vis = proj["visible"] == 1
     if vis.sum() < n // 2:
         return False
@@ -86,10 +86,11 @@ def _is_clear(s, cam, n):
     return np.min(np.diff(d)) > 4
 
 
-def _clear_tiny_scene(seed, n=48, W=64, H=48, f=50.0, n_big=0):
+def _clear_tiny_scene(seed, n=48, W=64, H=48, f=50.0, n_big=0, opts=None):
     """Random tiny scene and two cameras with every rect, cull and depth-order
-    decision far from a rounding flip (re-drawn until so).  The first n_big
-    Gaussians are wide ones near the middle of the view."""
+    decision far from a rounding flip (re-drawn until so) for the tiles of
+    opts.  The first n_big Gaussians are wide ones near the middle of the
+    view."""
     rs = np.random.default_rng(seed)
     cam = camera(f=f, width=W, height=H)
     cam2 = dict(cam, world_to_cam=np.concatenate([np.eye(3), [[0.3], [0.1], [0.5]]], 1))
@@ -100,7 +101,7 @@ def _clear_tiny_scene(seed, n=48, W=64, H=48, f=50.0, n_big=0):
         log_scales[:n_big] = rs.normal(math.log(0.5), 0.1, (n_big, 3))
         s = _f32(scene(means, log_scales=log_scales, quats=rs.standard_normal((n, 4)),
                        opacity=rs.uniform(0.05, 0.95, n), dc=rs.uniform(-1, 1, (n, 3))))
-        if _is_clear(s, cam, n) and _is_clear(s, cam2, n):
+        if _is_clear(s, cam, n, opts) and _is_clear(s, cam2, n, opts):
             return s, [cam, cam2]
     raise RuntimeError("no clear scene found")
 
@@ -113,28 +114,43 @@ def test_tile_lists_bit_exact(Renderer, seed, size, n_big, tile_test):
     """Tile lists, their order and ranges equal the oracle's, bit for bit.  The
     480x320 frames hold Gaussians spanning more than 255 tiles, whose counts
     do not fit the count byte the depth sort carries with each record id."""
+    _check_tile_lists(Renderer, seed, size, n_big, tile_test)
+
+
+@pytest.mark.parametrize("seed,size,n_blocks", [(5, (640, 720, 600.0), 460), (6, (1280, 720, 900.0), 920)])
+def test_tile_lists_bit_exact_one_wide_block_pass(Renderer, seed, size, n_blocks):
+    """8x8 tiles on frames of 257 to 1024 tile blocks: the block sort takes one
+    pass with 9-bit (460 blocks) or 10-bit (920 blocks) digits; the tile lists
+    expanded from it still equal the oracle's."""
+    W, H, _ = size
+    tx, ty = -(-W // 8), -(-H // 8)
+    assert 2 * (-(-tx // 8)) * (-(-ty // 4)) == n_blocks
+    _check_tile_lists(Renderer, seed, size, 3, "ellipse", tile=(8, 8))
+
+
+def _check_tile_lists(Renderer, seed, size, n_big, tile_test, tile=(16, 16)):
     W, H, f = size
-    s, cams = _clear_tiny_scene(seed, W=W, H=H, f=f, n_big=n_big)
+    oo = oracle.Options(tile_test=tile_test, tile_w=tile[0], tile_h=tile[1])
+    s, cams = _clear_tiny_scene(seed, W=W, H=H, f=f, n_big=n_big, opts=oo)
     r = Renderer()
     r.load_scene(s)
     r.set_cameras(cams)
-    parity.gpu_render(r, tile_test=tile_test, binning="tiles")
+    parity.gpu_render(r, tile_test=tile_test, binning="tiles", tile=tile)
     d = parity.debug_numpy(r)
     n = s["means"].shape[0]
     exp_tile, exp_rec, exp_rng = [], [], []
     tile_off, k_off = 0, 0
-    oo = oracle.Options(tile_test=tile_test)
     for ci, c in enumerate(cams):
         proj = oracle.preprocess(oracle.Scene64.from_scene(s), c, oo)
-        tile, gid, ranges = oracle.instances(proj, c, oo)
-        exp_tile.append(tile + tile_off)
+        tile_ids, gid, ranges = oracle.instances(proj, c, oo)
+        exp_tile.append(tile_ids + tile_off)
         exp_rec.append(gid + ci * n)
         rr = ranges.copy()
         nonempty = rr[:, 1] > rr[:, 0]
         rr[nonempty] += k_off
         exp_rng.append(rr)
         tile_off += ranges.shape[0]
-        k_off += tile.size
+        k_off += tile_ids.size
     if n_big:
         assert d["tiles_touched"].max() > 255
     np.testing.assert_array_equal(d["inst_tile"], np.concatenate(exp_tile))
@@ -148,29 +164,33 @@ def test_tile_lists_bit_exact(Renderer, seed, size, n_big, tile_test):
     r.close()
 
 
-@pytest.mark.parametrize("seed,size,n_big", [(2, (200, 120, 160.0), 0), (3, (200, 120, 160.0), 0),
-                                             (4, (480, 320, 400.0), 3)])
-def test_block_lists_filtered_per_tile_are_the_tile_lists(Renderer, seed, size, n_big):
+@pytest.mark.parametrize("seed,size,n_big,tile", [(2, (200, 120, 160.0), 0, (16, 16)),
+                                                  (3, (200, 120, 160.0), 0, (16, 16)),
+                                                  (4, (480, 320, 400.0), 3, (16, 16)),
+                                                  (6, (1280, 720, 900.0), 3, (8, 8))])
+def test_block_lists_filtered_per_tile_are_the_tile_lists(Renderer, seed, size, n_big, tile):
     """Block binning: walking a tile's block list and keeping the entries whose
     mask has the tile's bit gives exactly the oracle's tile list, in order
     (the 200x120 frames span several 8x4-tile blocks each way; the 480x320
-    ones hold records up to 20 tile rows tall across many blocks)."""
+    ones hold records up to 20 tile rows tall across many blocks; the 1280x720
+    pair at 8x8 tiles has 920 blocks, sorted in one pass of 10-bit digits)."""
     W, H, f = size
-    s, cams = _clear_tiny_scene(seed, W=W, H=H, f=f, n_big=n_big)
+    oo = oracle.Options(tile_w=tile[0], tile_h=tile[1])
+    s, cams = _clear_tiny_scene(seed, W=W, H=H, f=f, n_big=n_big, opts=oo)
     r = Renderer()
     r.load_scene(s)
     r.set_cameras(cams)
-    parity.gpu_render(r, binning="blocks")
+    parity.gpu_render(r, binning="blocks", tile=tile)
     d = parity.debug_numpy(r)
     n = s["means"].shape[0]
     rng = d["tile_ranges"].astype(np.int64)
     mask = d["inst_mask"].view(np.uint32)
     blk_off = 0
     for ci, c in enumerate(cams):
-        tx_n, ty_n = oracle.tile_grid(c, oracle.Options())
+        tx_n, ty_n = oracle.tile_grid(c, oo)
         bx_n, by_n = -(-tx_n // 8), -(-ty_n // 4)
-        proj = oracle.preprocess(oracle.Scene64.from_scene(s), c, oracle.Options())
-        _, gid, ranges = oracle.instances(proj, c, oracle.Options())
+        proj = oracle.preprocess(oracle.Scene64.from_scene(s), c, oo)
+        _, gid, ranges = oracle.instances(proj, c, oo)
         for t in range(tx_n * ty_n):
             tx, ty = t % tx_n, t // tx_n
             b = blk_off + (ty // 4) * bx_n + tx // 8
