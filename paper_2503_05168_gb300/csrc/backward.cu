@@ -18,6 +18,13 @@
 //   moments of the pixel offsets (sum de dx, de dy, de dx^2, ...) and turned
 //   into du, dv once per entry.  The pixels of a thread run branch-free under
 //   a per-pixel predicate.
+//   8x8 tiles (one warp per tile, two pixels per lane) sum in two phases:
+//   the lanes write each blended entry's per-pixel terms (de, colour weight)
+//   to one of eight shared-memory slots; once the slots are full, lane
+//   (e, q) adds up entry e over the pixels of columns q and q + 4, with the
+//   pixel offsets as constants, and four lanes combine an entry's totals --
+//   instead of nine per-pixel accumulations and a nine-value warp sum per
+//   entry.
 // preprocess_bwd_kernel: one thread per Gaussian, summing over cameras, runs
 //   the chain rule back through the raster record, the conic, the EWA
 //   projection, the covariance, the quaternion and the SH colour.
@@ -72,6 +79,12 @@ __device__ __forceinline__ float2 warp_sum9(const float (&v)[9], int lane) {
     return make_float2(a[0], w);
 }
 
+// Slots of the two-phase sum (8x8 tiles): 8 entries of 64 pixel pairs
+// (de, weight); the stride of 132 floats keeps the phase-B loads of a
+// half-warp in distinct banks.
+constexpr int kSlots = 8;
+constexpr int kSlotStride = 132;
+
 template <int TW, int TH, int PW, int PH, int GW, int GH, bool CR>
 __global__ void __launch_bounds__((TW / PW) * (TH / PH))
     raster_bwd_kernel(const uint32_t* __restrict__ starts, const uint32_t* __restrict__ ends,
@@ -88,9 +101,15 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
     // thread blocks (the forward pass's rule); GWL x GHL is its part here
     constexpr bool WHOLE = GW % PW == 0 && GH % PH == 0;
     constexpr int GWL = WHOLE ? PW : GW, GHL = WHOLE ? PH : GH;
+    // two-phase sum: one warp per 8x8 tile, lane l holds pixels 2l, 2l + 1
+    constexpr bool SLOTS = TW == 8 && TH == 8 && PW == 2 && PH == 1;
+    static_assert(!SLOTS || NT == 32, "one warp per tile");
     __shared__ float4 s0[NT], s1[NT], s2[NT];
     __shared__ uint32_t s_r[NT];
     __shared__ uint32_t s_max;
+    __shared__ __align__(16) float s_x[SLOTS ? kSlots * kSlotStride : 4];
+    __shared__ float4 s_g[SLOTS ? TW * TH : 1];  // dL/dC of the tile's pixels
+    __shared__ int s_slot[kSlots];
 
     // CTA -> (tile, chunk): the first n_tiles CTAs take chunk 0 of every
     // tile, the others the later chunks of long lists (see kCkptShift)
@@ -136,6 +155,7 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
             g2[p] = __ldg(gimg + 2 * plane + o);
             my_max = max(my_max, last[p]);
         }
+        if constexpr (SLOTS) s_g[NP * t + p] = make_float4(g0[p], g1[p], g2[p], 0.f);
     }
     if (t == 0) s_max = 0;
     __syncthreads();
@@ -162,9 +182,71 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
         }
     }
     const float fx0 = (float)bx + 0.5f, fy0 = (float)by + 0.5f;
+    const float Xc = (float)(tx * TW) + 0.5f * TW, Yc = (float)(ty * TH) + 0.5f * TH;  // the tile's centre
+    // Phase B of the two-phase sum over the ns filled slots.  Lane (e, q)
+    // takes pixels q + 4 i (column q + 4 (i & 1), row i >> 1): moments of de
+    // about column q and its colour sums, moved to the tile's centre,
+    // summed over the entry's four lanes, then about the Gaussian's centre.
+    auto flush = [&](int ns) {
+        constexpr unsigned kAll = 0xffffffffu;
+        __syncwarp();
+        const int e = lane & 7, q = lane >> 3;
+        float N0 = 0.f, Nx = 0.f, Ny = 0.f, Nxx = 0.f, Nxy = 0.f, Nyy = 0.f, cr = 0.f, cg = 0.f, cb = 0.f;
+        if (e < ns) {
+            const float* xr = s_x + e * kSlotStride + 2 * q;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const float2 xv = *reinterpret_cast<const float2*>(xr + 8 * i);
+                const float4 g = s_g[q + 4 * i];
+                const float oy = (float)(i >> 1) - 3.5f;  // row offset from the centre
+                N0 += xv.x;
+                Ny = fmaf(xv.x, oy, Ny);
+                Nyy = fmaf(xv.x, oy * oy, Nyy);
+                if (i & 1) {  // column q + 4: 4 right of column q
+                    const float t4 = 4.f * xv.x;
+                    Nx += t4;
+                    Nxx = fmaf(t4, 4.f, Nxx);
+                    Nxy = fmaf(t4, oy, Nxy);
+                }
+                cr = fmaf(xv.y, g.x, cr);
+                cg = fmaf(xv.y, g.y, cg);
+                cb = fmaf(xv.y, g.z, cb);
+            }
+        }
+        const float cq = (float)q - 3.5f;  // column q's offset from the centre
+        float M[9] = {N0, fmaf(cq, N0, Nx), Ny, fmaf(cq, fmaf(2.f, Nx, cq * N0), Nxx), fmaf(cq, Ny, Nxy), Nyy,
+                      cr, cg, cb};
+#pragma unroll
+        for (int v = 0; v < 9; ++v) {
+            M[v] += __shfl_xor_sync(kAll, M[v], 8);
+            M[v] += __shfl_xor_sync(kAll, M[v], 16);
+        }
+        if (e < ns) {
+            const int k = s_slot[e];
+            const float4 A = s0[k];
+            const float cC = s1[k].x;
+            const float U = Xc - A.x, V = Yc - A.y;  // pixel offset dx = ox + U, dy = oy + V
+            const float sx = fmaf(U, M[0], M[1]), sy = fmaf(V, M[0], M[2]);
+            const float sxx = fmaf(U, fmaf(U, M[0], 2.f * M[1]), M[3]);
+            const float sxy = fmaf(U, fmaf(V, M[0], M[2]), fmaf(V, M[1], M[4]));
+            const float syy = fmaf(V, fmaf(V, M[0], 2.f * M[2]), M[5]);
+            // de/du = -(2 cA dx + cB dy), de/dv = -(cB dx + 2 cC dy); the
+            // slots hold de / ln 2
+            const float du = -fmaf(2.f * A.z, sx, A.w * sy) * kLn2;
+            const float dv = -fmaf(A.w, sx, 2.f * cC * sy) * kLn2;
+            const float a0 = q == 0 ? du : q == 1 ? dv : q == 2 ? sxx * kLn2 : sxy * kLn2;
+            const float a1 = q == 0 ? syy * kLn2 : q == 1 ? M[0] * kLn2 : q == 2 ? M[6] : M[7];
+            float* G = grad_rec + 12 * (size_t)s_r[k];
+            if (a0 != 0.f) atomicAdd(G + q, a0);
+            if (a1 != 0.f) atomicAdd(G + 4 + q, a1);
+            if (q == 0 && M[8] != 0.f) atomicAdd(G + 8, M[8]);
+        }
+        __syncwarp();
+    };
     const float lx0 = (float)(bx / GW * GW) + 0.5f, ly0 = (float)(by / GH * GH) + 0.5f;  // the group's leader
     const float amax = fp.alpha_max;
 
+    int n_slot = 0;  // filled slots (warp-uniform)
     for (int b1 = (int)whi; b1 > (int)wlo; b1 -= NT) {
         const int b0 = max((int)wlo, b1 - NT);
         __syncthreads();
@@ -226,6 +308,32 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
                         }
                 }
             if (!__any_sync(0xffffffffu, mbits != 0u)) continue;
+            if constexpr (SLOTS) {
+                // phase A: the pixels' de / ln 2 and colour weights into a slot
+                float de[NP], wg[NP];
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    const bool m = (mbits >> p) & 1u;
+                    float al = ex2_approx_b(ev[p]);
+                    if (clampable) al = fminf(amax, al);
+                    const float inv = rcp_approx_b(1.f - al);
+                    const float Tb = T[p] * inv;
+                    wg[p] = m ? Tb * al : 0.f;
+                    const float gc = fmaf(g2[p], Cc.z, fmaf(g1[p], Cc.y, g0[p] * Cc.x));
+                    const float dal = fmaf(Tb, gc, -gS[p] * inv);
+                    gS[p] = fmaf(wg[p], gc, gS[p]);
+                    T[p] = m ? Tb : T[p];
+                    de[p] = (m && (!clampable || al < amax)) ? dal * al : 0.f;
+                }
+                *reinterpret_cast<float4*>(s_x + n_slot * kSlotStride + 4 * lane) =
+                    make_float4(de[0], wg[0], de[1], wg[1]);
+                if (lane == 0) s_slot[n_slot] = k;
+                if (++n_slot == kSlots) {
+                    flush(n_slot);
+                    n_slot = 0;
+                }
+                continue;
+            }
             // One pixel of the entry, branch-free: for a pixel the entry was
             // not blended into every update below adds zero or keeps the value.
             auto pixel = [&](int p, int pi, int pj) {
@@ -268,6 +376,11 @@ __global__ void __launch_bounds__((TW / PW) * (TH / PH))
             float* G = grad_rec + 12 * (size_t)s_r[k];
             if ((lane & 3) == 0 && tot.x != 0.f) atomicAdd(G + (lane >> 2), tot.x);
             if (lane == 1 && tot.y != 0.f) atomicAdd(G + 8, tot.y);
+        }
+        if constexpr (SLOTS) {
+            // the staged records are replaced next: sum the filled slots now
+            if (n_slot > 0) flush(n_slot);
+            n_slot = 0;
         }
     }
 }
