@@ -99,6 +99,8 @@ struct seele_ctx {
         ckpt, cfin, bmap, branges, tcnt, toff, emap, ecnt;
     // the last render wrote transmittance checkpoints for ckpt_slots slots
     bool ckpt_valid = false;
+    // the last render left its tiles' longest-list-first order in border
+    bool border_tiles = false;
     uint64_t ckpt_slots = 0;
     DeviceStatus* h_status = nullptr;  // pinned mirror of the device status
     cudaEvent_t ev[SEELE_NUM_STAGES + 1] = {};
@@ -1491,6 +1493,7 @@ seele_status seele_render(seele_ctx* c, const seele_options* opt, float* out_rgb
         // the frame (enqueued or replayed) wrote checkpoints for the backward pass
         c->ckpt_valid = !f.blocks && !count && c->skew_frac <= 0.0 && c->topk_k <= 0;
         c->ckpt_slots = (f.cap >> kCkptShift) + 2;
+        c->border_tiles = !f.blocks && !f.queue;
         if (!f.rgb_dev)
             SEELE_CUDA(c, cudaMemcpyAsync(out_rgb, c->rgb_tmp.p, 12 * f.pix_total, cudaMemcpyDeviceToHost, c->stream));
         if (out_T && !f.T_dev)
@@ -1815,11 +1818,16 @@ seele_status seele_render_backward(seele_ctx* c, const float* dL_drgb, const see
     a.T_final = ptr<float>(c->T);
     a.n_contrib = ptr<uint32_t>(c->nc);
     a.grad_rec = ptr<float>(c->grad_rec);
-    // tiles with the longest lists first, as in the forward pass
-    SEELE_CUDA(c, ensure(c->torder, 4ull * c->n_tiles_total));
-    launch_block_order(a.starts, a.ends, c->n_tiles_total, ptr<uint32_t>(c->torder), s);
-    SEELE_LAUNCHED(c);
-    a.tile_order = ptr<const uint32_t>(c->torder);
+    // tiles with the longest lists first, as in the forward pass (whose
+    // order of these very ranges is reused when it made one)
+    if (c->border_tiles) {
+        a.tile_order = ptr<const uint32_t>(c->border);
+    } else {
+        SEELE_CUDA(c, ensure(c->torder, 4ull * c->n_tiles_total));
+        launch_block_order(a.starts, a.ends, c->n_tiles_total, ptr<uint32_t>(c->torder), s);
+        SEELE_LAUNCHED(c);
+        a.tile_order = ptr<const uint32_t>(c->torder);
+    }
     // long lists are walked in kCkptL-entry chunks from the forward pass's
     // checkpoints, one CTA each
     a.ckpt = nullptr;

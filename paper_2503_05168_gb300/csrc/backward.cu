@@ -441,10 +441,29 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(SceneDev sc, const 
                                                              float* __restrict__ d_sh,
                                                              const uint32_t* __restrict__ order) {
     constexpr int NC = (DEG + 1) * (DEG + 1);
-    constexpr int NF = 3 * NC, RS = NF | 1;  // SH gradient row, padded to an odd stride
-    __shared__ float s_sh[ONE ? 128 * RS : 1];
+    constexpr int NF = 3 * NC;
+    // One camera: each thread's SH gradient row leaves through shared memory
+    // (whole rows per CTA).  With 16-byte rows, a borrowed scene's SH rows
+    // also come in through the same slot, copied asynchronously when the
+    // thread starts, so that the loads overlap the projection's recompute;
+    // the row stride is then a multiple of 16 bytes and odd in 16-byte units
+    // (float4 accesses in distinct banks), else odd in words.
+    constexpr bool STAGE = ONE && NF % 4 == 0;
+    constexpr int RS = STAGE ? ((NF / 4) % 2 == 0 ? NF + 4 : NF) : (NF | 1);
+    __shared__ __align__(16) float s_sh[ONE ? 128 * RS : 4];
     const int t = threadIdx.x;
     const int g = blockIdx.x * blockDim.x + t;
+    const bool aos = sc.means != nullptr;  // a BORROW scene read in place
+    const bool staged = STAGE && aos;
+    if (staged && g < fp.n) {
+        const float4* src = reinterpret_cast<const float4*>(sc.shc + (size_t)g * NF);
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(s_sh + t * RS);
+#pragma unroll
+        for (int jp = 0; jp < NF / 4; ++jp)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 16u * jp), "l"(src + jp) : "memory");
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    const float4* my_sh = reinterpret_cast<const float4*>(s_sh + t * RS);
     bool wrote = false;
     if (g < fp.n) {
     float gm[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, glogit = 0.f;
@@ -453,7 +472,6 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(SceneDev sc, const 
 #pragma unroll
         for (int i = 0; i < NF; ++i) gsh[i] = 0.f;
     }
-    const bool aos = sc.means != nullptr;  // a BORROW scene read in place
     const float4 pl = aos ? scene_pos_logit<true>(sc, g) : scene_pos_logit<false>(sc, g);
     const float4 q4 = aos ? scene_quat<true>(sc, g) : scene_quat<false>(sc, g);
     const float4 ls = aos ? scene_log_scale<true>(sc, g) : scene_log_scale<false>(sc, g);
@@ -587,11 +605,15 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(SceneDev sc, const 
         // first the raw colour, then w_k = sum_c gc_c sh_kc, so that the
         // direction gradient is sum_k w_k grad Y_k
         constexpr int NPL = (NF + 3) / 4;
+        if (staged) asm volatile("cp.async.wait_all;" ::: "memory");  // this thread's own row
+        auto sh4 = [&](int jp) {
+            if (staged) return my_sh[jp];
+            return aos ? scene_sh4<true, NC>(sc, fp.n, g, jp) : scene_sh4<false, NC>(sc, fp.n, g, jp);
+        };
         float raw[3] = {0.5f, 0.5f, 0.5f};
 #pragma unroll
         for (int jp = 0; jp < NPL; ++jp) {
-            const float4 vv = aos ? scene_sh4<true, NC>(sc, fp.n, g, jp)
-                                  : scene_sh4<false, NC>(sc, fp.n, g, jp);
+            const float4 vv = sh4(jp);
             const float e4[4] = {vv.x, vv.y, vv.z, vv.w};
 #pragma unroll
             for (int i = 0; i < 4; ++i)
@@ -604,14 +626,21 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(SceneDev sc, const 
         for (int k = 0; k < NC; ++k) w[k] = 0.f;
 #pragma unroll
         for (int jp = 0; jp < NPL; ++jp) {
-            const float4 vv = aos ? scene_sh4<true, NC>(sc, fp.n, g, jp)
-                                  : scene_sh4<false, NC>(sc, fp.n, g, jp);
+            const float4 vv = sh4(jp);
             const float e4[4] = {vv.x, vv.y, vv.z, vv.w};
 #pragma unroll
             for (int i = 0; i < 4; ++i)
                 if (4 * jp + i < NF) w[(4 * jp + i) / 3] = fmaf(e4[i], gc[(4 * jp + i) % 3], w[(4 * jp + i) / 3]);
         }
-        if constexpr (ONE) {
+        if constexpr (STAGE) {
+            // the input row has been read: the gradient row replaces it
+#pragma unroll
+            for (int jp = 0; jp < NF / 4; ++jp)
+                reinterpret_cast<float4*>(s_sh + t * RS)[jp] =
+                    make_float4(Yb[(4 * jp) / 3] * gc[(4 * jp) % 3], Yb[(4 * jp + 1) / 3] * gc[(4 * jp + 1) % 3],
+                                Yb[(4 * jp + 2) / 3] * gc[(4 * jp + 2) % 3], Yb[(4 * jp + 3) / 3] * gc[(4 * jp + 3) % 3]);
+            wrote = true;
+        } else if constexpr (ONE) {
 #pragma unroll
             for (int f = 0; f < NF; ++f) s_sh[t * RS + f] = Yb[f / 3] * gc[f % 3];
             wrote = true;
@@ -646,6 +675,8 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(SceneDev sc, const 
     }
     }  // g < n
     if constexpr (ONE) {
+        // a row copied in but not replaced (no tile reached): its copy lands first
+        if (staged) asm volatile("cp.async.wait_all;" ::: "memory");
         if (!wrote)
             for (int f = 0; f < NF; ++f) s_sh[t * RS + f] = 0.f;
         __syncthreads();
