@@ -141,6 +141,11 @@ __device__ __forceinline__ void raster_unit(uint32_t item, const uint32_t* __res
     constexpr bool WHOLE = GW % PW == 0 && GH % PH == 0;  // a group is one or more whole thread blocks
     static_assert(NT % 32 == 0 && kBlockW * kBlockH == 32, "whole warps; one mask word per block entry");
     __shared__ float4 s0[NT], s1[NT], s2[NT];
+    // CR with whole-thread groups: the leader tests read the fields they need
+    // field by field (negated mean, conic, offset, threshold), four records
+    // per vector load, and evaluate two records per packed FP32 instruction.
+    constexpr bool LEAD2 = CR && WHOLE;
+    __shared__ __align__(16) float sL[LEAD2 ? 7 : 1][LEAD2 ? NT : 4];
     __shared__ uint32_t s_idx[WIN];          // block binning: list indices of the window's tile entries
     __shared__ uint32_t s_wsum[NT / 32];
 
@@ -221,6 +226,23 @@ __device__ __forceinline__ void raster_unit(uint32_t item, const uint32_t* __res
         }
         return r;
     };
+    // thread t stages record r in slot t
+    auto stage = [&](uint32_t r) {
+        const float4 v0 = __ldg(rec + (size_t)kRecF4 * r);
+        const float4 v1 = __ldg(rec + (size_t)kRecF4 * r + 1);
+        s0[t] = v0;
+        s1[t] = v1;
+        s2[t] = __ldg(rec + (size_t)kRecF4 * r + 2);
+        if constexpr (LEAD2) {
+            sL[0][t] = -v0.x;  // lx0 + (-mx) is lx0 - mx exactly
+            sL[1][t] = -v0.y;
+            sL[2][t] = v0.z;
+            sL[3][t] = v0.w;
+            sL[4][t] = v1.x;
+            sL[5][t] = v1.y;
+            sL[6][t] = v1.z;
+        }
+    };
     const float fx0 = (float)bx + 0.5f, fy0 = (float)by + 0.5f;
     // the leader pixel of the group holding this thread's block (WHOLE groups)
     const float lx0 = (float)(bx / GW * GW) + 0.5f, ly0 = (float)(by / GH * GH) + 0.5f;
@@ -237,12 +259,7 @@ __device__ __forceinline__ void raster_unit(uint32_t item, const uint32_t* __res
         if (!BLOCKS) {
             if (cursor >= cursor_end) break;
             const uint32_t j = cursor + t;
-            if (j < rg.y) {
-                const uint32_t r = record_of(j);
-                s0[t] = __ldg(rec + (size_t)kRecF4 * r);
-                s1[t] = __ldg(rec + (size_t)kRecF4 * r + 1);
-                s2[t] = __ldg(rec + (size_t)kRecF4 * r + 2);
-            }
+            if (j < rg.y) stage(record_of(j));
             cnt = (int)min((uint32_t)NT, rg.y - cursor);
             cursor += NT;
             __syncthreads();
@@ -293,12 +310,7 @@ __device__ __forceinline__ void raster_unit(uint32_t item, const uint32_t* __res
                 if (n_idx == 0) continue;
             }
             cnt = min(NT, n_idx - idx_pos);
-            if (t < cnt) {
-                const uint32_t r = record_of(s_idx[idx_pos + t]);
-                s0[t] = __ldg(rec + (size_t)kRecF4 * r);
-                s1[t] = __ldg(rec + (size_t)kRecF4 * r + 1);
-                s2[t] = __ldg(rec + (size_t)kRecF4 * r + 2);
-            }
+            if (t < cnt) stage(record_of(s_idx[idx_pos + t]));
             idx_pos += cnt;
             __syncthreads();
         }
@@ -311,20 +323,41 @@ __device__ __forceinline__ void raster_unit(uint32_t item, const uint32_t* __res
             // thread's pixels (branch-free over the pixels: almost every pixel
             // of a kept Gaussian blends, and their chains interleave).
             if (all_stopped()) continue;
+            const float2 L2x = make_float2(lx0, lx0), L2y = make_float2(ly0, ly0);
             for (int c0 = 0; c0 < cnt; c0 += 32) {
                 const int n32 = min(32, cnt - c0);
+                // the leader's exponent for all 32 slots, two records per
+                // packed instruction: each lane rounds as the scalar
+                // fma(fma(a, dx, b dy), dx, fma(c dy, dy, off)) does, so the
+                // decisions are those of the scalar form bit for bit; slots
+                // past the batch hold stale values and are masked off
                 uint32_t pass = 0;
+#pragma unroll 1
+                for (int i = 0; i < 32; i += 4) {
+                    const float4 nx = *reinterpret_cast<const float4*>(&sL[0][c0 + i]);
+                    const float4 ny = *reinterpret_cast<const float4*>(&sL[1][c0 + i]);
+                    const float4 ca = *reinterpret_cast<const float4*>(&sL[2][c0 + i]);
+                    const float4 cb2 = *reinterpret_cast<const float4*>(&sL[3][c0 + i]);
+                    const float4 cc = *reinterpret_cast<const float4*>(&sL[4][c0 + i]);
+                    const float4 of = *reinterpret_cast<const float4*>(&sL[5][c0 + i]);
+                    const float4 th = *reinterpret_cast<const float4*>(&sL[6][c0 + i]);
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    if (i < n32) {
-                        const float4 A = s0[c0 + i];
-                        const float4 B = s1[c0 + i];
-                        const float dx = lx0 - A.x, dy = ly0 - A.y;
-                        const float e0 = fmaf(fmaf(A.z, dx, A.w * dy), dx, fmaf(B.x * dy, dy, B.y));
-                        if (COUNT) ++n_lead;
-                        pass |= e0 >= B.z ? 1u << i : 0u;
+                    for (int h = 0; h < 2; ++h) {
+                        const float2 X = h ? make_float2(nx.z, nx.w) : make_float2(nx.x, nx.y);
+                        const float2 Y = h ? make_float2(ny.z, ny.w) : make_float2(ny.x, ny.y);
+                        const float2 Ca = h ? make_float2(ca.z, ca.w) : make_float2(ca.x, ca.y);
+                        const float2 Cb = h ? make_float2(cb2.z, cb2.w) : make_float2(cb2.x, cb2.y);
+                        const float2 Cc2 = h ? make_float2(cc.z, cc.w) : make_float2(cc.x, cc.y);
+                        const float2 Of = h ? make_float2(of.z, of.w) : make_float2(of.x, of.y);
+                        const float2 Th = h ? make_float2(th.z, th.w) : make_float2(th.x, th.y);
+                        const float2 dx = __fadd2_rn(L2x, X), dy = __fadd2_rn(L2y, Y);
+                        const float2 e0 = __ffma2_rn(__ffma2_rn(Ca, dx, __fmul2_rn(Cb, dy)), dx,
+                                                     __ffma2_rn(__fmul2_rn(Cc2, dy), dy, Of));
+                        pass |= (e0.x >= Th.x ? 1u << (i + 2 * h) : 0u) | (e0.y >= Th.y ? 2u << (i + 2 * h) : 0u);
                     }
                 }
+                if (n32 < 32) pass &= (1u << n32) - 1u;
+                if (COUNT) n_lead += (uint32_t)n32;
                 while (pass != 0u) {
                     const int k = c0 + __ffs(pass) - 1;
                     pass &= pass - 1u;
@@ -350,7 +383,11 @@ __device__ __forceinline__ void raster_unit(uint32_t item, const uint32_t* __res
                     };
                     if (Cc.w != 0.f) pixels(std::true_type{});
                     else pixels(std::false_type{});
-                    if (all_stopped()) break;
+                    // with four or more pixels a thread leaves its kept list
+                    // once they have all stopped (a stopped pixel never
+                    // blends again, so with fewer the test costs more than
+                    // the rest of the batch's kept list)
+                    if (NP >= 4 && all_stopped()) break;
                 }
                 if (all_stopped()) break;
             }
