@@ -658,6 +658,24 @@ def run_gpu(args):
     clock_info = clocks.stop()
     t_plain = timed(plain_opts)
     t_async = timed(cr_async)
+    # per-stage device times (CUDA events inside the library, same stream),
+    # taken before the batched call below grows the instance capacity, so
+    # that the sorts run on the grids of the timed single-view frames
+    stage = {}
+    n_prof = max(3, min(args.steps, 10))
+    for i in range(n_prof):
+        r.set_cameras([cams[view_of(i, rank, ws, len(cams))]])
+        r.render(mode="cr", opacity_filter=True, profile=True)
+        for k, v in r.last_stats["stage_ms"].items():
+            stage[k] = stage.get(k, 0.0) + v / n_prof
+    kernels_per_frame = r.last_stats["n_kernels"]
+    n_vis, K = r.last_stats["n_visible"], r.last_stats["n_instances"]
+    stage_plain = {}
+    for i in range(n_prof):
+        r.set_cameras([cams[view_of(i, rank, ws, len(cams))]])
+        r.render(mode="plain", profile=True)
+        for k, v in r.last_stats["stage_ms"].items():
+            stage_plain[k] = stage_plain.get(k, 0.0) + v / n_prof
     # the 8 orbit views of the workload as one batched call per step (one
     # frame pass over all cameras; frames/s counts every view)
     batch_cams = [cams[(rank * 8 + j) % len(cams)] for j in range(8)]
@@ -721,22 +739,6 @@ def run_gpu(args):
     fps_plain = frames / t_plain_max
     fps_async = frames / _max_over_ranks(dist, t_async)
 
-    # per-stage device times (CUDA events inside the library, same stream)
-    stage = {}
-    n_prof = max(3, min(args.steps, 10))
-    for i in range(n_prof):
-        r.set_cameras([cams[view_of(i, rank, ws, len(cams))]])
-        r.render(mode="cr", opacity_filter=True, profile=True)
-        for k, v in r.last_stats["stage_ms"].items():
-            stage[k] = stage.get(k, 0.0) + v / n_prof
-    kernels_per_frame = r.last_stats["n_kernels"]
-    n_vis, K = r.last_stats["n_visible"], r.last_stats["n_instances"]
-    stage_plain = {}
-    for i in range(n_prof):
-        r.set_cameras([cams[view_of(i, rank, ws, len(cams))]])
-        r.render(mode="plain", profile=True)
-        for k, v in r.last_stats["stage_ms"].items():
-            stage_plain[k] = stage_plain.get(k, 0.0) + v / n_prof
     # algorithmic work of the rasterizer (counting variant, untimed)
     r.set_cameras([cams[rank % len(cams)]])
     r.render(mode="cr", opacity_filter=True, count=True)

@@ -349,16 +349,25 @@ void launch_tile_expand(const uint32_t* rec_ids, const uint32_t* mask, const uin
 // entries of its block list with one load when none of them reaches it.
 __global__ void mask_summary_kernel(const uint32_t* __restrict__ mask, const DeviceStatus* __restrict__ st,
                                     uint32_t* __restrict__ summary, uint32_t max_groups) {
+    constexpr int kInFlight = 8;  // groups per warp with their loads issued together
     pdl_enter();
     const uint32_t n = st->error == kOk ? st->n_inst_valid : 0u;
-    const uint32_t groups = (n + 31) / 32;
+    const uint32_t groups = min((n + 31) / 32, max_groups);
     const int lane = threadIdx.x & 31;
-    for (uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < groups && g < max_groups;
-         g += (gridDim.x * blockDim.x) >> 5) {
-        const uint32_t j = 32 * g + lane;
-        const uint32_t m = j < n ? __ldg(mask + j) : 0u;
-        const uint32_t o = __reduce_or_sync(0xffffffffu, m);
-        if (lane == 0) summary[g] = o;
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t g0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g0 < groups; g0 += kInFlight * warps) {
+        uint32_t m[kInFlight];
+#pragma unroll
+        for (int q = 0; q < kInFlight; ++q) {
+            const uint32_t j = 32 * (g0 + q * warps) + lane;
+            m[q] = j < n ? __ldg(mask + j) : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < kInFlight; ++q) {
+            const uint32_t g = g0 + q * warps;
+            const uint32_t o = __reduce_or_sync(0xffffffffu, m[q]);
+            if (lane == 0 && g < groups) summary[g] = o;
+        }
     }
 }
 
