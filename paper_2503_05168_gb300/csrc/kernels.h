@@ -30,9 +30,12 @@ void launch_scan_tiles(const uint32_t* cnt_sorted, uint32_t* chunk_sum, uint32_t
                        DeviceStatus* st, uint32_t capacity, cudaStream_t s);
 
 // Exclusive scan of a rows x stride row-major count matrix given its row
-// totals (no look-back); a radix pass has 256 rows, one per digit.
+// totals (no look-back); a radix pass has 256 rows, one per digit.  With
+// count_ptr the matrix is dense: its stride is ceil(*count_ptr / col_items)
+// (at least 1; the launch's stride is the maximum) and the rest is not read.
 void launch_digit_scan(const uint32_t* in, uint32_t stride, const uint32_t* row_total, uint32_t* out,
-                       cudaStream_t s, uint32_t rows = 256);
+                       cudaStream_t s, uint32_t rows = 256, const uint32_t* count_ptr = nullptr,
+                       uint32_t col_items = 1);
 // Single-pass scan with decoupled look-back (in 16-byte aligned).  status:
 // one word per block (exclusive_scan_blocks), entries of other epochs read as
 // unpublished; st->ticket[ticket] must be zero.  spin_limit: polls of a

@@ -282,11 +282,16 @@ __global__ void __launch_bounds__(kScanThreads) scan_tiles_kernel(const uint32_t
 __global__ void __launch_bounds__(kScanThreads) digit_scan_kernel(const uint32_t* __restrict__ in, uint32_t stride,
                                                                   uint32_t rows,
                                                                   const uint32_t* __restrict__ row_total,
-                                                                  uint32_t* __restrict__ out) {
+                                                                  uint32_t* __restrict__ out,
+                                                                  const uint32_t* __restrict__ count_ptr,
+                                                                  uint32_t col_items) {
     __shared__ uint32_t s_part[kScanThreads / 32];
     pdl_enter();
+    // a dense matrix: one column per col_items of the device count
+    if (count_ptr != nullptr) stride = max((*count_ptr + col_items - 1u) / col_items, 1u);
     const uint32_t n = rows * stride;
     const uint32_t first = blockIdx.x * kScanTile;
+    if (first >= n) return;
     const uint32_t base = first + threadIdx.x * kScanItems;
     uint32_t c[kScanItems];
     if (base + kScanItems <= n) {
@@ -366,9 +371,10 @@ __global__ void __launch_bounds__(kScanThreads) exclusive_scan_kernel(const uint
 }
 
 void launch_digit_scan(const uint32_t* in, uint32_t stride, const uint32_t* row_total, uint32_t* out,
-                       cudaStream_t s, uint32_t rows) {
+                       cudaStream_t s, uint32_t rows, const uint32_t* count_ptr, uint32_t col_items) {
     const uint32_t blocks = std::max<uint32_t>((rows * stride + kScanTile - 1) / kScanTile, 1u);
-    launch_pdl(digit_scan_kernel, dim3(blocks), dim3(kScanThreads), 0, s, in, stride, rows, row_total, out);
+    launch_pdl(digit_scan_kernel, dim3(blocks), dim3(kScanThreads), 0, s, in, stride, rows, row_total, out,
+               count_ptr, count_ptr ? col_items : 1u);
 }
 
 void launch_exclusive_scan(const uint32_t* in, uint32_t n, uint32_t* out, uint64_t* status, uint32_t epoch,

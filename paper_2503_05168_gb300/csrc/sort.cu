@@ -23,8 +23,11 @@
 // lays out each record's instance count in depth order (SortGather).
 //
 // Element counts live on the device (they are produced by the previous
-// kernel), so grids are sized for the capacity and surplus tiles write
-// nothing but zero counts.
+// kernel), so grids are sized for the capacity.  In the render path's sorts
+// the count matrix is dense in the tiles that hold elements: its stride is
+// ceil(n / 4096) for the device count n, which the upsweep, the scan and the
+// downsweep each derive from the same word, and surplus tiles return at once
+// (no zero counts written or scanned for the unused capacity).
 #include <algorithm>
 #include <type_traits>
 
@@ -42,11 +45,17 @@ constexpr int kWarps = kSortThreads / 32;
 // Per-tile digit counts, digit-major.  Counting ignores order, so each thread
 // reads 16 consecutive keys with vector loads and adds them to its warp's
 // shared counters.  RB: digit width in bits.
+// The count matrix's stride: the launch's (grid) stride, or with `dense` the
+// number of tiles that hold elements.
+__device__ __forceinline__ uint32_t count_stride(uint32_t n, uint32_t stride, int dense) {
+    return dense ? max((n + (uint32_t)kSortTile - 1u) / (uint32_t)kSortTile, 1u) : stride;
+}
+
 template <typename KeyT, int RB>
 __global__ void __launch_bounds__(kSortThreads) upsweep_kernel(const KeyT* __restrict__ keys,
                                                                const uint32_t* __restrict__ count_ptr, int shift,
                                                                uint32_t* __restrict__ counts, uint32_t stride,
-                                                               uint32_t* __restrict__ row_total) {
+                                                               uint32_t* __restrict__ row_total, int dense) {
     static_assert(kSortItems * sizeof(KeyT) % 16 == 0, "vector loads");
     constexpr uint32_t R = 1u << RB;
     static_assert(R % kSortThreads == 0, "whole digits per thread");
@@ -54,6 +63,8 @@ __global__ void __launch_bounds__(kSortThreads) upsweep_kernel(const KeyT* __res
     pdl_enter();
     const uint32_t tile = blockIdx.x;
     const uint32_t n = *count_ptr;
+    stride = count_stride(n, stride, dense);
+    if (tile >= stride) return;  // surplus tile of a dense matrix
     const int w = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < kWarps * (int)R; i += kSortThreads) (&s_w[0][0])[i] = 0;
     __syncthreads();
@@ -97,7 +108,7 @@ __global__ void __launch_bounds__(kSortThreads) downsweep_kernel(const KeyT* __r
                                                                  uint32_t* __restrict__ run_end,
                                                                  const uint32_t* __restrict__ aux_in,
                                                                  uint32_t* __restrict__ aux_out,
-                                                                 SortGather gather) {
+                                                                 SortGather gather, int dense) {
     constexpr uint32_t R = 1u << RB;
     constexpr int DPT = (int)R / kSortThreads;
     static_assert(DPT >= 1 && (int)R == DPT * kSortThreads, "whole digits per thread");
@@ -115,6 +126,7 @@ __global__ void __launch_bounds__(kSortThreads) downsweep_kernel(const KeyT* __r
     const uint32_t tile = blockIdx.x;
     const uint32_t n = *count_ptr;
     if (tile * (uint32_t)kSortTile >= n) return;
+    stride = count_stride(n, stride, dense);
     const uint32_t t0 = threadIdx.x * DPT;  // this thread's first digit
     for (int i = threadIdx.x; i < kWarps * (int)(R + 1); i += kSortThreads) (&s_wcount[0][0])[i] = 0;
 #pragma unroll
@@ -257,7 +269,7 @@ uint32_t sort_tile_items() { return kSortTile; }
 // Single passes of the sort, for callers that manage their own buffers.
 void launch_radix_upsweep_u32(const uint32_t* keys, const uint32_t* count_ptr, int shift, uint32_t* counts,
                               uint32_t stride, cudaStream_t s) {
-    upsweep_kernel<uint32_t, 8><<<stride, kSortThreads, 0, s>>>(keys, count_ptr, shift, counts, stride, nullptr);
+    upsweep_kernel<uint32_t, 8><<<stride, kSortThreads, 0, s>>>(keys, count_ptr, shift, counts, stride, nullptr, 0);
 }
 
 void launch_radix_downsweep_u32(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
@@ -267,11 +279,11 @@ void launch_radix_downsweep_u32(const uint32_t* keys_in, const uint32_t* vals_in
     if (keys_out)
         downsweep_kernel<uint32_t, true, false, 8><<<stride, kSortThreads, 0, s>>>(
             keys_in, vals_in, keys_out, vals_out, count_ptr, shift, nbits, offsets, stride, run_start, run_end,
-            nullptr, nullptr, SortGather{});
+            nullptr, nullptr, SortGather{}, 0);
     else
         downsweep_kernel<uint32_t, false, false, 8><<<stride, kSortThreads, 0, s>>>(
             keys_in, vals_in, keys_out, vals_out, count_ptr, shift, nbits, offsets, stride, run_start, run_end,
-            nullptr, nullptr, SortGather{});
+            nullptr, nullptr, SortGather{}, 0);
 }
 
 int radix_last_bits(int key_bits, int key_bytes) {
@@ -288,7 +300,7 @@ static void launch_downsweep(KeyT* keys[2], uint32_t* vals[2], uint32_t* const* 
                              uint32_t* rs, uint32_t* re, const SortGather& gather, cudaStream_t s) {
     launch_pdl(downsweep_kernel<KeyT, WK, AUX, RB>, dim3(stride), dim3(kSortThreads), 0, s, keys[a], vals[a], keys[b],
                vals[b], count_ptr, shift, nbits, offsets, stride, rs, re, AUX ? aux[a] : nullptr,
-               AUX ? aux[b] : nullptr, gather);
+               AUX ? aux[b] : nullptr, gather, 1);
 }
 
 template <typename KeyT, int RB>
@@ -297,8 +309,8 @@ static void launch_pass(KeyT* keys[2], uint32_t* vals[2], uint32_t* const* aux, 
                         uint32_t* totals, uint32_t stride, uint32_t* rs, uint32_t* re, const SortGather& g,
                         cudaStream_t s) {
     launch_pdl(upsweep_kernel<KeyT, RB>, dim3(stride), dim3(kSortThreads), 0, s, keys[a], count_ptr, shift, counts,
-               stride, totals);
-    launch_digit_scan(counts, stride, totals, offsets, s, 1u << RB);
+               stride, totals, 1);
+    launch_digit_scan(counts, stride, totals, offsets, s, 1u << RB, count_ptr, kSortTile);
     if (aux) {
         if (wk) launch_downsweep<KeyT, true, true, RB>(keys, vals, aux, a, b, count_ptr, shift, nbits, offsets, stride,
                                                         rs, re, g, s);
