@@ -462,6 +462,18 @@ def test_capacity_growth_is_transparent(Renderer):
     ref, proj, _, gid, ranges = oracle.render(oracle.Scene64.from_scene(s), cam, oo, nthreads=8)
     rep = parity.check_render(imgs[0], Ts[0], ref, proj, gid, ranges, cam, oo)
     assert rep["ok"], str(rep)
+    # a small frame on the grown context: the sorts' grids and count matrices
+    # stay sized for the large capacity while only a few tiles hold elements
+    s2 = _f32(scene(rs.uniform(-1, 1, (3000, 3)) + [0, 0, 4], log_scales=[math.log(0.05)] * 3, opacity=0.6,
+                    dc=rs.uniform(-1, 1, (3000, 3))))
+    r.load_scene(s2)
+    for binning in ("tiles", "blocks"):
+        imgs, Ts = parity.gpu_render(r, binning=binning)
+        st = r.last_stats
+        assert st["retries"] == 0 and 0 < st["n_instances"] < (1 << 16) and st["capacity"] > (1 << 20), st
+        ref, proj, _, gid, ranges = oracle.render(oracle.Scene64.from_scene(s2), cam, oo, nthreads=8)
+        rep = parity.check_render(imgs[0], Ts[0], ref, proj, gid, ranges, cam, oo)
+        assert rep["ok"], (binning, str(rep))
     r.close()
 
 
